@@ -1,0 +1,188 @@
+"""Power mismatch, fast-decoupled matrices, branch flows and FDPF (FP64).
+
+Test infrastructure (see the package docstring).
+
+Network model (pi-model branch l = (i, j), no taps): series admittance
+y = 1/(r + jx) = g + j b_y with g = r/(r^2+x^2), b_y = -x/(r^2+x^2); half of
+the total charging b_sh sits at each end.  The bus admittance matrix
+Y = G + jB has Y_ij = -y and Y_ii = sum (y + j b_sh/2); G_ij and B_ij are the
+quantities of eqs. (1)-(3).
+
+Fast-decoupled matrices (eqs. (4)-(5); the paper names no variant, the XB
+form is used): B' is the Laplacian of the in-service branches weighted by
+1/x, B'' the Laplacian weighted by x/(r^2+x^2) (charging excluded).  B' is
+restricted to the non-slack buses of the main island, B'' to its PQ buses;
+both are grounded Laplacians, hence symmetric positive definite.
+
+FDPF (eqs. (4)-(5), Sec. III.B): starting from a given state, repeat
+  evaluate dP, dQ; stop when max|dP| (PV and PQ buses) and max|dQ| (PQ buses)
+  are both <= tol; solve B' dtheta = dP/V, theta += dtheta; evaluate dQ;
+  solve B'' dV = dQ/V, V += dV.
+Every solve here is direct (re-formed, fully factorised matrix), so the
+result is the exact AC solution up to the tolerance.
+
+Pins (tests): hand-solved two-bus case, the radial closed form (tree,
+lossless, all-PV: flows fixed by Kirchhoff's current law, angles by arcsin),
+Newton-Raphson on small cases, Sherman-Morrison/LODF for the first post-outage
+P-theta solve, the power-balance and KCL invariants, the four-element
+difference of Sec. IV.B.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+from scipy.sparse import coo_matrix, csc_matrix
+from scipy.sparse.linalg import splu
+
+PQ, PV, SLACK = 0, 1, 2
+STATUS_OK, STATUS_MAXITER, STATUS_DIVERGED, STATUS_ISLAND_NO_GEN = 0, 1, 2, 3
+DIVERGE_LIMIT = 1.0e4   # p.u.; a mismatch above this is taken as divergence
+DENSE_MAX = 500          # direct solves use dense LU up to this size
+
+
+def series_admittance(r: np.ndarray, x: np.ndarray):
+    """(g, b_y) of y = 1/(r + jx)."""
+    d = r * r + x * x
+    return r / d, -x / d
+
+
+def ybus_entries(n_bus, f, t, r, x, b_sh, in_service):
+    """Summed nonzeros (row, col, G, B) of the bus admittance matrix."""
+    on = np.asarray(in_service, dtype=bool)
+    f, t, r, x, b_sh = f[on], t[on], r[on], x[on], b_sh[on]
+    g, b = series_admittance(r, x)
+    rows = np.concatenate([f, t, f, t])
+    cols = np.concatenate([t, f, f, t])
+    Gv = np.concatenate([-g, -g, g, g])
+    Bv = np.concatenate([-b, -b, b + 0.5 * b_sh, b + 0.5 * b_sh])
+    # diagonal entries for every bus, so isolated buses still appear
+    rows = np.concatenate([rows, np.arange(n_bus)])
+    cols = np.concatenate([cols, np.arange(n_bus)])
+    Gv = np.concatenate([Gv, np.zeros(n_bus)])
+    Bv = np.concatenate([Bv, np.zeros(n_bus)])
+    Gm = coo_matrix((Gv, (rows, cols)), shape=(n_bus, n_bus)).tocsr()
+    Bm = coo_matrix((Bv, (rows, cols)), shape=(n_bus, n_bus)).tocsr()
+    Gm.sum_duplicates()
+    Bm.sum_duplicates()
+    Gc, Bc = Gm.tocoo(), Bm.tocoo()
+    return Gc.row, Gc.col, Gc.data, Bc.data
+
+
+def mismatch(ybus, P_sched, Q_sched, theta, V):
+    """dP_i and dQ_i of eq. (1) (and its reactive counterpart), all buses.
+
+    dP_i = P_is - |V_i| sum_j |V_j| (G_ij cos th_ij + B_ij sin th_ij)
+    dQ_i = Q_is - |V_i| sum_j |V_j| (G_ij sin th_ij - B_ij cos th_ij)
+    with th_ij = th_i - th_j; the j = i term is the self term |V_i|^2 G_ii of
+    eq. (2) (and -|V_i|^2 B_ii for Q).
+    """
+    row, col, Gv, Bv = ybus
+    n = V.shape[0]
+    th = theta[row] - theta[col]
+    c, s = np.cos(th), np.sin(th)
+    vv = V[row] * V[col]
+    P = np.bincount(row, weights=vv * (Gv * c + Bv * s), minlength=n)
+    Q = np.bincount(row, weights=vv * (Gv * s - Bv * c), minlength=n)
+    return P_sched - P, Q_sched - Q
+
+
+def laplacian(n_bus, f, t, w, in_service, keep):
+    """Weighted Laplacian of the in-service branches, rows/cols ``keep``."""
+    on = np.asarray(in_service, dtype=bool)
+    f, t, w = f[on], t[on], w[on]
+    rows = np.concatenate([f, t, f, t])
+    cols = np.concatenate([f, t, t, f])
+    vals = np.concatenate([w, w, -w, -w])
+    L = coo_matrix((vals, (rows, cols)), shape=(n_bus, n_bus)).tocsr()
+    L.sum_duplicates()
+    return L[keep][:, keep].tocsc()
+
+
+def bprime(n_bus, f, t, x, in_service, keep):
+    """B' (eq. (4)): branch weights 1/x."""
+    return laplacian(n_bus, f, t, 1.0 / x, in_service, keep)
+
+
+def bdprime(n_bus, f, t, r, x, in_service, keep):
+    """B'' (eq. (5)): branch weights x/(r^2+x^2), charging excluded."""
+    return laplacian(n_bus, f, t, x / (r * r + x * x), in_service, keep)
+
+
+class DirectSolver:
+    """Full factorisation of one matrix, reused for every right-hand side."""
+
+    def __init__(self, A):
+        self.n = A.shape[0]
+        if self.n == 0:
+            self.kind = "empty"
+        elif self.n <= DENSE_MAX:
+            self.kind = "dense"
+            self.lu = sla.lu_factor(A.toarray())
+        else:
+            self.kind = "sparse"
+            self.lu = splu(csc_matrix(A))
+
+    def solve(self, b):
+        if self.kind == "empty":
+            return b.copy()
+        if self.kind == "dense":
+            return sla.lu_solve(self.lu, b)
+        return self.lu.solve(b)
+
+
+def branch_flows(f, t, r, x, in_service, theta, V):
+    """Active power at both ends of every branch (zero when out of service).
+
+    P_ij = V_i^2 g - V_i V_j (g cos th_ij + b_y sin th_ij), P_ji likewise.
+    """
+    g, b = series_admittance(r, x)
+    th = theta[f] - theta[t]
+    Vf, Vt = V[f], V[t]
+    Pf = Vf * Vf * g - Vf * Vt * (g * np.cos(th) + b * np.sin(th))
+    Pt = Vt * Vt * g - Vf * Vt * (g * np.cos(th) - b * np.sin(th))
+    on = np.asarray(in_service, dtype=bool)
+    return np.where(on, Pf, 0.0), np.where(on, Pt, 0.0)
+
+
+def fdpf(grid, in_service, active, P_sched, theta0, V0, tol, max_outer):
+    """Fast-decoupled power flow on the buses marked ``active``.
+
+    ``active`` excludes islanded buses (they keep theta = V = 0).  Returns
+    (theta, V, outer_iterations, status, final_max_mismatch).
+    """
+    n = grid.n_bus
+    bt = grid.bus_type
+    pvpq = np.flatnonzero(active & (bt != SLACK))
+    pq = np.flatnonzero(active & (bt == PQ))
+    on = np.asarray(in_service, dtype=bool)
+    # a branch touching an inactive bus is not part of the main network
+    on = on & active[grid.f] & active[grid.t]
+    ybus = ybus_entries(n, grid.f, grid.t, grid.r, grid.x, grid.b_sh, on)
+    solP = DirectSolver(bprime(n, grid.f, grid.t, grid.x, on, pvpq))
+    solQ = DirectSolver(bdprime(n, grid.f, grid.t, grid.r, grid.x, on, pq))
+    theta = np.where(active, theta0, 0.0).astype(np.float64)
+    V = np.where(active, V0, 0.0).astype(np.float64)
+    Q_sched = grid.Q_sched
+    k = 0
+    while True:
+        dP, dQ = mismatch(ybus, P_sched, Q_sched, theta, V)
+        err = max(np.abs(dP[pvpq]).max(initial=0.0), np.abs(dQ[pq]).max(initial=0.0))
+        if not np.isfinite(err) or err > DIVERGE_LIMIT:
+            return theta, V, k, STATUS_DIVERGED, err
+        if err <= tol:
+            return theta, V, k, STATUS_OK, err
+        if k >= max_outer:
+            return theta, V, k, STATUS_MAXITER, err
+        theta[pvpq] += solP.solve(dP[pvpq] / V[pvpq])
+        dP, dQ = mismatch(ybus, P_sched, Q_sched, theta, V)
+        V[pq] += solQ.solve(dQ[pq] / V[pq])
+        k += 1
+
+
+def base_case(grid, tol=1e-10, max_outer=100):
+    """FDPF of the intact grid from a flat start (theta = 0, |V| = V_set)."""
+    n = grid.n_bus
+    on = np.ones(grid.n_branch, dtype=bool)
+    active = np.ones(n, dtype=bool)
+    return fdpf(grid, on, active, grid.P_sched.astype(np.float64), np.zeros(n),
+                grid.V_set.astype(np.float64), tol, max_outer)

@@ -1,0 +1,95 @@
+"""The N-1 screen (Sec. IV.A): one scenario per single-branch outage.
+
+Test infrastructure (see the package docstring).
+
+For outage l: remove branch l; find the islands (Sec. IV.C); re-dispatch the
+islands' injection over the main island; run the FDPF on the main island
+starting from the base-case state (warm start, Sec. III.B); compute branch
+flows and the loading max(|P_ij|, |P_ji|)/rating of every branch.  Islanded
+buses report theta = V = 0, their branches zero flow.
+"""
+from __future__ import annotations
+
+import multiprocessing as mp
+import os
+
+import numpy as np
+
+from .islands import components, island_mask
+from .powerflow import (STATUS_ISLAND_NO_GEN, STATUS_OK, branch_flows,
+                        fdpf, mismatch, ybus_entries)
+from .redispatch import redispatch
+
+
+def outage_setup(grid, l):
+    """(in_service, labels, islanded mask, re-dispatched P_sched, no_gen)."""
+    on = np.ones(grid.n_branch, dtype=bool)
+    if l >= 0:
+        on[l] = False
+    label = components(grid.n_bus, grid.f, grid.t, on)
+    isl = island_mask(label, grid.slack)
+    P, no_gen = redispatch(grid.bus_type, grid.P_sched, grid.P_gen, isl)
+    return on, label, isl, P, no_gen
+
+
+def solve_outage(grid, theta0, V0, l, tol, max_outer):
+    on, label, isl, P, no_gen = outage_setup(grid, l)
+    active = ~isl
+    theta, V, k, status, err = fdpf(grid, on, active, P, theta0, V0, tol, max_outer)
+    live = on & active[grid.f] & active[grid.t]
+    Pf, Pt = branch_flows(grid.f, grid.t, grid.r, grid.x, live, theta, V)
+    loading = np.maximum(np.abs(Pf), np.abs(Pt)) / grid.rating
+    if status == STATUS_OK and no_gen:
+        status = STATUS_ISLAND_NO_GEN
+    return dict(theta=theta, V=V, flow=Pf, flow_to=Pt, label=label, outer=k,
+                status=status, max_loading=float(loading.max(initial=0.0)),
+                n_overload=int((loading > 1.0).sum()), err=err,
+                islanded=bool(isl.any()))
+
+
+def scenario_mismatch(grid, l, theta, V):
+    """Max |dP| (non-slack buses) and |dQ| (PQ buses) of the main island for
+    outage ``l`` at the given state: an independent check of any solver's
+    answer."""
+    on, label, isl, P, _ = outage_setup(grid, l)
+    active = ~isl
+    live = on & active[grid.f] & active[grid.t]
+    yb = ybus_entries(grid.n_bus, grid.f, grid.t, grid.r, grid.x, grid.b_sh, live)
+    dP, dQ = mismatch(yb, P, grid.Q_sched, np.where(active, theta, 0.0),
+                      np.where(active, V, 0.0))
+    bt = grid.bus_type
+    a = np.abs(dP[active & (bt != 2)]).max(initial=0.0)
+    b = np.abs(dQ[active & (bt == 0)]).max(initial=0.0)
+    return max(a, b)
+
+
+def _worker(args):
+    grid, theta0, V0, ls, tol, max_outer = args
+    return [solve_outage(grid, theta0, V0, int(l), tol, max_outer) for l in ls]
+
+
+def n1_screen(grid, theta0, V0, outages, tol=1e-4, max_outer=50, processes=None):
+    """Solve every outage in ``outages``; returns stacked result arrays."""
+    outages = np.asarray(outages, dtype=np.int64)
+    S = outages.shape[0]
+    if processes is None:
+        processes = len(os.sched_getaffinity(0))
+    processes = max(1, min(processes, S))
+    if processes == 1 or S < 8:
+        res = _worker((grid, theta0, V0, outages, tol, max_outer))
+    else:
+        chunks = np.array_split(outages, processes * 4)
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(processes) as pool:
+            parts = pool.map(_worker, [(grid, theta0, V0, c, tol, max_outer)
+                                       for c in chunks if c.size])
+        res = [r for p in parts for r in p]
+    out = {}
+    for key in ("theta", "V", "flow", "flow_to", "label"):
+        out[key] = np.stack([r[key] for r in res]) if S else np.zeros((0, 0))
+    for key, dt in (("outer", np.int32), ("status", np.int32),
+                    ("max_loading", np.float64), ("n_overload", np.int32),
+                    ("err", np.float64), ("islanded", bool)):
+        out[key] = np.asarray([r[key] for r in res], dtype=dt)
+    out["processes"] = processes
+    return out

@@ -1,0 +1,401 @@
+"""Pins of the CPU oracle against closed forms, invariants, brute force and
+an independent Newton-Raphson solve (no GPU needed)."""
+import itertools
+
+import numpy as np
+import pytest
+
+from cases import load_case, random_tree_grid, grid_from_arrays
+from gridgen import config_grid
+from oracle import factor, islands, powerflow as pf, redispatch, screen
+
+
+# ---------------------------------------------------------------- closed forms
+def test_two_bus_closed_form():
+    g, d = load_case("two_bus.json")
+    th, V, k, st, err = pf.base_case(g, tol=1e-13)
+    assert st == pf.STATUS_OK
+    exp = -np.arcsin(0.8 * 0.25 / (1.03 * 0.98))
+    assert abs(th[1] - exp) < 1e-12
+    assert V[0] == 1.03 and V[1] == 0.98
+
+
+def radial_angles(g, parent, in_service=None):
+    """Exact angles of a lossless tree whose non-slack buses are all PV:
+    the flow into each subtree is minus its summed injection (KCL) and
+    P_pc = V_p V_c sin(th_p - th_c)/x (eq. (1) with G = 0)."""
+    n = g.n_bus
+    children = [[] for _ in range(n)]
+    edge_x = {}
+    for e in range(g.n_branch):
+        if in_service is not None and not in_service[e]:
+            continue
+        a, b = int(g.f[e]), int(g.t[e])
+        edge_x[(a, b)] = edge_x[(b, a)] = g.x[e]
+    # orient from the slack by BFS
+    root = g.slack
+    order, par = [root], {root: -1}
+    adj = {i: [] for i in range(n)}
+    for (a, b) in edge_x:
+        adj[a].append(b)
+    for u in order:
+        for v in adj[u]:
+            if v not in par:
+                par[v] = u
+                order.append(v)
+    sub = g.P_sched.astype(float).copy()
+    for u in reversed(order[1:]):
+        sub[par[u]] += sub[u]
+    th = np.zeros(n)
+    V = g.V_set
+    for u in order[1:]:
+        p = par[u]
+        F = -sub[u]  # power flowing from p into the subtree of u
+        th[u] = th[p] - np.arcsin(F * edge_x[(p, u)] / (V[p] * V[u]))
+    return th
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_radial_closed_form(seed):
+    g, parent = random_tree_grid(40, seed)
+    th, V, k, st, err = pf.base_case(g, tol=1e-13)
+    assert st == pf.STATUS_OK
+    np.testing.assert_allclose(th, radial_angles(g, parent), rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("l", range(5))
+def test_ring_outage_becomes_radial(l):
+    g, _ = load_case("five_bus_ring.json")
+    th0, V0, _, st, _ = pf.base_case(g, tol=1e-13)
+    assert st == pf.STATUS_OK
+    r = screen.solve_outage(g, th0, V0, l, tol=1e-13, max_outer=100)
+    on = np.ones(g.n_branch, bool)
+    on[l] = False
+    assert r["status"] == pf.STATUS_OK and not r["islanded"]
+    np.testing.assert_allclose(r["theta"], radial_angles(g, None, on), atol=1e-11)
+    assert r["flow"][l] == 0.0
+
+
+# ------------------------------------------------------- independent Newton
+def newton_solution(g, tol=1e-13):
+    """Newton-Raphson on S = V conj(Y V) (complex form, finite-difference
+    Jacobian): an independent route to the AC fixed point."""
+    n = g.n_bus
+    Y = np.zeros((n, n), complex)
+    for e in range(g.n_branch):
+        i, j = int(g.f[e]), int(g.t[e])
+        y = 1.0 / (g.r[e] + 1j * g.x[e])
+        Y[i, j] -= y
+        Y[j, i] -= y
+        Y[i, i] += y + 0.5j * g.b_sh[e]
+        Y[j, j] += y + 0.5j * g.b_sh[e]
+    pvpq = np.flatnonzero(g.bus_type != 2)
+    pq = np.flatnonzero(g.bus_type == 0)
+
+    def F(z, th, V):
+        th = th.copy()
+        V = V.copy()
+        th[pvpq] = z[:len(pvpq)]
+        V[pq] = z[len(pvpq):]
+        Vc = V * np.exp(1j * th)
+        S = Vc * np.conj(Y @ Vc)
+        return np.r_[g.P_sched[pvpq] - S.real[pvpq], g.Q_sched[pq] - S.imag[pq]]
+
+    th = np.zeros(n)
+    V = g.V_set.astype(float).copy()
+    z = np.r_[th[pvpq], V[pq]]
+    for _ in range(50):
+        r = F(z, th, V)
+        if np.abs(r).max() < tol:
+            break
+        J = np.zeros((len(z), len(z)))
+        h = 1e-7
+        for c in range(len(z)):
+            dz = np.zeros(len(z))
+            dz[c] = h
+            J[:, c] = (F(z + dz, th, V) - F(z - dz, th, V)) / (2 * h)
+        z = z - np.linalg.solve(J, r)
+    th[pvpq] = z[:len(pvpq)]
+    V[pq] = z[len(pvpq):]
+    return th, V
+
+
+def test_lossy_case_matches_newton():
+    g, _ = load_case("five_bus_lossy.json")
+    th, V, k, st, err = pf.base_case(g, tol=1e-12)
+    assert st == pf.STATUS_OK and k > 2
+    thn, Vn = newton_solution(g)
+    np.testing.assert_allclose(th, thn, atol=1e-10)
+    np.testing.assert_allclose(V, Vn, atol=1e-10)
+
+
+def test_tree_with_pq_and_losses_matches_newton():
+    g, _ = random_tree_grid(12, 7, lossless=False, all_pv=False)
+    th, V, k, st, err = pf.base_case(g, tol=1e-12)
+    assert st == pf.STATUS_OK
+    thn, Vn = newton_solution(g)
+    np.testing.assert_allclose(th, thn, atol=1e-9)
+    np.testing.assert_allclose(V, Vn, atol=1e-9)
+
+
+def test_mismatch_zero_only_at_solution():
+    g, _ = load_case("five_bus_lossy.json")
+    thn, Vn = newton_solution(g)
+    yb = pf.ybus_entries(g.n_bus, g.f, g.t, g.r, g.x, g.b_sh, np.ones(g.n_branch, bool))
+    dP, dQ = pf.mismatch(yb, g.P_sched, g.Q_sched, thn, Vn)
+    assert np.abs(dP[1:]).max() < 1e-11 and np.abs(dQ[g.bus_type == 0]).max() < 1e-11
+    thp = thn.copy()
+    thp[3] += 1e-3
+    dP2, _ = pf.mismatch(yb, g.P_sched, g.Q_sched, thp, Vn)
+    assert np.abs(dP2[1:]).max() > 1e-3
+
+
+# ----------------------------------------------- outage algebra (Sec. IV.B)
+def test_sherman_morrison_first_solve():
+    """B'_s = B' - b a a^T (a = e_i - e_j): the solve with the re-formed
+    contingency matrix equals the rank-one update of the base solve."""
+    g = config_grid("grid120")
+    n = g.n_bus
+    keep = np.flatnonzero(g.bus_type != 2)
+    pos = -np.ones(n, int)
+    pos[keep] = np.arange(keep.size)
+    on = np.ones(g.n_branch, bool)
+    B0 = pf.bprime(n, g.f, g.t, g.x, on, keep).toarray()
+    rng = np.random.default_rng(3)
+    c = rng.standard_normal(keep.size)
+    base = np.linalg.solve(B0, c)
+    lab0 = islands.components(n, g.f, g.t, on)
+    tested = 0
+    for l in range(g.n_branch):
+        on_l = on.copy()
+        on_l[l] = False
+        if (islands.components(n, g.f, g.t, on_l) != lab0).any():
+            continue  # bridge: B'_s singular on the full bus set
+        a = np.zeros(keep.size)
+        if pos[g.f[l]] >= 0:
+            a[pos[g.f[l]]] = 1.0
+        if pos[g.t[l]] >= 0:
+            a[pos[g.t[l]]] = -1.0
+        b = 1.0 / g.x[l]
+        Ba = np.linalg.solve(B0, a)
+        sm = base + b * (a @ base) / (1.0 - b * (a @ Ba)) * Ba
+        Bs = pf.bprime(n, g.f, g.t, g.x, on_l, keep)
+        got = pf.DirectSolver(Bs).solve(c)
+        np.testing.assert_allclose(got, sm, rtol=1e-9, atol=1e-9 * np.abs(sm).max())
+        tested += 1
+    assert tested > 100
+
+
+def test_bridge_iff_ptdf_one():
+    """PTDF_ll = b_l a^T B'^{-1} a equals 1 exactly for bridges (the
+    Sherman-Morrison denominator vanishes: the contingency matrix of Table I's
+    'LU failure' cases is singular)."""
+    g = config_grid("grid120")
+    n = g.n_bus
+    keep = np.flatnonzero(g.bus_type != 2)
+    pos = -np.ones(n, int)
+    pos[keep] = np.arange(keep.size)
+    on = np.ones(g.n_branch, bool)
+    B0 = pf.bprime(n, g.f, g.t, g.x, on, keep).toarray()
+    Binv = np.linalg.inv(B0)
+    n_bridge = 0
+    for l in range(g.n_branch):
+        a = np.zeros(keep.size)
+        if pos[g.f[l]] >= 0:
+            a[pos[g.f[l]]] = 1.0
+        if pos[g.t[l]] >= 0:
+            a[pos[g.t[l]]] = -1.0
+        ptdf = a @ Binv @ a / g.x[l]
+        on_l = on.copy()
+        on_l[l] = False
+        bridge = len(set(islands.components(n, g.f, g.t, on_l))) > 1
+        n_bridge += bridge
+        if bridge:
+            assert abs(ptdf - 1.0) < 1e-9
+        else:
+            assert ptdf < 1.0 - 1e-6
+    assert n_bridge > 0
+
+
+def test_four_element_difference():
+    """Sec. IV.B: an outage changes exactly A_ii, A_jj, A_ij, A_ji of B'
+    (fewer when an endpoint is the slack; B'' only at PQ endpoints)."""
+    g = config_grid("grid120")
+    n = g.n_bus
+    on = np.ones(g.n_branch, bool)
+    keepP = np.flatnonzero(g.bus_type != 2)
+    keepQ = np.flatnonzero(g.bus_type == 0)
+    P0 = pf.bprime(n, g.f, g.t, g.x, on, keepP).toarray()
+    Q0 = pf.bdprime(n, g.f, g.t, g.r, g.x, on, keepQ).toarray()
+    for l in range(g.n_branch):
+        on_l = on.copy()
+        on_l[l] = False
+        dP = pf.bprime(n, g.f, g.t, g.x, on_l, keepP).toarray() - P0
+        dQ = pf.bdprime(n, g.f, g.t, g.r, g.x, on_l, keepQ).toarray() - Q0
+        endsP = sum(int(g.bus_type[b] != 2) for b in (g.f[l], g.t[l]))
+        endsQ = sum(int(g.bus_type[b] == 0) for b in (g.f[l], g.t[l]))
+        assert np.count_nonzero(np.abs(dP) > 1e-12) == endsP ** 2
+        assert np.count_nonzero(np.abs(dQ) > 1e-12) == endsQ ** 2
+
+
+# ------------------------------------------------------- islands (Sec. IV.C)
+def closure_labels(n, f, t, on):
+    R = np.eye(n, dtype=bool)
+    for e in range(len(f)):
+        if on[e]:
+            R[f[e], t[e]] = R[t[e], f[e]] = True
+    for k in range(n):  # Warshall
+        R = R | (R[:, [k]] & R[[k], :])
+    return np.array([int(np.flatnonzero(R[i])[0]) for i in range(n)])
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_islands_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(3, 11))
+    # random connected graph: a tree plus a few chords
+    f = [int(rng.integers(0, i)) for i in range(1, n)]
+    t = list(range(1, n))
+    for _ in range(int(rng.integers(0, n))):
+        a, b = sorted(rng.choice(n, 2, replace=False))
+        if (a, b) not in set(zip(f, t)) and (b, a) not in set(zip(f, t)):
+            f.append(int(a))
+            t.append(int(b))
+    f, t = np.array(f), np.array(t)
+    for l in range(len(f)):
+        on = np.ones(len(f), bool)
+        on[l] = False
+        np.testing.assert_array_equal(islands.components(n, f, t, on),
+                                      closure_labels(n, f, t, on))
+
+
+# ---------------------------------------------- invariants on full N-1 runs
+@pytest.fixture(scope="module")
+def grid120_n1():
+    g = config_grid("grid120")
+    th0, V0, _, st, _ = pf.base_case(g)
+    assert st == pf.STATUS_OK
+    res = screen.n1_screen(g, th0, V0, np.arange(g.n_branch), tol=1e-10, processes=1)
+    return g, res
+
+
+def test_n1_kcl_and_power_balance(grid120_n1):
+    g, res = grid120_n1
+    n = g.n_bus
+    ok = 0
+    for s in range(g.n_branch):
+        if res["status"][s] not in (pf.STATUS_OK, pf.STATUS_ISLAND_NO_GEN):
+            continue
+        on, label, isl, P, _ = screen.outage_setup(g, s)
+        net = np.zeros(n)
+        np.add.at(net, g.f, res["flow"][s])
+        np.add.at(net, g.t, res["flow_to"][s])
+        main = ~isl
+        nonslack = main & (g.bus_type != 2)
+        # KCL: the flows leaving a bus add up to its scheduled injection
+        assert np.abs(net[nonslack] - P[nonslack]).max() < 1e-9
+        # power balance: all injections = losses (sum of both-end flows)
+        losses = (res["flow"][s] + res["flow_to"][s]).sum()
+        slack_inj = net[g.slack]
+        assert abs(P[nonslack].sum() + slack_inj - losses) < 1e-9
+        assert np.all(res["theta"][s][isl] == 0) and np.all(res["V"][s][isl] == 0)
+        ok += 1
+    assert ok > 0.9 * g.n_branch
+
+
+def test_n1_islanding_handled(grid120_n1):
+    g, res = grid120_n1
+    isl = res["islanded"]
+    assert isl.any() and (~isl).any()
+    # every islanding scenario is solved after re-dispatch (Table I claim)
+    assert np.all(np.isin(res["status"][isl], [pf.STATUS_OK, pf.STATUS_ISLAND_NO_GEN]))
+
+
+def test_redispatch_conserves_main_island_injection():
+    g = config_grid("grid2k")
+    on = np.ones(g.n_branch, bool)
+    seen = 0
+    for l in range(g.n_branch):
+        on_l = on.copy()
+        on_l[l] = False
+        lab = islands.components(g.n_bus, g.f, g.t, on_l)
+        isl = islands.island_mask(lab, g.slack)
+        if not isl.any():
+            continue
+        P, no_gen = redispatch.redispatch(g.bus_type, g.P_sched, g.P_gen, isl)
+        if not no_gen:
+            assert abs(P[~isl].sum() - g.P_sched.sum()) < 1e-9
+        assert np.all(P[isl] == 0)
+        seen += 1
+        if seen > 40:
+            break
+    assert seen > 0
+
+
+@pytest.mark.parametrize("name", ["grid120", "grid2k", "grid10k"])
+def test_base_case_converges(name):
+    g = config_grid(name)
+    th, V, k, st, err = pf.base_case(g)
+    assert st == pf.STATUS_OK and err <= 1e-10
+
+
+# -------------------------------------------- incomplete Cholesky (eq. (6))
+def _lower_pattern(A):
+    A = A.tocsr()
+    return [sorted(int(c) for c in A.indices[A.indptr[i]:A.indptr[i + 1]] if c <= i)
+            for i in range(A.shape[0])]
+
+
+def test_ic0_reproduces_a_on_pattern():
+    g = config_grid("grid120")
+    keep = np.flatnonzero(g.bus_type != 2)
+    A = pf.bprime(g.n_bus, g.f, g.t, g.x, np.ones(g.n_branch, bool), keep)
+    pat = _lower_pattern(A)
+    L = factor.ic_on_pattern(A, pat)
+    Ld = factor.to_dense(L, A.shape[0])
+    Ad = A.toarray()
+    LLt = Ld @ Ld.T
+    for i, row in enumerate(pat):
+        for j in row:
+            assert abs(LLt[i, j] - Ad[i, j]) < 1e-10 * abs(Ad[i, i])
+    assert np.all(np.diag(Ld) > 0)
+
+
+def test_ic0_exact_on_tree_and_full_pattern():
+    g, _ = random_tree_grid(30, 4, lossless=False, all_pv=True)
+    keep = np.flatnonzero(g.bus_type != 2)
+    A = pf.bprime(g.n_bus, g.f, g.t, g.x, np.ones(g.n_branch, bool), keep)
+    # leaves-first ordering of a tree: IC(0) drops no fill
+    depth = np.zeros(g.n_bus, int)
+    for e in range(g.n_branch):
+        depth[g.t[e]] = depth[g.f[e]] + 1
+    order = np.argsort(-depth[keep], kind="stable")
+    Ao = A[order][:, order]
+    L = factor.to_dense(factor.ic_on_pattern(Ao, _lower_pattern(Ao)), Ao.shape[0])
+    np.testing.assert_allclose(L, np.linalg.cholesky(Ao.toarray()), atol=1e-12)
+    # meshed matrix: IC on the full symbolic pattern is the exact factor
+    m = config_grid("grid120")
+    keep = np.flatnonzero(m.bus_type != 2)
+    A = pf.bprime(m.n_bus, m.f, m.t, m.x, np.ones(m.n_branch, bool), keep)
+    full = factor.symbolic_cholesky(A.shape[0], _lower_pattern(A))
+    L = factor.to_dense(factor.ic_on_pattern(A, full), A.shape[0])
+    Lc = np.linalg.cholesky(A.toarray())
+    np.testing.assert_allclose(L, Lc, atol=1e-10)
+    # and the symbolic pattern holds every nonzero of the dense factor
+    mask = np.zeros_like(Lc, bool)
+    for i, row in enumerate(full):
+        mask[i, row] = True
+    assert np.abs(Lc[~mask]).max() < 1e-12
+
+
+def test_triangular_solves_invert():
+    rng = np.random.default_rng(0)
+    n = 25
+    M = np.tril(rng.uniform(-1, 1, (n, n)) * (rng.uniform(size=(n, n)) < 0.3))
+    M[np.diag_indices(n)] = rng.uniform(1, 2, n)
+    L = {i: {j: M[i, j] for j in range(i + 1) if M[i, j] != 0} for i in range(n)}
+    r = rng.standard_normal(n)
+    np.testing.assert_allclose(factor.forward(L, r), np.linalg.solve(M, r), atol=1e-12)
+    np.testing.assert_allclose(factor.backward(L, r), np.linalg.solve(M.T, r), atol=1e-12)
+    z = factor.apply_preconditioner(L, r)
+    np.testing.assert_allclose(M @ (M.T @ z), r, atol=1e-10)
