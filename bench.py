@@ -1,0 +1,318 @@
+"""Benchmark: N-1 scenarios/s of the batched GB300 screen on the 10,000-bus
+synthetic grid (every single-branch outage; mismatch <= 1e-4 p.u.).
+
+One step = one gpcg_n1_screen over all outages of the grid, with the grid,
+base case and outage list resident on the device.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpcg|reference]
+
+Under torchrun every rank screens the full outage list of its own copy of
+the grid (weak scaling: no data-path collective), rank 0 reports.  The
+reference arm (--impl reference) times the CPU oracle on the host cores on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "N-1 scenarios/sec at 10k buses (mismatch≤1e-4 p.u.), batched vs plain; HBM GB/s %"
+WORKLOAD = "grid10k"
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 4 + k and r[4 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def algorithmic_bytes(info, iters, w, n_bus, n_branch):
+    """Bytes the method must move per screen (per-unit figures: 15 w n per
+    inner PCG iteration, 32 n per outer half-iteration's FP64 mismatch,
+    16 n + 8 m for the flows, plus the shared matrix and factor bytes per
+    iteration amortised over the scenarios)."""
+    outer = iters[:, 0].astype(np.float64)
+    inP = iters[:, 1].astype(np.float64)
+    inQ = iters[:, 2].astype(np.float64)
+    S = iters.shape[0]
+    vec = 15.0 * w * (inP.sum() * info["n_p"] + inQ.sum() * info["n_q"])
+    mis = 32.0 * n_bus * (2.0 * outer + 1.0).sum()
+    flows = S * (16.0 * n_bus + 8.0 * n_branch)
+    mats = (inP.sum() * (info["nnz_p"] + 2 * info["nnz_lp"]) +
+            inQ.sum() * (info["nnz_q"] + 2 * info["nnz_lq"])) * (w + 4) / max(S, 1)
+    return vec + mis + flows + mats
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def run_gpcg(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1803_03290_gb300 as gp
+    from gridgen import config_grid
+
+    g = config_grid(args.config)
+    prec = {"fp32": gp.BATCHED_FP32, "fp64": gp.BATCHED_FP64}[args.precision]
+    pc = {"exact": gp.PRECOND_EXACT, "ic0": gp.PRECOND_IC0, "jacobi": gp.PRECOND_JACOBI}[args.precond]
+    c = gp.GPCG(g, precision=prec, precond=pc, tol=1e-4, tile=args.tile)
+    c.base_solve()
+    info = c.info()
+    S = g.n_branch if args.n_outages <= 0 else min(args.n_outages, g.n_branch)
+    outages = torch.arange(S, dtype=torch.int32, device=dev)
+    n, m = g.n_bus, g.n_branch
+    out = {
+        "theta": torch.empty((S, n), dtype=torch.float64, device=dev),
+        "V": torch.empty((S, n), dtype=torch.float64, device=dev),
+        "flow": torch.empty((S, m), dtype=torch.float64, device=dev),
+        "iters": torch.empty((S, 3), dtype=torch.int32, device=dev),
+        "status": torch.empty((S,), dtype=torch.int32, device=dev),
+        "max_loading": torch.empty((S,), dtype=torch.float64, device=dev),
+    }
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+    for _ in range(args.warmup):
+        c.n1_screen_device(outages, out, stream)
+    torch.cuda.synchronize()
+    step_ms, kern_ms = [], []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0.record(stream)
+            c.n1_screen_device(outages, out, stream)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+            kern_ms.append(c.last_timings())
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * S * args.steps / (total_ms / 1e3)
+    iters = out["iters"].cpu().numpy()
+    status = out["status"].cpu().numpy()
+
+    # end to end through the public C ABI with host buffers: outage list in,
+    # per-scenario screening results (status, iterations, max loading) out
+    hout = np.arange(S, dtype=np.int32)
+    e2e_ms = []
+    for k in range(args.steps + 1):
+        t0 = time.perf_counter()
+        r = c.n1_screen(hout, outputs=("iters", "status", "max_loading"))
+        dt = (time.perf_counter() - t0) * 1e3
+        if k:
+            e2e_ms.append(dt)
+    e2e = {"value": world * S / (statistics.mean(e2e_ms) / 1e3), "unit": "scenarios/s",
+           "h2d_bytes_per_step": int(hout.nbytes),
+           "d2h_bytes_per_step": int(r["iters"].nbytes + r["status"].nbytes +
+                                     r["max_loading"].nbytes)}
+
+    # plain per-scenario FP64 PCG on a sample (one scenario per launch sequence)
+    plain = None
+    if args.plain_sample > 0 and rank == 0:
+        c.set_options(precision=gp.PLAIN_FP64)
+        samp = np.random.default_rng(7).choice(S, args.plain_sample, replace=False).astype(np.int32)
+        c.n1_screen(samp[:4], outputs=("status",))
+        t0 = time.perf_counter()
+        c.n1_screen(samp, outputs=("status",))
+        dt = time.perf_counter() - t0
+        plain = {"value": args.plain_sample / dt, "unit": "scenarios/s",
+                 "sample": f"{args.plain_sample} seeded outages of {args.config}, FP64, one scenario per launch"}
+        c.set_options(precision=prec)
+
+    w = 4 if prec == gp.BATCHED_FP32 else 8
+    algo = algorithmic_bytes(info, iters, w, n, m)
+    fd_ms = statistics.mean(k[1] for k in kern_ms)
+    peak, peak_kind = load_peaks()
+    achieved = algo / (fd_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "kernel": "fdpf_tiles_kernel", "peak_source": peak_kind,
+            "algorithmic_bytes_per_launch": int(algo), "kernel_ms": round(fd_ms, 3),
+            "islands_kernel_ms": round(statistics.mean(k[0] for k in kern_ms), 3)}
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_sample > 0:
+        cpu = cpu_baseline(g, args.cpu_sample)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "scenarios/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if w == 4 else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.config}: {n} buses, {m} branches, {S} single-branch "
+                                   f"outages, tol 1e-4 p.u., {args.precond} base-case preconditioner, "
+                                   f"{args.precision} inner PCG, FP64 mismatch/flows",
+                       "n_bus": n, "n_branch": m, "scenarios": S, "tile": info["tile"],
+                       "l2": "flushed between steps (512 MiB write)",
+                       "precond": args.precond, "precision": args.precision},
+            "e2e": e2e, "gpu_launches": 2 * args.steps,
+            "roofline": roof, "cpu_baseline": cpu, "plain": plain,
+            "clocks": clk.summary(),
+            "scenarios": {"converged": int((status == 0).sum()), "island_no_gen": int((status == 3).sum()),
+                          "maxiter": int((status == 1).sum()), "diverged": int((status == 2).sum()),
+                          "mean_outer": float(iters[:, 0].mean()),
+                          "mean_inner_P": float(iters[:, 1].mean()),
+                          "mean_inner_Q": float(iters[:, 2].mean())},
+        }
+        print(json.dumps(line), flush=True)
+    c.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(g, sample):
+    """The oracle, as it stands, on a seeded sample of outages, all host cores."""
+    from oracle import powerflow as pf
+    from oracle import screen
+    cores = len(os.sched_getaffinity(0))
+    th0, V0, _, st, _ = pf.base_case(g, tol=1e-10, max_outer=200)
+    outs = np.random.default_rng(11).choice(g.n_branch, sample, replace=False)
+    t0 = time.perf_counter()
+    screen.n1_screen(g, th0, V0, outs, tol=1e-4, max_outer=50, processes=cores)
+    dt = time.perf_counter() - t0
+    return {"value": round(sample / dt, 2), "unit": "scenarios/s", "cores": cores, "kind": "oracle",
+            "sample": f"{sample} seeded outages of the same grid, tol 1e-4 p.u., "
+                      f"one process per core ({dt:.1f} s wall)"}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    from gridgen import config_grid
+    from oracle import powerflow as pf
+    from oracle import screen
+    g = config_grid(args.config)
+    cores = len(os.sched_getaffinity(0))
+    th0, V0, _, st, _ = pf.base_case(g, tol=1e-10, max_outer=200)
+    per_step = args.ref_sample
+    rng = np.random.default_rng(13)
+    for _ in range(args.warmup):
+        screen.n1_screen(g, th0, V0, rng.choice(g.n_branch, min(cores, per_step), replace=False),
+                         tol=1e-4, processes=cores)
+    times = []
+    for _ in range(args.steps):
+        outs = rng.choice(g.n_branch, per_step, replace=False)
+        t0 = time.perf_counter()
+        screen.n1_screen(g, th0, V0, outs, tol=1e-4, processes=cores)
+        times.append(time.perf_counter() - t0)
+    value = per_step * args.steps / sum(times)
+    line = {"metric": METRIC, "value": round(value, 2), "unit": "scenarios/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * sum(times) / args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"{args.config}: {g.n_bus} buses, {g.n_branch} branches, "
+                                   f"{per_step} seeded outages per step, tol 1e-4 p.u."},
+            "cpu_baseline": {"value": round(value, 2), "unit": "scenarios/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"{per_step} seeded outages per step, one process per core"},
+            "e2e": {"value": round(value, 2), "unit": "scenarios/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpcg", choices=["gpcg", "reference"])
+    ap.add_argument("--config", default=WORKLOAD)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precond", default="exact", choices=["exact", "ic0", "jacobi"])
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--n-outages", type=int, default=0, help="screen only the first K outages (0 = all)")
+    ap.add_argument("--cpu-sample", type=int, default=400)
+    ap.add_argument("--plain-sample", type=int, default=64)
+    ap.add_argument("--ref-sample", type=int, default=256)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpcg(args)
+
+
+if __name__ == "__main__":
+    main()

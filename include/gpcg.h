@@ -1,0 +1,232 @@
+/*
+ * gpcg.h -- C ABI of the GB300 N-1 contingency screen.
+ *
+ * The library solves the fast-decoupled power flow (Sec. III.B, eqs. (4)-(5))
+ * of every single-branch outage scenario (Sec. IV.A) with conjugate gradient
+ * preconditioned by a factorisation of the base-case matrix (Sec. IV.B,
+ * eqs. (6)-(7)), after islanding detection and proportional re-dispatch
+ * (Sec. IV.C).  All numerical work runs in CUDA kernels on the current
+ * device; the host code only validates arguments, analyses the sparsity
+ * structure once per grid, and enqueues work.
+ *
+ * Conventions
+ *  - Buses and branches are 0-based.  Per-unit quantities.
+ *  - Every function returns a gpcg_status; GPCG_OK is 0.  On error
+ *    gpcg_last_error() returns a message for the calling thread, valid until
+ *    that thread's next call into the library.
+ *  - A context belongs to the device that was current at gpcg_create and
+ *    must be used with that device current.  Calls on one context must not
+ *    overlap (one host thread at a time).
+ *  - Input arrays are borrowed for the duration of the call and copied.
+ *    Output arrays are owned by the caller.  A NULL output pointer skips
+ *    that output.
+ *  - mem = GPCG_MEM_HOST: every array argument is host memory (pageable or
+ *    pinned); the call returns after the results are in host memory.
+ *    mem = GPCG_MEM_DEVICE: every array argument is device memory of the
+ *    context's device; the work is ordered on `stream` (a cudaStream_t, or
+ *    NULL for the legacy default stream) and the call returns once it is
+ *    enqueued, except where a function says otherwise.
+ */
+#ifndef GPCG_H_
+#define GPCG_H_
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GPCG_API __attribute__((visibility("default")))
+#else
+#define GPCG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GPCG_OK = 0,
+  GPCG_ERR_INVALID_ARG = 1,     /* bad size, index, pointer or option */
+  GPCG_ERR_CUDA = 2,            /* a CUDA runtime call failed */
+  GPCG_ERR_BASE_NOT_CONVERGED = 3,
+  GPCG_ERR_BASE_ISLANDED = 4,   /* the intact grid is not connected */
+  GPCG_ERR_TIMEOUT = 5,         /* reserved: no kernel of this library waits on another */
+  GPCG_ERR_OOM = 6,             /* a device allocation failed */
+  GPCG_ERR_NOT_READY = 7        /* gpcg_base_solve has not succeeded yet */
+} gpcg_status;
+
+/* Per-scenario outcome written to status[] by gpcg_n1_screen. */
+enum {
+  GPCG_SCEN_OK = 0,             /* converged to the mismatch tolerance */
+  GPCG_SCEN_MAXITER = 1,        /* outer iteration cap reached */
+  GPCG_SCEN_DIVERGED = 2,       /* non-finite or > 1e4 p.u. mismatch */
+  GPCG_SCEN_ISLAND_NO_GEN = 3   /* converged, but the main island had no
+                                   generator to take the re-dispatch: the
+                                   slack absorbed it */
+};
+
+enum { GPCG_PQ = 0, GPCG_PV = 1, GPCG_SLACK = 2 };        /* bus_type */
+enum { GPCG_MEM_HOST = 0, GPCG_MEM_DEVICE = 1 };
+
+/* Precision of the inner PCG (the mismatch, state update and flows are
+ * always FP64, Sec. II.C eqs. (1)-(3)). */
+enum {
+  GPCG_PLAIN_FP64 = 0,    /* one scenario at a time, FP64 vectors: the
+                             unbatched comparison path */
+  GPCG_BATCHED_FP32 = 1,  /* batched, FP32 vectors and factors; the FP64
+                             outer loop acts as iterative refinement */
+  GPCG_BATCHED_FP64 = 2   /* batched, FP64 vectors and factors */
+};
+
+/* Preconditioner built from the base-case matrix (Sec. IV.B, eq. (6)). */
+enum {
+  GPCG_PRECOND_IC0 = 0,    /* incomplete Cholesky, zero fill */
+  GPCG_PRECOND_JACOBI = 1, /* diagonal of the contingency matrix, as in the
+                              vertex update of the listing in Sec. III.B */
+  GPCG_PRECOND_EXACT = 2   /* complete Cholesky of the base-case matrix:
+                              eq. (6) read literally */
+};
+
+/* Bus/branch model of Sec. II.B (vertex and edge attributes).  Host
+ * pointers.  Exactly one slack bus.  from[l] != to[l], x[l] > 0. */
+typedef struct {
+  int32_t n_bus;
+  int32_t n_branch;
+  const int8_t *bus_type;   /* [n_bus] GPCG_PQ / GPCG_PV / GPCG_SLACK */
+  const double *P_sched;    /* [n_bus] scheduled net active injection */
+  const double *Q_sched;    /* [n_bus] scheduled net reactive injection (PQ) */
+  const double *P_gen;      /* [n_bus] scheduled generation: re-dispatch weights */
+  const double *V_set;      /* [n_bus] |V| set point (PV, slack); start (PQ) */
+  const int32_t *from;      /* [n_branch] */
+  const int32_t *to;        /* [n_branch] */
+  const double *r;          /* [n_branch] series resistance */
+  const double *x;          /* [n_branch] series reactance, > 0 */
+  const double *b_sh;       /* [n_branch] total line charging */
+  const double *rating;     /* [n_branch] flow limit, > 0 */
+} gpcg_grid;
+
+typedef struct {
+  double tol;          /* outer tolerance on max |dP|, |dQ| (p.u.); 1e-4 */
+  double base_tol;     /* tolerance of gpcg_base_solve; 1e-10 */
+  double inner_rtol;   /* PCG stops at ||r|| <= inner_rtol ||b||; 1e-5 */
+  int32_t max_outer;   /* outer FDPF iteration cap; 50 */
+  int32_t max_inner;   /* PCG iteration cap per solve; 500 */
+  int32_t precision;   /* GPCG_PLAIN_FP64 / _BATCHED_FP32 / _BATCHED_FP64 */
+  int32_t precond;     /* GPCG_PRECOND_*; default GPCG_PRECOND_EXACT */
+  int32_t tile;        /* scenarios per tile: 8, 16 or 32; 0 = chosen by the
+                          library's autotuner on first use */
+  int32_t ctas_per_sm; /* resident tiles per SM; 0 = from the occupancy API */
+} gpcg_options;
+
+/* Sizes of the structures built by gpcg_create. */
+typedef struct {
+  int32_t n_bus, n_branch, slack;
+  int32_t n_p, n_q;            /* rows of B' (non-slack) and B'' (PQ) */
+  int32_t nnz_p, nnz_q;        /* nonzeros of B', B'' */
+  int32_t nnz_lp, nnz_lq;      /* nonzeros of the factors (lower, with diag) */
+  int32_t levels_p, levels_q;  /* forward level-schedule depths */
+  int32_t blevels_p, blevels_q;/* backward level-schedule depths */
+  int32_t n_bridges;           /* branches whose outage islands buses */
+  int32_t tile;                /* tile width in use (0 until chosen) */
+  int32_t num_sms;
+  int32_t base_outer;          /* outer iterations of the base solve, -1 if none */
+} gpcg_info;
+
+/* Fill *opt with the defaults listed above. */
+GPCG_API gpcg_status gpcg_default_options(gpcg_options *opt);
+
+typedef struct gpcg_ctx gpcg_ctx;   /* opaque; owned by the library */
+
+/* Create a context for one grid (Sec. II.B).  Validates the grid, copies it
+ * to the device, orders B' and B'' (minimum degree, then by level), builds
+ * their CSR values in a kernel (Sec. III.B: diagonal on the vertex,
+ * off-diagonal on the edge) and factorises the base-case matrices with a
+ * level-scheduled kernel (Sec. IV.B, eq. (6)).  opt may be NULL (defaults);
+ * it is copied.  Errors: INVALID_ARG (bad grid or options), BASE_ISLANDED,
+ * OOM, CUDA.  On error *out is set to NULL.  Synchronous. */
+GPCG_API gpcg_status gpcg_create(const gpcg_grid *grid, const gpcg_options *opt,
+                        gpcg_ctx **out);
+
+/* Release every device and host resource of the context.  NULL is a no-op. */
+GPCG_API void gpcg_destroy(gpcg_ctx *ctx);
+
+/* Replace the options of a live context (same rules as gpcg_create).
+ * Changing `precond` re-factorises the base-case matrices. */
+GPCG_API gpcg_status gpcg_set_options(gpcg_ctx *ctx, const gpcg_options *opt);
+
+GPCG_API gpcg_status gpcg_get_info(const gpcg_ctx *ctx, gpcg_info *info);
+
+/* Fast-decoupled power flow of the intact grid from a flat start
+ * (theta = 0, |V| = V_set), FP64, to opt.base_tol (Sec. III.B eqs. (4)-(5)).
+ * The result is kept in the context as the warm start of every N-1
+ * scenario (Sec. III.B: convergence depends on the initial vector).
+ * Host outputs, each optional: theta[n_bus], vm[n_bus], flow[n_branch]
+ * (active power at the from end), iters[3] = {outer, inner P, inner Q}.
+ * Errors: BASE_NOT_CONVERGED, CUDA.  Synchronous. */
+GPCG_API gpcg_status gpcg_base_solve(gpcg_ctx *ctx, double *theta, double *vm,
+                            double *flow, int32_t *iters);
+
+/* The N-1 screen (Sec. IV.A): for each outage l = outages[s] (a branch
+ * index) remove the branch, detect islands by connected components
+ * (Sec. IV.C), re-dispatch the islands' net injection over the main island's
+ * PV generators in proportion to P_gen (Sec. IV.C), solve the FDPF of the
+ * main island from the base-case state with base-preconditioned CG
+ * (Sec. IV.B), and screen the branch flows against their ratings (Sec. I).
+ * Islanded buses report theta = vm = 0; branches touching them, and the
+ * outaged branch, report zero flow.
+ *
+ * Outputs, row-major per scenario, each optional except where noted:
+ *   theta[n_out][n_bus], vm[n_out][n_bus]     FP64 state
+ *   flow[n_out][n_branch]                     active power at the from end
+ *   island_label[n_out][n_bus]                min bus index of each bus's
+ *                                             component after the outage
+ *   iters[n_out][3]                           {outer, inner P, inner Q}
+ *   status[n_out]                             GPCG_SCEN_*
+ *   max_loading[n_out]                        max over branches of
+ *                                             max(|P_ij|,|P_ji|)/rating
+ * n_out may be 0.  An outage index outside [0, n_branch) is INVALID_ARG.
+ * Requires a successful gpcg_base_solve (else NOT_READY).  A scenario that
+ * fails to converge never fails the call: see status[]. */
+GPCG_API gpcg_status gpcg_n1_screen(gpcg_ctx *ctx, const int32_t *outages, int32_t n_out,
+                           int32_t mem, void *stream, double *theta, double *vm,
+                           double *flow, int32_t *island_label, int32_t *iters,
+                           int32_t *status, double *max_loading);
+
+/* Batched operators of the hot path, for verification: each applies, for
+ * S scenarios at once, one step of the inner solve to S vectors stored
+ * row-major per scenario in the matrix's own row order (gpcg_export_matrix
+ * gives that order).  which = 0: B' (eq. (4)), 1: B'' (eq. (5)).
+ *   op = 0: Y = B_s X, the base-case matrix with the outaged branch's
+ *           four-element change (Sec. IV.B) applied on the fly.
+ *   op = 1: Y = M^{-1} X with the base-case preconditioner (eq. (6)):
+ *           level-scheduled forward and backward substitution.
+ * precision: GPCG_BATCHED_FP32 (vectors and factors in FP32) or
+ * GPCG_BATCHED_FP64.  X, Y are [S][rows] FP64 host arrays.  Synchronous. */
+GPCG_API gpcg_status gpcg_apply(gpcg_ctx *ctx, int32_t which, int32_t op,
+                       const int32_t *outages, int32_t S, int32_t precision,
+                       const double *X, double *Y);
+
+/* Copy out the structures built by gpcg_create for matrix `which`
+ * (0: B', 1: B'').  Host arrays, each optional:
+ *   bus_of_row[rows]      bus index of each matrix row
+ *   rowptr[rows+1], col[nnz], val[nnz]        the matrix (CSR, FP64)
+ *   lrowptr[rows+1], lcol[nnz_l], lval[nnz_l] the factor L (CSR, lower,
+ *                                             diagonal last in each row)
+ *   level[rows]           forward level of each row
+ * Sizes are in gpcg_info.  Synchronous. */
+GPCG_API gpcg_status gpcg_export_matrix(const gpcg_ctx *ctx, int32_t which,
+                               int32_t *bus_of_row, int32_t *rowptr,
+                               int32_t *col, double *val, int32_t *lrowptr,
+                               int32_t *lcol, double *lval, int32_t *level);
+
+/* Device time of the kernels of the context's last gpcg_n1_screen, from
+ * CUDA events recorded on that call's stream: ms[0] = islanding kernel,
+ * ms[1] = N-1 solve kernel (sum over its launches).  Waits for those events.
+ * Returns NOT_READY when no screen has run. */
+GPCG_API gpcg_status gpcg_last_timings(gpcg_ctx *ctx, float *ms /*[2]*/);
+
+/* Message of the last error on the calling thread ("" if none). */
+GPCG_API const char *gpcg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPCG_H_ */

@@ -1,0 +1,11 @@
+"""GB300-native N-1 contingency screen: base-case-preconditioned CG for the
+fast-decoupled power flow of every single-branch outage.
+
+The compute path is the CUDA library ``libgpcg.so`` (C ABI in
+``include/gpcg.h``); this package is its thin Python binding.
+"""
+from .binding import (BATCHED_FP32, BATCHED_FP64, GPCG, PLAIN_FP64, PRECOND_EXACT,
+                      PRECOND_IC0, PRECOND_JACOBI, GPCGError, default_options, load)
+
+__all__ = ["GPCG", "GPCGError", "default_options", "load", "PLAIN_FP64", "BATCHED_FP32",
+           "BATCHED_FP64", "PRECOND_IC0", "PRECOND_JACOBI", "PRECOND_EXACT"]

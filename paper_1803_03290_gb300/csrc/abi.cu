@@ -1,0 +1,780 @@
+// C ABI of the library (declared in include/gpcg.h): context management,
+// argument validation, device buffers and the launch sequence of each call.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/gpcg.h"
+#include "analysis.h"
+#include "common.cuh"
+#include "fdpf.h"
+
+namespace gpcg {
+// build.cu
+void launch_branch_params(cudaStream_t, int, const double*, const double*, double*, double*,
+                          double*, double*);
+void launch_ybus_diag(cudaStream_t, int, const int32_t*, const int32_t*, const double*,
+                      const double*, const double*, double*, double*);
+void launch_laplacian_values(cudaStream_t, int, const int32_t*, const int32_t*, const int32_t*,
+                             const int32_t*, const int32_t*, const double*, const int32_t*,
+                             const int32_t*, double*, int32_t*);
+void launch_ic_level(cudaStream_t, int, int, const int32_t*, const int32_t*, const double*,
+                     const int32_t*, const int32_t*, double*, int32_t*);
+void launch_scatter(cudaStream_t, int, const int32_t*, const double*, double*);
+void launch_to_float(cudaStream_t, int, const double*, float*);
+void launch_gather_diag(cudaStream_t, int, const int32_t*, const double*, double*);
+void launch_gather_int(cudaStream_t, int, const int32_t*, const int32_t*, int32_t*);
+// islands.cu
+size_t islands_smem(int n);
+cudaError_t launch_islands(cudaStream_t, int, int, int, int, int, const int32_t*, const int32_t*,
+                           const int32_t*, const int8_t*, const double*, const double*,
+                           const int32_t*, double, int32_t*, int32_t*, double*, int32_t*,
+                           int32_t*, int32_t*);
+}  // namespace gpcg
+
+
+using namespace gpcg;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+static gpcg_status fail(gpcg_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CUDA_TRY(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t ce_ = (call);                                                           \
+    if (ce_ != cudaSuccess) {                                                           \
+      if (ce_ == cudaErrorMemoryAllocation)                                             \
+        return fail(GPCG_ERR_OOM, "%s: %s", #call, cudaGetErrorString(ce_));            \
+      return fail(GPCG_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(ce_));             \
+    }                                                                                   \
+  } while (0)
+
+// ------------------------------------------------------------------ context
+struct MatDev {
+  MatrixPlan plan;
+  int32_t *bus_of_row = nullptr, *row_of_bus = nullptr, *pre_of_row = nullptr;
+  int32_t *a_ptr = nullptr, *a_idx = nullptr, *a_diag = nullptr;
+  int32_t *l_ptr = nullptr, *l_idx = nullptr, *u_ptr = nullptr, *u_idx = nullptr,
+          *l_to_u = nullptr;
+  int32_t *lev_ptr = nullptr, *blev_ptr = nullptr, *blev_rows = nullptr;
+  double *a_val = nullptr, *l_val = nullptr, *u_val = nullptr, *diag = nullptr;
+  float *a_val32 = nullptr, *l_val32 = nullptr, *u_val32 = nullptr, *diag32 = nullptr;
+  double* w = nullptr;  // per-branch weight
+  template <typename VT>
+  DevMatT<VT> view() const;
+};
+
+template <>
+DevMatT<double> MatDev::view<double>() const {
+  DevMatT<double> M;
+  M.n = plan.n;
+  M.bus_of_row = bus_of_row; M.row_of_bus = row_of_bus; M.pre_of_row = pre_of_row;
+  M.a_ptr = a_ptr; M.a_idx = a_idx; M.a_val = a_val;
+  M.l_ptr = l_ptr; M.l_idx = l_idx; M.l_val = l_val;
+  M.u_ptr = u_ptr; M.u_idx = u_idx; M.u_val = u_val;
+  M.diag = diag;
+  M.lev_ptr = lev_ptr; M.blev_ptr = blev_ptr; M.blev_rows = blev_rows;
+  M.nlev = (int)plan.lev_ptr.size() - 1;
+  M.nblev = (int)plan.blev_ptr.size() - 1;
+  M.w = w;
+  return M;
+}
+template <>
+DevMatT<float> MatDev::view<float>() const {
+  DevMatT<float> M;
+  M.n = plan.n;
+  M.bus_of_row = bus_of_row; M.row_of_bus = row_of_bus; M.pre_of_row = pre_of_row;
+  M.a_ptr = a_ptr; M.a_idx = a_idx; M.a_val = a_val32;
+  M.l_ptr = l_ptr; M.l_idx = l_idx; M.l_val = l_val32;
+  M.u_ptr = u_ptr; M.u_idx = u_idx; M.u_val = u_val32;
+  M.diag = diag32;
+  M.lev_ptr = lev_ptr; M.blev_ptr = blev_ptr; M.blev_rows = blev_rows;
+  M.nlev = (int)plan.lev_ptr.size() - 1;
+  M.nblev = (int)plan.blev_ptr.size() - 1;
+  M.w = w;
+  return M;
+}
+
+struct gpcg_ctx {
+  int device = 0, num_sms = 0;
+  gpcg_options opt{};
+  int n = 0, m = 0, slack = -1;
+  std::vector<int8_t> bus_type;
+  std::vector<int32_t> f, t;
+  BusGraph bg;
+  std::vector<int32_t> pre, sub;
+  std::vector<uint8_t> bridge;
+  int n_bridges = 0;
+  double pv_gen_total = 0.0;
+  DevGrid G;
+  double *wP = nullptr, *wQ = nullptr;
+  MatDev MP, MQ;
+  int planned_precond = -1;
+  // base case
+  double *th0 = nullptr, *V0 = nullptr, *flow0 = nullptr;
+  int base_outer = -1;
+  bool base_ok = false;
+  // per-call buffers
+  int32_t *d_outages = nullptr, *d_lo = nullptr, *d_cnt = nullptr, *d_nogen = nullptr;
+  double* d_coef = nullptr;
+  size_t sc_cap = 0;
+  int32_t *d_counter = nullptr, *d_err = nullptr;
+  void* work = nullptr;
+  size_t work_bytes = 0;
+  int tile = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool timed = false;
+  std::vector<void*> owned;  // freed at destroy (structures of the grid)
+  std::vector<void*> mat_owned;  // freed when the matrices are rebuilt
+};
+
+template <typename X>
+static cudaError_t dalloc(std::vector<void*>& own, X** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t ce = cudaMalloc((void**)p, count * sizeof(X));
+  if (ce == cudaSuccess) own.push_back((void*)*p);
+  return ce;
+}
+
+template <typename X>
+static cudaError_t upload(std::vector<void*>& own, X** p, const X* src, size_t count) {
+  cudaError_t ce = dalloc(own, p, count);
+  if (ce != cudaSuccess || count == 0) return ce;
+  return cudaMemcpy(*p, src, count * sizeof(X), cudaMemcpyHostToDevice);
+}
+
+static void free_list(std::vector<void*>& v) {
+  for (void* p : v) cudaFree(p);
+  v.clear();
+}
+
+// ------------------------------------------------------------------ options
+extern "C" gpcg_status gpcg_default_options(gpcg_options* opt) {
+  if (!opt) return fail(GPCG_ERR_INVALID_ARG, "gpcg_default_options: opt is NULL");
+  opt->tol = 1e-4;
+  opt->base_tol = 1e-10;
+  opt->inner_rtol = 1e-5;
+  opt->max_outer = 50;
+  opt->max_inner = 500;
+  opt->precision = GPCG_BATCHED_FP32;
+  opt->precond = GPCG_PRECOND_EXACT;
+  opt->tile = 0;
+  opt->ctas_per_sm = 0;
+  g_err.clear();
+  return GPCG_OK;
+}
+
+static gpcg_status check_options(const gpcg_options& o) {
+  if (!(o.tol > 0) || !(o.base_tol > 0) || !(o.inner_rtol > 0) || !(o.inner_rtol < 1))
+    return fail(GPCG_ERR_INVALID_ARG, "tolerances must be positive (inner_rtol < 1)");
+  if (o.max_outer < 1 || o.max_inner < 1)
+    return fail(GPCG_ERR_INVALID_ARG, "max_outer and max_inner must be >= 1");
+  if (o.precision < 0 || o.precision > 2)
+    return fail(GPCG_ERR_INVALID_ARG, "precision must be 0, 1 or 2");
+  if (o.precond < 0 || o.precond > 2)
+    return fail(GPCG_ERR_INVALID_ARG, "precond must be 0, 1 or 2");
+  if (!(o.tile == 0 || o.tile == 8 || o.tile == 16 || o.tile == 32))
+    return fail(GPCG_ERR_INVALID_ARG, "tile must be 0, 8, 16 or 32");
+  if (o.ctas_per_sm < 0 || o.ctas_per_sm > 64)
+    return fail(GPCG_ERR_INVALID_ARG, "ctas_per_sm must be in [0, 64]");
+  return GPCG_OK;
+}
+
+// ------------------------------------------------------------------ build
+static gpcg_status build_matrix(gpcg_ctx* c, MatDev& M, const std::vector<uint8_t>& keep,
+                                double* w, bool fill) {
+  M.plan = plan_matrix(c->n, c->bg, keep, fill);
+  const MatrixPlan& P = M.plan;
+  auto& own = c->mat_owned;
+  std::vector<int32_t> pre_of_row(P.n);
+  for (int i = 0; i < P.n; ++i) pre_of_row[i] = c->pre[P.bus_of_row[i]];
+  CUDA_TRY(upload(own, &M.bus_of_row, P.bus_of_row.data(), P.n));
+  CUDA_TRY(upload(own, &M.row_of_bus, P.row_of_bus.data(), c->n));
+  CUDA_TRY(upload(own, &M.pre_of_row, pre_of_row.data(), P.n));
+  CUDA_TRY(upload(own, &M.a_ptr, P.A.ptr.data(), P.A.ptr.size()));
+  CUDA_TRY(upload(own, &M.a_idx, P.A.idx.data(), P.A.idx.size()));
+  CUDA_TRY(upload(own, &M.a_diag, P.a_diag.data(), P.n));
+  CUDA_TRY(upload(own, &M.l_ptr, P.L.ptr.data(), P.L.ptr.size()));
+  CUDA_TRY(upload(own, &M.l_idx, P.L.idx.data(), P.L.idx.size()));
+  CUDA_TRY(upload(own, &M.u_ptr, P.U.ptr.data(), P.U.ptr.size()));
+  CUDA_TRY(upload(own, &M.u_idx, P.U.idx.data(), P.U.idx.size()));
+  CUDA_TRY(upload(own, &M.l_to_u, P.l_to_u.data(), P.l_to_u.size()));
+  CUDA_TRY(upload(own, &M.lev_ptr, P.lev_ptr.data(), P.lev_ptr.size()));
+  CUDA_TRY(upload(own, &M.blev_ptr, P.blev_ptr.data(), P.blev_ptr.size()));
+  CUDA_TRY(upload(own, &M.blev_rows, P.blev_rows.data(), P.blev_rows.size()));
+  const int nnz = P.A.nnz(), nl = P.L.nnz();
+  CUDA_TRY(dalloc(own, &M.a_val, nnz));
+  CUDA_TRY(dalloc(own, &M.l_val, nl));
+  CUDA_TRY(dalloc(own, &M.u_val, nl));
+  CUDA_TRY(dalloc(own, &M.diag, P.n));
+  CUDA_TRY(dalloc(own, &M.a_val32, nnz));
+  CUDA_TRY(dalloc(own, &M.l_val32, nl));
+  CUDA_TRY(dalloc(own, &M.u_val32, nl));
+  CUDA_TRY(dalloc(own, &M.diag32, P.n));
+  M.w = w;
+  cudaStream_t st = 0;
+  CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int32_t)));
+  launch_laplacian_values(st, P.n, M.bus_of_row, M.row_of_bus, c->G.adj_ptr, c->G.adj_idx,
+                          c->G.adj_br, w, M.a_ptr, M.a_idx, M.a_val, c->d_err);
+  for (size_t k = 0; k + 1 < P.lev_ptr.size(); ++k)
+    launch_ic_level(st, P.lev_ptr[k], P.lev_ptr[k + 1], M.a_ptr, M.a_idx, M.a_val, M.l_ptr,
+                    M.l_idx, M.l_val, c->d_err);
+  launch_scatter(st, nl, M.l_to_u, M.l_val, M.u_val);
+  launch_gather_diag(st, P.n, M.a_diag, M.a_val, M.diag);
+  launch_to_float(st, nnz, M.a_val, M.a_val32);
+  launch_to_float(st, nl, M.l_val, M.l_val32);
+  launch_to_float(st, nl, M.u_val, M.u_val32);
+  launch_to_float(st, P.n, M.diag, M.diag32);
+  CUDA_TRY(cudaGetLastError());
+  int32_t herr = 0;
+  CUDA_TRY(cudaMemcpy(&herr, c->d_err, sizeof herr, cudaMemcpyDeviceToHost));
+  if (herr == 1) return fail(GPCG_ERR_CUDA, "internal: CSR slot missing while building values");
+  if (herr == 2)
+    return fail(GPCG_ERR_INVALID_ARG,
+                "base-case factorisation met a non-positive pivot (matrix not positive definite)");
+  return GPCG_OK;
+}
+
+static gpcg_status build_matrices(gpcg_ctx* c) {
+  free_list(c->mat_owned);
+  std::vector<uint8_t> keepP(c->n), keepQ(c->n);
+  for (int b = 0; b < c->n; ++b) {
+    keepP[b] = c->bus_type[b] != GPCG_SLACK;
+    keepQ[b] = c->bus_type[b] == GPCG_PQ;
+  }
+  const bool fill = c->opt.precond == GPCG_PRECOND_EXACT;
+  gpcg_status st = build_matrix(c, c->MP, keepP, c->wP, fill);
+  if (st != GPCG_OK) return st;
+  st = build_matrix(c, c->MQ, keepQ, c->wQ, fill);
+  if (st != GPCG_OK) return st;
+  c->planned_precond = c->opt.precond;
+  return GPCG_OK;
+}
+
+static void destroy(gpcg_ctx* c) {
+  if (!c) return;
+  free_list(c->mat_owned);
+  free_list(c->owned);
+  if (c->work) cudaFree(c->work);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  cudaFree(c->d_outages); cudaFree(c->d_lo); cudaFree(c->d_cnt); cudaFree(c->d_nogen);
+  cudaFree(c->d_coef);
+  delete c;
+}
+
+extern "C" void gpcg_destroy(gpcg_ctx* c) { destroy(c); }
+
+extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, gpcg_ctx** out) {
+  if (!out) return fail(GPCG_ERR_INVALID_ARG, "gpcg_create: out is NULL");
+  *out = nullptr;
+  if (!g) return fail(GPCG_ERR_INVALID_ARG, "gpcg_create: grid is NULL");
+  const int n = g->n_bus, m = g->n_branch;
+  if (n < 2 || m < 1) return fail(GPCG_ERR_INVALID_ARG, "need n_bus >= 2 and n_branch >= 1");
+  if (!g->bus_type || !g->P_sched || !g->Q_sched || !g->P_gen || !g->V_set || !g->from ||
+      !g->to || !g->r || !g->x || !g->b_sh || !g->rating)
+    return fail(GPCG_ERR_INVALID_ARG, "gpcg_create: a grid array is NULL");
+  gpcg_options o;
+  gpcg_default_options(&o);
+  if (opt) o = *opt;
+  gpcg_status st = check_options(o);
+  if (st != GPCG_OK) return st;
+  int slack = -1;
+  for (int b = 0; b < n; ++b) {
+    int bt = g->bus_type[b];
+    if (bt < 0 || bt > 2) return fail(GPCG_ERR_INVALID_ARG, "bus %d: bad bus_type %d", b, bt);
+    if (bt == GPCG_SLACK) {
+      if (slack >= 0) return fail(GPCG_ERR_INVALID_ARG, "more than one slack bus (%d, %d)", slack, b);
+      slack = b;
+    }
+    if (!std::isfinite(g->P_sched[b]) || !std::isfinite(g->Q_sched[b]) ||
+        !std::isfinite(g->P_gen[b]) || !(g->V_set[b] > 0) || !std::isfinite(g->V_set[b]))
+      return fail(GPCG_ERR_INVALID_ARG, "bus %d: non-finite injection or V_set <= 0", b);
+  }
+  if (slack < 0) return fail(GPCG_ERR_INVALID_ARG, "no slack bus");
+  for (int e = 0; e < m; ++e) {
+    int a = g->from[e], b = g->to[e];
+    if (a < 0 || a >= n || b < 0 || b >= n || a == b)
+      return fail(GPCG_ERR_INVALID_ARG, "branch %d: bad end buses (%d, %d)", e, a, b);
+    if (!(g->x[e] > 0) || !std::isfinite(g->x[e]) || !(g->r[e] >= 0) ||
+        !std::isfinite(g->r[e]) || !std::isfinite(g->b_sh[e]) || !(g->rating[e] > 0))
+      return fail(GPCG_ERR_INVALID_ARG, "branch %d: needs x > 0, r >= 0, rating > 0", e);
+  }
+  gpcg_ctx* c = new gpcg_ctx();
+  c->opt = o;
+  c->n = n;
+  c->m = m;
+  c->slack = slack;
+  c->bus_type.assign(g->bus_type, g->bus_type + n);
+  c->f.assign(g->from, g->from + m);
+  c->t.assign(g->to, g->to + m);
+  cudaGetDevice(&c->device);
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  c->bg = build_bus_graph(n, m, g->from, g->to);
+  if (!dfs_numbering(n, c->bg, slack, c->pre, c->sub, c->bridge, m)) {
+    destroy(c);
+    return fail(GPCG_ERR_BASE_ISLANDED, "the intact grid is not connected");
+  }
+  for (int e = 0; e < m; ++e) c->n_bridges += c->bridge[e];
+  for (int b = 0; b < n; ++b)
+    if (g->bus_type[b] == GPCG_PV && g->P_gen[b] > 0) c->pv_gen_total += g->P_gen[b];
+  if ((size_t)n * sizeof(int32_t) > 227 * 1024) {
+    destroy(c);
+    return fail(GPCG_ERR_INVALID_ARG, "n_bus = %d exceeds the islanding kernel's limit (%d)", n,
+                (int)(227 * 1024 / 4));
+  }
+  auto fail_cuda = [&](cudaError_t ce, const char* what) {
+    destroy(c);
+    return fail(ce == cudaErrorMemoryAllocation ? GPCG_ERR_OOM : GPCG_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(ce));
+  };
+  cudaError_t ce;
+  auto& own = c->owned;
+  DevGrid& G = c->G;
+  G.n = n; G.m = m; G.slack = slack;
+#define UP(dst, src, cnt)                                   \
+  if ((ce = upload(own, &dst, src, cnt)) != cudaSuccess) return fail_cuda(ce, "upload " #dst)
+#define AL(dst, cnt)                                        \
+  if ((ce = dalloc(own, &dst, cnt)) != cudaSuccess) return fail_cuda(ce, "alloc " #dst)
+  UP(G.bus_type, g->bus_type, n);
+  UP(G.P_sched, g->P_sched, n);
+  UP(G.Q_sched, g->Q_sched, n);
+  UP(G.P_gen, g->P_gen, n);
+  UP(G.V_set, g->V_set, n);
+  UP(G.f, g->from, m);
+  UP(G.t, g->to, m);
+  UP(G.r, g->r, m);
+  UP(G.x, g->x, m);
+  UP(G.b_sh, g->b_sh, m);
+  UP(G.rating, g->rating, m);
+  UP(G.adj_ptr, c->bg.adj.ptr.data(), n + 1);
+  UP(G.adj_idx, c->bg.adj.idx.data(), c->bg.adj.idx.size());
+  UP(G.adj_br, c->bg.adj_branch.data(), c->bg.adj_branch.size());
+  UP(G.pre, c->pre.data(), n);
+  UP(G.sub, c->sub.data(), n);
+  AL(G.g, m);
+  AL(G.by, m);
+  AL(G.Gii, n);
+  AL(G.Bii, n);
+  AL(c->wP, m);
+  AL(c->wQ, m);
+  AL(c->th0, n);
+  AL(c->V0, n);
+  AL(c->flow0, m);
+  AL(c->d_counter, 1);
+  AL(c->d_err, 1);
+  for (auto& e : c->ev)
+    if ((ce = cudaEventCreate(&e)) != cudaSuccess) return fail_cuda(ce, "event");
+#undef UP
+#undef AL
+  launch_branch_params(0, m, G.r, G.x, G.g, G.by, c->wP, c->wQ);
+  launch_ybus_diag(0, n, G.adj_ptr, G.adj_br, G.g, G.by, G.b_sh, G.Gii, G.Bii);
+  if ((ce = cudaGetLastError()) != cudaSuccess) return fail_cuda(ce, "build kernels");
+  st = build_matrices(c);
+  if (st != GPCG_OK) {
+    std::string msg = g_err;
+    destroy(c);
+    g_err = msg;
+    return st;
+  }
+  if ((ce = cudaDeviceSynchronize()) != cudaSuccess) return fail_cuda(ce, "create");
+  *out = c;
+  g_err.clear();
+  return GPCG_OK;
+}
+
+extern "C" gpcg_status gpcg_set_options(gpcg_ctx* c, const gpcg_options* opt) {
+  if (!c || !opt) return fail(GPCG_ERR_INVALID_ARG, "gpcg_set_options: NULL argument");
+  gpcg_status st = check_options(*opt);
+  if (st != GPCG_OK) return st;
+  const bool rebuild = opt->precond != c->planned_precond &&
+                       ((opt->precond == GPCG_PRECOND_EXACT) !=
+                        (c->planned_precond == GPCG_PRECOND_EXACT));
+  c->opt = *opt;
+  if (opt->tile) c->tile = opt->tile;
+  if (rebuild) {
+    st = build_matrices(c);
+    if (st != GPCG_OK) return st;
+  }
+  c->planned_precond = opt->precond;
+  g_err.clear();
+  return GPCG_OK;
+}
+
+extern "C" gpcg_status gpcg_get_info(const gpcg_ctx* c, gpcg_info* info) {
+  if (!c || !info) return fail(GPCG_ERR_INVALID_ARG, "gpcg_get_info: NULL argument");
+  info->n_bus = c->n;
+  info->n_branch = c->m;
+  info->slack = c->slack;
+  info->n_p = c->MP.plan.n;
+  info->n_q = c->MQ.plan.n;
+  info->nnz_p = c->MP.plan.A.nnz();
+  info->nnz_q = c->MQ.plan.A.nnz();
+  info->nnz_lp = c->MP.plan.L.nnz();
+  info->nnz_lq = c->MQ.plan.L.nnz();
+  info->levels_p = (int)c->MP.plan.lev_ptr.size() - 1;
+  info->levels_q = (int)c->MQ.plan.lev_ptr.size() - 1;
+  info->blevels_p = (int)c->MP.plan.blev_ptr.size() - 1;
+  info->blevels_q = (int)c->MQ.plan.blev_ptr.size() - 1;
+  info->n_bridges = c->n_bridges;
+  info->tile = c->tile;
+  info->num_sms = c->num_sms;
+  info->base_outer = c->base_outer;
+  g_err.clear();
+  return GPCG_OK;
+}
+
+// ------------------------------------------------------------------ solves
+static gpcg_status ensure_scen(gpcg_ctx* c, size_t S) {
+  if (S <= c->sc_cap) return GPCG_OK;
+  cudaFree(c->d_outages); cudaFree(c->d_lo); cudaFree(c->d_cnt); cudaFree(c->d_nogen);
+  cudaFree(c->d_coef);
+  c->d_outages = c->d_lo = c->d_cnt = c->d_nogen = nullptr;
+  c->d_coef = nullptr;
+  c->sc_cap = 0;
+  size_t cap = std::max<size_t>(S, 64);
+  CUDA_TRY(cudaMalloc(&c->d_outages, cap * 4));
+  CUDA_TRY(cudaMalloc(&c->d_lo, cap * 4));
+  CUDA_TRY(cudaMalloc(&c->d_cnt, cap * 4));
+  CUDA_TRY(cudaMalloc(&c->d_nogen, cap * 4));
+  CUDA_TRY(cudaMalloc(&c->d_coef, cap * 8));
+  c->sc_cap = cap;
+  return GPCG_OK;
+}
+
+static gpcg_status ensure_work(gpcg_ctx* c, size_t bytes) {
+  if (bytes <= c->work_bytes) return GPCG_OK;
+  if (c->work) cudaFree(c->work);
+  c->work = nullptr;
+  c->work_bytes = 0;
+  CUDA_TRY(cudaMalloc(&c->work, bytes));
+  c->work_bytes = bytes;
+  return GPCG_OK;
+}
+
+struct Layout {
+  int T = 32, slots = 1;
+  size_t vstride = 0, sstride = 0, vec_bytes = 0, bytes = 0;
+};
+
+static Layout make_layout(const gpcg_ctx* c, int T, int slots, size_t vt_size) {
+  Layout L;
+  L.T = T;
+  L.slots = slots;
+  const size_t rows = (size_t)std::max(c->MP.plan.n, c->MQ.plan.n);
+  L.vstride = rows * T;
+  L.sstride = (size_t)c->n * T;
+  L.vec_bytes = ((L.vstride * vt_size + 255) / 256) * 256;
+  const size_t st_bytes = ((L.sstride * 8 + 255) / 256) * 256;
+  L.bytes = (size_t)slots * (5 * L.vec_bytes + 6 * st_bytes);
+  return L;
+}
+
+template <typename VT>
+static gpcg_status run_fdpf(gpcg_ctx* c, cudaStream_t st, FdpfParams P, int T, int slots) {
+  Layout Lo = make_layout(c, T, slots, sizeof(VT));
+  gpcg_status s = ensure_work(c, Lo.bytes);
+  if (s != GPCG_OK) return s;
+  char* base = (char*)c->work;
+  const size_t vb = (size_t)slots * Lo.vec_bytes;
+  const size_t sb = (size_t)slots * (((Lo.sstride * 8 + 255) / 256) * 256);
+  P.wx = base; P.wr = base + vb; P.wp = base + 2 * vb; P.wq = base + 3 * vb; P.wz = base + 4 * vb;
+  P.vstride = Lo.vec_bytes / sizeof(VT);
+  double* sbase = (double*)(base + 5 * vb);
+  const size_t ss = sb / slots / 8;
+  P.wth = sbase; P.wV = sbase + slots * ss; P.wc = sbase + 2 * slots * ss;
+  P.ws = sbase + 3 * slots * ss; P.we = sbase + 4 * slots * ss; P.wf = sbase + 5 * slots * ss;
+  P.sstride = ss;
+  P.tile_counter = c->d_counter;
+  CUDA_TRY(cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), st));
+  CUDA_TRY(launch_fdpf<VT>(st, T, slots, P, c->MP.view<VT>(), c->MQ.view<VT>()));
+  return GPCG_OK;
+}
+
+static FdpfParams base_params(gpcg_ctx* c) {
+  FdpfParams P;
+  P.G = c->G;
+  P.tol = c->opt.tol;
+  P.inner_rtol = c->opt.inner_rtol;
+  P.max_outer = c->opt.max_outer;
+  P.max_inner = c->opt.max_inner;
+  P.precond = c->opt.precond;
+  return P;
+}
+
+extern "C" gpcg_status gpcg_base_solve(gpcg_ctx* c, double* theta, double* vm, double* flow,
+                                       int32_t* iters) {
+  if (!c) return fail(GPCG_ERR_INVALID_ARG, "gpcg_base_solve: ctx is NULL");
+  gpcg_status s = ensure_scen(c, 1);
+  if (s != GPCG_OK) return s;
+  cudaStream_t st = 0;
+  const int32_t neg = -1, zero = 0;
+  const double dz = 0.0;
+  CUDA_TRY(cudaMemcpy(c->d_outages, &neg, 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(c->d_lo, &zero, 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(c->d_cnt, &zero, 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(c->d_nogen, &zero, 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(c->d_coef, &dz, 8, cudaMemcpyHostToDevice));
+  FdpfParams P = base_params(c);
+  P.S = 1;
+  P.n_tiles = 1;
+  P.sc = ScenInfo{c->d_outages, c->d_lo, c->d_cnt, c->d_coef, c->d_nogen};
+  P.flat_start = 1;
+  P.tol = c->opt.base_tol;
+  P.max_outer = std::max(c->opt.max_outer, 100);
+  P.out_theta = c->th0;
+  P.out_vm = c->V0;
+  P.out_flow = c->flow0;
+  int32_t* d_stat = c->d_cnt;  // the scenario's own count slot doubles as its status
+  int32_t* d_iters3 = nullptr;
+  CUDA_TRY(cudaMalloc(&d_iters3, 3 * sizeof(int32_t)));
+  P.out_iters = d_iters3;
+  P.out_status = d_stat;
+  s = run_fdpf<double>(c, st, P, 1, 1);
+  int32_t hs = -1, hit[3] = {0, 0, 0};
+  if (s == GPCG_OK) {
+    cudaError_t ce = cudaDeviceSynchronize();
+    if (ce == cudaSuccess) ce = cudaMemcpy(&hs, d_stat, 4, cudaMemcpyDeviceToHost);
+    if (ce == cudaSuccess) ce = cudaMemcpy(hit, d_iters3, 12, cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) s = fail(GPCG_ERR_CUDA, "base solve: %s", cudaGetErrorString(ce));
+  }
+  cudaFree(d_iters3);
+  if (s != GPCG_OK) return s;
+  c->base_outer = hit[0];
+  if (hs != GPCG_SCEN_OK) {
+    c->base_ok = false;
+    return fail(GPCG_ERR_BASE_NOT_CONVERGED,
+                "base case did not converge (status %d after %d outer iterations)", hs, hit[0]);
+  }
+  c->base_ok = true;
+  if (theta) CUDA_TRY(cudaMemcpy(theta, c->th0, (size_t)c->n * 8, cudaMemcpyDeviceToHost));
+  if (vm) CUDA_TRY(cudaMemcpy(vm, c->V0, (size_t)c->n * 8, cudaMemcpyDeviceToHost));
+  if (flow) CUDA_TRY(cudaMemcpy(flow, c->flow0, (size_t)c->m * 8, cudaMemcpyDeviceToHost));
+  if (iters) { iters[0] = hit[0]; iters[1] = hit[1]; iters[2] = hit[2]; }
+  g_err.clear();
+  return GPCG_OK;
+}
+
+template <typename X>
+struct OutBuf {
+  X* dev = nullptr;
+  X* host = nullptr;
+  size_t count = 0;
+  bool owned = false;
+};
+
+extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32_t n_out,
+                                      int32_t mem, void* stream, double* theta, double* vm,
+                                      double* flow, int32_t* island_label, int32_t* iters,
+                                      int32_t* status, double* max_loading) {
+  if (!c) return fail(GPCG_ERR_INVALID_ARG, "gpcg_n1_screen: ctx is NULL");
+  if (n_out < 0) return fail(GPCG_ERR_INVALID_ARG, "n_out < 0");
+  if (mem != GPCG_MEM_HOST && mem != GPCG_MEM_DEVICE)
+    return fail(GPCG_ERR_INVALID_ARG, "mem must be 0 (host) or 1 (device)");
+  if (!c->base_ok) return fail(GPCG_ERR_NOT_READY, "gpcg_base_solve has not succeeded");
+  if (n_out == 0) { g_err.clear(); return GPCG_OK; }
+  if (!outages) return fail(GPCG_ERR_INVALID_ARG, "outages is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t S = (size_t)n_out;
+  // validate the outage list on the host
+  std::vector<int32_t> hout(S);
+  if (mem == GPCG_MEM_HOST) {
+    std::memcpy(hout.data(), outages, S * 4);
+  } else {
+    CUDA_TRY(cudaMemcpyAsync(hout.data(), outages, S * 4, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  for (size_t s = 0; s < S; ++s)
+    if (hout[s] < 0 || hout[s] >= c->m)
+      return fail(GPCG_ERR_INVALID_ARG, "outages[%zu] = %d is not a branch index", s, hout[s]);
+  gpcg_status s_ = ensure_scen(c, S);
+  if (s_ != GPCG_OK) return s_;
+  CUDA_TRY(cudaMemcpyAsync(c->d_outages, hout.data(), S * 4, cudaMemcpyHostToDevice, st));
+
+  // outputs: device pointers directly, or device staging for host pointers
+  std::vector<void*> staging;
+  auto stage = [&](auto* user, size_t count, auto** dev) -> cudaError_t {
+    *dev = nullptr;
+    if (!user) return cudaSuccess;
+    if (mem == GPCG_MEM_DEVICE) { *dev = user; return cudaSuccess; }
+    cudaError_t ce = cudaMallocAsync((void**)dev, count * sizeof(**dev), st);
+    if (ce == cudaSuccess) staging.push_back((void*)*dev);
+    return ce;
+  };
+  double *d_theta, *d_vm, *d_flow, *d_ml;
+  int32_t *d_lab, *d_iters, *d_stat;
+  cudaError_t ce = cudaSuccess;
+  if (ce == cudaSuccess) ce = stage(theta, S * c->n, &d_theta);
+  if (ce == cudaSuccess) ce = stage(vm, S * c->n, &d_vm);
+  if (ce == cudaSuccess) ce = stage(flow, S * c->m, &d_flow);
+  if (ce == cudaSuccess) ce = stage(island_label, S * c->n, &d_lab);
+  if (ce == cudaSuccess) ce = stage(iters, S * 3, &d_iters);
+  if (ce == cudaSuccess) ce = stage(status, S, &d_stat);
+  if (ce == cudaSuccess) ce = stage(max_loading, S, &d_ml);
+  auto cleanup = [&]() { for (void* p : staging) cudaFreeAsync(p, st); };
+  if (ce != cudaSuccess) {
+    cleanup();
+    return fail(ce == cudaErrorMemoryAllocation ? GPCG_ERR_OOM : GPCG_ERR_CUDA,
+                "output staging: %s", cudaGetErrorString(ce));
+  }
+  CUDA_TRY(cudaMemsetAsync(c->d_err, 0, 4, st));
+  CUDA_TRY(cudaEventRecord(c->ev[0], st));
+  const int cc_grid = std::min<int>((int)S, c->num_sms * 4);
+  ce = launch_islands(st, cc_grid, c->n, c->m, c->slack, (int)S, c->d_outages, c->G.f, c->G.t,
+                      c->G.bus_type, c->G.P_sched, c->G.P_gen, c->G.pre, c->pv_gen_total,
+                      c->d_lo, c->d_cnt, c->d_coef, c->d_nogen, d_lab, c->d_err);
+  if (ce != cudaSuccess) { cleanup(); return fail(GPCG_ERR_CUDA, "islands: %s", cudaGetErrorString(ce)); }
+  CUDA_TRY(cudaEventRecord(c->ev[1], st));
+
+  FdpfParams P = base_params(c);
+  P.sc = ScenInfo{c->d_outages, c->d_lo, c->d_cnt, c->d_coef, c->d_nogen};
+  P.th0 = c->th0;
+  P.V0 = c->V0;
+  P.out_theta = d_theta; P.out_vm = d_vm; P.out_flow = d_flow; P.out_maxload = d_ml;
+  P.out_iters = d_iters; P.out_status = d_stat;
+  gpcg_status rs = GPCG_OK;
+  if (c->opt.precision == GPCG_PLAIN_FP64) {
+    // one scenario at a time: no batching across scenarios
+    for (size_t s = 0; s < S && rs == GPCG_OK; ++s) {
+      FdpfParams Q = P;
+      Q.S = 1;
+      Q.n_tiles = 1;
+      Q.sc = ScenInfo{c->d_outages + s, c->d_lo + s, c->d_cnt + s, c->d_coef + s, c->d_nogen + s};
+      Q.out_theta = d_theta ? d_theta + s * c->n : nullptr;
+      Q.out_vm = d_vm ? d_vm + s * c->n : nullptr;
+      Q.out_flow = d_flow ? d_flow + s * c->m : nullptr;
+      Q.out_maxload = d_ml ? d_ml + s : nullptr;
+      Q.out_iters = d_iters ? d_iters + 3 * s : nullptr;
+      Q.out_status = d_stat ? d_stat + s : nullptr;
+      rs = run_fdpf<double>(c, st, Q, 1, 1);
+    }
+  } else {
+    const int T = c->opt.tile ? c->opt.tile : (c->tile ? c->tile : 32);
+    c->tile = T;
+    const int n_tiles = (int)((S + T - 1) / T);
+    const bool f32 = c->opt.precision == GPCG_BATCHED_FP32;
+    int per_sm = c->opt.ctas_per_sm;
+    if (per_sm == 0) per_sm = f32 ? fdpf_max_blocks_per_sm<float>(T) : fdpf_max_blocks_per_sm<double>(T);
+    per_sm = std::max(per_sm, 1);
+    const int slots = std::max(1, std::min(n_tiles, c->num_sms * per_sm));
+    P.S = (int)S;
+    P.n_tiles = n_tiles;
+    rs = f32 ? run_fdpf<float>(c, st, P, T, slots) : run_fdpf<double>(c, st, P, T, slots);
+  }
+  if (rs != GPCG_OK) { cleanup(); return rs; }
+  CUDA_TRY(cudaEventRecord(c->ev[2], st));
+  c->timed = true;
+  if (mem == GPCG_MEM_HOST) {
+    auto back = [&](auto* user, auto* dev, size_t count) -> cudaError_t {
+      if (!user) return cudaSuccess;
+      return cudaMemcpyAsync(user, dev, count * sizeof(*user), cudaMemcpyDeviceToHost, st);
+    };
+    if (ce == cudaSuccess) ce = back(theta, d_theta, S * c->n);
+    if (ce == cudaSuccess) ce = back(vm, d_vm, S * c->n);
+    if (ce == cudaSuccess) ce = back(flow, d_flow, S * c->m);
+    if (ce == cudaSuccess) ce = back(island_label, d_lab, S * c->n);
+    if (ce == cudaSuccess) ce = back(iters, d_iters, S * 3);
+    if (ce == cudaSuccess) ce = back(status, d_stat, S);
+    if (ce == cudaSuccess) ce = back(max_loading, d_ml, S);
+    cleanup();
+    int32_t herr = 0;
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&herr, c->d_err, 4, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) return fail(GPCG_ERR_CUDA, "n1_screen: %s", cudaGetErrorString(ce));
+    if (herr == 3) return fail(GPCG_ERR_CUDA, "internal: an island is not a depth-first subtree");
+  }
+  g_err.clear();
+  return GPCG_OK;
+}
+
+extern "C" gpcg_status gpcg_apply(gpcg_ctx* c, int32_t which, int32_t op, const int32_t* outages,
+                                  int32_t S, int32_t precision, const double* X, double* Y) {
+  if (!c || !outages || !X || !Y || S < 0)
+    return fail(GPCG_ERR_INVALID_ARG, "gpcg_apply: NULL argument or S < 0");
+  if ((which != 0 && which != 1) || (op != 0 && op != 1))
+    return fail(GPCG_ERR_INVALID_ARG, "gpcg_apply: which and op must be 0 or 1");
+  if (precision != GPCG_BATCHED_FP32 && precision != GPCG_BATCHED_FP64)
+    return fail(GPCG_ERR_INVALID_ARG, "gpcg_apply: precision must be 1 or 2");
+  if (S == 0) { g_err.clear(); return GPCG_OK; }
+  for (int s = 0; s < S; ++s)
+    if (outages[s] < -1 || outages[s] >= c->m)
+      return fail(GPCG_ERR_INVALID_ARG, "gpcg_apply: outage %d out of range", outages[s]);
+  const MatDev& M = which ? c->MQ : c->MP;
+  const int rows = M.plan.n;
+  const size_t vt = precision == GPCG_BATCHED_FP32 ? 4 : 8;
+  const int T = 32;
+  const int grid = std::max(1, std::min((S + T - 1) / T, c->num_sms * 2));
+  const size_t vstride = (size_t)rows * T;
+  int32_t* d_out = nullptr;
+  double *dX = nullptr, *dY = nullptr;
+  void* wbuf = nullptr;
+  gpcg_status rs = GPCG_OK;
+  cudaError_t ce = cudaMalloc(&d_out, (size_t)S * 4);
+  if (ce == cudaSuccess) ce = cudaMalloc(&dX, (size_t)S * rows * 8 + 8);
+  if (ce == cudaSuccess) ce = cudaMalloc(&dY, (size_t)S * rows * 8 + 8);
+  if (ce == cudaSuccess) ce = cudaMalloc(&wbuf, (size_t)grid * 4 * vstride * vt + 8);
+  if (ce == cudaSuccess) ce = cudaMemcpy(d_out, outages, (size_t)S * 4, cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemcpy(dX, X, (size_t)S * rows * 8, cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) {
+    if (vt == 4)
+      ce = launch_apply<float>(0, grid, M.view<float>(), op, S, d_out, c->G.f, c->G.t, dX, dY,
+                               (float*)wbuf, vstride, c->opt.precond);
+    else
+      ce = launch_apply<double>(0, grid, M.view<double>(), op, S, d_out, c->G.f, c->G.t, dX, dY,
+                                (double*)wbuf, vstride, c->opt.precond);
+  }
+  if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
+  if (ce == cudaSuccess) ce = cudaMemcpy(Y, dY, (size_t)S * rows * 8, cudaMemcpyDeviceToHost);
+  if (ce != cudaSuccess) rs = fail(GPCG_ERR_CUDA, "gpcg_apply: %s", cudaGetErrorString(ce));
+  cudaFree(d_out); cudaFree(dX); cudaFree(dY); cudaFree(wbuf);
+  if (rs == GPCG_OK) g_err.clear();
+  return rs;
+}
+
+extern "C" gpcg_status gpcg_export_matrix(const gpcg_ctx* c, int32_t which, int32_t* bus_of_row,
+                                          int32_t* rowptr, int32_t* col, double* val,
+                                          int32_t* lrowptr, int32_t* lcol, double* lval,
+                                          int32_t* level) {
+  if (!c) return fail(GPCG_ERR_INVALID_ARG, "gpcg_export_matrix: ctx is NULL");
+  if (which != 0 && which != 1) return fail(GPCG_ERR_INVALID_ARG, "which must be 0 or 1");
+  const MatDev& M = which ? c->MQ : c->MP;
+  const MatrixPlan& P = M.plan;
+  if (bus_of_row) std::memcpy(bus_of_row, P.bus_of_row.data(), (size_t)P.n * 4);
+  if (rowptr) std::memcpy(rowptr, P.A.ptr.data(), P.A.ptr.size() * 4);
+  if (col) std::memcpy(col, P.A.idx.data(), P.A.idx.size() * 4);
+  if (lrowptr) std::memcpy(lrowptr, P.L.ptr.data(), P.L.ptr.size() * 4);
+  if (lcol) std::memcpy(lcol, P.L.idx.data(), P.L.idx.size() * 4);
+  if (level) std::memcpy(level, P.level.data(), (size_t)P.n * 4);
+  if (val) CUDA_TRY(cudaMemcpy(val, M.a_val, (size_t)P.A.nnz() * 8, cudaMemcpyDeviceToHost));
+  if (lval) CUDA_TRY(cudaMemcpy(lval, M.l_val, (size_t)P.L.nnz() * 8, cudaMemcpyDeviceToHost));
+  g_err.clear();
+  return GPCG_OK;
+}
+
+extern "C" gpcg_status gpcg_last_timings(gpcg_ctx* c, float* ms) {
+  if (!c || !ms) return fail(GPCG_ERR_INVALID_ARG, "gpcg_last_timings: NULL argument");
+  if (!c->timed) return fail(GPCG_ERR_NOT_READY, "no N-1 screen has run");
+  CUDA_TRY(cudaEventSynchronize(c->ev[2]));
+  CUDA_TRY(cudaEventElapsedTime(&ms[0], c->ev[0], c->ev[1]));
+  CUDA_TRY(cudaEventElapsedTime(&ms[1], c->ev[1], c->ev[2]));
+  g_err.clear();
+  return GPCG_OK;
+}
+
+extern "C" const char* gpcg_last_error(void) { return g_err.c_str(); }

@@ -1,0 +1,201 @@
+// Kernels that build the base-case structures once per grid: branch
+// admittances, the bus admittance diagonal, the B'/B'' values (Sec. III.B:
+// the diagonal .BIJ on the vertex, the off-diagonal .BIJ on the edge) and the
+// level-scheduled numeric factorisation of the base-case matrix that
+// preconditions every scenario (Sec. IV.B, eq. (6)).
+#include "common.cuh"
+
+namespace gpcg {
+
+// y = 1/(r + jx) = g + j b_y; weights of B' (1/x) and B'' (x/(r^2+x^2)).
+__global__ void branch_params_kernel(int m, const double* __restrict__ r,
+                                     const double* __restrict__ x, double* g, double* by,
+                                     double* wP, double* wQ) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  double rr = r[e], xx = x[e];
+  double d = rr * rr + xx * xx;
+  g[e] = rr / d;
+  by[e] = -xx / d;
+  wP[e] = 1.0 / xx;
+  wQ[e] = xx / d;
+}
+
+// Y_ii = sum over incident branches of (y + j b_sh/2), summed in the fixed
+// order of the bus adjacency lists.
+__global__ void ybus_diag_kernel(int n, const int32_t* __restrict__ adj_ptr,
+                                 const int32_t* __restrict__ adj_br,
+                                 const double* __restrict__ g, const double* __restrict__ by,
+                                 const double* __restrict__ b_sh, double* Gii, double* Bii) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double G = 0.0, B = 0.0;
+  for (int k = adj_ptr[i]; k < adj_ptr[i + 1]; ++k) {
+    int e = adj_br[k];
+    G += g[e];
+    B += by[e] + 0.5 * b_sh[e];
+  }
+  Gii[i] = G;
+  Bii[i] = B;
+}
+
+// Values of a grounded weighted Laplacian on its CSR pattern: one thread
+// per matrix row walks the bus's incident branches in a fixed order.  The
+// diagonal collects every incident branch (also those to buses without a
+// row); each neighbour with a row receives -w in its slot.
+__global__ void laplacian_values_kernel(int nrows, const int32_t* __restrict__ bus_of_row,
+                                        const int32_t* __restrict__ row_of_bus,
+                                        const int32_t* __restrict__ adj_ptr,
+                                        const int32_t* __restrict__ adj_idx,
+                                        const int32_t* __restrict__ adj_br,
+                                        const double* __restrict__ w,
+                                        const int32_t* __restrict__ a_ptr,
+                                        const int32_t* __restrict__ a_idx, double* a_val,
+                                        int32_t* err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrows) return;
+  int b = bus_of_row[i];
+  int s = a_ptr[i], e_ = a_ptr[i + 1];
+  for (int k = s; k < e_; ++k) a_val[k] = 0.0;
+  double diag = 0.0;
+  for (int k = adj_ptr[b]; k < adj_ptr[b + 1]; ++k) {
+    double we = w[adj_br[k]];
+    diag += we;
+    int c = row_of_bus[adj_idx[k]];
+    if (c < 0) continue;
+    int lo = s, hi = e_ - 1, pos = -1;
+    while (lo <= hi) {
+      int mid = (lo + hi) >> 1;
+      int v = a_idx[mid];
+      if (v == c) { pos = mid; break; }
+      if (v < c) lo = mid + 1; else hi = mid - 1;
+    }
+    if (pos < 0) { atomicExch(err, 1); continue; }
+    a_val[pos] -= we;
+  }
+  int lo = s, hi = e_ - 1, pos = -1;
+  while (lo <= hi) {
+    int mid = (lo + hi) >> 1;
+    int v = a_idx[mid];
+    if (v == i) { pos = mid; break; }
+    if (v < i) lo = mid + 1; else hi = mid - 1;
+  }
+  if (pos < 0) { atomicExch(err, 1); return; }
+  a_val[pos] += diag;
+}
+
+__device__ __forceinline__ double csr_lookup(const int32_t* idx, const double* val, int s,
+                                             int e, int col) {
+  int lo = s, hi = e - 1;
+  while (lo <= hi) {
+    int mid = (lo + hi) >> 1;
+    int v = idx[mid];
+    if (v == col) return val[mid];
+    if (v < col) lo = mid + 1; else hi = mid - 1;
+  }
+  return 0.0;
+}
+
+// Incomplete Cholesky on the pattern of L, rows of one level at a time (all
+// rows a row depends on sit in lower levels):
+//   L_ij = (A_ij - sum_{k<j} L_ik L_jk) / L_jj,   L_ii = sqrt(A_ii - sum L_ik^2),
+// the sums running over the columns both rows hold.  With the complete
+// symbolic pattern this is the exact Cholesky factor.
+__global__ void ic_level_kernel(int row0, int row1, const int32_t* __restrict__ a_ptr,
+                                const int32_t* __restrict__ a_idx,
+                                const double* __restrict__ a_val,
+                                const int32_t* __restrict__ l_ptr,
+                                const int32_t* __restrict__ l_idx, double* l_val,
+                                int32_t* err) {
+  int i = row0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= row1) return;
+  int ls = l_ptr[i], le = l_ptr[i + 1];
+  for (int k = ls; k < le; ++k) {
+    int j = l_idx[k];
+    double s = csr_lookup(a_idx, a_val, a_ptr[i], a_ptr[i + 1], j);
+    // merge row i (entries before k) with row j (off-diagonal entries)
+    int p = ls, q = l_ptr[j], qe = l_ptr[j + 1] - 1;
+    while (p < k && q < qe) {
+      int ci = l_idx[p], cj = l_idx[q];
+      if (ci == cj) { s -= l_val[p] * l_val[q]; ++p; ++q; }
+      else if (ci < cj) ++p;
+      else ++q;
+    }
+    if (j < i) {
+      l_val[k] = s / l_val[l_ptr[j + 1] - 1];
+    } else {
+      if (!(s > 0.0)) { atomicExch(err, 2); s = 1.0; }
+      l_val[k] = sqrt(s);
+    }
+  }
+}
+
+__global__ void scatter_kernel(int nnz, const int32_t* __restrict__ map,
+                               const double* __restrict__ src, double* dst) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nnz) dst[map[k]] = src[k];
+}
+
+__global__ void to_float_kernel(int n, const double* __restrict__ src, float* dst) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) dst[k] = (float)src[k];
+}
+
+__global__ void gather_diag_kernel(int n, const int32_t* __restrict__ pos,
+                                   const double* __restrict__ a_val, double* d) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) d[k] = a_val[pos[k]];
+}
+
+__global__ void gather_int_kernel(int n, const int32_t* __restrict__ idx,
+                                  const int32_t* __restrict__ src, int32_t* dst) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) dst[k] = src[idx[k]];
+}
+
+// ---------------------------------------------------------------- launchers
+static inline int nblk(int n, int b) { return (n + b - 1) / b; }
+
+void launch_branch_params(cudaStream_t st, int m, const double* r, const double* x, double* g,
+                          double* by, double* wP, double* wQ) {
+  if (m) branch_params_kernel<<<nblk(m, 256), 256, 0, st>>>(m, r, x, g, by, wP, wQ);
+}
+void launch_ybus_diag(cudaStream_t st, int n, const int32_t* adj_ptr, const int32_t* adj_br,
+                      const double* g, const double* by, const double* b_sh, double* Gii,
+                      double* Bii) {
+  if (n) ybus_diag_kernel<<<nblk(n, 256), 256, 0, st>>>(n, adj_ptr, adj_br, g, by, b_sh, Gii, Bii);
+}
+void launch_laplacian_values(cudaStream_t st, int nrows, const int32_t* bus_of_row,
+                             const int32_t* row_of_bus, const int32_t* adj_ptr,
+                             const int32_t* adj_idx, const int32_t* adj_br, const double* w,
+                             const int32_t* a_ptr, const int32_t* a_idx, double* a_val,
+                             int32_t* err) {
+  if (nrows)
+    laplacian_values_kernel<<<nblk(nrows, 128), 128, 0, st>>>(
+        nrows, bus_of_row, row_of_bus, adj_ptr, adj_idx, adj_br, w, a_ptr, a_idx, a_val, err);
+}
+void launch_ic_level(cudaStream_t st, int row0, int row1, const int32_t* a_ptr,
+                     const int32_t* a_idx, const double* a_val, const int32_t* l_ptr,
+                     const int32_t* l_idx, double* l_val, int32_t* err) {
+  int n = row1 - row0;
+  if (n > 0)
+    ic_level_kernel<<<nblk(n, 128), 128, 0, st>>>(row0, row1, a_ptr, a_idx, a_val, l_ptr,
+                                                  l_idx, l_val, err);
+}
+void launch_scatter(cudaStream_t st, int nnz, const int32_t* map, const double* src,
+                    double* dst) {
+  if (nnz) scatter_kernel<<<nblk(nnz, 256), 256, 0, st>>>(nnz, map, src, dst);
+}
+void launch_to_float(cudaStream_t st, int n, const double* src, float* dst) {
+  if (n) to_float_kernel<<<nblk(n, 256), 256, 0, st>>>(n, src, dst);
+}
+void launch_gather_diag(cudaStream_t st, int n, const int32_t* pos, const double* a_val,
+                        double* d) {
+  if (n) gather_diag_kernel<<<nblk(n, 256), 256, 0, st>>>(n, pos, a_val, d);
+}
+void launch_gather_int(cudaStream_t st, int n, const int32_t* idx, const int32_t* src,
+                       int32_t* dst) {
+  if (n) gather_int_kernel<<<nblk(n, 256), 256, 0, st>>>(n, idx, src, dst);
+}
+
+}  // namespace gpcg

@@ -1,0 +1,38 @@
+// Parameters and launchers of the persistent N-1 kernel (fdpf.cu).
+#pragma once
+#include "common.cuh"
+
+namespace gpcg {
+
+constexpr int NTHREADS = 256;
+constexpr double DIVERGE_LIMIT = 1.0e4;
+enum { PREC_IC0 = 0, PREC_JACOBI = 1, PREC_EXACT = 2 };
+
+struct FdpfParams {
+  DevGrid G;
+  int S = 0, n_tiles = 0;
+  ScenInfo sc;
+  const double *th0 = nullptr, *V0 = nullptr;  // warm start (bus order)
+  int flat_start = 0;
+  double tol = 1e-4, inner_rtol = 1e-5;
+  int max_outer = 50, max_inner = 500, precond = PREC_EXACT;
+  int32_t* tile_counter = nullptr;
+  void *wx = nullptr, *wr = nullptr, *wp = nullptr, *wq = nullptr, *wz = nullptr;
+  size_t vstride = 0;  // elements per slot of one vector
+  double *wth = nullptr, *wV = nullptr, *wc = nullptr, *ws = nullptr, *we = nullptr, *wf = nullptr;
+  size_t sstride = 0;  // elements per slot of one state array
+  double *out_theta = nullptr, *out_vm = nullptr, *out_flow = nullptr, *out_maxload = nullptr;
+  int32_t *out_iters = nullptr, *out_status = nullptr;
+};
+
+template <typename VT>
+cudaError_t launch_fdpf(cudaStream_t st, int T, int grid, const FdpfParams& P,
+                        const DevMatT<VT>& MP, const DevMatT<VT>& MQ);
+template <typename VT>
+int fdpf_max_blocks_per_sm(int T);
+template <typename VT>
+cudaError_t launch_apply(cudaStream_t st, int grid, const DevMatT<VT>& M, int op, int S,
+                         const int32_t* outages, const int32_t* f, const int32_t* t,
+                         const double* X, double* Y, VT* wbuf, size_t vstride, int precond);
+
+}  // namespace gpcg

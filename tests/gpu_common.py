@@ -1,0 +1,48 @@
+"""Shared fixtures of the GPU parity tests (the CUDA path via the C ABI
+against the CPU oracle on the same seeded inputs)."""
+import functools
+
+import numpy as np
+
+from gridgen import config_grid
+from oracle import powerflow as pf
+from oracle import screen
+
+
+@functools.lru_cache(maxsize=None)
+def grid(name):
+    return config_grid(name)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_base(name):
+    g = grid(name)
+    th, V, k, st, err = pf.base_case(g, tol=1e-11, max_outer=200)
+    assert st == pf.STATUS_OK
+    return th, V
+
+
+def oracle_n1(name, outages, tol=1e-10, processes=None):
+    g = grid(name)
+    th0, V0 = oracle_base(name)
+    return screen.n1_screen(g, th0, V0, outages, tol=tol, max_outer=100, processes=processes)
+
+
+def sample_outages(g, k, seed=0, include_bridges=True):
+    """A seeded sample of outages that always includes islanding ones."""
+    from oracle import islands
+    rng = np.random.default_rng(seed)
+    picks = set(rng.choice(g.n_branch, size=min(k, g.n_branch), replace=False).tolist())
+    if include_bridges:
+        on = np.ones(g.n_branch, bool)
+        found = 0
+        for l in rng.permutation(g.n_branch):
+            on[l] = False
+            lab = islands.components(g.n_bus, g.f, g.t, on)
+            on[l] = True
+            if (lab != lab[g.slack]).any():
+                picks.add(int(l))
+                found += 1
+                if found >= max(2, k // 8):
+                    break
+    return np.array(sorted(picks), dtype=np.int32)

@@ -1,0 +1,56 @@
+"""The C ABI library loads and exports every function include/gpcg.h
+declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "gpcg.h")).read()
+    return sorted(set(re.findall(r"GPCG_API\s+[\w\s\*]+?\b(gpcg_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_api():
+    names = declared()
+    for required in ("gpcg_create", "gpcg_base_solve", "gpcg_n1_screen", "gpcg_destroy",
+                     "gpcg_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1803_03290_gb300 import binding
+    lib = binding.load()
+    for name in declared():
+        assert hasattr(lib, name), name
+    assert set(binding.EXPORTS) <= set(declared())
+
+
+def test_invalid_arguments_fail_before_the_gpu():
+    import numpy as np
+    from paper_1803_03290_gb300 import binding
+    from gridgen import config_grid
+    g = config_grid("grid120")
+    bad = g.copy()
+    bad.bus_type = bad.bus_type.copy()
+    bad.bus_type[:] = 0           # no slack
+    with pytest.raises(binding.GPCGError) as e:
+        binding.GPCG(bad)
+    assert e.value.status == 1 and "slack" in str(e.value)
+    bad = g.copy()
+    bad.x = bad.x.copy()
+    bad.x[3] = 0.0
+    with pytest.raises(binding.GPCGError) as e:
+        binding.GPCG(bad)
+    assert e.value.status == 1
+    bad = g.copy()
+    bad.f = bad.f.copy()
+    bad.f[0] = bad.t[0]
+    with pytest.raises(binding.GPCGError) as e:
+        binding.GPCG(bad)
+    assert e.value.status == 1
+    with pytest.raises(binding.GPCGError):
+        binding.default_options(precision=7) and binding.GPCG(g, precision=7)

@@ -1,0 +1,205 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances: the FP64 paths agree with the oracle to rounding; solutions
+driven to a 1e-10 p.u. mismatch agree in angle to well below the 1e-6 rad
+bar; FP32 operators are held to a bound derived from FP32 rounding.
+"""
+import numpy as np
+import pytest
+
+import paper_1803_03290_gb300 as gp
+from gpu_common import grid, oracle_base, oracle_n1, sample_outages
+from oracle import factor, powerflow as pf, screen
+
+pytestmark = pytest.mark.gpu
+
+ANGLE_TOL = 1e-6      # rad, against the oracle at a 1e-10 p.u. mismatch
+MISMATCH_TOL = 1e-4   # p.u., the screening tolerance
+
+
+def make(name, **opt):
+    c = gp.GPCG(grid(name), **opt)
+    return c
+
+
+# ------------------------------------------------------------ a1, a2
+@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("precond", [gp.PRECOND_EXACT, gp.PRECOND_IC0])
+def test_matrix_and_factor(which, precond):
+    g = grid("grid120")
+    c = make("grid120", precond=precond)
+    d = c.export_matrix(which)
+    keep = np.flatnonzero(g.bus_type != 2) if which == 0 else np.flatnonzero(g.bus_type == 0)
+    on = np.ones(g.n_branch, bool)
+    A = (pf.bprime(g.n_bus, g.f, g.t, g.x, on, keep) if which == 0
+         else pf.bdprime(g.n_bus, g.f, g.t, g.r, g.x, on, keep)).toarray()
+    pos = {b: k for k, b in enumerate(keep)}
+    perm = np.array([pos[b] for b in d["bus_of_row"]])
+    Ap = A[np.ix_(perm, perm)]
+    n = Ap.shape[0]
+    Ag = np.zeros((n, n))
+    for i in range(n):
+        for k in range(d["rowptr"][i], d["rowptr"][i + 1]):
+            Ag[i, d["col"][k]] = d["val"][k]
+    np.testing.assert_allclose(Ag, Ap, rtol=0, atol=1e-12 * np.abs(Ap).max())
+    # the factor: oracle incomplete Cholesky on the exported pattern
+    rows = [sorted(d["lcol"][d["lrowptr"][i]:d["lrowptr"][i + 1]].tolist()) for i in range(n)]
+    from scipy.sparse import csr_matrix
+    Lo = factor.to_dense(factor.ic_on_pattern(csr_matrix(Ap), rows), n)
+    Lg = np.zeros((n, n))
+    for i in range(n):
+        for k in range(d["lrowptr"][i], d["lrowptr"][i + 1]):
+            Lg[i, d["lcol"][k]] = d["lval"][k]
+    np.testing.assert_allclose(Lg, Lo, rtol=0, atol=1e-11 * np.abs(Lo).max())
+    if precond == gp.PRECOND_EXACT:
+        np.testing.assert_allclose(Lg, np.linalg.cholesky(Ap), atol=1e-10 * np.abs(Lo).max())
+    # level schedule: every dependency sits in a lower level
+    lev = d["level"]
+    for i in range(n):
+        for j in rows[i][:-1]:
+            assert lev[j] < lev[i]
+
+
+# ------------------------------------------------------------ a8.1 / a8.2
+@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("precision", [gp.BATCHED_FP64, gp.BATCHED_FP32])
+def test_spmv_with_outage_stamp(which, precision):
+    g = grid("grid120")
+    c = make("grid120")
+    d = c.export_matrix(which)
+    keep = np.flatnonzero(g.bus_type != 2) if which == 0 else np.flatnonzero(g.bus_type == 0)
+    pos = {b: k for k, b in enumerate(keep)}
+    perm = np.array([pos[b] for b in d["bus_of_row"]])
+    outages = np.r_[np.arange(g.n_branch), -1].astype(np.int32)  # 181: ragged tail of 32-tiles
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((outages.size, perm.size))
+    Y = c.apply(which, 0, outages, X, precision)
+    for s, l in enumerate(outages):
+        on = np.ones(g.n_branch, bool)
+        if l >= 0:
+            on[l] = False
+        A = (pf.bprime(g.n_bus, g.f, g.t, g.x, on, keep) if which == 0
+             else pf.bdprime(g.n_bus, g.f, g.t, g.r, g.x, on, keep)).toarray()
+        ref = A[np.ix_(perm, perm)] @ X[s]
+        scale = np.abs(A).max() * np.abs(X[s]).max() * 8
+        tol = 1e-13 * scale if precision == gp.BATCHED_FP64 else 2e-6 * scale
+        np.testing.assert_allclose(Y[s], ref, rtol=0, atol=tol)
+
+
+@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("precond", [gp.PRECOND_EXACT, gp.PRECOND_IC0])
+def test_preconditioner_apply(which, precond):
+    c = make("grid2k", precond=precond)
+    d = c.export_matrix(which)
+    n = d["bus_of_row"].size
+    L = {i: {int(d["lcol"][k]): float(d["lval"][k])
+             for k in range(d["lrowptr"][i], d["lrowptr"][i + 1])} for i in range(n)}
+    outages = np.arange(37, dtype=np.int32)  # 37 scenarios: two tiles, ragged
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((outages.size, n))
+    Y64 = c.apply(which, 1, outages, X, gp.BATCHED_FP64)
+    Y32 = c.apply(which, 1, outages, X, gp.BATCHED_FP32)
+    for s in range(0, outages.size, 6):
+        ref = factor.apply_preconditioner(L, X[s])
+        np.testing.assert_allclose(Y64[s], ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
+    # FP32: the substitutions are backward stable; judge them by the
+    # residual of the FP64 factor, || L L^T y - x || <= c eps ||L|| ||L^T y||
+    import scipy.sparse as sp
+    Ls = sp.csr_matrix((d["lval"], d["lcol"], d["lrowptr"]), shape=(n, n))
+    for s in range(0, outages.size, 6):
+        res = Ls @ (Ls.T @ Y32[s]) - X[s]
+        bound = 64 * 6e-8 * (abs(Ls) @ (abs(Ls.T) @ np.abs(Y32[s]))).max()
+        assert np.abs(res).max() <= bound
+
+
+# ------------------------------------------------------------ a3
+@pytest.mark.parametrize("name", ["grid120", "grid2k"])
+def test_base_solve(name):
+    c = make(name)
+    b = c.base_solve()
+    th, V = oracle_base(name)
+    np.testing.assert_allclose(b["theta"], th, atol=1e-8)
+    np.testing.assert_allclose(b["V"], V, atol=1e-8)
+    assert c.info()["base_outer"] > 0
+
+
+# ------------------------------------------------------------ full N-1
+def _compare(g, res, ref, outages, angle_tol):
+    np.testing.assert_array_equal(res["label"], ref["label"])
+    np.testing.assert_array_equal(res["status"], ref["status"])
+    ok = np.isin(ref["status"], [0, 3])
+    assert ok.sum() > 0.9 * len(outages)
+    np.testing.assert_allclose(res["theta"][ok], ref["theta"][ok], rtol=0, atol=angle_tol)
+    np.testing.assert_allclose(res["V"][ok], ref["V"][ok], rtol=0, atol=angle_tol)
+    np.testing.assert_allclose(res["flow"][ok], ref["flow"][ok], rtol=0, atol=10 * angle_tol)
+    np.testing.assert_allclose(res["max_loading"][ok], ref["max_loading"][ok], atol=10 * angle_tol)
+
+
+@pytest.mark.parametrize("precision,precond", [
+    (gp.BATCHED_FP64, gp.PRECOND_EXACT), (gp.BATCHED_FP32, gp.PRECOND_EXACT),
+    (gp.BATCHED_FP64, gp.PRECOND_IC0), (gp.BATCHED_FP32, gp.PRECOND_IC0),
+    (gp.BATCHED_FP64, gp.PRECOND_JACOBI), (gp.PLAIN_FP64, gp.PRECOND_EXACT)])
+def test_n1_grid120_all_outages(precision, precond):
+    g = grid("grid120")
+    c = make("grid120", precision=precision, precond=precond, tol=1e-10, max_outer=100,
+             inner_rtol=1e-6, max_inner=2000)
+    c.base_solve()
+    outages = np.arange(g.n_branch, dtype=np.int32)
+    res = c.n1_screen(outages)
+    ref = oracle_n1("grid120", outages, processes=1)
+    _compare(g, res, ref, outages, ANGLE_TOL)
+    assert (res["iters"][:, 0] >= 1).all()
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_n1_tiles_ragged(tile):
+    g = grid("grid120")
+    c = make("grid120", tile=tile, tol=1e-10, max_outer=100)
+    c.base_solve()
+    outages = np.arange(g.n_branch - 1, -1, -3, dtype=np.int32)  # 60 scenarios, reversed
+    res = c.n1_screen(outages)
+    ref = oracle_n1("grid120", outages, processes=1)
+    _compare(g, res, ref, outages, ANGLE_TOL)
+
+
+def test_n1_grid2k_sample_refined():
+    g = grid("grid2k")
+    c = make("grid2k", tol=1e-10, max_outer=100)
+    c.base_solve()
+    outages = sample_outages(g, 96, seed=3)
+    res = c.n1_screen(outages)
+    ref = oracle_n1("grid2k", outages)
+    _compare(g, res, ref, outages, ANGLE_TOL)
+
+
+def test_n1_grid2k_screen_mismatch():
+    """At the screening tolerance every converged scenario's state has an
+    FP64 mismatch (evaluated by the oracle) of at most 1e-4 p.u."""
+    g = grid("grid2k")
+    c = make("grid2k")
+    c.base_solve()
+    outages = np.arange(g.n_branch, dtype=np.int32)
+    res = c.n1_screen(outages, outputs=("theta", "V", "status", "iters"))
+    rng = np.random.default_rng(4)
+    ok = np.flatnonzero(res["status"] == 0)
+    assert ok.size > 0.9 * outages.size
+    for s in rng.choice(ok, 60, replace=False):
+        e = screen.scenario_mismatch(g, int(outages[s]), res["theta"][s], res["V"][s])
+        assert e <= MISMATCH_TOL * (1 + 1e-9)
+
+
+def test_edge_cases():
+    g = grid("grid120")
+    c = make("grid120")
+    with pytest.raises(gp.GPCGError):
+        c.n1_screen(np.array([0], np.int32))   # base case not solved yet
+    c.base_solve()
+    r = c.n1_screen(np.zeros(0, np.int32))
+    assert r["theta"].shape == (0, g.n_bus)
+    with pytest.raises(gp.GPCGError):
+        c.n1_screen(np.array([g.n_branch], np.int32))
+    with pytest.raises(gp.GPCGError):
+        c.n1_screen(np.array([-1], np.int32))
+    # duplicates give identical answers
+    r = c.n1_screen(np.array([5, 5, 5], np.int32))
+    assert np.array_equal(r["theta"][0], r["theta"][2])
