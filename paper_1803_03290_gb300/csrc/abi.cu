@@ -30,11 +30,15 @@ void launch_scatter(cudaStream_t, int, const int32_t*, const double*, double*);
 void launch_to_float(cudaStream_t, int, const double*, float*);
 void launch_gather_diag(cudaStream_t, int, const int32_t*, const double*, double*);
 void launch_gather_int(cudaStream_t, int, const int32_t*, const int32_t*, int32_t*);
+void launch_gather_val(cudaStream_t, int, const int32_t*, const double*, double*, float*);
+void launch_inv_diag(cudaStream_t, int, const int32_t*, const double*, double*, float*);
+void launch_adj_values(cudaStream_t, int, const int32_t*, const double*, const double*, double*,
+                       double*);
 // islands.cu
 size_t islands_smem(int n);
 cudaError_t launch_islands(cudaStream_t, int, int, int, int, int, const int32_t*, const int32_t*,
                            const int32_t*, const int8_t*, const double*, const double*,
-                           const int32_t*, double, int32_t*, int32_t*, double*, int32_t*,
+                           const int32_t*, int32_t*, int32_t*, double*, int32_t*,
                            int32_t*, int32_t*);
 }  // namespace gpcg
 
@@ -65,15 +69,34 @@ static gpcg_status fail(gpcg_status st, const char* fmt, ...) {
   } while (0)
 
 // ------------------------------------------------------------------ context
+// Padded rows (ELL) of one operator: integer structure built on the host,
+// values gathered on the device from the CSR values through `src`.
+struct EllDev {
+  int K = 0;
+  int32_t *col = nullptr, *src = nullptr;    // [n*K]; src = CSR position or -1
+  int32_t *optr = nullptr, *ocol = nullptr, *osrc = nullptr;
+  double* val = nullptr;
+  float* val32 = nullptr;
+  double* oval = nullptr;
+  float* oval32 = nullptr;
+  int nslot = 0, nover = 0;
+  template <typename VT>
+  Ell<VT> view() const;
+};
+template <>
+Ell<double> EllDev::view<double>() const { return Ell<double>{col, val, optr, ocol, oval}; }
+template <>
+Ell<float> EllDev::view<float>() const { return Ell<float>{col, val32, optr, ocol, oval32}; }
+
 struct MatDev {
   MatrixPlan plan;
   int32_t *bus_of_row = nullptr, *row_of_bus = nullptr, *pre_of_row = nullptr;
   int32_t *a_ptr = nullptr, *a_idx = nullptr, *a_diag = nullptr;
-  int32_t *l_ptr = nullptr, *l_idx = nullptr, *u_ptr = nullptr, *u_idx = nullptr,
-          *l_to_u = nullptr;
+  int32_t *l_ptr = nullptr, *l_idx = nullptr, *l_diag = nullptr;
   int32_t *lev_ptr = nullptr, *blev_ptr = nullptr, *blev_rows = nullptr;
-  double *a_val = nullptr, *l_val = nullptr, *u_val = nullptr, *diag = nullptr;
-  float *a_val32 = nullptr, *l_val32 = nullptr, *u_val32 = nullptr, *diag32 = nullptr;
+  double *a_val = nullptr, *l_val = nullptr, *diag = nullptr, *inv_diag = nullptr;
+  float *diag32 = nullptr, *inv_diag32 = nullptr;
+  EllDev A, L, U;
   double* w = nullptr;  // per-branch weight
   template <typename VT>
   DevMatT<VT> view() const;
@@ -84,9 +107,8 @@ DevMatT<double> MatDev::view<double>() const {
   DevMatT<double> M;
   M.n = plan.n;
   M.bus_of_row = bus_of_row; M.row_of_bus = row_of_bus; M.pre_of_row = pre_of_row;
-  M.a_ptr = a_ptr; M.a_idx = a_idx; M.a_val = a_val;
-  M.l_ptr = l_ptr; M.l_idx = l_idx; M.l_val = l_val;
-  M.u_ptr = u_ptr; M.u_idx = u_idx; M.u_val = u_val;
+  M.A = A.view<double>(); M.L = L.view<double>(); M.U = U.view<double>();
+  M.inv_diag = inv_diag;
   M.diag = diag;
   M.lev_ptr = lev_ptr; M.blev_ptr = blev_ptr; M.blev_rows = blev_rows;
   M.nlev = (int)plan.lev_ptr.size() - 1;
@@ -99,9 +121,8 @@ DevMatT<float> MatDev::view<float>() const {
   DevMatT<float> M;
   M.n = plan.n;
   M.bus_of_row = bus_of_row; M.row_of_bus = row_of_bus; M.pre_of_row = pre_of_row;
-  M.a_ptr = a_ptr; M.a_idx = a_idx; M.a_val = a_val32;
-  M.l_ptr = l_ptr; M.l_idx = l_idx; M.l_val = l_val32;
-  M.u_ptr = u_ptr; M.u_idx = u_idx; M.u_val = u_val32;
+  M.A = A.view<float>(); M.L = L.view<float>(); M.U = U.view<float>();
+  M.inv_diag = inv_diag32;
   M.diag = diag32;
   M.lev_ptr = lev_ptr; M.blev_ptr = blev_ptr; M.blev_rows = blev_rows;
   M.nlev = (int)plan.lev_ptr.size() - 1;
@@ -121,12 +142,13 @@ struct gpcg_ctx {
   std::vector<uint8_t> bridge;
   int n_bridges = 0;
   double pv_gen_total = 0.0;
+  int n_adj_slots = 0, n_adj_over = 0;
   DevGrid G;
   double *wP = nullptr, *wQ = nullptr;
   MatDev MP, MQ;
   int planned_precond = -1;
   // base case
-  double *th0 = nullptr, *V0 = nullptr, *flow0 = nullptr;
+  double *th0 = nullptr, *V0 = nullptr, *flow0 = nullptr, *c0 = nullptr, *s0 = nullptr;
   int base_outer = -1;
   bool base_ok = false;
   // per-call buffers
@@ -197,6 +219,59 @@ static gpcg_status check_options(const gpcg_options& o) {
 }
 
 // ------------------------------------------------------------------ build
+// Host side of a padded-row operator: for each row the first K entries of
+// `entries[row]` (pairs of column, source position) go to the slots, the
+// rest to the overflow CSR; padding points at `pad_col` with source -1.
+struct EllHost {
+  int K = 0;
+  std::vector<int32_t> col, src, optr, ocol, osrc;
+};
+
+static EllHost ell_from_rows(const std::vector<std::vector<std::pair<int, int>>>& rows, int K,
+                             int pad_col) {
+  EllHost E;
+  E.K = K;
+  const int n = (int)rows.size();
+  E.col.assign((size_t)n * K, pad_col);
+  E.src.assign((size_t)n * K, -1);
+  E.optr.assign(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    const auto& r = rows[i];
+    for (size_t k = 0; k < r.size(); ++k) {
+      if ((int)k < K) {
+        E.col[(size_t)i * K + k] = r[k].first;
+        E.src[(size_t)i * K + k] = r[k].second;
+      } else {
+        E.ocol.push_back(r[k].first);
+        E.osrc.push_back(r[k].second);
+      }
+    }
+    E.optr[i + 1] = (int32_t)E.ocol.size();
+  }
+  return E;
+}
+
+static cudaError_t ell_upload(std::vector<void*>& own, const EllHost& H, EllDev& D) {
+  cudaError_t ce;
+  D.K = H.K;
+  D.nslot = (int)H.col.size();
+  D.nover = (int)H.ocol.size();
+  if ((ce = upload(own, &D.col, H.col.data(), H.col.size())) != cudaSuccess) return ce;
+  if ((ce = upload(own, &D.src, H.src.data(), H.src.size())) != cudaSuccess) return ce;
+  if ((ce = upload(own, &D.optr, H.optr.data(), H.optr.size())) != cudaSuccess) return ce;
+  if ((ce = upload(own, &D.ocol, H.ocol.data(), H.ocol.size())) != cudaSuccess) return ce;
+  if ((ce = upload(own, &D.osrc, H.osrc.data(), H.osrc.size())) != cudaSuccess) return ce;
+  if ((ce = dalloc(own, &D.val, H.col.size())) != cudaSuccess) return ce;
+  if ((ce = dalloc(own, &D.val32, H.col.size())) != cudaSuccess) return ce;
+  if ((ce = dalloc(own, &D.oval, H.ocol.size())) != cudaSuccess) return ce;
+  return dalloc(own, &D.oval32, H.ocol.size());
+}
+
+static void ell_fill(cudaStream_t st, EllDev& D, const double* csr_val) {
+  launch_gather_val(st, D.nslot, D.src, csr_val, D.val, D.val32);
+  launch_gather_val(st, D.nover, D.osrc, csr_val, D.oval, D.oval32);
+}
+
 static gpcg_status build_matrix(gpcg_ctx* c, MatDev& M, const std::vector<uint8_t>& keep,
                                 double* w, bool fill) {
   M.plan = plan_matrix(c->n, c->bg, keep, fill);
@@ -212,21 +287,34 @@ static gpcg_status build_matrix(gpcg_ctx* c, MatDev& M, const std::vector<uint8_
   CUDA_TRY(upload(own, &M.a_diag, P.a_diag.data(), P.n));
   CUDA_TRY(upload(own, &M.l_ptr, P.L.ptr.data(), P.L.ptr.size()));
   CUDA_TRY(upload(own, &M.l_idx, P.L.idx.data(), P.L.idx.size()));
-  CUDA_TRY(upload(own, &M.u_ptr, P.U.ptr.data(), P.U.ptr.size()));
-  CUDA_TRY(upload(own, &M.u_idx, P.U.idx.data(), P.U.idx.size()));
-  CUDA_TRY(upload(own, &M.l_to_u, P.l_to_u.data(), P.l_to_u.size()));
   CUDA_TRY(upload(own, &M.lev_ptr, P.lev_ptr.data(), P.lev_ptr.size()));
   CUDA_TRY(upload(own, &M.blev_ptr, P.blev_ptr.data(), P.blev_ptr.size()));
   CUDA_TRY(upload(own, &M.blev_rows, P.blev_rows.data(), P.blev_rows.size()));
+  std::vector<int32_t> ldiag(P.n);
+  for (int i = 0; i < P.n; ++i) ldiag[i] = P.L.ptr[i + 1] - 1;
+  CUDA_TRY(upload(own, &M.l_diag, ldiag.data(), P.n));
   const int nnz = P.A.nnz(), nl = P.L.nnz();
   CUDA_TRY(dalloc(own, &M.a_val, nnz));
   CUDA_TRY(dalloc(own, &M.l_val, nl));
-  CUDA_TRY(dalloc(own, &M.u_val, nl));
   CUDA_TRY(dalloc(own, &M.diag, P.n));
-  CUDA_TRY(dalloc(own, &M.a_val32, nnz));
-  CUDA_TRY(dalloc(own, &M.l_val32, nl));
-  CUDA_TRY(dalloc(own, &M.u_val32, nl));
   CUDA_TRY(dalloc(own, &M.diag32, P.n));
+  CUDA_TRY(dalloc(own, &M.inv_diag, P.n));
+  CUDA_TRY(dalloc(own, &M.inv_diag32, P.n));
+  // padded rows: A (all entries), strictly lower L, strictly upper L^T
+  {
+    std::vector<std::vector<std::pair<int, int>>> ra(P.n), rl(P.n), ru(P.n);
+    for (int i = 0; i < P.n; ++i) {
+      for (int k = P.A.ptr[i]; k < P.A.ptr[i + 1]; ++k) ra[i].push_back({P.A.idx[k], k});
+      for (int k = P.L.ptr[i]; k < P.L.ptr[i + 1] - 1; ++k) rl[i].push_back({P.L.idx[k], k});
+    }
+    std::vector<int32_t> u_to_l(nl);
+    for (int k = 0; k < nl; ++k) u_to_l[P.l_to_u[k]] = k;
+    for (int i = 0; i < P.n; ++i)
+      for (int k = P.U.ptr[i] + 1; k < P.U.ptr[i + 1]; ++k) ru[i].push_back({P.U.idx[k], u_to_l[k]});
+    CUDA_TRY(ell_upload(own, ell_from_rows(ra, KA, P.n), M.A));
+    CUDA_TRY(ell_upload(own, ell_from_rows(rl, KL, P.n), M.L));
+    CUDA_TRY(ell_upload(own, ell_from_rows(ru, KU, P.n), M.U));
+  }
   M.w = w;
   cudaStream_t st = 0;
   CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int32_t)));
@@ -235,12 +323,12 @@ static gpcg_status build_matrix(gpcg_ctx* c, MatDev& M, const std::vector<uint8_
   for (size_t k = 0; k + 1 < P.lev_ptr.size(); ++k)
     launch_ic_level(st, P.lev_ptr[k], P.lev_ptr[k + 1], M.a_ptr, M.a_idx, M.a_val, M.l_ptr,
                     M.l_idx, M.l_val, c->d_err);
-  launch_scatter(st, nl, M.l_to_u, M.l_val, M.u_val);
   launch_gather_diag(st, P.n, M.a_diag, M.a_val, M.diag);
-  launch_to_float(st, nnz, M.a_val, M.a_val32);
-  launch_to_float(st, nl, M.l_val, M.l_val32);
-  launch_to_float(st, nl, M.u_val, M.u_val32);
   launch_to_float(st, P.n, M.diag, M.diag32);
+  launch_inv_diag(st, P.n, M.l_diag, M.l_val, M.inv_diag, M.inv_diag32);
+  ell_fill(st, M.A, M.a_val);
+  ell_fill(st, M.L, M.l_val);
+  ell_fill(st, M.U, M.l_val);
   CUDA_TRY(cudaGetLastError());
   int32_t herr = 0;
   CUDA_TRY(cudaMemcpy(&herr, c->d_err, sizeof herr, cudaMemcpyDeviceToHost));
@@ -367,6 +455,30 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
   UP(G.adj_idx, c->bg.adj.idx.data(), c->bg.adj.idx.size());
   UP(G.adj_br, c->bg.adj_branch.data(), c->bg.adj_branch.size());
   UP(G.pre, c->pre.data(), n);
+  {
+    // padded adjacency of the mismatch: padding repeats the bus itself with a
+    // zero admittance and branch id -2
+    std::vector<std::vector<std::pair<int, int>>> rows(n);
+    for (int b = 0; b < n; ++b)
+      for (int k = c->bg.adj.ptr[b]; k < c->bg.adj.ptr[b + 1]; ++k)
+        rows[b].push_back({c->bg.adj.idx[k], c->bg.adj_branch[k]});
+    EllHost E = ell_from_rows(rows, KG, 0);
+    std::vector<int32_t> pad_nbr(E.col), brl(E.src);
+    for (int b = 0; b < n; ++b)
+      for (int k = 0; k < KG; ++k)
+        if (brl[(size_t)b * KG + k] < 0) { pad_nbr[(size_t)b * KG + k] = b; brl[(size_t)b * KG + k] = -2; }
+    UP(G.adj_nbr, pad_nbr.data(), pad_nbr.size());
+    UP(G.adj_brl, brl.data(), brl.size());
+    UP(G.adj_optr, E.optr.data(), E.optr.size());
+    UP(G.adj_onbr, E.ocol.data(), E.ocol.size());
+    UP(G.adj_obr, E.osrc.data(), E.osrc.size());
+    AL(G.adj_g, pad_nbr.size());
+    AL(G.adj_b, pad_nbr.size());
+    AL(G.adj_og, E.ocol.size());
+    AL(G.adj_ob, E.ocol.size());
+    c->n_adj_slots = (int)pad_nbr.size();
+    c->n_adj_over = (int)E.ocol.size();
+  }
   UP(G.sub, c->sub.data(), n);
   AL(G.g, m);
   AL(G.by, m);
@@ -377,6 +489,8 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
   AL(c->th0, n);
   AL(c->V0, n);
   AL(c->flow0, m);
+  AL(c->c0, n);
+  AL(c->s0, n);
   AL(c->d_counter, 1);
   AL(c->d_err, 1);
   for (auto& e : c->ev)
@@ -385,6 +499,8 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
 #undef AL
   launch_branch_params(0, m, G.r, G.x, G.g, G.by, c->wP, c->wQ);
   launch_ybus_diag(0, n, G.adj_ptr, G.adj_br, G.g, G.by, G.b_sh, G.Gii, G.Bii);
+  launch_adj_values(0, c->n_adj_slots, G.adj_brl, G.g, G.by, G.adj_g, G.adj_b);
+  launch_adj_values(0, c->n_adj_over, G.adj_obr, G.g, G.by, G.adj_og, G.adj_ob);
   if ((ce = cudaGetLastError()) != cudaSuccess) return fail_cuda(ce, "build kernels");
   st = build_matrices(c);
   if (st != GPCG_OK) {
@@ -477,7 +593,7 @@ static Layout make_layout(const gpcg_ctx* c, int T, int slots, size_t vt_size) {
   Layout L;
   L.T = T;
   L.slots = slots;
-  const size_t rows = (size_t)std::max(c->MP.plan.n, c->MQ.plan.n);
+  const size_t rows = (size_t)std::max(c->MP.plan.n, c->MQ.plan.n) + 1;  // + the zero row
   L.vstride = rows * T;
   L.sstride = (size_t)c->n * T;
   L.vec_bytes = ((L.vstride * vt_size + 255) / 256) * 256;
@@ -546,7 +662,7 @@ extern "C" gpcg_status gpcg_base_solve(gpcg_ctx* c, double* theta, double* vm, d
   CUDA_TRY(cudaMalloc(&d_iters3, 3 * sizeof(int32_t)));
   P.out_iters = d_iters3;
   P.out_status = d_stat;
-  s = run_fdpf<double>(c, st, P, 1, 1);
+  s = run_fdpf<double>(c, st, P, 2, 1);
   int32_t hs = -1, hit[3] = {0, 0, 0};
   if (s == GPCG_OK) {
     cudaError_t ce = cudaDeviceSynchronize();
@@ -562,6 +678,8 @@ extern "C" gpcg_status gpcg_base_solve(gpcg_ctx* c, double* theta, double* vm, d
     return fail(GPCG_ERR_BASE_NOT_CONVERGED,
                 "base case did not converge (status %d after %d outer iterations)", hs, hit[0]);
   }
+  CUDA_TRY(launch_base_trig(0, c->n, c->th0, c->c0, c->s0));
+  CUDA_TRY(cudaDeviceSynchronize());
   c->base_ok = true;
   if (theta) CUDA_TRY(cudaMemcpy(theta, c->th0, (size_t)c->n * 8, cudaMemcpyDeviceToHost));
   if (vm) CUDA_TRY(cudaMemcpy(vm, c->V0, (size_t)c->n * 8, cudaMemcpyDeviceToHost));
@@ -637,7 +755,7 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
   CUDA_TRY(cudaEventRecord(c->ev[0], st));
   const int cc_grid = std::min<int>((int)S, c->num_sms * 4);
   ce = launch_islands(st, cc_grid, c->n, c->m, c->slack, (int)S, c->d_outages, c->G.f, c->G.t,
-                      c->G.bus_type, c->G.P_sched, c->G.P_gen, c->G.pre, c->pv_gen_total,
+                      c->G.bus_type, c->G.P_sched, c->G.P_gen, c->G.pre,
                       c->d_lo, c->d_cnt, c->d_coef, c->d_nogen, d_lab, c->d_err);
   if (ce != cudaSuccess) { cleanup(); return fail(GPCG_ERR_CUDA, "islands: %s", cudaGetErrorString(ce)); }
   CUDA_TRY(cudaEventRecord(c->ev[1], st));
@@ -646,6 +764,8 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
   P.sc = ScenInfo{c->d_outages, c->d_lo, c->d_cnt, c->d_coef, c->d_nogen};
   P.th0 = c->th0;
   P.V0 = c->V0;
+  P.c0 = c->c0;
+  P.s0 = c->s0;
   P.out_theta = d_theta; P.out_vm = d_vm; P.out_flow = d_flow; P.out_maxload = d_ml;
   P.out_iters = d_iters; P.out_status = d_stat;
   gpcg_status rs = GPCG_OK;
@@ -662,7 +782,7 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
       Q.out_maxload = d_ml ? d_ml + s : nullptr;
       Q.out_iters = d_iters ? d_iters + 3 * s : nullptr;
       Q.out_status = d_stat ? d_stat + s : nullptr;
-      rs = run_fdpf<double>(c, st, Q, 1, 1);
+      rs = run_fdpf<double>(c, st, Q, 2, 1);
     }
   } else {
     const int T = c->opt.tile ? c->opt.tile : (c->tile ? c->tile : 32);
@@ -720,7 +840,7 @@ extern "C" gpcg_status gpcg_apply(gpcg_ctx* c, int32_t which, int32_t op, const 
   const size_t vt = precision == GPCG_BATCHED_FP32 ? 4 : 8;
   const int T = 32;
   const int grid = std::max(1, std::min((S + T - 1) / T, c->num_sms * 2));
-  const size_t vstride = (size_t)rows * T;
+  const size_t vstride = (size_t)(rows + 1) * T;
   int32_t* d_out = nullptr;
   double *dX = nullptr, *dY = nullptr;
   void* wbuf = nullptr;
@@ -728,7 +848,7 @@ extern "C" gpcg_status gpcg_apply(gpcg_ctx* c, int32_t which, int32_t op, const 
   cudaError_t ce = cudaMalloc(&d_out, (size_t)S * 4);
   if (ce == cudaSuccess) ce = cudaMalloc(&dX, (size_t)S * rows * 8 + 8);
   if (ce == cudaSuccess) ce = cudaMalloc(&dY, (size_t)S * rows * 8 + 8);
-  if (ce == cudaSuccess) ce = cudaMalloc(&wbuf, (size_t)grid * 4 * vstride * vt + 8);
+  if (ce == cudaSuccess) ce = cudaMalloc(&wbuf, (size_t)grid * 3 * vstride * vt + 16);
   if (ce == cudaSuccess) ce = cudaMemcpy(d_out, outages, (size_t)S * 4, cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(dX, X, (size_t)S * rows * 8, cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) {

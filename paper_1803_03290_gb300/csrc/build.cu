@@ -199,3 +199,51 @@ void launch_gather_int(cudaStream_t st, int n, const int32_t* idx, const int32_t
 }
 
 }  // namespace gpcg
+
+namespace gpcg {
+
+// dst[k] = csr[src[k]] (0 where src[k] < 0), in FP64 and FP32.
+__global__ void gather_val_kernel(int n, const int32_t* __restrict__ src,
+                                  const double* __restrict__ csr, double* dst, float* dst32) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int s = src[k];
+  const double v = s >= 0 ? csr[s] : 0.0;
+  dst[k] = v;
+  dst32[k] = (float)v;
+}
+
+__global__ void inv_diag_kernel(int n, const int32_t* __restrict__ pos,
+                                const double* __restrict__ l_val, double* inv, float* inv32) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double d = 1.0 / l_val[pos[i]];
+  inv[i] = d;
+  inv32[i] = (float)d;
+}
+
+// Per-slot branch admittance of the mismatch adjacency (0 on padding).
+__global__ void adj_values_kernel(int n, const int32_t* __restrict__ br,
+                                  const double* __restrict__ g, const double* __restrict__ by,
+                                  double* ag, double* ab) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int e = br[k];
+  ag[k] = e >= 0 ? g[e] : 0.0;
+  ab[k] = e >= 0 ? by[e] : 0.0;
+}
+
+void launch_gather_val(cudaStream_t st, int n, const int32_t* src, const double* csr, double* dst,
+                       float* dst32) {
+  if (n > 0) gather_val_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, src, csr, dst, dst32);
+}
+void launch_inv_diag(cudaStream_t st, int n, const int32_t* pos, const double* l_val, double* inv,
+                     float* inv32) {
+  if (n > 0) inv_diag_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, pos, l_val, inv, inv32);
+}
+void launch_adj_values(cudaStream_t st, int n, const int32_t* br, const double* g,
+                       const double* by, double* ag, double* ab) {
+  if (n > 0) adj_values_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, br, g, by, ag, ab);
+}
+
+}  // namespace gpcg

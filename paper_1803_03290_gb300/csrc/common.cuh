@@ -5,6 +5,14 @@
 
 namespace gpcg {
 
+// Slots per row of the padded row descriptors (ELL layout: row i's entries
+// at [i*K, i*K+K), padding points at the zero row and carries value 0;
+// entries beyond K live in a small per-matrix overflow CSR).
+constexpr int KA = 6;   // B' / B'' rows, diagonal included
+constexpr int KL = 4;   // strictly lower part of the factor
+constexpr int KU = 4;   // strictly upper part (L^T)
+constexpr int KG = 6;   // bus adjacency of the mismatch
+
 // Grid arrays on the device (bus order and branch order of the caller).
 struct DevGrid {
   int n = 0, m = 0, slack = -1;
@@ -13,24 +21,37 @@ struct DevGrid {
   int32_t *f = nullptr, *t = nullptr;
   double *r = nullptr, *x = nullptr, *b_sh = nullptr, *rating = nullptr;
   double *g = nullptr, *by = nullptr;        // series admittance g + j b_y
-  int32_t *adj_ptr = nullptr, *adj_idx = nullptr, *adj_br = nullptr;
+  int32_t *adj_ptr = nullptr, *adj_idx = nullptr, *adj_br = nullptr;  // CSR adjacency
   double *Gii = nullptr, *Bii = nullptr;     // bus admittance diagonal
   int32_t *pre = nullptr, *sub = nullptr;    // depth-first preorder, subtree size
+  // padded adjacency for the mismatch: neighbour, branch, -g, -b_y per slot
+  int32_t *adj_nbr = nullptr, *adj_brl = nullptr;
+  double *adj_g = nullptr, *adj_b = nullptr;
+  int32_t *adj_optr = nullptr, *adj_onbr = nullptr, *adj_obr = nullptr;
+  double *adj_og = nullptr, *adj_ob = nullptr;
+};
+
+// Padded rows plus overflow of one sparse operator.
+template <typename VT>
+struct Ell {
+  const int32_t* col = nullptr;   // [n*K]
+  const VT* val = nullptr;        // [n*K]
+  const int32_t* optr = nullptr;  // [n+1] overflow CSR
+  const int32_t* ocol = nullptr;
+  const VT* oval = nullptr;
 };
 
 // One fast-decoupled matrix (B' or B'') with its base-case factor.  VT is
-// the value type used by the solve kernels (float or double).
+// the value type used by the solve kernels (float or double).  Vectors of
+// this matrix have n+1 rows per scenario: row n is kept at zero and is what
+// padding slots point at.
 template <typename VT>
 struct DevMatT {
   int n = 0;
   const int32_t *bus_of_row = nullptr, *row_of_bus = nullptr, *pre_of_row = nullptr;
-  const int32_t *a_ptr = nullptr, *a_idx = nullptr;
-  const VT* a_val = nullptr;
-  const int32_t *l_ptr = nullptr, *l_idx = nullptr;
-  const VT* l_val = nullptr;
-  const int32_t *u_ptr = nullptr, *u_idx = nullptr;
-  const VT* u_val = nullptr;
-  const VT* diag = nullptr;                  // diagonal of A (Jacobi)
+  Ell<VT> A, L, U;
+  const VT* inv_diag = nullptr;              // 1 / L_ii
+  const VT* diag = nullptr;                  // A_ii (Jacobi)
   const int32_t *lev_ptr = nullptr;          // forward levels (contiguous rows)
   const int32_t *blev_ptr = nullptr, *blev_rows = nullptr;
   int nlev = 0, nblev = 0;

@@ -2,9 +2,10 @@
 // whole fast-decoupled power flow of that tile (Sec. III.B eqs. (4)-(5),
 // Sec. IV) without leaving the kernel, then takes the next tile from a
 // device-side counter.  Vectors live in global memory as [row][T] per CTA
-// slot, so every row access of a warp is one contiguous chunk across the
-// tile's scenarios.  Tiles are independent: the only inter-CTA traffic is
-// the atomic tile counter, and no CTA ever waits on another.
+// slot, so a row touches one contiguous chunk across the tile's scenarios;
+// each thread owns two adjacent scenario lanes of a row.  Tiles are
+// independent: the only inter-CTA traffic is the atomic tile counter, and no
+// CTA ever waits on another.
 //
 // Per outer iteration and scenario (Sec. III.B, eqs. (4)-(5)):
 //   FP64 mismatch dP, dQ (eqs. (1)-(3)), convergence test;
@@ -15,73 +16,124 @@
 // four-element change (Sec. IV.B) applied on the fly inside the SpMV.
 // Islanded buses (Sec. IV.C) are masked out of the right-hand side and of
 // the search directions; their state stays zero.
+//
+// Every sparse row is read through a padded descriptor (ELL): its column
+// indices and values sit at fixed offsets, so a thread issues all of a row's
+// gathers at once instead of walking a row pointer first.
 #include <math.h>
 #include "common.cuh"
 #include "fdpf.h"
 
 namespace gpcg {
 
+constexpr int LP = 2;  // scenario lanes per thread
+#ifndef FDPF_MIN_BLOCKS
+#define FDPF_MIN_BLOCKS 2  // resident CTAs per SM the register budget is cut for
+#endif
+
 // Inner iterations without progress after which a solve stops: the outer
 // FP64 loop then refines the answer (iterative refinement).
-constexpr int STALL_ITERS = 16;
+constexpr int STALL_ITERS = 50;
+
+// ------------------------------------------------------------ helpers
+template <typename VT> struct Pair { VT a, b; };
+
+__device__ __forceinline__ Pair<float> ld2(const float* p) {
+  const float2 v = *reinterpret_cast<const float2*>(p);
+  return {v.x, v.y};
+}
+__device__ __forceinline__ Pair<double> ld2(const double* p) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void st2(float* p, Pair<float> v) {
+  *reinterpret_cast<float2*>(p) = make_float2(v.a, v.b);
+}
+__device__ __forceinline__ void st2(double* p, Pair<double> v) {
+  *reinterpret_cast<double2*>(p) = make_double2(v.a, v.b);
+}
+
+template <int K>
+__device__ __forceinline__ void ld_cols(const int32_t* p, int (&c)[K]) {
+  static_assert(K % 2 == 0, "slots come in pairs");
+#pragma unroll
+  for (int k = 0; k < K; k += 2) {
+    const int2 v = __ldg(reinterpret_cast<const int2*>(p + k));
+    c[k] = v.x; c[k + 1] = v.y;
+  }
+}
+template <int K>
+__device__ __forceinline__ void ld_vals(const float* p, float (&v)[K]) {
+#pragma unroll
+  for (int k = 0; k < K; k += 2) {
+    const float2 u = __ldg(reinterpret_cast<const float2*>(p + k));
+    v[k] = u.x; v[k + 1] = u.y;
+  }
+}
+template <int K>
+__device__ __forceinline__ void ld_vals(const double* p, double (&v)[K]) {
+#pragma unroll
+  for (int k = 0; k < K; k += 2) {
+    const double2 u = __ldg(reinterpret_cast<const double2*>(p + k));
+    v[k] = u.x; v[k + 1] = u.y;
+  }
+}
 
 // ------------------------------------------------------------ lane state
 template <int T>
 struct LaneState {
   int scen[T], l[T], fb[T], tb[T], lo[T], cnt[T];
   int raP[T], rbP[T], raQ[T], rbQ[T];
-  double wP[T], wQ[T], coef[T], gl[T], bl[T], bshl[T];
+  double wP[T], wQ[T], coef[T], gl[T], bl[T];
   int active[T], outer[T], inP[T], inQ[T], status[T], nogen[T];
   double err[T];
   double rz[T], bb[T], alpha[T], beta[T], rrmin[T];
   int pdone[T], stall[T];
-  double red[NTHREADS];
+  double red[NTHREADS * LP];
   int flag;
   int tile;
 };
 
-// Sum (or max) over the R row groups of each lane's partial value.
+template <int T>
+struct Geo {
+  static constexpr int TPR = T / LP;             // threads per row
+  static constexpr int RPS = NTHREADS / TPR;     // rows per step
+  int rs, lane;                                  // row slot, first lane
+  __device__ Geo() : rs(threadIdx.x / TPR), lane((threadIdx.x % TPR) * LP) {}
+};
+
+// Sum (or max) over the row slots of each lane's partial values.
 template <int T, bool MAX>
-__device__ __forceinline__ double lane_reduce(LaneState<T>& L, double v) {
-  constexpr int R = NTHREADS / T;
-  const int tid = threadIdx.x;
-  L.red[tid] = v;
+__device__ __forceinline__ Pair<double> lane_reduce(LaneState<T>& L, double v0, double v1) {
+  const Geo<T> g;
+  constexpr int RPS = Geo<T>::RPS;
+  L.red[g.rs * T + g.lane] = v0;
+  L.red[g.rs * T + g.lane + 1] = v1;
   __syncthreads();
 #pragma unroll
-  for (int st = R / 2; st > 0; st >>= 1) {
-    if (tid / T < st) {
-      double a = L.red[tid], b = L.red[tid + st * T];
-      L.red[tid] = MAX ? ((b > a || b != b) ? b : a) : a + b;
+  for (int st = RPS / 2; st > 0; st >>= 1) {
+    if (g.rs < st) {
+#pragma unroll
+      for (int j = 0; j < LP; ++j) {
+        const int o = g.rs * T + g.lane + j;
+        const double a = L.red[o], b = L.red[o + st * T];
+        L.red[o] = MAX ? ((b > a || b != b) ? b : a) : a + b;
+      }
     }
     __syncthreads();
   }
-  double out = L.red[tid % T];
+  const Pair<double> out{L.red[g.lane], L.red[g.lane + 1]};
   __syncthreads();
   return out;
 }
 
-// True when some lane has a nonzero entry in `flags` (block-uniform).
-template <int T>
-__device__ __forceinline__ bool any_lane_d(LaneState<T>& L, const double* flags) {
+// True when some lane has a nonzero flag (block-uniform).
+template <int T, typename F>
+__device__ __forceinline__ bool any_lane(LaneState<T>& L, const F* flags) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int any = 0;
-    for (int s = 0; s < T; ++s) any |= (flags[s] != 0.0);
-    L.flag = any;
-  }
-  __syncthreads();
-  const bool r = L.flag != 0;
-  __syncthreads();
-  return r;
-}
-
-// True when some lane has a nonzero entry in `flags` (block-uniform).
-template <int T>
-__device__ __forceinline__ bool any_lane(LaneState<T>& L, const int* flags) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int any = 0;
-    for (int s = 0; s < T; ++s) any |= flags[s];
+    for (int s = 0; s < T; ++s) any |= (flags[s] != 0);
     L.flag = any;
   }
   __syncthreads();
@@ -91,212 +143,323 @@ __device__ __forceinline__ bool any_lane(LaneState<T>& L, const int* flags) {
 }
 
 __device__ __forceinline__ void upd_max(double& m, double d) {
-  double a = fabs(d);
+  const double a = fabs(d);
   if (!(a <= m)) m = (a == a) ? a : INFINITY;
 }
 
 // ----------------------------------------------------- batched operators
-// q = B_s p for the lane's scenario: base CSR times p, plus the outaged
+// q = B_s p for the thread's two lanes: base row times p, plus the outaged
 // branch's four-element change (Sec. IV.B) -- off-diagonal +w, diagonal -w
-// at both ends.  Returns the lane's partial p.q.
+// at both ends.  Returns the lanes' partial p.q.
 template <int T, typename VT>
-__device__ __forceinline__ double spmv_pass(const DevMatT<VT>& M, const VT* p, VT* q, int ra,
-                                            int rb, VT w) {
-  constexpr int R = NTHREADS / T;
-  const int lane = threadIdx.x % T, rg = threadIdx.x / T;
-  double pq = 0.0;
-  for (int i = rg; i < M.n; i += R) {
-    const int oth = (i == ra) ? rb : ((i == rb) ? ra : -2);
-    VT acc = 0, pi = 0;
-    for (int k = M.a_ptr[i]; k < M.a_ptr[i + 1]; ++k) {
-      const int c = M.a_idx[k];
-      const VT pc = p[(size_t)c * T + lane];
-      acc += M.a_val[k] * pc;
-      if (c == oth) acc += w * pc;
-      if (c == i) pi = pc;
+__device__ __forceinline__ Pair<double> spmv_pass(const DevMatT<VT>& M, const VT* __restrict__ p,
+                                                  VT* __restrict__ q, int ra0, int rb0, VT w0,
+                                                  int ra1, int rb1, VT w1) {
+  const Geo<T> g;
+  double pq0 = 0.0, pq1 = 0.0;
+  for (int i = g.rs; i < M.n; i += Geo<T>::RPS) {
+    const int oth0 = (i == ra0) ? rb0 : ((i == rb0) ? ra0 : -2);
+    const int oth1 = (i == ra1) ? rb1 : ((i == rb1) ? ra1 : -2);
+    int c[KA];
+    VT v[KA];
+    ld_cols<KA>(M.A.col + (size_t)i * KA, c);
+    ld_vals<KA>(M.A.val + (size_t)i * KA, v);
+    Pair<VT> pc[KA];
+#pragma unroll
+    for (int k = 0; k < KA; ++k) pc[k] = ld2(p + (size_t)c[k] * T + g.lane);
+    const Pair<VT> pi = ld2(p + (size_t)i * T + g.lane);
+    VT a0 = 0, a1 = 0;
+#pragma unroll
+    for (int k = 0; k < KA; ++k) {
+      a0 += (v[k] + (c[k] == oth0 ? w0 : (VT)0)) * pc[k].a;
+      a1 += (v[k] + (c[k] == oth1 ? w1 : (VT)0)) * pc[k].b;
     }
-    if (oth != -2) acc -= w * pi;
-    q[(size_t)i * T + lane] = acc;
-    pq += (double)(pi * acc);
+    const int o0 = __ldg(M.A.optr + i), o1 = __ldg(M.A.optr + i + 1);
+    for (int o = o0; o < o1; ++o) {
+      const int cc = __ldg(M.A.ocol + o);
+      const VT vv = __ldg(M.A.oval + o);
+      const Pair<VT> pp = ld2(p + (size_t)cc * T + g.lane);
+      a0 += (vv + (cc == oth0 ? w0 : (VT)0)) * pp.a;
+      a1 += (vv + (cc == oth1 ? w1 : (VT)0)) * pp.b;
+    }
+    if (oth0 != -2) a0 -= w0 * pi.a;
+    if (oth1 != -2) a1 -= w1 * pi.b;
+    st2(q + (size_t)i * T + g.lane, Pair<VT>{a0, a1});
+    pq0 += (double)(pi.a * a0);
+    pq1 += (double)(pi.b * a1);
   }
-  return pq;
+  return {pq0, pq1};
 }
 
 // Forward substitution L y = r over the level schedule (rows of one level
 // are independent).  With FUSED, first x += alpha p and r -= alpha q (the
-// PCG update), accumulating r.r; without it, accumulates r.r of the input.
+// PCG update); without it, x = 0.  Accumulates r.r.
 template <int T, typename VT, bool FUSED>
-__device__ __forceinline__ double fwd_pass(const DevMatT<VT>& M, VT* x, VT* r, const VT* p,
-                                           const VT* q, VT* z, VT alpha) {
-  constexpr int R = NTHREADS / T;
-  const int lane = threadIdx.x % T, rg = threadIdx.x / T;
-  double rr = 0.0;
+__device__ __forceinline__ Pair<double> fwd_pass(const DevMatT<VT>& M, VT* __restrict__ x,
+                                                 VT* __restrict__ r, const VT* __restrict__ p,
+                                                 const VT* __restrict__ q, VT* __restrict__ z,
+                                                 VT al0, VT al1) {
+  const Geo<T> g;
+  double rr0 = 0.0, rr1 = 0.0;
   for (int lev = 0; lev < M.nlev; ++lev) {
-    const int r0 = M.lev_ptr[lev], r1 = M.lev_ptr[lev + 1];
-    for (int i = r0 + rg; i < r1; i += R) {
-      const size_t o = (size_t)i * T + lane;
-      VT ri = r[o];
+    const int r0 = __ldg(M.lev_ptr + lev), r1 = __ldg(M.lev_ptr + lev + 1);
+    for (int i = r0 + g.rs; i < r1; i += Geo<T>::RPS) {
+      const size_t o = (size_t)i * T + g.lane;
+      int c[KL];
+      VT v[KL];
+      ld_cols<KL>(M.L.col + (size_t)i * KL, c);
+      ld_vals<KL>(M.L.val + (size_t)i * KL, v);
+      Pair<VT> zc[KL];
+#pragma unroll
+      for (int k = 0; k < KL; ++k) zc[k] = ld2(z + (size_t)c[k] * T + g.lane);
+      Pair<VT> ri = ld2(r + o);
       if (FUSED) {
-        const VT pi = p[o];
-        x[o] += alpha * pi;
-        ri -= alpha * q[o];
-        r[o] = ri;
+        const Pair<VT> pi = ld2(p + o), qi = ld2(q + o), xi = ld2(x + o);
+        st2(x + o, Pair<VT>{xi.a + al0 * pi.a, xi.b + al1 * pi.b});
+        ri.a -= al0 * qi.a;
+        ri.b -= al1 * qi.b;
+        st2(r + o, ri);
       } else {
-        x[o] = 0;
+        st2(x + o, Pair<VT>{(VT)0, (VT)0});
       }
-      rr += (double)(ri * ri);
-      const int ks = M.l_ptr[i], ke = M.l_ptr[i + 1] - 1;
-      VT acc = ri;
-      for (int k = ks; k < ke; ++k) acc -= M.l_val[k] * z[(size_t)M.l_idx[k] * T + lane];
-      z[o] = acc / M.l_val[ke];
+      rr0 += (double)(ri.a * ri.a);
+      rr1 += (double)(ri.b * ri.b);
+      VT a0 = ri.a, a1 = ri.b;
+#pragma unroll
+      for (int k = 0; k < KL; ++k) {
+        a0 -= v[k] * zc[k].a;
+        a1 -= v[k] * zc[k].b;
+      }
+      const int o0 = __ldg(M.L.optr + i), o1 = __ldg(M.L.optr + i + 1);
+      for (int e = o0; e < o1; ++e) {
+        const VT vv = __ldg(M.L.oval + e);
+        const Pair<VT> zz = ld2(z + (size_t)__ldg(M.L.ocol + e) * T + g.lane);
+        a0 -= vv * zz.a;
+        a1 -= vv * zz.b;
+      }
+      const VT id = __ldg(M.inv_diag + i);
+      st2(z + o, Pair<VT>{a0 * id, a1 * id});
     }
     __syncthreads();
   }
-  return rr;
+  return {rr0, rr1};
 }
 
 // Back substitution L^T z = y in place (z holds y on entry), over the
 // backward level schedule; accumulates r.z.
 template <int T, typename VT>
-__device__ __forceinline__ double bwd_pass(const DevMatT<VT>& M, const VT* r, VT* z) {
-  constexpr int R = NTHREADS / T;
-  const int lane = threadIdx.x % T, rg = threadIdx.x / T;
-  double rz = 0.0;
+__device__ __forceinline__ Pair<double> bwd_pass(const DevMatT<VT>& M, const VT* __restrict__ r,
+                                                 VT* __restrict__ z) {
+  const Geo<T> g;
+  double rz0 = 0.0, rz1 = 0.0;
   for (int lev = 0; lev < M.nblev; ++lev) {
-    const int r0 = M.blev_ptr[lev], r1 = M.blev_ptr[lev + 1];
-    for (int k0 = r0 + rg; k0 < r1; k0 += R) {
-      const int i = M.blev_rows[k0];
-      const size_t o = (size_t)i * T + lane;
-      const int ks = M.u_ptr[i], ke = M.u_ptr[i + 1];  // diagonal first
-      VT acc = z[o];
-      for (int k = ks + 1; k < ke; ++k) acc -= M.u_val[k] * z[(size_t)M.u_idx[k] * T + lane];
-      const VT zi = acc / M.u_val[ks];
-      z[o] = zi;
-      rz += (double)(r[o] * zi);
+    const int r0 = __ldg(M.blev_ptr + lev), r1 = __ldg(M.blev_ptr + lev + 1);
+    for (int k0 = r0 + g.rs; k0 < r1; k0 += Geo<T>::RPS) {
+      const int i = __ldg(M.blev_rows + k0);
+      const size_t o = (size_t)i * T + g.lane;
+      int c[KU];
+      VT v[KU];
+      ld_cols<KU>(M.U.col + (size_t)i * KU, c);
+      ld_vals<KU>(M.U.val + (size_t)i * KU, v);
+      Pair<VT> zc[KU];
+#pragma unroll
+      for (int k = 0; k < KU; ++k) zc[k] = ld2(z + (size_t)c[k] * T + g.lane);
+      const Pair<VT> yi = ld2(z + o), ri = ld2(r + o);
+      VT a0 = yi.a, a1 = yi.b;
+#pragma unroll
+      for (int k = 0; k < KU; ++k) {
+        a0 -= v[k] * zc[k].a;
+        a1 -= v[k] * zc[k].b;
+      }
+      const int o0 = __ldg(M.U.optr + i), o1 = __ldg(M.U.optr + i + 1);
+      for (int e = o0; e < o1; ++e) {
+        const VT vv = __ldg(M.U.oval + e);
+        const Pair<VT> zz = ld2(z + (size_t)__ldg(M.U.ocol + e) * T + g.lane);
+        a0 -= vv * zz.a;
+        a1 -= vv * zz.b;
+      }
+      const VT id = __ldg(M.inv_diag + i);
+      a0 *= id;
+      a1 *= id;
+      st2(z + o, Pair<VT>{a0, a1});
+      rz0 += (double)(ri.a * a0);
+      rz1 += (double)(ri.b * a1);
     }
     __syncthreads();
   }
-  return rz;
+  return {rz0, rz1};
 }
 
-// Jacobi: z = r / diag(B_s) (the diagonal with the outage applied).
+// Jacobi: z = r / diag(B_s), the diagonal with the outage applied; a row
+// whose diagonal vanishes (a bus the outage isolates) gets z = 0.
 template <int T, typename VT, bool FUSED>
-__device__ __forceinline__ void jacobi_pass(const DevMatT<VT>& M, VT* x, VT* r, const VT* p,
-                                            const VT* q, VT* z, VT alpha, int ra, int rb, VT w,
-                                            double& rr, double& rz) {
-  constexpr int R = NTHREADS / T;
-  const int lane = threadIdx.x % T, rg = threadIdx.x / T;
-  for (int i = rg; i < M.n; i += R) {
-    const size_t o = (size_t)i * T + lane;
-    VT ri = r[o];
+__device__ __forceinline__ void jacobi_pass(const DevMatT<VT>& M, VT* __restrict__ x,
+                                            VT* __restrict__ r, const VT* __restrict__ p,
+                                            const VT* __restrict__ q, VT* __restrict__ z, VT al0,
+                                            VT al1, int ra0, int rb0, VT w0, int ra1, int rb1,
+                                            VT w1, Pair<double>& rr, Pair<double>& rz) {
+  const Geo<T> g;
+  for (int i = g.rs; i < M.n; i += Geo<T>::RPS) {
+    const size_t o = (size_t)i * T + g.lane;
+    Pair<VT> ri = ld2(r + o);
     if (FUSED) {
-      x[o] += alpha * p[o];
-      ri -= alpha * q[o];
-      r[o] = ri;
+      const Pair<VT> pi = ld2(p + o), qi = ld2(q + o), xi = ld2(x + o);
+      st2(x + o, Pair<VT>{xi.a + al0 * pi.a, xi.b + al1 * pi.b});
+      ri.a -= al0 * qi.a;
+      ri.b -= al1 * qi.b;
+      st2(r + o, ri);
     } else {
-      x[o] = 0;
+      st2(x + o, Pair<VT>{(VT)0, (VT)0});
     }
-    VT d = M.diag[i] - ((i == ra || i == rb) ? w : (VT)0);
-    VT zi = ri / d;
-    z[o] = zi;
-    rr += (double)(ri * ri);
-    rz += (double)(ri * zi);
+    const VT dg = __ldg(M.diag + i);
+    const VT d0 = dg - ((i == ra0 || i == rb0) ? w0 : (VT)0);
+    const VT d1 = dg - ((i == ra1 || i == rb1) ? w1 : (VT)0);
+    const VT z0 = d0 > (VT)0 ? ri.a / d0 : (VT)0;
+    const VT z1 = d1 > (VT)0 ? ri.b / d1 : (VT)0;
+    st2(z + o, Pair<VT>{z0, z1});
+    rr.a += (double)(ri.a * ri.a);
+    rr.b += (double)(ri.b * ri.b);
+    rz.a += (double)(ri.a * z0);
+    rz.b += (double)(ri.b * z1);
   }
   __syncthreads();
 }
 
 // p = mask(z) + beta p: islanded rows keep a zero search direction.
 template <int T, typename VT>
-__device__ __forceinline__ void pupdate_pass(const DevMatT<VT>& M, const VT* z, VT* p, VT beta,
-                                             int lo, int cnt, bool first) {
-  constexpr int R = NTHREADS / T;
-  const int lane = threadIdx.x % T, rg = threadIdx.x / T;
-  for (int i = rg; i < M.n; i += R) {
-    const size_t o = (size_t)i * T + lane;
-    const bool isl = in_island(M.pre_of_row[i], lo, cnt);
-    VT zi = isl ? (VT)0 : z[o];
-    p[o] = first ? zi : zi + beta * p[o];
+__device__ __forceinline__ void pupdate_pass(const DevMatT<VT>& M, const VT* __restrict__ z,
+                                             VT* __restrict__ p, VT be0, VT be1, int lo0,
+                                             int cnt0, int lo1, int cnt1, bool first) {
+  const Geo<T> g;
+  for (int i = g.rs; i < M.n; i += Geo<T>::RPS) {
+    const size_t o = (size_t)i * T + g.lane;
+    const int pr = __ldg(M.pre_of_row + i);
+    const Pair<VT> zi = ld2(z + o);
+    Pair<VT> pn{in_island(pr, lo0, cnt0) ? (VT)0 : zi.a, in_island(pr, lo1, cnt1) ? (VT)0 : zi.b};
+    if (!first) {
+      const Pair<VT> pi = ld2(p + o);
+      pn.a += be0 * pi.a;
+      pn.b += be1 * pi.b;
+    }
+    st2(p + o, pn);
   }
   __syncthreads();
 }
 
 // ------------------------------------------------------------ the solve
 // Batched PCG (Sec. III.A listing, read as textbook PCG) on B_s x = r for
-// the lanes that are active; x starts at 0.  Returns nothing; adds the
-// lane's iteration count to *iters.
+// the lanes that are active; x starts at 0.  Adds each lane's iteration
+// count to iters[lane].
 template <int T, typename VT>
 __device__ void pcg_solve(const FdpfParams& P, const DevMatT<VT>& M, LaneState<T>& L, VT* x,
                           VT* r, VT* p, VT* q, VT* z, const int* ra_, const int* rb_,
                           const double* w_, int* iters) {
-  const int tid = threadIdx.x, lane = tid % T, rg = tid / T;
-  const int ra = ra_[lane], rb = rb_[lane];
-  const VT w = (VT)w_[lane];
-  const int lo = L.lo[lane], cnt = L.cnt[lane];
+  const Geo<T> g;
+  const int l0 = g.lane, l1 = g.lane + 1;
+  const int ra0 = ra_[l0], rb0 = rb_[l0], ra1 = ra_[l1], rb1 = rb_[l1];
+  const VT w0 = (VT)w_[l0], w1 = (VT)w_[l1];
+  const int lo0 = L.lo[l0], cnt0 = L.cnt[l0], lo1 = L.lo[l1], cnt1 = L.cnt[l1];
   const bool jac = (P.precond == PREC_JACOBI);
-  if (rg == 0) L.pdone[lane] = !L.active[lane];
+  // the zero row that padding slots point at
+  if (g.rs == 0) {
+    st2(p + (size_t)M.n * T + g.lane, Pair<VT>{(VT)0, (VT)0});
+    st2(z + (size_t)M.n * T + g.lane, Pair<VT>{(VT)0, (VT)0});
+    L.pdone[l0] = !L.active[l0];
+    L.pdone[l1] = !L.active[l1];
+  }
   __syncthreads();
-  double bbp = 0.0, rzp = 0.0;
+  Pair<double> bbp{0.0, 0.0}, rzp{0.0, 0.0};
   if (jac) {
-    jacobi_pass<T, VT, false>(M, x, r, p, q, z, (VT)0, ra, rb, w, bbp, rzp);
+    jacobi_pass<T, VT, false>(M, x, r, p, q, z, (VT)0, (VT)0, ra0, rb0, w0, ra1, rb1, w1, bbp, rzp);
   } else {
-    bbp = fwd_pass<T, VT, false>(M, x, r, p, q, z, (VT)0);
+    bbp = fwd_pass<T, VT, false>(M, x, r, p, q, z, (VT)0, (VT)0);
     rzp = bwd_pass<T, VT>(M, r, z);
   }
-  const double bb = lane_reduce<T, false>(L, bbp);
-  const double rz0 = lane_reduce<T, false>(L, rzp);
-  pupdate_pass<T, VT>(M, z, p, (VT)0, lo, cnt, true);
-  if (rg == 0) {
-    L.bb[lane] = bb;
-    L.rz[lane] = rz0;
-    L.rrmin[lane] = bb;
-    L.stall[lane] = 0;
-    if (!(bb > 0.0) || !(rz0 > 0.0)) L.pdone[lane] = 1;
+  const Pair<double> bb = lane_reduce<T, false>(L, bbp.a, bbp.b);
+  const Pair<double> rz0 = lane_reduce<T, false>(L, rzp.a, rzp.b);
+  pupdate_pass<T, VT>(M, z, p, (VT)0, (VT)0, lo0, cnt0, lo1, cnt1, true);
+  if (g.rs == 0) {
+#pragma unroll
+    for (int j = 0; j < LP; ++j) {
+      const int ln = g.lane + j;
+      const double b_ = j ? bb.b : bb.a, r_ = j ? rz0.b : rz0.a;
+      L.bb[ln] = b_;
+      L.rz[ln] = r_;
+      L.rrmin[ln] = b_;
+      L.stall[ln] = 0;
+      if (!(b_ > 0.0) || !(r_ > 0.0)) L.pdone[ln] = 1;
+    }
   }
   const double tol2 = P.inner_rtol * P.inner_rtol;
   for (int it = 0; it < P.max_inner; ++it) {
-    if (rg == 0) L.alpha[lane] = L.pdone[lane] ? 0.0 : 1.0;  // alpha doubles as "still running"
-    if (!any_lane_d<T>(L, L.alpha)) break;
-    const double pq = lane_reduce<T, false>(L, spmv_pass<T, VT>(M, p, q, ra, rb, w));
-    if (rg == 0) {
-      double a = 0.0;
-      if (!L.pdone[lane]) {
-        if (pq > 0.0 && isfinite(pq)) a = L.rz[lane] / pq;
-        else L.pdone[lane] = 1;  // breakdown: keep the current iterate
+    __syncthreads();
+    if (g.rs == 0) {
+      L.alpha[l0] = L.pdone[l0] ? 0.0 : 1.0;  // alpha doubles as "still running"
+      L.alpha[l1] = L.pdone[l1] ? 0.0 : 1.0;
+    }
+    if (!any_lane<T>(L, L.alpha)) break;
+    const Pair<double> pqp = spmv_pass<T, VT>(M, p, q, ra0, rb0, w0, ra1, rb1, w1);
+    const Pair<double> pq = lane_reduce<T, false>(L, pqp.a, pqp.b);
+    if (g.rs == 0) {
+#pragma unroll
+      for (int j = 0; j < LP; ++j) {
+        const int ln = g.lane + j;
+        const double v = j ? pq.b : pq.a;
+        double a = 0.0;
+        if (!L.pdone[ln]) {
+          if (v > 0.0 && isfinite(v)) a = L.rz[ln] / v;
+          else L.pdone[ln] = 1;  // breakdown: keep the current iterate
+        }
+        L.alpha[ln] = a;
       }
-      L.alpha[lane] = a;
     }
     __syncthreads();
-    const VT alpha = (VT)L.alpha[lane];
-    double rrp = 0.0, rzn = 0.0;
+    const VT al0 = (VT)L.alpha[l0], al1 = (VT)L.alpha[l1];
+    Pair<double> rrp{0.0, 0.0}, rzn{0.0, 0.0};
     if (jac) {
-      jacobi_pass<T, VT, true>(M, x, r, p, q, z, alpha, ra, rb, w, rrp, rzn);
+      jacobi_pass<T, VT, true>(M, x, r, p, q, z, al0, al1, ra0, rb0, w0, ra1, rb1, w1, rrp, rzn);
     } else {
-      rrp = fwd_pass<T, VT, true>(M, x, r, p, q, z, alpha);
+      rrp = fwd_pass<T, VT, true>(M, x, r, p, q, z, al0, al1);
     }
-    const double rr = lane_reduce<T, false>(L, rrp);
-    if (rg == 0 && !L.pdone[lane]) {
-      iters[lane] += 1;
-      // converged; or stagnated at the rounding floor of VT (no 0.1 % gain
-      // in STALL_ITERS iterations); or growing away from the best residual
-      if (rr < 0.999 * L.rrmin[lane]) { L.rrmin[lane] = rr; L.stall[lane] = 0; }
-      else L.stall[lane] += 1;
-      if (rr <= tol2 * L.bb[lane] || !isfinite(rr) || L.stall[lane] >= STALL_ITERS ||
-          rr > 1e4 * L.rrmin[lane])
-        L.pdone[lane] = 1;
+    const Pair<double> rr = lane_reduce<T, false>(L, rrp.a, rrp.b);
+    if (g.rs == 0) {
+#pragma unroll
+      for (int j = 0; j < LP; ++j) {
+        const int ln = g.lane + j;
+        const double v = j ? rr.b : rr.a;
+        if (L.pdone[ln]) continue;
+        iters[ln] += 1;
+        // converged; or stagnated at the rounding floor of VT (no 0.1 % gain
+        // in STALL_ITERS iterations); or growing away from the best residual
+        if (v < 0.999 * L.rrmin[ln]) { L.rrmin[ln] = v; L.stall[ln] = 0; }
+        else L.stall[ln] += 1;
+        if (v <= tol2 * L.bb[ln] || !isfinite(v) || L.stall[ln] >= STALL_ITERS ||
+            v > 1e4 * L.rrmin[ln])
+          L.pdone[ln] = 1;
+      }
     }
     __syncthreads();
-    if (rg == 0) L.beta[lane] = L.pdone[lane] ? 0.0 : 1.0;
-    if (!any_lane_d<T>(L, L.beta)) break;
+    if (g.rs == 0) {
+      L.beta[l0] = L.pdone[l0] ? 0.0 : 1.0;
+      L.beta[l1] = L.pdone[l1] ? 0.0 : 1.0;
+    }
+    if (!any_lane<T>(L, L.beta)) break;
     if (!jac) rzn = bwd_pass<T, VT>(M, r, z);
-    const double rz = lane_reduce<T, false>(L, rzn);
-    if (rg == 0) {
-      L.beta[lane] = L.pdone[lane] ? 0.0 : rz / L.rz[lane];
-      if (!L.pdone[lane]) L.rz[lane] = rz;
-      if (!(rz > 0.0)) L.pdone[lane] = 1;
+    const Pair<double> rz = lane_reduce<T, false>(L, rzn.a, rzn.b);
+    if (g.rs == 0) {
+#pragma unroll
+      for (int j = 0; j < LP; ++j) {
+        const int ln = g.lane + j;
+        const double v = j ? rz.b : rz.a;
+        L.beta[ln] = L.pdone[ln] ? 0.0 : v / L.rz[ln];
+        if (!L.pdone[ln]) L.rz[ln] = v;
+        if (!(v > 0.0)) L.pdone[ln] = 1;
+      }
     }
     __syncthreads();
-    pupdate_pass<T, VT>(M, z, p, (VT)L.beta[lane], lo, cnt, false);
+    pupdate_pass<T, VT>(M, z, p, (VT)L.beta[l0], (VT)L.beta[l1], lo0, cnt0, lo1, cnt1, false);
   }
+  __syncthreads();
 }
 
 // ------------------------------------------------------------ mismatch
@@ -307,95 +470,151 @@ __device__ void pcg_solve(const FdpfParams& P, const DevMatT<VT>& M, LaneState<T
 // convergence test); otherwise writes dQ/V into the B'' right-hand side.
 template <int T, typename VT, bool WITH_P>
 __device__ void mismatch_pass(const FdpfParams& P, const DevMatT<VT>& MP, const DevMatT<VT>& MQ,
-                              LaneState<T>& L, const double* E, const double* F,
-                              const double* V, VT* rhs, double& errP, double& errQ) {
-  constexpr int R = NTHREADS / T;
-  const int lane = threadIdx.x % T, rg = threadIdx.x / T;
+                              LaneState<T>& L, const double* __restrict__ E,
+                              const double* __restrict__ F, const double* __restrict__ V,
+                              VT* __restrict__ rhs, Pair<double>& errP, Pair<double>& errQ) {
+  const Geo<T> g;
   const DevGrid& G = P.G;
-  const int l = L.l[lane], fb = L.fb[lane], tb = L.tb[lane];
-  const int lo = L.lo[lane], cnt = L.cnt[lane];
-  const bool act = L.active[lane];
-  const double coef = L.coef[lane], gl = L.gl[lane], bl = L.bl[lane] + 0.5 * L.bshl[lane];
+  const int l0 = g.lane, l1 = g.lane + 1;
+  const int br0 = L.l[l0], br1 = L.l[l1];
+  const int fb0 = L.fb[l0], tb0 = L.tb[l0], fb1 = L.fb[l1], tb1 = L.tb[l1];
+  const int lo0 = L.lo[l0], cnt0 = L.cnt[l0], lo1 = L.lo[l1], cnt1 = L.cnt[l1];
+  const bool act0 = L.active[l0], act1 = L.active[l1];
+  const double cf0 = L.coef[l0], cf1 = L.coef[l1];
+  const double gl0 = L.gl[l0], bl0 = L.bl[l0], gl1 = L.gl[l1], bl1 = L.bl[l1];
   const int nrows = WITH_P ? G.n : MQ.n;
-  for (int k = rg; k < nrows; k += R) {
-    const int i = WITH_P ? k : MQ.bus_of_row[k];
+  for (int k = g.rs; k < nrows; k += Geo<T>::RPS) {
+    const int i = WITH_P ? k : __ldg(MQ.bus_of_row + k);
     const int bt = G.bus_type[i];
     if (WITH_P && bt == 2) continue;
-    const bool isl = in_island(G.pre[i], lo, cnt);
-    VT out = 0;
-    if (act && !isl) {
-      const size_t o = (size_t)i * T + lane;
-      const double ei = E[o], fi = F[o];
-      double Gd = G.Gii[i], Bd = G.Bii[i];
-      if (i == fb || i == tb) { Gd -= gl; Bd -= bl; }
-      double re = Gd * ei - Bd * fi, im = Gd * fi + Bd * ei;
-      for (int a = G.adj_ptr[i]; a < G.adj_ptr[i + 1]; ++a) {
-        const int e = G.adj_br[a];
-        if (e == l) continue;
-        const int j = G.adj_idx[a];
-        const double ej = E[(size_t)j * T + lane], fj = F[(size_t)j * T + lane];
-        const double g = G.g[e], b = G.by[e];
-        re -= g * ej - b * fj;
-        im -= g * fj + b * ej;
+    const int pr = __ldg(G.pre + i);
+    const bool on0 = act0 && !in_island(pr, lo0, cnt0);
+    const bool on1 = act1 && !in_island(pr, lo1, cnt1);
+    Pair<VT> out{(VT)0, (VT)0};
+    if (on0 || on1) {
+      const size_t o = (size_t)i * T + g.lane;
+      int nb[KG], br[KG];
+      ld_cols<KG>(G.adj_nbr + (size_t)i * KG, nb);
+      ld_cols<KG>(G.adj_brl + (size_t)i * KG, br);
+      double gg[KG], bb[KG];
+      ld_vals<KG>(G.adj_g + (size_t)i * KG, gg);
+      ld_vals<KG>(G.adj_b + (size_t)i * KG, bb);
+      Pair<double> ej[KG], fj[KG];
+#pragma unroll
+      for (int a = 0; a < KG; ++a) {
+        ej[a] = ld2(E + (size_t)nb[a] * T + g.lane);
+        fj[a] = ld2(F + (size_t)nb[a] * T + g.lane);
       }
-      const double Vi = V[o];
-      const double dQ = G.Q_sched[i] - (fi * re - ei * im);
+      const Pair<double> ei = ld2(E + o), fi = ld2(F + o), Vi = ld2(V + o);
+      double Gd0 = __ldg(G.Gii + i), Bd0 = __ldg(G.Bii + i);
+      double Gd1 = Gd0, Bd1 = Bd0;
+      if (i == fb0 || i == tb0) { Gd0 -= gl0; Bd0 -= bl0; }
+      if (i == fb1 || i == tb1) { Gd1 -= gl1; Bd1 -= bl1; }
+      double re0 = Gd0 * ei.a - Bd0 * fi.a, im0 = Gd0 * fi.a + Bd0 * ei.a;
+      double re1 = Gd1 * ei.b - Bd1 * fi.b, im1 = Gd1 * fi.b + Bd1 * ei.b;
+#pragma unroll
+      for (int a = 0; a < KG; ++a) {
+        const double g0 = br[a] == br0 ? 0.0 : gg[a], b0 = br[a] == br0 ? 0.0 : bb[a];
+        const double g1 = br[a] == br1 ? 0.0 : gg[a], b1 = br[a] == br1 ? 0.0 : bb[a];
+        re0 -= g0 * ej[a].a - b0 * fj[a].a;
+        im0 -= g0 * fj[a].a + b0 * ej[a].a;
+        re1 -= g1 * ej[a].b - b1 * fj[a].b;
+        im1 -= g1 * fj[a].b + b1 * ej[a].b;
+      }
+      const int o0 = __ldg(G.adj_optr + i), o1 = __ldg(G.adj_optr + i + 1);
+      for (int e = o0; e < o1; ++e) {
+        const int j = __ldg(G.adj_onbr + e), b_ = __ldg(G.adj_obr + e);
+        const double gv = __ldg(G.adj_og + e), bv = __ldg(G.adj_ob + e);
+        const Pair<double> ee = ld2(E + (size_t)j * T + g.lane), ff = ld2(F + (size_t)j * T + g.lane);
+        if (b_ != br0) { re0 -= gv * ee.a - bv * ff.a; im0 -= gv * ff.a + bv * ee.a; }
+        if (b_ != br1) { re1 -= gv * ee.b - bv * ff.b; im1 -= gv * ff.b + bv * ee.b; }
+      }
+      const double qs = __ldg(G.Q_sched + i);
+      const double dQ0 = qs - (fi.a * re0 - ei.a * im0);
+      const double dQ1 = qs - (fi.b * re1 - ei.b * im1);
       if (WITH_P) {
-        double Ps = G.P_sched[i];
-        if (bt == 1) Ps += coef * G.P_gen[i];
-        const double dP = Ps - (ei * re + fi * im);
-        upd_max(errP, dP);
-        if (bt == 0) upd_max(errQ, dQ);
-        out = (VT)(dP / Vi);
+        double Ps0 = __ldg(G.P_sched + i), Ps1 = Ps0;
+        if (bt == 1) {
+          const double pg = __ldg(G.P_gen + i);
+          Ps0 += cf0 * pg;
+          Ps1 += cf1 * pg;
+        }
+        const double dP0 = Ps0 - (ei.a * re0 + fi.a * im0);
+        const double dP1 = Ps1 - (ei.b * re1 + fi.b * im1);
+        if (on0) { upd_max(errP.a, dP0); if (bt == 0) upd_max(errQ.a, dQ0); out.a = (VT)dP0 / (VT)Vi.a; }
+        if (on1) { upd_max(errP.b, dP1); if (bt == 0) upd_max(errQ.b, dQ1); out.b = (VT)dP1 / (VT)Vi.b; }
       } else {
-        out = (VT)(dQ / Vi);
+        if (on0) out.a = (VT)dQ0 / (VT)Vi.a;
+        if (on1) out.b = (VT)dQ1 / (VT)Vi.b;
       }
     }
-    if (WITH_P) rhs[(size_t)MP.row_of_bus[i] * T + lane] = out;
-    else rhs[(size_t)k * T + lane] = out;
+    if (WITH_P) st2(rhs + (size_t)__ldg(MP.row_of_bus + i) * T + g.lane, out);
+    else st2(rhs + (size_t)k * T + g.lane, out);
+  }
+}
+
+// (cos, sin) of theta + d from those of theta: for |d| <= 0.05 the
+// rotation by d uses the Taylor series of sin d and cos d (truncation below
+// 1e-21), else the angle is recomputed.
+__device__ __forceinline__ void rotate(double th_new, double d, double& c, double& s) {
+  if (fabs(d) <= 0.05) {
+    const double d2 = d * d;
+    const double sd = d * (1.0 - d2 / 6.0 * (1.0 - d2 / 20.0 * (1.0 - d2 / 42.0 * (1.0 - d2 / 72.0))));
+    const double cd = 1.0 - d2 / 2.0 * (1.0 - d2 / 12.0 * (1.0 - d2 / 30.0 * (1.0 - d2 / 56.0 * (1.0 - d2 / 90.0))));
+    const double cn = c * cd - s * sd, sn = s * cd + c * sd;
+    c = cn;
+    s = sn;
+  } else {
+    sincos(th_new, &s, &c);
   }
 }
 
 // theta += dtheta (P half-step) or |V| += dV (Q half-step) on the matrix's
 // rows, then refresh the rectangular voltages.
 template <int T, typename VT, bool IS_P>
-__device__ void update_pass(const DevMatT<VT>& M, LaneState<T>& L, const VT* x, double* th,
-                            double* V, double* C, double* Sn, double* E, double* F) {
-  constexpr int R = NTHREADS / T;
-  const int lane = threadIdx.x % T, rg = threadIdx.x / T;
-  const int lo = L.lo[lane], cnt = L.cnt[lane];
-  if (!L.active[lane]) return;
-  for (int k = rg; k < M.n; k += R) {
-    if (in_island(M.pre_of_row[k], lo, cnt)) continue;
-    const int i = M.bus_of_row[k];
-    const size_t o = (size_t)i * T + lane;
-    const double dx = (double)x[(size_t)k * T + lane];
+__device__ void update_pass(const DevMatT<VT>& M, LaneState<T>& L, const VT* __restrict__ x,
+                            double* th, double* V, double* C, double* Sn, double* E, double* F) {
+  const Geo<T> g;
+  const int l0 = g.lane, l1 = g.lane + 1;
+  const int lo0 = L.lo[l0], cnt0 = L.cnt[l0], lo1 = L.lo[l1], cnt1 = L.cnt[l1];
+  const bool act0 = L.active[l0], act1 = L.active[l1];
+  if (!act0 && !act1) return;
+  for (int k = g.rs; k < M.n; k += Geo<T>::RPS) {
+    const int pr = __ldg(M.pre_of_row + k);
+    const bool on0 = act0 && !in_island(pr, lo0, cnt0);
+    const bool on1 = act1 && !in_island(pr, lo1, cnt1);
+    if (!on0 && !on1) continue;
+    const int i = __ldg(M.bus_of_row + k);
+    const size_t o = (size_t)i * T + g.lane;
+    const Pair<VT> dx = ld2(x + (size_t)k * T + g.lane);
+    const double d0 = on0 ? (double)dx.a : 0.0, d1 = on1 ? (double)dx.b : 0.0;
+    Pair<double> c = ld2(C + o), s = ld2(Sn + o), v = ld2(V + o);
     if (IS_P) {
-      const double t = th[o] + dx;
-      double sn, cs;
-      sincos(t, &sn, &cs);
-      const double v = V[o];
-      th[o] = t;
-      C[o] = cs;
-      Sn[o] = sn;
-      E[o] = v * cs;
-      F[o] = v * sn;
+      Pair<double> t = ld2(th + o);
+      t.a += d0;
+      t.b += d1;
+      if (on0) rotate(t.a, d0, c.a, s.a);
+      if (on1) rotate(t.b, d1, c.b, s.b);
+      st2(th + o, t);
+      st2(C + o, c);
+      st2(Sn + o, s);
     } else {
-      const double v = V[o] + dx;
-      V[o] = v;
-      E[o] = v * C[o];
-      F[o] = v * Sn[o];
+      v.a += d0;
+      v.b += d1;
+      st2(V + o, v);
     }
+    st2(E + o, Pair<double>{v.a * c.a, v.b * c.b});
+    st2(F + o, Pair<double>{v.a * s.a, v.b * s.b});
   }
 }
 
 // ------------------------------------------------------------ the kernel
 template <int T, typename VT>
-__global__ void __launch_bounds__(NTHREADS) fdpf_tiles_kernel(FdpfParams P, DevMatT<VT> MP,
+__global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS) fdpf_tiles_kernel(FdpfParams P, DevMatT<VT> MP,
                                                               DevMatT<VT> MQ) {
-  constexpr int R = NTHREADS / T;
   __shared__ LaneState<T> L;
-  const int tid = threadIdx.x, lane = tid % T, rg = tid / T;
+  const Geo<T> g;
+  const int tid = threadIdx.x;
   const DevGrid& G = P.G;
   VT* x = (VT*)P.wx + (size_t)blockIdx.x * P.vstride;
   VT* r = (VT*)P.wr + (size_t)blockIdx.x * P.vstride;
@@ -411,163 +630,220 @@ __global__ void __launch_bounds__(NTHREADS) fdpf_tiles_kernel(FdpfParams P, DevM
     __syncthreads();
     const int tile = L.tile;
     if (tile >= P.n_tiles) break;
-    if (rg == 0) {
-      const int s = tile * T + lane;
+    if (tid < T) {
+      const int ln = tid;
+      const int s = tile * T + ln;
       const bool valid = s < P.S;
       const int l = valid ? P.sc.outage[s] : -1;
-      L.scen[lane] = valid ? s : -1;
-      L.l[lane] = l;
-      L.fb[lane] = l >= 0 ? G.f[l] : -1;
-      L.tb[lane] = l >= 0 ? G.t[l] : -1;
-      L.lo[lane] = valid ? P.sc.isl_lo[s] : 0;
-      L.cnt[lane] = valid ? P.sc.isl_cnt[s] : 0;
-      L.coef[lane] = valid ? P.sc.coef[s] : 0.0;
-      L.nogen[lane] = valid ? P.sc.no_gen[s] : 0;
-      L.raP[lane] = l >= 0 ? MP.row_of_bus[G.f[l]] : -1;
-      L.rbP[lane] = l >= 0 ? MP.row_of_bus[G.t[l]] : -1;
-      L.raQ[lane] = l >= 0 ? MQ.row_of_bus[G.f[l]] : -1;
-      L.rbQ[lane] = l >= 0 ? MQ.row_of_bus[G.t[l]] : -1;
-      L.wP[lane] = l >= 0 ? MP.w[l] : 0.0;
-      L.wQ[lane] = l >= 0 ? MQ.w[l] : 0.0;
-      L.gl[lane] = l >= 0 ? G.g[l] : 0.0;
-      L.bl[lane] = l >= 0 ? G.by[l] : 0.0;
-      L.bshl[lane] = l >= 0 ? G.b_sh[l] : 0.0;
-      L.active[lane] = valid;
-      L.outer[lane] = 0;
-      L.inP[lane] = 0;
-      L.inQ[lane] = 0;
-      L.status[lane] = 0;
-      L.err[lane] = 0.0;
+      L.scen[ln] = valid ? s : -1;
+      L.l[ln] = l;
+      L.fb[ln] = l >= 0 ? G.f[l] : -1;
+      L.tb[ln] = l >= 0 ? G.t[l] : -1;
+      L.lo[ln] = valid ? P.sc.isl_lo[s] : 0;
+      L.cnt[ln] = valid ? P.sc.isl_cnt[s] : 0;
+      L.coef[ln] = valid ? P.sc.coef[s] : 0.0;
+      L.nogen[ln] = valid ? P.sc.no_gen[s] : 0;
+      L.raP[ln] = l >= 0 ? MP.row_of_bus[G.f[l]] : -1;
+      L.rbP[ln] = l >= 0 ? MP.row_of_bus[G.t[l]] : -1;
+      L.raQ[ln] = l >= 0 ? MQ.row_of_bus[G.f[l]] : -1;
+      L.rbQ[ln] = l >= 0 ? MQ.row_of_bus[G.t[l]] : -1;
+      L.wP[ln] = l >= 0 ? MP.w[l] : 0.0;
+      L.wQ[ln] = l >= 0 ? MQ.w[l] : 0.0;
+      L.gl[ln] = l >= 0 ? G.g[l] : 0.0;
+      L.bl[ln] = l >= 0 ? G.by[l] + 0.5 * G.b_sh[l] : 0.0;
+      L.active[ln] = valid;
+      L.outer[ln] = 0;
+      L.inP[ln] = 0;
+      L.inQ[ln] = 0;
+      L.status[ln] = 0;
+      L.err[ln] = 0.0;
     }
     __syncthreads();
     // warm start from the base case (Sec. III.B); islanded buses at zero
     {
-      const int lo = L.lo[lane], cnt = L.cnt[lane];
-      for (int i = rg; i < G.n; i += R) {
-        const size_t o = (size_t)i * T + lane;
-        double t0, v0;
-        if (P.flat_start) { t0 = 0.0; v0 = G.V_set[i]; }
-        else { t0 = P.th0[i]; v0 = P.V0[i]; }
-        if (in_island(G.pre[i], lo, cnt)) { t0 = 0.0; v0 = 0.0; }
-        double sn, cs;
-        sincos(t0, &sn, &cs);
-        th[o] = t0; V[o] = v0; C[o] = cs; Sn[o] = sn; E[o] = v0 * cs; F[o] = v0 * sn;
+      const int l0 = g.lane, l1 = g.lane + 1;
+      const int lo0 = L.lo[l0], cnt0 = L.cnt[l0], lo1 = L.lo[l1], cnt1 = L.cnt[l1];
+      for (int i = g.rs; i < G.n; i += Geo<T>::RPS) {
+        const size_t o = (size_t)i * T + g.lane;
+        double t0, v0, c0, s0;
+        if (P.flat_start) { t0 = 0.0; v0 = G.V_set[i]; c0 = 1.0; s0 = 0.0; }
+        else { t0 = P.th0[i]; v0 = P.V0[i]; c0 = P.c0[i]; s0 = P.s0[i]; }
+        const int pr = G.pre[i];
+        const bool i0 = in_island(pr, lo0, cnt0), i1 = in_island(pr, lo1, cnt1);
+        st2(th + o, Pair<double>{i0 ? 0.0 : t0, i1 ? 0.0 : t0});
+        st2(V + o, Pair<double>{i0 ? 0.0 : v0, i1 ? 0.0 : v0});
+        st2(C + o, Pair<double>{c0, c0});
+        st2(Sn + o, Pair<double>{s0, s0});
+        st2(E + o, Pair<double>{i0 ? 0.0 : v0 * c0, i1 ? 0.0 : v0 * c0});
+        st2(F + o, Pair<double>{i0 ? 0.0 : v0 * s0, i1 ? 0.0 : v0 * s0});
       }
     }
     __syncthreads();
     for (;;) {
       // P half-step: mismatch + convergence test
-      double eP = 0.0, eQ = 0.0;
+      Pair<double> eP{0.0, 0.0}, eQ{0.0, 0.0};
       mismatch_pass<T, VT, true>(P, MP, MQ, L, E, F, V, r, eP, eQ);
-      eP = lane_reduce<T, true>(L, eP);
-      eQ = lane_reduce<T, true>(L, eQ);
-      if (rg == 0 && L.active[lane]) {
-        const double e2 = (eP != eP || eQ != eQ) ? INFINITY : fmax(eP, eQ);
-        L.err[lane] = e2;
-        if (!(e2 <= DIVERGE_LIMIT)) { L.status[lane] = 2; L.active[lane] = 0; }
-        else if (e2 <= P.tol) { L.status[lane] = 0; L.active[lane] = 0; }
-        else if (L.outer[lane] >= P.max_outer) { L.status[lane] = 1; L.active[lane] = 0; }
+      const Pair<double> mP = lane_reduce<T, true>(L, eP.a, eP.b);
+      const Pair<double> mQ = lane_reduce<T, true>(L, eQ.a, eQ.b);
+      if (g.rs == 0) {
+#pragma unroll
+        for (int j = 0; j < LP; ++j) {
+          const int ln = g.lane + j;
+          if (!L.active[ln]) continue;
+          const double a = j ? mP.b : mP.a, b = j ? mQ.b : mQ.a;
+          const double e2 = (a != a || b != b) ? INFINITY : fmax(a, b);
+          L.err[ln] = e2;
+          if (!(e2 <= DIVERGE_LIMIT)) { L.status[ln] = 2; L.active[ln] = 0; }
+          else if (e2 <= P.tol) { L.status[ln] = 0; L.active[ln] = 0; }
+          else if (L.outer[ln] >= P.max_outer) { L.status[ln] = 1; L.active[ln] = 0; }
+        }
       }
       if (!any_lane<T>(L, L.active)) break;
       pcg_solve<T, VT>(P, MP, L, x, r, p, q, z, L.raP, L.rbP, L.wP, L.inP);
       update_pass<T, VT, true>(MP, L, x, th, V, C, Sn, E, F);
       __syncthreads();
       // Q half-step
-      double d0 = 0.0, d1 = 0.0;
+      Pair<double> d0{0.0, 0.0}, d1{0.0, 0.0};
       mismatch_pass<T, VT, false>(P, MP, MQ, L, E, F, V, r, d0, d1);
       __syncthreads();
       pcg_solve<T, VT>(P, MQ, L, x, r, p, q, z, L.raQ, L.rbQ, L.wQ, L.inQ);
       update_pass<T, VT, false>(MQ, L, x, th, V, C, Sn, E, F);
-      if (rg == 0 && L.active[lane]) L.outer[lane] += 1;
+      if (g.rs == 0) {
+        if (L.active[g.lane]) L.outer[g.lane] += 1;
+        if (L.active[g.lane + 1]) L.outer[g.lane + 1] += 1;
+      }
       __syncthreads();
     }
     // outputs: state, branch flows, loading (Sec. I: overload screening)
-    const int s = L.scen[lane];
-    if (s >= 0) {
-      if (P.out_theta || P.out_vm) {
-        for (int i = rg; i < G.n; i += R) {
-          const size_t o = (size_t)i * T + lane;
-          if (P.out_theta) P.out_theta[(size_t)s * G.n + i] = th[o];
-          if (P.out_vm) P.out_vm[(size_t)s * G.n + i] = V[o];
+    const int s0 = L.scen[g.lane], s1 = L.scen[g.lane + 1];
+    if (P.out_theta || P.out_vm) {
+      for (int i = g.rs; i < G.n; i += Geo<T>::RPS) {
+        const size_t o = (size_t)i * T + g.lane;
+        const Pair<double> t = ld2(th + o), v = ld2(V + o);
+        if (P.out_theta) {
+          if (s0 >= 0) P.out_theta[(size_t)s0 * G.n + i] = t.a;
+          if (s1 >= 0) P.out_theta[(size_t)s1 * G.n + i] = t.b;
+        }
+        if (P.out_vm) {
+          if (s0 >= 0) P.out_vm[(size_t)s0 * G.n + i] = v.a;
+          if (s1 >= 0) P.out_vm[(size_t)s1 * G.n + i] = v.b;
         }
       }
     }
-    double mload = 0.0;
+    double ml0 = 0.0, ml1 = 0.0;
     {
-      const int l = L.l[lane], lo = L.lo[lane], cnt = L.cnt[lane];
-      for (int k = rg; k < G.m; k += R) {
-        const int a = G.f[k], b = G.t[k];
-        double Pab = 0.0, Pba = 0.0;
-        const bool off = (k == l) || in_island(G.pre[a], lo, cnt) || in_island(G.pre[b], lo, cnt);
-        if (!off) {
-          const double ea = E[(size_t)a * T + lane], fa = F[(size_t)a * T + lane];
-          const double eb = E[(size_t)b * T + lane], fbv = F[(size_t)b * T + lane];
-          const double g = G.g[k], by = G.by[k];
-          const double cr = ea * eb + fa * fbv, sr = fa * eb - ea * fbv;
-          Pab = g * (ea * ea + fa * fa) - g * cr - by * sr;
-          Pba = g * (eb * eb + fbv * fbv) - g * cr + by * sr;
+      const int l0 = g.lane, l1 = g.lane + 1;
+      const int br0 = L.l[l0], br1 = L.l[l1];
+      const int lo0 = L.lo[l0], cnt0 = L.cnt[l0], lo1 = L.lo[l1], cnt1 = L.cnt[l1];
+      for (int k = g.rs; k < G.m; k += Geo<T>::RPS) {
+        const int a = __ldg(G.f + k), b = __ldg(G.t + k);
+        const int pa = __ldg(G.pre + a), pb = __ldg(G.pre + b);
+        const bool off0 = (k == br0) || in_island(pa, lo0, cnt0) || in_island(pb, lo0, cnt0);
+        const bool off1 = (k == br1) || in_island(pa, lo1, cnt1) || in_island(pb, lo1, cnt1);
+        const Pair<double> ea = ld2(E + (size_t)a * T + g.lane), fa = ld2(F + (size_t)a * T + g.lane);
+        const Pair<double> eb = ld2(E + (size_t)b * T + g.lane), fb = ld2(F + (size_t)b * T + g.lane);
+        const double gk = __ldg(G.g + k), bk = __ldg(G.by + k), rk = __ldg(G.rating + k);
+        double Pab0 = 0.0, Pba0 = 0.0, Pab1 = 0.0, Pba1 = 0.0;
+        if (!off0) {
+          const double cr = ea.a * eb.a + fa.a * fb.a, sr = fa.a * eb.a - ea.a * fb.a;
+          Pab0 = gk * (ea.a * ea.a + fa.a * fa.a) - gk * cr - bk * sr;
+          Pba0 = gk * (eb.a * eb.a + fb.a * fb.a) - gk * cr + bk * sr;
         }
-        upd_max(mload, fmax(fabs(Pab), fabs(Pba)) / G.rating[k]);
-        if (s >= 0 && P.out_flow) P.out_flow[(size_t)s * G.m + k] = Pab;
+        if (!off1) {
+          const double cr = ea.b * eb.b + fa.b * fb.b, sr = fa.b * eb.b - ea.b * fb.b;
+          Pab1 = gk * (ea.b * ea.b + fa.b * fa.b) - gk * cr - bk * sr;
+          Pba1 = gk * (eb.b * eb.b + fb.b * fb.b) - gk * cr + bk * sr;
+        }
+        upd_max(ml0, fmax(fabs(Pab0), fabs(Pba0)) / rk);
+        upd_max(ml1, fmax(fabs(Pab1), fabs(Pba1)) / rk);
+        if (P.out_flow) {
+          if (s0 >= 0) P.out_flow[(size_t)s0 * G.m + k] = Pab0;
+          if (s1 >= 0) P.out_flow[(size_t)s1 * G.m + k] = Pab1;
+        }
       }
     }
-    mload = lane_reduce<T, true>(L, mload);
-    if (rg == 0 && s >= 0) {
-      int st = L.status[lane];
-      if (st == 0 && L.nogen[lane]) st = 3;
-      if (P.out_status) P.out_status[s] = st;
-      if (P.out_iters) {
-        P.out_iters[(size_t)s * 3 + 0] = L.outer[lane];
-        P.out_iters[(size_t)s * 3 + 1] = L.inP[lane];
-        P.out_iters[(size_t)s * 3 + 2] = L.inQ[lane];
+    const Pair<double> ml = lane_reduce<T, true>(L, ml0, ml1);
+    if (g.rs == 0) {
+#pragma unroll
+      for (int j = 0; j < LP; ++j) {
+        const int ln = g.lane + j, s = L.scen[ln];
+        if (s < 0) continue;
+        int st = L.status[ln];
+        if (st == 0 && L.nogen[ln]) st = 3;
+        if (P.out_status) P.out_status[s] = st;
+        if (P.out_iters) {
+          P.out_iters[(size_t)s * 3 + 0] = L.outer[ln];
+          P.out_iters[(size_t)s * 3 + 1] = L.inP[ln];
+          P.out_iters[(size_t)s * 3 + 2] = L.inQ[ln];
+        }
+        if (P.out_maxload) P.out_maxload[s] = j ? ml.b : ml.a;
       }
-      if (P.out_maxload) P.out_maxload[s] = mload;
     }
     __syncthreads();
   }
 }
 
 // Batched operator application for verification (gpcg_apply): X and Y are
-// [S][rows]; each CTA handles tiles of T scenarios.
+// [S][rows]; each CTA handles tiles of T = 32 scenarios.
 template <int T, typename VT>
 __global__ void __launch_bounds__(NTHREADS) apply_kernel(DevMatT<VT> M, int op, int S,
                                                          const int32_t* outages,
                                                          const int32_t* f_, const int32_t* t_,
                                                          const double* X, double* Y, VT* wbuf,
                                                          size_t vstride, int precond) {
-  constexpr int R = NTHREADS / T;
-  __shared__ LaneState<T> L;
-  const int tid = threadIdx.x, lane = tid % T, rg = tid / T;
-  VT* a = wbuf + (size_t)blockIdx.x * 4 * vstride;
+  const Geo<T> g;
+  VT* a = wbuf + (size_t)blockIdx.x * 3 * vstride;
   VT* b = a + vstride;
   VT* c = b + vstride;
-  VT* d = c + vstride;
   const int ntiles = (S + T - 1) / T;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int s = tile * T + lane;
-    const bool valid = s < S;
-    const int l = valid ? outages[s] : -1;
-    const int ra = l >= 0 ? M.row_of_bus[f_[l]] : -1;
-    const int rb = l >= 0 ? M.row_of_bus[t_[l]] : -1;
-    const VT w = l >= 0 ? (VT)M.w[l] : (VT)0;
-    for (int i = rg; i < M.n; i += R) a[(size_t)i * T + lane] = valid ? (VT)X[(size_t)s * M.n + i] : (VT)0;
+    int ra[LP], rb[LP];
+    VT w[LP];
+    bool valid[LP];
+    int s[LP];
+#pragma unroll
+    for (int j = 0; j < LP; ++j) {
+      s[j] = tile * T + g.lane + j;
+      valid[j] = s[j] < S;
+      const int l = valid[j] ? outages[s[j]] : -1;
+      ra[j] = l >= 0 ? M.row_of_bus[f_[l]] : -1;
+      rb[j] = l >= 0 ? M.row_of_bus[t_[l]] : -1;
+      w[j] = l >= 0 ? (VT)M.w[l] : (VT)0;
+    }
+    for (int i = g.rs; i <= M.n; i += Geo<T>::RPS) {
+      Pair<VT> v{(VT)0, (VT)0};
+      if (i < M.n) {
+        if (valid[0]) v.a = (VT)X[(size_t)s[0] * M.n + i];
+        if (valid[1]) v.b = (VT)X[(size_t)s[1] * M.n + i];
+      }
+      st2(a + (size_t)i * T + g.lane, v);
+      st2(b + (size_t)i * T + g.lane, Pair<VT>{(VT)0, (VT)0});
+    }
     __syncthreads();
     if (op == 0) {
-      spmv_pass<T, VT>(M, a, b, ra, rb, w);
+      spmv_pass<T, VT>(M, a, b, ra[0], rb[0], w[0], ra[1], rb[1], w[1]);
     } else if (precond == PREC_JACOBI) {
-      double rr = 0.0, rz = 0.0;
-      jacobi_pass<T, VT, false>(M, c, a, nullptr, nullptr, b, (VT)0, ra, rb, w, rr, rz);
+      Pair<double> rr{0.0, 0.0}, rz{0.0, 0.0};
+      jacobi_pass<T, VT, false>(M, c, a, nullptr, nullptr, b, (VT)0, (VT)0, ra[0], rb[0], w[0],
+                                ra[1], rb[1], w[1], rr, rz);
     } else {
-      fwd_pass<T, VT, false>(M, c, a, nullptr, nullptr, b, (VT)0);
+      fwd_pass<T, VT, false>(M, c, a, nullptr, nullptr, b, (VT)0, (VT)0);
       bwd_pass<T, VT>(M, a, b);
     }
     __syncthreads();
-    for (int i = rg; i < M.n; i += R)
-      if (valid) Y[(size_t)s * M.n + i] = (double)b[(size_t)i * T + lane];
+    for (int i = g.rs; i < M.n; i += Geo<T>::RPS) {
+      const Pair<VT> v = ld2(b + (size_t)i * T + g.lane);
+      if (valid[0]) Y[(size_t)s[0] * M.n + i] = (double)v.a;
+      if (valid[1]) Y[(size_t)s[1] * M.n + i] = (double)v.b;
+    }
     __syncthreads();
   }
-  (void)d;
-  (void)L;
+}
+
+// Base-case cos/sin per bus, shared by every scenario's warm start.
+__global__ void base_trig_kernel(int n, const double* th, double* c, double* s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) sincos(th[i], &s[i], &c[i]);
 }
 
 // ----------------------------------------------------------- launchers
@@ -582,7 +858,7 @@ template <typename VT>
 cudaError_t launch_fdpf(cudaStream_t st, int T, int grid, const FdpfParams& P,
                         const DevMatT<VT>& MP, const DevMatT<VT>& MQ) {
   switch (T) {
-    case 1: return launch_fdpf_t<1, VT>(st, grid, P, MP, MQ);
+    case 2: return launch_fdpf_t<2, VT>(st, grid, P, MP, MQ);
     case 8: return launch_fdpf_t<8, VT>(st, grid, P, MP, MQ);
     case 16: return launch_fdpf_t<16, VT>(st, grid, P, MP, MQ);
     case 32: return launch_fdpf_t<32, VT>(st, grid, P, MP, MQ);
@@ -595,7 +871,7 @@ int fdpf_max_blocks_per_sm(int T) {
   int nb = 0;
   cudaError_t ce = cudaErrorInvalidValue;
   switch (T) {
-    case 1: ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fdpf_tiles_kernel<1, VT>, NTHREADS, 0); break;
+    case 2: ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fdpf_tiles_kernel<2, VT>, NTHREADS, 0); break;
     case 8: ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fdpf_tiles_kernel<8, VT>, NTHREADS, 0); break;
     case 16: ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fdpf_tiles_kernel<16, VT>, NTHREADS, 0); break;
     case 32: ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fdpf_tiles_kernel<32, VT>, NTHREADS, 0); break;
@@ -609,6 +885,11 @@ cudaError_t launch_apply(cudaStream_t st, int grid, const DevMatT<VT>& M, int op
                          const double* X, double* Y, VT* wbuf, size_t vstride, int precond) {
   apply_kernel<32, VT><<<grid, NTHREADS, 0, st>>>(M, op, S, outages, f, t, X, Y, wbuf, vstride,
                                                   precond);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_base_trig(cudaStream_t st, int n, const double* th, double* c, double* s) {
+  base_trig_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, th, c, s);
   return cudaGetLastError();
 }
 

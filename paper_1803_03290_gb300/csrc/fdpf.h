@@ -13,6 +13,7 @@ struct FdpfParams {
   int S = 0, n_tiles = 0;
   ScenInfo sc;
   const double *th0 = nullptr, *V0 = nullptr;  // warm start (bus order)
+  const double *c0 = nullptr, *s0 = nullptr;   // cos, sin of th0
   int flat_start = 0;
   double tol = 1e-4, inner_rtol = 1e-5;
   int max_outer = 50, max_inner = 500, precond = PREC_EXACT;
@@ -34,5 +35,6 @@ template <typename VT>
 cudaError_t launch_apply(cudaStream_t st, int grid, const DevMatT<VT>& M, int op, int S,
                          const int32_t* outages, const int32_t* f, const int32_t* t,
                          const double* X, double* Y, VT* wbuf, size_t vstride, int precond);
+cudaError_t launch_base_trig(cudaStream_t st, int n, const double* th, double* c, double* s);
 
 }  // namespace gpcg

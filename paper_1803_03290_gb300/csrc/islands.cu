@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(NT) islands_kernel(
     int n, int m, int slack, int S, const int32_t* __restrict__ outages,
     const int32_t* __restrict__ f, const int32_t* __restrict__ t,
     const int8_t* __restrict__ bus_type, const double* __restrict__ P_sched,
-    const double* __restrict__ P_gen, const int32_t* __restrict__ pre, double pv_gen_total,
+    const double* __restrict__ P_gen, const int32_t* __restrict__ pre,
     int32_t* isl_lo, int32_t* isl_cnt, double* coef, int32_t* no_gen, int32_t* label_out,
     int32_t* err) {
   extern __shared__ int32_t parent[];
@@ -62,15 +62,16 @@ __global__ void __launch_bounds__(NT) islands_kernel(
     for (int i = tid; i < n; i += NT) parent[i] = uf_find(parent, i);
     __syncthreads();
     int main_lab = parent[slack];
-    double sumP = 0.0, genI = 0.0;
+    double sumP = 0.0, genM = 0.0;  // island net injection, main-island PV generation
     int cnt = 0, lo = 0x7fffffff, hi = -1;
     for (int i = tid; i < n; i += NT) {
       int lab = parent[i];
       if (label_out) label_out[(size_t)s * n + i] = lab;
-      if (lab != main_lab) {
+      if (lab == main_lab) {
+        if (bus_type[i] == 1 && P_gen[i] > 0.0) genM += P_gen[i];
+      } else {
         ++cnt;
         sumP += P_sched[i];
-        if (bus_type[i] == 1 && P_gen[i] > 0.0) genI += P_gen[i];
         int pr = pre[i];
         lo = min(lo, pr);
         hi = max(hi, pr);
@@ -78,13 +79,13 @@ __global__ void __launch_bounds__(NT) islands_kernel(
     }
     for (int o = 16; o; o >>= 1) {
       sumP += __shfl_xor_sync(0xffffffffu, sumP, o);
-      genI += __shfl_xor_sync(0xffffffffu, genI, o);
+      genM += __shfl_xor_sync(0xffffffffu, genM, o);
       cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
       lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
       hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
     if (ln == 0) {
-      red_d[0][wid] = sumP; red_d[1][wid] = genI;
+      red_d[0][wid] = sumP; red_d[1][wid] = genM;
       red_i[0][wid] = cnt; red_i[1][wid] = lo; red_i[2][wid] = hi;
     }
     __syncthreads();
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(NT) islands_kernel(
       if (c > 0 && b - a + 1 != c) atomicExch(err, 3);
       isl_lo[s] = c > 0 ? a : 0;
       isl_cnt[s] = c;
-      double den = pv_gen_total - gi;
+      const double den = gi;  // main-island PV generation
       int ng = (c > 0) && !(den > 0.0);
       no_gen[s] = ng;
       coef[s] = (c > 0 && !ng) ? sp / den : 0.0;
@@ -112,7 +113,7 @@ size_t islands_smem(int n) { return (size_t)n * sizeof(int32_t); }
 cudaError_t launch_islands(cudaStream_t st, int grid, int n, int m, int slack, int S,
                            const int32_t* outages, const int32_t* f, const int32_t* t,
                            const int8_t* bus_type, const double* P_sched, const double* P_gen,
-                           const int32_t* pre, double pv_gen_total, int32_t* isl_lo,
+                           const int32_t* pre, int32_t* isl_lo,
                            int32_t* isl_cnt, double* coef, int32_t* no_gen, int32_t* label_out,
                            int32_t* err) {
   if (S == 0) return cudaSuccess;
@@ -121,7 +122,7 @@ cudaError_t launch_islands(cudaStream_t st, int grid, int n, int m, int slack, i
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (ce != cudaSuccess) return ce;
   islands_kernel<512><<<grid, 512, smem, st>>>(n, m, slack, S, outages, f, t, bus_type, P_sched,
-                                               P_gen, pre, pv_gen_total, isl_lo, isl_cnt, coef,
+                                               P_gen, pre, isl_lo, isl_cnt, coef,
                                                no_gen, label_out, err);
   return cudaGetLastError();
 }
