@@ -111,7 +111,7 @@ typedef struct {
   int32_t max_inner;   /* PCG iteration cap per solve; 500 */
   int32_t precision;   /* GPCG_PLAIN_FP64 / _BATCHED_FP32 / _BATCHED_FP64 */
   int32_t precond;     /* GPCG_PRECOND_*; default GPCG_PRECOND_EXACT */
-  int32_t tile;        /* scenarios per tile: 8, 16 or 32; 0 = chosen by the
+  int32_t tile;        /* scenarios per tile: 4, 8, 16 or 32; 0 = chosen by the
                           library's autotuner on first use */
   int32_t ctas_per_sm; /* resident tiles per SM; 0 = from the occupancy API */
 } gpcg_options;

@@ -18,6 +18,10 @@ FDPF (eqs. (4)-(5), Sec. III.B): starting from a given state, repeat
   evaluate dP, dQ; stop when max|dP| (PV and PQ buses) and max|dQ| (PQ buses)
   are both <= tol; solve B' dtheta = dP/V, theta += dtheta; evaluate dQ;
   solve B'' dV = dQ/V, V += dV.
+The paper gives no stopping rule for a diverging case; here a run is
+declared diverged when the mismatch is not finite, exceeds DIVERGE_LIMIT, or
+has grown to DIVERGE_GROWTH times the smallest value it reached (the
+iteration has left its basin of convergence).
 Every solve here is direct (re-formed, fully factorised matrix), so the
 result is the exact AC solution up to the tolerance.
 
@@ -37,6 +41,7 @@ from scipy.sparse.linalg import splu
 PQ, PV, SLACK = 0, 1, 2
 STATUS_OK, STATUS_MAXITER, STATUS_DIVERGED, STATUS_ISLAND_NO_GEN = 0, 1, 2, 3
 DIVERGE_LIMIT = 1.0e4   # p.u.; a mismatch above this is taken as divergence
+DIVERGE_GROWTH = 10.0   # or one this many times above the smallest seen so far
 DENSE_MAX = 500          # direct solves use dense LU up to this size
 
 
@@ -164,11 +169,13 @@ def fdpf(grid, in_service, active, P_sched, theta0, V0, tol, max_outer):
     V = np.where(active, V0, 0.0).astype(np.float64)
     Q_sched = grid.Q_sched
     k = 0
+    best = np.inf
     while True:
         dP, dQ = mismatch(ybus, P_sched, Q_sched, theta, V)
         err = max(np.abs(dP[pvpq]).max(initial=0.0), np.abs(dQ[pq]).max(initial=0.0))
-        if not np.isfinite(err) or err > DIVERGE_LIMIT:
+        if not np.isfinite(err) or err > DIVERGE_LIMIT or err > DIVERGE_GROWTH * best:
             return theta, V, k, STATUS_DIVERGED, err
+        best = min(best, err)
         if err <= tol:
             return theta, V, k, STATUS_OK, err
         if k >= max_outer:

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -143,6 +144,10 @@ struct gpcg_ctx {
   int n_bridges = 0;
   double pv_gen_total = 0.0;
   int n_adj_slots = 0, n_adj_over = 0;
+  std::vector<int32_t> deg;
+  int32_t *mis_order = nullptr, *misq_order = nullptr;
+  unsigned long long* phase = nullptr;
+  bool phase_on = false;
   DevGrid G;
   double *wP = nullptr, *wQ = nullptr;
   MatDev MP, MQ;
@@ -152,7 +157,9 @@ struct gpcg_ctx {
   int base_outer = -1;
   bool base_ok = false;
   // per-call buffers
-  int32_t *d_outages = nullptr, *d_lo = nullptr, *d_cnt = nullptr, *d_nogen = nullptr;
+  int32_t *d_outages = nullptr, *d_lo = nullptr, *d_cnt = nullptr, *d_nogen = nullptr,
+          *d_order = nullptr;
+  std::vector<double> base_flow;  // |P_ij| of the base case: scheduling priority
   double* d_coef = nullptr;
   size_t sc_cap = 0;
   int32_t *d_counter = nullptr, *d_err = nullptr;
@@ -211,8 +218,8 @@ static gpcg_status check_options(const gpcg_options& o) {
     return fail(GPCG_ERR_INVALID_ARG, "precision must be 0, 1 or 2");
   if (o.precond < 0 || o.precond > 2)
     return fail(GPCG_ERR_INVALID_ARG, "precond must be 0, 1 or 2");
-  if (!(o.tile == 0 || o.tile == 8 || o.tile == 16 || o.tile == 32))
-    return fail(GPCG_ERR_INVALID_ARG, "tile must be 0, 8, 16 or 32");
+  if (!(o.tile == 0 || o.tile == 4 || o.tile == 8 || o.tile == 16 || o.tile == 32))
+    return fail(GPCG_ERR_INVALID_ARG, "tile must be 0, 4, 8, 16 or 32");
   if (o.ctas_per_sm < 0 || o.ctas_per_sm > 64)
     return fail(GPCG_ERR_INVALID_ARG, "ctas_per_sm must be in [0, 64]");
   return GPCG_OK;
@@ -351,6 +358,15 @@ static gpcg_status build_matrices(gpcg_ctx* c) {
   if (st != GPCG_OK) return st;
   st = build_matrix(c, c->MQ, keepQ, c->wQ, fill);
   if (st != GPCG_OK) return st;
+  {
+    const MatrixPlan& Q = c->MQ.plan;
+    std::vector<int32_t> order(Q.n);
+    for (int k = 0; k < Q.n; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return c->deg[Q.bus_of_row[a]] > c->deg[Q.bus_of_row[b]];
+    });
+    CUDA_TRY(upload(c->mat_owned, &c->misq_order, order.data(), order.size()));
+  }
   c->planned_precond = c->opt.precond;
   return GPCG_OK;
 }
@@ -363,7 +379,7 @@ static void destroy(gpcg_ctx* c) {
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   cudaFree(c->d_outages); cudaFree(c->d_lo); cudaFree(c->d_cnt); cudaFree(c->d_nogen);
-  cudaFree(c->d_coef);
+  cudaFree(c->d_coef); cudaFree(c->d_order);
   delete c;
 }
 
@@ -478,6 +494,14 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
     AL(G.adj_ob, E.ocol.size());
     c->n_adj_slots = (int)pad_nbr.size();
     c->n_adj_over = (int)E.ocol.size();
+    std::vector<int32_t> deg(n), order;
+    for (int b = 0; b < n; ++b) deg[b] = std::min(c->bg.adj.ptr[b + 1] - c->bg.adj.ptr[b], KG);
+    for (int b = 0; b < n; ++b)
+      if (b != slack) order.push_back(b);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return deg[a] > deg[b]; });
+    UP(G.adj_deg, deg.data(), n);
+    UP(c->mis_order, order.data(), order.size());
+    c->deg = deg;
   }
   UP(G.sub, c->sub.data(), n);
   AL(G.g, m);
@@ -495,6 +519,11 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
   AL(c->d_err, 1);
   for (auto& e : c->ev)
     if ((ce = cudaEventCreate(&e)) != cudaSuccess) return fail_cuda(ce, "event");
+  AL(c->phase, 8);
+  {
+    const char* ev = std::getenv("GPCG_PHASE_TIMERS");
+    c->phase_on = ev && ev[0] == '1';
+  }
 #undef UP
 #undef AL
   launch_branch_params(0, m, G.r, G.x, G.g, G.by, c->wP, c->wQ);
@@ -560,8 +589,8 @@ extern "C" gpcg_status gpcg_get_info(const gpcg_ctx* c, gpcg_info* info) {
 static gpcg_status ensure_scen(gpcg_ctx* c, size_t S) {
   if (S <= c->sc_cap) return GPCG_OK;
   cudaFree(c->d_outages); cudaFree(c->d_lo); cudaFree(c->d_cnt); cudaFree(c->d_nogen);
-  cudaFree(c->d_coef);
-  c->d_outages = c->d_lo = c->d_cnt = c->d_nogen = nullptr;
+  cudaFree(c->d_coef); cudaFree(c->d_order);
+  c->d_outages = c->d_lo = c->d_cnt = c->d_nogen = c->d_order = nullptr;
   c->d_coef = nullptr;
   c->sc_cap = 0;
   size_t cap = std::max<size_t>(S, 64);
@@ -570,6 +599,7 @@ static gpcg_status ensure_scen(gpcg_ctx* c, size_t S) {
   CUDA_TRY(cudaMalloc(&c->d_cnt, cap * 4));
   CUDA_TRY(cudaMalloc(&c->d_nogen, cap * 4));
   CUDA_TRY(cudaMalloc(&c->d_coef, cap * 8));
+  CUDA_TRY(cudaMalloc(&c->d_order, cap * 4));
   c->sc_cap = cap;
   return GPCG_OK;
 }
@@ -626,6 +656,9 @@ static gpcg_status run_fdpf(gpcg_ctx* c, cudaStream_t st, FdpfParams P, int T, i
 static FdpfParams base_params(gpcg_ctx* c) {
   FdpfParams P;
   P.G = c->G;
+  P.mis_order = c->mis_order;
+  P.misq_order = c->misq_order;
+  P.phase_cycles = c->phase_on ? c->phase : nullptr;
   P.tol = c->opt.tol;
   P.inner_rtol = c->opt.inner_rtol;
   P.max_outer = c->opt.max_outer;
@@ -680,6 +713,9 @@ extern "C" gpcg_status gpcg_base_solve(gpcg_ctx* c, double* theta, double* vm, d
   }
   CUDA_TRY(launch_base_trig(0, c->n, c->th0, c->c0, c->s0));
   CUDA_TRY(cudaDeviceSynchronize());
+  c->base_flow.resize(c->m);
+  CUDA_TRY(cudaMemcpy(c->base_flow.data(), c->flow0, (size_t)c->m * 8, cudaMemcpyDeviceToHost));
+  for (auto& v : c->base_flow) v = std::fabs(v);
   c->base_ok = true;
   if (theta) CUDA_TRY(cudaMemcpy(theta, c->th0, (size_t)c->n * 8, cudaMemcpyDeviceToHost));
   if (vm) CUDA_TRY(cudaMemcpy(vm, c->V0, (size_t)c->n * 8, cudaMemcpyDeviceToHost));
@@ -724,6 +760,15 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
   gpcg_status s_ = ensure_scen(c, S);
   if (s_ != GPCG_OK) return s_;
   CUDA_TRY(cudaMemcpyAsync(c->d_outages, hout.data(), S * 4, cudaMemcpyHostToDevice, st));
+  // scheduling order: heavily loaded branches first (their outages take the
+  // most outer iterations), so the longest scenarios start earliest
+  std::vector<int32_t> order(S);
+  for (size_t s = 0; s < S; ++s) order[s] = (int32_t)s;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return c->base_flow[hout[a]] > c->base_flow[hout[b]];
+  });
+  CUDA_TRY(cudaMemcpyAsync(c->d_order, order.data(), S * 4, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors above go out of scope
 
   // outputs: device pointers directly, or device staging for host pointers
   std::vector<void*> staging;
@@ -760,6 +805,7 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
   if (ce != cudaSuccess) { cleanup(); return fail(GPCG_ERR_CUDA, "islands: %s", cudaGetErrorString(ce)); }
   CUDA_TRY(cudaEventRecord(c->ev[1], st));
 
+  if (c->phase_on) CUDA_TRY(cudaMemsetAsync(c->phase, 0, 8 * sizeof(unsigned long long), st));
   FdpfParams P = base_params(c);
   P.sc = ScenInfo{c->d_outages, c->d_lo, c->d_cnt, c->d_coef, c->d_nogen};
   P.th0 = c->th0;
@@ -785,7 +831,7 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
       rs = run_fdpf<double>(c, st, Q, 2, 1);
     }
   } else {
-    const int T = c->opt.tile ? c->opt.tile : (c->tile ? c->tile : 32);
+    const int T = c->opt.tile ? c->opt.tile : (c->tile ? c->tile : 4);
     c->tile = T;
     const int n_tiles = (int)((S + T - 1) / T);
     const bool f32 = c->opt.precision == GPCG_BATCHED_FP32;
@@ -795,11 +841,26 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
     const int slots = std::max(1, std::min(n_tiles, c->num_sms * per_sm));
     P.S = (int)S;
     P.n_tiles = n_tiles;
+    P.order = c->d_order;
     rs = f32 ? run_fdpf<float>(c, st, P, T, slots) : run_fdpf<double>(c, st, P, T, slots);
   }
   if (rs != GPCG_OK) { cleanup(); return rs; }
   CUDA_TRY(cudaEventRecord(c->ev[2], st));
   c->timed = true;
+  if (c->phase_on) {
+    // diagnostics requested through GPCG_PHASE_TIMERS=1: SM cycles per phase,
+    // summed over CTAs (thread 0 of each CTA)
+    unsigned long long h[8];
+    CUDA_TRY(cudaMemcpyAsync(h, c->phase, sizeof h, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    static const char* names[8] = {"init", "mismatchP", "pcgP", "updateP", "mismatchQ",
+                                   "pcgQ", "updateQ", "output"};
+    double tot = 0;
+    for (int k = 0; k < 8; ++k) tot += (double)h[k];
+    std::fprintf(stderr, "gpcg phase cycles (sum over CTAs):");
+    for (int k = 0; k < 8; ++k) std::fprintf(stderr, " %s=%.1f%%", names[k], 100.0 * h[k] / tot);
+    std::fprintf(stderr, " total=%.3e\n", tot);
+  }
   if (mem == GPCG_MEM_HOST) {
     auto back = [&](auto* user, auto* dev, size_t count) -> cudaError_t {
       if (!user) return cudaSuccess;

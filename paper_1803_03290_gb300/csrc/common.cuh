@@ -25,7 +25,7 @@ struct DevGrid {
   double *Gii = nullptr, *Bii = nullptr;     // bus admittance diagonal
   int32_t *pre = nullptr, *sub = nullptr;    // depth-first preorder, subtree size
   // padded adjacency for the mismatch: neighbour, branch, -g, -b_y per slot
-  int32_t *adj_nbr = nullptr, *adj_brl = nullptr;
+  int32_t *adj_nbr = nullptr, *adj_brl = nullptr, *adj_deg = nullptr;  // deg = used slots
   double *adj_g = nullptr, *adj_b = nullptr;
   int32_t *adj_optr = nullptr, *adj_onbr = nullptr, *adj_obr = nullptr;
   double *adj_og = nullptr, *adj_ob = nullptr;

@@ -27,6 +27,15 @@
 namespace gpcg {
 
 constexpr int LP = 2;  // scenario lanes per thread
+#ifndef FDPF_UNROLL
+#define FDPF_UNROLL 1
+#endif
+constexpr int UNR = FDPF_UNROLL;  // rows per thread in flight in the PCG passes
+// Large passes are kept out of line by default (separate register
+// allocation); -DGPCG_PASS_INLINE=__forceinline__ inlines them.
+#ifndef GPCG_PASS_INLINE
+#define GPCG_PASS_INLINE __noinline__
+#endif
 #ifndef FDPF_MIN_BLOCKS
 #define FDPF_MIN_BLOCKS 2  // resident CTAs per SM the register budget is cut for
 #endif
@@ -86,12 +95,14 @@ struct LaneState {
   int raP[T], rbP[T], raQ[T], rbQ[T];
   double wP[T], wQ[T], coef[T], gl[T], bl[T];
   int active[T], outer[T], inP[T], inQ[T], status[T], nogen[T];
-  double err[T];
+  double err[T], best[T];
   double rz[T], bb[T], alpha[T], beta[T], rrmin[T];
+  unsigned long long tphase[8];
   int pdone[T], stall[T];
+  int done[T], fresh[T];
   double red[NTHREADS * LP];
   int flag;
-  int tile;
+  int drained;
 };
 
 template <int T>
@@ -156,39 +167,64 @@ __device__ __forceinline__ Pair<double> spmv_pass(const DevMatT<VT>& M, const VT
                                                   VT* __restrict__ q, int ra0, int rb0, VT w0,
                                                   int ra1, int rb1, VT w1) {
   const Geo<T> g;
-  double pq0 = 0.0, pq1 = 0.0;
-  for (int i = g.rs; i < M.n; i += Geo<T>::RPS) {
-    const int oth0 = (i == ra0) ? rb0 : ((i == rb0) ? ra0 : -2);
-    const int oth1 = (i == ra1) ? rb1 : ((i == rb1) ? ra1 : -2);
-    int c[KA];
-    VT v[KA];
-    ld_cols<KA>(M.A.col + (size_t)i * KA, c);
-    ld_vals<KA>(M.A.val + (size_t)i * KA, v);
-    Pair<VT> pc[KA];
+  constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
+  VT pq0 = 0, pq1 = 0;
+  // UNR rows per thread per step, and the column indices of the next step
+  // loaded one step ahead: each step waits on one memory latency for
+  // UNR rows' gathers
+  int cn[UNR][KA];
 #pragma unroll
-    for (int k = 0; k < KA; ++k) pc[k] = ld2(p + (size_t)c[k] * T + g.lane);
-    const Pair<VT> pi = ld2(p + (size_t)i * T + g.lane);
-    VT a0 = 0, a1 = 0;
+  for (int u = 0; u < UNR; ++u)
+    if (g.rs + u * RPS < M.n) ld_cols<KA>(M.A.col + (size_t)(g.rs + u * RPS) * KA, cn[u]);
+  for (int i0 = g.rs; i0 < M.n; i0 += STEP) {
+    int c[UNR][KA];
+    VT v[UNR][KA];
+    Pair<VT> pc[UNR][KA], pi[UNR];
 #pragma unroll
-    for (int k = 0; k < KA; ++k) {
-      a0 += (v[k] + (c[k] == oth0 ? w0 : (VT)0)) * pc[k].a;
-      a1 += (v[k] + (c[k] == oth1 ? w1 : (VT)0)) * pc[k].b;
+    for (int u = 0; u < UNR; ++u) {
+#pragma unroll
+      for (int k = 0; k < KA; ++k) c[u][k] = cn[u][k];
+      const int in = i0 + STEP + u * RPS;
+      if (in < M.n) ld_cols<KA>(M.A.col + (size_t)in * KA, cn[u]);
     }
-    const int o0 = __ldg(M.A.optr + i), o1 = __ldg(M.A.optr + i + 1);
-    for (int o = o0; o < o1; ++o) {
-      const int cc = __ldg(M.A.ocol + o);
-      const VT vv = __ldg(M.A.oval + o);
-      const Pair<VT> pp = ld2(p + (size_t)cc * T + g.lane);
-      a0 += (vv + (cc == oth0 ? w0 : (VT)0)) * pp.a;
-      a1 += (vv + (cc == oth1 ? w1 : (VT)0)) * pp.b;
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const int i = i0 + u * RPS;
+      if (i < M.n) {
+        ld_vals<KA>(M.A.val + (size_t)i * KA, v[u]);
+#pragma unroll
+        for (int k = 0; k < KA; ++k) pc[u][k] = ld2(p + (size_t)c[u][k] * T + g.lane);
+        pi[u] = ld2(p + (size_t)i * T + g.lane);
+      }
     }
-    if (oth0 != -2) a0 -= w0 * pi.a;
-    if (oth1 != -2) a1 -= w1 * pi.b;
-    st2(q + (size_t)i * T + g.lane, Pair<VT>{a0, a1});
-    pq0 += (double)(pi.a * a0);
-    pq1 += (double)(pi.b * a1);
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const int i = i0 + u * RPS;
+      if (i >= M.n) continue;
+      const int oth0 = (i == ra0) ? rb0 : ((i == rb0) ? ra0 : -2);
+      const int oth1 = (i == ra1) ? rb1 : ((i == rb1) ? ra1 : -2);
+      VT a0 = 0, a1 = 0;
+#pragma unroll
+      for (int k = 0; k < KA; ++k) {
+        a0 += (v[u][k] + (c[u][k] == oth0 ? w0 : (VT)0)) * pc[u][k].a;
+        a1 += (v[u][k] + (c[u][k] == oth1 ? w1 : (VT)0)) * pc[u][k].b;
+      }
+      const int o0 = __ldg(M.A.optr + i), o1 = __ldg(M.A.optr + i + 1);
+      for (int o = o0; o < o1; ++o) {
+        const int cc = __ldg(M.A.ocol + o);
+        const VT vv = __ldg(M.A.oval + o);
+        const Pair<VT> pp = ld2(p + (size_t)cc * T + g.lane);
+        a0 += (vv + (cc == oth0 ? w0 : (VT)0)) * pp.a;
+        a1 += (vv + (cc == oth1 ? w1 : (VT)0)) * pp.b;
+      }
+      if (oth0 != -2) a0 -= w0 * pi[u].a;
+      if (oth1 != -2) a1 -= w1 * pi[u].b;
+      st2(q + (size_t)i * T + g.lane, Pair<VT>{a0, a1});
+      pq0 += pi[u].a * a0;
+      pq1 += pi[u].b * a1;
+    }
   }
-  return {pq0, pq1};
+  return {(double)pq0, (double)pq1};
 }
 
 // Forward substitution L y = r over the level schedule (rows of one level
@@ -200,49 +236,77 @@ __device__ __forceinline__ Pair<double> fwd_pass(const DevMatT<VT>& M, VT* __res
                                                  const VT* __restrict__ q, VT* __restrict__ z,
                                                  VT al0, VT al1) {
   const Geo<T> g;
-  double rr0 = 0.0, rr1 = 0.0;
+  constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
+  VT rr0 = 0, rr1 = 0;
   for (int lev = 0; lev < M.nlev; ++lev) {
     const int r0 = __ldg(M.lev_ptr + lev), r1 = __ldg(M.lev_ptr + lev + 1);
-    for (int i = r0 + g.rs; i < r1; i += Geo<T>::RPS) {
-      const size_t o = (size_t)i * T + g.lane;
-      int c[KL];
-      VT v[KL];
-      ld_cols<KL>(M.L.col + (size_t)i * KL, c);
-      ld_vals<KL>(M.L.val + (size_t)i * KL, v);
-      Pair<VT> zc[KL];
+    int cn[UNR][KL];
 #pragma unroll
-      for (int k = 0; k < KL; ++k) zc[k] = ld2(z + (size_t)c[k] * T + g.lane);
-      Pair<VT> ri = ld2(r + o);
-      if (FUSED) {
-        const Pair<VT> pi = ld2(p + o), qi = ld2(q + o), xi = ld2(x + o);
-        st2(x + o, Pair<VT>{xi.a + al0 * pi.a, xi.b + al1 * pi.b});
-        ri.a -= al0 * qi.a;
-        ri.b -= al1 * qi.b;
-        st2(r + o, ri);
-      } else {
-        st2(x + o, Pair<VT>{(VT)0, (VT)0});
-      }
-      rr0 += (double)(ri.a * ri.a);
-      rr1 += (double)(ri.b * ri.b);
-      VT a0 = ri.a, a1 = ri.b;
+    for (int u = 0; u < UNR; ++u)
+      if (r0 + g.rs + u * RPS < r1) ld_cols<KL>(M.L.col + (size_t)(r0 + g.rs + u * RPS) * KL, cn[u]);
+    for (int i0 = r0 + g.rs; i0 < r1; i0 += STEP) {
+      int c[UNR][KL];
+      VT v[UNR][KL];
+      Pair<VT> zc[UNR][KL], ri[UNR], pi[UNR], qi[UNR], xi[UNR];
 #pragma unroll
-      for (int k = 0; k < KL; ++k) {
-        a0 -= v[k] * zc[k].a;
-        a1 -= v[k] * zc[k].b;
+      for (int u = 0; u < UNR; ++u) {
+#pragma unroll
+        for (int k = 0; k < KL; ++k) c[u][k] = cn[u][k];
+        const int in = i0 + STEP + u * RPS;
+        if (in < r1) ld_cols<KL>(M.L.col + (size_t)in * KL, cn[u]);
       }
-      const int o0 = __ldg(M.L.optr + i), o1 = __ldg(M.L.optr + i + 1);
-      for (int e = o0; e < o1; ++e) {
-        const VT vv = __ldg(M.L.oval + e);
-        const Pair<VT> zz = ld2(z + (size_t)__ldg(M.L.ocol + e) * T + g.lane);
-        a0 -= vv * zz.a;
-        a1 -= vv * zz.b;
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const int i = i0 + u * RPS;
+        if (i < r1) {
+          const size_t o = (size_t)i * T + g.lane;
+          ld_vals<KL>(M.L.val + (size_t)i * KL, v[u]);
+#pragma unroll
+          for (int k = 0; k < KL; ++k) zc[u][k] = ld2(z + (size_t)c[u][k] * T + g.lane);
+          ri[u] = ld2(r + o);
+          if (FUSED) {
+            pi[u] = ld2(p + o);
+            qi[u] = ld2(q + o);
+            xi[u] = ld2(x + o);
+          }
+        }
       }
-      const VT id = __ldg(M.inv_diag + i);
-      st2(z + o, Pair<VT>{a0 * id, a1 * id});
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const int i = i0 + u * RPS;
+        if (i >= r1) continue;
+        const size_t o = (size_t)i * T + g.lane;
+        Pair<VT> rv = ri[u];
+        if (FUSED) {
+          st2(x + o, Pair<VT>{xi[u].a + al0 * pi[u].a, xi[u].b + al1 * pi[u].b});
+          rv.a -= al0 * qi[u].a;
+          rv.b -= al1 * qi[u].b;
+          st2(r + o, rv);
+        } else {
+          st2(x + o, Pair<VT>{(VT)0, (VT)0});
+        }
+        rr0 += rv.a * rv.a;
+        rr1 += rv.b * rv.b;
+        VT a0 = rv.a, a1 = rv.b;
+#pragma unroll
+        for (int k = 0; k < KL; ++k) {
+          a0 -= v[u][k] * zc[u][k].a;
+          a1 -= v[u][k] * zc[u][k].b;
+        }
+        const int o0 = __ldg(M.L.optr + i), o1 = __ldg(M.L.optr + i + 1);
+        for (int e = o0; e < o1; ++e) {
+          const VT vv = __ldg(M.L.oval + e);
+          const Pair<VT> zz = ld2(z + (size_t)__ldg(M.L.ocol + e) * T + g.lane);
+          a0 -= vv * zz.a;
+          a1 -= vv * zz.b;
+        }
+        const VT id = __ldg(M.inv_diag + i);
+        st2(z + o, Pair<VT>{a0 * id, a1 * id});
+      }
     }
     __syncthreads();
   }
-  return {rr0, rr1};
+  return {(double)rr0, (double)rr1};
 }
 
 // Back substitution L^T z = y in place (z holds y on entry), over the
@@ -251,43 +315,74 @@ template <int T, typename VT>
 __device__ __forceinline__ Pair<double> bwd_pass(const DevMatT<VT>& M, const VT* __restrict__ r,
                                                  VT* __restrict__ z) {
   const Geo<T> g;
-  double rz0 = 0.0, rz1 = 0.0;
+  constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
+  VT rz0 = 0, rz1 = 0;
   for (int lev = 0; lev < M.nblev; ++lev) {
     const int r0 = __ldg(M.blev_ptr + lev), r1 = __ldg(M.blev_ptr + lev + 1);
-    for (int k0 = r0 + g.rs; k0 < r1; k0 += Geo<T>::RPS) {
-      const int i = __ldg(M.blev_rows + k0);
-      const size_t o = (size_t)i * T + g.lane;
-      int c[KU];
-      VT v[KU];
-      ld_cols<KU>(M.U.col + (size_t)i * KU, c);
-      ld_vals<KU>(M.U.val + (size_t)i * KU, v);
-      Pair<VT> zc[KU];
+    int in_[UNR], cn[UNR][KU];
 #pragma unroll
-      for (int k = 0; k < KU; ++k) zc[k] = ld2(z + (size_t)c[k] * T + g.lane);
-      const Pair<VT> yi = ld2(z + o), ri = ld2(r + o);
-      VT a0 = yi.a, a1 = yi.b;
+    for (int u = 0; u < UNR; ++u) {
+      in_[u] = 0;
+      if (r0 + g.rs + u * RPS < r1) {
+        in_[u] = __ldg(M.blev_rows + r0 + g.rs + u * RPS);
+        ld_cols<KU>(M.U.col + (size_t)in_[u] * KU, cn[u]);
+      }
+    }
+    for (int k0 = r0 + g.rs; k0 < r1; k0 += STEP) {
+      int ii[UNR], c[UNR][KU];
+      VT v[UNR][KU];
+      Pair<VT> zc[UNR][KU], yi[UNR], ri[UNR];
 #pragma unroll
-      for (int k = 0; k < KU; ++k) {
-        a0 -= v[k] * zc[k].a;
-        a1 -= v[k] * zc[k].b;
+      for (int u = 0; u < UNR; ++u) {
+        ii[u] = in_[u];
+#pragma unroll
+        for (int k = 0; k < KU; ++k) c[u][k] = cn[u][k];
+        const int kn = k0 + STEP + u * RPS;
+        if (kn < r1) {
+          in_[u] = __ldg(M.blev_rows + kn);
+          ld_cols<KU>(M.U.col + (size_t)in_[u] * KU, cn[u]);
+        }
       }
-      const int o0 = __ldg(M.U.optr + i), o1 = __ldg(M.U.optr + i + 1);
-      for (int e = o0; e < o1; ++e) {
-        const VT vv = __ldg(M.U.oval + e);
-        const Pair<VT> zz = ld2(z + (size_t)__ldg(M.U.ocol + e) * T + g.lane);
-        a0 -= vv * zz.a;
-        a1 -= vv * zz.b;
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        if (k0 + u * RPS < r1) {
+          const size_t o = (size_t)ii[u] * T + g.lane;
+          ld_vals<KU>(M.U.val + (size_t)ii[u] * KU, v[u]);
+#pragma unroll
+          for (int k = 0; k < KU; ++k) zc[u][k] = ld2(z + (size_t)c[u][k] * T + g.lane);
+          yi[u] = ld2(z + o);
+          ri[u] = ld2(r + o);
+        }
       }
-      const VT id = __ldg(M.inv_diag + i);
-      a0 *= id;
-      a1 *= id;
-      st2(z + o, Pair<VT>{a0, a1});
-      rz0 += (double)(ri.a * a0);
-      rz1 += (double)(ri.b * a1);
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        if (k0 + u * RPS >= r1) continue;
+        const int i = ii[u];
+        const size_t o = (size_t)i * T + g.lane;
+        VT a0 = yi[u].a, a1 = yi[u].b;
+#pragma unroll
+        for (int k = 0; k < KU; ++k) {
+          a0 -= v[u][k] * zc[u][k].a;
+          a1 -= v[u][k] * zc[u][k].b;
+        }
+        const int o0 = __ldg(M.U.optr + i), o1 = __ldg(M.U.optr + i + 1);
+        for (int e = o0; e < o1; ++e) {
+          const VT vv = __ldg(M.U.oval + e);
+          const Pair<VT> zz = ld2(z + (size_t)__ldg(M.U.ocol + e) * T + g.lane);
+          a0 -= vv * zz.a;
+          a1 -= vv * zz.b;
+        }
+        const VT id = __ldg(M.inv_diag + i);
+        a0 *= id;
+        a1 *= id;
+        st2(z + o, Pair<VT>{a0, a1});
+        rz0 += ri[u].a * a0;
+        rz1 += ri[u].b * a1;
+      }
     }
     __syncthreads();
   }
-  return {rz0, rz1};
+  return {(double)rz0, (double)rz1};
 }
 
 // Jacobi: z = r / diag(B_s), the diagonal with the outage applied; a row
@@ -331,17 +426,32 @@ __device__ __forceinline__ void pupdate_pass(const DevMatT<VT>& M, const VT* __r
                                              VT* __restrict__ p, VT be0, VT be1, int lo0,
                                              int cnt0, int lo1, int cnt1, bool first) {
   const Geo<T> g;
-  for (int i = g.rs; i < M.n; i += Geo<T>::RPS) {
-    const size_t o = (size_t)i * T + g.lane;
-    const int pr = __ldg(M.pre_of_row + i);
-    const Pair<VT> zi = ld2(z + o);
-    Pair<VT> pn{in_island(pr, lo0, cnt0) ? (VT)0 : zi.a, in_island(pr, lo1, cnt1) ? (VT)0 : zi.b};
-    if (!first) {
-      const Pair<VT> pi = ld2(p + o);
-      pn.a += be0 * pi.a;
-      pn.b += be1 * pi.b;
+  constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
+  for (int i0 = g.rs; i0 < M.n; i0 += STEP) {
+    int pr[UNR];
+    Pair<VT> zi[UNR], pi[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const int i = i0 + u * RPS;
+      if (i < M.n) {
+        const size_t o = (size_t)i * T + g.lane;
+        pr[u] = __ldg(M.pre_of_row + i);
+        zi[u] = ld2(z + o);
+        if (!first) pi[u] = ld2(p + o);
+      }
     }
-    st2(p + o, pn);
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const int i = i0 + u * RPS;
+      if (i >= M.n) continue;
+      Pair<VT> pn{in_island(pr[u], lo0, cnt0) ? (VT)0 : zi[u].a,
+                  in_island(pr[u], lo1, cnt1) ? (VT)0 : zi[u].b};
+      if (!first) {
+        pn.a += be0 * pi[u].a;
+        pn.b += be1 * pi[u].b;
+      }
+      st2(p + (size_t)i * T + g.lane, pn);
+    }
   }
   __syncthreads();
 }
@@ -351,7 +461,7 @@ __device__ __forceinline__ void pupdate_pass(const DevMatT<VT>& M, const VT* __r
 // the lanes that are active; x starts at 0.  Adds each lane's iteration
 // count to iters[lane].
 template <int T, typename VT>
-__device__ void pcg_solve(const FdpfParams& P, const DevMatT<VT>& M, LaneState<T>& L, VT* x,
+__device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT>& M, LaneState<T>& L, VT* x,
                           VT* r, VT* p, VT* q, VT* z, const int* ra_, const int* rb_,
                           const double* w_, int* iters) {
   const Geo<T> g;
@@ -469,7 +579,7 @@ __device__ void pcg_solve(const FdpfParams& P, const DevMatT<VT>& M, LaneState<T
 // dP/V into the B' right-hand side and tracks max|dP| and max|dQ| for the
 // convergence test); otherwise writes dQ/V into the B'' right-hand side.
 template <int T, typename VT, bool WITH_P>
-__device__ void mismatch_pass(const FdpfParams& P, const DevMatT<VT>& MP, const DevMatT<VT>& MQ,
+__device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMatT<VT>& MP, const DevMatT<VT>& MQ,
                               LaneState<T>& L, const double* __restrict__ E,
                               const double* __restrict__ F, const double* __restrict__ V,
                               VT* __restrict__ rhs, Pair<double>& errP, Pair<double>& errQ) {
@@ -482,70 +592,91 @@ __device__ void mismatch_pass(const FdpfParams& P, const DevMatT<VT>& MP, const 
   const bool act0 = L.active[l0], act1 = L.active[l1];
   const double cf0 = L.coef[l0], cf1 = L.coef[l1];
   const double gl0 = L.gl[l0], bl0 = L.bl[l0], gl1 = L.gl[l1], bl1 = L.bl[l1];
-  const int nrows = WITH_P ? G.n : MQ.n;
-  for (int k = g.rs; k < nrows; k += Geo<T>::RPS) {
+  // rows are visited in order of bus degree, so the threads of a warp run
+  // neighbour loops of equal length and no FP64 work is spent on padding
+  const int nrows = WITH_P ? G.n - 1 : MQ.n;
+  const int32_t* order = WITH_P ? P.mis_order : P.misq_order;
+  int kn = 0, nbn[KG];
+  if (g.rs < nrows) {
+    kn = __ldg(order + g.rs);
+    ld_cols<KG>(G.adj_nbr + (size_t)(WITH_P ? kn : __ldg(MQ.bus_of_row + kn)) * KG, nbn);
+  }
+  for (int kk = g.rs; kk < nrows; kk += Geo<T>::RPS) {
+    const int k = kn;
+    int nb[KG];
+#pragma unroll
+    for (int a = 0; a < KG; ++a) nb[a] = nbn[a];
+    if (kk + Geo<T>::RPS < nrows) {
+      kn = __ldg(order + kk + Geo<T>::RPS);
+      ld_cols<KG>(G.adj_nbr + (size_t)(WITH_P ? kn : __ldg(MQ.bus_of_row + kn)) * KG, nbn);
+    }
     const int i = WITH_P ? k : __ldg(MQ.bus_of_row + k);
     const int bt = G.bus_type[i];
-    if (WITH_P && bt == 2) continue;
     const int pr = __ldg(G.pre + i);
     const bool on0 = act0 && !in_island(pr, lo0, cnt0);
     const bool on1 = act1 && !in_island(pr, lo1, cnt1);
     Pair<VT> out{(VT)0, (VT)0};
     if (on0 || on1) {
-      const size_t o = (size_t)i * T + g.lane;
-      int nb[KG], br[KG];
-      ld_cols<KG>(G.adj_nbr + (size_t)i * KG, nb);
+      const int deg = __ldg(G.adj_deg + i);
+      int br[KG];
       ld_cols<KG>(G.adj_brl + (size_t)i * KG, br);
-      double gg[KG], bb[KG];
-      ld_vals<KG>(G.adj_g + (size_t)i * KG, gg);
-      ld_vals<KG>(G.adj_b + (size_t)i * KG, bb);
-      Pair<double> ej[KG], fj[KG];
-#pragma unroll
-      for (int a = 0; a < KG; ++a) {
-        ej[a] = ld2(E + (size_t)nb[a] * T + g.lane);
-        fj[a] = ld2(F + (size_t)nb[a] * T + g.lane);
-      }
-      const Pair<double> ei = ld2(E + o), fi = ld2(F + o), Vi = ld2(V + o);
-      double Gd0 = __ldg(G.Gii + i), Bd0 = __ldg(G.Bii + i);
-      double Gd1 = Gd0, Bd1 = Bd0;
-      if (i == fb0 || i == tb0) { Gd0 -= gl0; Bd0 -= bl0; }
-      if (i == fb1 || i == tb1) { Gd1 -= gl1; Bd1 -= bl1; }
-      double re0 = Gd0 * ei.a - Bd0 * fi.a, im0 = Gd0 * fi.a + Bd0 * ei.a;
-      double re1 = Gd1 * ei.b - Bd1 * fi.b, im1 = Gd1 * fi.b + Bd1 * ei.b;
-#pragma unroll
-      for (int a = 0; a < KG; ++a) {
-        const double g0 = br[a] == br0 ? 0.0 : gg[a], b0 = br[a] == br0 ? 0.0 : bb[a];
-        const double g1 = br[a] == br1 ? 0.0 : gg[a], b1 = br[a] == br1 ? 0.0 : bb[a];
-        re0 -= g0 * ej[a].a - b0 * fj[a].a;
-        im0 -= g0 * fj[a].a + b0 * ej[a].a;
-        re1 -= g1 * ej[a].b - b1 * fj[a].b;
-        im1 -= g1 * fj[a].b + b1 * ej[a].b;
-      }
       const int o0 = __ldg(G.adj_optr + i), o1 = __ldg(G.adj_optr + i + 1);
-      for (int e = o0; e < o1; ++e) {
-        const int j = __ldg(G.adj_onbr + e), b_ = __ldg(G.adj_obr + e);
-        const double gv = __ldg(G.adj_og + e), bv = __ldg(G.adj_ob + e);
-        const Pair<double> ee = ld2(E + (size_t)j * T + g.lane), ff = ld2(F + (size_t)j * T + g.lane);
-        if (b_ != br0) { re0 -= gv * ee.a - bv * ff.a; im0 -= gv * ff.a + bv * ee.a; }
-        if (b_ != br1) { re1 -= gv * ee.b - bv * ff.b; im1 -= gv * ff.b + bv * ee.b; }
-      }
-      const double qs = __ldg(G.Q_sched + i);
-      const double dQ0 = qs - (fi.a * re0 - ei.a * im0);
-      const double dQ1 = qs - (fi.b * re1 - ei.b * im1);
+      const double Gii = __ldg(G.Gii + i), Bii = __ldg(G.Bii + i), qs = __ldg(G.Q_sched + i);
+      double Ps = 0.0, pg = 0.0;
       if (WITH_P) {
-        double Ps0 = __ldg(G.P_sched + i), Ps1 = Ps0;
-        if (bt == 1) {
-          const double pg = __ldg(G.P_gen + i);
-          Ps0 += cf0 * pg;
-          Ps1 += cf1 * pg;
+        Ps = __ldg(G.P_sched + i);
+        if (bt == 1) pg = __ldg(G.P_gen + i);
+      }
+      // the two lanes one after the other: half the live FP64 registers
+#pragma unroll 1
+      for (int j = 0; j < LP; ++j) {
+        if (!(j ? on1 : on0)) continue;
+        const int ln = g.lane + j;
+        const size_t o = (size_t)i * T + ln;
+        const int brl = j ? br1 : br0;
+        double ej[KG], fj[KG], gg[KG], bb[KG];
+        ld_vals<KG>(G.adj_g + (size_t)i * KG, gg);
+        ld_vals<KG>(G.adj_b + (size_t)i * KG, bb);
+#pragma unroll
+        for (int a = 0; a < KG; ++a) {
+          if (a < deg) {
+            ej[a] = E[(size_t)nb[a] * T + ln];
+            fj[a] = F[(size_t)nb[a] * T + ln];
+          }
         }
-        const double dP0 = Ps0 - (ei.a * re0 + fi.a * im0);
-        const double dP1 = Ps1 - (ei.b * re1 + fi.b * im1);
-        if (on0) { upd_max(errP.a, dP0); if (bt == 0) upd_max(errQ.a, dQ0); out.a = (VT)dP0 / (VT)Vi.a; }
-        if (on1) { upd_max(errP.b, dP1); if (bt == 0) upd_max(errQ.b, dQ1); out.b = (VT)dP1 / (VT)Vi.b; }
-      } else {
-        if (on0) out.a = (VT)dQ0 / (VT)Vi.a;
-        if (on1) out.b = (VT)dQ1 / (VT)Vi.b;
+        const double ei = E[o], fi = F[o], Vi = V[o];
+        double Gd = Gii, Bd = Bii;
+        if (i == (j ? fb1 : fb0) || i == (j ? tb1 : tb0)) {
+          Gd -= j ? gl1 : gl0;
+          Bd -= j ? bl1 : bl0;
+        }
+        double re = Gd * ei - Bd * fi, im = Gd * fi + Bd * ei;
+#pragma unroll
+        for (int a = 0; a < KG; ++a) {
+          if (a < deg && br[a] != brl) {
+            re -= gg[a] * ej[a] - bb[a] * fj[a];
+            im -= gg[a] * fj[a] + bb[a] * ej[a];
+          }
+        }
+        for (int e = o0; e < o1; ++e) {
+          const int jn = __ldg(G.adj_onbr + e), b_ = __ldg(G.adj_obr + e);
+          if (b_ == brl) continue;
+          const double gv = __ldg(G.adj_og + e), bv = __ldg(G.adj_ob + e);
+          const double ee = E[(size_t)jn * T + ln], ff = F[(size_t)jn * T + ln];
+          re -= gv * ee - bv * ff;
+          im -= gv * ff + bv * ee;
+        }
+        const double dQ = qs - (fi * re - ei * im);
+        VT res;
+        if (WITH_P) {
+          const double dP = Ps + (j ? cf1 : cf0) * pg - (ei * re + fi * im);
+          if (j) { upd_max(errP.b, dP); if (bt == 0) upd_max(errQ.b, dQ); }
+          else { upd_max(errP.a, dP); if (bt == 0) upd_max(errQ.a, dQ); }
+          res = (VT)dP / (VT)Vi;
+        } else {
+          res = (VT)dQ / (VT)Vi;
+        }
+        if (j) out.b = res; else out.a = res;
       }
     }
     if (WITH_P) st2(rhs + (size_t)__ldg(MP.row_of_bus + i) * T + g.lane, out);
@@ -558,9 +689,12 @@ __device__ void mismatch_pass(const FdpfParams& P, const DevMatT<VT>& MP, const 
 // 1e-21), else the angle is recomputed.
 __device__ __forceinline__ void rotate(double th_new, double d, double& c, double& s) {
   if (fabs(d) <= 0.05) {
+    // nested Horner forms of the series; 1/k! ratios as multiplications
     const double d2 = d * d;
-    const double sd = d * (1.0 - d2 / 6.0 * (1.0 - d2 / 20.0 * (1.0 - d2 / 42.0 * (1.0 - d2 / 72.0))));
-    const double cd = 1.0 - d2 / 2.0 * (1.0 - d2 / 12.0 * (1.0 - d2 / 30.0 * (1.0 - d2 / 56.0 * (1.0 - d2 / 90.0))));
+    const double sd = d * (1.0 - d2 * (1.0 / 6.0) * (1.0 - d2 * (1.0 / 20.0) *
+                                   (1.0 - d2 * (1.0 / 42.0) * (1.0 - d2 * (1.0 / 72.0)))));
+    const double cd = 1.0 - d2 * 0.5 * (1.0 - d2 * (1.0 / 12.0) * (1.0 - d2 * (1.0 / 30.0) *
+                                   (1.0 - d2 * (1.0 / 56.0) * (1.0 - d2 * (1.0 / 90.0)))));
     const double cn = c * cd - s * sd, sn = s * cd + c * sd;
     c = cn;
     s = sn;
@@ -572,7 +706,7 @@ __device__ __forceinline__ void rotate(double th_new, double d, double& c, doubl
 // theta += dtheta (P half-step) or |V| += dV (Q half-step) on the matrix's
 // rows, then refresh the rectangular voltages.
 template <int T, typename VT, bool IS_P>
-__device__ void update_pass(const DevMatT<VT>& M, LaneState<T>& L, const VT* __restrict__ x,
+__device__ __forceinline__ void update_pass(const DevMatT<VT>& M, LaneState<T>& L, const VT* __restrict__ x,
                             double* th, double* V, double* C, double* Sn, double* E, double* F) {
   const Geo<T> g;
   const int l0 = g.lane, l1 = g.lane + 1;
@@ -609,13 +743,162 @@ __device__ void update_pass(const DevMatT<VT>& M, LaneState<T>& L, const VT* __r
 }
 
 // ------------------------------------------------------------ the kernel
+// Scenario info of a lane taking scenario s (thread `ln`, one per lane).
+template <int T, typename VT>
+__device__ __forceinline__ void setup_lane(const FdpfParams& P, const DevMatT<VT>& MP,
+                                           const DevMatT<VT>& MQ, LaneState<T>& L, int ln) {
+  const DevGrid& G = P.G;
+  const int s = L.scen[ln];
+  const int l = P.sc.outage[s];
+  L.l[ln] = l;
+  L.fb[ln] = l >= 0 ? G.f[l] : -1;
+  L.tb[ln] = l >= 0 ? G.t[l] : -1;
+  L.lo[ln] = P.sc.isl_lo[s];
+  L.cnt[ln] = P.sc.isl_cnt[s];
+  L.coef[ln] = P.sc.coef[s];
+  L.nogen[ln] = P.sc.no_gen[s];
+  L.raP[ln] = l >= 0 ? MP.row_of_bus[G.f[l]] : -1;
+  L.rbP[ln] = l >= 0 ? MP.row_of_bus[G.t[l]] : -1;
+  L.raQ[ln] = l >= 0 ? MQ.row_of_bus[G.f[l]] : -1;
+  L.rbQ[ln] = l >= 0 ? MQ.row_of_bus[G.t[l]] : -1;
+  L.wP[ln] = l >= 0 ? MP.w[l] : 0.0;
+  L.wQ[ln] = l >= 0 ? MQ.w[l] : 0.0;
+  L.gl[ln] = l >= 0 ? G.g[l] : 0.0;
+  L.bl[ln] = l >= 0 ? G.by[l] + 0.5 * G.b_sh[l] : 0.0;
+  L.active[ln] = 1;
+  L.outer[ln] = 0;
+  L.inP[ln] = 0;
+  L.inQ[ln] = 0;
+  L.status[ln] = 0;
+  L.err[ln] = 0.0;
+  L.best[ln] = INFINITY;
+}
+
+// Warm start (Sec. III.B) of the lanes flagged `fresh`: the base-case state,
+// zero on islanded buses.  Other lanes keep their state.
+template <int T>
+__device__ GPCG_PASS_INLINE void init_pass(const FdpfParams& P, LaneState<T>& L, double* th, double* V, double* C,
+                          double* Sn, double* E, double* F) {
+  const Geo<T> g;
+  const DevGrid& G = P.G;
+  const int l0 = g.lane, l1 = g.lane + 1;
+  const bool n0 = L.fresh[l0], n1 = L.fresh[l1];
+  if (!n0 && !n1) return;
+  const int lo0 = L.lo[l0], cnt0 = L.cnt[l0], lo1 = L.lo[l1], cnt1 = L.cnt[l1];
+  for (int i = g.rs; i < G.n; i += Geo<T>::RPS) {
+    const size_t o = (size_t)i * T + g.lane;
+    double t0, v0, c0, s0;
+    if (P.flat_start) { t0 = 0.0; v0 = G.V_set[i]; c0 = 1.0; s0 = 0.0; }
+    else { t0 = P.th0[i]; v0 = P.V0[i]; c0 = P.c0[i]; s0 = P.s0[i]; }
+    const int pr = G.pre[i];
+    const bool i0 = in_island(pr, lo0, cnt0), i1 = in_island(pr, lo1, cnt1);
+    auto put = [&](double* dst, double va, double vb) {
+      Pair<double> v{va, vb};
+      if (!(n0 && n1)) {
+        const Pair<double> old = ld2(dst + o);
+        if (!n0) v.a = old.a;
+        if (!n1) v.b = old.b;
+      }
+      st2(dst + o, v);
+    };
+    put(th, i0 ? 0.0 : t0, i1 ? 0.0 : t0);
+    put(V, i0 ? 0.0 : v0, i1 ? 0.0 : v0);
+    put(C, c0, c0);
+    put(Sn, s0, s0);
+    put(E, i0 ? 0.0 : v0 * c0, i1 ? 0.0 : v0 * c0);
+    put(F, i0 ? 0.0 : v0 * s0, i1 ? 0.0 : v0 * s0);
+  }
+}
+
+// Outputs of the lanes flagged `done`: state, branch flows and loading
+// (Sec. I: overload screening), status and iteration counts.
+template <int T>
+__device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& L, const double* th,
+                            const double* V, const double* E, const double* F) {
+  const Geo<T> g;
+  const DevGrid& G = P.G;
+  const int l0 = g.lane, l1 = g.lane + 1;
+  const bool d0 = L.done[l0], d1 = L.done[l1];
+  const int s0 = d0 ? L.scen[l0] : -1, s1 = d1 ? L.scen[l1] : -1;
+  if ((P.out_theta || P.out_vm) && (d0 || d1)) {
+    for (int i = g.rs; i < G.n; i += Geo<T>::RPS) {
+      const size_t o = (size_t)i * T + g.lane;
+      const Pair<double> t = ld2(th + o), v = ld2(V + o);
+      if (P.out_theta) {
+        if (s0 >= 0) P.out_theta[(size_t)s0 * G.n + i] = t.a;
+        if (s1 >= 0) P.out_theta[(size_t)s1 * G.n + i] = t.b;
+      }
+      if (P.out_vm) {
+        if (s0 >= 0) P.out_vm[(size_t)s0 * G.n + i] = v.a;
+        if (s1 >= 0) P.out_vm[(size_t)s1 * G.n + i] = v.b;
+      }
+    }
+  }
+  double ml0 = 0.0, ml1 = 0.0;
+  if (d0 || d1) {
+    const int br0 = L.l[l0], br1 = L.l[l1];
+    const int lo0 = L.lo[l0], cnt0 = L.cnt[l0], lo1 = L.lo[l1], cnt1 = L.cnt[l1];
+    for (int k = g.rs; k < G.m; k += Geo<T>::RPS) {
+      const int a = __ldg(G.f + k), b = __ldg(G.t + k);
+      const int pa = __ldg(G.pre + a), pb = __ldg(G.pre + b);
+      const bool off0 = !d0 || (k == br0) || in_island(pa, lo0, cnt0) || in_island(pb, lo0, cnt0);
+      const bool off1 = !d1 || (k == br1) || in_island(pa, lo1, cnt1) || in_island(pb, lo1, cnt1);
+      const Pair<double> ea = ld2(E + (size_t)a * T + g.lane), fa = ld2(F + (size_t)a * T + g.lane);
+      const Pair<double> eb = ld2(E + (size_t)b * T + g.lane), fb = ld2(F + (size_t)b * T + g.lane);
+      const double gk = __ldg(G.g + k), bk = __ldg(G.by + k), rk = __ldg(G.rating + k);
+      double Pab0 = 0.0, Pba0 = 0.0, Pab1 = 0.0, Pba1 = 0.0;
+      if (!off0) {
+        const double cr = ea.a * eb.a + fa.a * fb.a, sr = fa.a * eb.a - ea.a * fb.a;
+        Pab0 = gk * (ea.a * ea.a + fa.a * fa.a) - gk * cr - bk * sr;
+        Pba0 = gk * (eb.a * eb.a + fb.a * fb.a) - gk * cr + bk * sr;
+      }
+      if (!off1) {
+        const double cr = ea.b * eb.b + fa.b * fb.b, sr = fa.b * eb.b - ea.b * fb.b;
+        Pab1 = gk * (ea.b * ea.b + fa.b * fa.b) - gk * cr - bk * sr;
+        Pba1 = gk * (eb.b * eb.b + fb.b * fb.b) - gk * cr + bk * sr;
+      }
+      upd_max(ml0, fmax(fabs(Pab0), fabs(Pba0)) / rk);
+      upd_max(ml1, fmax(fabs(Pab1), fabs(Pba1)) / rk);
+      if (P.out_flow) {
+        if (s0 >= 0) P.out_flow[(size_t)s0 * G.m + k] = Pab0;
+        if (s1 >= 0) P.out_flow[(size_t)s1 * G.m + k] = Pab1;
+      }
+    }
+  }
+  const Pair<double> ml = lane_reduce<T, true>(L, ml0, ml1);
+  if (g.rs == 0) {
+#pragma unroll
+    for (int j = 0; j < LP; ++j) {
+      const int ln = g.lane + j, s = L.scen[ln];
+      if (!L.done[ln] || s < 0) continue;
+      int st = L.status[ln];
+      if (st == 0 && L.nogen[ln]) st = 3;
+      if (P.out_status) P.out_status[s] = st;
+      if (P.out_iters) {
+        P.out_iters[(size_t)s * 3 + 0] = L.outer[ln];
+        P.out_iters[(size_t)s * 3 + 1] = L.inP[ln];
+        P.out_iters[(size_t)s * 3 + 2] = L.inQ[ln];
+      }
+      if (P.out_maxload) P.out_maxload[s] = j ? ml.b : ml.a;
+      L.done[ln] = 0;
+      L.scen[ln] = -1;
+    }
+  }
+  __syncthreads();
+}
+
+// One persistent CTA = one slot of T scenario lanes.  Lanes draw scenarios
+// from a device-side queue (in the order P.order gives); a lane whose
+// scenario has converged, failed or diverged is retired at the next outer
+// iteration and immediately refilled, so converged scenarios never hold a
+// lane (the slot's lanes are compacted onto live work) and the kernel ends
+// when the queue is drained and every lane has retired.
 template <int T, typename VT>
 __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS) fdpf_tiles_kernel(FdpfParams P, DevMatT<VT> MP,
                                                               DevMatT<VT> MQ) {
   __shared__ LaneState<T> L;
   const Geo<T> g;
   const int tid = threadIdx.x;
-  const DevGrid& G = P.G;
   VT* x = (VT*)P.wx + (size_t)blockIdx.x * P.vstride;
   VT* r = (VT*)P.wr + (size_t)blockIdx.x * P.vstride;
   VT* p = (VT*)P.wp + (size_t)blockIdx.x * P.vstride;
@@ -625,162 +908,111 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS) fdpf_tiles_kernel(F
   double *th = P.wth + so, *V = P.wV + so, *C = P.wc + so, *Sn = P.ws + so, *E = P.we + so,
          *F = P.wf + so;
 
+  // optional per-phase cycle counters (thread 0's view of the CTA)
+  const bool tim = P.phase_cycles != nullptr;
+  long long t_prev = 0;
+  if (tid == 0) {
+    for (int k = 0; k < 8; ++k) L.tphase[k] = 0;
+    t_prev = clock64();
+    L.drained = 0;
+  }
+  if (tid < T) {
+    L.scen[tid] = -1;
+    L.active[tid] = 0;
+    L.done[tid] = 0;
+    L.fresh[tid] = 0;
+  }
+  __syncthreads();
+#define GPCG_PHASE(k)                                  \
+  if (tim && tid == 0) {                               \
+    const long long t_ = clock64();                    \
+    L.tphase[k] += (unsigned long long)(t_ - t_prev);  \
+    t_prev = t_;                                       \
+  }
+
   for (;;) {
-    if (tid == 0) L.tile = atomicAdd(P.tile_counter, 1);
-    __syncthreads();
-    const int tile = L.tile;
-    if (tile >= P.n_tiles) break;
-    if (tid < T) {
-      const int ln = tid;
-      const int s = tile * T + ln;
-      const bool valid = s < P.S;
-      const int l = valid ? P.sc.outage[s] : -1;
-      L.scen[ln] = valid ? s : -1;
-      L.l[ln] = l;
-      L.fb[ln] = l >= 0 ? G.f[l] : -1;
-      L.tb[ln] = l >= 0 ? G.t[l] : -1;
-      L.lo[ln] = valid ? P.sc.isl_lo[s] : 0;
-      L.cnt[ln] = valid ? P.sc.isl_cnt[s] : 0;
-      L.coef[ln] = valid ? P.sc.coef[s] : 0.0;
-      L.nogen[ln] = valid ? P.sc.no_gen[s] : 0;
-      L.raP[ln] = l >= 0 ? MP.row_of_bus[G.f[l]] : -1;
-      L.rbP[ln] = l >= 0 ? MP.row_of_bus[G.t[l]] : -1;
-      L.raQ[ln] = l >= 0 ? MQ.row_of_bus[G.f[l]] : -1;
-      L.rbQ[ln] = l >= 0 ? MQ.row_of_bus[G.t[l]] : -1;
-      L.wP[ln] = l >= 0 ? MP.w[l] : 0.0;
-      L.wQ[ln] = l >= 0 ? MQ.w[l] : 0.0;
-      L.gl[ln] = l >= 0 ? G.g[l] : 0.0;
-      L.bl[ln] = l >= 0 ? G.by[l] + 0.5 * G.b_sh[l] : 0.0;
-      L.active[ln] = valid;
-      L.outer[ln] = 0;
-      L.inP[ln] = 0;
-      L.inQ[ln] = 0;
-      L.status[ln] = 0;
-      L.err[ln] = 0.0;
-    }
-    __syncthreads();
-    // warm start from the base case (Sec. III.B); islanded buses at zero
-    {
-      const int l0 = g.lane, l1 = g.lane + 1;
-      const int lo0 = L.lo[l0], cnt0 = L.cnt[l0], lo1 = L.lo[l1], cnt1 = L.cnt[l1];
-      for (int i = g.rs; i < G.n; i += Geo<T>::RPS) {
-        const size_t o = (size_t)i * T + g.lane;
-        double t0, v0, c0, s0;
-        if (P.flat_start) { t0 = 0.0; v0 = G.V_set[i]; c0 = 1.0; s0 = 0.0; }
-        else { t0 = P.th0[i]; v0 = P.V0[i]; c0 = P.c0[i]; s0 = P.s0[i]; }
-        const int pr = G.pre[i];
-        const bool i0 = in_island(pr, lo0, cnt0), i1 = in_island(pr, lo1, cnt1);
-        st2(th + o, Pair<double>{i0 ? 0.0 : t0, i1 ? 0.0 : t0});
-        st2(V + o, Pair<double>{i0 ? 0.0 : v0, i1 ? 0.0 : v0});
-        st2(C + o, Pair<double>{c0, c0});
-        st2(Sn + o, Pair<double>{s0, s0});
-        st2(E + o, Pair<double>{i0 ? 0.0 : v0 * c0, i1 ? 0.0 : v0 * c0});
-        st2(F + o, Pair<double>{i0 ? 0.0 : v0 * s0, i1 ? 0.0 : v0 * s0});
+    // retire finished lanes, then refill empty lanes from the queue
+    if (any_lane<T>(L, L.done)) retire_pass<T>(P, L, th, V, E, F);
+    GPCG_PHASE(7);
+    if (tid == 0 && !L.drained) {
+      int need = 0;
+      for (int s = 0; s < T; ++s) need += (L.scen[s] < 0);
+      if (need) {
+        const int base = atomicAdd(P.tile_counter, need);
+        int j = 0;
+        for (int s = 0; s < T; ++s) {
+          if (L.scen[s] >= 0) continue;
+          const int qi = base + j++;
+          if (qi < P.S) {
+            L.scen[s] = P.order ? P.order[qi] : qi;
+            L.fresh[s] = 1;
+          }
+        }
+        if (base + need >= P.S) L.drained = 1;
       }
     }
     __syncthreads();
-    for (;;) {
-      // P half-step: mismatch + convergence test
-      Pair<double> eP{0.0, 0.0}, eQ{0.0, 0.0};
-      mismatch_pass<T, VT, true>(P, MP, MQ, L, E, F, V, r, eP, eQ);
-      const Pair<double> mP = lane_reduce<T, true>(L, eP.a, eP.b);
-      const Pair<double> mQ = lane_reduce<T, true>(L, eQ.a, eQ.b);
-      if (g.rs == 0) {
-#pragma unroll
-        for (int j = 0; j < LP; ++j) {
-          const int ln = g.lane + j;
-          if (!L.active[ln]) continue;
-          const double a = j ? mP.b : mP.a, b = j ? mQ.b : mQ.a;
-          const double e2 = (a != a || b != b) ? INFINITY : fmax(a, b);
-          L.err[ln] = e2;
-          if (!(e2 <= DIVERGE_LIMIT)) { L.status[ln] = 2; L.active[ln] = 0; }
-          else if (e2 <= P.tol) { L.status[ln] = 0; L.active[ln] = 0; }
-          else if (L.outer[ln] >= P.max_outer) { L.status[ln] = 1; L.active[ln] = 0; }
-        }
-      }
-      if (!any_lane<T>(L, L.active)) break;
-      pcg_solve<T, VT>(P, MP, L, x, r, p, q, z, L.raP, L.rbP, L.wP, L.inP);
-      update_pass<T, VT, true>(MP, L, x, th, V, C, Sn, E, F);
-      __syncthreads();
-      // Q half-step
-      Pair<double> d0{0.0, 0.0}, d1{0.0, 0.0};
-      mismatch_pass<T, VT, false>(P, MP, MQ, L, E, F, V, r, d0, d1);
-      __syncthreads();
-      pcg_solve<T, VT>(P, MQ, L, x, r, p, q, z, L.raQ, L.rbQ, L.wQ, L.inQ);
-      update_pass<T, VT, false>(MQ, L, x, th, V, C, Sn, E, F);
-      if (g.rs == 0) {
-        if (L.active[g.lane]) L.outer[g.lane] += 1;
-        if (L.active[g.lane + 1]) L.outer[g.lane + 1] += 1;
-      }
-      __syncthreads();
+    if (tid < T && L.fresh[tid]) setup_lane<T, VT>(P, MP, MQ, L, tid);
+    __syncthreads();
+    init_pass<T>(P, L, th, V, C, Sn, E, F);
+    __syncthreads();
+    if (tid < T) L.fresh[tid] = 0;
+    GPCG_PHASE(0);
+    if (!any_lane<T>(L, L.active)) {
+      if (L.drained) break;
+      continue;
     }
-    // outputs: state, branch flows, loading (Sec. I: overload screening)
-    const int s0 = L.scen[g.lane], s1 = L.scen[g.lane + 1];
-    if (P.out_theta || P.out_vm) {
-      for (int i = g.rs; i < G.n; i += Geo<T>::RPS) {
-        const size_t o = (size_t)i * T + g.lane;
-        const Pair<double> t = ld2(th + o), v = ld2(V + o);
-        if (P.out_theta) {
-          if (s0 >= 0) P.out_theta[(size_t)s0 * G.n + i] = t.a;
-          if (s1 >= 0) P.out_theta[(size_t)s1 * G.n + i] = t.b;
-        }
-        if (P.out_vm) {
-          if (s0 >= 0) P.out_vm[(size_t)s0 * G.n + i] = v.a;
-          if (s1 >= 0) P.out_vm[(size_t)s1 * G.n + i] = v.b;
-        }
-      }
-    }
-    double ml0 = 0.0, ml1 = 0.0;
-    {
-      const int l0 = g.lane, l1 = g.lane + 1;
-      const int br0 = L.l[l0], br1 = L.l[l1];
-      const int lo0 = L.lo[l0], cnt0 = L.cnt[l0], lo1 = L.lo[l1], cnt1 = L.cnt[l1];
-      for (int k = g.rs; k < G.m; k += Geo<T>::RPS) {
-        const int a = __ldg(G.f + k), b = __ldg(G.t + k);
-        const int pa = __ldg(G.pre + a), pb = __ldg(G.pre + b);
-        const bool off0 = (k == br0) || in_island(pa, lo0, cnt0) || in_island(pb, lo0, cnt0);
-        const bool off1 = (k == br1) || in_island(pa, lo1, cnt1) || in_island(pb, lo1, cnt1);
-        const Pair<double> ea = ld2(E + (size_t)a * T + g.lane), fa = ld2(F + (size_t)a * T + g.lane);
-        const Pair<double> eb = ld2(E + (size_t)b * T + g.lane), fb = ld2(F + (size_t)b * T + g.lane);
-        const double gk = __ldg(G.g + k), bk = __ldg(G.by + k), rk = __ldg(G.rating + k);
-        double Pab0 = 0.0, Pba0 = 0.0, Pab1 = 0.0, Pba1 = 0.0;
-        if (!off0) {
-          const double cr = ea.a * eb.a + fa.a * fb.a, sr = fa.a * eb.a - ea.a * fb.a;
-          Pab0 = gk * (ea.a * ea.a + fa.a * fa.a) - gk * cr - bk * sr;
-          Pba0 = gk * (eb.a * eb.a + fb.a * fb.a) - gk * cr + bk * sr;
-        }
-        if (!off1) {
-          const double cr = ea.b * eb.b + fa.b * fb.b, sr = fa.b * eb.b - ea.b * fb.b;
-          Pab1 = gk * (ea.b * ea.b + fa.b * fa.b) - gk * cr - bk * sr;
-          Pba1 = gk * (eb.b * eb.b + fb.b * fb.b) - gk * cr + bk * sr;
-        }
-        upd_max(ml0, fmax(fabs(Pab0), fabs(Pba0)) / rk);
-        upd_max(ml1, fmax(fabs(Pab1), fabs(Pba1)) / rk);
-        if (P.out_flow) {
-          if (s0 >= 0) P.out_flow[(size_t)s0 * G.m + k] = Pab0;
-          if (s1 >= 0) P.out_flow[(size_t)s1 * G.m + k] = Pab1;
-        }
-      }
-    }
-    const Pair<double> ml = lane_reduce<T, true>(L, ml0, ml1);
+    // P half-step: mismatch + convergence test
+    Pair<double> eP{0.0, 0.0}, eQ{0.0, 0.0};
+    mismatch_pass<T, VT, true>(P, MP, MQ, L, E, F, V, r, eP, eQ);
+    const Pair<double> mP = lane_reduce<T, true>(L, eP.a, eP.b);
+    const Pair<double> mQ = lane_reduce<T, true>(L, eQ.a, eQ.b);
     if (g.rs == 0) {
 #pragma unroll
       for (int j = 0; j < LP; ++j) {
-        const int ln = g.lane + j, s = L.scen[ln];
-        if (s < 0) continue;
-        int st = L.status[ln];
-        if (st == 0 && L.nogen[ln]) st = 3;
-        if (P.out_status) P.out_status[s] = st;
-        if (P.out_iters) {
-          P.out_iters[(size_t)s * 3 + 0] = L.outer[ln];
-          P.out_iters[(size_t)s * 3 + 1] = L.inP[ln];
-          P.out_iters[(size_t)s * 3 + 2] = L.inQ[ln];
+        const int ln = g.lane + j;
+        if (!L.active[ln]) continue;
+        const double a = j ? mP.b : mP.a, b = j ? mQ.b : mQ.a;
+        const double e2 = (a != a || b != b) ? INFINITY : fmax(a, b);
+        L.err[ln] = e2;
+        int st = -1;
+        if (!(e2 <= DIVERGE_LIMIT) || e2 > DIVERGE_GROWTH * L.best[ln]) st = 2;
+        else if (e2 <= P.tol) st = 0;
+        else if (L.outer[ln] >= P.max_outer) st = 1;
+        L.best[ln] = fmin(L.best[ln], e2);
+        if (st >= 0) {
+          L.status[ln] = st;
+          L.active[ln] = 0;
+          L.done[ln] = 1;
         }
-        if (P.out_maxload) P.out_maxload[s] = j ? ml.b : ml.a;
       }
     }
+    const bool more = any_lane<T>(L, L.active);
+    GPCG_PHASE(1);
+    if (!more) continue;
+    pcg_solve<T, VT>(P, MP, L, x, r, p, q, z, L.raP, L.rbP, L.wP, L.inP);
+    GPCG_PHASE(2);
+    update_pass<T, VT, true>(MP, L, x, th, V, C, Sn, E, F);
     __syncthreads();
+    GPCG_PHASE(3);
+    // Q half-step
+    Pair<double> d0{0.0, 0.0}, d1{0.0, 0.0};
+    mismatch_pass<T, VT, false>(P, MP, MQ, L, E, F, V, r, d0, d1);
+    __syncthreads();
+    GPCG_PHASE(4);
+    pcg_solve<T, VT>(P, MQ, L, x, r, p, q, z, L.raQ, L.rbQ, L.wQ, L.inQ);
+    GPCG_PHASE(5);
+    update_pass<T, VT, false>(MQ, L, x, th, V, C, Sn, E, F);
+    if (g.rs == 0) {
+      if (L.active[g.lane]) L.outer[g.lane] += 1;
+      if (L.active[g.lane + 1]) L.outer[g.lane + 1] += 1;
+    }
+    __syncthreads();
+    GPCG_PHASE(6);
   }
+  if (tim && tid == 0)
+    for (int k = 0; k < 8; ++k) atomicAdd(P.phase_cycles + k, L.tphase[k]);
+#undef GPCG_PHASE
 }
 
 // Batched operator application for verification (gpcg_apply): X and Y are
@@ -859,6 +1091,7 @@ cudaError_t launch_fdpf(cudaStream_t st, int T, int grid, const FdpfParams& P,
                         const DevMatT<VT>& MP, const DevMatT<VT>& MQ) {
   switch (T) {
     case 2: return launch_fdpf_t<2, VT>(st, grid, P, MP, MQ);
+    case 4: return launch_fdpf_t<4, VT>(st, grid, P, MP, MQ);
     case 8: return launch_fdpf_t<8, VT>(st, grid, P, MP, MQ);
     case 16: return launch_fdpf_t<16, VT>(st, grid, P, MP, MQ);
     case 32: return launch_fdpf_t<32, VT>(st, grid, P, MP, MQ);
@@ -872,6 +1105,7 @@ int fdpf_max_blocks_per_sm(int T) {
   cudaError_t ce = cudaErrorInvalidValue;
   switch (T) {
     case 2: ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fdpf_tiles_kernel<2, VT>, NTHREADS, 0); break;
+    case 4: ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fdpf_tiles_kernel<4, VT>, NTHREADS, 0); break;
     case 8: ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fdpf_tiles_kernel<8, VT>, NTHREADS, 0); break;
     case 16: ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fdpf_tiles_kernel<16, VT>, NTHREADS, 0); break;
     case 32: ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fdpf_tiles_kernel<32, VT>, NTHREADS, 0); break;

@@ -4,8 +4,12 @@
 
 namespace gpcg {
 
-constexpr int NTHREADS = 256;
-constexpr double DIVERGE_LIMIT = 1.0e4;
+#ifndef FDPF_NTHREADS
+#define FDPF_NTHREADS 256
+#endif
+constexpr int NTHREADS = FDPF_NTHREADS;  // threads per CTA of the persistent kernel
+constexpr double DIVERGE_LIMIT = 1.0e4;   // p.u.: a larger mismatch is divergence
+constexpr double DIVERGE_GROWTH = 10.0;   // as is growth to this multiple of the best
 enum { PREC_IC0 = 0, PREC_JACOBI = 1, PREC_EXACT = 2 };
 
 struct FdpfParams {
@@ -17,13 +21,17 @@ struct FdpfParams {
   int flat_start = 0;
   double tol = 1e-4, inner_rtol = 1e-5;
   int max_outer = 50, max_inner = 500, precond = PREC_EXACT;
-  int32_t* tile_counter = nullptr;
+  int32_t* tile_counter = nullptr;     // scenario queue head
+  const int32_t* order = nullptr;      // scenarios in processing order (null: 0..S-1)
   void *wx = nullptr, *wr = nullptr, *wp = nullptr, *wq = nullptr, *wz = nullptr;
   size_t vstride = 0;  // elements per slot of one vector
   double *wth = nullptr, *wV = nullptr, *wc = nullptr, *ws = nullptr, *we = nullptr, *wf = nullptr;
   size_t sstride = 0;  // elements per slot of one state array
   double *out_theta = nullptr, *out_vm = nullptr, *out_flow = nullptr, *out_maxload = nullptr;
   int32_t *out_iters = nullptr, *out_status = nullptr;
+  unsigned long long* phase_cycles = nullptr;  // [8] per-phase SM cycles, or null
+  const int32_t* mis_order = nullptr;   // non-slack buses sorted by degree
+  const int32_t* misq_order = nullptr;  // B'' rows sorted by their bus's degree
 };
 
 template <typename VT>
