@@ -223,6 +223,43 @@ GPCG_API gpcg_status gpcg_export_matrix(const gpcg_ctx *ctx, int32_t which,
  * Returns NOT_READY when no screen has run. */
 GPCG_API gpcg_status gpcg_last_timings(gpcg_ctx *ctx, float *ms /*[2]*/);
 
+/* Size of the device array gpcg_n1_screen_noalloc works in (64 MiB). */
+#define GPCG_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* The N-1 screen of gpcg_n1_screen with device memory (mem = 1), for
+ * callers that must not allocate GPU memory while they run: a control loop
+ * or service with a fixed memory budget, a process whose GPU memory is
+ * already held by another allocator, or code that cannot afford the device
+ * synchronisation that cudaMalloc and cudaFree may cause.  The paper has no
+ * counterpart; this is a deployment variant of the same computation.
+ *
+ * It allocates nothing: all scratch (island data, the solve's per-tile
+ * vectors and state, the scenario queue) comes from one static device array
+ * of GPCG_NOALLOC_SCRATCH_BYTES that every GPU which loads the library holds
+ * until the process exits.  The first call on a device looks the array up
+ * for that device (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  The caller provides the context (built earlier by
+ * gpcg_create and gpcg_base_solve, which do allocate) and every input and
+ * output, all in device memory; outputs as in gpcg_n1_screen.  The outage
+ * list is checked through a fixed host buffer, which synchronises `stream`;
+ * the rest is enqueued on `stream`.
+ *
+ * Every call shares the one array, which keeps the previous call's contents
+ * (the call resets what must start at zero): calls that overlap on the GPU
+ * -- from two streams, threads or contexts of the same device -- race and
+ * give wrong results.  The solve runs as many scenario tiles at once as fit
+ * in the array, so large grids run with fewer tiles than gpcg_n1_screen.
+ * Errors: INVALID_ARG when the scenarios and one tile of the grid do not
+ * fit in the array (the message gives the bytes needed), when an outage is
+ * not a branch index, or when the context's precision is
+ * GPCG_PLAIN_FP64 (only the batched solve is offered here); NOT_READY
+ * before a successful gpcg_base_solve; CUDA. */
+GPCG_API gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx *ctx, const int32_t *outages,
+                                            int32_t n_out, void *stream, double *theta,
+                                            double *vm, double *flow, int32_t *island_label,
+                                            int32_t *iters, int32_t *status,
+                                            double *max_loading);
+
 /* Message of the last error on the calling thread ("" if none). */
 GPCG_API const char *gpcg_last_error(void);
 

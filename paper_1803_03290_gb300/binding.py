@@ -53,7 +53,8 @@ class Info(C.Structure):
 
 EXPORTS = ("gpcg_default_options", "gpcg_create", "gpcg_destroy", "gpcg_set_options",
            "gpcg_get_info", "gpcg_base_solve", "gpcg_n1_screen", "gpcg_apply",
-           "gpcg_export_matrix", "gpcg_last_timings", "gpcg_last_error")
+           "gpcg_export_matrix", "gpcg_last_timings", "gpcg_n1_screen_noalloc",
+           "gpcg_last_error")
 
 _lib = None
 
@@ -85,6 +86,7 @@ def load(build_if_missing: bool = True):
     lib.gpcg_apply.argtypes = [vp, i32, i32, vp, i32, i32, vp, vp]
     lib.gpcg_export_matrix.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gpcg_last_timings.argtypes = [vp, vp]
+    lib.gpcg_n1_screen_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gpcg_last_error.argtypes = []
     lib.gpcg_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -219,6 +221,17 @@ class GPCG:
         ms = np.zeros(2, np.float32)
         _check(self._lib, self._lib.gpcg_last_timings(self._h, _ptr(ms)))
         return float(ms[0]), float(ms[1])
+
+    def n1_screen_noalloc_device(self, outages, out: dict, stream=None):
+        """gpcg_n1_screen_noalloc: like n1_screen_device, but the library
+        takes all scratch from its fixed device array instead of allocating."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        g = lambda k: _ptr(out.get(k))
+        _check(self._lib, self._lib.gpcg_n1_screen_noalloc(
+            self._h, _ptr(outages), int(outages.shape[0]), C.c_void_p(s.cuda_stream),
+            g("theta"), g("V"), g("flow"), g("label"), g("iters"), g("status"),
+            g("max_loading")))
 
     def apply(self, which, op, outages, X, precision=BATCHED_FP64):
         out = np.ascontiguousarray(outages, dtype=np.int32)

@@ -14,6 +14,7 @@
 #include "../../include/gpcg.h"
 #include "analysis.h"
 #include "common.cuh"
+#include "ctx_view.h"
 #include "fdpf.h"
 
 namespace gpcg {
@@ -959,3 +960,36 @@ extern "C" gpcg_status gpcg_last_timings(gpcg_ctx* c, float* ms) {
 }
 
 extern "C" const char* gpcg_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------ internal view
+// Read-only view of a context for other translation units of the library.
+namespace gpcg {
+bool ctx_view(const gpcg_ctx* c, CtxView* v) {
+  if (!c || !v) return false;
+  v->G = c->G;
+  v->MPf = c->MP.view<float>();
+  v->MQf = c->MQ.view<float>();
+  v->MPd = c->MP.view<double>();
+  v->MQd = c->MQ.view<double>();
+  v->th0 = c->th0;
+  v->V0 = c->V0;
+  v->c0 = c->c0;
+  v->s0 = c->s0;
+  v->mis_order = c->mis_order;
+  v->misq_order = c->misq_order;
+  v->opt = c->opt;
+  v->num_sms = c->num_sms;
+  v->n = c->n;
+  v->m = c->m;
+  v->slack = c->slack;
+  v->rows = std::max(c->MP.plan.n, c->MQ.plan.n);
+  v->tile = c->tile;
+  v->base_ok = c->base_ok;
+  return true;
+}
+}  // namespace gpcg
+
+namespace gpcg {
+// Record the calling thread's error message (read by gpcg_last_error).
+void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+}  // namespace gpcg

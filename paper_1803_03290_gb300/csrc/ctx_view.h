@@ -1,0 +1,22 @@
+// Read-only view of a gpcg context for translation units other than the
+// one that defines the context (abi.cu).
+#pragma once
+#include "../../include/gpcg.h"
+#include "common.cuh"
+
+namespace gpcg {
+
+struct CtxView {
+  DevGrid G;
+  DevMatT<float> MPf, MQf;
+  DevMatT<double> MPd, MQd;
+  const double *th0 = nullptr, *V0 = nullptr, *c0 = nullptr, *s0 = nullptr;
+  const int32_t *mis_order = nullptr, *misq_order = nullptr;
+  gpcg_options opt{};
+  int num_sms = 0, n = 0, m = 0, slack = -1, rows = 0, tile = 0;
+  bool base_ok = false;
+};
+
+bool ctx_view(const gpcg_ctx* c, CtxView* v);
+
+}  // namespace gpcg
