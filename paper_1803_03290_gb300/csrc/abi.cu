@@ -92,7 +92,7 @@ Ell<float> EllDev::view<float>() const { return Ell<float>{col, val32, optr, oco
 
 struct MatDev {
   MatrixPlan plan;
-  int32_t *bus_of_row = nullptr, *row_of_bus = nullptr, *pre_of_row = nullptr;
+  int32_t *bus_of_row = nullptr, *row_of_bus = nullptr, *pre_of_row = nullptr, *visit = nullptr;
   int32_t *a_ptr = nullptr, *a_idx = nullptr, *a_diag = nullptr;
   int32_t *l_ptr = nullptr, *l_idx = nullptr, *l_diag = nullptr;
   int32_t *lev_ptr = nullptr, *blev_ptr = nullptr, *blev_rows = nullptr;
@@ -109,6 +109,7 @@ DevMatT<double> MatDev::view<double>() const {
   DevMatT<double> M;
   M.n = plan.n;
   M.bus_of_row = bus_of_row; M.row_of_bus = row_of_bus; M.pre_of_row = pre_of_row;
+  M.visit = visit;
   M.A = A.view<double>(); M.L = L.view<double>(); M.U = U.view<double>();
   M.inv_diag = inv_diag;
   M.diag = diag;
@@ -123,6 +124,7 @@ DevMatT<float> MatDev::view<float>() const {
   DevMatT<float> M;
   M.n = plan.n;
   M.bus_of_row = bus_of_row; M.row_of_bus = row_of_bus; M.pre_of_row = pre_of_row;
+  M.visit = visit;
   M.A = A.view<float>(); M.L = L.view<float>(); M.U = U.view<float>();
   M.inv_diag = inv_diag32;
   M.diag = diag32;
@@ -136,8 +138,13 @@ DevMatT<float> MatDev::view<float>() const {
 struct gpcg_ctx {
   int device = 0, num_sms = 0;
   gpcg_options opt{};
-  int n = 0, m = 0, slack = -1;
-  std::vector<int8_t> bus_type;
+  int n = 0, m = 0, slack = -1, slack_user = -1;  // slack: internal numbering
+  std::vector<int8_t> bus_type;                    // internal numbering
+  std::vector<int32_t> user_of, intl;              // internal -> user, user -> internal
+  // caller-numbered copies for the islanding kernel (labels are user indices)
+  int32_t *u_f = nullptr, *u_t = nullptr, *u_pre = nullptr;
+  int8_t* u_bus_type = nullptr;
+  double *u_P_sched = nullptr, *u_P_gen = nullptr;
   std::vector<int32_t> f, t;
   BusGraph bg;
   std::vector<int32_t> pre, sub;
@@ -219,8 +226,8 @@ static gpcg_status check_options(const gpcg_options& o) {
     return fail(GPCG_ERR_INVALID_ARG, "precision must be 0, 1 or 2");
   if (o.precond < 0 || o.precond > 2)
     return fail(GPCG_ERR_INVALID_ARG, "precond must be 0, 1 or 2");
-  if (!(o.tile == 0 || o.tile == 4 || o.tile == 8 || o.tile == 16 || o.tile == 32))
-    return fail(GPCG_ERR_INVALID_ARG, "tile must be 0, 4, 8, 16 or 32");
+  if (!(o.tile == 0 || o.tile == 2 || o.tile == 4 || o.tile == 8 || o.tile == 16 || o.tile == 32))
+    return fail(GPCG_ERR_INVALID_ARG, "tile must be 0, 2, 4, 8, 16 or 32");
   if (o.ctas_per_sm < 0 || o.ctas_per_sm > 64)
     return fail(GPCG_ERR_INVALID_ARG, "ctas_per_sm must be in [0, 64]");
   return GPCG_OK;
@@ -290,6 +297,13 @@ static gpcg_status build_matrix(gpcg_ctx* c, MatDev& M, const std::vector<uint8_
   CUDA_TRY(upload(own, &M.bus_of_row, P.bus_of_row.data(), P.n));
   CUDA_TRY(upload(own, &M.row_of_bus, P.row_of_bus.data(), c->n));
   CUDA_TRY(upload(own, &M.pre_of_row, pre_of_row.data(), P.n));
+  {
+    std::vector<int32_t> visit(P.n);
+    for (int i = 0; i < P.n; ++i) visit[i] = i;
+    std::sort(visit.begin(), visit.end(),
+              [&](int a, int b) { return P.bus_of_row[a] < P.bus_of_row[b]; });
+    CUDA_TRY(upload(own, &M.visit, visit.data(), P.n));
+  }
   CUDA_TRY(upload(own, &M.a_ptr, P.A.ptr.data(), P.A.ptr.size()));
   CUDA_TRY(upload(own, &M.a_idx, P.A.idx.data(), P.A.idx.size()));
   CUDA_TRY(upload(own, &M.a_diag, P.a_diag.data(), P.n));
@@ -363,9 +377,13 @@ static gpcg_status build_matrices(gpcg_ctx* c) {
     const MatrixPlan& Q = c->MQ.plan;
     std::vector<int32_t> order(Q.n);
     for (int k = 0; k < Q.n; ++k) order[k] = k;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-      return c->deg[Q.bus_of_row[a]] > c->deg[Q.bus_of_row[b]];
-    });
+    std::sort(order.begin(), order.end(),
+              [&](int a, int b) { return Q.bus_of_row[a] < Q.bus_of_row[b]; });
+    for (size_t w0 = 0; w0 < order.size(); w0 += 128)
+      std::stable_sort(order.begin() + w0, order.begin() + std::min(order.size(), w0 + 128),
+                       [&](int a, int b) {
+                         return c->deg[Q.bus_of_row[a]] > c->deg[Q.bus_of_row[b]];
+                       });
     CUDA_TRY(upload(c->mat_owned, &c->misq_order, order.data(), order.size()));
   }
   c->planned_precond = c->opt.precond;
@@ -425,17 +443,43 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
   c->opt = o;
   c->n = n;
   c->m = m;
-  c->slack = slack;
-  c->bus_type.assign(g->bus_type, g->bus_type + n);
-  c->f.assign(g->from, g->from + m);
-  c->t.assign(g->to, g->to + m);
+  c->slack_user = slack;
+  // internal bus numbering: reverse Cuthill-McKee of the bus graph, so buses
+  // adjacent in the grid sit close together in every per-bus array
+  {
+    BusGraph gu = build_bus_graph(n, m, g->from, g->to);
+    c->user_of = rcm_order(n, gu);
+  }
+  c->intl.assign(n, 0);
+  for (int k = 0; k < n; ++k) c->intl[c->user_of[k]] = k;
+  const std::vector<int32_t>& U = c->user_of;
+  const std::vector<int32_t>& I = c->intl;
+  std::vector<int8_t> bt_i(n);
+  std::vector<double> P_i(n), Q_i(n), Pg_i(n), V_i(n);
+  for (int k = 0; k < n; ++k) {
+    bt_i[k] = g->bus_type[U[k]];
+    P_i[k] = g->P_sched[U[k]];
+    Q_i[k] = g->Q_sched[U[k]];
+    Pg_i[k] = g->P_gen[U[k]];
+    V_i[k] = g->V_set[U[k]];
+  }
+  std::vector<int32_t> f_i(m), t_i(m);
+  for (int e = 0; e < m; ++e) {
+    f_i[e] = I[g->from[e]];
+    t_i[e] = I[g->to[e]];
+  }
+  c->slack = I[slack];
+  c->bus_type = bt_i;
+  c->f = f_i;
+  c->t = t_i;
   cudaGetDevice(&c->device);
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
-  c->bg = build_bus_graph(n, m, g->from, g->to);
-  if (!dfs_numbering(n, c->bg, slack, c->pre, c->sub, c->bridge, m)) {
+  c->bg = build_bus_graph(n, m, f_i.data(), t_i.data());
+  if (!dfs_numbering(n, c->bg, c->slack, c->pre, c->sub, c->bridge, m)) {
     destroy(c);
     return fail(GPCG_ERR_BASE_ISLANDED, "the intact grid is not connected");
   }
+  slack = c->slack;
   for (int e = 0; e < m; ++e) c->n_bridges += c->bridge[e];
   for (int b = 0; b < n; ++b)
     if (g->bus_type[b] == GPCG_PV && g->P_gen[b] > 0) c->pv_gen_total += g->P_gen[b];
@@ -457,13 +501,24 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
   if ((ce = upload(own, &dst, src, cnt)) != cudaSuccess) return fail_cuda(ce, "upload " #dst)
 #define AL(dst, cnt)                                        \
   if ((ce = dalloc(own, &dst, cnt)) != cudaSuccess) return fail_cuda(ce, "alloc " #dst)
-  UP(G.bus_type, g->bus_type, n);
-  UP(G.P_sched, g->P_sched, n);
-  UP(G.Q_sched, g->Q_sched, n);
-  UP(G.P_gen, g->P_gen, n);
-  UP(G.V_set, g->V_set, n);
-  UP(G.f, g->from, m);
-  UP(G.t, g->to, m);
+  UP(G.bus_type, bt_i.data(), n);
+  UP(G.P_sched, P_i.data(), n);
+  UP(G.Q_sched, Q_i.data(), n);
+  UP(G.P_gen, Pg_i.data(), n);
+  UP(G.V_set, V_i.data(), n);
+  UP(G.f, f_i.data(), m);
+  UP(G.t, t_i.data(), m);
+  UP(G.user_of_bus, U.data(), n);
+  {
+    std::vector<int32_t> pre_u(n);
+    for (int b = 0; b < n; ++b) pre_u[b] = c->pre[I[b]];
+    UP(c->u_pre, pre_u.data(), n);
+  }
+  UP(c->u_f, g->from, m);
+  UP(c->u_t, g->to, m);
+  UP(c->u_bus_type, g->bus_type, n);
+  UP(c->u_P_sched, g->P_sched, n);
+  UP(c->u_P_gen, g->P_gen, n);
   UP(G.r, g->r, m);
   UP(G.x, g->x, m);
   UP(G.b_sh, g->b_sh, m);
@@ -499,7 +554,11 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
     for (int b = 0; b < n; ++b) deg[b] = std::min(c->bg.adj.ptr[b + 1] - c->bg.adj.ptr[b], KG);
     for (int b = 0; b < n; ++b)
       if (b != slack) order.push_back(b);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return deg[a] > deg[b]; });
+    // bus order (neighbours close), degree-sorted inside windows of 128 rows
+    // so the threads of a warp mostly run neighbour loops of equal length
+    for (size_t w0 = 0; w0 < order.size(); w0 += 128)
+      std::stable_sort(order.begin() + w0, order.begin() + std::min(order.size(), w0 + 128),
+                       [&](int a, int b) { return deg[a] > deg[b]; });
     UP(G.adj_deg, deg.data(), n);
     UP(c->mis_order, order.data(), order.size());
     c->deg = deg;
@@ -567,7 +626,7 @@ extern "C" gpcg_status gpcg_get_info(const gpcg_ctx* c, gpcg_info* info) {
   if (!c || !info) return fail(GPCG_ERR_INVALID_ARG, "gpcg_get_info: NULL argument");
   info->n_bus = c->n;
   info->n_branch = c->m;
-  info->slack = c->slack;
+  info->slack = c->slack_user;
   info->n_p = c->MP.plan.n;
   info->n_q = c->MQ.plan.n;
   info->nnz_p = c->MP.plan.A.nnz();
@@ -718,8 +777,17 @@ extern "C" gpcg_status gpcg_base_solve(gpcg_ctx* c, double* theta, double* vm, d
   CUDA_TRY(cudaMemcpy(c->base_flow.data(), c->flow0, (size_t)c->m * 8, cudaMemcpyDeviceToHost));
   for (auto& v : c->base_flow) v = std::fabs(v);
   c->base_ok = true;
-  if (theta) CUDA_TRY(cudaMemcpy(theta, c->th0, (size_t)c->n * 8, cudaMemcpyDeviceToHost));
-  if (vm) CUDA_TRY(cudaMemcpy(vm, c->V0, (size_t)c->n * 8, cudaMemcpyDeviceToHost));
+  if (theta || vm) {
+    std::vector<double> h(c->n);
+    if (theta) {
+      CUDA_TRY(cudaMemcpy(h.data(), c->th0, (size_t)c->n * 8, cudaMemcpyDeviceToHost));
+      for (int k = 0; k < c->n; ++k) theta[c->user_of[k]] = h[k];
+    }
+    if (vm) {
+      CUDA_TRY(cudaMemcpy(h.data(), c->V0, (size_t)c->n * 8, cudaMemcpyDeviceToHost));
+      for (int k = 0; k < c->n; ++k) vm[c->user_of[k]] = h[k];
+    }
+  }
   if (flow) CUDA_TRY(cudaMemcpy(flow, c->flow0, (size_t)c->m * 8, cudaMemcpyDeviceToHost));
   if (iters) { iters[0] = hit[0]; iters[1] = hit[1]; iters[2] = hit[2]; }
   g_err.clear();
@@ -800,8 +868,8 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
   CUDA_TRY(cudaMemsetAsync(c->d_err, 0, 4, st));
   CUDA_TRY(cudaEventRecord(c->ev[0], st));
   const int cc_grid = std::min<int>((int)S, c->num_sms * 4);
-  ce = launch_islands(st, cc_grid, c->n, c->m, c->slack, (int)S, c->d_outages, c->G.f, c->G.t,
-                      c->G.bus_type, c->G.P_sched, c->G.P_gen, c->G.pre,
+  ce = launch_islands(st, cc_grid, c->n, c->m, c->slack_user, (int)S, c->d_outages, c->u_f,
+                      c->u_t, c->u_bus_type, c->u_P_sched, c->u_P_gen, c->u_pre,
                       c->d_lo, c->d_cnt, c->d_coef, c->d_nogen, d_lab, c->d_err);
   if (ce != cudaSuccess) { cleanup(); return fail(GPCG_ERR_CUDA, "islands: %s", cudaGetErrorString(ce)); }
   CUDA_TRY(cudaEventRecord(c->ev[1], st));
@@ -814,6 +882,7 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
   P.c0 = c->c0;
   P.s0 = c->s0;
   P.out_theta = d_theta; P.out_vm = d_vm; P.out_flow = d_flow; P.out_maxload = d_ml;
+  P.out_bus_map = c->G.user_of_bus;
   P.out_iters = d_iters; P.out_status = d_stat;
   gpcg_status rs = GPCG_OK;
   if (c->opt.precision == GPCG_PLAIN_FP64) {
@@ -832,7 +901,7 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
       rs = run_fdpf<double>(c, st, Q, 2, 1);
     }
   } else {
-    const int T = c->opt.tile ? c->opt.tile : (c->tile ? c->tile : 4);
+    const int T = c->opt.tile ? c->opt.tile : (c->tile ? c->tile : 2);
     c->tile = T;
     const int n_tiles = (int)((S + T - 1) / T);
     const bool f32 = c->opt.precision == GPCG_BATCHED_FP32;
@@ -937,7 +1006,8 @@ extern "C" gpcg_status gpcg_export_matrix(const gpcg_ctx* c, int32_t which, int3
   if (which != 0 && which != 1) return fail(GPCG_ERR_INVALID_ARG, "which must be 0 or 1");
   const MatDev& M = which ? c->MQ : c->MP;
   const MatrixPlan& P = M.plan;
-  if (bus_of_row) std::memcpy(bus_of_row, P.bus_of_row.data(), (size_t)P.n * 4);
+  if (bus_of_row)
+    for (int i = 0; i < P.n; ++i) bus_of_row[i] = c->user_of[P.bus_of_row[i]];
   if (rowptr) std::memcpy(rowptr, P.A.ptr.data(), P.A.ptr.size() * 4);
   if (col) std::memcpy(col, P.A.idx.data(), P.A.idx.size() * 4);
   if (lrowptr) std::memcpy(lrowptr, P.L.ptr.data(), P.L.ptr.size() * 4);
@@ -983,6 +1053,13 @@ bool ctx_view(const gpcg_ctx* c, CtxView* v) {
   v->m = c->m;
   v->slack = c->slack;
   v->rows = std::max(c->MP.plan.n, c->MQ.plan.n);
+  v->slack_user = c->slack_user;
+  v->u_f = c->u_f;
+  v->u_t = c->u_t;
+  v->u_pre = c->u_pre;
+  v->u_bus_type = c->u_bus_type;
+  v->u_P_sched = c->u_P_sched;
+  v->u_P_gen = c->u_P_gen;
   v->tile = c->tile;
   v->base_ok = c->base_ok;
   return true;

@@ -137,9 +137,13 @@ MatrixPlan plan_matrix(int n_bus, const BusGraph& g, const std::vector<uint8_t>&
       if (j != i) m = std::max(m, lev[j]);
     lev[i] = m + 1;
   }
+  // final order: by level; within a level by vertex (= bus) index, so rows of
+  // a level that are close in the bus numbering are close in memory
   std::vector<int> byl(n);
   std::iota(byl.begin(), byl.end(), 0);
-  std::stable_sort(byl.begin(), byl.end(), [&](int a, int b) { return lev[a] < lev[b]; });
+  std::sort(byl.begin(), byl.end(), [&](int a, int b) {
+    return lev[a] != lev[b] ? lev[a] < lev[b] : order[a] < order[b];
+  });
   std::vector<int> fin(n);  // minimum-degree position -> final row
   for (int r = 0; r < n; ++r) fin[byl[r]] = r;
 
@@ -210,6 +214,39 @@ MatrixPlan plan_matrix(int n_bus, const BusGraph& g, const std::vector<uint8_t>&
   std::vector<int32_t> bf(P.blev_ptr.begin(), P.blev_ptr.end() - 1);
   for (int i = 0; i < n; ++i) P.blev_rows[bf[blev[i]]++] = i;
   return P;
+}
+
+std::vector<int32_t> rcm_order(int n, const BusGraph& g) {
+  std::vector<int32_t> deg(n), out;
+  for (int v = 0; v < n; ++v) deg[v] = g.adj.ptr[v + 1] - g.adj.ptr[v];
+  std::vector<char> seen(n, 0);
+  out.reserve(n);
+  auto bfs = [&](int s, std::vector<int32_t>& ord, std::vector<char>& mark) {
+    size_t head = ord.size();
+    ord.push_back(s);
+    mark[s] = 1;
+    std::vector<int32_t> nb;
+    while (head < ord.size()) {
+      const int u = ord[head++];
+      nb.clear();
+      for (int k = g.adj.ptr[u]; k < g.adj.ptr[u + 1]; ++k)
+        if (!mark[g.adj.idx[k]]) { mark[g.adj.idx[k]] = 1; nb.push_back(g.adj.idx[k]); }
+      std::sort(nb.begin(), nb.end(), [&](int a, int b) { return deg[a] != deg[b] ? deg[a] < deg[b] : a < b; });
+      ord.insert(ord.end(), nb.begin(), nb.end());
+    }
+  };
+  for (int s0 = 0; s0 < n; ++s0) {
+    if (seen[s0]) continue;
+    // start from a pseudo-peripheral vertex: the last vertex of a BFS from s0
+    std::vector<int32_t> tmp;
+    std::vector<char> mark(seen);
+    bfs(s0, tmp, mark);
+    const int start = tmp.back();
+    const size_t before = out.size();
+    bfs(start, out, seen);
+    std::reverse(out.begin() + before, out.end());
+  }
+  return out;
 }
 
 bool dfs_numbering(int n_bus, const BusGraph& g, int root, std::vector<int32_t>& pre,

@@ -50,6 +50,10 @@ BusGraph build_bus_graph(int n_bus, int n_branch, const int32_t* f, const int32_
 MatrixPlan plan_matrix(int n_bus, const BusGraph& g, const std::vector<uint8_t>& keep,
                        bool fill);
 
+// Reverse Cuthill-McKee order of the bus graph (new position -> bus): buses
+// adjacent in the grid get nearby positions.
+std::vector<int32_t> rcm_order(int n, const BusGraph& g);
+
 // Depth-first numbering from `root`: pre[b] (preorder) and size[b]
 // (subtree size).  Returns false when some bus is unreachable.  bridge[l]
 // is set for branches whose removal disconnects the graph.

@@ -13,7 +13,9 @@ constexpr int KL = 4;   // strictly lower part of the factor
 constexpr int KU = 4;   // strictly upper part (L^T)
 constexpr int KG = 6;   // bus adjacency of the mismatch
 
-// Grid arrays on the device (bus order and branch order of the caller).
+// Grid arrays on the device.  Buses use the library's internal numbering (a
+// bandwidth-reducing order of the bus graph); branches keep the caller's
+// order, their end buses in internal numbers.
 struct DevGrid {
   int n = 0, m = 0, slack = -1;
   int8_t* bus_type = nullptr;
@@ -24,6 +26,7 @@ struct DevGrid {
   int32_t *adj_ptr = nullptr, *adj_idx = nullptr, *adj_br = nullptr;  // CSR adjacency
   double *Gii = nullptr, *Bii = nullptr;     // bus admittance diagonal
   int32_t *pre = nullptr, *sub = nullptr;    // depth-first preorder, subtree size
+  int32_t* user_of_bus = nullptr;            // internal bus index -> caller's index
   // padded adjacency for the mismatch: neighbour, branch, -g, -b_y per slot
   int32_t *adj_nbr = nullptr, *adj_brl = nullptr, *adj_deg = nullptr;  // deg = used slots
   double *adj_g = nullptr, *adj_b = nullptr;
@@ -49,6 +52,7 @@ template <typename VT>
 struct DevMatT {
   int n = 0;
   const int32_t *bus_of_row = nullptr, *row_of_bus = nullptr, *pre_of_row = nullptr;
+  const int32_t* visit = nullptr;            // rows in bus order (SpMV, p update)
   Ell<VT> A, L, U;
   const VT* inv_diag = nullptr;              // 1 / L_ii
   const VT* diag = nullptr;                  // A_ii (Jacobi)

@@ -13,7 +13,10 @@ struct CtxView {
   const double *th0 = nullptr, *V0 = nullptr, *c0 = nullptr, *s0 = nullptr;
   const int32_t *mis_order = nullptr, *misq_order = nullptr;
   gpcg_options opt{};
-  int num_sms = 0, n = 0, m = 0, slack = -1, rows = 0, tile = 0;
+  int num_sms = 0, n = 0, m = 0, slack = -1, rows = 0, tile = 0, slack_user = -1;
+  const int32_t *u_f = nullptr, *u_t = nullptr, *u_pre = nullptr;  // caller numbering
+  const int8_t* u_bus_type = nullptr;
+  const double *u_P_sched = nullptr, *u_P_gen = nullptr;
   bool base_ok = false;
 };
 

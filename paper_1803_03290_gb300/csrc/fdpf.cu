@@ -31,13 +31,17 @@ constexpr int LP = 2;  // scenario lanes per thread
 #define FDPF_UNROLL 1
 #endif
 constexpr int UNR = FDPF_UNROLL;  // rows per thread in flight in the PCG passes
+#ifndef FDPF_MIS_GROUP
+#define FDPF_MIS_GROUP 3
+#endif
+constexpr int MIS_GROUP = FDPF_MIS_GROUP;  // neighbours loaded together in the mismatch
 // Large passes are kept out of line by default (separate register
 // allocation); -DGPCG_PASS_INLINE=__forceinline__ inlines them.
 #ifndef GPCG_PASS_INLINE
 #define GPCG_PASS_INLINE __noinline__
 #endif
 #ifndef FDPF_MIN_BLOCKS
-#define FDPF_MIN_BLOCKS 2  // resident CTAs per SM the register budget is cut for
+#define FDPF_MIN_BLOCKS 5  // resident CTAs per SM the register budget is cut for
 #endif
 
 // Inner iterations without progress after which a solve stops: the outer
@@ -172,25 +176,34 @@ __device__ __forceinline__ Pair<double> spmv_pass(const DevMatT<VT>& M, const VT
   // UNR rows per thread per step, and the column indices of the next step
   // loaded one step ahead: each step waits on one memory latency for
   // UNR rows' gathers
-  int cn[UNR][KA];
+  // rows are visited in bus order (M.visit), so a row's neighbours were
+  // visited just before it and their chunks of p are still in cache
+  int cn[UNR][KA], vn[UNR];
 #pragma unroll
   for (int u = 0; u < UNR; ++u)
-    if (g.rs + u * RPS < M.n) ld_cols<KA>(M.A.col + (size_t)(g.rs + u * RPS) * KA, cn[u]);
+    if (g.rs + u * RPS < M.n) {
+      vn[u] = __ldg(M.visit + g.rs + u * RPS);
+      ld_cols<KA>(M.A.col + (size_t)vn[u] * KA, cn[u]);
+    }
   for (int i0 = g.rs; i0 < M.n; i0 += STEP) {
-    int c[UNR][KA];
+    int c[UNR][KA], ii[UNR];
     VT v[UNR][KA];
     Pair<VT> pc[UNR][KA], pi[UNR];
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
+      ii[u] = vn[u];
 #pragma unroll
       for (int k = 0; k < KA; ++k) c[u][k] = cn[u][k];
       const int in = i0 + STEP + u * RPS;
-      if (in < M.n) ld_cols<KA>(M.A.col + (size_t)in * KA, cn[u]);
+      if (in < M.n) {
+        vn[u] = __ldg(M.visit + in);
+        ld_cols<KA>(M.A.col + (size_t)vn[u] * KA, cn[u]);
+      }
     }
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
-      const int i = i0 + u * RPS;
-      if (i < M.n) {
+      const int i = ii[u];
+      if (i0 + u * RPS < M.n) {
         ld_vals<KA>(M.A.val + (size_t)i * KA, v[u]);
 #pragma unroll
         for (int k = 0; k < KA; ++k) pc[u][k] = ld2(p + (size_t)c[u][k] * T + g.lane);
@@ -199,8 +212,8 @@ __device__ __forceinline__ Pair<double> spmv_pass(const DevMatT<VT>& M, const VT
     }
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
-      const int i = i0 + u * RPS;
-      if (i >= M.n) continue;
+      const int i = ii[u];
+      if (i0 + u * RPS >= M.n) continue;
       const int oth0 = (i == ra0) ? rb0 : ((i == rb0) ? ra0 : -2);
       const int oth1 = (i == ra1) ? rb1 : ((i == rb1) ? ra1 : -2);
       VT a0 = 0, a1 = 0;
@@ -428,12 +441,13 @@ __device__ __forceinline__ void pupdate_pass(const DevMatT<VT>& M, const VT* __r
   const Geo<T> g;
   constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
   for (int i0 = g.rs; i0 < M.n; i0 += STEP) {
-    int pr[UNR];
+    int pr[UNR], ii[UNR];
     Pair<VT> zi[UNR], pi[UNR];
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
-      const int i = i0 + u * RPS;
-      if (i < M.n) {
+      const int i = i0 + u * RPS < M.n ? __ldg(M.visit + i0 + u * RPS) : 0;
+      ii[u] = i;
+      if (i0 + u * RPS < M.n) {
         const size_t o = (size_t)i * T + g.lane;
         pr[u] = __ldg(M.pre_of_row + i);
         zi[u] = ld2(z + o);
@@ -442,8 +456,8 @@ __device__ __forceinline__ void pupdate_pass(const DevMatT<VT>& M, const VT* __r
     }
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
-      const int i = i0 + u * RPS;
-      if (i >= M.n) continue;
+      const int i = ii[u];
+      if (i0 + u * RPS >= M.n) continue;
       Pair<VT> pn{in_island(pr[u], lo0, cnt0) ? (VT)0 : zi[u].a,
                   in_island(pr[u], lo1, cnt1) ? (VT)0 : zi[u].b};
       if (!first) {
@@ -634,16 +648,6 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
         const int ln = g.lane + j;
         const size_t o = (size_t)i * T + ln;
         const int brl = j ? br1 : br0;
-        double ej[KG], fj[KG], gg[KG], bb[KG];
-        ld_vals<KG>(G.adj_g + (size_t)i * KG, gg);
-        ld_vals<KG>(G.adj_b + (size_t)i * KG, bb);
-#pragma unroll
-        for (int a = 0; a < KG; ++a) {
-          if (a < deg) {
-            ej[a] = E[(size_t)nb[a] * T + ln];
-            fj[a] = F[(size_t)nb[a] * T + ln];
-          }
-        }
         const double ei = E[o], fi = F[o], Vi = V[o];
         double Gd = Gii, Bd = Bii;
         if (i == (j ? fb1 : fb0) || i == (j ? tb1 : tb0)) {
@@ -651,12 +655,25 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
           Bd -= j ? bl1 : bl0;
         }
         double re = Gd * ei - Bd * fi, im = Gd * fi + Bd * ei;
+        // neighbours in groups of MIS_GROUP: bounds the live FP64 registers
 #pragma unroll
-        for (int a = 0; a < KG; ++a) {
-          if (a < deg && br[a] != brl) {
-            re -= gg[a] * ej[a] - bb[a] * fj[a];
-            im -= gg[a] * fj[a] + bb[a] * ej[a];
-          }
+        for (int a0 = 0; a0 < KG; a0 += MIS_GROUP) {
+          double ej[MIS_GROUP], fj[MIS_GROUP];
+#pragma unroll
+          for (int a = 0; a < MIS_GROUP; ++a)
+            if (a0 + a < deg) {
+              ej[a] = E[(size_t)nb[a0 + a] * T + ln];
+              fj[a] = F[(size_t)nb[a0 + a] * T + ln];
+            }
+#pragma unroll
+          for (int a = 0; a < MIS_GROUP; ++a)
+            if (a0 + a < deg && br[a0 + a] != brl) {
+              const double gv = __ldg(G.adj_g + (size_t)i * KG + a0 + a);
+              const double bv = __ldg(G.adj_b + (size_t)i * KG + a0 + a);
+              re -= gv * ej[a] - bv * fj[a];
+              im -= gv * fj[a] + bv * ej[a];
+            }
+          asm volatile("" ::: "memory");
         }
         for (int e = o0; e < o1; ++e) {
           const int jn = __ldg(G.adj_onbr + e), b_ = __ldg(G.adj_obr + e);
@@ -824,13 +841,14 @@ __device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& 
     for (int i = g.rs; i < G.n; i += Geo<T>::RPS) {
       const size_t o = (size_t)i * T + g.lane;
       const Pair<double> t = ld2(th + o), v = ld2(V + o);
+      const int iu = P.out_bus_map ? __ldg(P.out_bus_map + i) : i;
       if (P.out_theta) {
-        if (s0 >= 0) P.out_theta[(size_t)s0 * G.n + i] = t.a;
-        if (s1 >= 0) P.out_theta[(size_t)s1 * G.n + i] = t.b;
+        if (s0 >= 0) P.out_theta[(size_t)s0 * G.n + iu] = t.a;
+        if (s1 >= 0) P.out_theta[(size_t)s1 * G.n + iu] = t.b;
       }
       if (P.out_vm) {
-        if (s0 >= 0) P.out_vm[(size_t)s0 * G.n + i] = v.a;
-        if (s1 >= 0) P.out_vm[(size_t)s1 * G.n + i] = v.b;
+        if (s0 >= 0) P.out_vm[(size_t)s0 * G.n + iu] = v.a;
+        if (s1 >= 0) P.out_vm[(size_t)s1 * G.n + iu] = v.b;
       }
     }
   }

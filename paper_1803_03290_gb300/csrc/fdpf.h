@@ -28,6 +28,7 @@ struct FdpfParams {
   double *wth = nullptr, *wV = nullptr, *wc = nullptr, *ws = nullptr, *we = nullptr, *wf = nullptr;
   size_t sstride = 0;  // elements per slot of one state array
   double *out_theta = nullptr, *out_vm = nullptr, *out_flow = nullptr, *out_maxload = nullptr;
+  const int32_t* out_bus_map = nullptr;  // internal bus -> output column (null: identity)
   int32_t *out_iters = nullptr, *out_status = nullptr;
   unsigned long long* phase_cycles = nullptr;  // [8] per-phase SM cycles, or null
   const int32_t* mis_order = nullptr;   // non-slack buses sorted by degree

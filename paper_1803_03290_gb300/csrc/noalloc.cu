@@ -89,7 +89,7 @@ extern "C" gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx* ctx, const int32_t* outa
 
   // layout: [counter, error flag] [per-scenario island data] [solve slots]
   const size_t S = (size_t)n_out;
-  const int T = c.opt.tile ? c.opt.tile : (c.tile ? c.tile : 4);
+  const int T = c.opt.tile ? c.opt.tile : (c.tile ? c.tile : 2);
   const bool f32 = c.opt.precision == GPCG_BATCHED_FP32;
   const size_t vt = f32 ? 4 : 8;
   const size_t head = 256;
@@ -135,9 +135,9 @@ extern "C" gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx* ctx, const int32_t* outa
 
   cudaError_t ce = cudaMemsetAsync(base, 0, head, st);  // queue head and error flag start at 0
   if (ce != cudaSuccess) return err(GPCG_ERR_CUDA, "scratch reset: %s", cudaGetErrorString(ce));
-  ce = launch_islands(st, std::min<int>((int)S, c.num_sms * 4), c.n, c.m, c.slack, (int)S, outages,
-                      c.G.f, c.G.t, c.G.bus_type, c.G.P_sched, c.G.P_gen, c.G.pre, lo, cnt, coef,
-                      nogen, island_label, eflag);
+  ce = launch_islands(st, std::min<int>((int)S, c.num_sms * 4), c.n, c.m, c.slack_user, (int)S,
+                      outages, c.u_f, c.u_t, c.u_bus_type, c.u_P_sched, c.u_P_gen, c.u_pre, lo,
+                      cnt, coef, nogen, island_label, eflag);
   if (ce != cudaSuccess) return err(GPCG_ERR_CUDA, "islands: %s", cudaGetErrorString(ce));
 
   FdpfParams P;
@@ -153,6 +153,7 @@ extern "C" gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx* ctx, const int32_t* outa
   P.th0 = c.th0; P.V0 = c.V0; P.c0 = c.c0; P.s0 = c.s0;
   P.out_theta = theta; P.out_vm = vm; P.out_flow = flow; P.out_maxload = max_loading;
   P.out_iters = iters; P.out_status = status;
+  P.out_bus_map = c.G.user_of_bus;
   P.S = (int)S;
   P.n_tiles = n_tiles;
   P.tile_counter = counter;
