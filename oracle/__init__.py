@@ -23,15 +23,18 @@ What it computes, and where the paper defines it:
   that apply it.
 * ``screen``     -- the N-1 loop over all single-branch outages (Sec. IV.A),
   run across host processes.
+* ``adjoint``    -- loss and gradients of a smooth overload penalty summed
+  over N-1 scenarios of the P-theta (DC) model, by one adjoint solve per
+  scenario; pinned by finite differences.
 
 Parity status of each function is stated in its docstring; the one function
 the paper gives no formula for (the re-dispatch weights) says
 "parity unpinned".
 """
-from . import factor, islands, powerflow, redispatch, screen  # noqa: F401
+from . import adjoint, factor, islands, powerflow, redispatch, screen  # noqa: F401
 from .powerflow import (STATUS_DIVERGED, STATUS_ISLAND_NO_GEN, STATUS_MAXITER,
                         STATUS_OK)
 
-__all__ = ["factor", "islands", "powerflow", "redispatch", "screen",
+__all__ = ["adjoint", "factor", "islands", "powerflow", "redispatch", "screen",
            "STATUS_OK", "STATUS_MAXITER", "STATUS_DIVERGED",
            "STATUS_ISLAND_NO_GEN"]

@@ -399,3 +399,73 @@ def test_triangular_solves_invert():
     np.testing.assert_allclose(factor.backward(L, r), np.linalg.solve(M.T, r), atol=1e-12)
     z = factor.apply_preconditioner(L, r)
     np.testing.assert_allclose(M @ (M.T @ z), r, atol=1e-10)
+
+
+# -------------------------------------------------- adjoint (DC, eq. (4))
+def _adjoint_case():
+    g = config_grid("grid120")
+    b = 1.0 / g.x
+    # scale the injections so that some flows exceed their ratings and the
+    # penalty has curvature
+    P = g.P_sched * 8.0
+    outages = np.arange(0, g.n_branch, 3)
+    return g, P, b, outages
+
+
+def _fd5(fun, x, i, h):
+    """Five-point central difference d fun / d x_i (error O(h^4))."""
+    def at(d):
+        y = x.copy()
+        y[i] += d
+        return fun(y)
+    return (-at(2 * h) + 8 * at(h) - 8 * at(-h) + at(-2 * h)) / (12 * h)
+
+
+def test_adjoint_matches_central_differences():
+    from oracle import adjoint
+    g, P, b, outages = _adjoint_case()
+    L, gP, gb = adjoint.loss_and_grad(g, outages, P, b)
+    assert L > 0
+    rng = np.random.default_rng(0)
+    nonslack = np.flatnonzero(g.bus_type != 2)
+    # h = 1e-6 (the plain central difference) is limited by the rounding of the
+    # summed loss, about eps |L| / h; the five-point rule at h = 1e-4 brings
+    # the check to 1e-6 relative
+    for i in rng.choice(nonslack, 8, replace=False):
+        fd = _fd5(lambda y: adjoint.loss_only(g, outages, y, b), P, i, 1e-4)
+        assert abs(fd - gP[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, gP[i])
+        Pp, Pm = P.copy(), P.copy()
+        Pp[i] += 1e-6
+        Pm[i] -= 1e-6
+        fd6 = (adjoint.loss_only(g, outages, Pp, b) - adjoint.loss_only(g, outages, Pm, b)) / 2e-6
+        assert abs(fd6 - gP[i]) <= 1e-6 * max(1.0, abs(fd6)) + 64 * np.finfo(float).eps * L / 1e-6
+    for k in rng.choice(g.n_branch, 8, replace=False):
+        fd = _fd5(lambda y: adjoint.loss_only(g, outages, P, y), b, k, 1e-4 * b[k])
+        assert abs(fd - gb[k]) <= 1e-6 * max(1.0, abs(fd)), (k, fd, gb[k])
+    # the slack's injection does not enter the DC model
+    assert gP[g.slack] == 0.0
+
+
+def test_adjoint_dc_angles_match_sherman_morrison():
+    """theta_s of the adjoint's forward model is the DC solve of the
+    re-formed contingency matrix: check it against the rank-one update of
+    the base solve for a non-bridge outage."""
+    from oracle import adjoint
+    g, P, b, _ = _adjoint_case()
+    n = g.n_bus
+    keep = np.flatnonzero(g.bus_type != 2)
+    B0 = pf.bprime(n, g.f, g.t, g.x, np.ones(g.n_branch, bool), keep).toarray()
+    th0 = np.linalg.solve(B0, P[keep])
+    for l in range(g.n_branch):
+        S = adjoint.scenario_setup(g, l, b)
+        if S["isl"].any():
+            continue
+        a = np.zeros(n)
+        a[g.f[l]] += 1.0
+        a[g.t[l]] -= 1.0
+        a = a[keep]
+        Ba = np.linalg.solve(B0, a)
+        sm = th0 + b[l] * (a @ th0) / (1 - b[l] * (a @ Ba)) * Ba
+        th = adjoint._theta(g, P, S)[keep]
+        np.testing.assert_allclose(th, sm, rtol=1e-9, atol=1e-12)
+        break
