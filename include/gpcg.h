@@ -190,6 +190,30 @@ GPCG_API gpcg_status gpcg_n1_screen(gpcg_ctx *ctx, const int32_t *outages, int32
                            double *flow, int32_t *island_label, int32_t *iters,
                            int32_t *status, double *max_loading);
 
+/* Loss and gradients of a smooth overload penalty summed over the N-1
+ * scenarios of the P-theta (DC) model (eq. (4) with |V| = 1, Sec. IV.A's
+ * quick screen).  For outage l = outages[s]:
+ *   theta_s = B'_s^{-1} R_s P,   f_s = diag(b_s) A theta_s,
+ *   loss = sum_s sum_k softplus(|f_ks| / rating_k - 1)^2,
+ * where B'_s is the base matrix built from the susceptances b with the
+ * outage's four-element change (Sec. IV.B), islands removed and their
+ * injection re-dispatched with frozen weights (Sec. IV.C), R_s that
+ * re-dispatch map.  The gradients take one more batched PCG solve per
+ * scenario with the symmetric B'_s:
+ *   dL/dP = sum_s R_s^T lambda_s,  lambda_s = B'_s^{-1} A^T diag(b_s) g_s,
+ *   dL/db_k = sum_s [g_ks (A theta_s)_k - (A lambda_s)_k (A theta_s)_k],
+ * with g = dloss/df.  The base case is factorised for the given b, and the
+ * solves run in FP64.
+ * Inputs: P[n_bus] bus injections (NULL: the grid's P_sched), b[n_branch]
+ * branch susceptances, > 0 (NULL: 1/x).  Outputs: loss[1]; dL_dP[n_bus] and
+ * dL_db[n_branch], each optional.  mem and stream as in gpcg_n1_screen; the
+ * call returns when the results are written.  Sums over scenarios are taken
+ * in a fixed order (deterministic).  Errors: INVALID_ARG, OOM, CUDA. */
+GPCG_API gpcg_status gpcg_n1_adjoint(gpcg_ctx *ctx, const int32_t *outages, int32_t n_out,
+                                     int32_t mem, void *stream, const double *P,
+                                     const double *b, double *loss, double *dL_dP,
+                                     double *dL_db);
+
 /* Batched operators of the hot path, for verification: each applies, for
  * S scenarios at once, one step of the inner solve to S vectors stored
  * row-major per scenario in the matrix's own row order (gpcg_export_matrix

@@ -7,5 +7,11 @@ The compute path is the CUDA library ``libgpcg.so`` (C ABI in
 from .binding import (BATCHED_FP32, BATCHED_FP64, GPCG, PLAIN_FP64, PRECOND_EXACT,
                       PRECOND_IC0, PRECOND_JACOBI, GPCGError, default_options, load)
 
-__all__ = ["GPCG", "GPCGError", "default_options", "load", "PLAIN_FP64", "BATCHED_FP32",
+def overload_loss(solver, outages, P, b):
+    """Differentiable N-1 overload penalty (see autograd.N1OverloadLoss)."""
+    from .autograd import N1OverloadLoss
+    return N1OverloadLoss.apply(solver, outages, P, b)
+
+
+__all__ = ["overload_loss", "GPCG", "GPCGError", "default_options", "load", "PLAIN_FP64", "BATCHED_FP32",
            "BATCHED_FP64", "PRECOND_IC0", "PRECOND_JACOBI", "PRECOND_EXACT"]

@@ -54,6 +54,7 @@ class Info(C.Structure):
 EXPORTS = ("gpcg_default_options", "gpcg_create", "gpcg_destroy", "gpcg_set_options",
            "gpcg_get_info", "gpcg_base_solve", "gpcg_n1_screen", "gpcg_apply",
            "gpcg_export_matrix", "gpcg_last_timings", "gpcg_n1_screen_noalloc",
+           "gpcg_n1_adjoint",
            "gpcg_last_error")
 
 _lib = None
@@ -86,6 +87,7 @@ def load(build_if_missing: bool = True):
     lib.gpcg_apply.argtypes = [vp, i32, i32, vp, i32, i32, vp, vp]
     lib.gpcg_export_matrix.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gpcg_last_timings.argtypes = [vp, vp]
+    lib.gpcg_n1_adjoint.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
     lib.gpcg_n1_screen_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gpcg_last_error.argtypes = []
     lib.gpcg_last_error.restype = C.c_char_p
@@ -232,6 +234,27 @@ class GPCG:
             self._h, _ptr(outages), int(outages.shape[0]), C.c_void_p(s.cuda_stream),
             g("theta"), g("V"), g("flow"), g("label"), g("iters"), g("status"),
             g("max_loading")))
+
+    def n1_adjoint(self, outages, P=None, b=None, grads=True):
+        """Host arrays: (loss, dL/dP, dL/db) of the N-1 overload penalty."""
+        out = np.ascontiguousarray(outages, dtype=np.int32)
+        Pa = None if P is None else np.ascontiguousarray(P, dtype=np.float64)
+        ba = None if b is None else np.ascontiguousarray(b, dtype=np.float64)
+        loss = np.zeros(1)
+        gP = np.zeros(self.n_bus) if grads else None
+        gb = np.zeros(self.n_branch) if grads else None
+        _check(self._lib, self._lib.gpcg_n1_adjoint(
+            self._h, _ptr(out), out.shape[0], 0, None, _ptr(Pa), _ptr(ba), _ptr(loss),
+            _ptr(gP), _ptr(gb)))
+        return float(loss[0]), gP, gb
+
+    def n1_adjoint_device(self, outages, P, b, loss, gP, gb, stream=None):
+        """Device tensors in and out (see gpcg_n1_adjoint)."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(self._lib, self._lib.gpcg_n1_adjoint(
+            self._h, _ptr(outages), int(outages.shape[0]), 1, C.c_void_p(s.cuda_stream),
+            _ptr(P), _ptr(b), _ptr(loss), _ptr(gP), _ptr(gb)))
 
     def apply(self, which, op, outages, X, precision=BATCHED_FP64):
         out = np.ascontiguousarray(outages, dtype=np.int32)

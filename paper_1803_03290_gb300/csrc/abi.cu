@@ -174,6 +174,12 @@ struct gpcg_ctx {
   void* work = nullptr;
   size_t work_bytes = 0;
   int tile = 0;
+  // adjoint: B' with caller-given susceptances (structure of MP, own values)
+  MatDev MA;
+  bool ma_ready = false;
+  std::vector<void*> adj_owned;
+  double* adj_acc = nullptr;
+  size_t adj_acc_bytes = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   bool timed = false;
   std::vector<void*> owned;  // freed at destroy (structures of the grid)
@@ -287,6 +293,36 @@ static void ell_fill(cudaStream_t st, EllDev& D, const double* csr_val) {
   launch_gather_val(st, D.nover, D.osrc, csr_val, D.oval, D.oval32);
 }
 
+// Values of a matrix whose structure is built: the weighted Laplacian
+// (weights w per branch), its factor on the planned pattern, diagonals and
+// padded-row values.  Synchronous.
+static gpcg_status fill_values(gpcg_ctx* c, MatDev& M, const double* w) {
+  const MatrixPlan& P = M.plan;
+  const int nl = P.L.nnz();
+  (void)nl;
+  cudaStream_t st = 0;
+  CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int32_t)));
+  launch_laplacian_values(st, P.n, M.bus_of_row, M.row_of_bus, c->G.adj_ptr, c->G.adj_idx,
+                          c->G.adj_br, w, M.a_ptr, M.a_idx, M.a_val, c->d_err);
+  for (size_t k = 0; k + 1 < P.lev_ptr.size(); ++k)
+    launch_ic_level(st, P.lev_ptr[k], P.lev_ptr[k + 1], M.a_ptr, M.a_idx, M.a_val, M.l_ptr,
+                    M.l_idx, M.l_val, c->d_err);
+  launch_gather_diag(st, P.n, M.a_diag, M.a_val, M.diag);
+  launch_to_float(st, P.n, M.diag, M.diag32);
+  launch_inv_diag(st, P.n, M.l_diag, M.l_val, M.inv_diag, M.inv_diag32);
+  ell_fill(st, M.A, M.a_val);
+  ell_fill(st, M.L, M.l_val);
+  ell_fill(st, M.U, M.l_val);
+  CUDA_TRY(cudaGetLastError());
+  int32_t herr = 0;
+  CUDA_TRY(cudaMemcpy(&herr, c->d_err, sizeof herr, cudaMemcpyDeviceToHost));
+  if (herr == 1) return fail(GPCG_ERR_CUDA, "internal: CSR slot missing while building values");
+  if (herr == 2)
+    return fail(GPCG_ERR_INVALID_ARG,
+                "base-case factorisation met a non-positive pivot (matrix not positive definite)");
+  return GPCG_OK;
+}
+
 static gpcg_status build_matrix(gpcg_ctx* c, MatDev& M, const std::vector<uint8_t>& keep,
                                 double* w, bool fill) {
   M.plan = plan_matrix(c->n, c->bg, keep, fill);
@@ -338,30 +374,12 @@ static gpcg_status build_matrix(gpcg_ctx* c, MatDev& M, const std::vector<uint8_
     CUDA_TRY(ell_upload(own, ell_from_rows(ru, KU, P.n), M.U));
   }
   M.w = w;
-  cudaStream_t st = 0;
-  CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int32_t)));
-  launch_laplacian_values(st, P.n, M.bus_of_row, M.row_of_bus, c->G.adj_ptr, c->G.adj_idx,
-                          c->G.adj_br, w, M.a_ptr, M.a_idx, M.a_val, c->d_err);
-  for (size_t k = 0; k + 1 < P.lev_ptr.size(); ++k)
-    launch_ic_level(st, P.lev_ptr[k], P.lev_ptr[k + 1], M.a_ptr, M.a_idx, M.a_val, M.l_ptr,
-                    M.l_idx, M.l_val, c->d_err);
-  launch_gather_diag(st, P.n, M.a_diag, M.a_val, M.diag);
-  launch_to_float(st, P.n, M.diag, M.diag32);
-  launch_inv_diag(st, P.n, M.l_diag, M.l_val, M.inv_diag, M.inv_diag32);
-  ell_fill(st, M.A, M.a_val);
-  ell_fill(st, M.L, M.l_val);
-  ell_fill(st, M.U, M.l_val);
-  CUDA_TRY(cudaGetLastError());
-  int32_t herr = 0;
-  CUDA_TRY(cudaMemcpy(&herr, c->d_err, sizeof herr, cudaMemcpyDeviceToHost));
-  if (herr == 1) return fail(GPCG_ERR_CUDA, "internal: CSR slot missing while building values");
-  if (herr == 2)
-    return fail(GPCG_ERR_INVALID_ARG,
-                "base-case factorisation met a non-positive pivot (matrix not positive definite)");
-  return GPCG_OK;
+  return fill_values(c, M, w);
 }
 
 static gpcg_status build_matrices(gpcg_ctx* c) {
+  free_list(c->adj_owned);
+  c->ma_ready = false;
   free_list(c->mat_owned);
   std::vector<uint8_t> keepP(c->n), keepQ(c->n);
   for (int b = 0; b < c->n; ++b) {
@@ -392,6 +410,8 @@ static gpcg_status build_matrices(gpcg_ctx* c) {
 
 static void destroy(gpcg_ctx* c) {
   if (!c) return;
+  free_list(c->adj_owned);
+  if (c->adj_acc) cudaFree(c->adj_acc);
   free_list(c->mat_owned);
   free_list(c->owned);
   if (c->work) cudaFree(c->work);
@@ -950,6 +970,169 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
     if (ce != cudaSuccess) return fail(GPCG_ERR_CUDA, "n1_screen: %s", cudaGetErrorString(ce));
     if (herr == 3) return fail(GPCG_ERR_CUDA, "internal: an island is not a depth-first subtree");
   }
+  g_err.clear();
+  return GPCG_OK;
+}
+
+// ------------------------------------------------------------------ adjoint
+static gpcg_status ensure_adj_matrix(gpcg_ctx* c) {
+  if (c->ma_ready) return GPCG_OK;
+  MatDev& M = c->MA;
+  M = c->MP;  // structure shared; values replaced below
+  auto& own = c->adj_owned;
+  const int n = M.plan.n, nnz = M.plan.A.nnz(), nl = M.plan.L.nnz();
+  CUDA_TRY(dalloc(own, &M.a_val, nnz));
+  CUDA_TRY(dalloc(own, &M.l_val, nl));
+  CUDA_TRY(dalloc(own, &M.diag, n));
+  CUDA_TRY(dalloc(own, &M.diag32, n));
+  CUDA_TRY(dalloc(own, &M.inv_diag, n));
+  CUDA_TRY(dalloc(own, &M.inv_diag32, n));
+  for (EllDev* E : {&M.A, &M.L, &M.U}) {
+    CUDA_TRY(dalloc(own, &E->val, E->nslot));
+    CUDA_TRY(dalloc(own, &E->val32, E->nslot));
+    CUDA_TRY(dalloc(own, &E->oval, E->nover));
+    CUDA_TRY(dalloc(own, &E->oval32, E->nover));
+  }
+  c->ma_ready = true;
+  return GPCG_OK;
+}
+
+extern "C" gpcg_status gpcg_n1_adjoint(gpcg_ctx* c, const int32_t* outages, int32_t n_out,
+                                       int32_t mem, void* stream, const double* P_in,
+                                       const double* b_in, double* loss, double* dL_dP,
+                                       double* dL_db) {
+  if (!c) return fail(GPCG_ERR_INVALID_ARG, "gpcg_n1_adjoint: ctx is NULL");
+  if (n_out < 0 || !loss) return fail(GPCG_ERR_INVALID_ARG, "n_out < 0 or loss is NULL");
+  if (mem != GPCG_MEM_HOST && mem != GPCG_MEM_DEVICE)
+    return fail(GPCG_ERR_INVALID_ARG, "mem must be 0 (host) or 1 (device)");
+  if (n_out > 0 && !outages) return fail(GPCG_ERR_INVALID_ARG, "outages is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = c->n, m = c->m;
+  const size_t S = (size_t)n_out;
+  std::vector<int32_t> hout(S);
+  if (S) {
+    if (mem == GPCG_MEM_HOST) std::memcpy(hout.data(), outages, S * 4);
+    else {
+      CUDA_TRY(cudaMemcpyAsync(hout.data(), outages, S * 4, cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(cudaStreamSynchronize(st));
+    }
+  }
+  for (size_t s = 0; s < S; ++s)
+    if (hout[s] < 0 || hout[s] >= m)
+      return fail(GPCG_ERR_INVALID_ARG, "outages[%zu] = %d is not a branch index", s, hout[s]);
+  std::vector<double> hb;
+  if (b_in) {
+    hb.resize(m);
+    if (mem == GPCG_MEM_HOST) std::memcpy(hb.data(), b_in, (size_t)m * 8);
+    else {
+      CUDA_TRY(cudaMemcpyAsync(hb.data(), b_in, (size_t)m * 8, cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    for (int k = 0; k < m; ++k)
+      if (!(hb[k] > 0) || !std::isfinite(hb[k]))
+        return fail(GPCG_ERR_INVALID_ARG, "b[%d] = %g: susceptances must be positive", k, hb[k]);
+  }
+  gpcg_status s_ = ensure_scen(c, std::max<size_t>(S, 1));
+  if (s_ != GPCG_OK) return s_;
+  s_ = ensure_adj_matrix(c);
+  if (s_ != GPCG_OK) return s_;
+  // inputs on the device: P in the caller's and in the internal bus order, b
+  double *dPu = nullptr, *dPi = nullptr, *db = nullptr;
+  std::vector<void*> tmp;
+  auto cleanup = [&]() { for (void* p : tmp) cudaFree(p); };
+  auto alloc = [&](double** p, size_t cnt) -> cudaError_t {
+    cudaError_t ce = cudaMalloc((void**)p, cnt * 8);
+    if (ce == cudaSuccess) tmp.push_back(*p);
+    return ce;
+  };
+  cudaError_t ce = alloc(&dPi, n);
+  if (ce == cudaSuccess) {
+    if (!P_in) dPu = c->u_P_sched;
+    else if (mem == GPCG_MEM_DEVICE) dPu = const_cast<double*>(P_in);
+    else if ((ce = alloc(&dPu, n)) == cudaSuccess)
+      ce = cudaMemcpy(dPu, P_in, (size_t)n * 8, cudaMemcpyHostToDevice);
+  }
+  if (ce == cudaSuccess) {
+    if (!b_in) db = c->wP;
+    else if ((ce = alloc(&db, m)) == cudaSuccess)
+      ce = cudaMemcpy(db, hb.data(), (size_t)m * 8, cudaMemcpyHostToDevice);
+  }
+  if (ce == cudaSuccess) ce = launch_gather_perm(st, n, c->G.user_of_bus, dPu, dPi);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) { cleanup(); return fail(GPCG_ERR_CUDA, "adjoint inputs: %s", cudaGetErrorString(ce)); }
+  // base-case B' with the given susceptances, and its factor
+  s_ = fill_values(c, c->MA, db);
+  if (s_ != GPCG_OK) { cleanup(); return s_; }
+  // outputs (device staging in host mode)
+  double *oL = nullptr, *oP = nullptr, *ob = nullptr;
+  if (mem == GPCG_MEM_DEVICE) { oL = loss; oP = dL_dP; ob = dL_db; }
+  else {
+    if ((ce = alloc(&oL, 1)) == cudaSuccess && dL_dP) ce = alloc(&oP, n);
+    if (ce == cudaSuccess && dL_db) ce = alloc(&ob, m);
+    if (ce != cudaSuccess) { cleanup(); return fail(GPCG_ERR_OOM, "adjoint outputs: %s", cudaGetErrorString(ce)); }
+  }
+  const int T = 2;
+  const int n_tiles = (int)((S + T - 1) / T);
+  const int per_sm = std::max(1, adjoint_max_blocks_per_sm());
+  const int slots = std::max(1, std::min(n_tiles, c->num_sms * per_sm));
+  const size_t acc_bytes = (size_t)slots * ((size_t)n + m + 1) * 8;
+  if (acc_bytes > c->adj_acc_bytes) {
+    if (c->adj_acc) cudaFree(c->adj_acc);
+    c->adj_acc = nullptr;
+    c->adj_acc_bytes = 0;
+    ce = cudaMalloc(&c->adj_acc, acc_bytes);
+    if (ce != cudaSuccess) { cleanup(); return fail(GPCG_ERR_OOM, "adjoint sums: %s", cudaGetErrorString(ce)); }
+    c->adj_acc_bytes = acc_bytes;
+  }
+  double* accP = c->adj_acc;
+  double* accb = accP + (size_t)slots * n;
+  double* accL = accb + (size_t)slots * m;
+  if (S) {
+    CUDA_TRY(cudaMemcpyAsync(c->d_outages, hout.data(), S * 4, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(c->d_err, 0, 4, st));
+    ce = launch_islands(st, std::min<int>((int)S, c->num_sms * 4), n, m, c->slack_user, (int)S,
+                        c->d_outages, c->u_f, c->u_t, c->u_bus_type, dPu, c->u_P_gen, c->u_pre,
+                        c->d_lo, c->d_cnt, c->d_coef, c->d_nogen, nullptr, c->d_err);
+    if (ce != cudaSuccess) { cleanup(); return fail(GPCG_ERR_CUDA, "islands: %s", cudaGetErrorString(ce)); }
+    FdpfParams P = base_params(c);
+    P.inner_rtol = 1e-12;  // gradients want converged solves (2-3 iterations with the exact factor)
+    P.max_inner = std::max(c->opt.max_inner, 2000);
+    P.S = (int)S;
+    P.n_tiles = n_tiles;
+    P.sc = ScenInfo{c->d_outages, c->d_lo, c->d_cnt, c->d_coef, c->d_nogen};
+    Layout Lo = make_layout(c, T, slots, 8);
+    s_ = ensure_work(c, Lo.bytes);
+    if (s_ != GPCG_OK) { cleanup(); return s_; }
+    char* base = (char*)c->work;
+    const size_t vb = (size_t)slots * Lo.vec_bytes;
+    const size_t ss = (((Lo.sstride * 8 + 255) / 256) * 256) / 8;
+    P.wx = base; P.wr = base + vb; P.wp = base + 2 * vb; P.wq = base + 3 * vb; P.wz = base + 4 * vb;
+    P.vstride = Lo.vec_bytes / 8;
+    double* sbase = (double*)(base + 5 * vb);
+    P.wth = sbase; P.wV = sbase + slots * ss; P.wc = sbase + 2 * slots * ss;
+    P.ws = sbase + 3 * slots * ss; P.we = sbase + 4 * slots * ss; P.wf = sbase + 5 * slots * ss;
+    P.sstride = ss;
+    P.tile_counter = c->d_counter;
+    CUDA_TRY(cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), st));
+    AdjParamsView A{dPi, db, accP, accb, accL};
+    ce = launch_adjoint(st, slots, P, A, c->MA.view<double>());
+    if (ce == cudaSuccess) ce = launch_slot_sum(st, 1, slots, accL, nullptr, oL);
+    if (ce == cudaSuccess && oP) ce = launch_slot_sum(st, n, slots, accP, c->G.user_of_bus, oP);
+    if (ce == cudaSuccess && ob) ce = launch_slot_sum(st, m, slots, accb, nullptr, ob);
+  } else {
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(oL, 0, 8, st);
+    if (ce == cudaSuccess && oP) ce = cudaMemsetAsync(oP, 0, (size_t)n * 8, st);
+    if (ce == cudaSuccess && ob) ce = cudaMemsetAsync(ob, 0, (size_t)m * 8, st);
+  }
+  if (ce != cudaSuccess) { cleanup(); return fail(GPCG_ERR_CUDA, "adjoint: %s", cudaGetErrorString(ce)); }
+  if (mem == GPCG_MEM_HOST) {
+    ce = cudaMemcpyAsync(loss, oL, 8, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess && dL_dP) ce = cudaMemcpyAsync(dL_dP, oP, (size_t)n * 8, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess && dL_db) ce = cudaMemcpyAsync(dL_db, ob, (size_t)m * 8, cudaMemcpyDeviceToHost, st);
+  }
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);  // temporaries are freed below
+  cleanup();
+  if (ce != cudaSuccess) return fail(GPCG_ERR_CUDA, "adjoint: %s", cudaGetErrorString(ce));
   g_err.clear();
   return GPCG_OK;
 }

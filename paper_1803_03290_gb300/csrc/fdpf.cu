@@ -23,568 +23,9 @@
 #include <math.h>
 #include "common.cuh"
 #include "fdpf.h"
+#include "fdpf_ops.cuh"
 
 namespace gpcg {
-
-constexpr int LP = 2;  // scenario lanes per thread
-#ifndef FDPF_UNROLL
-#define FDPF_UNROLL 1
-#endif
-constexpr int UNR = FDPF_UNROLL;  // rows per thread in flight in the PCG passes
-#ifndef FDPF_MIS_GROUP
-#define FDPF_MIS_GROUP 3
-#endif
-constexpr int MIS_GROUP = FDPF_MIS_GROUP;  // neighbours loaded together in the mismatch
-// Large passes are kept out of line by default (separate register
-// allocation); -DGPCG_PASS_INLINE=__forceinline__ inlines them.
-#ifndef GPCG_PASS_INLINE
-#define GPCG_PASS_INLINE __noinline__
-#endif
-#ifndef FDPF_MIN_BLOCKS
-#define FDPF_MIN_BLOCKS 5  // resident CTAs per SM the register budget is cut for
-#endif
-
-// Inner iterations without progress after which a solve stops: the outer
-// FP64 loop then refines the answer (iterative refinement).
-constexpr int STALL_ITERS = 50;
-
-// ------------------------------------------------------------ helpers
-template <typename VT> struct Pair { VT a, b; };
-
-__device__ __forceinline__ Pair<float> ld2(const float* p) {
-  const float2 v = *reinterpret_cast<const float2*>(p);
-  return {v.x, v.y};
-}
-__device__ __forceinline__ Pair<double> ld2(const double* p) {
-  const double2 v = *reinterpret_cast<const double2*>(p);
-  return {v.x, v.y};
-}
-__device__ __forceinline__ void st2(float* p, Pair<float> v) {
-  *reinterpret_cast<float2*>(p) = make_float2(v.a, v.b);
-}
-__device__ __forceinline__ void st2(double* p, Pair<double> v) {
-  *reinterpret_cast<double2*>(p) = make_double2(v.a, v.b);
-}
-
-template <int K>
-__device__ __forceinline__ void ld_cols(const int32_t* p, int (&c)[K]) {
-  static_assert(K % 2 == 0, "slots come in pairs");
-#pragma unroll
-  for (int k = 0; k < K; k += 2) {
-    const int2 v = __ldg(reinterpret_cast<const int2*>(p + k));
-    c[k] = v.x; c[k + 1] = v.y;
-  }
-}
-template <int K>
-__device__ __forceinline__ void ld_vals(const float* p, float (&v)[K]) {
-#pragma unroll
-  for (int k = 0; k < K; k += 2) {
-    const float2 u = __ldg(reinterpret_cast<const float2*>(p + k));
-    v[k] = u.x; v[k + 1] = u.y;
-  }
-}
-template <int K>
-__device__ __forceinline__ void ld_vals(const double* p, double (&v)[K]) {
-#pragma unroll
-  for (int k = 0; k < K; k += 2) {
-    const double2 u = __ldg(reinterpret_cast<const double2*>(p + k));
-    v[k] = u.x; v[k + 1] = u.y;
-  }
-}
-
-// ------------------------------------------------------------ lane state
-template <int T>
-struct LaneState {
-  int scen[T], l[T], fb[T], tb[T], lo[T], cnt[T];
-  int raP[T], rbP[T], raQ[T], rbQ[T];
-  double wP[T], wQ[T], coef[T], gl[T], bl[T];
-  int active[T], outer[T], inP[T], inQ[T], status[T], nogen[T];
-  double err[T], best[T];
-  double rz[T], bb[T], alpha[T], beta[T], rrmin[T];
-  unsigned long long tphase[8];
-  int pdone[T], stall[T];
-  int done[T], fresh[T];
-  double red[NTHREADS * LP];
-  int flag;
-  int drained;
-};
-
-template <int T>
-struct Geo {
-  static constexpr int TPR = T / LP;             // threads per row
-  static constexpr int RPS = NTHREADS / TPR;     // rows per step
-  int rs, lane;                                  // row slot, first lane
-  __device__ Geo() : rs(threadIdx.x / TPR), lane((threadIdx.x % TPR) * LP) {}
-};
-
-// Sum (or max) over the row slots of each lane's partial values.
-template <int T, bool MAX>
-__device__ __forceinline__ Pair<double> lane_reduce(LaneState<T>& L, double v0, double v1) {
-  const Geo<T> g;
-  constexpr int RPS = Geo<T>::RPS;
-  L.red[g.rs * T + g.lane] = v0;
-  L.red[g.rs * T + g.lane + 1] = v1;
-  __syncthreads();
-#pragma unroll
-  for (int st = RPS / 2; st > 0; st >>= 1) {
-    if (g.rs < st) {
-#pragma unroll
-      for (int j = 0; j < LP; ++j) {
-        const int o = g.rs * T + g.lane + j;
-        const double a = L.red[o], b = L.red[o + st * T];
-        L.red[o] = MAX ? ((b > a || b != b) ? b : a) : a + b;
-      }
-    }
-    __syncthreads();
-  }
-  const Pair<double> out{L.red[g.lane], L.red[g.lane + 1]};
-  __syncthreads();
-  return out;
-}
-
-// True when some lane has a nonzero flag (block-uniform).
-template <int T, typename F>
-__device__ __forceinline__ bool any_lane(LaneState<T>& L, const F* flags) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int any = 0;
-    for (int s = 0; s < T; ++s) any |= (flags[s] != 0);
-    L.flag = any;
-  }
-  __syncthreads();
-  const bool r = L.flag != 0;
-  __syncthreads();
-  return r;
-}
-
-__device__ __forceinline__ void upd_max(double& m, double d) {
-  const double a = fabs(d);
-  if (!(a <= m)) m = (a == a) ? a : INFINITY;
-}
-
-// ----------------------------------------------------- batched operators
-// q = B_s p for the thread's two lanes: base row times p, plus the outaged
-// branch's four-element change (Sec. IV.B) -- off-diagonal +w, diagonal -w
-// at both ends.  Returns the lanes' partial p.q.
-template <int T, typename VT>
-__device__ __forceinline__ Pair<double> spmv_pass(const DevMatT<VT>& M, const VT* __restrict__ p,
-                                                  VT* __restrict__ q, int ra0, int rb0, VT w0,
-                                                  int ra1, int rb1, VT w1) {
-  const Geo<T> g;
-  constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
-  VT pq0 = 0, pq1 = 0;
-  // UNR rows per thread per step, and the column indices of the next step
-  // loaded one step ahead: each step waits on one memory latency for
-  // UNR rows' gathers
-  // rows are visited in bus order (M.visit), so a row's neighbours were
-  // visited just before it and their chunks of p are still in cache
-  int cn[UNR][KA], vn[UNR];
-#pragma unroll
-  for (int u = 0; u < UNR; ++u)
-    if (g.rs + u * RPS < M.n) {
-      vn[u] = __ldg(M.visit + g.rs + u * RPS);
-      ld_cols<KA>(M.A.col + (size_t)vn[u] * KA, cn[u]);
-    }
-  for (int i0 = g.rs; i0 < M.n; i0 += STEP) {
-    int c[UNR][KA], ii[UNR];
-    VT v[UNR][KA];
-    Pair<VT> pc[UNR][KA], pi[UNR];
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      ii[u] = vn[u];
-#pragma unroll
-      for (int k = 0; k < KA; ++k) c[u][k] = cn[u][k];
-      const int in = i0 + STEP + u * RPS;
-      if (in < M.n) {
-        vn[u] = __ldg(M.visit + in);
-        ld_cols<KA>(M.A.col + (size_t)vn[u] * KA, cn[u]);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      const int i = ii[u];
-      if (i0 + u * RPS < M.n) {
-        ld_vals<KA>(M.A.val + (size_t)i * KA, v[u]);
-#pragma unroll
-        for (int k = 0; k < KA; ++k) pc[u][k] = ld2(p + (size_t)c[u][k] * T + g.lane);
-        pi[u] = ld2(p + (size_t)i * T + g.lane);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      const int i = ii[u];
-      if (i0 + u * RPS >= M.n) continue;
-      const int oth0 = (i == ra0) ? rb0 : ((i == rb0) ? ra0 : -2);
-      const int oth1 = (i == ra1) ? rb1 : ((i == rb1) ? ra1 : -2);
-      VT a0 = 0, a1 = 0;
-#pragma unroll
-      for (int k = 0; k < KA; ++k) {
-        a0 += (v[u][k] + (c[u][k] == oth0 ? w0 : (VT)0)) * pc[u][k].a;
-        a1 += (v[u][k] + (c[u][k] == oth1 ? w1 : (VT)0)) * pc[u][k].b;
-      }
-      const int o0 = __ldg(M.A.optr + i), o1 = __ldg(M.A.optr + i + 1);
-      for (int o = o0; o < o1; ++o) {
-        const int cc = __ldg(M.A.ocol + o);
-        const VT vv = __ldg(M.A.oval + o);
-        const Pair<VT> pp = ld2(p + (size_t)cc * T + g.lane);
-        a0 += (vv + (cc == oth0 ? w0 : (VT)0)) * pp.a;
-        a1 += (vv + (cc == oth1 ? w1 : (VT)0)) * pp.b;
-      }
-      if (oth0 != -2) a0 -= w0 * pi[u].a;
-      if (oth1 != -2) a1 -= w1 * pi[u].b;
-      st2(q + (size_t)i * T + g.lane, Pair<VT>{a0, a1});
-      pq0 += pi[u].a * a0;
-      pq1 += pi[u].b * a1;
-    }
-  }
-  return {(double)pq0, (double)pq1};
-}
-
-// Forward substitution L y = r over the level schedule (rows of one level
-// are independent).  With FUSED, first x += alpha p and r -= alpha q (the
-// PCG update); without it, x = 0.  Accumulates r.r.
-template <int T, typename VT, bool FUSED>
-__device__ __forceinline__ Pair<double> fwd_pass(const DevMatT<VT>& M, VT* __restrict__ x,
-                                                 VT* __restrict__ r, const VT* __restrict__ p,
-                                                 const VT* __restrict__ q, VT* __restrict__ z,
-                                                 VT al0, VT al1) {
-  const Geo<T> g;
-  constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
-  VT rr0 = 0, rr1 = 0;
-  for (int lev = 0; lev < M.nlev; ++lev) {
-    const int r0 = __ldg(M.lev_ptr + lev), r1 = __ldg(M.lev_ptr + lev + 1);
-    int cn[UNR][KL];
-#pragma unroll
-    for (int u = 0; u < UNR; ++u)
-      if (r0 + g.rs + u * RPS < r1) ld_cols<KL>(M.L.col + (size_t)(r0 + g.rs + u * RPS) * KL, cn[u]);
-    for (int i0 = r0 + g.rs; i0 < r1; i0 += STEP) {
-      int c[UNR][KL];
-      VT v[UNR][KL];
-      Pair<VT> zc[UNR][KL], ri[UNR], pi[UNR], qi[UNR], xi[UNR];
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-#pragma unroll
-        for (int k = 0; k < KL; ++k) c[u][k] = cn[u][k];
-        const int in = i0 + STEP + u * RPS;
-        if (in < r1) ld_cols<KL>(M.L.col + (size_t)in * KL, cn[u]);
-      }
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        const int i = i0 + u * RPS;
-        if (i < r1) {
-          const size_t o = (size_t)i * T + g.lane;
-          ld_vals<KL>(M.L.val + (size_t)i * KL, v[u]);
-#pragma unroll
-          for (int k = 0; k < KL; ++k) zc[u][k] = ld2(z + (size_t)c[u][k] * T + g.lane);
-          ri[u] = ld2(r + o);
-          if (FUSED) {
-            pi[u] = ld2(p + o);
-            qi[u] = ld2(q + o);
-            xi[u] = ld2(x + o);
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        const int i = i0 + u * RPS;
-        if (i >= r1) continue;
-        const size_t o = (size_t)i * T + g.lane;
-        Pair<VT> rv = ri[u];
-        if (FUSED) {
-          st2(x + o, Pair<VT>{xi[u].a + al0 * pi[u].a, xi[u].b + al1 * pi[u].b});
-          rv.a -= al0 * qi[u].a;
-          rv.b -= al1 * qi[u].b;
-          st2(r + o, rv);
-        } else {
-          st2(x + o, Pair<VT>{(VT)0, (VT)0});
-        }
-        rr0 += rv.a * rv.a;
-        rr1 += rv.b * rv.b;
-        VT a0 = rv.a, a1 = rv.b;
-#pragma unroll
-        for (int k = 0; k < KL; ++k) {
-          a0 -= v[u][k] * zc[u][k].a;
-          a1 -= v[u][k] * zc[u][k].b;
-        }
-        const int o0 = __ldg(M.L.optr + i), o1 = __ldg(M.L.optr + i + 1);
-        for (int e = o0; e < o1; ++e) {
-          const VT vv = __ldg(M.L.oval + e);
-          const Pair<VT> zz = ld2(z + (size_t)__ldg(M.L.ocol + e) * T + g.lane);
-          a0 -= vv * zz.a;
-          a1 -= vv * zz.b;
-        }
-        const VT id = __ldg(M.inv_diag + i);
-        st2(z + o, Pair<VT>{a0 * id, a1 * id});
-      }
-    }
-    __syncthreads();
-  }
-  return {(double)rr0, (double)rr1};
-}
-
-// Back substitution L^T z = y in place (z holds y on entry), over the
-// backward level schedule; accumulates r.z.
-template <int T, typename VT>
-__device__ __forceinline__ Pair<double> bwd_pass(const DevMatT<VT>& M, const VT* __restrict__ r,
-                                                 VT* __restrict__ z) {
-  const Geo<T> g;
-  constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
-  VT rz0 = 0, rz1 = 0;
-  for (int lev = 0; lev < M.nblev; ++lev) {
-    const int r0 = __ldg(M.blev_ptr + lev), r1 = __ldg(M.blev_ptr + lev + 1);
-    int in_[UNR], cn[UNR][KU];
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      in_[u] = 0;
-      if (r0 + g.rs + u * RPS < r1) {
-        in_[u] = __ldg(M.blev_rows + r0 + g.rs + u * RPS);
-        ld_cols<KU>(M.U.col + (size_t)in_[u] * KU, cn[u]);
-      }
-    }
-    for (int k0 = r0 + g.rs; k0 < r1; k0 += STEP) {
-      int ii[UNR], c[UNR][KU];
-      VT v[UNR][KU];
-      Pair<VT> zc[UNR][KU], yi[UNR], ri[UNR];
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        ii[u] = in_[u];
-#pragma unroll
-        for (int k = 0; k < KU; ++k) c[u][k] = cn[u][k];
-        const int kn = k0 + STEP + u * RPS;
-        if (kn < r1) {
-          in_[u] = __ldg(M.blev_rows + kn);
-          ld_cols<KU>(M.U.col + (size_t)in_[u] * KU, cn[u]);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        if (k0 + u * RPS < r1) {
-          const size_t o = (size_t)ii[u] * T + g.lane;
-          ld_vals<KU>(M.U.val + (size_t)ii[u] * KU, v[u]);
-#pragma unroll
-          for (int k = 0; k < KU; ++k) zc[u][k] = ld2(z + (size_t)c[u][k] * T + g.lane);
-          yi[u] = ld2(z + o);
-          ri[u] = ld2(r + o);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        if (k0 + u * RPS >= r1) continue;
-        const int i = ii[u];
-        const size_t o = (size_t)i * T + g.lane;
-        VT a0 = yi[u].a, a1 = yi[u].b;
-#pragma unroll
-        for (int k = 0; k < KU; ++k) {
-          a0 -= v[u][k] * zc[u][k].a;
-          a1 -= v[u][k] * zc[u][k].b;
-        }
-        const int o0 = __ldg(M.U.optr + i), o1 = __ldg(M.U.optr + i + 1);
-        for (int e = o0; e < o1; ++e) {
-          const VT vv = __ldg(M.U.oval + e);
-          const Pair<VT> zz = ld2(z + (size_t)__ldg(M.U.ocol + e) * T + g.lane);
-          a0 -= vv * zz.a;
-          a1 -= vv * zz.b;
-        }
-        const VT id = __ldg(M.inv_diag + i);
-        a0 *= id;
-        a1 *= id;
-        st2(z + o, Pair<VT>{a0, a1});
-        rz0 += ri[u].a * a0;
-        rz1 += ri[u].b * a1;
-      }
-    }
-    __syncthreads();
-  }
-  return {(double)rz0, (double)rz1};
-}
-
-// Jacobi: z = r / diag(B_s), the diagonal with the outage applied; a row
-// whose diagonal vanishes (a bus the outage isolates) gets z = 0.
-template <int T, typename VT, bool FUSED>
-__device__ __forceinline__ void jacobi_pass(const DevMatT<VT>& M, VT* __restrict__ x,
-                                            VT* __restrict__ r, const VT* __restrict__ p,
-                                            const VT* __restrict__ q, VT* __restrict__ z, VT al0,
-                                            VT al1, int ra0, int rb0, VT w0, int ra1, int rb1,
-                                            VT w1, Pair<double>& rr, Pair<double>& rz) {
-  const Geo<T> g;
-  for (int i = g.rs; i < M.n; i += Geo<T>::RPS) {
-    const size_t o = (size_t)i * T + g.lane;
-    Pair<VT> ri = ld2(r + o);
-    if (FUSED) {
-      const Pair<VT> pi = ld2(p + o), qi = ld2(q + o), xi = ld2(x + o);
-      st2(x + o, Pair<VT>{xi.a + al0 * pi.a, xi.b + al1 * pi.b});
-      ri.a -= al0 * qi.a;
-      ri.b -= al1 * qi.b;
-      st2(r + o, ri);
-    } else {
-      st2(x + o, Pair<VT>{(VT)0, (VT)0});
-    }
-    const VT dg = __ldg(M.diag + i);
-    const VT d0 = dg - ((i == ra0 || i == rb0) ? w0 : (VT)0);
-    const VT d1 = dg - ((i == ra1 || i == rb1) ? w1 : (VT)0);
-    const VT z0 = d0 > (VT)0 ? ri.a / d0 : (VT)0;
-    const VT z1 = d1 > (VT)0 ? ri.b / d1 : (VT)0;
-    st2(z + o, Pair<VT>{z0, z1});
-    rr.a += (double)(ri.a * ri.a);
-    rr.b += (double)(ri.b * ri.b);
-    rz.a += (double)(ri.a * z0);
-    rz.b += (double)(ri.b * z1);
-  }
-  __syncthreads();
-}
-
-// p = mask(z) + beta p: islanded rows keep a zero search direction.
-template <int T, typename VT>
-__device__ __forceinline__ void pupdate_pass(const DevMatT<VT>& M, const VT* __restrict__ z,
-                                             VT* __restrict__ p, VT be0, VT be1, int lo0,
-                                             int cnt0, int lo1, int cnt1, bool first) {
-  const Geo<T> g;
-  constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
-  for (int i0 = g.rs; i0 < M.n; i0 += STEP) {
-    int pr[UNR], ii[UNR];
-    Pair<VT> zi[UNR], pi[UNR];
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      const int i = i0 + u * RPS < M.n ? __ldg(M.visit + i0 + u * RPS) : 0;
-      ii[u] = i;
-      if (i0 + u * RPS < M.n) {
-        const size_t o = (size_t)i * T + g.lane;
-        pr[u] = __ldg(M.pre_of_row + i);
-        zi[u] = ld2(z + o);
-        if (!first) pi[u] = ld2(p + o);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      const int i = ii[u];
-      if (i0 + u * RPS >= M.n) continue;
-      Pair<VT> pn{in_island(pr[u], lo0, cnt0) ? (VT)0 : zi[u].a,
-                  in_island(pr[u], lo1, cnt1) ? (VT)0 : zi[u].b};
-      if (!first) {
-        pn.a += be0 * pi[u].a;
-        pn.b += be1 * pi[u].b;
-      }
-      st2(p + (size_t)i * T + g.lane, pn);
-    }
-  }
-  __syncthreads();
-}
-
-// ------------------------------------------------------------ the solve
-// Batched PCG (Sec. III.A listing, read as textbook PCG) on B_s x = r for
-// the lanes that are active; x starts at 0.  Adds each lane's iteration
-// count to iters[lane].
-template <int T, typename VT>
-__device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT>& M, LaneState<T>& L, VT* x,
-                          VT* r, VT* p, VT* q, VT* z, const int* ra_, const int* rb_,
-                          const double* w_, int* iters) {
-  const Geo<T> g;
-  const int l0 = g.lane, l1 = g.lane + 1;
-  const int ra0 = ra_[l0], rb0 = rb_[l0], ra1 = ra_[l1], rb1 = rb_[l1];
-  const VT w0 = (VT)w_[l0], w1 = (VT)w_[l1];
-  const int lo0 = L.lo[l0], cnt0 = L.cnt[l0], lo1 = L.lo[l1], cnt1 = L.cnt[l1];
-  const bool jac = (P.precond == PREC_JACOBI);
-  // the zero row that padding slots point at
-  if (g.rs == 0) {
-    st2(p + (size_t)M.n * T + g.lane, Pair<VT>{(VT)0, (VT)0});
-    st2(z + (size_t)M.n * T + g.lane, Pair<VT>{(VT)0, (VT)0});
-    L.pdone[l0] = !L.active[l0];
-    L.pdone[l1] = !L.active[l1];
-  }
-  __syncthreads();
-  Pair<double> bbp{0.0, 0.0}, rzp{0.0, 0.0};
-  if (jac) {
-    jacobi_pass<T, VT, false>(M, x, r, p, q, z, (VT)0, (VT)0, ra0, rb0, w0, ra1, rb1, w1, bbp, rzp);
-  } else {
-    bbp = fwd_pass<T, VT, false>(M, x, r, p, q, z, (VT)0, (VT)0);
-    rzp = bwd_pass<T, VT>(M, r, z);
-  }
-  const Pair<double> bb = lane_reduce<T, false>(L, bbp.a, bbp.b);
-  const Pair<double> rz0 = lane_reduce<T, false>(L, rzp.a, rzp.b);
-  pupdate_pass<T, VT>(M, z, p, (VT)0, (VT)0, lo0, cnt0, lo1, cnt1, true);
-  if (g.rs == 0) {
-#pragma unroll
-    for (int j = 0; j < LP; ++j) {
-      const int ln = g.lane + j;
-      const double b_ = j ? bb.b : bb.a, r_ = j ? rz0.b : rz0.a;
-      L.bb[ln] = b_;
-      L.rz[ln] = r_;
-      L.rrmin[ln] = b_;
-      L.stall[ln] = 0;
-      if (!(b_ > 0.0) || !(r_ > 0.0)) L.pdone[ln] = 1;
-    }
-  }
-  const double tol2 = P.inner_rtol * P.inner_rtol;
-  for (int it = 0; it < P.max_inner; ++it) {
-    __syncthreads();
-    if (g.rs == 0) {
-      L.alpha[l0] = L.pdone[l0] ? 0.0 : 1.0;  // alpha doubles as "still running"
-      L.alpha[l1] = L.pdone[l1] ? 0.0 : 1.0;
-    }
-    if (!any_lane<T>(L, L.alpha)) break;
-    const Pair<double> pqp = spmv_pass<T, VT>(M, p, q, ra0, rb0, w0, ra1, rb1, w1);
-    const Pair<double> pq = lane_reduce<T, false>(L, pqp.a, pqp.b);
-    if (g.rs == 0) {
-#pragma unroll
-      for (int j = 0; j < LP; ++j) {
-        const int ln = g.lane + j;
-        const double v = j ? pq.b : pq.a;
-        double a = 0.0;
-        if (!L.pdone[ln]) {
-          if (v > 0.0 && isfinite(v)) a = L.rz[ln] / v;
-          else L.pdone[ln] = 1;  // breakdown: keep the current iterate
-        }
-        L.alpha[ln] = a;
-      }
-    }
-    __syncthreads();
-    const VT al0 = (VT)L.alpha[l0], al1 = (VT)L.alpha[l1];
-    Pair<double> rrp{0.0, 0.0}, rzn{0.0, 0.0};
-    if (jac) {
-      jacobi_pass<T, VT, true>(M, x, r, p, q, z, al0, al1, ra0, rb0, w0, ra1, rb1, w1, rrp, rzn);
-    } else {
-      rrp = fwd_pass<T, VT, true>(M, x, r, p, q, z, al0, al1);
-    }
-    const Pair<double> rr = lane_reduce<T, false>(L, rrp.a, rrp.b);
-    if (g.rs == 0) {
-#pragma unroll
-      for (int j = 0; j < LP; ++j) {
-        const int ln = g.lane + j;
-        const double v = j ? rr.b : rr.a;
-        if (L.pdone[ln]) continue;
-        iters[ln] += 1;
-        // converged; or stagnated at the rounding floor of VT (no 0.1 % gain
-        // in STALL_ITERS iterations); or growing away from the best residual
-        if (v < 0.999 * L.rrmin[ln]) { L.rrmin[ln] = v; L.stall[ln] = 0; }
-        else L.stall[ln] += 1;
-        if (v <= tol2 * L.bb[ln] || !isfinite(v) || L.stall[ln] >= STALL_ITERS ||
-            v > 1e4 * L.rrmin[ln])
-          L.pdone[ln] = 1;
-      }
-    }
-    __syncthreads();
-    if (g.rs == 0) {
-      L.beta[l0] = L.pdone[l0] ? 0.0 : 1.0;
-      L.beta[l1] = L.pdone[l1] ? 0.0 : 1.0;
-    }
-    if (!any_lane<T>(L, L.beta)) break;
-    if (!jac) rzn = bwd_pass<T, VT>(M, r, z);
-    const Pair<double> rz = lane_reduce<T, false>(L, rzn.a, rzn.b);
-    if (g.rs == 0) {
-#pragma unroll
-      for (int j = 0; j < LP; ++j) {
-        const int ln = g.lane + j;
-        const double v = j ? rz.b : rz.a;
-        L.beta[ln] = L.pdone[ln] ? 0.0 : v / L.rz[ln];
-        if (!L.pdone[ln]) L.rz[ln] = v;
-        if (!(v > 0.0)) L.pdone[ln] = 1;
-      }
-    }
-    __syncthreads();
-    pupdate_pass<T, VT>(M, z, p, (VT)L.beta[l0], (VT)L.beta[l1], lo0, cnt0, lo1, cnt1, false);
-  }
-  __syncthreads();
-}
 
 // ------------------------------------------------------------ mismatch
 // dP_i, dQ_i of eqs. (1)-(3) from the rectangular voltages e + jf:
@@ -639,7 +80,7 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
       double Ps = 0.0, pg = 0.0;
       if (WITH_P) {
         Ps = __ldg(G.P_sched + i);
-        if (bt == 1) pg = __ldg(G.P_gen + i);
+        if (bt == 1) pg = fmax(__ldg(G.P_gen + i), 0.0);  // generators with P_gen > 0 take it
       }
       // the two lanes one after the other: half the live FP64 registers
 #pragma unroll 1

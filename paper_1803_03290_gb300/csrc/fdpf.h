@@ -46,4 +46,18 @@ cudaError_t launch_apply(cudaStream_t st, int grid, const DevMatT<VT>& M, int op
                          const double* X, double* Y, VT* wbuf, size_t vstride, int precond);
 cudaError_t launch_base_trig(cudaStream_t st, int n, const double* th, double* c, double* s);
 
+// adjoint.cu
+struct AdjParamsView {
+  const double* P;   // [n] injections, internal bus order
+  const double* b;   // [m] branch susceptances
+  double *gP, *gb, *loss;  // per-slot sums: [slots][n], [slots][m], [slots]
+};
+cudaError_t launch_adjoint(cudaStream_t st, int grid, const FdpfParams& P, const AdjParamsView& A,
+                           const DevMatT<double>& M);
+int adjoint_max_blocks_per_sm();
+cudaError_t launch_slot_sum(cudaStream_t st, int n, int slots, const double* acc,
+                            const int32_t* map, double* out);
+cudaError_t launch_gather_perm(cudaStream_t st, int n, const int32_t* idx, const double* src,
+                               double* dst);
+
 }  // namespace gpcg
