@@ -163,11 +163,8 @@ def run_gpcg(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    from paper_1803_03290_gb300.shard import max_over_ranks
+    total_ms = max_over_ranks(float(sum(step_ms)), device=dev)
     value = world * S * args.steps / (total_ms / 1e3)
     iters = out["iters"].cpu().numpy()
     status = out["status"].cpu().numpy()

@@ -284,6 +284,30 @@ GPCG_API gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx *ctx, const int32_t *outage
                                             int32_t *iters, int32_t *status,
                                             double *max_loading);
 
+/* Sizes of a structural plan (gpcg_analyze). */
+typedef struct {
+  int32_t n_rows, nnz_a, nnz_l, levels, blevels, n_bridges;
+} gpcg_plan_info;
+
+/* The host-side structural analysis of gpcg_create alone, without a GPU:
+ * the internal bus numbering (a reverse Cuthill-McKee order of the bus
+ * graph), and for matrix `which` (0: B', 1: B'') the row order, the factor
+ * pattern for `precond` (GPCG_PRECOND_EXACT: the complete symbolic
+ * Cholesky pattern under the minimum-degree order; otherwise the lower
+ * triangle of the matrix, i.e. IC(0)) and its forward level schedule
+ * (Sec. IV.B), plus the branches whose outage splits the grid (Sec. IV.C).
+ * Call with NULL arrays to get the sizes in *info, then again with:
+ *   bus_order[n_bus]      internal position -> bus
+ *   bus_of_row[n_rows]    matrix row -> bus
+ *   lrowptr[n_rows+1], lcol[nnz_l]  the factor pattern (CSR, lower, diagonal last)
+ *   level[n_rows]         forward level of each row
+ *   bridge[n_branch]      1 where the branch is a bridge
+ * Errors: INVALID_ARG (as gpcg_create), BASE_ISLANDED. */
+GPCG_API gpcg_status gpcg_analyze(const gpcg_grid *grid, int32_t precond, int32_t which,
+                                  gpcg_plan_info *info, int32_t *bus_order,
+                                  int32_t *bus_of_row, int32_t *lrowptr, int32_t *lcol,
+                                  int32_t *level, uint8_t *bridge);
+
 /* Message of the last error on the calling thread ("" if none). */
 GPCG_API const char *gpcg_last_error(void);
 

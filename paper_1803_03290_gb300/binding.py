@@ -54,7 +54,7 @@ class Info(C.Structure):
 EXPORTS = ("gpcg_default_options", "gpcg_create", "gpcg_destroy", "gpcg_set_options",
            "gpcg_get_info", "gpcg_base_solve", "gpcg_n1_screen", "gpcg_apply",
            "gpcg_export_matrix", "gpcg_last_timings", "gpcg_n1_screen_noalloc",
-           "gpcg_n1_adjoint",
+           "gpcg_n1_adjoint", "gpcg_analyze",
            "gpcg_last_error")
 
 _lib = None
@@ -88,6 +88,7 @@ def load(build_if_missing: bool = True):
     lib.gpcg_export_matrix.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gpcg_last_timings.argtypes = [vp, vp]
     lib.gpcg_n1_adjoint.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
+    lib.gpcg_analyze.argtypes = [C.POINTER(_Grid), i32, i32, vp, vp, vp, vp, vp, vp, vp]
     lib.gpcg_n1_screen_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gpcg_last_error.argtypes = []
     lib.gpcg_last_error.restype = C.c_char_p
@@ -109,6 +110,46 @@ def _ptr(a):
     if hasattr(a, "data_ptr"):
         return C.c_void_p(a.data_ptr())
     return a.ctypes.data_as(C.c_void_p)
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [(k, C.c_int32) for k in ("n_rows", "nnz_a", "nnz_l", "levels", "blevels",
+                                          "n_bridges")]
+
+
+def _grid_struct(grid):
+    keep = dict(
+        bus_type=np.ascontiguousarray(grid.bus_type, dtype=np.int8),
+        P_sched=np.ascontiguousarray(grid.P_sched, dtype=np.float64),
+        Q_sched=np.ascontiguousarray(grid.Q_sched, dtype=np.float64),
+        P_gen=np.ascontiguousarray(grid.P_gen, dtype=np.float64),
+        V_set=np.ascontiguousarray(grid.V_set, dtype=np.float64),
+        from_=np.ascontiguousarray(grid.f, dtype=np.int32),
+        to=np.ascontiguousarray(grid.t, dtype=np.int32),
+        r=np.ascontiguousarray(grid.r, dtype=np.float64),
+        x=np.ascontiguousarray(grid.x, dtype=np.float64),
+        b_sh=np.ascontiguousarray(grid.b_sh, dtype=np.float64),
+        rating=np.ascontiguousarray(grid.rating, dtype=np.float64))
+    g = _Grid(n_bus=int(grid.n_bus), n_branch=int(grid.n_branch),
+              **{k: v.ctypes.data for k, v in keep.items()})
+    return g, keep
+
+
+def analyze(grid, precond=PRECOND_EXACT, which=0):
+    """Host-only structural plan (gpcg_analyze): numpy arrays."""
+    lib = load()
+    g, keep = _grid_struct(grid)
+    info = PlanInfo()
+    _check(lib, lib.gpcg_analyze(C.byref(g), precond, which, C.byref(info), None, None, None,
+                                 None, None, None))
+    d = dict(bus_order=np.empty(grid.n_bus, np.int32), bus_of_row=np.empty(info.n_rows, np.int32),
+             lrowptr=np.empty(info.n_rows + 1, np.int32), lcol=np.empty(info.nnz_l, np.int32),
+             level=np.empty(info.n_rows, np.int32), bridge=np.empty(grid.n_branch, np.uint8))
+    _check(lib, lib.gpcg_analyze(C.byref(g), precond, which, C.byref(info),
+                                 *[_ptr(d[k]) for k in ("bus_order", "bus_of_row", "lrowptr",
+                                                         "lcol", "level", "bridge")]))
+    d["info"] = {k: getattr(info, k) for k, _ in info._fields_}
+    return d
 
 
 def default_options(**kw) -> Options:

@@ -424,20 +424,13 @@ static void destroy(gpcg_ctx* c) {
 
 extern "C" void gpcg_destroy(gpcg_ctx* c) { destroy(c); }
 
-extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, gpcg_ctx** out) {
-  if (!out) return fail(GPCG_ERR_INVALID_ARG, "gpcg_create: out is NULL");
-  *out = nullptr;
-  if (!g) return fail(GPCG_ERR_INVALID_ARG, "gpcg_create: grid is NULL");
+// Checks a grid; on success *slack_out is the slack bus.
+static gpcg_status validate_grid(const gpcg_grid* g, int* slack_out) {
   const int n = g->n_bus, m = g->n_branch;
   if (n < 2 || m < 1) return fail(GPCG_ERR_INVALID_ARG, "need n_bus >= 2 and n_branch >= 1");
   if (!g->bus_type || !g->P_sched || !g->Q_sched || !g->P_gen || !g->V_set || !g->from ||
       !g->to || !g->r || !g->x || !g->b_sh || !g->rating)
-    return fail(GPCG_ERR_INVALID_ARG, "gpcg_create: a grid array is NULL");
-  gpcg_options o;
-  gpcg_default_options(&o);
-  if (opt) o = *opt;
-  gpcg_status st = check_options(o);
-  if (st != GPCG_OK) return st;
+    return fail(GPCG_ERR_INVALID_ARG, "a grid array is NULL");
   int slack = -1;
   for (int b = 0; b < n; ++b) {
     int bt = g->bus_type[b];
@@ -459,6 +452,23 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
         !std::isfinite(g->r[e]) || !std::isfinite(g->b_sh[e]) || !(g->rating[e] > 0))
       return fail(GPCG_ERR_INVALID_ARG, "branch %d: needs x > 0, r >= 0, rating > 0", e);
   }
+  *slack_out = slack;
+  return GPCG_OK;
+}
+
+extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, gpcg_ctx** out) {
+  if (!out) return fail(GPCG_ERR_INVALID_ARG, "gpcg_create: out is NULL");
+  *out = nullptr;
+  if (!g) return fail(GPCG_ERR_INVALID_ARG, "gpcg_create: grid is NULL");
+  const int n = g->n_bus, m = g->n_branch;
+  gpcg_options o;
+  gpcg_default_options(&o);
+  if (opt) o = *opt;
+  gpcg_status st = check_options(o);
+  if (st != GPCG_OK) return st;
+  int slack = -1;
+  st = validate_grid(g, &slack);
+  if (st != GPCG_OK) return st;
   gpcg_ctx* c = new gpcg_ctx();
   c->opt = o;
   c->n = n;
@@ -1208,6 +1218,56 @@ extern "C" gpcg_status gpcg_last_timings(gpcg_ctx* c, float* ms) {
   CUDA_TRY(cudaEventSynchronize(c->ev[2]));
   CUDA_TRY(cudaEventElapsedTime(&ms[0], c->ev[0], c->ev[1]));
   CUDA_TRY(cudaEventElapsedTime(&ms[1], c->ev[1], c->ev[2]));
+  g_err.clear();
+  return GPCG_OK;
+}
+
+extern "C" gpcg_status gpcg_analyze(const gpcg_grid* g, int32_t precond, int32_t which,
+                                    gpcg_plan_info* info, int32_t* bus_order,
+                                    int32_t* bus_of_row, int32_t* lrowptr, int32_t* lcol,
+                                    int32_t* level, uint8_t* bridge) {
+  if (!g || !info) return fail(GPCG_ERR_INVALID_ARG, "gpcg_analyze: NULL argument");
+  if (precond < 0 || precond > 2) return fail(GPCG_ERR_INVALID_ARG, "precond must be 0, 1 or 2");
+  if (which != 0 && which != 1) return fail(GPCG_ERR_INVALID_ARG, "which must be 0 or 1");
+  int slack = -1;
+  gpcg_status st = validate_grid(g, &slack);
+  if (st != GPCG_OK) return st;
+  const int n = g->n_bus, m = g->n_branch;
+  // the same steps as gpcg_create: internal numbering, bus graph, depth-first
+  // numbering, matrix plan
+  const std::vector<int32_t> U = rcm_order(n, build_bus_graph(n, m, g->from, g->to));
+  std::vector<int32_t> I(n);
+  for (int k = 0; k < n; ++k) I[U[k]] = k;
+  std::vector<int32_t> f_i(m), t_i(m);
+  for (int e = 0; e < m; ++e) {
+    f_i[e] = I[g->from[e]];
+    t_i[e] = I[g->to[e]];
+  }
+  const BusGraph bg = build_bus_graph(n, m, f_i.data(), t_i.data());
+  std::vector<int32_t> pre, sub;
+  std::vector<uint8_t> br;
+  if (!dfs_numbering(n, bg, I[slack], pre, sub, br, m))
+    return fail(GPCG_ERR_BASE_ISLANDED, "the intact grid is not connected");
+  std::vector<uint8_t> keep(n);
+  for (int k = 0; k < n; ++k) {
+    const int bt = g->bus_type[U[k]];
+    keep[k] = which == 0 ? bt != GPCG_SLACK : bt == GPCG_PQ;
+  }
+  const MatrixPlan P = plan_matrix(n, bg, keep, precond == GPCG_PRECOND_EXACT);
+  info->n_rows = P.n;
+  info->nnz_a = P.A.nnz();
+  info->nnz_l = P.L.nnz();
+  info->levels = (int)P.lev_ptr.size() - 1;
+  info->blevels = (int)P.blev_ptr.size() - 1;
+  info->n_bridges = 0;
+  for (int e = 0; e < m; ++e) info->n_bridges += br[e];
+  if (bus_order) std::memcpy(bus_order, U.data(), (size_t)n * 4);
+  if (bus_of_row)
+    for (int i = 0; i < P.n; ++i) bus_of_row[i] = U[P.bus_of_row[i]];
+  if (lrowptr) std::memcpy(lrowptr, P.L.ptr.data(), P.L.ptr.size() * 4);
+  if (lcol) std::memcpy(lcol, P.L.idx.data(), P.L.idx.size() * 4);
+  if (level) std::memcpy(level, P.level.data(), (size_t)P.n * 4);
+  if (bridge) std::memcpy(bridge, br.data(), (size_t)m);
   g_err.clear();
   return GPCG_OK;
 }
