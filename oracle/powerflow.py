@@ -20,8 +20,8 @@ FDPF (eqs. (4)-(5), Sec. III.B): starting from a given state, repeat
   solve B'' dV = dQ/V, V += dV.
 The paper gives no stopping rule for a diverging case; here a run is
 declared diverged when the mismatch is not finite, exceeds DIVERGE_LIMIT, or
-has grown to DIVERGE_GROWTH times the smallest value it reached (the
-iteration has left its basin of convergence).
+(for warm-started scenarios) has grown to DIVERGE_GROWTH times the smallest
+value it reached (the iteration has left its basin of convergence).
 Every solve here is direct (re-formed, fully factorised matrix), so the
 result is the exact AC solution up to the tolerance.
 
@@ -149,7 +149,7 @@ def branch_flows(f, t, r, x, in_service, theta, V):
     return np.where(on, Pf, 0.0), np.where(on, Pt, 0.0)
 
 
-def fdpf(grid, in_service, active, P_sched, theta0, V0, tol, max_outer):
+def fdpf(grid, in_service, active, P_sched, theta0, V0, tol, max_outer, growth_rule=True):
     """Fast-decoupled power flow on the buses marked ``active``.
 
     ``active`` excludes islanded buses (they keep theta = V = 0).  Returns
@@ -173,7 +173,8 @@ def fdpf(grid, in_service, active, P_sched, theta0, V0, tol, max_outer):
     while True:
         dP, dQ = mismatch(ybus, P_sched, Q_sched, theta, V)
         err = max(np.abs(dP[pvpq]).max(initial=0.0), np.abs(dQ[pq]).max(initial=0.0))
-        if not np.isfinite(err) or err > DIVERGE_LIMIT or err > DIVERGE_GROWTH * best:
+        if (not np.isfinite(err) or err > DIVERGE_LIMIT
+                or (growth_rule and err > DIVERGE_GROWTH * best)):
             return theta, V, k, STATUS_DIVERGED, err
         best = min(best, err)
         if err <= tol:
@@ -187,9 +188,11 @@ def fdpf(grid, in_service, active, P_sched, theta0, V0, tol, max_outer):
 
 
 def base_case(grid, tol=1e-10, max_outer=100):
-    """FDPF of the intact grid from a flat start (theta = 0, |V| = V_set)."""
+    """FDPF of the intact grid from a flat start (theta = 0, |V| = V_set).
+    A flat start may pass through large mismatches on its way, so the growth
+    rule for divergence is not applied here (only the absolute limit)."""
     n = grid.n_bus
     on = np.ones(grid.n_branch, dtype=bool)
     active = np.ones(n, dtype=bool)
     return fdpf(grid, on, active, grid.P_sched.astype(np.float64), np.zeros(n),
-                grid.V_set.astype(np.float64), tol, max_outer)
+                grid.V_set.astype(np.float64), tol, max_outer, growth_rule=False)

@@ -142,23 +142,33 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
   }
 }
 
-// (cos, sin) of theta + d from those of theta: for |d| <= 0.05 the
-// rotation by d uses the Taylor series of sin d and cos d (truncation below
-// 1e-21), else the angle is recomputed.
+// (cos, sin) of theta + d from those of theta, by rotating through d.  The
+// sine and cosine of d come from their Taylor series: two and three terms
+// for |d| <= 0.005 (remainders d^5/120 and d^6/720 below 3e-14), five up to
+// 0.05 (remainders below 1e-21); larger steps recompute the angle.  Most increments of an
+// N-1 scenario are tiny (the outage moves few angles much), so the short form
+// is the common case and saves most of the FP64 work of the update.
 __device__ __forceinline__ void rotate(double th_new, double d, double& c, double& s) {
-  if (fabs(d) <= 0.05) {
+  const double ad = fabs(d);
+  double sd, cd;
+  if (ad <= 0.005) {
+    const double d2 = d * d;
+    sd = d - d * d2 * (1.0 / 6.0);
+    cd = 1.0 - d2 * (0.5 - d2 * (1.0 / 24.0));
+  } else if (ad <= 0.05) {
     // nested Horner forms of the series; 1/k! ratios as multiplications
     const double d2 = d * d;
-    const double sd = d * (1.0 - d2 * (1.0 / 6.0) * (1.0 - d2 * (1.0 / 20.0) *
+    sd = d * (1.0 - d2 * (1.0 / 6.0) * (1.0 - d2 * (1.0 / 20.0) *
                                    (1.0 - d2 * (1.0 / 42.0) * (1.0 - d2 * (1.0 / 72.0)))));
-    const double cd = 1.0 - d2 * 0.5 * (1.0 - d2 * (1.0 / 12.0) * (1.0 - d2 * (1.0 / 30.0) *
+    cd = 1.0 - d2 * 0.5 * (1.0 - d2 * (1.0 / 12.0) * (1.0 - d2 * (1.0 / 30.0) *
                                    (1.0 - d2 * (1.0 / 56.0) * (1.0 - d2 * (1.0 / 90.0)))));
-    const double cn = c * cd - s * sd, sn = s * cd + c * sd;
-    c = cn;
-    s = sn;
   } else {
     sincos(th_new, &s, &c);
+    return;
   }
+  const double cn = c * cd - s * sd, sn = s * cd + c * sd;
+  c = cn;
+  s = sn;
 }
 
 // theta += dtheta (P half-step) or |V| += dV (Q half-step) on the matrix's
@@ -435,7 +445,9 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS) fdpf_tiles_kernel(F
         const double e2 = (a != a || b != b) ? INFINITY : fmax(a, b);
         L.err[ln] = e2;
         int st = -1;
-        if (!(e2 <= DIVERGE_LIMIT) || e2 > DIVERGE_GROWTH * L.best[ln]) st = 2;
+        // growth rule only for warm-started scenarios: a flat start may pass
+        // through large mismatches on its way
+        if (!(e2 <= DIVERGE_LIMIT) || (!P.flat_start && e2 > DIVERGE_GROWTH * L.best[ln])) st = 2;
         else if (e2 <= P.tol) st = 0;
         else if (L.outer[ln] >= P.max_outer) st = 1;
         L.best[ln] = fmin(L.best[ln], e2);

@@ -332,7 +332,7 @@ def test_redispatch_conserves_main_island_injection():
     assert seen > 0
 
 
-@pytest.mark.parametrize("name", ["grid120", "grid2k", "grid10k"])
+@pytest.mark.parametrize("name", ["grid120", "grid2k", "grid10k", "grid50k"])
 def test_base_case_converges(name):
     g = config_grid(name)
     th, V, k, st, err = pf.base_case(g)
