@@ -124,7 +124,8 @@ def run_gpcg(args):
     from gridgen import config_grid
 
     g = config_grid(args.config)
-    prec = {"fp32": gp.BATCHED_FP32, "fp64": gp.BATCHED_FP64}[args.precision]
+    prec = {"fp32": gp.BATCHED_FP32, "fp64": gp.BATCHED_FP64,
+            "fp16f": gp.BATCHED_FP32_F16}[args.precision]
     pc = {"exact": gp.PRECOND_EXACT, "ic0": gp.PRECOND_IC0, "jacobi": gp.PRECOND_JACOBI}[args.precond]
     c = gp.GPCG(g, precision=prec, precond=pc, tol=1e-4, tile=args.tile)
     c.base_solve()
@@ -197,7 +198,7 @@ def run_gpcg(args):
                  "sample": f"{args.plain_sample} seeded outages of {args.config}, FP64, one scenario per launch"}
         c.set_options(precision=prec)
 
-    w = 4 if prec == gp.BATCHED_FP32 else 8
+    w = 8 if prec == gp.BATCHED_FP64 else 4
     algo = algorithmic_bytes(info, iters, w, n, m)
     fd_ms = statistics.mean(k[1] for k in kern_ms)
     peak, peak_kind = load_peaks()
@@ -297,7 +298,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpcg", choices=["gpcg", "reference"])
     ap.add_argument("--config", default=WORKLOAD)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16f"],
+                    help="inner PCG: FP32, FP64, or FP32 vectors with a scaled FP16 factor")
     ap.add_argument("--precond", default="exact", choices=["exact", "ic0", "jacobi"])
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--n-outages", type=int, default=0, help="screen only the first K outages (0 = all)")

@@ -73,7 +73,10 @@ enum {
                              unbatched comparison path */
   GPCG_BATCHED_FP32 = 1,  /* batched, FP32 vectors and factors; the FP64
                              outer loop acts as iterative refinement */
-  GPCG_BATCHED_FP64 = 2   /* batched, FP64 vectors and factors */
+  GPCG_BATCHED_FP64 = 2,  /* batched, FP64 vectors and factors */
+  GPCG_BATCHED_FP32_F16 = 3 /* batched, FP32 vectors; the base-case factor
+                               stored scaled to a unit diagonal in FP16
+                               (L = Ls D, Ls in FP16, D^-2 in FP32) */
 };
 
 /* Preconditioner built from the base-case matrix (Sec. IV.B, eq. (6)). */
@@ -222,8 +225,9 @@ GPCG_API gpcg_status gpcg_n1_adjoint(gpcg_ctx *ctx, const int32_t *outages, int3
  *           four-element change (Sec. IV.B) applied on the fly.
  *   op = 1: Y = M^{-1} X with the base-case preconditioner (eq. (6)):
  *           level-scheduled forward and backward substitution.
- * precision: GPCG_BATCHED_FP32 (vectors and factors in FP32) or
- * GPCG_BATCHED_FP64.  X, Y are [S][rows] FP64 host arrays.  Synchronous. */
+ * precision: GPCG_BATCHED_FP32 (vectors and factors in FP32),
+ * GPCG_BATCHED_FP64, or GPCG_BATCHED_FP32_F16 (scaled FP16 factor).
+ * X, Y are [S][rows] FP64 host arrays.  Synchronous. */
 GPCG_API gpcg_status gpcg_apply(gpcg_ctx *ctx, int32_t which, int32_t op,
                        const int32_t *outages, int32_t S, int32_t precision,
                        const double *X, double *Y);

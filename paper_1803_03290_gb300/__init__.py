@@ -4,7 +4,7 @@ fast-decoupled power flow of every single-branch outage.
 The compute path is the CUDA library ``libgpcg.so`` (C ABI in
 ``include/gpcg.h``); this package is its thin Python binding.
 """
-from .binding import (BATCHED_FP32, BATCHED_FP64, GPCG, PLAIN_FP64, PRECOND_EXACT,
+from .binding import (BATCHED_FP32, BATCHED_FP32_F16, BATCHED_FP64, GPCG, PLAIN_FP64, PRECOND_EXACT,
                       PRECOND_IC0, PRECOND_JACOBI, GPCGError, default_options, load)
 
 def overload_loss(solver, outages, P, b):
@@ -13,5 +13,5 @@ def overload_loss(solver, outages, P, b):
     return N1OverloadLoss.apply(solver, outages, P, b)
 
 
-__all__ = ["overload_loss", "GPCG", "GPCGError", "default_options", "load", "PLAIN_FP64", "BATCHED_FP32",
+__all__ = ["overload_loss", "BATCHED_FP32_F16", "GPCG", "GPCGError", "default_options", "load", "PLAIN_FP64", "BATCHED_FP32",
            "BATCHED_FP64", "PRECOND_IC0", "PRECOND_JACOBI", "PRECOND_EXACT"]

@@ -16,7 +16,7 @@ from . import _build
 GPCG_OK = 0
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "BASE_NOT_CONVERGED", 4: "BASE_ISLANDED",
           5: "TIMEOUT", 6: "OOM", 7: "NOT_READY"}
-PLAIN_FP64, BATCHED_FP32, BATCHED_FP64 = 0, 1, 2
+PLAIN_FP64, BATCHED_FP32, BATCHED_FP64, BATCHED_FP32_F16 = 0, 1, 2, 3
 PRECOND_IC0, PRECOND_JACOBI, PRECOND_EXACT = 0, 1, 2
 SCEN_OK, SCEN_MAXITER, SCEN_DIVERGED, SCEN_ISLAND_NO_GEN = 0, 1, 2, 3
 

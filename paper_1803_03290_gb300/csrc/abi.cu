@@ -33,6 +33,9 @@ void launch_to_float(cudaStream_t, int, const double*, float*);
 void launch_gather_diag(cudaStream_t, int, const int32_t*, const double*, double*);
 void launch_gather_int(cudaStream_t, int, const int32_t*, const int32_t*, int32_t*);
 void launch_gather_val(cudaStream_t, int, const int32_t*, const double*, double*, float*);
+void launch_scale_factor(cudaStream_t, int, const int32_t*, const int32_t*, const double*, double*,
+                         double*, float*);
+void launch_gather_half(cudaStream_t, int, const int32_t*, const double*, __half*);
 void launch_inv_diag(cudaStream_t, int, const int32_t*, const double*, double*, float*);
 void launch_adj_values(cudaStream_t, int, const int32_t*, const double*, const double*, double*,
                        double*);
@@ -81,6 +84,7 @@ struct EllDev {
   float* val32 = nullptr;
   double* oval = nullptr;
   float* oval32 = nullptr;
+  __half *valh = nullptr, *ovalh = nullptr;  // scaled factor values in FP16 (L, U only)
   int nslot = 0, nover = 0;
   template <typename VT>
   Ell<VT> view() const;
@@ -98,14 +102,16 @@ struct MatDev {
   int32_t *lev_ptr = nullptr, *blev_ptr = nullptr, *blev_rows = nullptr;
   double *a_val = nullptr, *l_val = nullptr, *diag = nullptr, *inv_diag = nullptr;
   float *diag32 = nullptr, *inv_diag32 = nullptr;
+  double *lsc = nullptr, *inv_d2 = nullptr;  // scaled factor (FP64) and 1 / L_ii^2
+  float* inv_d2_32 = nullptr;
   EllDev A, L, U;
   double* w = nullptr;  // per-branch weight
   template <typename VT>
-  DevMatT<VT> view() const;
+  DevMatT<VT> view(bool f16 = false) const;
 };
 
 template <>
-DevMatT<double> MatDev::view<double>() const {
+DevMatT<double> MatDev::view<double>(bool) const {
   DevMatT<double> M;
   M.n = plan.n;
   M.bus_of_row = bus_of_row; M.row_of_bus = row_of_bus; M.pre_of_row = pre_of_row;
@@ -120,7 +126,7 @@ DevMatT<double> MatDev::view<double>() const {
   return M;
 }
 template <>
-DevMatT<float> MatDev::view<float>() const {
+DevMatT<float> MatDev::view<float>(bool f16) const {
   DevMatT<float> M;
   M.n = plan.n;
   M.bus_of_row = bus_of_row; M.row_of_bus = row_of_bus; M.pre_of_row = pre_of_row;
@@ -128,6 +134,10 @@ DevMatT<float> MatDev::view<float>() const {
   M.A = A.view<float>(); M.L = L.view<float>(); M.U = U.view<float>();
   M.inv_diag = inv_diag32;
   M.diag = diag32;
+  if (f16) {
+    M.Lh = L.valh; M.Loh = L.ovalh; M.Uh = U.valh; M.Uoh = U.ovalh;
+    M.inv_d2 = inv_d2_32;
+  }
   M.lev_ptr = lev_ptr; M.blev_ptr = blev_ptr; M.blev_rows = blev_rows;
   M.nlev = (int)plan.lev_ptr.size() - 1;
   M.nblev = (int)plan.blev_ptr.size() - 1;
@@ -228,8 +238,10 @@ static gpcg_status check_options(const gpcg_options& o) {
     return fail(GPCG_ERR_INVALID_ARG, "tolerances must be positive (inner_rtol < 1)");
   if (o.max_outer < 1 || o.max_inner < 1)
     return fail(GPCG_ERR_INVALID_ARG, "max_outer and max_inner must be >= 1");
-  if (o.precision < 0 || o.precision > 2)
-    return fail(GPCG_ERR_INVALID_ARG, "precision must be 0, 1 or 2");
+  if (o.precision < 0 || o.precision > 3)
+    return fail(GPCG_ERR_INVALID_ARG, "precision must be 0, 1, 2 or 3");
+  if (o.precision == GPCG_BATCHED_FP32_F16 && o.precond == GPCG_PRECOND_JACOBI)
+    return fail(GPCG_ERR_INVALID_ARG, "FP16 factors need a factor preconditioner (IC0 or EXACT)");
   if (o.precond < 0 || o.precond > 2)
     return fail(GPCG_ERR_INVALID_ARG, "precond must be 0, 1 or 2");
   if (!(o.tile == 0 || o.tile == 2 || o.tile == 4 || o.tile == 8 || o.tile == 16 || o.tile == 32))
@@ -313,6 +325,14 @@ static gpcg_status fill_values(gpcg_ctx* c, MatDev& M, const double* w) {
   ell_fill(st, M.A, M.a_val);
   ell_fill(st, M.L, M.l_val);
   ell_fill(st, M.U, M.l_val);
+  if (M.lsc) {
+    launch_scale_factor(st, P.n, M.l_ptr, M.l_idx, M.l_val, M.lsc, M.inv_d2, M.inv_d2_32);
+    for (EllDev* E : {&M.L, &M.U}) {
+      if (!E->valh) continue;
+      launch_gather_half(st, E->nslot, E->src, M.lsc, E->valh);
+      launch_gather_half(st, E->nover, E->osrc, M.lsc, E->ovalh);
+    }
+  }
   CUDA_TRY(cudaGetLastError());
   int32_t herr = 0;
   CUDA_TRY(cudaMemcpy(&herr, c->d_err, sizeof herr, cudaMemcpyDeviceToHost));
@@ -358,6 +378,9 @@ static gpcg_status build_matrix(gpcg_ctx* c, MatDev& M, const std::vector<uint8_
   CUDA_TRY(dalloc(own, &M.diag32, P.n));
   CUDA_TRY(dalloc(own, &M.inv_diag, P.n));
   CUDA_TRY(dalloc(own, &M.inv_diag32, P.n));
+  CUDA_TRY(dalloc(own, &M.lsc, nl));
+  CUDA_TRY(dalloc(own, &M.inv_d2, P.n));
+  CUDA_TRY(dalloc(own, &M.inv_d2_32, P.n));
   // padded rows: A (all entries), strictly lower L, strictly upper L^T
   {
     std::vector<std::vector<std::pair<int, int>>> ra(P.n), rl(P.n), ru(P.n);
@@ -372,6 +395,10 @@ static gpcg_status build_matrix(gpcg_ctx* c, MatDev& M, const std::vector<uint8_
     CUDA_TRY(ell_upload(own, ell_from_rows(ra, KA, P.n), M.A));
     CUDA_TRY(ell_upload(own, ell_from_rows(rl, KL, P.n), M.L));
     CUDA_TRY(ell_upload(own, ell_from_rows(ru, KU, P.n), M.U));
+    for (EllDev* E : {&M.L, &M.U}) {
+      CUDA_TRY(dalloc(own, &E->valh, E->nslot));
+      CUDA_TRY(dalloc(own, &E->ovalh, E->nover));
+    }
   }
   M.w = w;
   return fill_values(c, M, w);
@@ -723,7 +750,8 @@ static Layout make_layout(const gpcg_ctx* c, int T, int slots, size_t vt_size) {
 }
 
 template <typename VT>
-static gpcg_status run_fdpf(gpcg_ctx* c, cudaStream_t st, FdpfParams P, int T, int slots) {
+static gpcg_status run_fdpf(gpcg_ctx* c, cudaStream_t st, FdpfParams P, int T, int slots,
+                            bool f16 = false) {
   Layout Lo = make_layout(c, T, slots, sizeof(VT));
   gpcg_status s = ensure_work(c, Lo.bytes);
   if (s != GPCG_OK) return s;
@@ -739,7 +767,7 @@ static gpcg_status run_fdpf(gpcg_ctx* c, cudaStream_t st, FdpfParams P, int T, i
   P.sstride = ss;
   P.tile_counter = c->d_counter;
   CUDA_TRY(cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), st));
-  CUDA_TRY(launch_fdpf<VT>(st, T, slots, P, c->MP.view<VT>(), c->MQ.view<VT>()));
+  CUDA_TRY(launch_fdpf<VT>(st, T, slots, P, c->MP.view<VT>(f16), c->MQ.view<VT>(f16)));
   return GPCG_OK;
 }
 
@@ -934,7 +962,8 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
     const int T = c->opt.tile ? c->opt.tile : (c->tile ? c->tile : 2);
     c->tile = T;
     const int n_tiles = (int)((S + T - 1) / T);
-    const bool f32 = c->opt.precision == GPCG_BATCHED_FP32;
+    const bool f16 = c->opt.precision == GPCG_BATCHED_FP32_F16;
+    const bool f32 = c->opt.precision == GPCG_BATCHED_FP32 || f16;
     int per_sm = c->opt.ctas_per_sm;
     if (per_sm == 0) per_sm = f32 ? fdpf_max_blocks_per_sm<float>(T) : fdpf_max_blocks_per_sm<double>(T);
     per_sm = std::max(per_sm, 1);
@@ -942,7 +971,7 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
     P.S = (int)S;
     P.n_tiles = n_tiles;
     P.order = c->d_order;
-    rs = f32 ? run_fdpf<float>(c, st, P, T, slots) : run_fdpf<double>(c, st, P, T, slots);
+    rs = f32 ? run_fdpf<float>(c, st, P, T, slots, f16) : run_fdpf<double>(c, st, P, T, slots);
   }
   if (rs != GPCG_OK) { cleanup(); return rs; }
   CUDA_TRY(cudaEventRecord(c->ev[2], st));
@@ -989,6 +1018,8 @@ static gpcg_status ensure_adj_matrix(gpcg_ctx* c) {
   if (c->ma_ready) return GPCG_OK;
   MatDev& M = c->MA;
   M = c->MP;  // structure shared; values replaced below
+  M.lsc = nullptr;  // the adjoint solves in FP64: no scaled FP16 factor
+  M.L.valh = M.L.ovalh = M.U.valh = M.U.ovalh = nullptr;
   auto& own = c->adj_owned;
   const int n = M.plan.n, nnz = M.plan.A.nnz(), nl = M.plan.L.nnz();
   CUDA_TRY(dalloc(own, &M.a_val, nnz));
@@ -1153,15 +1184,16 @@ extern "C" gpcg_status gpcg_apply(gpcg_ctx* c, int32_t which, int32_t op, const 
     return fail(GPCG_ERR_INVALID_ARG, "gpcg_apply: NULL argument or S < 0");
   if ((which != 0 && which != 1) || (op != 0 && op != 1))
     return fail(GPCG_ERR_INVALID_ARG, "gpcg_apply: which and op must be 0 or 1");
-  if (precision != GPCG_BATCHED_FP32 && precision != GPCG_BATCHED_FP64)
-    return fail(GPCG_ERR_INVALID_ARG, "gpcg_apply: precision must be 1 or 2");
+  if (precision != GPCG_BATCHED_FP32 && precision != GPCG_BATCHED_FP64 &&
+      precision != GPCG_BATCHED_FP32_F16)
+    return fail(GPCG_ERR_INVALID_ARG, "gpcg_apply: precision must be 1, 2 or 3");
   if (S == 0) { g_err.clear(); return GPCG_OK; }
   for (int s = 0; s < S; ++s)
     if (outages[s] < -1 || outages[s] >= c->m)
       return fail(GPCG_ERR_INVALID_ARG, "gpcg_apply: outage %d out of range", outages[s]);
   const MatDev& M = which ? c->MQ : c->MP;
   const int rows = M.plan.n;
-  const size_t vt = precision == GPCG_BATCHED_FP32 ? 4 : 8;
+  const size_t vt = precision == GPCG_BATCHED_FP64 ? 8 : 4;
   const int T = 32;
   const int grid = std::max(1, std::min((S + T - 1) / T, c->num_sms * 2));
   const size_t vstride = (size_t)(rows + 1) * T;
@@ -1177,7 +1209,8 @@ extern "C" gpcg_status gpcg_apply(gpcg_ctx* c, int32_t which, int32_t op, const 
   if (ce == cudaSuccess) ce = cudaMemcpy(dX, X, (size_t)S * rows * 8, cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) {
     if (vt == 4)
-      ce = launch_apply<float>(0, grid, M.view<float>(), op, S, d_out, c->G.f, c->G.t, dX, dY,
+      ce = launch_apply<float>(0, grid, M.view<float>(precision == GPCG_BATCHED_FP32_F16), op, S,
+                               d_out, c->G.f, c->G.t, dX, dY,
                                (float*)wbuf, vstride, c->opt.precond);
     else
       ce = launch_apply<double>(0, grid, M.view<double>(), op, S, d_out, c->G.f, c->G.t, dX, dY,
@@ -1280,8 +1313,9 @@ namespace gpcg {
 bool ctx_view(const gpcg_ctx* c, CtxView* v) {
   if (!c || !v) return false;
   v->G = c->G;
-  v->MPf = c->MP.view<float>();
-  v->MQf = c->MQ.view<float>();
+  const bool f16 = c->opt.precision == GPCG_BATCHED_FP32_F16;
+  v->MPf = c->MP.view<float>(f16);
+  v->MQf = c->MQ.view<float>(f16);
   v->MPd = c->MP.view<double>();
   v->MQd = c->MQ.view<double>();
   v->th0 = c->th0;

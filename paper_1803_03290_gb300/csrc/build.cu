@@ -247,3 +247,42 @@ void launch_adj_values(cudaStream_t st, int n, const int32_t* br, const double* 
 }
 
 }  // namespace gpcg
+
+namespace gpcg {
+
+// Scaled factor for FP16 storage: L = Ls D, D = diag(L); Ls_ij = L_ij / L_jj
+// (unit diagonal), and 1 / L_ii^2 for the back substitution.
+__global__ void scale_factor_kernel(int n, const int32_t* __restrict__ l_ptr,
+                                    const int32_t* __restrict__ l_idx,
+                                    const double* __restrict__ l_val, double* lsc, double* inv_d2,
+                                    float* inv_d2_32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int k = l_ptr[i]; k < l_ptr[i + 1]; ++k) {
+    const int j = l_idx[k];
+    lsc[k] = l_val[k] / l_val[l_ptr[j + 1] - 1];
+  }
+  const double d = l_val[l_ptr[i + 1] - 1];
+  inv_d2[i] = 1.0 / (d * d);
+  inv_d2_32[i] = (float)(1.0 / (d * d));
+}
+
+__global__ void gather_half_kernel(int n, const int32_t* __restrict__ src,
+                                   const double* __restrict__ v, __half* dst) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int s = src[k];
+  dst[k] = __double2half(s >= 0 ? v[s] : 0.0);
+}
+
+void launch_scale_factor(cudaStream_t st, int n, const int32_t* l_ptr, const int32_t* l_idx,
+                         const double* l_val, double* lsc, double* inv_d2, float* inv_d2_32) {
+  if (n > 0)
+    scale_factor_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, l_ptr, l_idx, l_val, lsc, inv_d2,
+                                                         inv_d2_32);
+}
+void launch_gather_half(cudaStream_t st, int n, const int32_t* src, const double* v, __half* dst) {
+  if (n > 0) gather_half_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, src, v, dst);
+}
+
+}  // namespace gpcg

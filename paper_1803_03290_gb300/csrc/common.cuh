@@ -1,5 +1,6 @@
 // Shared device-side definitions of the GB300 N-1 screen.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -55,6 +56,10 @@ struct DevMatT {
   const int32_t* visit = nullptr;            // rows in bus order (SpMV, p update)
   Ell<VT> A, L, U;
   const VT* inv_diag = nullptr;              // 1 / L_ii
+  // optional scaled FP16 factor: L = Ls D with D = diag(L), Ls unit lower;
+  // when set, the substitutions use Ls (values here) and 1 / L_ii^2
+  const __half *Lh = nullptr, *Loh = nullptr, *Uh = nullptr, *Uoh = nullptr;
+  const VT* inv_d2 = nullptr;
   const VT* diag = nullptr;                  // A_ii (Jacobi)
   const int32_t *lev_ptr = nullptr;          // forward levels (contiguous rows)
   const int32_t *blev_ptr = nullptr, *blev_rows = nullptr;

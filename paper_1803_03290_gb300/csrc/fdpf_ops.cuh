@@ -78,6 +78,23 @@ __device__ __forceinline__ void ld_vals(const double* p, double (&v)[K]) {
   }
 }
 
+template <int K>
+__device__ __forceinline__ void ld_halfs(const __half* p, float (&v)[K]) {
+#pragma unroll
+  for (int k = 0; k < K; k += 2) {
+    const __half2 h = __ldg(reinterpret_cast<const __half2*>(p + k));
+    const float2 f = __half22float2(h);
+    v[k] = f.x; v[k + 1] = f.y;
+  }
+}
+template <int K>
+__device__ __forceinline__ void ld_halfs(const __half* p, double (&v)[K]) {
+  float f[K];
+  ld_halfs<K>(p, f);
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = f[k];
+}
+
 // ------------------------------------------------------------ lane state
 template <int T>
 struct LaneState {
@@ -259,7 +276,8 @@ __device__ __forceinline__ Pair<double> fwd_pass(const DevMatT<VT>& M, VT* __res
         const int i = i0 + u * RPS;
         if (i < r1) {
           const size_t o = (size_t)i * T + g.lane;
-          ld_vals<KL>(M.L.val + (size_t)i * KL, v[u]);
+          if (M.Lh) ld_halfs<KL>(M.Lh + (size_t)i * KL, v[u]);
+          else ld_vals<KL>(M.L.val + (size_t)i * KL, v[u]);
 #pragma unroll
           for (int k = 0; k < KL; ++k) zc[u][k] = ld2(z + (size_t)c[u][k] * T + g.lane);
           ri[u] = ld2(r + o);
@@ -294,12 +312,13 @@ __device__ __forceinline__ Pair<double> fwd_pass(const DevMatT<VT>& M, VT* __res
         }
         const int o0 = __ldg(M.L.optr + i), o1 = __ldg(M.L.optr + i + 1);
         for (int e = o0; e < o1; ++e) {
-          const VT vv = __ldg(M.L.oval + e);
+          const VT vv = M.Lh ? (VT)__half2float(M.Loh[e]) : __ldg(M.L.oval + e);
           const Pair<VT> zz = ld2(z + (size_t)__ldg(M.L.ocol + e) * T + g.lane);
           a0 -= vv * zz.a;
           a1 -= vv * zz.b;
         }
-        const VT id = __ldg(M.inv_diag + i);
+        // scaled factor: unit diagonal, w = D y is what is stored
+        const VT id = M.Lh ? (VT)1 : __ldg(M.inv_diag + i);
         st2(z + o, Pair<VT>{a0 * id, a1 * id});
       }
     }
@@ -346,7 +365,8 @@ __device__ __forceinline__ Pair<double> bwd_pass(const DevMatT<VT>& M, const VT*
       for (int u = 0; u < UNR; ++u) {
         if (k0 + u * RPS < r1) {
           const size_t o = (size_t)ii[u] * T + g.lane;
-          ld_vals<KU>(M.U.val + (size_t)ii[u] * KU, v[u]);
+          if (M.Uh) ld_halfs<KU>(M.Uh + (size_t)ii[u] * KU, v[u]);
+          else ld_vals<KU>(M.U.val + (size_t)ii[u] * KU, v[u]);
 #pragma unroll
           for (int k = 0; k < KU; ++k) zc[u][k] = ld2(z + (size_t)c[u][k] * T + g.lane);
           yi[u] = ld2(z + o);
@@ -358,7 +378,9 @@ __device__ __forceinline__ Pair<double> bwd_pass(const DevMatT<VT>& M, const VT*
         if (k0 + u * RPS >= r1) continue;
         const int i = ii[u];
         const size_t o = (size_t)i * T + g.lane;
-        VT a0 = yi[u].a, a1 = yi[u].b;
+        // scaled factor: L_s^T z = D^-2 w with a unit diagonal
+        const VT pre = M.Uh ? __ldg(M.inv_d2 + i) : (VT)1;
+        VT a0 = yi[u].a * pre, a1 = yi[u].b * pre;
 #pragma unroll
         for (int k = 0; k < KU; ++k) {
           a0 -= v[u][k] * zc[u][k].a;
@@ -366,12 +388,12 @@ __device__ __forceinline__ Pair<double> bwd_pass(const DevMatT<VT>& M, const VT*
         }
         const int o0 = __ldg(M.U.optr + i), o1 = __ldg(M.U.optr + i + 1);
         for (int e = o0; e < o1; ++e) {
-          const VT vv = __ldg(M.U.oval + e);
+          const VT vv = M.Uh ? (VT)__half2float(M.Uoh[e]) : __ldg(M.U.oval + e);
           const Pair<VT> zz = ld2(z + (size_t)__ldg(M.U.ocol + e) * T + g.lane);
           a0 -= vv * zz.a;
           a1 -= vv * zz.b;
         }
-        const VT id = __ldg(M.inv_diag + i);
+        const VT id = M.Uh ? (VT)1 : __ldg(M.inv_diag + i);
         a0 *= id;
         a1 *= id;
         st2(z + o, Pair<VT>{a0, a1});

@@ -77,9 +77,10 @@ extern "C" gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx* ctx, const int32_t* outa
   if (!ctx_view(ctx, &c)) return err(GPCG_ERR_INVALID_ARG, "gpcg_n1_screen_noalloc: ctx is NULL");
   if (n_out < 0) return err(GPCG_ERR_INVALID_ARG, "n_out < 0");
   if (!c.base_ok) return err(GPCG_ERR_NOT_READY, "gpcg_base_solve has not succeeded");
-  if (c.opt.precision != GPCG_BATCHED_FP32 && c.opt.precision != GPCG_BATCHED_FP64)
+  if (c.opt.precision != GPCG_BATCHED_FP32 && c.opt.precision != GPCG_BATCHED_FP64 &&
+      c.opt.precision != GPCG_BATCHED_FP32_F16)
     return err(GPCG_ERR_INVALID_ARG,
-               "gpcg_n1_screen_noalloc runs the batched solve only (precision 1 or 2)");
+               "gpcg_n1_screen_noalloc runs the batched solve only (precision 1, 2 or 3)");
   if (n_out == 0) { set_last_error(""); return GPCG_OK; }
   if (!outages) return err(GPCG_ERR_INVALID_ARG, "outages is NULL");
   cudaStream_t st = (cudaStream_t)stream;
@@ -90,7 +91,7 @@ extern "C" gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx* ctx, const int32_t* outa
   // layout: [counter, error flag] [per-scenario island data] [solve slots]
   const size_t S = (size_t)n_out;
   const int T = c.opt.tile ? c.opt.tile : (c.tile ? c.tile : 2);
-  const bool f32 = c.opt.precision == GPCG_BATCHED_FP32;
+  const bool f32 = c.opt.precision != GPCG_BATCHED_FP64;
   const size_t vt = f32 ? 4 : 8;
   const size_t head = 256;
   const size_t scen = up256(S * 4) * 3 + up256(S * 8);

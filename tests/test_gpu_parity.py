@@ -112,6 +112,29 @@ def test_preconditioner_apply(which, precond):
         assert np.abs(res).max() <= bound
 
 
+def test_preconditioner_apply_fp16_factor():
+    """Scaled FP16 storage: L = Ls D with Ls rounded to FP16.  The GPU's
+    substitutions with FP32 vectors are held to the FP32 backward-error bound
+    of the FP16-rounded factor, rebuilt here from the exported FP64 factor."""
+    import scipy.sparse as sp
+    c = make("grid2k")
+    d = c.export_matrix(0)
+    n = d["bus_of_row"].size
+    rows = np.repeat(np.arange(n), np.diff(d["lrowptr"]))
+    diag = d["lval"][d["lrowptr"][1:] - 1]
+    ls = (d["lval"] / diag[d["lcol"]]).astype(np.float16).astype(np.float64)
+    L16 = sp.csr_matrix((ls * diag[d["lcol"]], d["lcol"], d["lrowptr"]), shape=(n, n))
+    assert np.all(rows >= d["lcol"])
+    outages = np.arange(33, dtype=np.int32)
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((outages.size, n))
+    Y = c.apply(0, 1, outages, X, gp.BATCHED_FP32_F16)
+    for s in range(0, outages.size, 8):
+        res = L16 @ (L16.T @ Y[s]) - X[s]
+        bound = 64 * 6e-8 * (abs(L16) @ (abs(L16.T) @ np.abs(Y[s]))).max()
+        assert np.abs(res).max() <= bound
+
+
 # ------------------------------------------------------------ a3
 @pytest.mark.parametrize("name", ["grid120", "grid2k"])
 def test_base_solve(name):
@@ -138,7 +161,8 @@ def _compare(g, res, ref, outages, angle_tol):
 @pytest.mark.parametrize("precision,precond", [
     (gp.BATCHED_FP64, gp.PRECOND_EXACT), (gp.BATCHED_FP32, gp.PRECOND_EXACT),
     (gp.BATCHED_FP64, gp.PRECOND_IC0), (gp.BATCHED_FP32, gp.PRECOND_IC0),
-    (gp.BATCHED_FP64, gp.PRECOND_JACOBI), (gp.PLAIN_FP64, gp.PRECOND_EXACT)])
+    (gp.BATCHED_FP64, gp.PRECOND_JACOBI), (gp.PLAIN_FP64, gp.PRECOND_EXACT),
+    (gp.BATCHED_FP32_F16, gp.PRECOND_EXACT), (gp.BATCHED_FP32_F16, gp.PRECOND_IC0)])
 def test_n1_grid120_all_outages(precision, precond):
     g = grid("grid120")
     c = make("grid120", precision=precision, precond=precond, tol=1e-10, max_outer=100,
