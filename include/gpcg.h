@@ -114,8 +114,8 @@ typedef struct {
   int32_t max_inner;   /* PCG iteration cap per solve; 500 */
   int32_t precision;   /* GPCG_PLAIN_FP64 / _BATCHED_FP32 / _BATCHED_FP64 */
   int32_t precond;     /* GPCG_PRECOND_*; default GPCG_PRECOND_EXACT */
-  int32_t tile;        /* scenarios per tile: 4, 8, 16 or 32; 0 = chosen by the
-                          library's autotuner on first use */
+  int32_t tile;        /* scenarios per tile: 2, 4, 8, 16 or 32; 0 = chosen by
+                          the library's autotuner on first use */
   int32_t ctas_per_sm; /* resident tiles per SM; 0 = from the occupancy API */
 } gpcg_options;
 
@@ -187,7 +187,18 @@ GPCG_API gpcg_status gpcg_base_solve(gpcg_ctx *ctx, double *theta, double *vm,
  *                                             max(|P_ij|,|P_ji|)/rating
  * n_out may be 0.  An outage index outside [0, n_branch) is INVALID_ARG.
  * Requires a successful gpcg_base_solve (else NOT_READY).  A scenario that
- * fails to converge never fails the call: see status[]. */
+ * fails to converge never fails the call: see status[].
+ *
+ * mem = 0: every pointer is host memory; the call returns with the results
+ * written.  mem = 1: every pointer is device memory; the outage list is read
+ * back to validate it and order the scenarios (a synchronisation of
+ * `stream`), and the call returns once the solve is enqueued on `stream`.
+ * In device mode the islanding and solve launches are captured once as a
+ * CUDA graph, keyed on n_out, the output pointers and the options, and
+ * replayed while that key holds (gpcg_set_options drops it).
+ * With opt.tile = 0 the first batched screen of a context times tiles of
+ * 2, 4 and 8 scenarios on its first min(n_out, 1024) outages and keeps the
+ * fastest for the life of the context (gpcg_info.tile). */
 GPCG_API gpcg_status gpcg_n1_screen(gpcg_ctx *ctx, const int32_t *outages, int32_t n_out,
                            int32_t mem, void *stream, double *theta, double *vm,
                            double *flow, int32_t *island_label, int32_t *iters,

@@ -192,6 +192,10 @@ struct gpcg_ctx {
   size_t adj_acc_bytes = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   bool timed = false;
+  // the screen's launch sequence, captured once per argument set and replayed
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<uintptr_t> graph_key;
   std::vector<void*> owned;  // freed at destroy (structures of the grid)
   std::vector<void*> mat_owned;  // freed when the matrices are rebuilt
 };
@@ -444,6 +448,8 @@ static void destroy(gpcg_ctx* c) {
   if (c->work) cudaFree(c->work);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   cudaFree(c->d_outages); cudaFree(c->d_lo); cudaFree(c->d_cnt); cudaFree(c->d_nogen);
   cudaFree(c->d_coef); cudaFree(c->d_order);
   delete c;
@@ -637,6 +643,8 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
   for (auto& e : c->ev)
     if ((ce = cudaEventCreate(&e)) != cudaSuccess) return fail_cuda(ce, "event");
   AL(c->phase, 8);
+  if ((ce = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return fail_cuda(ce, "stream");
   {
     const char* ev = std::getenv("GPCG_PHASE_TIMERS");
     c->phase_on = ev && ev[0] == '1';
@@ -661,6 +669,12 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
   return GPCG_OK;
 }
 
+static void drop_graph(gpcg_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  c->graph_key.clear();
+}
+
 extern "C" gpcg_status gpcg_set_options(gpcg_ctx* c, const gpcg_options* opt) {
   if (!c || !opt) return fail(GPCG_ERR_INVALID_ARG, "gpcg_set_options: NULL argument");
   gpcg_status st = check_options(*opt);
@@ -668,6 +682,7 @@ extern "C" gpcg_status gpcg_set_options(gpcg_ctx* c, const gpcg_options* opt) {
   const bool rebuild = opt->precond != c->planned_precond &&
                        ((opt->precond == GPCG_PRECOND_EXACT) !=
                         (c->planned_precond == GPCG_PRECOND_EXACT));
+  drop_graph(c);
   c->opt = *opt;
   if (opt->tile) c->tile = opt->tile;
   if (rebuild) {
@@ -705,6 +720,7 @@ extern "C" gpcg_status gpcg_get_info(const gpcg_ctx* c, gpcg_info* info) {
 // ------------------------------------------------------------------ solves
 static gpcg_status ensure_scen(gpcg_ctx* c, size_t S) {
   if (S <= c->sc_cap) return GPCG_OK;
+  drop_graph(c);
   cudaFree(c->d_outages); cudaFree(c->d_lo); cudaFree(c->d_cnt); cudaFree(c->d_nogen);
   cudaFree(c->d_coef); cudaFree(c->d_order);
   c->d_outages = c->d_lo = c->d_cnt = c->d_nogen = c->d_order = nullptr;
@@ -723,6 +739,7 @@ static gpcg_status ensure_scen(gpcg_ctx* c, size_t S) {
 
 static gpcg_status ensure_work(gpcg_ctx* c, size_t bytes) {
   if (bytes <= c->work_bytes) return GPCG_OK;
+  drop_graph(c);
   if (c->work) cudaFree(c->work);
   c->work = nullptr;
   c->work_bytes = 0;
@@ -923,16 +940,6 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
     return fail(ce == cudaErrorMemoryAllocation ? GPCG_ERR_OOM : GPCG_ERR_CUDA,
                 "output staging: %s", cudaGetErrorString(ce));
   }
-  CUDA_TRY(cudaMemsetAsync(c->d_err, 0, 4, st));
-  CUDA_TRY(cudaEventRecord(c->ev[0], st));
-  const int cc_grid = std::min<int>((int)S, c->num_sms * 4);
-  ce = launch_islands(st, cc_grid, c->n, c->m, c->slack_user, (int)S, c->d_outages, c->u_f,
-                      c->u_t, c->u_bus_type, c->u_P_sched, c->u_P_gen, c->u_pre,
-                      c->d_lo, c->d_cnt, c->d_coef, c->d_nogen, d_lab, c->d_err);
-  if (ce != cudaSuccess) { cleanup(); return fail(GPCG_ERR_CUDA, "islands: %s", cudaGetErrorString(ce)); }
-  CUDA_TRY(cudaEventRecord(c->ev[1], st));
-
-  if (c->phase_on) CUDA_TRY(cudaMemsetAsync(c->phase, 0, 8 * sizeof(unsigned long long), st));
   FdpfParams P = base_params(c);
   P.sc = ScenInfo{c->d_outages, c->d_lo, c->d_cnt, c->d_coef, c->d_nogen};
   P.th0 = c->th0;
@@ -942,8 +949,67 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
   P.out_theta = d_theta; P.out_vm = d_vm; P.out_flow = d_flow; P.out_maxload = d_ml;
   P.out_bus_map = c->G.user_of_bus;
   P.out_iters = d_iters; P.out_status = d_stat;
+  const bool plain = c->opt.precision == GPCG_PLAIN_FP64;
+  const bool f16 = c->opt.precision == GPCG_BATCHED_FP32_F16;
+  const bool f32 = c->opt.precision == GPCG_BATCHED_FP32 || f16;
+  const int cc_grid = std::min<int>((int)S, c->num_sms * 4);
+  // islanding for every outage (the autotuner's probes need it too)
+  // (inside a stream capture the events become event-record nodes of the graph)
+  auto record = [](cudaEvent_t ev, cudaStream_t s, bool cap) {
+    return cap ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal) : cudaEventRecord(ev, s);
+  };
+  auto enqueue_islands = [&](cudaStream_t s, bool cap = false) -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(c->d_err, 0, 4, s);
+    if (e == cudaSuccess) e = record(c->ev[0], s, cap);
+    if (e == cudaSuccess)
+      e = launch_islands(s, cc_grid, c->n, c->m, c->slack_user, (int)S, c->d_outages, c->u_f,
+                         c->u_t, c->u_bus_type, c->u_P_sched, c->u_P_gen, c->u_pre, c->d_lo,
+                         c->d_cnt, c->d_coef, c->d_nogen, d_lab, c->d_err);
+    if (e == cudaSuccess) e = record(c->ev[1], s, cap);
+    return e;
+  };
   gpcg_status rs = GPCG_OK;
-  if (c->opt.precision == GPCG_PLAIN_FP64) {
+  int T = 2, slots = 1;
+  if (!plain) {
+    if (!c->opt.tile && !c->tile) {
+      // autotuner: the tile width that screens a probe of the first outages
+      // fastest, chosen on the first batched screen of the context
+      CUDA_TRY(enqueue_islands(st));
+      const int probe = (int)std::min<size_t>(S, 1024);
+      float best = 0.f;
+      int bestT = 2;
+      for (int t : {2, 4, 8}) {
+        FdpfParams Q = base_params(c);
+        Q.sc = P.sc;
+        Q.th0 = P.th0; Q.V0 = P.V0; Q.c0 = P.c0; Q.s0 = P.s0;
+        Q.S = probe;
+        Q.n_tiles = (probe + t - 1) / t;
+        int ps = f32 ? fdpf_max_blocks_per_sm<float>(t) : fdpf_max_blocks_per_sm<double>(t);
+        const int sl = std::max(1, std::min(Q.n_tiles, c->num_sms * std::max(ps, 1)));
+        CUDA_TRY(cudaEventRecord(c->ev[3], st));
+        rs = f32 ? run_fdpf<float>(c, st, Q, t, sl, f16) : run_fdpf<double>(c, st, Q, t, sl);
+        if (rs != GPCG_OK) { cleanup(); return rs; }
+        CUDA_TRY(cudaEventRecord(c->ev[2], st));
+        CUDA_TRY(cudaEventSynchronize(c->ev[2]));
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[3], c->ev[2]));
+        if (t == 2 || ms < best) { best = ms; bestT = t; }
+      }
+      c->tile = bestT;
+    }
+    T = c->opt.tile ? c->opt.tile : (c->tile ? c->tile : 2);
+    const int n_tiles = (int)((S + T - 1) / T);
+    int per_sm = c->opt.ctas_per_sm;
+    if (per_sm == 0) per_sm = f32 ? fdpf_max_blocks_per_sm<float>(T) : fdpf_max_blocks_per_sm<double>(T);
+    per_sm = std::max(per_sm, 1);
+    slots = std::max(1, std::min(n_tiles, c->num_sms * per_sm));
+    P.S = (int)S;
+    P.n_tiles = n_tiles;
+    P.order = c->d_order;
+  }
+  if (c->phase_on) CUDA_TRY(cudaMemsetAsync(c->phase, 0, 8 * sizeof(unsigned long long), st));
+  if (plain) {
+    CUDA_TRY(enqueue_islands(st));
     // one scenario at a time: no batching across scenarios
     for (size_t s = 0; s < S && rs == GPCG_OK; ++s) {
       FdpfParams Q = P;
@@ -958,19 +1024,49 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
       Q.out_status = d_stat ? d_stat + s : nullptr;
       rs = run_fdpf<double>(c, st, Q, 2, 1);
     }
+  } else if (mem == GPCG_MEM_DEVICE && !c->phase_on) {
+    // device mode: islanding + solve as one CUDA graph, captured on the
+    // context's own stream for this argument set and replayed on `st`
+    Layout Lo = make_layout(c, T, slots, f32 ? 4 : 8);
+    s_ = ensure_work(c, Lo.bytes);
+    if (s_ != GPCG_OK) { cleanup(); return s_; }
+    std::vector<uintptr_t> key = {S, (uintptr_t)T, (uintptr_t)slots,
+                                  (uintptr_t)c->opt.precision, (uintptr_t)c->opt.precond,
+                                  (uintptr_t)c->work, (uintptr_t)d_theta, (uintptr_t)d_vm,
+                                  (uintptr_t)d_flow, (uintptr_t)d_lab, (uintptr_t)d_iters,
+                                  (uintptr_t)d_stat, (uintptr_t)d_ml, (uintptr_t)c->d_outages,
+                                  (uintptr_t)c->d_order, (uintptr_t)c->d_lo};
+    {
+      double opts[3] = {c->opt.tol, c->opt.inner_rtol, 0.0};
+      uintptr_t bits[3];
+      std::memcpy(bits, opts, sizeof bits);
+      key.insert(key.end(), {bits[0], bits[1], (uintptr_t)c->opt.max_outer,
+                             (uintptr_t)c->opt.max_inner});
+    }
+    if (!c->graph || key != c->graph_key) {
+      if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+      cudaGraph_t gr = nullptr;
+      CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = enqueue_islands(c->cap_stream, true);
+      if (e == cudaSuccess) {
+        rs = f32 ? run_fdpf<float>(c, c->cap_stream, P, T, slots, f16)
+                 : run_fdpf<double>(c, c->cap_stream, P, T, slots);
+        if (rs == GPCG_OK) e = record(c->ev[2], c->cap_stream, true);
+      }
+      cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &gr);
+      if (rs != GPCG_OK) { if (gr) cudaGraphDestroy(gr); cleanup(); return rs; }
+      if (e == cudaSuccess) e = e2;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, gr, 0);
+      if (gr) cudaGraphDestroy(gr);
+      if (e != cudaSuccess) { c->graph = nullptr; cleanup(); return fail(GPCG_ERR_CUDA, "graph: %s", cudaGetErrorString(e)); }
+      c->graph_key = key;
+    }
+    CUDA_TRY(cudaGraphLaunch(c->graph, st));
+    c->timed = true;
+    g_err.clear();
+    return GPCG_OK;
   } else {
-    const int T = c->opt.tile ? c->opt.tile : (c->tile ? c->tile : 2);
-    c->tile = T;
-    const int n_tiles = (int)((S + T - 1) / T);
-    const bool f16 = c->opt.precision == GPCG_BATCHED_FP32_F16;
-    const bool f32 = c->opt.precision == GPCG_BATCHED_FP32 || f16;
-    int per_sm = c->opt.ctas_per_sm;
-    if (per_sm == 0) per_sm = f32 ? fdpf_max_blocks_per_sm<float>(T) : fdpf_max_blocks_per_sm<double>(T);
-    per_sm = std::max(per_sm, 1);
-    const int slots = std::max(1, std::min(n_tiles, c->num_sms * per_sm));
-    P.S = (int)S;
-    P.n_tiles = n_tiles;
-    P.order = c->d_order;
+    CUDA_TRY(enqueue_islands(st));
     rs = f32 ? run_fdpf<float>(c, st, P, T, slots, f16) : run_fdpf<double>(c, st, P, T, slots);
   }
   if (rs != GPCG_OK) { cleanup(); return rs; }
