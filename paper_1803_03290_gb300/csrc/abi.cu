@@ -586,6 +586,11 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
   UP(G.x, g->x, m);
   UP(G.b_sh, g->b_sh, m);
   UP(G.rating, g->rating, m);
+  {
+    std::vector<double> inv(m);
+    for (int e = 0; e < m; ++e) inv[e] = 1.0 / g->rating[e];
+    UP(G.inv_rating, inv.data(), m);
+  }
   UP(G.adj_ptr, c->bg.adj.ptr.data(), n + 1);
   UP(G.adj_idx, c->bg.adj.idx.data(), c->bg.adj.idx.size());
   UP(G.adj_br, c->bg.adj_branch.data(), c->bg.adj_branch.size());

@@ -23,6 +23,7 @@ struct DevGrid {
   double *P_sched = nullptr, *Q_sched = nullptr, *P_gen = nullptr, *V_set = nullptr;
   int32_t *f = nullptr, *t = nullptr;
   double *r = nullptr, *x = nullptr, *b_sh = nullptr, *rating = nullptr;
+  double* inv_rating = nullptr;              // 1 / rating
   double *g = nullptr, *by = nullptr;        // series admittance g + j b_y
   int32_t *adj_ptr = nullptr, *adj_idx = nullptr, *adj_br = nullptr;  // CSR adjacency
   double *Gii = nullptr, *Bii = nullptr;     // bus admittance diagonal

@@ -37,7 +37,8 @@ template <int T, typename VT, bool WITH_P>
 __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMatT<VT>& MP, const DevMatT<VT>& MQ,
                               LaneState<T>& L, const double* __restrict__ E,
                               const double* __restrict__ F, const double* __restrict__ V,
-                              VT* __restrict__ rhs, Pair<double>& errP, Pair<double>& errQ) {
+                              VT* __restrict__ rhs, Pair<unsigned long long>& errP,
+                              Pair<unsigned long long>& errQ) {
   const Geo<T> g;
   const DevGrid& G = P.G;
   const int l0 = g.lane, l1 = g.lane + 1;
@@ -95,7 +96,8 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
           Gd -= j ? gl1 : gl0;
           Bd -= j ? bl1 : bl0;
         }
-        double re = Gd * ei - Bd * fi, im = Gd * fi + Bd * ei;
+        // I_i = sum_j Y_ij V_j accumulated as -I_i with fused multiply-adds
+        double re = fma(Gd, ei, -Bd * fi), im = fma(Gd, fi, Bd * ei);
         // neighbours in groups of MIS_GROUP: bounds the live FP64 registers
 #pragma unroll
         for (int a0 = 0; a0 < KG; a0 += MIS_GROUP) {
@@ -111,8 +113,8 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
             if (a0 + a < deg && br[a0 + a] != brl) {
               const double gv = __ldg(G.adj_g + (size_t)i * KG + a0 + a);
               const double bv = __ldg(G.adj_b + (size_t)i * KG + a0 + a);
-              re -= gv * ej[a] - bv * fj[a];
-              im -= gv * fj[a] + bv * ej[a];
+              re = fma(-gv, ej[a], fma(bv, fj[a], re));
+              im = fma(-gv, fj[a], fma(-bv, ej[a], im));
             }
           asm volatile("" ::: "memory");
         }
@@ -121,17 +123,21 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
           if (b_ == brl) continue;
           const double gv = __ldg(G.adj_og + e), bv = __ldg(G.adj_ob + e);
           const double ee = E[(size_t)jn * T + ln], ff = F[(size_t)jn * T + ln];
-          re -= gv * ee - bv * ff;
-          im -= gv * ff + bv * ee;
+          re = fma(-gv, ee, fma(bv, ff, re));
+          im = fma(-gv, ff, fma(-bv, ee, im));
         }
-        const double dQ = qs - (fi * re - ei * im);
+        // dQ = Q_sched - Im(V_i conj(I_i)); dP = P_sched + re-dispatch - Re(...)
         VT res;
         if (WITH_P) {
-          const double dP = Ps + (j ? cf1 : cf0) * pg - (ei * re + fi * im);
-          if (j) { upd_max(errP.b, dP); if (bt == 0) upd_max(errQ.b, dQ); }
-          else { upd_max(errP.a, dP); if (bt == 0) upd_max(errQ.a, dQ); }
+          const double dP = fma(-ei, re, fma(-fi, im, fma(j ? cf1 : cf0, pg, Ps)));
+          if (j) upd_max_bits(errP.b, dP); else upd_max_bits(errP.a, dP);
+          if (bt == 0) {
+            const double dQ = fma(-fi, re, fma(ei, im, qs));
+            if (j) upd_max_bits(errQ.b, dQ); else upd_max_bits(errQ.a, dQ);
+          }
           res = (VT)dP / (VT)Vi;
         } else {
+          const double dQ = fma(-fi, re, fma(ei, im, qs));
           res = (VT)dQ / (VT)Vi;
         }
         if (j) out.b = res; else out.a = res;
@@ -303,7 +309,7 @@ __device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& 
       }
     }
   }
-  double ml0 = 0.0, ml1 = 0.0;
+  unsigned long long ml0 = 0ull, ml1 = 0ull;  // max loading as abs_bits patterns
   if (d0 || d1) {
     const int br0 = L.l[l0], br1 = L.l[l1];
     const int lo0 = L.lo[l0], cnt0 = L.cnt[l0], lo1 = L.lo[l1], cnt1 = L.cnt[l1];
@@ -314,27 +320,40 @@ __device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& 
       const bool off1 = !d1 || (k == br1) || in_island(pa, lo1, cnt1) || in_island(pb, lo1, cnt1);
       const Pair<double> ea = ld2(E + (size_t)a * T + g.lane), fa = ld2(F + (size_t)a * T + g.lane);
       const Pair<double> eb = ld2(E + (size_t)b * T + g.lane), fb = ld2(F + (size_t)b * T + g.lane);
-      const double gk = __ldg(G.g + k), bk = __ldg(G.by + k), rk = __ldg(G.rating + k);
+      const double gk = __ldg(G.g + k), bk = __ldg(G.by + k), ir = __ldg(G.inv_rating + k);
       double Pab0 = 0.0, Pba0 = 0.0, Pab1 = 0.0, Pba1 = 0.0;
+      // P_ab = g |V_a|^2 - g Re(V_a conj V_b) - b Im(V_a conj V_b), and P_ba
+      // with a and b swapped (the imaginary part changes sign)
       if (!off0) {
-        const double cr = ea.a * eb.a + fa.a * fb.a, sr = fa.a * eb.a - ea.a * fb.a;
-        Pab0 = gk * (ea.a * ea.a + fa.a * fa.a) - gk * cr - bk * sr;
-        Pba0 = gk * (eb.a * eb.a + fb.a * fb.a) - gk * cr + bk * sr;
+        const double cr = fma(ea.a, eb.a, fa.a * fb.a), sr = fma(fa.a, eb.a, -ea.a * fb.a);
+        const double gc = gk * cr;
+        Pab0 = fma(gk, fma(ea.a, ea.a, fa.a * fa.a), -fma(bk, sr, gc));
+        Pba0 = fma(gk, fma(eb.a, eb.a, fb.a * fb.a), fma(bk, sr, -gc));
       }
       if (!off1) {
-        const double cr = ea.b * eb.b + fa.b * fb.b, sr = fa.b * eb.b - ea.b * fb.b;
-        Pab1 = gk * (ea.b * ea.b + fa.b * fa.b) - gk * cr - bk * sr;
-        Pba1 = gk * (eb.b * eb.b + fb.b * fb.b) - gk * cr + bk * sr;
+        const double cr = fma(ea.b, eb.b, fa.b * fb.b), sr = fma(fa.b, eb.b, -ea.b * fb.b);
+        const double gc = gk * cr;
+        Pab1 = fma(gk, fma(ea.b, ea.b, fa.b * fa.b), -fma(bk, sr, gc));
+        Pba1 = fma(gk, fma(eb.b, eb.b, fb.b * fb.b), fma(bk, sr, -gc));
       }
-      upd_max(ml0, fmax(fabs(Pab0), fabs(Pba0)) / rk);
-      upd_max(ml1, fmax(fabs(Pab1), fabs(Pba1)) / rk);
+      // loading max(|P_ab|, |P_ba|) / rating: the larger end picked on the
+      // bit patterns, one multiplication per lane
+      if (!off0) {
+        const unsigned long long u = abs_bits(Pab0), v = abs_bits(Pba0);
+        upd_max_bits(ml0, __longlong_as_double((long long)(u > v ? u : v)) * ir);
+      }
+      if (!off1) {
+        const unsigned long long u = abs_bits(Pab1), v = abs_bits(Pba1);
+        upd_max_bits(ml1, __longlong_as_double((long long)(u > v ? u : v)) * ir);
+      }
       if (P.out_flow) {
         if (s0 >= 0) P.out_flow[(size_t)s0 * G.m + k] = Pab0;
         if (s1 >= 0) P.out_flow[(size_t)s1 * G.m + k] = Pab1;
       }
     }
   }
-  const Pair<double> ml = lane_reduce<T, true>(L, ml0, ml1);
+  const Pair<unsigned long long> mlb = lane_max_bits<T, RS_LOAD>(L, ml0, ml1);
+  const Pair<double> ml{from_bits(mlb.a), from_bits(mlb.b)};
   if (g.rs == 0) {
 #pragma unroll
     for (int j = 0; j < LP; ++j) {
@@ -432,10 +451,12 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS) fdpf_tiles_kernel(F
       continue;
     }
     // P half-step: mismatch + convergence test
-    Pair<double> eP{0.0, 0.0}, eQ{0.0, 0.0};
+    Pair<unsigned long long> eP{0ull, 0ull}, eQ{0ull, 0ull};
     mismatch_pass<T, VT, true>(P, MP, MQ, L, E, F, V, r, eP, eQ);
-    const Pair<double> mP = lane_reduce<T, true>(L, eP.a, eP.b);
-    const Pair<double> mQ = lane_reduce<T, true>(L, eQ.a, eQ.b);
+    const Pair<unsigned long long> bP = lane_max_bits<T, RS_ERRP>(L, eP.a, eP.b);
+    const Pair<unsigned long long> bQ = lane_max_bits<T, RS_ERRQ>(L, eQ.a, eQ.b);
+    const Pair<double> mP{from_bits(bP.a), from_bits(bP.b)};
+    const Pair<double> mQ{from_bits(bQ.a), from_bits(bQ.b)};
     if (g.rs == 0) {
 #pragma unroll
       for (int j = 0; j < LP; ++j) {
@@ -467,7 +488,7 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS) fdpf_tiles_kernel(F
     __syncthreads();
     GPCG_PHASE(3);
     // Q half-step
-    Pair<double> d0{0.0, 0.0}, d1{0.0, 0.0};
+    Pair<unsigned long long> d0{0ull, 0ull}, d1{0ull, 0ull};
     mismatch_pass<T, VT, false>(P, MP, MQ, L, E, F, V, r, d0, d1);
     __syncthreads();
     GPCG_PHASE(4);
@@ -526,7 +547,7 @@ __global__ void __launch_bounds__(NTHREADS) apply_kernel(DevMatT<VT> M, int op, 
     if (op == 0) {
       spmv_pass<T, VT>(M, a, b, ra[0], rb[0], w[0], ra[1], rb[1], w[1]);
     } else if (precond == PREC_JACOBI) {
-      Pair<double> rr{0.0, 0.0}, rz{0.0, 0.0};
+      Pair<VT> rr{0, 0}, rz{0, 0};
       jacobi_pass<T, VT, false>(M, c, a, nullptr, nullptr, b, (VT)0, (VT)0, ra[0], rb[0], w[0],
                                 ra[1], rb[1], w[1], rr, rz);
     } else {

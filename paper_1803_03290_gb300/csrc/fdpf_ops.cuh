@@ -96,6 +96,9 @@ __device__ __forceinline__ void ld_halfs(const __half* p, double (&v)[K]) {
 }
 
 // ------------------------------------------------------------ lane state
+constexpr int NRED_SITES = 8;  // reduction sites with a buffer of their own
+enum RedSite { RS_BB = 0, RS_RZ0, RS_PQ, RS_RR, RS_RZ, RS_ERRP, RS_ERRQ, RS_LOAD };
+
 template <int T>
 struct LaneState {
   int scen[T], l[T], fb[T], tb[T], lo[T], cnt[T];
@@ -108,6 +111,8 @@ struct LaneState {
   int pdone[T], stall[T];
   int done[T], fresh[T];
   double red[NTHREADS * LP];
+  // one small buffer per reduction site (see lane_sum): [site][warp][lane]
+  double red2[NRED_SITES * (NTHREADS / 32) * T];
   int flag;
   int drained;
 };
@@ -165,12 +170,88 @@ __device__ __forceinline__ void upd_max(double& m, double d) {
   if (!(a <= m)) m = (a == a) ? a : INFINITY;
 }
 
+// |d| as an unsigned 64-bit pattern: for non-negative doubles the integer
+// order is the numeric order (a NaN sorts above +inf), so running maxima of
+// |d| take integer instructions and leave the FP64 pipe alone.
+__device__ __forceinline__ unsigned long long abs_bits(double d) {
+  return (unsigned long long)__double_as_longlong(d) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ void upd_max_bits(unsigned long long& m, double d) {
+  const unsigned long long a = abs_bits(d);
+  m = a > m ? a : m;
+}
+__device__ __forceinline__ double from_bits(unsigned long long b) {
+  const double v = __longlong_as_double((long long)b);
+  return v == v ? v : INFINITY;
+}
+
+// Per-lane sum of the threads' partial values in a fixed order: a shuffle
+// tree inside each warp over the threads that hold the same lanes, then the
+// warps' partials through shared memory (buffer SITE) and one barrier.
+// Every thread returns the totals of its own two lanes.  A site's buffer is
+// read right after the barrier and rewritten only after a later barrier,
+// so consecutive reductions at different sites need no barrier between.
+template <int T, int SITE, typename X>
+__device__ __forceinline__ Pair<X> lane_sum(LaneState<T>& L, X v0, X v1) {
+  const Geo<T> g;
+  constexpr int TPR = Geo<T>::TPR, NW = NTHREADS / 32;
+#pragma unroll
+  for (int off = 16; off >= TPR; off >>= 1) {
+    v0 += __shfl_xor_sync(0xffffffffu, v0, off);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, off);
+  }
+  X* buf = reinterpret_cast<X*>(L.red2 + SITE * NW * T);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) < TPR) {
+    buf[w * T + g.lane] = v0;
+    buf[w * T + g.lane + 1] = v1;
+  }
+  __syncthreads();
+  X s0 = buf[g.lane], s1 = buf[g.lane + 1];
+#pragma unroll
+  for (int k = 1; k < NW; ++k) {
+    s0 += buf[k * T + g.lane];
+    s1 += buf[k * T + g.lane + 1];
+  }
+  return {s0, s1};
+}
+
+// The same for running maxima held as abs_bits patterns.
+template <int T, int SITE>
+__device__ __forceinline__ Pair<unsigned long long> lane_max_bits(LaneState<T>& L,
+                                                                   unsigned long long v0,
+                                                                   unsigned long long v1) {
+  const Geo<T> g;
+  constexpr int TPR = Geo<T>::TPR, NW = NTHREADS / 32;
+#pragma unroll
+  for (int off = 16; off >= TPR; off >>= 1) {
+    const unsigned long long u0 = __shfl_xor_sync(0xffffffffu, v0, off);
+    const unsigned long long u1 = __shfl_xor_sync(0xffffffffu, v1, off);
+    v0 = u0 > v0 ? u0 : v0;
+    v1 = u1 > v1 ? u1 : v1;
+  }
+  unsigned long long* buf = reinterpret_cast<unsigned long long*>(L.red2 + SITE * NW * T);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) < TPR) {
+    buf[w * T + g.lane] = v0;
+    buf[w * T + g.lane + 1] = v1;
+  }
+  __syncthreads();
+  unsigned long long s0 = buf[g.lane], s1 = buf[g.lane + 1];
+#pragma unroll
+  for (int k = 1; k < NW; ++k) {
+    s0 = buf[k * T + g.lane] > s0 ? buf[k * T + g.lane] : s0;
+    s1 = buf[k * T + g.lane + 1] > s1 ? buf[k * T + g.lane + 1] : s1;
+  }
+  return {s0, s1};
+}
+
 // ----------------------------------------------------- batched operators
 // q = B_s p for the thread's two lanes: base row times p, plus the outaged
 // branch's four-element change (Sec. IV.B) -- off-diagonal +w, diagonal -w
 // at both ends.  Returns the lanes' partial p.q.
 template <int T, typename VT>
-__device__ __forceinline__ Pair<double> spmv_pass(const DevMatT<VT>& M, const VT* __restrict__ p,
+__device__ __forceinline__ Pair<VT> spmv_pass(const DevMatT<VT>& M, const VT* __restrict__ p,
                                                   VT* __restrict__ q, int ra0, int rb0, VT w0,
                                                   int ra1, int rb1, VT w1) {
   const Geo<T> g;
@@ -240,14 +321,14 @@ __device__ __forceinline__ Pair<double> spmv_pass(const DevMatT<VT>& M, const VT
       pq1 += pi[u].b * a1;
     }
   }
-  return {(double)pq0, (double)pq1};
+  return {pq0, pq1};
 }
 
 // Forward substitution L y = r over the level schedule (rows of one level
 // are independent).  With FUSED, first x += alpha p and r -= alpha q (the
 // PCG update); without it, x = 0.  Accumulates r.r.
 template <int T, typename VT, bool FUSED>
-__device__ __forceinline__ Pair<double> fwd_pass(const DevMatT<VT>& M, VT* __restrict__ x,
+__device__ __forceinline__ Pair<VT> fwd_pass(const DevMatT<VT>& M, VT* __restrict__ x,
                                                  VT* __restrict__ r, const VT* __restrict__ p,
                                                  const VT* __restrict__ q, VT* __restrict__ z,
                                                  VT al0, VT al1) {
@@ -324,13 +405,13 @@ __device__ __forceinline__ Pair<double> fwd_pass(const DevMatT<VT>& M, VT* __res
     }
     __syncthreads();
   }
-  return {(double)rr0, (double)rr1};
+  return {rr0, rr1};
 }
 
 // Back substitution L^T z = y in place (z holds y on entry), over the
 // backward level schedule; accumulates r.z.
 template <int T, typename VT>
-__device__ __forceinline__ Pair<double> bwd_pass(const DevMatT<VT>& M, const VT* __restrict__ r,
+__device__ __forceinline__ Pair<VT> bwd_pass(const DevMatT<VT>& M, const VT* __restrict__ r,
                                                  VT* __restrict__ z) {
   const Geo<T> g;
   constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
@@ -403,7 +484,7 @@ __device__ __forceinline__ Pair<double> bwd_pass(const DevMatT<VT>& M, const VT*
     }
     __syncthreads();
   }
-  return {(double)rz0, (double)rz1};
+  return {rz0, rz1};
 }
 
 // Jacobi: z = r / diag(B_s), the diagonal with the outage applied; a row
@@ -413,7 +494,7 @@ __device__ __forceinline__ void jacobi_pass(const DevMatT<VT>& M, VT* __restrict
                                             VT* __restrict__ r, const VT* __restrict__ p,
                                             const VT* __restrict__ q, VT* __restrict__ z, VT al0,
                                             VT al1, int ra0, int rb0, VT w0, int ra1, int rb1,
-                                            VT w1, Pair<double>& rr, Pair<double>& rz) {
+                                            VT w1, Pair<VT>& rr, Pair<VT>& rz) {
   const Geo<T> g;
   for (int i = g.rs; i < M.n; i += Geo<T>::RPS) {
     const size_t o = (size_t)i * T + g.lane;
@@ -433,10 +514,10 @@ __device__ __forceinline__ void jacobi_pass(const DevMatT<VT>& M, VT* __restrict
     const VT z0 = d0 > (VT)0 ? ri.a / d0 : (VT)0;
     const VT z1 = d1 > (VT)0 ? ri.b / d1 : (VT)0;
     st2(z + o, Pair<VT>{z0, z1});
-    rr.a += (double)(ri.a * ri.a);
-    rr.b += (double)(ri.b * ri.b);
-    rz.a += (double)(ri.a * z0);
-    rz.b += (double)(ri.b * z1);
+    rr.a += ri.a * ri.a;
+    rr.b += ri.b * ri.b;
+    rz.a += ri.a * z0;
+    rz.b += ri.b * z1;
   }
   __syncthreads();
 }
@@ -479,13 +560,30 @@ __device__ __forceinline__ void pupdate_pass(const DevMatT<VT>& M, const VT* __r
 }
 
 // ------------------------------------------------------------ the solve
+// Per-lane scalars of the inner solve.  Each is written by the threads of
+// row slot 0 in one phase of an iteration and read by every thread only
+// after a later barrier; r.z alternates between two copies so the old value
+// can be read while the new one is written.
+template <int T, typename VT>
+struct PcgLanes {
+  VT rz[2][T];
+  VT bb[T], rrmin[T];
+  int stall[T];
+  int pdone[T];  // stopped at the convergence test (written after r.r)
+  int brk[T];    // p.Bp breakdown (written after p.Bp)
+  int stop[T];   // r.z breakdown (written after r.z)
+};
+
 // Batched PCG (Sec. III.A listing, read as textbook PCG) on B_s x = r for
 // the lanes that are active; x starts at 0.  Adds each lane's iteration
-// count to iters[lane].
+// count to iters[lane].  Every thread computes alpha and beta of its own
+// lanes from the reduced sums, so an iteration has five barriers besides
+// the substitution levels'.
 template <int T, typename VT>
 __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT>& M, LaneState<T>& L, VT* x,
                           VT* r, VT* p, VT* q, VT* z, const int* ra_, const int* rb_,
                           const double* w_, int* iters) {
+  __shared__ PcgLanes<T, VT> S;
   const Geo<T> g;
   const int l0 = g.lane, l1 = g.lane + 1;
   const int ra0 = ra_[l0], rb0 = rb_[l0], ra1 = ra_[l1], rb1 = rb_[l1];
@@ -496,100 +594,104 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
   if (g.rs == 0) {
     st2(p + (size_t)M.n * T + g.lane, Pair<VT>{(VT)0, (VT)0});
     st2(z + (size_t)M.n * T + g.lane, Pair<VT>{(VT)0, (VT)0});
-    L.pdone[l0] = !L.active[l0];
-    L.pdone[l1] = !L.active[l1];
   }
   __syncthreads();
-  Pair<double> bbp{0.0, 0.0}, rzp{0.0, 0.0};
+  Pair<VT> bbp{0, 0}, rzp{0, 0};
   if (jac) {
     jacobi_pass<T, VT, false>(M, x, r, p, q, z, (VT)0, (VT)0, ra0, rb0, w0, ra1, rb1, w1, bbp, rzp);
   } else {
     bbp = fwd_pass<T, VT, false>(M, x, r, p, q, z, (VT)0, (VT)0);
     rzp = bwd_pass<T, VT>(M, r, z);
   }
-  const Pair<double> bb = lane_reduce<T, false>(L, bbp.a, bbp.b);
-  const Pair<double> rz0 = lane_reduce<T, false>(L, rzp.a, rzp.b);
-  pupdate_pass<T, VT>(M, z, p, (VT)0, (VT)0, lo0, cnt0, lo1, cnt1, true);
+  const Pair<VT> bb = lane_sum<T, RS_BB>(L, bbp.a, bbp.b);
+  const Pair<VT> rz0 = lane_sum<T, RS_RZ0>(L, rzp.a, rzp.b);
   if (g.rs == 0) {
 #pragma unroll
     for (int j = 0; j < LP; ++j) {
       const int ln = g.lane + j;
-      const double b_ = j ? bb.b : bb.a, r_ = j ? rz0.b : rz0.a;
-      L.bb[ln] = b_;
-      L.rz[ln] = r_;
-      L.rrmin[ln] = b_;
-      L.stall[ln] = 0;
-      if (!(b_ > 0.0) || !(r_ > 0.0)) L.pdone[ln] = 1;
+      const VT b_ = j ? bb.b : bb.a, r_ = j ? rz0.b : rz0.a;
+      S.bb[ln] = b_;
+      S.rz[0][ln] = r_;
+      S.rrmin[ln] = b_;
+      S.stall[ln] = 0;
+      S.brk[ln] = 0;
+      S.stop[ln] = 0;
+      S.pdone[ln] = !L.active[ln] || !(b_ > (VT)0) || !(r_ > (VT)0);
     }
   }
-  const double tol2 = P.inner_rtol * P.inner_rtol;
+  pupdate_pass<T, VT>(M, z, p, (VT)0, (VT)0, lo0, cnt0, lo1, cnt1, true);  // ends in a barrier
+  const VT tol2 = (VT)(P.inner_rtol * P.inner_rtol);
+  int par = 0;
   for (int it = 0; it < P.max_inner; ++it) {
-    __syncthreads();
-    if (g.rs == 0) {
-      L.alpha[l0] = L.pdone[l0] ? 0.0 : 1.0;  // alpha doubles as "still running"
-      L.alpha[l1] = L.pdone[l1] ? 0.0 : 1.0;
+    bool any = false;
+#pragma unroll 1
+    for (int k = 0; k < T; ++k) any |= !(S.pdone[k] | S.stop[k]);
+    if (!any) break;
+    const bool run0 = !(S.pdone[l0] | S.stop[l0]), run1 = !(S.pdone[l1] | S.stop[l1]);
+    const Pair<VT> pqp = spmv_pass<T, VT>(M, p, q, ra0, rb0, w0, ra1, rb1, w1);
+    const Pair<VT> pq = lane_sum<T, RS_PQ>(L, pqp.a, pqp.b);
+    VT al0 = 0, al1 = 0;
+    bool bk0 = false, bk1 = false;
+    if (run0) {
+      if (pq.a > (VT)0 && isfinite(pq.a)) al0 = S.rz[par][l0] / pq.a;
+      else bk0 = true;  // breakdown: keep the current iterate
     }
-    if (!any_lane<T>(L, L.alpha)) break;
-    const Pair<double> pqp = spmv_pass<T, VT>(M, p, q, ra0, rb0, w0, ra1, rb1, w1);
-    const Pair<double> pq = lane_reduce<T, false>(L, pqp.a, pqp.b);
-    if (g.rs == 0) {
-#pragma unroll
-      for (int j = 0; j < LP; ++j) {
-        const int ln = g.lane + j;
-        const double v = j ? pq.b : pq.a;
-        double a = 0.0;
-        if (!L.pdone[ln]) {
-          if (v > 0.0 && isfinite(v)) a = L.rz[ln] / v;
-          else L.pdone[ln] = 1;  // breakdown: keep the current iterate
-        }
-        L.alpha[ln] = a;
-      }
+    if (run1) {
+      if (pq.b > (VT)0 && isfinite(pq.b)) al1 = S.rz[par][l1] / pq.b;
+      else bk1 = true;
     }
-    __syncthreads();
-    const VT al0 = (VT)L.alpha[l0], al1 = (VT)L.alpha[l1];
-    Pair<double> rrp{0.0, 0.0}, rzn{0.0, 0.0};
+    if (g.rs == 0) {
+      if (bk0) S.brk[l0] = 1;
+      if (bk1) S.brk[l1] = 1;
+    }
+    Pair<VT> rrp{0, 0}, rzn{0, 0};
     if (jac) {
       jacobi_pass<T, VT, true>(M, x, r, p, q, z, al0, al1, ra0, rb0, w0, ra1, rb1, w1, rrp, rzn);
     } else {
       rrp = fwd_pass<T, VT, true>(M, x, r, p, q, z, al0, al1);
     }
-    const Pair<double> rr = lane_reduce<T, false>(L, rrp.a, rrp.b);
+    const Pair<VT> rr = lane_sum<T, RS_RR>(L, rrp.a, rrp.b);
     if (g.rs == 0) {
 #pragma unroll
       for (int j = 0; j < LP; ++j) {
         const int ln = g.lane + j;
-        const double v = j ? rr.b : rr.a;
-        if (L.pdone[ln]) continue;
+        const VT v = j ? rr.b : rr.a;
+        if (S.pdone[ln] | S.stop[ln]) continue;
+        if (S.brk[ln]) { S.pdone[ln] = 1; continue; }
         iters[ln] += 1;
         // converged; or stagnated at the rounding floor of VT (no 0.1 % gain
         // in STALL_ITERS iterations); or growing away from the best residual
-        if (v < 0.999 * L.rrmin[ln]) { L.rrmin[ln] = v; L.stall[ln] = 0; }
-        else L.stall[ln] += 1;
-        if (v <= tol2 * L.bb[ln] || !isfinite(v) || L.stall[ln] >= STALL_ITERS ||
-            v > 1e4 * L.rrmin[ln])
-          L.pdone[ln] = 1;
+        if (v < (VT)0.999 * S.rrmin[ln]) { S.rrmin[ln] = v; S.stall[ln] = 0; }
+        else S.stall[ln] += 1;
+        if (v <= tol2 * S.bb[ln] || !isfinite(v) || S.stall[ln] >= STALL_ITERS ||
+            v > (VT)1e4 * S.rrmin[ln])
+          S.pdone[ln] = 1;
       }
     }
     __syncthreads();
-    if (g.rs == 0) {
-      L.beta[l0] = L.pdone[l0] ? 0.0 : 1.0;
-      L.beta[l1] = L.pdone[l1] ? 0.0 : 1.0;
-    }
-    if (!any_lane<T>(L, L.beta)) break;
+    // lanes still running, read before S.stop is next written (after r.z)
+    const bool go0 = !(S.pdone[l0] | S.stop[l0]), go1 = !(S.pdone[l1] | S.stop[l1]);
+    any = false;
+#pragma unroll 1
+    for (int k = 0; k < T; ++k) any |= !(S.pdone[k] | S.stop[k]);
+    if (!any) break;
     if (!jac) rzn = bwd_pass<T, VT>(M, r, z);
-    const Pair<double> rz = lane_reduce<T, false>(L, rzn.a, rzn.b);
+    const Pair<VT> rz = lane_sum<T, RS_RZ>(L, rzn.a, rzn.b);
+    VT be0 = 0, be1 = 0;
+    if (go0) be0 = rz.a / S.rz[par][l0];
+    if (go1) be1 = rz.b / S.rz[par][l1];
     if (g.rs == 0) {
 #pragma unroll
       for (int j = 0; j < LP; ++j) {
         const int ln = g.lane + j;
-        const double v = j ? rz.b : rz.a;
-        L.beta[ln] = L.pdone[ln] ? 0.0 : v / L.rz[ln];
-        if (!L.pdone[ln]) L.rz[ln] = v;
-        if (!(v > 0.0)) L.pdone[ln] = 1;
+        if (!(j ? go1 : go0)) continue;
+        const VT v = j ? rz.b : rz.a;
+        S.rz[par ^ 1][ln] = v;
+        if (!(v > (VT)0)) S.stop[ln] = 1;
       }
     }
-    __syncthreads();
-    pupdate_pass<T, VT>(M, z, p, (VT)L.beta[l0], (VT)L.beta[l1], lo0, cnt0, lo1, cnt1, false);
+    pupdate_pass<T, VT>(M, z, p, be0, be1, lo0, cnt0, lo1, cnt1, false);  // ends in a barrier
+    par ^= 1;
   }
   __syncthreads();
 }
