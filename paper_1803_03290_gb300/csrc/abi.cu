@@ -37,6 +37,8 @@ void launch_scale_factor(cudaStream_t, int, const int32_t*, const int32_t*, cons
                          double*, float*);
 void launch_gather_half(cudaStream_t, int, const int32_t*, const double*, __half*);
 void launch_inv_diag(cudaStream_t, int, const int32_t*, const double*, double*, float*);
+void launch_tail_inverse(cudaStream_t, int, int, const int32_t*, const int32_t*, const double*,
+                         const double*, double*, double*, float*, float*);
 void launch_adj_values(cudaStream_t, int, const int32_t*, const double*, const double*, double*,
                        double*);
 // islands.cu
@@ -100,6 +102,10 @@ struct MatDev {
   int32_t *a_ptr = nullptr, *a_idx = nullptr, *a_diag = nullptr;
   int32_t *l_ptr = nullptr, *l_idx = nullptr, *l_diag = nullptr;
   int32_t *lev_ptr = nullptr, *blev_ptr = nullptr, *blev_rows = nullptr;
+  int32_t *tblev_ptr = nullptr, *tblev_rows = nullptr;
+  double *xc = nullptr, *xr = nullptr;  // inverse of the factor's tail block
+  float *xc32 = nullptr, *xr32 = nullptr;
+  float *xch = nullptr, *xrh = nullptr;  // the same for the FP16-stored factor
   double *a_val = nullptr, *l_val = nullptr, *diag = nullptr, *inv_diag = nullptr;
   float *diag32 = nullptr, *inv_diag32 = nullptr;
   double *lsc = nullptr, *inv_d2 = nullptr;  // scaled factor (FP64) and 1 / L_ii^2
@@ -122,6 +128,10 @@ DevMatT<double> MatDev::view<double>(bool) const {
   M.lev_ptr = lev_ptr; M.blev_ptr = blev_ptr; M.blev_rows = blev_rows;
   M.nlev = (int)plan.lev_ptr.size() - 1;
   M.nblev = (int)plan.blev_ptr.size() - 1;
+  M.tail_lev = plan.tail_lev; M.tail_row0 = plan.tail_row0;
+  M.tblev_ptr = tblev_ptr; M.tblev_rows = tblev_rows;
+  M.ntblev = (int)plan.tblev_ptr.size() - 1;
+  M.xc = xc; M.xr = xr;
   M.w = w;
   return M;
 }
@@ -141,6 +151,11 @@ DevMatT<float> MatDev::view<float>(bool f16) const {
   M.lev_ptr = lev_ptr; M.blev_ptr = blev_ptr; M.blev_rows = blev_rows;
   M.nlev = (int)plan.lev_ptr.size() - 1;
   M.nblev = (int)plan.blev_ptr.size() - 1;
+  M.tail_lev = plan.tail_lev; M.tail_row0 = plan.tail_row0;
+  M.tblev_ptr = tblev_ptr; M.tblev_rows = tblev_rows;
+  M.ntblev = (int)plan.tblev_ptr.size() - 1;
+  M.xc = f16 && xch ? xch : xc32;
+  M.xr = f16 && xrh ? xrh : xr32;
   M.w = w;
   return M;
 }
@@ -336,7 +351,14 @@ static gpcg_status fill_values(gpcg_ctx* c, MatDev& M, const double* w) {
       launch_gather_half(st, E->nslot, E->src, M.lsc, E->valh);
       launch_gather_half(st, E->nover, E->osrc, M.lsc, E->ovalh);
     }
+    // tail inverse of the FP16-stored factor (M.xc as FP64 scratch, then
+    // overwritten below)
+    if (M.xch)
+      launch_tail_inverse(st, P.tail_row0, P.n - P.tail_row0, M.l_ptr, M.l_idx, M.l_val, M.lsc,
+                          M.xc, nullptr, M.xch, M.xrh);
   }
+  launch_tail_inverse(st, P.tail_row0, P.n - P.tail_row0, M.l_ptr, M.l_idx, M.l_val, nullptr,
+                      M.xc, M.xr, M.xc32, M.xr32);
   CUDA_TRY(cudaGetLastError());
   int32_t herr = 0;
   CUDA_TRY(cudaMemcpy(&herr, c->d_err, sizeof herr, cudaMemcpyDeviceToHost));
@@ -350,6 +372,7 @@ static gpcg_status fill_values(gpcg_ctx* c, MatDev& M, const double* w) {
 static gpcg_status build_matrix(gpcg_ctx* c, MatDev& M, const std::vector<uint8_t>& keep,
                                 double* w, bool fill) {
   M.plan = plan_matrix(c->n, c->bg, keep, fill);
+  plan_tail(M.plan, TAIL_ROWS);
   const MatrixPlan& P = M.plan;
   auto& own = c->mat_owned;
   std::vector<int32_t> pre_of_row(P.n);
@@ -372,6 +395,16 @@ static gpcg_status build_matrix(gpcg_ctx* c, MatDev& M, const std::vector<uint8_
   CUDA_TRY(upload(own, &M.lev_ptr, P.lev_ptr.data(), P.lev_ptr.size()));
   CUDA_TRY(upload(own, &M.blev_ptr, P.blev_ptr.data(), P.blev_ptr.size()));
   CUDA_TRY(upload(own, &M.blev_rows, P.blev_rows.data(), P.blev_rows.size()));
+  CUDA_TRY(upload(own, &M.tblev_ptr, P.tblev_ptr.data(), P.tblev_ptr.size()));
+  if (!P.tblev_rows.empty())
+    CUDA_TRY(upload(own, &M.tblev_rows, P.tblev_rows.data(), P.tblev_rows.size()));
+  {
+    const size_t nt = (size_t)(P.n - P.tail_row0);
+    CUDA_TRY(dalloc(own, &M.xc, nt * nt));
+    CUDA_TRY(dalloc(own, &M.xr, nt * nt));
+    CUDA_TRY(dalloc(own, &M.xc32, nt * nt));
+    CUDA_TRY(dalloc(own, &M.xr32, nt * nt));
+  }
   std::vector<int32_t> ldiag(P.n);
   for (int i = 0; i < P.n; ++i) ldiag[i] = P.L.ptr[i + 1] - 1;
   CUDA_TRY(upload(own, &M.l_diag, ldiag.data(), P.n));
@@ -383,6 +416,11 @@ static gpcg_status build_matrix(gpcg_ctx* c, MatDev& M, const std::vector<uint8_
   CUDA_TRY(dalloc(own, &M.inv_diag, P.n));
   CUDA_TRY(dalloc(own, &M.inv_diag32, P.n));
   CUDA_TRY(dalloc(own, &M.lsc, nl));
+  {
+    const size_t nt = (size_t)(P.n - P.tail_row0);
+    CUDA_TRY(dalloc(own, &M.xch, nt * nt));
+    CUDA_TRY(dalloc(own, &M.xrh, nt * nt));
+  }
   CUDA_TRY(dalloc(own, &M.inv_d2, P.n));
   CUDA_TRY(dalloc(own, &M.inv_d2_32, P.n));
   // padded rows: A (all entries), strictly lower L, strictly upper L^T
@@ -1120,6 +1158,7 @@ static gpcg_status ensure_adj_matrix(gpcg_ctx* c) {
   MatDev& M = c->MA;
   M = c->MP;  // structure shared; values replaced below
   M.lsc = nullptr;  // the adjoint solves in FP64: no scaled FP16 factor
+  M.xch = M.xrh = nullptr;
   M.L.valh = M.L.ovalh = M.U.valh = M.U.ovalh = nullptr;
   auto& own = c->adj_owned;
   const int n = M.plan.n, nnz = M.plan.A.nnz(), nl = M.plan.L.nnz();
@@ -1129,6 +1168,13 @@ static gpcg_status ensure_adj_matrix(gpcg_ctx* c) {
   CUDA_TRY(dalloc(own, &M.diag32, n));
   CUDA_TRY(dalloc(own, &M.inv_diag, n));
   CUDA_TRY(dalloc(own, &M.inv_diag32, n));
+  {
+    const size_t nt = (size_t)(n - M.plan.tail_row0);
+    CUDA_TRY(dalloc(own, &M.xc, nt * nt));
+    CUDA_TRY(dalloc(own, &M.xr, nt * nt));
+    CUDA_TRY(dalloc(own, &M.xc32, nt * nt));
+    CUDA_TRY(dalloc(own, &M.xr32, nt * nt));
+  }
   for (EllDev* E : {&M.A, &M.L, &M.U}) {
     CUDA_TRY(dalloc(own, &E->val, E->nslot));
     CUDA_TRY(dalloc(own, &E->val32, E->nslot));

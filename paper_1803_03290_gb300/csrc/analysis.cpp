@@ -216,6 +216,33 @@ MatrixPlan plan_matrix(int n_bus, const BusGraph& g, const std::vector<uint8_t>&
   return P;
 }
 
+void plan_tail(MatrixPlan& P, int max_rows) {
+  const int n = P.n, nlev = (int)P.lev_ptr.size() - 1;
+  int tl = nlev;
+  while (tl > 0 && n - P.lev_ptr[tl - 1] <= max_rows) --tl;
+  if (nlev - tl < 2) tl = nlev;  // a single level gains nothing
+  P.tail_lev = tl;
+  P.tail_row0 = nlev > 0 ? P.lev_ptr[tl] : 0;
+  const int t0 = P.tail_row0;
+  // backward levels of rows < t0, waiting only for rows < t0
+  std::vector<int> blev(t0, 0);
+  for (int i = t0 - 1; i >= 0; --i) {
+    int m = -1;
+    for (int k = P.U.ptr[i]; k < P.U.ptr[i + 1]; ++k) {
+      const int j = P.U.idx[k];
+      if (j != i && j < t0) m = std::max(m, blev[j]);
+    }
+    blev[i] = m + 1;
+  }
+  const int nb = t0 ? (*std::max_element(blev.begin(), blev.end()) + 1) : 0;
+  P.tblev_ptr.assign(nb + 1, 0);
+  for (int i = 0; i < t0; ++i) P.tblev_ptr[blev[i] + 1]++;
+  for (int k = 0; k < nb; ++k) P.tblev_ptr[k + 1] += P.tblev_ptr[k];
+  P.tblev_rows.resize(t0);
+  std::vector<int32_t> bf(P.tblev_ptr.begin(), P.tblev_ptr.end() - 1);
+  for (int i = 0; i < t0; ++i) P.tblev_rows[bf[blev[i]]++] = i;
+}
+
 std::vector<int32_t> rcm_order(int n, const BusGraph& g) {
   std::vector<int32_t> deg(n), out;
   for (int v = 0; v < n; ++v) deg[v] = g.adj.ptr[v + 1] - g.adj.ptr[v];

@@ -38,6 +38,10 @@ struct MatrixPlan {
   std::vector<int32_t> lev_ptr;       // rows of level k: [lev_ptr[k], lev_ptr[k+1])
   std::vector<int32_t> blev_ptr;      // backward levels: positions into blev_rows
   std::vector<int32_t> blev_rows;
+  // tail of the forward schedule (see plan_tail): levels [tail_lev, nlev),
+  // rows [tail_row0, n); and the backward levels of the rows before it
+  int tail_lev = 0, tail_row0 = 0;
+  std::vector<int32_t> tblev_ptr, tblev_rows;
 };
 
 // Build the bus adjacency from the branch list.
@@ -49,6 +53,14 @@ BusGraph build_bus_graph(int n_bus, int n_branch, const int32_t* f, const int32_
 // degree, then rows sorted by forward level.
 MatrixPlan plan_matrix(int n_bus, const BusGraph& g, const std::vector<uint8_t>& keep,
                        bool fill);
+
+// Split off the tail of the forward level schedule: the longest run of
+// final levels with at most max_rows rows together (none if that is a
+// single level).  The rows of a tail only depend, in the backward solve, on
+// rows of the tail, so both substitutions of the tail can be done at once
+// after the forward levels before it; the backward schedule of the
+// remaining rows (tblev_*) treats the tail rows as solved.
+void plan_tail(MatrixPlan& P, int max_rows);
 
 // Reverse Cuthill-McKee order of the bus graph (new position -> bus): buses
 // adjacent in the grid get nearby positions.

@@ -241,6 +241,51 @@ void launch_inv_diag(cudaStream_t st, int n, const int32_t* pos, const double* l
                      float* inv32) {
   if (n > 0) inv_diag_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, pos, l_val, inv, inv32);
 }
+// X = inverse of the factor's tail block L_tt (rows and columns
+// [t0, t0 + nt) of L, lower triangular): column c of X by forward
+// substitution of L_tt x = e_c, one thread per column, in FP64.  Written
+// column-major (xc[c nt + i] = X_ic) and row-major (xr[i nt + c] = X_ic),
+// zeros above the diagonal, in FP64 (xr optional) and FP32.
+// With lsc (the scaled factor Ls = L D^-1) the block inverted is the one
+// the FP16 storage represents: L_ij = fp16(Ls_ij) L_jj.
+__global__ void tail_inverse_kernel(int t0, int nt, const int32_t* __restrict__ l_ptr,
+                                    const int32_t* __restrict__ l_idx,
+                                    const double* __restrict__ l_val,
+                                    const double* __restrict__ lsc, double* xc, double* xr,
+                                    float* xc32, float* xr32) {
+  for (int c = threadIdx.x; c < nt; c += blockDim.x) {
+    // xc holds the column in FP64 while it is built (its earlier entries
+    // are the unknowns solved before)
+    for (int i = 0; i < nt; ++i) {
+      double v = 0.0;
+      if (i >= c) {
+        const int R = t0 + i, e0 = l_ptr[R], e1 = l_ptr[R + 1] - 1;  // diagonal last
+        double sum = (i == c) ? 1.0 : 0.0;
+        for (int e = e0; e < e1; ++e) {
+          const int jg = l_idx[e], j = jg - t0;
+          if (j < c) continue;
+          const double lij =
+              lsc ? (double)__half2float(__double2half(lsc[e])) * l_val[l_ptr[jg + 1] - 1]
+                  : l_val[e];
+          sum -= lij * xc[(size_t)c * nt + j];
+        }
+        v = sum / l_val[e1];
+      }
+      xc[(size_t)c * nt + i] = v;
+      if (xr) xr[(size_t)i * nt + c] = v;
+      xc32[(size_t)c * nt + i] = (float)v;
+      xr32[(size_t)i * nt + c] = (float)v;
+    }
+  }
+}
+
+void launch_tail_inverse(cudaStream_t st, int t0, int nt, const int32_t* l_ptr,
+                         const int32_t* l_idx, const double* l_val, const double* lsc, double* xc,
+                         double* xr, float* xc32, float* xr32) {
+  if (nt > 0)
+    tail_inverse_kernel<<<1, 128, 0, st>>>(t0, nt, l_ptr, l_idx, l_val, lsc, xc, xr, xc32, xr32);
+}
+
 void launch_adj_values(cudaStream_t st, int n, const int32_t* br, const double* g,
                        const double* by, double* ag, double* ab) {
   if (n > 0) adj_values_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, br, g, by, ag, ab);

@@ -13,6 +13,12 @@ constexpr int KA = 6;   // B' / B'' rows, diagonal included
 constexpr int KL = 4;   // strictly lower part of the factor
 constexpr int KU = 4;   // strictly upper part (L^T)
 constexpr int KG = 6;   // bus adjacency of the mismatch
+// Tail of the forward level schedule solved with the dense inverse of its
+// factor block: the last levels, together at most TAIL_ROWS rows.
+#ifndef GPCG_TAIL_ROWS
+#define GPCG_TAIL_ROWS 256
+#endif
+constexpr int TAIL_ROWS = GPCG_TAIL_ROWS;
 
 // Grid arrays on the device.  Buses use the library's internal numbering (a
 // bandwidth-reducing order of the bus graph); branches keep the caller's
@@ -65,6 +71,13 @@ struct DevMatT {
   const int32_t *lev_ptr = nullptr;          // forward levels (contiguous rows)
   const int32_t *blev_ptr = nullptr, *blev_rows = nullptr;
   int nlev = 0, nblev = 0;
+  // the tail: forward levels [tail_lev, nlev) = rows [tail_row0, n), solved
+  // with X = inverse of the factor's tail block, stored column-major (xc)
+  // and row-major (xr); and the backward levels of rows < tail_row0 with
+  // the tail taken as solved
+  int tail_lev = 0, tail_row0 = 0, ntblev = 0;
+  const int32_t *tblev_ptr = nullptr, *tblev_rows = nullptr;
+  const VT *xc = nullptr, *xr = nullptr;
   const double* w = nullptr;                 // per-branch weight of this matrix
 };
 

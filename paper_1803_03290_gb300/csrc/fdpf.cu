@@ -515,6 +515,7 @@ __global__ void __launch_bounds__(NTHREADS) apply_kernel(DevMatT<VT> M, int op, 
                                                          const int32_t* f_, const int32_t* t_,
                                                          const double* X, double* Y, VT* wbuf,
                                                          size_t vstride, int precond) {
+  __shared__ __align__(16) VT zt[TAIL_ROWS * T];
   const Geo<T> g;
   VT* a = wbuf + (size_t)blockIdx.x * 3 * vstride;
   VT* b = a + vstride;
@@ -551,8 +552,9 @@ __global__ void __launch_bounds__(NTHREADS) apply_kernel(DevMatT<VT> M, int op, 
       jacobi_pass<T, VT, false>(M, c, a, nullptr, nullptr, b, (VT)0, (VT)0, ra[0], rb[0], w[0],
                                 ra[1], rb[1], w[1], rr, rz);
     } else {
-      fwd_pass<T, VT, false>(M, c, a, nullptr, nullptr, b, (VT)0, (VT)0);
-      bwd_pass<T, VT>(M, a, b);
+      Pair<VT> rzt{0, 0};
+      fwd_pass<T, VT, false>(M, c, a, nullptr, nullptr, b, (VT)0, (VT)0, zt, rzt);
+      bwd_pass<T, VT>(M, a, b, rzt);
     }
     __syncthreads();
     for (int i = g.rs; i < M.n; i += Geo<T>::RPS) {

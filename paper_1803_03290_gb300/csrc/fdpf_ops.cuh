@@ -324,6 +324,115 @@ __device__ __forceinline__ Pair<VT> spmv_pass(const DevMatT<VT>& M, const VT* __
   return {pq0, pq1};
 }
 
+// The tail of the level schedule (rows [tail_row0, n): the last, narrow
+// levels) is solved densely instead of level by level: with X = L_tt^-1 the
+// inverse of the factor's tail block (computed once per factor),
+//   forward:  y_t = X (r_t - L_t,s y_s)   (s: the rows solved before)
+//   backward: z_t = X^T y_t               (tail rows depend on tail rows only)
+// Each is one pass of all threads over X (stored both column- and row-major
+// so both products read it coalesced) instead of one block barrier and one
+// memory latency per narrow level.  s holds the tail's right-hand side,
+// then y (TAIL_ROWS rows of T lanes).  Adds the tail rows' r.r to rr and
+// their r.z to rzt; writes the tail's final z.
+template <int T, typename VT, bool FUSED>
+__device__ __forceinline__ void tail_solve(const DevMatT<VT>& M, VT* __restrict__ x,
+                                           VT* __restrict__ r, const VT* __restrict__ p,
+                                           const VT* __restrict__ q, VT* __restrict__ z,
+                                           VT al0, VT al1, VT* __restrict__ s, VT& rr0, VT& rr1,
+                                           Pair<VT>& rzt) {
+  const Geo<T> g;
+  constexpr int RPS = Geo<T>::RPS, NPT = (TAIL_ROWS + RPS - 1) / RPS;
+  const int t0 = M.tail_row0, nt = M.n - t0;
+  // (a) right-hand side: the PCG update of the tail rows, minus the part of
+  // their factor rows on the rows solved before the tail
+  for (int k = g.rs; k < nt; k += RPS) {
+    const int i = t0 + k;
+    const size_t o = (size_t)i * T + g.lane;
+    int c[KL];
+    VT v[KL];
+    ld_cols<KL>(M.L.col + (size_t)i * KL, c);
+    if (M.Lh) ld_halfs<KL>(M.Lh + (size_t)i * KL, v);
+    else ld_vals<KL>(M.L.val + (size_t)i * KL, v);
+    Pair<VT> rv = ld2(r + o);
+    if (FUSED) {
+      const Pair<VT> pi = ld2(p + o), qi = ld2(q + o), xi = ld2(x + o);
+      st2(x + o, Pair<VT>{xi.a + al0 * pi.a, xi.b + al1 * pi.b});
+      rv.a -= al0 * qi.a;
+      rv.b -= al1 * qi.b;
+      st2(r + o, rv);
+    } else {
+      st2(x + o, Pair<VT>{(VT)0, (VT)0});
+    }
+    rr0 += rv.a * rv.a;
+    rr1 += rv.b * rv.b;
+    VT a0 = rv.a, a1 = rv.b;
+#pragma unroll
+    for (int k2 = 0; k2 < KL; ++k2) {
+      if (c[k2] >= t0) continue;
+      const Pair<VT> zz = ld2(z + (size_t)c[k2] * T + g.lane);
+      a0 -= v[k2] * zz.a;
+      a1 -= v[k2] * zz.b;
+    }
+    const int o0 = __ldg(M.L.optr + i), o1 = __ldg(M.L.optr + i + 1);
+    for (int e = o0; e < o1; ++e) {
+      const int cc = __ldg(M.L.ocol + e);
+      if (cc >= t0) continue;
+      const VT vv = M.Lh ? (VT)__half2float(M.Loh[e]) : __ldg(M.L.oval + e);
+      const Pair<VT> zz = ld2(z + (size_t)cc * T + g.lane);
+      a0 -= vv * zz.a;
+      a1 -= vv * zz.b;
+    }
+    st2(s + (size_t)k * T + g.lane, Pair<VT>{a0, a1});
+  }
+  __syncthreads();
+  // (b) y_t = X rhs: X_kj = xc[j nt + k], zero above the diagonal
+  Pair<VT> y[NPT];
+#pragma unroll
+  for (int m = 0; m < NPT; ++m) {
+    const int k = g.rs + m * RPS;
+    VT a0 = 0, a1 = 0;
+    if (k < nt) {
+      const VT* col = M.xc + k;
+#pragma unroll 4
+      for (int j = 0; j < nt; ++j) {
+        const VT xv = __ldg(col + (size_t)j * nt);
+        const Pair<VT> sv = ld2(s + (size_t)j * T + g.lane);
+        a0 += xv * sv.a;
+        a1 += xv * sv.b;
+      }
+    }
+    y[m] = Pair<VT>{a0, a1};
+  }
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < NPT; ++m) {
+    const int k = g.rs + m * RPS;
+    if (k < nt) st2(s + (size_t)k * T + g.lane, y[m]);
+  }
+  __syncthreads();
+  // (c) z_t = X^T y_t: X_ik = xr[i nt + k], zero for i < k
+#pragma unroll
+  for (int m = 0; m < NPT; ++m) {
+    const int k = g.rs + m * RPS;
+    if (k >= nt) continue;
+    const VT* col = M.xr + k;
+    VT a0 = 0, a1 = 0;
+#pragma unroll 4
+    for (int i = 0; i < nt; ++i) {
+      const VT xv = __ldg(col + (size_t)i * nt);
+      const Pair<VT> sv = ld2(s + (size_t)i * T + g.lane);
+      a0 += xv * sv.a;
+      a1 += xv * sv.b;
+    }
+    const size_t o = (size_t)(t0 + k) * T + g.lane;
+    st2(z + o, Pair<VT>{a0, a1});
+    const Pair<VT> ri = ld2(r + o);
+    rzt.a += ri.a * a0;
+    rzt.b += ri.b * a1;
+  }
+  __syncthreads();
+}
+
 // Forward substitution L y = r over the level schedule (rows of one level
 // are independent).  With FUSED, first x += alpha p and r -= alpha q (the
 // PCG update); without it, x = 0.  Accumulates r.r.
@@ -331,11 +440,11 @@ template <int T, typename VT, bool FUSED>
 __device__ __forceinline__ Pair<VT> fwd_pass(const DevMatT<VT>& M, VT* __restrict__ x,
                                                  VT* __restrict__ r, const VT* __restrict__ p,
                                                  const VT* __restrict__ q, VT* __restrict__ z,
-                                                 VT al0, VT al1) {
+                                                 VT al0, VT al1, VT* zt, Pair<VT>& rzt) {
   const Geo<T> g;
   constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
   VT rr0 = 0, rr1 = 0;
-  for (int lev = 0; lev < M.nlev; ++lev) {
+  for (int lev = 0; lev < M.tail_lev; ++lev) {
     const int r0 = __ldg(M.lev_ptr + lev), r1 = __ldg(M.lev_ptr + lev + 1);
     int cn[UNR][KL];
 #pragma unroll
@@ -405,6 +514,7 @@ __device__ __forceinline__ Pair<VT> fwd_pass(const DevMatT<VT>& M, VT* __restric
     }
     __syncthreads();
   }
+  if (M.tail_row0 < M.n) tail_solve<T, VT, FUSED>(M, x, r, p, q, z, al0, al1, zt, rr0, rr1, rzt);
   return {rr0, rr1};
 }
 
@@ -412,18 +522,22 @@ __device__ __forceinline__ Pair<VT> fwd_pass(const DevMatT<VT>& M, VT* __restric
 // backward level schedule; accumulates r.z.
 template <int T, typename VT>
 __device__ __forceinline__ Pair<VT> bwd_pass(const DevMatT<VT>& M, const VT* __restrict__ r,
-                                                 VT* __restrict__ z) {
+                                                 VT* __restrict__ z, Pair<VT> rzt) {
   const Geo<T> g;
   constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
-  VT rz0 = 0, rz1 = 0;
-  for (int lev = 0; lev < M.nblev; ++lev) {
-    const int r0 = __ldg(M.blev_ptr + lev), r1 = __ldg(M.blev_ptr + lev + 1);
+  VT rz0 = rzt.a, rz1 = rzt.b;
+  // the tail was solved in fwd_pass: only the rows before it remain
+  const int nb = M.ntblev;
+  const int32_t* bptr = M.tblev_ptr;
+  const int32_t* brows = M.tblev_rows;
+  for (int lev = 0; lev < nb; ++lev) {
+    const int r0 = __ldg(bptr + lev), r1 = __ldg(bptr + lev + 1);
     int in_[UNR], cn[UNR][KU];
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
       in_[u] = 0;
       if (r0 + g.rs + u * RPS < r1) {
-        in_[u] = __ldg(M.blev_rows + r0 + g.rs + u * RPS);
+        in_[u] = __ldg(brows + r0 + g.rs + u * RPS);
         ld_cols<KU>(M.U.col + (size_t)in_[u] * KU, cn[u]);
       }
     }
@@ -438,7 +552,7 @@ __device__ __forceinline__ Pair<VT> bwd_pass(const DevMatT<VT>& M, const VT* __r
         for (int k = 0; k < KU; ++k) c[u][k] = cn[u][k];
         const int kn = k0 + STEP + u * RPS;
         if (kn < r1) {
-          in_[u] = __ldg(M.blev_rows + kn);
+          in_[u] = __ldg(brows + kn);
           ld_cols<KU>(M.U.col + (size_t)in_[u] * KU, cn[u]);
         }
       }
@@ -584,6 +698,8 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
                           VT* r, VT* p, VT* q, VT* z, const int* ra_, const int* rb_,
                           const double* w_, int* iters) {
   __shared__ PcgLanes<T, VT> S;
+  // right-hand side and y of the schedule's tail (lane pairs: 16-byte aligned)
+  __shared__ __align__(16) VT zt[TAIL_ROWS * T];
   const Geo<T> g;
   const int l0 = g.lane, l1 = g.lane + 1;
   const int ra0 = ra_[l0], rb0 = rb_[l0], ra1 = ra_[l1], rb1 = rb_[l1];
@@ -600,8 +716,9 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
   if (jac) {
     jacobi_pass<T, VT, false>(M, x, r, p, q, z, (VT)0, (VT)0, ra0, rb0, w0, ra1, rb1, w1, bbp, rzp);
   } else {
-    bbp = fwd_pass<T, VT, false>(M, x, r, p, q, z, (VT)0, (VT)0);
-    rzp = bwd_pass<T, VT>(M, r, z);
+    Pair<VT> rzt{0, 0};
+    bbp = fwd_pass<T, VT, false>(M, x, r, p, q, z, (VT)0, (VT)0, zt, rzt);
+    rzp = bwd_pass<T, VT>(M, r, z, rzt);
   }
   const Pair<VT> bb = lane_sum<T, RS_BB>(L, bbp.a, bbp.b);
   const Pair<VT> rz0 = lane_sum<T, RS_RZ0>(L, rzp.a, rzp.b);
@@ -648,7 +765,7 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
     if (jac) {
       jacobi_pass<T, VT, true>(M, x, r, p, q, z, al0, al1, ra0, rb0, w0, ra1, rb1, w1, rrp, rzn);
     } else {
-      rrp = fwd_pass<T, VT, true>(M, x, r, p, q, z, al0, al1);
+      rrp = fwd_pass<T, VT, true>(M, x, r, p, q, z, al0, al1, zt, rzn);  // rzn: the tail's r.z
     }
     const Pair<VT> rr = lane_sum<T, RS_RR>(L, rrp.a, rrp.b);
     if (g.rs == 0) {
@@ -675,7 +792,7 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
 #pragma unroll 1
     for (int k = 0; k < T; ++k) any |= !(S.pdone[k] | S.stop[k]);
     if (!any) break;
-    if (!jac) rzn = bwd_pass<T, VT>(M, r, z);
+    if (!jac) rzn = bwd_pass<T, VT>(M, r, z, rzn);
     const Pair<VT> rz = lane_sum<T, RS_RZ>(L, rzn.a, rzn.b);
     VT be0 = 0, be1 = 0;
     if (go0) be0 = rz.a / S.rz[par][l0];
