@@ -180,7 +180,7 @@ __device__ __forceinline__ void rotate(double th_new, double d, double& c, doubl
 // theta += dtheta (P half-step) or |V| += dV (Q half-step) on the matrix's
 // rows, then refresh the rectangular voltages.
 template <int T, typename VT, bool IS_P>
-__device__ __forceinline__ void update_pass(const DevMatT<VT>& M, LaneState<T>& L, const VT* __restrict__ x,
+__device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>& L, const VT* __restrict__ x,
                             double* th, double* V, double* C, double* Sn, double* E, double* F) {
   const Geo<T> g;
   const int l0 = g.lane, l1 = g.lane + 1;
@@ -382,11 +382,25 @@ __device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& 
 // lane (the slot's lanes are compacted onto live work) and the kernel ends
 // when the queue is drained and every lane has retired.
 template <int T, typename VT>
-__global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS) fdpf_tiles_kernel(FdpfParams P, DevMatT<VT> MP,
-                                                              DevMatT<VT> MQ) {
+__global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
+    fdpf_tiles_kernel(FdpfParams P_, DevMatT<VT> MP_, DevMatT<VT> MQ_) {
   __shared__ LaneState<T> L;
-  const Geo<T> g;
+  // the parameter blocks in shared memory: the out-of-line passes take them
+  // by reference, so their fields are read from shared memory rather than
+  // from a per-thread local copy
+  __shared__ __align__(16) unsigned char pbuf[sizeof(FdpfParams)];
+  __shared__ __align__(16) unsigned char mbuf[2][sizeof(DevMatT<VT>)];
   const int tid = threadIdx.x;
+  if (tid == 0) {
+    memcpy(pbuf, &P_, sizeof(FdpfParams));
+    memcpy(mbuf[0], &MP_, sizeof(DevMatT<VT>));
+    memcpy(mbuf[1], &MQ_, sizeof(DevMatT<VT>));
+  }
+  __syncthreads();
+  const FdpfParams& P = *reinterpret_cast<const FdpfParams*>(pbuf);
+  const DevMatT<VT>& MP = *reinterpret_cast<const DevMatT<VT>*>(mbuf[0]);
+  const DevMatT<VT>& MQ = *reinterpret_cast<const DevMatT<VT>*>(mbuf[1]);
+  const Geo<T> g;
   VT* x = (VT*)P.wx + (size_t)blockIdx.x * P.vstride;
   VT* r = (VT*)P.wr + (size_t)blockIdx.x * P.vstride;
   VT* p = (VT*)P.wp + (size_t)blockIdx.x * P.vstride;
@@ -546,7 +560,7 @@ __global__ void __launch_bounds__(NTHREADS) apply_kernel(DevMatT<VT> M, int op, 
     }
     __syncthreads();
     if (op == 0) {
-      spmv_pass<T, VT>(M, a, b, ra[0], rb[0], w[0], ra[1], rb[1], w[1]);
+      spmv_pass<T, VT, false>(M, a, nullptr, b, ra[0], rb[0], w[0], ra[1], rb[1], w[1]);
     } else if (precond == PREC_JACOBI) {
       Pair<VT> rr{0, 0}, rz{0, 0};
       jacobi_pass<T, VT, false>(M, c, a, nullptr, nullptr, b, (VT)0, (VT)0, ra[0], rb[0], w[0],

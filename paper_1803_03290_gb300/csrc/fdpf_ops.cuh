@@ -26,6 +26,11 @@ constexpr int MIS_GROUP = FDPF_MIS_GROUP;  // neighbours loaded together in the 
 #ifndef GPCG_PASS_INLINE
 #define GPCG_PASS_INLINE __noinline__
 #endif
+// The row loops of the inner solve: inlined into their caller by default;
+// -DGPCG_LOOP_INLINE=__noinline__ gives each its own register allocation.
+#ifndef GPCG_LOOP_INLINE
+#define GPCG_LOOP_INLINE __forceinline__
+#endif
 #ifndef FDPF_MIN_BLOCKS
 #define FDPF_MIN_BLOCKS 5  // resident CTAs per SM the register budget is cut for
 #endif
@@ -247,13 +252,24 @@ __device__ __forceinline__ Pair<unsigned long long> lane_max_bits(LaneState<T>& 
 }
 
 // ----------------------------------------------------- batched operators
-// q = B_s p for the thread's two lanes: base row times p, plus the outaged
+// y = B_s v for the thread's two lanes: base row times v, plus the outaged
 // branch's four-element change (Sec. IV.B) -- off-diagonal +w, diagonal -w
-// at both ends.  Returns the lanes' partial p.q.
-template <int T, typename VT>
-__device__ __forceinline__ Pair<VT> spmv_pass(const DevMatT<VT>& M, const VT* __restrict__ p,
-                                                  VT* __restrict__ q, int ra0, int rb0, VT w0,
-                                                  int ra1, int rb1, VT w1) {
+// at both ends.
+//
+// Plain (DIRECTION = false): q = B_s p, returns the lanes' partial p.q.
+// DIRECTION = true, the PCG direction update folded in: with v = z,
+//   p <- mask(z) + beta p,   q <- mask(B_s z) + beta q,
+// which is q = B_s p for the new p because q held B_s p for the old one
+// (first: p = mask(z), q = mask(B_s z)).  mask zeroes the rows of islanded
+// buses: B_s couples no main-island row to an islanded one, so on the main
+// island B_s z = B_s mask(z).  Returns the partial p.q of the new p, q.
+template <int T, typename VT, bool DIRECTION>
+__device__ GPCG_LOOP_INLINE Pair<VT> spmv_pass(const DevMatT<VT>& M, const VT* __restrict__ v_,
+                                              VT* __restrict__ p, VT* __restrict__ q, int ra0,
+                                              int rb0, VT w0, int ra1, int rb1, VT w1,
+                                              VT be0 = 0, VT be1 = 0, bool first = true,
+                                              int lo0 = 0, int cnt0 = 0, int lo1 = 0,
+                                              int cnt1 = 0) {
   const Geo<T> g;
   constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
   VT pq0 = 0, pq1 = 0;
@@ -261,7 +277,7 @@ __device__ __forceinline__ Pair<VT> spmv_pass(const DevMatT<VT>& M, const VT* __
   // loaded one step ahead: each step waits on one memory latency for
   // UNR rows' gathers
   // rows are visited in bus order (M.visit), so a row's neighbours were
-  // visited just before it and their chunks of p are still in cache
+  // visited just before it and their chunks of v are still in cache
   int cn[UNR][KA], vn[UNR];
 #pragma unroll
   for (int u = 0; u < UNR; ++u)
@@ -290,8 +306,8 @@ __device__ __forceinline__ Pair<VT> spmv_pass(const DevMatT<VT>& M, const VT* __
       if (i0 + u * RPS < M.n) {
         ld_vals<KA>(M.A.val + (size_t)i * KA, v[u]);
 #pragma unroll
-        for (int k = 0; k < KA; ++k) pc[u][k] = ld2(p + (size_t)c[u][k] * T + g.lane);
-        pi[u] = ld2(p + (size_t)i * T + g.lane);
+        for (int k = 0; k < KA; ++k) pc[u][k] = ld2(v_ + (size_t)c[u][k] * T + g.lane);
+        pi[u] = ld2(v_ + (size_t)i * T + g.lane);
       }
     }
 #pragma unroll
@@ -310,15 +326,34 @@ __device__ __forceinline__ Pair<VT> spmv_pass(const DevMatT<VT>& M, const VT* __
       for (int o = o0; o < o1; ++o) {
         const int cc = __ldg(M.A.ocol + o);
         const VT vv = __ldg(M.A.oval + o);
-        const Pair<VT> pp = ld2(p + (size_t)cc * T + g.lane);
+        const Pair<VT> pp = ld2(v_ + (size_t)cc * T + g.lane);
         a0 += (vv + (cc == oth0 ? w0 : (VT)0)) * pp.a;
         a1 += (vv + (cc == oth1 ? w1 : (VT)0)) * pp.b;
       }
       if (oth0 != -2) a0 -= w0 * pi[u].a;
       if (oth1 != -2) a1 -= w1 * pi[u].b;
-      st2(q + (size_t)i * T + g.lane, Pair<VT>{a0, a1});
-      pq0 += pi[u].a * a0;
-      pq1 += pi[u].b * a1;
+      const size_t o = (size_t)i * T + g.lane;
+      if (DIRECTION) {
+        const int pr = __ldg(M.pre_of_row + i);
+        const bool m0 = in_island(pr, lo0, cnt0), m1 = in_island(pr, lo1, cnt1);
+        Pair<VT> pn{m0 ? (VT)0 : pi[u].a, m1 ? (VT)0 : pi[u].b};
+        Pair<VT> qn{m0 ? (VT)0 : a0, m1 ? (VT)0 : a1};
+        if (!first) {
+          const Pair<VT> po = ld2(p + o), qo = ld2(q + o);
+          pn.a += be0 * po.a;
+          pn.b += be1 * po.b;
+          qn.a += be0 * qo.a;
+          qn.b += be1 * qo.b;
+        }
+        st2(p + o, pn);
+        st2(q + o, qn);
+        pq0 += pn.a * qn.a;
+        pq1 += pn.b * qn.b;
+      } else {
+        st2(q + o, Pair<VT>{a0, a1});
+        pq0 += pi[u].a * a0;
+        pq1 += pi[u].b * a1;
+      }
     }
   }
   return {pq0, pq1};
@@ -335,7 +370,7 @@ __device__ __forceinline__ Pair<VT> spmv_pass(const DevMatT<VT>& M, const VT* __
 // then y (TAIL_ROWS rows of T lanes).  Adds the tail rows' r.r to rr and
 // their r.z to rzt; writes the tail's final z.
 template <int T, typename VT, bool FUSED>
-__device__ __forceinline__ void tail_solve(const DevMatT<VT>& M, VT* __restrict__ x,
+__device__ GPCG_LOOP_INLINE void tail_solve(const DevMatT<VT>& M, VT* __restrict__ x,
                                            VT* __restrict__ r, const VT* __restrict__ p,
                                            const VT* __restrict__ q, VT* __restrict__ z,
                                            VT al0, VT al1, VT* __restrict__ s, VT& rr0, VT& rr1,
@@ -437,7 +472,7 @@ __device__ __forceinline__ void tail_solve(const DevMatT<VT>& M, VT* __restrict_
 // are independent).  With FUSED, first x += alpha p and r -= alpha q (the
 // PCG update); without it, x = 0.  Accumulates r.r.
 template <int T, typename VT, bool FUSED>
-__device__ __forceinline__ Pair<VT> fwd_pass(const DevMatT<VT>& M, VT* __restrict__ x,
+__device__ GPCG_LOOP_INLINE Pair<VT> fwd_pass(const DevMatT<VT>& M, VT* __restrict__ x,
                                                  VT* __restrict__ r, const VT* __restrict__ p,
                                                  const VT* __restrict__ q, VT* __restrict__ z,
                                                  VT al0, VT al1, VT* zt, Pair<VT>& rzt) {
@@ -521,7 +556,7 @@ __device__ __forceinline__ Pair<VT> fwd_pass(const DevMatT<VT>& M, VT* __restric
 // Back substitution L^T z = y in place (z holds y on entry), over the
 // backward level schedule; accumulates r.z.
 template <int T, typename VT>
-__device__ __forceinline__ Pair<VT> bwd_pass(const DevMatT<VT>& M, const VT* __restrict__ r,
+__device__ GPCG_LOOP_INLINE Pair<VT> bwd_pass(const DevMatT<VT>& M, const VT* __restrict__ r,
                                                  VT* __restrict__ z, Pair<VT> rzt) {
   const Geo<T> g;
   constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
@@ -604,7 +639,7 @@ __device__ __forceinline__ Pair<VT> bwd_pass(const DevMatT<VT>& M, const VT* __r
 // Jacobi: z = r / diag(B_s), the diagonal with the outage applied; a row
 // whose diagonal vanishes (a bus the outage isolates) gets z = 0.
 template <int T, typename VT, bool FUSED>
-__device__ __forceinline__ void jacobi_pass(const DevMatT<VT>& M, VT* __restrict__ x,
+__device__ GPCG_LOOP_INLINE void jacobi_pass(const DevMatT<VT>& M, VT* __restrict__ x,
                                             VT* __restrict__ r, const VT* __restrict__ p,
                                             const VT* __restrict__ q, VT* __restrict__ z, VT al0,
                                             VT al1, int ra0, int rb0, VT w0, int ra1, int rb1,
@@ -632,43 +667,6 @@ __device__ __forceinline__ void jacobi_pass(const DevMatT<VT>& M, VT* __restrict
     rr.b += ri.b * ri.b;
     rz.a += ri.a * z0;
     rz.b += ri.b * z1;
-  }
-  __syncthreads();
-}
-
-// p = mask(z) + beta p: islanded rows keep a zero search direction.
-template <int T, typename VT>
-__device__ __forceinline__ void pupdate_pass(const DevMatT<VT>& M, const VT* __restrict__ z,
-                                             VT* __restrict__ p, VT be0, VT be1, int lo0,
-                                             int cnt0, int lo1, int cnt1, bool first) {
-  const Geo<T> g;
-  constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
-  for (int i0 = g.rs; i0 < M.n; i0 += STEP) {
-    int pr[UNR], ii[UNR];
-    Pair<VT> zi[UNR], pi[UNR];
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      const int i = i0 + u * RPS < M.n ? __ldg(M.visit + i0 + u * RPS) : 0;
-      ii[u] = i;
-      if (i0 + u * RPS < M.n) {
-        const size_t o = (size_t)i * T + g.lane;
-        pr[u] = __ldg(M.pre_of_row + i);
-        zi[u] = ld2(z + o);
-        if (!first) pi[u] = ld2(p + o);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      const int i = ii[u];
-      if (i0 + u * RPS >= M.n) continue;
-      Pair<VT> pn{in_island(pr[u], lo0, cnt0) ? (VT)0 : zi[u].a,
-                  in_island(pr[u], lo1, cnt1) ? (VT)0 : zi[u].b};
-      if (!first) {
-        pn.a += be0 * pi[u].a;
-        pn.b += be1 * pi[u].b;
-      }
-      st2(p + (size_t)i * T + g.lane, pn);
-    }
   }
   __syncthreads();
 }
@@ -736,16 +734,19 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
       S.pdone[ln] = !L.active[ln] || !(b_ > (VT)0) || !(r_ > (VT)0);
     }
   }
-  pupdate_pass<T, VT>(M, z, p, (VT)0, (VT)0, lo0, cnt0, lo1, cnt1, true);  // ends in a barrier
+  __syncthreads();  // publishes S and the first z
   const VT tol2 = (VT)(P.inner_rtol * P.inner_rtol);
   int par = 0;
+  VT be0 = 0, be1 = 0;
   for (int it = 0; it < P.max_inner; ++it) {
     bool any = false;
 #pragma unroll 1
     for (int k = 0; k < T; ++k) any |= !(S.pdone[k] | S.stop[k]);
     if (!any) break;
     const bool run0 = !(S.pdone[l0] | S.stop[l0]), run1 = !(S.pdone[l1] | S.stop[l1]);
-    const Pair<VT> pqp = spmv_pass<T, VT>(M, p, q, ra0, rb0, w0, ra1, rb1, w1);
+    // new direction p = mask(z) + beta p and q = B_s p in one pass
+    const Pair<VT> pqp = spmv_pass<T, VT, true>(M, z, p, q, ra0, rb0, w0, ra1, rb1, w1, be0,
+                                                be1, it == 0, lo0, cnt0, lo1, cnt1);
     const Pair<VT> pq = lane_sum<T, RS_PQ>(L, pqp.a, pqp.b);
     VT al0 = 0, al1 = 0;
     bool bk0 = false, bk1 = false;
@@ -794,9 +795,8 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
     if (!any) break;
     if (!jac) rzn = bwd_pass<T, VT>(M, r, z, rzn);
     const Pair<VT> rz = lane_sum<T, RS_RZ>(L, rzn.a, rzn.b);
-    VT be0 = 0, be1 = 0;
-    if (go0) be0 = rz.a / S.rz[par][l0];
-    if (go1) be1 = rz.b / S.rz[par][l1];
+    be0 = go0 ? rz.a / S.rz[par][l0] : (VT)0;
+    be1 = go1 ? rz.b / S.rz[par][l1] : (VT)0;
     if (g.rs == 0) {
 #pragma unroll
       for (int j = 0; j < LP; ++j) {
@@ -807,7 +807,7 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
         if (!(v > (VT)0)) S.stop[ln] = 1;
       }
     }
-    pupdate_pass<T, VT>(M, z, p, be0, be1, lo0, cnt0, lo1, cnt1, false);  // ends in a barrier
+    __syncthreads();  // publishes S.rz, S.stop and z
     par ^= 1;
   }
   __syncthreads();
