@@ -419,10 +419,15 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     L.drained = 0;
   }
   if (tid < T) {
+    // a lane the queue never fills keeps these: no outage, nothing islanded
     L.scen[tid] = -1;
     L.active[tid] = 0;
     L.done[tid] = 0;
     L.fresh[tid] = 0;
+    L.l[tid] = L.fb[tid] = L.tb[tid] = -1;
+    L.raP[tid] = L.rbP[tid] = L.raQ[tid] = L.rbQ[tid] = -1;
+    L.wP[tid] = L.wQ[tid] = 0.0;
+    L.lo[tid] = L.cnt[tid] = 0;
   }
   __syncthreads();
 #define GPCG_PHASE(k)                                  \

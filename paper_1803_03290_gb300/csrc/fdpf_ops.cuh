@@ -314,24 +314,30 @@ __device__ GPCG_LOOP_INLINE Pair<VT> spmv_pass(const DevMatT<VT>& M, const VT* _
     for (int u = 0; u < UNR; ++u) {
       const int i = ii[u];
       if (i0 + u * RPS >= M.n) continue;
-      const int oth0 = (i == ra0) ? rb0 : ((i == rb0) ? ra0 : -2);
-      const int oth1 = (i == ra1) ? rb1 : ((i == rb1) ? ra1 : -2);
       VT a0 = 0, a1 = 0;
 #pragma unroll
       for (int k = 0; k < KA; ++k) {
-        a0 += (v[u][k] + (c[u][k] == oth0 ? w0 : (VT)0)) * pc[u][k].a;
-        a1 += (v[u][k] + (c[u][k] == oth1 ? w1 : (VT)0)) * pc[u][k].b;
+        a0 += v[u][k] * pc[u][k].a;
+        a1 += v[u][k] * pc[u][k].b;
       }
       const int o0 = __ldg(M.A.optr + i), o1 = __ldg(M.A.optr + i + 1);
       for (int o = o0; o < o1; ++o) {
         const int cc = __ldg(M.A.ocol + o);
         const VT vv = __ldg(M.A.oval + o);
         const Pair<VT> pp = ld2(v_ + (size_t)cc * T + g.lane);
-        a0 += (vv + (cc == oth0 ? w0 : (VT)0)) * pp.a;
-        a1 += (vv + (cc == oth1 ? w1 : (VT)0)) * pp.b;
+        a0 += vv * pp.a;
+        a1 += vv * pp.b;
       }
-      if (oth0 != -2) a0 -= w0 * pi[u].a;
-      if (oth1 != -2) a1 -= w1 * pi[u].b;
+      // the outage's change, on the two rows of the outaged branch only:
+      // + w v_other (when the other end has a row) - w v_own
+      if (i == ra0 || i == rb0) {
+        const int oth = (i == ra0) ? rb0 : ra0;
+        a0 += w0 * ((oth >= 0 ? v_[(size_t)oth * T + g.lane] : (VT)0) - pi[u].a);
+      }
+      if (i == ra1 || i == rb1) {
+        const int oth = (i == ra1) ? rb1 : ra1;
+        a1 += w1 * ((oth >= 0 ? v_[(size_t)oth * T + g.lane + 1] : (VT)0) - pi[u].b);
+      }
       const size_t o = (size_t)i * T + g.lane;
       if (DIRECTION) {
         const int pr = __ldg(M.pre_of_row + i);
@@ -470,168 +476,175 @@ __device__ GPCG_LOOP_INLINE void tail_solve(const DevMatT<VT>& M, VT* __restrict
 
 // Forward substitution L y = r over the level schedule (rows of one level
 // are independent).  With FUSED, first x += alpha p and r -= alpha q (the
-// PCG update); without it, x = 0.  Accumulates r.r.
+// PCG update); without it, x = 0.  Accumulates r.r.  Each thread loads the
+// column indices of its next row -- in this level or the next -- while it
+// works on the current one, and the next level's bounds a level ahead, so
+// after a level barrier only the gathers of the solved values are waited on.
 template <int T, typename VT, bool FUSED>
 __device__ GPCG_LOOP_INLINE Pair<VT> fwd_pass(const DevMatT<VT>& M, VT* __restrict__ x,
                                                  VT* __restrict__ r, const VT* __restrict__ p,
                                                  const VT* __restrict__ q, VT* __restrict__ z,
                                                  VT al0, VT al1, VT* zt, Pair<VT>& rzt) {
   const Geo<T> g;
-  constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
+  constexpr int RPS = Geo<T>::RPS;
   VT rr0 = 0, rr1 = 0;
-  for (int lev = 0; lev < M.tail_lev; ++lev) {
-    const int r0 = __ldg(M.lev_ptr + lev), r1 = __ldg(M.lev_ptr + lev + 1);
-    int cn[UNR][KL];
+  const int nl = M.tail_lev;
+  int r0 = 0, r1 = 0, pf = -1, cn[KL];
+  if (nl > 0) {
+    r0 = __ldg(M.lev_ptr);
+    r1 = __ldg(M.lev_ptr + 1);
+    if (r0 + g.rs < r1) {
+      pf = r0 + g.rs;
+      ld_cols<KL>(M.L.col + (size_t)pf * KL, cn);
+    }
+  }
+  for (int lev = 0; lev < nl; ++lev) {
+    const int r2 = (lev + 1 < nl) ? __ldg(M.lev_ptr + lev + 2) : r1;  // end of the next level
+    for (int i = r0 + g.rs; i < r1; i += RPS) {
+      int c[KL];
+      if (pf == i) {
 #pragma unroll
-    for (int u = 0; u < UNR; ++u)
-      if (r0 + g.rs + u * RPS < r1) ld_cols<KL>(M.L.col + (size_t)(r0 + g.rs + u * RPS) * KL, cn[u]);
-    for (int i0 = r0 + g.rs; i0 < r1; i0 += STEP) {
-      int c[UNR][KL];
-      VT v[UNR][KL];
-      Pair<VT> zc[UNR][KL], ri[UNR], pi[UNR], qi[UNR], xi[UNR];
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-#pragma unroll
-        for (int k = 0; k < KL; ++k) c[u][k] = cn[u][k];
-        const int in = i0 + STEP + u * RPS;
-        if (in < r1) ld_cols<KL>(M.L.col + (size_t)in * KL, cn[u]);
+        for (int k = 0; k < KL; ++k) c[k] = cn[k];
+      } else {
+        ld_cols<KL>(M.L.col + (size_t)i * KL, c);
       }
+      const size_t o = (size_t)i * T + g.lane;
+      VT v[KL];
+      Pair<VT> zc[KL], ri, pi, qi, xi;
+      if (M.Lh) ld_halfs<KL>(M.Lh + (size_t)i * KL, v);
+      else ld_vals<KL>(M.L.val + (size_t)i * KL, v);
 #pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        const int i = i0 + u * RPS;
-        if (i < r1) {
-          const size_t o = (size_t)i * T + g.lane;
-          if (M.Lh) ld_halfs<KL>(M.Lh + (size_t)i * KL, v[u]);
-          else ld_vals<KL>(M.L.val + (size_t)i * KL, v[u]);
-#pragma unroll
-          for (int k = 0; k < KL; ++k) zc[u][k] = ld2(z + (size_t)c[u][k] * T + g.lane);
-          ri[u] = ld2(r + o);
-          if (FUSED) {
-            pi[u] = ld2(p + o);
-            qi[u] = ld2(q + o);
-            xi[u] = ld2(x + o);
-          }
-        }
+      for (int k = 0; k < KL; ++k) zc[k] = ld2(z + (size_t)c[k] * T + g.lane);
+      ri = ld2(r + o);
+      if (FUSED) {
+        pi = ld2(p + o);
+        qi = ld2(q + o);
+        xi = ld2(x + o);
       }
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        const int i = i0 + u * RPS;
-        if (i >= r1) continue;
-        const size_t o = (size_t)i * T + g.lane;
-        Pair<VT> rv = ri[u];
-        if (FUSED) {
-          st2(x + o, Pair<VT>{xi[u].a + al0 * pi[u].a, xi[u].b + al1 * pi[u].b});
-          rv.a -= al0 * qi[u].a;
-          rv.b -= al1 * qi[u].b;
-          st2(r + o, rv);
-        } else {
-          st2(x + o, Pair<VT>{(VT)0, (VT)0});
-        }
-        rr0 += rv.a * rv.a;
-        rr1 += rv.b * rv.b;
-        VT a0 = rv.a, a1 = rv.b;
-#pragma unroll
-        for (int k = 0; k < KL; ++k) {
-          a0 -= v[u][k] * zc[u][k].a;
-          a1 -= v[u][k] * zc[u][k].b;
-        }
-        const int o0 = __ldg(M.L.optr + i), o1 = __ldg(M.L.optr + i + 1);
-        for (int e = o0; e < o1; ++e) {
-          const VT vv = M.Lh ? (VT)__half2float(M.Loh[e]) : __ldg(M.L.oval + e);
-          const Pair<VT> zz = ld2(z + (size_t)__ldg(M.L.ocol + e) * T + g.lane);
-          a0 -= vv * zz.a;
-          a1 -= vv * zz.b;
-        }
-        // scaled factor: unit diagonal, w = D y is what is stored
-        const VT id = M.Lh ? (VT)1 : __ldg(M.inv_diag + i);
-        st2(z + o, Pair<VT>{a0 * id, a1 * id});
+      // the thread's next row: in this level, else the first of the next
+      const int is = (i + RPS < r1) ? i + RPS : ((lev + 1 < nl && r1 + g.rs < r2) ? r1 + g.rs : -1);
+      pf = is;
+      if (is >= 0) ld_cols<KL>(M.L.col + (size_t)is * KL, cn);
+      Pair<VT> rv = ri;
+      if (FUSED) {
+        st2(x + o, Pair<VT>{xi.a + al0 * pi.a, xi.b + al1 * pi.b});
+        rv.a -= al0 * qi.a;
+        rv.b -= al1 * qi.b;
+        st2(r + o, rv);
+      } else {
+        st2(x + o, Pair<VT>{(VT)0, (VT)0});
       }
+      rr0 += rv.a * rv.a;
+      rr1 += rv.b * rv.b;
+      VT a0 = rv.a, a1 = rv.b;
+#pragma unroll
+      for (int k = 0; k < KL; ++k) {
+        a0 -= v[k] * zc[k].a;
+        a1 -= v[k] * zc[k].b;
+      }
+      const int o0 = __ldg(M.L.optr + i), o1 = __ldg(M.L.optr + i + 1);
+      for (int e = o0; e < o1; ++e) {
+        const VT vv = M.Lh ? (VT)__half2float(M.Loh[e]) : __ldg(M.L.oval + e);
+        const Pair<VT> zz = ld2(z + (size_t)__ldg(M.L.ocol + e) * T + g.lane);
+        a0 -= vv * zz.a;
+        a1 -= vv * zz.b;
+      }
+      // scaled factor: unit diagonal, w = D y is what is stored
+      const VT id = M.Lh ? (VT)1 : __ldg(M.inv_diag + i);
+      st2(z + o, Pair<VT>{a0 * id, a1 * id});
+    }
+    // no row in this level: load the next level's first row ahead anyway
+    if (pf < 0 && lev + 1 < nl && r1 + g.rs < r2) {
+      pf = r1 + g.rs;
+      ld_cols<KL>(M.L.col + (size_t)pf * KL, cn);
     }
     __syncthreads();
+    r0 = r1;
+    r1 = r2;
   }
   if (M.tail_row0 < M.n) tail_solve<T, VT, FUSED>(M, x, r, p, q, z, al0, al1, zt, rr0, rr1, rzt);
   return {rr0, rr1};
 }
 
 // Back substitution L^T z = y in place (z holds y on entry), over the
-// backward level schedule; accumulates r.z.
+// backward level schedule of the rows before the tail (the tail was solved
+// in fwd_pass); accumulates r.z.  Rows and their column indices are loaded
+// one row ahead across level barriers, as in fwd_pass.
 template <int T, typename VT>
 __device__ GPCG_LOOP_INLINE Pair<VT> bwd_pass(const DevMatT<VT>& M, const VT* __restrict__ r,
                                                  VT* __restrict__ z, Pair<VT> rzt) {
   const Geo<T> g;
-  constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
+  constexpr int RPS = Geo<T>::RPS;
   VT rz0 = rzt.a, rz1 = rzt.b;
-  // the tail was solved in fwd_pass: only the rows before it remain
   const int nb = M.ntblev;
   const int32_t* bptr = M.tblev_ptr;
   const int32_t* brows = M.tblev_rows;
-  for (int lev = 0; lev < nb; ++lev) {
-    const int r0 = __ldg(bptr + lev), r1 = __ldg(bptr + lev + 1);
-    int in_[UNR], cn[UNR][KU];
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      in_[u] = 0;
-      if (r0 + g.rs + u * RPS < r1) {
-        in_[u] = __ldg(brows + r0 + g.rs + u * RPS);
-        ld_cols<KU>(M.U.col + (size_t)in_[u] * KU, cn[u]);
-      }
+  int r0 = 0, r1 = 0, pk = -1, pi_ = 0, cn[KU];
+  if (nb > 0) {
+    r0 = __ldg(bptr);
+    r1 = __ldg(bptr + 1);
+    if (r0 + g.rs < r1) {
+      pk = r0 + g.rs;
+      pi_ = __ldg(brows + pk);
+      ld_cols<KU>(M.U.col + (size_t)pi_ * KU, cn);
     }
-    for (int k0 = r0 + g.rs; k0 < r1; k0 += STEP) {
-      int ii[UNR], c[UNR][KU];
-      VT v[UNR][KU];
-      Pair<VT> zc[UNR][KU], yi[UNR], ri[UNR];
+  }
+  for (int lev = 0; lev < nb; ++lev) {
+    const int r2 = (lev + 1 < nb) ? __ldg(bptr + lev + 2) : r1;
+    for (int k = r0 + g.rs; k < r1; k += RPS) {
+      int i, c[KU];
+      if (pk == k) {
+        i = pi_;
 #pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        ii[u] = in_[u];
-#pragma unroll
-        for (int k = 0; k < KU; ++k) c[u][k] = cn[u][k];
-        const int kn = k0 + STEP + u * RPS;
-        if (kn < r1) {
-          in_[u] = __ldg(brows + kn);
-          ld_cols<KU>(M.U.col + (size_t)in_[u] * KU, cn[u]);
-        }
+        for (int a = 0; a < KU; ++a) c[a] = cn[a];
+      } else {
+        i = __ldg(brows + k);
+        ld_cols<KU>(M.U.col + (size_t)i * KU, c);
       }
+      const size_t o = (size_t)i * T + g.lane;
+      VT v[KU];
+      Pair<VT> zc[KU];
+      if (M.Uh) ld_halfs<KU>(M.Uh + (size_t)i * KU, v);
+      else ld_vals<KU>(M.U.val + (size_t)i * KU, v);
 #pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        if (k0 + u * RPS < r1) {
-          const size_t o = (size_t)ii[u] * T + g.lane;
-          if (M.Uh) ld_halfs<KU>(M.Uh + (size_t)ii[u] * KU, v[u]);
-          else ld_vals<KU>(M.U.val + (size_t)ii[u] * KU, v[u]);
-#pragma unroll
-          for (int k = 0; k < KU; ++k) zc[u][k] = ld2(z + (size_t)c[u][k] * T + g.lane);
-          yi[u] = ld2(z + o);
-          ri[u] = ld2(r + o);
-        }
+      for (int a = 0; a < KU; ++a) zc[a] = ld2(z + (size_t)c[a] * T + g.lane);
+      const Pair<VT> yi = ld2(z + o), ri = ld2(r + o);
+      const int ks = (k + RPS < r1) ? k + RPS : ((lev + 1 < nb && r1 + g.rs < r2) ? r1 + g.rs : -1);
+      pk = ks;
+      if (ks >= 0) {
+        pi_ = __ldg(brows + ks);
+        ld_cols<KU>(M.U.col + (size_t)pi_ * KU, cn);
       }
+      // scaled factor: L_s^T z = D^-2 w with a unit diagonal
+      const VT pre = M.Uh ? __ldg(M.inv_d2 + i) : (VT)1;
+      VT a0 = yi.a * pre, a1 = yi.b * pre;
 #pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        if (k0 + u * RPS >= r1) continue;
-        const int i = ii[u];
-        const size_t o = (size_t)i * T + g.lane;
-        // scaled factor: L_s^T z = D^-2 w with a unit diagonal
-        const VT pre = M.Uh ? __ldg(M.inv_d2 + i) : (VT)1;
-        VT a0 = yi[u].a * pre, a1 = yi[u].b * pre;
-#pragma unroll
-        for (int k = 0; k < KU; ++k) {
-          a0 -= v[u][k] * zc[u][k].a;
-          a1 -= v[u][k] * zc[u][k].b;
-        }
-        const int o0 = __ldg(M.U.optr + i), o1 = __ldg(M.U.optr + i + 1);
-        for (int e = o0; e < o1; ++e) {
-          const VT vv = M.Uh ? (VT)__half2float(M.Uoh[e]) : __ldg(M.U.oval + e);
-          const Pair<VT> zz = ld2(z + (size_t)__ldg(M.U.ocol + e) * T + g.lane);
-          a0 -= vv * zz.a;
-          a1 -= vv * zz.b;
-        }
-        const VT id = M.Uh ? (VT)1 : __ldg(M.inv_diag + i);
-        a0 *= id;
-        a1 *= id;
-        st2(z + o, Pair<VT>{a0, a1});
-        rz0 += ri[u].a * a0;
-        rz1 += ri[u].b * a1;
+      for (int a = 0; a < KU; ++a) {
+        a0 -= v[a] * zc[a].a;
+        a1 -= v[a] * zc[a].b;
       }
+      const int o0 = __ldg(M.U.optr + i), o1 = __ldg(M.U.optr + i + 1);
+      for (int e = o0; e < o1; ++e) {
+        const VT vv = M.Uh ? (VT)__half2float(M.Uoh[e]) : __ldg(M.U.oval + e);
+        const Pair<VT> zz = ld2(z + (size_t)__ldg(M.U.ocol + e) * T + g.lane);
+        a0 -= vv * zz.a;
+        a1 -= vv * zz.b;
+      }
+      const VT id = M.Uh ? (VT)1 : __ldg(M.inv_diag + i);
+      a0 *= id;
+      a1 *= id;
+      st2(z + o, Pair<VT>{a0, a1});
+      rz0 += ri.a * a0;
+      rz1 += ri.b * a1;
+    }
+    if (pk < 0 && lev + 1 < nb && r1 + g.rs < r2) {
+      pk = r1 + g.rs;
+      pi_ = __ldg(brows + pk);
+      ld_cols<KU>(M.U.col + (size_t)pi_ * KU, cn);
     }
     __syncthreads();
+    r0 = r1;
+    r1 = r2;
   }
   return {rz0, rz1};
 }
@@ -700,7 +713,11 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
   __shared__ __align__(16) VT zt[TAIL_ROWS * T];
   const Geo<T> g;
   const int l0 = g.lane, l1 = g.lane + 1;
-  const int ra0 = ra_[l0], rb0 = rb_[l0], ra1 = ra_[l1], rb1 = rb_[l1];
+  // the outage's rows (-1: none) of the lanes that run; the SpMV reads the
+  // vector at the other end's row
+  const bool on0 = L.active[l0], on1 = L.active[l1];
+  const int ra0 = on0 ? ra_[l0] : -1, rb0 = on0 ? rb_[l0] : -1;
+  const int ra1 = on1 ? ra_[l1] : -1, rb1 = on1 ? rb_[l1] : -1;
   const VT w0 = (VT)w_[l0], w1 = (VT)w_[l1];
   const int lo0 = L.lo[l0], cnt0 = L.cnt[l0], lo1 = L.lo[l1], cnt1 = L.cnt[l1];
   const bool jac = (P.precond == PREC_JACOBI);
