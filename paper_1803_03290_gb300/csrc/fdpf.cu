@@ -28,17 +28,29 @@
 namespace gpcg {
 
 // ------------------------------------------------------------ mismatch
-// dP_i, dQ_i of eqs. (1)-(3) from the rectangular voltages e + jf:
+// The rectangular voltages e + jf of a slot are stored interleaved,
+// [bus][lane][e, f], so one 16-byte load gives a lane's (e, f) and a thread's
+// two lanes sit in 32 contiguous bytes.
+template <int T>
+__device__ __forceinline__ size_t ef_at(int bus, int lane) {
+  return ((size_t)bus * T + lane) * 2;
+}
+
+// dP_i, dQ_i of eqs. (1)-(3) from the rectangular voltages:
 // I = Y V, P + jQ = V conj(I).  The outaged branch is left out of the
 // neighbour sum and of the diagonal.  WITH_P: the P half-step (writes
 // dP/V into the B' right-hand side and tracks max|dP| and max|dQ| for the
 // convergence test); otherwise writes dQ/V into the B'' right-hand side.
+// A thread takes a bus and both of its lanes at once: each neighbour's
+// admittance and the lanes' voltages are loaded once for the two lanes.
 template <int T, typename VT, bool WITH_P>
-__device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMatT<VT>& MP, const DevMatT<VT>& MQ,
-                              LaneState<T>& L, const double* __restrict__ E,
-                              const double* __restrict__ F, const double* __restrict__ V,
-                              VT* __restrict__ rhs, Pair<unsigned long long>& errP,
-                              Pair<unsigned long long>& errQ) {
+__device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMatT<VT>& MP,
+                                               const DevMatT<VT>& MQ, LaneState<T>& L,
+                                               const double* __restrict__ EF,
+                                               const double* __restrict__ V,
+                                               VT* __restrict__ rhs,
+                                               Pair<unsigned long long>& errP,
+                                               Pair<unsigned long long>& errQ) {
   const Geo<T> g;
   const DevGrid& G = P.G;
   const int l0 = g.lane, l1 = g.lane + 1;
@@ -67,65 +79,80 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
       ld_cols<KG>(G.adj_nbr + (size_t)(WITH_P ? kn : __ldg(MQ.bus_of_row + kn)) * KG, nbn);
     }
     const int i = WITH_P ? k : __ldg(MQ.bus_of_row + k);
-    const int bt = G.bus_type[i];
     const int pr = __ldg(G.pre + i);
     const bool on0 = act0 && !in_island(pr, lo0, cnt0);
     const bool on1 = act1 && !in_island(pr, lo1, cnt1);
     Pair<VT> out{(VT)0, (VT)0};
     if (on0 || on1) {
       const int deg = __ldg(G.adj_deg + i);
-      int br[KG];
-      ld_cols<KG>(G.adj_brl + (size_t)i * KG, br);
+      // -sum over the neighbours of Y_ij V_j, both lanes
+      double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
+#pragma unroll
+      for (int a0 = 0; a0 < KG; a0 += MIS_GROUP) {
+        double2 u0[MIS_GROUP], u1[MIS_GROUP];
+        double gv[MIS_GROUP], bv[MIS_GROUP];
+        int bb[MIS_GROUP];
+#pragma unroll
+        for (int a = 0; a < MIS_GROUP; ++a)
+          if (a0 + a < deg) {
+            const double2* q2 = reinterpret_cast<const double2*>(EF + ef_at<T>(nb[a0 + a], l0));
+            u0[a] = q2[0];
+            u1[a] = q2[1];
+            gv[a] = __ldg(G.adj_g + (size_t)i * KG + a0 + a);
+            bv[a] = __ldg(G.adj_b + (size_t)i * KG + a0 + a);
+            bb[a] = __ldg(G.adj_brl + (size_t)i * KG + a0 + a);
+          }
+#pragma unroll
+        for (int a = 0; a < MIS_GROUP; ++a)
+          if (a0 + a < deg) {
+            if (on0 && bb[a] != br0) {
+              re0 = fma(-gv[a], u0[a].x, fma(bv[a], u0[a].y, re0));
+              im0 = fma(-gv[a], u0[a].y, fma(-bv[a], u0[a].x, im0));
+            }
+            if (on1 && bb[a] != br1) {
+              re1 = fma(-gv[a], u1[a].x, fma(bv[a], u1[a].y, re1));
+              im1 = fma(-gv[a], u1[a].y, fma(-bv[a], u1[a].x, im1));
+            }
+          }
+      }
       const int o0 = __ldg(G.adj_optr + i), o1 = __ldg(G.adj_optr + i + 1);
+      for (int e = o0; e < o1; ++e) {
+        const int jn = __ldg(G.adj_onbr + e), b_ = __ldg(G.adj_obr + e);
+        const double gw = __ldg(G.adj_og + e), bw = __ldg(G.adj_ob + e);
+        const double2* q2 = reinterpret_cast<const double2*>(EF + ef_at<T>(jn, l0));
+        const double2 v0 = q2[0], v1 = q2[1];
+        if (on0 && b_ != br0) {
+          re0 = fma(-gw, v0.x, fma(bw, v0.y, re0));
+          im0 = fma(-gw, v0.y, fma(-bw, v0.x, im0));
+        }
+        if (on1 && b_ != br1) {
+          re1 = fma(-gw, v1.x, fma(bw, v1.y, re1));
+          im1 = fma(-gw, v1.y, fma(-bw, v1.x, im1));
+        }
+      }
+      // own voltage, the diagonal term and the mismatch of each lane
+      const double2* own = reinterpret_cast<const double2*>(EF + ef_at<T>(i, l0));
+      const double2 w0 = own[0], w1 = own[1];
+      const Pair<double> vi = ld2(V + (size_t)i * T + g.lane);
+      const int bt = G.bus_type[i];
       const double Gii = __ldg(G.Gii + i), Bii = __ldg(G.Bii + i), qs = __ldg(G.Q_sched + i);
       double Ps = 0.0, pg = 0.0;
       if (WITH_P) {
         Ps = __ldg(G.P_sched + i);
         if (bt == 1) pg = fmax(__ldg(G.P_gen + i), 0.0);  // generators with P_gen > 0 take it
       }
-      // the two lanes one after the other: half the live FP64 registers
-#pragma unroll 1
+#pragma unroll
       for (int j = 0; j < LP; ++j) {
         if (!(j ? on1 : on0)) continue;
-        const int ln = g.lane + j;
-        const size_t o = (size_t)i * T + ln;
-        const int brl = j ? br1 : br0;
-        const double ei = E[o], fi = F[o], Vi = V[o];
+        const double ei = j ? w1.x : w0.x, fi = j ? w1.y : w0.y;
         double Gd = Gii, Bd = Bii;
         if (i == (j ? fb1 : fb0) || i == (j ? tb1 : tb0)) {
           Gd -= j ? gl1 : gl0;
           Bd -= j ? bl1 : bl0;
         }
-        // I_i = sum_j Y_ij V_j accumulated as -I_i with fused multiply-adds
-        double re = fma(Gd, ei, -Bd * fi), im = fma(Gd, fi, Bd * ei);
-        // neighbours in groups of MIS_GROUP: bounds the live FP64 registers
-#pragma unroll
-        for (int a0 = 0; a0 < KG; a0 += MIS_GROUP) {
-          double ej[MIS_GROUP], fj[MIS_GROUP];
-#pragma unroll
-          for (int a = 0; a < MIS_GROUP; ++a)
-            if (a0 + a < deg) {
-              ej[a] = E[(size_t)nb[a0 + a] * T + ln];
-              fj[a] = F[(size_t)nb[a0 + a] * T + ln];
-            }
-#pragma unroll
-          for (int a = 0; a < MIS_GROUP; ++a)
-            if (a0 + a < deg && br[a0 + a] != brl) {
-              const double gv = __ldg(G.adj_g + (size_t)i * KG + a0 + a);
-              const double bv = __ldg(G.adj_b + (size_t)i * KG + a0 + a);
-              re = fma(-gv, ej[a], fma(bv, fj[a], re));
-              im = fma(-gv, fj[a], fma(-bv, ej[a], im));
-            }
-          asm volatile("" ::: "memory");
-        }
-        for (int e = o0; e < o1; ++e) {
-          const int jn = __ldg(G.adj_onbr + e), b_ = __ldg(G.adj_obr + e);
-          if (b_ == brl) continue;
-          const double gv = __ldg(G.adj_og + e), bv = __ldg(G.adj_ob + e);
-          const double ee = E[(size_t)jn * T + ln], ff = F[(size_t)jn * T + ln];
-          re = fma(-gv, ee, fma(bv, ff, re));
-          im = fma(-gv, ff, fma(-bv, ee, im));
-        }
+        // I_i = Y_ii V_i + sum_j Y_ij V_j
+        const double re = fma(Gd, ei, fma(-Bd, fi, j ? re1 : re0));
+        const double im = fma(Gd, fi, fma(Bd, ei, j ? im1 : im0));
         // dQ = Q_sched - Im(V_i conj(I_i)); dP = P_sched + re-dispatch - Re(...)
         VT res;
         if (WITH_P) {
@@ -135,10 +162,10 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
             const double dQ = fma(-fi, re, fma(ei, im, qs));
             if (j) upd_max_bits(errQ.b, dQ); else upd_max_bits(errQ.a, dQ);
           }
-          res = (VT)dP / (VT)Vi;
+          res = (VT)dP / (VT)(j ? vi.b : vi.a);
         } else {
           const double dQ = fma(-fi, re, fma(ei, im, qs));
-          res = (VT)dQ / (VT)Vi;
+          res = (VT)dQ / (VT)(j ? vi.b : vi.a);
         }
         if (j) out.b = res; else out.a = res;
       }
@@ -180,8 +207,9 @@ __device__ __forceinline__ void rotate(double th_new, double d, double& c, doubl
 // theta += dtheta (P half-step) or |V| += dV (Q half-step) on the matrix's
 // rows, then refresh the rectangular voltages.
 template <int T, typename VT, bool IS_P>
-__device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>& L, const VT* __restrict__ x,
-                            double* th, double* V, double* C, double* Sn, double* E, double* F) {
+__device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>& L,
+                                             const VT* __restrict__ x, double* th, double* V,
+                                             double* C, double* Sn, double* EF) {
   const Geo<T> g;
   const int l0 = g.lane, l1 = g.lane + 1;
   const int lo0 = L.lo[l0], cnt0 = L.cnt[l0], lo1 = L.lo[l1], cnt1 = L.cnt[l1];
@@ -211,8 +239,9 @@ __device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>&
       v.b += d1;
       st2(V + o, v);
     }
-    st2(E + o, Pair<double>{v.a * c.a, v.b * c.b});
-    st2(F + o, Pair<double>{v.a * s.a, v.b * s.b});
+    double2* ef = reinterpret_cast<double2*>(EF + ef_at<T>(i, g.lane));
+    ef[0] = make_double2(v.a * c.a, v.a * s.a);
+    ef[1] = make_double2(v.b * c.b, v.b * s.b);
   }
 }
 
@@ -251,8 +280,8 @@ __device__ __forceinline__ void setup_lane(const FdpfParams& P, const DevMatT<VT
 // Warm start (Sec. III.B) of the lanes flagged `fresh`: the base-case state,
 // zero on islanded buses.  Other lanes keep their state.
 template <int T>
-__device__ GPCG_PASS_INLINE void init_pass(const FdpfParams& P, LaneState<T>& L, double* th, double* V, double* C,
-                          double* Sn, double* E, double* F) {
+__device__ GPCG_PASS_INLINE void init_pass(const FdpfParams& P, LaneState<T>& L, double* th,
+                                           double* V, double* C, double* Sn, double* EF) {
   const Geo<T> g;
   const DevGrid& G = P.G;
   const int l0 = g.lane, l1 = g.lane + 1;
@@ -279,16 +308,19 @@ __device__ GPCG_PASS_INLINE void init_pass(const FdpfParams& P, LaneState<T>& L,
     put(V, i0 ? 0.0 : v0, i1 ? 0.0 : v0);
     put(C, c0, c0);
     put(Sn, s0, s0);
-    put(E, i0 ? 0.0 : v0 * c0, i1 ? 0.0 : v0 * c0);
-    put(F, i0 ? 0.0 : v0 * s0, i1 ? 0.0 : v0 * s0);
+    double2* ef = reinterpret_cast<double2*>(EF + ef_at<T>(i, g.lane));
+    const double e0 = v0 * c0, f0 = v0 * s0;
+    if (n0) ef[0] = i0 ? make_double2(0.0, 0.0) : make_double2(e0, f0);
+    if (n1) ef[1] = i1 ? make_double2(0.0, 0.0) : make_double2(e0, f0);
   }
 }
 
 // Outputs of the lanes flagged `done`: state, branch flows and loading
 // (Sec. I: overload screening), status and iteration counts.
 template <int T>
-__device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& L, const double* th,
-                            const double* V, const double* E, const double* F) {
+__device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& L,
+                                             const double* th, const double* V,
+                                             const double* EF) {
   const Geo<T> g;
   const DevGrid& G = P.G;
   const int l0 = g.lane, l1 = g.lane + 1;
@@ -318,8 +350,11 @@ __device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& 
       const int pa = __ldg(G.pre + a), pb = __ldg(G.pre + b);
       const bool off0 = !d0 || (k == br0) || in_island(pa, lo0, cnt0) || in_island(pb, lo0, cnt0);
       const bool off1 = !d1 || (k == br1) || in_island(pa, lo1, cnt1) || in_island(pb, lo1, cnt1);
-      const Pair<double> ea = ld2(E + (size_t)a * T + g.lane), fa = ld2(F + (size_t)a * T + g.lane);
-      const Pair<double> eb = ld2(E + (size_t)b * T + g.lane), fb = ld2(F + (size_t)b * T + g.lane);
+      const double2* qa = reinterpret_cast<const double2*>(EF + ef_at<T>(a, g.lane));
+      const double2* qb = reinterpret_cast<const double2*>(EF + ef_at<T>(b, g.lane));
+      const double2 va0 = qa[0], va1 = qa[1], vb0 = qb[0], vb1 = qb[1];
+      const Pair<double> ea{va0.x, va1.x}, fa{va0.y, va1.y};
+      const Pair<double> eb{vb0.x, vb1.x}, fb{vb0.y, vb1.y};
       const double gk = __ldg(G.g + k), bk = __ldg(G.by + k), ir = __ldg(G.inv_rating + k);
       double Pab0 = 0.0, Pba0 = 0.0, Pab1 = 0.0, Pba1 = 0.0;
       // P_ab = g |V_a|^2 - g Re(V_a conj V_b) - b Im(V_a conj V_b), and P_ba
@@ -407,8 +442,8 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
   VT* q = (VT*)P.wq + (size_t)blockIdx.x * P.vstride;
   VT* z = (VT*)P.wz + (size_t)blockIdx.x * P.vstride;
   const size_t so = (size_t)blockIdx.x * P.sstride;
-  double *th = P.wth + so, *V = P.wV + so, *C = P.wc + so, *Sn = P.ws + so, *E = P.we + so,
-         *F = P.wf + so;
+  // E and F regions of the slots taken together: [slot][bus][lane][e, f]
+  double *th = P.wth + so, *V = P.wV + so, *C = P.wc + so, *Sn = P.ws + so, *EF = P.we + 2 * so;
 
   // optional per-phase cycle counters (thread 0's view of the CTA)
   const bool tim = P.phase_cycles != nullptr;
@@ -439,7 +474,7 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
 
   for (;;) {
     // retire finished lanes, then refill empty lanes from the queue
-    if (any_lane<T>(L, L.done)) retire_pass<T>(P, L, th, V, E, F);
+    if (any_lane<T>(L, L.done)) retire_pass<T>(P, L, th, V, EF);
     GPCG_PHASE(7);
     if (tid == 0 && !L.drained) {
       int need = 0;
@@ -461,7 +496,7 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     __syncthreads();
     if (tid < T && L.fresh[tid]) setup_lane<T, VT>(P, MP, MQ, L, tid);
     __syncthreads();
-    init_pass<T>(P, L, th, V, C, Sn, E, F);
+    init_pass<T>(P, L, th, V, C, Sn, EF);
     __syncthreads();
     if (tid < T) L.fresh[tid] = 0;
     GPCG_PHASE(0);
@@ -471,7 +506,7 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     }
     // P half-step: mismatch + convergence test
     Pair<unsigned long long> eP{0ull, 0ull}, eQ{0ull, 0ull};
-    mismatch_pass<T, VT, true>(P, MP, MQ, L, E, F, V, r, eP, eQ);
+    mismatch_pass<T, VT, true>(P, MP, MQ, L, EF, V, r, eP, eQ);
     const Pair<unsigned long long> bP = lane_max_bits<T, RS_ERRP>(L, eP.a, eP.b);
     const Pair<unsigned long long> bQ = lane_max_bits<T, RS_ERRQ>(L, eQ.a, eQ.b);
     const Pair<double> mP{from_bits(bP.a), from_bits(bP.b)};
@@ -503,17 +538,17 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     if (!more) continue;
     pcg_solve<T, VT>(P, MP, L, x, r, p, q, z, L.raP, L.rbP, L.wP, L.inP);
     GPCG_PHASE(2);
-    update_pass<T, VT, true>(MP, L, x, th, V, C, Sn, E, F);
+    update_pass<T, VT, true>(MP, L, x, th, V, C, Sn, EF);
     __syncthreads();
     GPCG_PHASE(3);
     // Q half-step
     Pair<unsigned long long> d0{0ull, 0ull}, d1{0ull, 0ull};
-    mismatch_pass<T, VT, false>(P, MP, MQ, L, E, F, V, r, d0, d1);
+    mismatch_pass<T, VT, false>(P, MP, MQ, L, EF, V, r, d0, d1);
     __syncthreads();
     GPCG_PHASE(4);
     pcg_solve<T, VT>(P, MQ, L, x, r, p, q, z, L.raQ, L.rbQ, L.wQ, L.inQ);
     GPCG_PHASE(5);
-    update_pass<T, VT, false>(MQ, L, x, th, V, C, Sn, E, F);
+    update_pass<T, VT, false>(MQ, L, x, th, V, C, Sn, EF);
     if (g.rs == 0) {
       if (L.active[g.lane]) L.outer[g.lane] += 1;
       if (L.active[g.lane + 1]) L.outer[g.lane + 1] += 1;

@@ -18,7 +18,7 @@ constexpr int LP = 2;  // scenario lanes per thread
 #endif
 constexpr int UNR = FDPF_UNROLL;  // rows per thread in flight in the PCG passes
 #ifndef FDPF_MIS_GROUP
-#define FDPF_MIS_GROUP 3
+#define FDPF_MIS_GROUP 1
 #endif
 constexpr int MIS_GROUP = FDPF_MIS_GROUP;  // neighbours loaded together in the mismatch
 // Large passes are kept out of line by default (separate register
