@@ -542,6 +542,7 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
   if (st != GPCG_OK) return st;
   gpcg_ctx* c = new gpcg_ctx();
   c->opt = o;
+  c->tile = o.tile;  // 0: chosen on the first batched screen
   c->n = n;
   c->m = m;
   c->slack_user = slack;

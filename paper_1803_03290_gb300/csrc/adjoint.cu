@@ -42,7 +42,7 @@ __device__ __forceinline__ double penalty_grad(double F, double rating) {
 template <int T, typename VT>
 __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     adjoint_tiles_kernel(FdpfParams P, AdjParams A, DevMatT<VT> M) {
-  static_assert(T == LP, "one thread per row: the slot sums need no atomics");
+  static_assert(T == 2 && Geo<T>::LP == 2, "one thread per row, two lanes: the slot sums need no atomics");
   __shared__ LaneState<T> L;
   const Geo<T> g;
   const int tid = threadIdx.x;
@@ -219,13 +219,13 @@ cudaError_t launch_adjoint(cudaStream_t st, int grid, const FdpfParams& P, const
   a.gP = A.gP;
   a.gb = A.gb;
   a.loss = A.loss;
-  adjoint_tiles_kernel<LP, double><<<grid, NTHREADS, 0, st>>>(P, a, M);
+  adjoint_tiles_kernel<2, double><<<grid, NTHREADS, 0, st>>>(P, a, M);
   return cudaGetLastError();
 }
 
 int adjoint_max_blocks_per_sm() {
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, adjoint_tiles_kernel<LP, double>, NTHREADS, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, adjoint_tiles_kernel<2, double>, NTHREADS, 0);
   return nb;
 }
 

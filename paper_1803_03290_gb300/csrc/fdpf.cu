@@ -41,25 +41,19 @@ __device__ __forceinline__ size_t ef_at(int bus, int lane) {
 // neighbour sum and of the diagonal.  WITH_P: the P half-step (writes
 // dP/V into the B' right-hand side and tracks max|dP| and max|dQ| for the
 // convergence test); otherwise writes dQ/V into the B'' right-hand side.
-// A thread takes a bus and both of its lanes at once: each neighbour's
-// admittance and the lanes' voltages are loaded once for the two lanes.
+// A thread takes a bus and its lanes two at a time: each neighbour's
+// admittance and the pair's voltages are loaded once for the two lanes.
 template <int T, typename VT, bool WITH_P>
 __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMatT<VT>& MP,
                                                const DevMatT<VT>& MQ, LaneState<T>& L,
                                                const double* __restrict__ EF,
                                                const double* __restrict__ V,
                                                VT* __restrict__ rhs,
-                                               Pair<unsigned long long>& errP,
-                                               Pair<unsigned long long>& errQ) {
+                                               Vec<unsigned long long, Geo<T>::LP>& errP,
+                                               Vec<unsigned long long, Geo<T>::LP>& errQ) {
+  constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
   const DevGrid& G = P.G;
-  const int l0 = g.lane, l1 = g.lane + 1;
-  const int br0 = L.l[l0], br1 = L.l[l1];
-  const int fb0 = L.fb[l0], tb0 = L.tb[l0], fb1 = L.fb[l1], tb1 = L.tb[l1];
-  const int lo0 = L.lo[l0], cnt0 = L.cnt[l0], lo1 = L.lo[l1], cnt1 = L.cnt[l1];
-  const bool act0 = L.active[l0], act1 = L.active[l1];
-  const double cf0 = L.coef[l0], cf1 = L.coef[l1];
-  const double gl0 = L.gl[l0], bl0 = L.bl[l0], gl1 = L.gl[l1], bl1 = L.bl[l1];
   // rows are visited in order of bus degree, so the threads of a warp run
   // neighbour loops of equal length and no FP64 work is spent on padding
   const int nrows = WITH_P ? G.n - 1 : MQ.n;
@@ -80,12 +74,16 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
     }
     const int i = WITH_P ? k : __ldg(MQ.bus_of_row + k);
     const int pr = __ldg(G.pre + i);
-    const bool on0 = act0 && !in_island(pr, lo0, cnt0);
-    const bool on1 = act1 && !in_island(pr, lo1, cnt1);
-    Pair<VT> out{(VT)0, (VT)0};
-    if (on0 || on1) {
-      const int deg = __ldg(G.adj_deg + i);
-      // -sum over the neighbours of Y_ij V_j, both lanes
+    const int deg = __ldg(G.adj_deg + i);
+    Vec<VT, LP> out = vzero<VT, LP>();
+#pragma unroll 1
+    for (int jp = 0; jp < LP; jp += 2) {
+      const int l0 = g.lane + jp, l1 = l0 + 1;
+      const bool on0 = L.active[l0] && !in_island(pr, L.lo[l0], L.cnt[l0]);
+      const bool on1 = L.active[l1] && !in_island(pr, L.lo[l1], L.cnt[l1]);
+      if (!(on0 || on1)) continue;
+      const int br0 = L.l[l0], br1 = L.l[l1];
+      // -sum over the neighbours of Y_ij V_j, both lanes of the pair
       double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
 #pragma unroll
       for (int a0 = 0; a0 < KG; a0 += MIS_GROUP) {
@@ -133,7 +131,7 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
       // own voltage, the diagonal term and the mismatch of each lane
       const double2* own = reinterpret_cast<const double2*>(EF + ef_at<T>(i, l0));
       const double2 w0 = own[0], w1 = own[1];
-      const Pair<double> vi = ld2(V + (size_t)i * T + g.lane);
+      const Pair<double> vi = ld2(V + (size_t)i * T + l0);
       const int bt = G.bus_type[i];
       const double Gii = __ldg(G.Gii + i), Bii = __ldg(G.Bii + i), qs = __ldg(G.Q_sched + i);
       double Ps = 0.0, pg = 0.0;
@@ -142,13 +140,14 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
         if (bt == 1) pg = fmax(__ldg(G.P_gen + i), 0.0);  // generators with P_gen > 0 take it
       }
 #pragma unroll
-      for (int j = 0; j < LP; ++j) {
+      for (int j = 0; j < 2; ++j) {
         if (!(j ? on1 : on0)) continue;
+        const int ln = j ? l1 : l0;
         const double ei = j ? w1.x : w0.x, fi = j ? w1.y : w0.y;
         double Gd = Gii, Bd = Bii;
-        if (i == (j ? fb1 : fb0) || i == (j ? tb1 : tb0)) {
-          Gd -= j ? gl1 : gl0;
-          Bd -= j ? bl1 : bl0;
+        if (i == L.fb[ln] || i == L.tb[ln]) {  // the outaged branch's share
+          Gd -= L.gl[ln];
+          Bd -= L.bl[ln];
         }
         // I_i = Y_ii V_i + sum_j Y_ij V_j
         const double re = fma(Gd, ei, fma(-Bd, fi, j ? re1 : re0));
@@ -156,22 +155,19 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
         // dQ = Q_sched - Im(V_i conj(I_i)); dP = P_sched + re-dispatch - Re(...)
         VT res;
         if (WITH_P) {
-          const double dP = fma(-ei, re, fma(-fi, im, fma(j ? cf1 : cf0, pg, Ps)));
-          if (j) upd_max_bits(errP.b, dP); else upd_max_bits(errP.a, dP);
-          if (bt == 0) {
-            const double dQ = fma(-fi, re, fma(ei, im, qs));
-            if (j) upd_max_bits(errQ.b, dQ); else upd_max_bits(errQ.a, dQ);
-          }
+          const double dP = fma(-ei, re, fma(-fi, im, fma(L.coef[ln], pg, Ps)));
+          upd_max_bits(errP.v[jp + j], dP);
+          if (bt == 0) upd_max_bits(errQ.v[jp + j], fma(-fi, re, fma(ei, im, qs)));
           res = (VT)dP / (VT)(j ? vi.b : vi.a);
         } else {
           const double dQ = fma(-fi, re, fma(ei, im, qs));
           res = (VT)dQ / (VT)(j ? vi.b : vi.a);
         }
-        if (j) out.b = res; else out.a = res;
+        out.v[jp + j] = res;
       }
     }
-    if (WITH_P) st2(rhs + (size_t)__ldg(MP.row_of_bus + i) * T + g.lane, out);
-    else st2(rhs + (size_t)k * T + g.lane, out);
+    if (WITH_P) stv<LP>(rhs + (size_t)__ldg(MP.row_of_bus + i) * T + g.lane, out);
+    else stv<LP>(rhs + (size_t)k * T + g.lane, out);
   }
 }
 
@@ -205,43 +201,48 @@ __device__ __forceinline__ void rotate(double th_new, double d, double& c, doubl
 }
 
 // theta += dtheta (P half-step) or |V| += dV (Q half-step) on the matrix's
-// rows, then refresh the rectangular voltages.
+// rows, then refresh the rectangular voltages; lanes two at a time.
 template <int T, typename VT, bool IS_P>
 __device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>& L,
                                              const VT* __restrict__ x, double* th, double* V,
                                              double* C, double* Sn, double* EF) {
+  constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
-  const int l0 = g.lane, l1 = g.lane + 1;
-  const int lo0 = L.lo[l0], cnt0 = L.cnt[l0], lo1 = L.lo[l1], cnt1 = L.cnt[l1];
-  const bool act0 = L.active[l0], act1 = L.active[l1];
-  if (!act0 && !act1) return;
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < LP; ++j) any |= L.active[g.lane + j] != 0;
+  if (!any) return;
   for (int k = g.rs; k < M.n; k += Geo<T>::RPS) {
     const int pr = __ldg(M.pre_of_row + k);
-    const bool on0 = act0 && !in_island(pr, lo0, cnt0);
-    const bool on1 = act1 && !in_island(pr, lo1, cnt1);
-    if (!on0 && !on1) continue;
     const int i = __ldg(M.bus_of_row + k);
-    const size_t o = (size_t)i * T + g.lane;
-    const Pair<VT> dx = ld2(x + (size_t)k * T + g.lane);
-    const double d0 = on0 ? (double)dx.a : 0.0, d1 = on1 ? (double)dx.b : 0.0;
-    Pair<double> c = ld2(C + o), s = ld2(Sn + o), v = ld2(V + o);
-    if (IS_P) {
-      Pair<double> t = ld2(th + o);
-      t.a += d0;
-      t.b += d1;
-      if (on0) rotate(t.a, d0, c.a, s.a);
-      if (on1) rotate(t.b, d1, c.b, s.b);
-      st2(th + o, t);
-      st2(C + o, c);
-      st2(Sn + o, s);
-    } else {
-      v.a += d0;
-      v.b += d1;
-      st2(V + o, v);
+#pragma unroll 1
+    for (int jp = 0; jp < LP; jp += 2) {
+      const int l0 = g.lane + jp, l1 = l0 + 1;
+      const bool on0 = L.active[l0] && !in_island(pr, L.lo[l0], L.cnt[l0]);
+      const bool on1 = L.active[l1] && !in_island(pr, L.lo[l1], L.cnt[l1]);
+      if (!on0 && !on1) continue;
+      const size_t o = (size_t)i * T + l0;
+      const Pair<VT> dx = ld2(x + (size_t)k * T + l0);
+      const double d0 = on0 ? (double)dx.a : 0.0, d1 = on1 ? (double)dx.b : 0.0;
+      Pair<double> c = ld2(C + o), s = ld2(Sn + o), v = ld2(V + o);
+      if (IS_P) {
+        Pair<double> t = ld2(th + o);
+        t.a += d0;
+        t.b += d1;
+        if (on0) rotate(t.a, d0, c.a, s.a);
+        if (on1) rotate(t.b, d1, c.b, s.b);
+        st2(th + o, t);
+        st2(C + o, c);
+        st2(Sn + o, s);
+      } else {
+        v.a += d0;
+        v.b += d1;
+        st2(V + o, v);
+      }
+      double2* ef = reinterpret_cast<double2*>(EF + ef_at<T>(i, l0));
+      ef[0] = make_double2(v.a * c.a, v.a * s.a);
+      ef[1] = make_double2(v.b * c.b, v.b * s.b);
     }
-    double2* ef = reinterpret_cast<double2*>(EF + ef_at<T>(i, g.lane));
-    ef[0] = make_double2(v.a * c.a, v.a * s.a);
-    ef[1] = make_double2(v.b * c.b, v.b * s.b);
   }
 }
 
@@ -282,36 +283,31 @@ __device__ __forceinline__ void setup_lane(const FdpfParams& P, const DevMatT<VT
 template <int T>
 __device__ GPCG_PASS_INLINE void init_pass(const FdpfParams& P, LaneState<T>& L, double* th,
                                            double* V, double* C, double* Sn, double* EF) {
+  constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
   const DevGrid& G = P.G;
-  const int l0 = g.lane, l1 = g.lane + 1;
-  const bool n0 = L.fresh[l0], n1 = L.fresh[l1];
-  if (!n0 && !n1) return;
-  const int lo0 = L.lo[l0], cnt0 = L.cnt[l0], lo1 = L.lo[l1], cnt1 = L.cnt[l1];
+  int fresh = 0;
+#pragma unroll
+  for (int j = 0; j < LP; ++j) fresh |= (L.fresh[g.lane + j] != 0) << j;
+  if (!fresh) return;
   for (int i = g.rs; i < G.n; i += Geo<T>::RPS) {
-    const size_t o = (size_t)i * T + g.lane;
     double t0, v0, c0, s0;
     if (P.flat_start) { t0 = 0.0; v0 = G.V_set[i]; c0 = 1.0; s0 = 0.0; }
     else { t0 = P.th0[i]; v0 = P.V0[i]; c0 = P.c0[i]; s0 = P.s0[i]; }
     const int pr = G.pre[i];
-    const bool i0 = in_island(pr, lo0, cnt0), i1 = in_island(pr, lo1, cnt1);
-    auto put = [&](double* dst, double va, double vb) {
-      Pair<double> v{va, vb};
-      if (!(n0 && n1)) {
-        const Pair<double> old = ld2(dst + o);
-        if (!n0) v.a = old.a;
-        if (!n1) v.b = old.b;
-      }
-      st2(dst + o, v);
-    };
-    put(th, i0 ? 0.0 : t0, i1 ? 0.0 : t0);
-    put(V, i0 ? 0.0 : v0, i1 ? 0.0 : v0);
-    put(C, c0, c0);
-    put(Sn, s0, s0);
-    double2* ef = reinterpret_cast<double2*>(EF + ef_at<T>(i, g.lane));
-    const double e0 = v0 * c0, f0 = v0 * s0;
-    if (n0) ef[0] = i0 ? make_double2(0.0, 0.0) : make_double2(e0, f0);
-    if (n1) ef[1] = i1 ? make_double2(0.0, 0.0) : make_double2(e0, f0);
+#pragma unroll
+    for (int j = 0; j < LP; ++j) {
+      if (!((fresh >> j) & 1)) continue;
+      const int ln = g.lane + j;
+      const size_t o = (size_t)i * T + ln;
+      const bool isl = in_island(pr, L.lo[ln], L.cnt[ln]);
+      th[o] = isl ? 0.0 : t0;
+      V[o] = isl ? 0.0 : v0;
+      C[o] = c0;
+      Sn[o] = s0;
+      reinterpret_cast<double2*>(EF + ef_at<T>(i, ln))[0] =
+          isl ? make_double2(0.0, 0.0) : make_double2(v0 * c0, v0 * s0);
+    }
   }
 }
 
@@ -321,74 +317,62 @@ template <int T>
 __device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& L,
                                              const double* th, const double* V,
                                              const double* EF) {
+  constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
   const DevGrid& G = P.G;
-  const int l0 = g.lane, l1 = g.lane + 1;
-  const bool d0 = L.done[l0], d1 = L.done[l1];
-  const int s0 = d0 ? L.scen[l0] : -1, s1 = d1 ? L.scen[l1] : -1;
-  if ((P.out_theta || P.out_vm) && (d0 || d1)) {
+  int dn = 0;
+#pragma unroll
+  for (int j = 0; j < LP; ++j) dn |= (L.done[g.lane + j] != 0) << j;
+  if ((P.out_theta || P.out_vm) && dn) {
     for (int i = g.rs; i < G.n; i += Geo<T>::RPS) {
-      const size_t o = (size_t)i * T + g.lane;
-      const Pair<double> t = ld2(th + o), v = ld2(V + o);
       const int iu = P.out_bus_map ? __ldg(P.out_bus_map + i) : i;
-      if (P.out_theta) {
-        if (s0 >= 0) P.out_theta[(size_t)s0 * G.n + iu] = t.a;
-        if (s1 >= 0) P.out_theta[(size_t)s1 * G.n + iu] = t.b;
-      }
-      if (P.out_vm) {
-        if (s0 >= 0) P.out_vm[(size_t)s0 * G.n + iu] = v.a;
-        if (s1 >= 0) P.out_vm[(size_t)s1 * G.n + iu] = v.b;
+#pragma unroll
+      for (int j = 0; j < LP; ++j) {
+        if (!((dn >> j) & 1)) continue;
+        const int ln = g.lane + j, s = L.scen[ln];
+        const size_t o = (size_t)i * T + ln;
+        if (P.out_theta) P.out_theta[(size_t)s * G.n + iu] = th[o];
+        if (P.out_vm) P.out_vm[(size_t)s * G.n + iu] = V[o];
       }
     }
   }
-  unsigned long long ml0 = 0ull, ml1 = 0ull;  // max loading as abs_bits patterns
-  if (d0 || d1) {
-    const int br0 = L.l[l0], br1 = L.l[l1];
-    const int lo0 = L.lo[l0], cnt0 = L.cnt[l0], lo1 = L.lo[l1], cnt1 = L.cnt[l1];
+  Vec<unsigned long long, LP> ml = vzero<unsigned long long, LP>();  // abs_bits patterns
+  if (dn) {
     for (int k = g.rs; k < G.m; k += Geo<T>::RPS) {
       const int a = __ldg(G.f + k), b = __ldg(G.t + k);
       const int pa = __ldg(G.pre + a), pb = __ldg(G.pre + b);
-      const bool off0 = !d0 || (k == br0) || in_island(pa, lo0, cnt0) || in_island(pb, lo0, cnt0);
-      const bool off1 = !d1 || (k == br1) || in_island(pa, lo1, cnt1) || in_island(pb, lo1, cnt1);
-      const double2* qa = reinterpret_cast<const double2*>(EF + ef_at<T>(a, g.lane));
-      const double2* qb = reinterpret_cast<const double2*>(EF + ef_at<T>(b, g.lane));
-      const double2 va0 = qa[0], va1 = qa[1], vb0 = qb[0], vb1 = qb[1];
-      const Pair<double> ea{va0.x, va1.x}, fa{va0.y, va1.y};
-      const Pair<double> eb{vb0.x, vb1.x}, fb{vb0.y, vb1.y};
       const double gk = __ldg(G.g + k), bk = __ldg(G.by + k), ir = __ldg(G.inv_rating + k);
-      double Pab0 = 0.0, Pba0 = 0.0, Pab1 = 0.0, Pba1 = 0.0;
-      // P_ab = g |V_a|^2 - g Re(V_a conj V_b) - b Im(V_a conj V_b), and P_ba
-      // with a and b swapped (the imaginary part changes sign)
-      if (!off0) {
-        const double cr = fma(ea.a, eb.a, fa.a * fb.a), sr = fma(fa.a, eb.a, -ea.a * fb.a);
-        const double gc = gk * cr;
-        Pab0 = fma(gk, fma(ea.a, ea.a, fa.a * fa.a), -fma(bk, sr, gc));
-        Pba0 = fma(gk, fma(eb.a, eb.a, fb.a * fb.a), fma(bk, sr, -gc));
-      }
-      if (!off1) {
-        const double cr = fma(ea.b, eb.b, fa.b * fb.b), sr = fma(fa.b, eb.b, -ea.b * fb.b);
-        const double gc = gk * cr;
-        Pab1 = fma(gk, fma(ea.b, ea.b, fa.b * fa.b), -fma(bk, sr, gc));
-        Pba1 = fma(gk, fma(eb.b, eb.b, fb.b * fb.b), fma(bk, sr, -gc));
-      }
-      // loading max(|P_ab|, |P_ba|) / rating: the larger end picked on the
-      // bit patterns, one multiplication per lane
-      if (!off0) {
-        const unsigned long long u = abs_bits(Pab0), v = abs_bits(Pba0);
-        upd_max_bits(ml0, __longlong_as_double((long long)(u > v ? u : v)) * ir);
-      }
-      if (!off1) {
-        const unsigned long long u = abs_bits(Pab1), v = abs_bits(Pba1);
-        upd_max_bits(ml1, __longlong_as_double((long long)(u > v ? u : v)) * ir);
-      }
-      if (P.out_flow) {
-        if (s0 >= 0) P.out_flow[(size_t)s0 * G.m + k] = Pab0;
-        if (s1 >= 0) P.out_flow[(size_t)s1 * G.m + k] = Pab1;
+#pragma unroll 1
+      for (int jp = 0; jp < LP; jp += 2) {
+        if (!((dn >> jp) & 3)) continue;
+        const double2* qa = reinterpret_cast<const double2*>(EF + ef_at<T>(a, g.lane + jp));
+        const double2* qb = reinterpret_cast<const double2*>(EF + ef_at<T>(b, g.lane + jp));
+        const double2 va[2] = {qa[0], qa[1]}, vb[2] = {qb[0], qb[1]};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = jp + h, ln = g.lane + j;
+          if (!((dn >> j) & 1)) continue;
+          const int lo = L.lo[ln], cnt = L.cnt[ln];
+          double Pab = 0.0;
+          if (k != L.l[ln] && !in_island(pa, lo, cnt) && !in_island(pb, lo, cnt)) {
+            // P_ab = g |V_a|^2 - g Re(V_a conj V_b) - b Im(V_a conj V_b), and
+            // P_ba with a and b swapped (the imaginary part changes sign)
+            const double ea = va[h].x, fa = va[h].y, eb = vb[h].x, fb = vb[h].y;
+            const double cr = fma(ea, eb, fa * fb), sr = fma(fa, eb, -ea * fb);
+            const double gc = gk * cr;
+            Pab = fma(gk, fma(ea, ea, fa * fa), -fma(bk, sr, gc));
+            const double Pba = fma(gk, fma(eb, eb, fb * fb), fma(bk, sr, -gc));
+            // loading max(|P_ab|, |P_ba|) / rating: the larger end picked on
+            // the bit patterns, one multiplication
+            const unsigned long long u = abs_bits(Pab), v = abs_bits(Pba);
+            upd_max_bits(ml.v[j], __longlong_as_double((long long)(u > v ? u : v)) * ir);
+          }
+          if (P.out_flow) P.out_flow[(size_t)L.scen[ln] * G.m + k] = Pab;
+        }
       }
     }
   }
-  const Pair<unsigned long long> mlb = lane_max_bits<T, RS_LOAD>(L, ml0, ml1);
-  const Pair<double> ml{from_bits(mlb.a), from_bits(mlb.b)};
+  const Vec<unsigned long long, LP> mlb = lane_max_bits<T, RS_LOAD>(L, ml);
   if (g.rs == 0) {
 #pragma unroll
     for (int j = 0; j < LP; ++j) {
@@ -402,7 +386,7 @@ __device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& 
         P.out_iters[(size_t)s * 3 + 1] = L.inP[ln];
         P.out_iters[(size_t)s * 3 + 2] = L.inQ[ln];
       }
-      if (P.out_maxload) P.out_maxload[s] = j ? ml.b : ml.a;
+      if (P.out_maxload) P.out_maxload[s] = from_bits(mlb.v[j]);
       L.done[ln] = 0;
       L.scen[ln] = -1;
     }
@@ -435,6 +419,7 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
   const FdpfParams& P = *reinterpret_cast<const FdpfParams*>(pbuf);
   const DevMatT<VT>& MP = *reinterpret_cast<const DevMatT<VT>*>(mbuf[0]);
   const DevMatT<VT>& MQ = *reinterpret_cast<const DevMatT<VT>*>(mbuf[1]);
+  constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
   VT* x = (VT*)P.wx + (size_t)blockIdx.x * P.vstride;
   VT* r = (VT*)P.wr + (size_t)blockIdx.x * P.vstride;
@@ -505,18 +490,16 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
       continue;
     }
     // P half-step: mismatch + convergence test
-    Pair<unsigned long long> eP{0ull, 0ull}, eQ{0ull, 0ull};
+    Vec<unsigned long long, LP> eP = vzero<unsigned long long, LP>(), eQ = eP;
     mismatch_pass<T, VT, true>(P, MP, MQ, L, EF, V, r, eP, eQ);
-    const Pair<unsigned long long> bP = lane_max_bits<T, RS_ERRP>(L, eP.a, eP.b);
-    const Pair<unsigned long long> bQ = lane_max_bits<T, RS_ERRQ>(L, eQ.a, eQ.b);
-    const Pair<double> mP{from_bits(bP.a), from_bits(bP.b)};
-    const Pair<double> mQ{from_bits(bQ.a), from_bits(bQ.b)};
+    const Vec<unsigned long long, LP> bP = lane_max_bits<T, RS_ERRP>(L, eP);
+    const Vec<unsigned long long, LP> bQ = lane_max_bits<T, RS_ERRQ>(L, eQ);
     if (g.rs == 0) {
 #pragma unroll
       for (int j = 0; j < LP; ++j) {
         const int ln = g.lane + j;
         if (!L.active[ln]) continue;
-        const double a = j ? mP.b : mP.a, b = j ? mQ.b : mQ.a;
+        const double a = from_bits(bP.v[j]), b = from_bits(bQ.v[j]);
         const double e2 = (a != a || b != b) ? INFINITY : fmax(a, b);
         L.err[ln] = e2;
         int st = -1;
@@ -542,17 +525,17 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     __syncthreads();
     GPCG_PHASE(3);
     // Q half-step
-    Pair<unsigned long long> d0{0ull, 0ull}, d1{0ull, 0ull};
+    Vec<unsigned long long, LP> d0 = vzero<unsigned long long, LP>(), d1 = d0;
     mismatch_pass<T, VT, false>(P, MP, MQ, L, EF, V, r, d0, d1);
     __syncthreads();
     GPCG_PHASE(4);
     pcg_solve<T, VT>(P, MQ, L, x, r, p, q, z, L.raQ, L.rbQ, L.wQ, L.inQ);
     GPCG_PHASE(5);
     update_pass<T, VT, false>(MQ, L, x, th, V, C, Sn, EF);
-    if (g.rs == 0) {
-      if (L.active[g.lane]) L.outer[g.lane] += 1;
-      if (L.active[g.lane + 1]) L.outer[g.lane + 1] += 1;
-    }
+    if (g.rs == 0)
+#pragma unroll
+      for (int j = 0; j < LP; ++j)
+        if (L.active[g.lane + j]) L.outer[g.lane + j] += 1;
     __syncthreads();
     GPCG_PHASE(6);
   }
@@ -562,59 +545,61 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
 }
 
 // Batched operator application for verification (gpcg_apply): X and Y are
-// [S][rows]; each CTA handles tiles of T = 32 scenarios.
+// [S][rows]; each CTA handles tiles of T scenarios.
 template <int T, typename VT>
 __global__ void __launch_bounds__(NTHREADS) apply_kernel(DevMatT<VT> M, int op, int S,
                                                          const int32_t* outages,
                                                          const int32_t* f_, const int32_t* t_,
                                                          const double* X, double* Y, VT* wbuf,
                                                          size_t vstride, int precond) {
+  constexpr int LP = Geo<T>::LP;
   __shared__ __align__(16) VT zt[TAIL_ROWS * T];
+  __shared__ Stamp<T, VT> St;
   const Geo<T> g;
   VT* a = wbuf + (size_t)blockIdx.x * 3 * vstride;
   VT* b = a + vstride;
   VT* c = b + vstride;
   const int ntiles = (S + T - 1) / T;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    int ra[LP], rb[LP];
-    VT w[LP];
-    bool valid[LP];
-    int s[LP];
-#pragma unroll
-    for (int j = 0; j < LP; ++j) {
-      s[j] = tile * T + g.lane + j;
-      valid[j] = s[j] < S;
-      const int l = valid[j] ? outages[s[j]] : -1;
-      ra[j] = l >= 0 ? M.row_of_bus[f_[l]] : -1;
-      rb[j] = l >= 0 ? M.row_of_bus[t_[l]] : -1;
-      w[j] = l >= 0 ? (VT)M.w[l] : (VT)0;
+    if (threadIdx.x < T) {
+      const int s = tile * T + threadIdx.x;
+      const int l = s < S ? outages[s] : -1;
+      St.ra[threadIdx.x] = l >= 0 ? M.row_of_bus[f_[l]] : -1;
+      St.rb[threadIdx.x] = l >= 0 ? M.row_of_bus[t_[l]] : -1;
+      St.w[threadIdx.x] = l >= 0 ? (VT)M.w[l] : (VT)0;
     }
     for (int i = g.rs; i <= M.n; i += Geo<T>::RPS) {
-      Pair<VT> v{(VT)0, (VT)0};
-      if (i < M.n) {
-        if (valid[0]) v.a = (VT)X[(size_t)s[0] * M.n + i];
-        if (valid[1]) v.b = (VT)X[(size_t)s[1] * M.n + i];
-      }
-      st2(a + (size_t)i * T + g.lane, v);
-      st2(b + (size_t)i * T + g.lane, Pair<VT>{(VT)0, (VT)0});
+      Vec<VT, LP> v = vzero<VT, LP>();
+      if (i < M.n)
+#pragma unroll
+        for (int j = 0; j < LP; ++j) {
+          const int s = tile * T + g.lane + j;
+          if (s < S) v.v[j] = (VT)X[(size_t)s * M.n + i];
+        }
+      stv<LP>(a + (size_t)i * T + g.lane, v);
+      stv<LP>(b + (size_t)i * T + g.lane, vzero<VT, LP>());
     }
     __syncthreads();
+    const unsigned long long filt = stamp_filter<T, VT>(St);
+    const Vec<VT, LP> zero = vzero<VT, LP>();
     if (op == 0) {
-      spmv_pass<T, VT, false>(M, a, nullptr, b, ra[0], rb[0], w[0], ra[1], rb[1], w[1]);
+      spmv_pass<T, VT, false>(M, a, nullptr, b, St, filt, zero, true, nullptr);
     } else if (precond == PREC_JACOBI) {
-      Pair<VT> rr{0, 0}, rz{0, 0};
-      jacobi_pass<T, VT, false>(M, c, a, nullptr, nullptr, b, (VT)0, (VT)0, ra[0], rb[0], w[0],
-                                ra[1], rb[1], w[1], rr, rz);
+      Vec<VT, LP> rr = zero, rz = zero;
+      jacobi_pass<T, VT, false>(M, c, a, nullptr, nullptr, b, zero, St, rr, rz);
     } else {
-      Pair<VT> rzt{0, 0};
-      fwd_pass<T, VT, false>(M, c, a, nullptr, nullptr, b, (VT)0, (VT)0, zt, rzt);
+      Vec<VT, LP> rzt = zero;
+      fwd_pass<T, VT, false>(M, c, a, nullptr, nullptr, b, zero, zt, rzt);
       bwd_pass<T, VT>(M, a, b, rzt);
     }
     __syncthreads();
     for (int i = g.rs; i < M.n; i += Geo<T>::RPS) {
-      const Pair<VT> v = ld2(b + (size_t)i * T + g.lane);
-      if (valid[0]) Y[(size_t)s[0] * M.n + i] = (double)v.a;
-      if (valid[1]) Y[(size_t)s[1] * M.n + i] = (double)v.b;
+      const Vec<VT, LP> v = ldv<LP>(b + (size_t)i * T + g.lane);
+#pragma unroll
+      for (int j = 0; j < LP; ++j) {
+        const int s = tile * T + g.lane + j;
+        if (s < S) Y[(size_t)s * M.n + i] = (double)v.v[j];
+      }
     }
     __syncthreads();
   }

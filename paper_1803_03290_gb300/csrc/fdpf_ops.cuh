@@ -1,9 +1,9 @@
 // Batched operators and the batched PCG shared by the persistent kernels
 // (fdpf.cu: the N-1 screen; adjoint.cu: the overload-penalty adjoint).
 //
-// A CTA owns T scenario lanes; vectors are [row][T]; each thread owns two
-// adjacent lanes of a row.  Every sparse row is read through a padded
-// descriptor (ELL) so a thread issues all of a row's gathers at once.
+// A CTA owns T scenario lanes; vectors are [row][T]; each thread owns LP
+// adjacent lanes of a row (Geo<T>::LP).  Every sparse row is read through a
+// padded descriptor (ELL) so a thread issues all of a row's gathers at once.
 #pragma once
 #include <math.h>
 #include "common.cuh"
@@ -11,12 +11,14 @@
 
 namespace gpcg {
 
-
-constexpr int LP = 2;  // scenario lanes per thread
+#ifndef FDPF_LP
+#define FDPF_LP 2
+#endif
+constexpr int LP_MAX = FDPF_LP;  // scenario lanes a thread holds, at most
 #ifndef FDPF_UNROLL
 #define FDPF_UNROLL 1
 #endif
-constexpr int UNR = FDPF_UNROLL;  // rows per thread in flight in the PCG passes
+constexpr int UNR = FDPF_UNROLL;  // rows per thread in flight in the SpMV
 #ifndef FDPF_MIS_GROUP
 #define FDPF_MIS_GROUP 1
 #endif
@@ -40,7 +42,8 @@ constexpr int MIS_GROUP = FDPF_MIS_GROUP;  // neighbours loaded together in the 
 constexpr int STALL_ITERS = 50;
 
 // ------------------------------------------------------------ helpers
-template <typename VT> struct Pair { VT a, b; };
+template <typename X> struct Pair { X a, b; };
+template <typename X, int N> struct Vec { X v[N]; };
 
 __device__ __forceinline__ Pair<float> ld2(const float* p) {
   const float2 v = *reinterpret_cast<const float2*>(p);
@@ -55,6 +58,55 @@ __device__ __forceinline__ void st2(float* p, Pair<float> v) {
 }
 __device__ __forceinline__ void st2(double* p, Pair<double> v) {
   *reinterpret_cast<double2*>(p) = make_double2(v.a, v.b);
+}
+
+// N consecutive lanes (N = 2 or 4), one vector access per 8 or 16 bytes.
+template <int N>
+__device__ __forceinline__ Vec<float, N> ldv(const float* p) {
+  Vec<float, N> r;
+  if constexpr (N == 2) {
+    const float2 u = *reinterpret_cast<const float2*>(p);
+    r.v[0] = u.x; r.v[1] = u.y;
+  } else {
+    static_assert(N == 4, "2 or 4 lanes");
+    const float4 u = *reinterpret_cast<const float4*>(p);
+    r.v[0] = u.x; r.v[1] = u.y; r.v[2] = u.z; r.v[3] = u.w;
+  }
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Vec<double, N> ldv(const double* p) {
+  static_assert(N == 2 || N == 4, "2 or 4 lanes");
+  Vec<double, N> r;
+#pragma unroll
+  for (int k = 0; k < N; k += 2) {
+    const double2 u = reinterpret_cast<const double2*>(p)[k / 2];
+    r.v[k] = u.x; r.v[k + 1] = u.y;
+  }
+  return r;
+}
+template <int N>
+__device__ __forceinline__ void stv(float* p, const Vec<float, N>& r) {
+  if constexpr (N == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(r.v[0], r.v[1]);
+  } else {
+    static_assert(N == 4, "2 or 4 lanes");
+    *reinterpret_cast<float4*>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+  }
+}
+template <int N>
+__device__ __forceinline__ void stv(double* p, const Vec<double, N>& r) {
+  static_assert(N == 2 || N == 4, "2 or 4 lanes");
+#pragma unroll
+  for (int k = 0; k < N; k += 2)
+    reinterpret_cast<double2*>(p)[k / 2] = make_double2(r.v[k], r.v[k + 1]);
+}
+template <typename X, int N>
+__device__ __forceinline__ Vec<X, N> vzero() {
+  Vec<X, N> r;
+#pragma unroll
+  for (int j = 0; j < N; ++j) r.v[j] = (X)0;
+  return r;
 }
 
 template <int K>
@@ -100,6 +152,16 @@ __device__ __forceinline__ void ld_halfs(const __half* p, double (&v)[K]) {
   for (int k = 0; k < K; ++k) v[k] = f[k];
 }
 
+// ------------------------------------------------------------ geometry
+template <int T>
+struct Geo {
+  static constexpr int LP = T < LP_MAX ? T : LP_MAX;  // lanes per thread
+  static constexpr int TPR = T / LP;                  // threads per row
+  static constexpr int RPS = NTHREADS / TPR;          // rows per step
+  int rs, lane;                                       // row slot, first lane
+  __device__ Geo() : rs(threadIdx.x / TPR), lane((threadIdx.x % TPR) * LP) {}
+};
+
 // ------------------------------------------------------------ lane state
 constexpr int NRED_SITES = 8;  // reduction sites with a buffer of their own
 enum RedSite { RS_BB = 0, RS_RZ0, RS_PQ, RS_RR, RS_RZ, RS_ERRP, RS_ERRQ, RS_LOAD };
@@ -111,28 +173,20 @@ struct LaneState {
   double wP[T], wQ[T], coef[T], gl[T], bl[T];
   int active[T], outer[T], inP[T], inQ[T], status[T], nogen[T];
   double err[T], best[T];
-  double rz[T], bb[T], alpha[T], beta[T], rrmin[T];
   unsigned long long tphase[8];
-  int pdone[T], stall[T];
   int done[T], fresh[T];
-  double red[NTHREADS * LP];
+  double red[NTHREADS * 2];  // lane_reduce (two lanes per thread)
   // one small buffer per reduction site (see lane_sum): [site][warp][lane]
   double red2[NRED_SITES * (NTHREADS / 32) * T];
   int flag;
   int drained;
 };
 
-template <int T>
-struct Geo {
-  static constexpr int TPR = T / LP;             // threads per row
-  static constexpr int RPS = NTHREADS / TPR;     // rows per step
-  int rs, lane;                                  // row slot, first lane
-  __device__ Geo() : rs(threadIdx.x / TPR), lane((threadIdx.x % TPR) * LP) {}
-};
-
-// Sum (or max) over the row slots of each lane's partial values.
+// Sum (or max) over the row slots of each lane's partial values, for
+// layouts with two lanes per thread.
 template <int T, bool MAX>
 __device__ __forceinline__ Pair<double> lane_reduce(LaneState<T>& L, double v0, double v1) {
+  static_assert(Geo<T>::LP == 2, "two lanes per thread");
   const Geo<T> g;
   constexpr int RPS = Geo<T>::RPS;
   L.red[g.rs * T + g.lane] = v0;
@@ -142,7 +196,7 @@ __device__ __forceinline__ Pair<double> lane_reduce(LaneState<T>& L, double v0, 
   for (int st = RPS / 2; st > 0; st >>= 1) {
     if (g.rs < st) {
 #pragma unroll
-      for (int j = 0; j < LP; ++j) {
+      for (int j = 0; j < 2; ++j) {
         const int o = g.rs * T + g.lane + j;
         const double a = L.red[o], b = L.red[o + st * T];
         L.red[o] = MAX ? ((b > a || b != b) ? b : a) : a + b;
@@ -193,66 +247,91 @@ __device__ __forceinline__ double from_bits(unsigned long long b) {
 // Per-lane sum of the threads' partial values in a fixed order: a shuffle
 // tree inside each warp over the threads that hold the same lanes, then the
 // warps' partials through shared memory (buffer SITE) and one barrier.
-// Every thread returns the totals of its own two lanes.  A site's buffer is
+// Every thread returns the totals of its own lanes.  A site's buffer is
 // read right after the barrier and rewritten only after a later barrier,
 // so consecutive reductions at different sites need no barrier between.
-template <int T, int SITE, typename X>
-__device__ __forceinline__ Pair<X> lane_sum(LaneState<T>& L, X v0, X v1) {
+template <int T, int SITE, typename X, int N>
+__device__ __forceinline__ Vec<X, N> lane_sum(LaneState<T>& L, Vec<X, N> v) {
+  static_assert(N == Geo<T>::LP, "a thread's lanes");
   const Geo<T> g;
   constexpr int TPR = Geo<T>::TPR, NW = NTHREADS / 32;
 #pragma unroll
-  for (int off = 16; off >= TPR; off >>= 1) {
-    v0 += __shfl_xor_sync(0xffffffffu, v0, off);
-    v1 += __shfl_xor_sync(0xffffffffu, v1, off);
-  }
+  for (int off = 16; off >= TPR; off >>= 1)
+#pragma unroll
+    for (int j = 0; j < N; ++j) v.v[j] += __shfl_xor_sync(0xffffffffu, v.v[j], off);
   X* buf = reinterpret_cast<X*>(L.red2 + SITE * NW * T);
   const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) < TPR) {
-    buf[w * T + g.lane] = v0;
-    buf[w * T + g.lane + 1] = v1;
-  }
-  __syncthreads();
-  X s0 = buf[g.lane], s1 = buf[g.lane + 1];
+  if ((threadIdx.x & 31) < TPR)
 #pragma unroll
-  for (int k = 1; k < NW; ++k) {
-    s0 += buf[k * T + g.lane];
-    s1 += buf[k * T + g.lane + 1];
-  }
-  return {s0, s1};
+    for (int j = 0; j < N; ++j) buf[w * T + g.lane + j] = v.v[j];
+  __syncthreads();
+  Vec<X, N> s;
+#pragma unroll
+  for (int j = 0; j < N; ++j) s.v[j] = buf[g.lane + j];
+#pragma unroll
+  for (int k = 1; k < NW; ++k)
+#pragma unroll
+    for (int j = 0; j < N; ++j) s.v[j] += buf[k * T + g.lane + j];
+  return s;
 }
 
 // The same for running maxima held as abs_bits patterns.
-template <int T, int SITE>
-__device__ __forceinline__ Pair<unsigned long long> lane_max_bits(LaneState<T>& L,
-                                                                   unsigned long long v0,
-                                                                   unsigned long long v1) {
+template <int T, int SITE, int N>
+__device__ __forceinline__ Vec<unsigned long long, N> lane_max_bits(
+    LaneState<T>& L, Vec<unsigned long long, N> v) {
+  static_assert(N == Geo<T>::LP, "a thread's lanes");
   const Geo<T> g;
   constexpr int TPR = Geo<T>::TPR, NW = NTHREADS / 32;
 #pragma unroll
-  for (int off = 16; off >= TPR; off >>= 1) {
-    const unsigned long long u0 = __shfl_xor_sync(0xffffffffu, v0, off);
-    const unsigned long long u1 = __shfl_xor_sync(0xffffffffu, v1, off);
-    v0 = u0 > v0 ? u0 : v0;
-    v1 = u1 > v1 ? u1 : v1;
-  }
+  for (int off = 16; off >= TPR; off >>= 1)
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const unsigned long long u = __shfl_xor_sync(0xffffffffu, v.v[j], off);
+      v.v[j] = u > v.v[j] ? u : v.v[j];
+    }
   unsigned long long* buf = reinterpret_cast<unsigned long long*>(L.red2 + SITE * NW * T);
   const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) < TPR) {
-    buf[w * T + g.lane] = v0;
-    buf[w * T + g.lane + 1] = v1;
-  }
-  __syncthreads();
-  unsigned long long s0 = buf[g.lane], s1 = buf[g.lane + 1];
+  if ((threadIdx.x & 31) < TPR)
 #pragma unroll
-  for (int k = 1; k < NW; ++k) {
-    s0 = buf[k * T + g.lane] > s0 ? buf[k * T + g.lane] : s0;
-    s1 = buf[k * T + g.lane + 1] > s1 ? buf[k * T + g.lane + 1] : s1;
+    for (int j = 0; j < N; ++j) buf[w * T + g.lane + j] = v.v[j];
+  __syncthreads();
+  Vec<unsigned long long, N> s;
+#pragma unroll
+  for (int j = 0; j < N; ++j) s.v[j] = buf[g.lane + j];
+#pragma unroll
+  for (int k = 1; k < NW; ++k)
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const unsigned long long u = buf[k * T + g.lane + j];
+      s.v[j] = u > s.v[j] ? u : s.v[j];
+    }
+  return s;
+}
+
+// ----------------------------------------------------- the outage's change
+// Rows and weight of each lane's outaged branch in the matrix being solved
+// (-1: that end has no row).  stamp_filter sets bit (row & 63) for every
+// such row, so the SpMV tests one bit per row and looks at the lanes only
+// on a hit.
+template <int T, typename VT>
+struct Stamp {
+  int ra[T], rb[T];
+  VT w[T];
+};
+
+template <int T, typename VT>
+__device__ __forceinline__ unsigned long long stamp_filter(const Stamp<T, VT>& S) {
+  unsigned long long f = 0ull;
+#pragma unroll 1
+  for (int j = 0; j < T; ++j) {
+    if (S.ra[j] >= 0) f |= 1ull << (S.ra[j] & 63);
+    if (S.rb[j] >= 0) f |= 1ull << (S.rb[j] & 63);
   }
-  return {s0, s1};
+  return f;
 }
 
 // ----------------------------------------------------- batched operators
-// y = B_s v for the thread's two lanes: base row times v, plus the outaged
+// y = B_s v for the thread's lanes: base row times v, plus the outaged
 // branch's four-element change (Sec. IV.B) -- off-diagonal +w, diagonal -w
 // at both ends.
 //
@@ -261,18 +340,18 @@ __device__ __forceinline__ Pair<unsigned long long> lane_max_bits(LaneState<T>& 
 //   p <- mask(z) + beta p,   q <- mask(B_s z) + beta q,
 // which is q = B_s p for the new p because q held B_s p for the old one
 // (first: p = mask(z), q = mask(B_s z)).  mask zeroes the rows of islanded
-// buses: B_s couples no main-island row to an islanded one, so on the main
-// island B_s z = B_s mask(z).  Returns the partial p.q of the new p, q.
+// buses (isl: the lanes' island intervals, null when no lane has one):
+// B_s couples no main-island row to an islanded one, so on the main island
+// B_s z = B_s mask(z).  Returns the partial p.q of the new p, q.
 template <int T, typename VT, bool DIRECTION>
-__device__ GPCG_LOOP_INLINE Pair<VT> spmv_pass(const DevMatT<VT>& M, const VT* __restrict__ v_,
-                                              VT* __restrict__ p, VT* __restrict__ q, int ra0,
-                                              int rb0, VT w0, int ra1, int rb1, VT w1,
-                                              VT be0 = 0, VT be1 = 0, bool first = true,
-                                              int lo0 = 0, int cnt0 = 0, int lo1 = 0,
-                                              int cnt1 = 0) {
+__device__ GPCG_LOOP_INLINE Vec<VT, Geo<T>::LP> spmv_pass(
+    const DevMatT<VT>& M, const VT* __restrict__ v_, VT* __restrict__ p, VT* __restrict__ q,
+    const Stamp<T, VT>& S, unsigned long long filt, Vec<VT, Geo<T>::LP> be, bool first,
+    const LaneState<T>* isl) {
+  constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
   constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
-  VT pq0 = 0, pq1 = 0;
+  Vec<VT, LP> pq = vzero<VT, LP>();
   // UNR rows per thread per step, and the column indices of the next step
   // loaded one step ahead: each step waits on one memory latency for
   // UNR rows' gathers
@@ -287,8 +366,6 @@ __device__ GPCG_LOOP_INLINE Pair<VT> spmv_pass(const DevMatT<VT>& M, const VT* _
     }
   for (int i0 = g.rs; i0 < M.n; i0 += STEP) {
     int c[UNR][KA], ii[UNR];
-    VT v[UNR][KA];
-    Pair<VT> pc[UNR][KA], pi[UNR];
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
       ii[u] = vn[u];
@@ -303,66 +380,96 @@ __device__ GPCG_LOOP_INLINE Pair<VT> spmv_pass(const DevMatT<VT>& M, const VT* _
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
       const int i = ii[u];
-      if (i0 + u * RPS < M.n) {
-        ld_vals<KA>(M.A.val + (size_t)i * KA, v[u]);
-#pragma unroll
-        for (int k = 0; k < KA; ++k) pc[u][k] = ld2(v_ + (size_t)c[u][k] * T + g.lane);
-        pi[u] = ld2(v_ + (size_t)i * T + g.lane);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      const int i = ii[u];
       if (i0 + u * RPS >= M.n) continue;
-      VT a0 = 0, a1 = 0;
+      VT v[KA];
+      Vec<VT, LP> pc[KA];
+      ld_vals<KA>(M.A.val + (size_t)i * KA, v);
 #pragma unroll
-      for (int k = 0; k < KA; ++k) {
-        a0 += v[u][k] * pc[u][k].a;
-        a1 += v[u][k] * pc[u][k].b;
-      }
+      for (int k = 0; k < KA; ++k) pc[k] = ldv<LP>(v_ + (size_t)c[u][k] * T + g.lane);
+      const size_t o = (size_t)i * T + g.lane;
+      const Vec<VT, LP> pi = ldv<LP>(v_ + o);
+      Vec<VT, LP> a = vzero<VT, LP>();
+#pragma unroll
+      for (int k = 0; k < KA; ++k)
+#pragma unroll
+        for (int j = 0; j < LP; ++j) a.v[j] += v[k] * pc[k].v[j];
       const int o0 = __ldg(M.A.optr + i), o1 = __ldg(M.A.optr + i + 1);
-      for (int o = o0; o < o1; ++o) {
-        const int cc = __ldg(M.A.ocol + o);
-        const VT vv = __ldg(M.A.oval + o);
-        const Pair<VT> pp = ld2(v_ + (size_t)cc * T + g.lane);
-        a0 += vv * pp.a;
-        a1 += vv * pp.b;
+      for (int e = o0; e < o1; ++e) {
+        const int cc = __ldg(M.A.ocol + e);
+        const VT vv = __ldg(M.A.oval + e);
+        const Vec<VT, LP> pp = ldv<LP>(v_ + (size_t)cc * T + g.lane);
+#pragma unroll
+        for (int j = 0; j < LP; ++j) a.v[j] += vv * pp.v[j];
       }
       // the outage's change, on the two rows of the outaged branch only:
       // + w v_other (when the other end has a row) - w v_own
-      if (i == ra0 || i == rb0) {
-        const int oth = (i == ra0) ? rb0 : ra0;
-        a0 += w0 * ((oth >= 0 ? v_[(size_t)oth * T + g.lane] : (VT)0) - pi[u].a);
-      }
-      if (i == ra1 || i == rb1) {
-        const int oth = (i == ra1) ? rb1 : ra1;
-        a1 += w1 * ((oth >= 0 ? v_[(size_t)oth * T + g.lane + 1] : (VT)0) - pi[u].b);
-      }
-      const size_t o = (size_t)i * T + g.lane;
-      if (DIRECTION) {
-        const int pr = __ldg(M.pre_of_row + i);
-        const bool m0 = in_island(pr, lo0, cnt0), m1 = in_island(pr, lo1, cnt1);
-        Pair<VT> pn{m0 ? (VT)0 : pi[u].a, m1 ? (VT)0 : pi[u].b};
-        Pair<VT> qn{m0 ? (VT)0 : a0, m1 ? (VT)0 : a1};
-        if (!first) {
-          const Pair<VT> po = ld2(p + o), qo = ld2(q + o);
-          pn.a += be0 * po.a;
-          pn.b += be1 * po.b;
-          qn.a += be0 * qo.a;
-          qn.b += be1 * qo.b;
+      if ((filt >> (i & 63)) & 1ull) {
+#pragma unroll
+        for (int j = 0; j < LP; ++j) {
+          const int ln = g.lane + j, ra = S.ra[ln], rb = S.rb[ln];
+          if (i == ra || i == rb) {
+            const int oth = (i == ra) ? rb : ra;
+            a.v[j] += S.w[ln] * ((oth >= 0 ? v_[(size_t)oth * T + ln] : (VT)0) - pi.v[j]);
+          }
         }
-        st2(p + o, pn);
-        st2(q + o, qn);
-        pq0 += pn.a * qn.a;
-        pq1 += pn.b * qn.b;
+      }
+      if (DIRECTION) {
+        Vec<VT, LP> pn = pi, qn = a;
+        if (isl) {
+          const int pr = __ldg(M.pre_of_row + i);
+#pragma unroll
+          for (int j = 0; j < LP; ++j)
+            if (in_island(pr, isl->lo[g.lane + j], isl->cnt[g.lane + j])) {
+              pn.v[j] = (VT)0;
+              qn.v[j] = (VT)0;
+            }
+        }
+        if (!first) {
+          const Vec<VT, LP> po = ldv<LP>(p + o), qo = ldv<LP>(q + o);
+#pragma unroll
+          for (int j = 0; j < LP; ++j) {
+            pn.v[j] += be.v[j] * po.v[j];
+            qn.v[j] += be.v[j] * qo.v[j];
+          }
+        }
+        stv<LP>(p + o, pn);
+        stv<LP>(q + o, qn);
+#pragma unroll
+        for (int j = 0; j < LP; ++j) pq.v[j] += pn.v[j] * qn.v[j];
       } else {
-        st2(q + o, Pair<VT>{a0, a1});
-        pq0 += pi[u].a * a0;
-        pq1 += pi[u].b * a1;
+        stv<LP>(q + o, a);
+#pragma unroll
+        for (int j = 0; j < LP; ++j) pq.v[j] += pi.v[j] * a.v[j];
       }
     }
   }
-  return {pq0, pq1};
+  return pq;
+}
+
+// The PCG update of one row in the forward pass: x += alpha p, r -= alpha q
+// (FUSED), or x = 0; returns the row's residual and adds its r.r.
+template <int T, typename VT, bool FUSED>
+__device__ __forceinline__ Vec<VT, Geo<T>::LP> pcg_update_row(
+    size_t o, VT* __restrict__ x, VT* __restrict__ r, const VT* __restrict__ p,
+    const VT* __restrict__ q, const Vec<VT, Geo<T>::LP>& al, Vec<VT, Geo<T>::LP>& rr) {
+  constexpr int LP = Geo<T>::LP;
+  Vec<VT, LP> rv = ldv<LP>(r + o);
+  if (FUSED) {
+    const Vec<VT, LP> pi = ldv<LP>(p + o), qi = ldv<LP>(q + o);
+    Vec<VT, LP> xi = ldv<LP>(x + o);
+#pragma unroll
+    for (int j = 0; j < LP; ++j) {
+      xi.v[j] += al.v[j] * pi.v[j];
+      rv.v[j] -= al.v[j] * qi.v[j];
+    }
+    stv<LP>(x + o, xi);
+    stv<LP>(r + o, rv);
+  } else {
+    stv<LP>(x + o, vzero<VT, LP>());
+  }
+#pragma unroll
+  for (int j = 0; j < LP; ++j) rr.v[j] += rv.v[j] * rv.v[j];
+  return rv;
 }
 
 // The tail of the level schedule (rows [tail_row0, n): the last, narrow
@@ -379,8 +486,9 @@ template <int T, typename VT, bool FUSED>
 __device__ GPCG_LOOP_INLINE void tail_solve(const DevMatT<VT>& M, VT* __restrict__ x,
                                            VT* __restrict__ r, const VT* __restrict__ p,
                                            const VT* __restrict__ q, VT* __restrict__ z,
-                                           VT al0, VT al1, VT* __restrict__ s, VT& rr0, VT& rr1,
-                                           Pair<VT>& rzt) {
+                                           const Vec<VT, Geo<T>::LP>& al, VT* __restrict__ s,
+                                           Vec<VT, Geo<T>::LP>& rr, Vec<VT, Geo<T>::LP>& rzt) {
+  constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
   constexpr int RPS = Geo<T>::RPS, NPT = (TAIL_ROWS + RPS - 1) / RPS;
   const int t0 = M.tail_row0, nt = M.n - t0;
@@ -394,61 +502,48 @@ __device__ GPCG_LOOP_INLINE void tail_solve(const DevMatT<VT>& M, VT* __restrict
     ld_cols<KL>(M.L.col + (size_t)i * KL, c);
     if (M.Lh) ld_halfs<KL>(M.Lh + (size_t)i * KL, v);
     else ld_vals<KL>(M.L.val + (size_t)i * KL, v);
-    Pair<VT> rv = ld2(r + o);
-    if (FUSED) {
-      const Pair<VT> pi = ld2(p + o), qi = ld2(q + o), xi = ld2(x + o);
-      st2(x + o, Pair<VT>{xi.a + al0 * pi.a, xi.b + al1 * pi.b});
-      rv.a -= al0 * qi.a;
-      rv.b -= al1 * qi.b;
-      st2(r + o, rv);
-    } else {
-      st2(x + o, Pair<VT>{(VT)0, (VT)0});
-    }
-    rr0 += rv.a * rv.a;
-    rr1 += rv.b * rv.b;
-    VT a0 = rv.a, a1 = rv.b;
+    Vec<VT, LP> a = pcg_update_row<T, VT, FUSED>(o, x, r, p, q, al, rr);
 #pragma unroll
     for (int k2 = 0; k2 < KL; ++k2) {
       if (c[k2] >= t0) continue;
-      const Pair<VT> zz = ld2(z + (size_t)c[k2] * T + g.lane);
-      a0 -= v[k2] * zz.a;
-      a1 -= v[k2] * zz.b;
+      const Vec<VT, LP> zz = ldv<LP>(z + (size_t)c[k2] * T + g.lane);
+#pragma unroll
+      for (int j = 0; j < LP; ++j) a.v[j] -= v[k2] * zz.v[j];
     }
     const int o0 = __ldg(M.L.optr + i), o1 = __ldg(M.L.optr + i + 1);
     for (int e = o0; e < o1; ++e) {
       const int cc = __ldg(M.L.ocol + e);
       if (cc >= t0) continue;
       const VT vv = M.Lh ? (VT)__half2float(M.Loh[e]) : __ldg(M.L.oval + e);
-      const Pair<VT> zz = ld2(z + (size_t)cc * T + g.lane);
-      a0 -= vv * zz.a;
-      a1 -= vv * zz.b;
+      const Vec<VT, LP> zz = ldv<LP>(z + (size_t)cc * T + g.lane);
+#pragma unroll
+      for (int j = 0; j < LP; ++j) a.v[j] -= vv * zz.v[j];
     }
-    st2(s + (size_t)k * T + g.lane, Pair<VT>{a0, a1});
+    stv<LP>(s + (size_t)k * T + g.lane, a);
   }
   __syncthreads();
   // (b) y_t = X rhs: X_kj = xc[j nt + k], zero above the diagonal
-  Pair<VT> y[NPT];
+  Vec<VT, LP> y[NPT];
 #pragma unroll
   for (int m = 0; m < NPT; ++m) {
     const int k = g.rs + m * RPS;
-    VT a0 = 0, a1 = 0;
+    y[m] = vzero<VT, LP>();
     if (k < nt) {
       const VT* col = M.xc + k;
 #pragma unroll 4
       for (int j = 0; j < nt; ++j) {
         const VT xv = __ldg(col + (size_t)j * nt);
-        const Pair<VT> sv = ld2(s + (size_t)j * T + g.lane);
-        a0 += xv * sv.a;
-        a1 += xv * sv.b;
+        const Vec<VT, LP> sv = ldv<LP>(s + (size_t)j * T + g.lane);
+#pragma unroll
+        for (int l = 0; l < LP; ++l) y[m].v[l] += xv * sv.v[l];
       }
     }
-    y[m] = Pair<VT>{a0, a1};
   }
   __syncthreads();
 #pragma unroll
   for (int m = 0; m < NPT; ++m) {
     const int k = g.rs + m * RPS;
-    if (k < nt) st2(s + (size_t)k * T + g.lane, y[m]);
+    if (k < nt) stv<LP>(s + (size_t)k * T + g.lane, y[m]);
   }
   __syncthreads();
   // (c) z_t = X^T y_t: X_ik = xr[i nt + k], zero for i < k
@@ -457,19 +552,19 @@ __device__ GPCG_LOOP_INLINE void tail_solve(const DevMatT<VT>& M, VT* __restrict
     const int k = g.rs + m * RPS;
     if (k >= nt) continue;
     const VT* col = M.xr + k;
-    VT a0 = 0, a1 = 0;
+    Vec<VT, LP> a = vzero<VT, LP>();
 #pragma unroll 4
     for (int i = 0; i < nt; ++i) {
       const VT xv = __ldg(col + (size_t)i * nt);
-      const Pair<VT> sv = ld2(s + (size_t)i * T + g.lane);
-      a0 += xv * sv.a;
-      a1 += xv * sv.b;
+      const Vec<VT, LP> sv = ldv<LP>(s + (size_t)i * T + g.lane);
+#pragma unroll
+      for (int l = 0; l < LP; ++l) a.v[l] += xv * sv.v[l];
     }
     const size_t o = (size_t)(t0 + k) * T + g.lane;
-    st2(z + o, Pair<VT>{a0, a1});
-    const Pair<VT> ri = ld2(r + o);
-    rzt.a += ri.a * a0;
-    rzt.b += ri.b * a1;
+    stv<LP>(z + o, a);
+    const Vec<VT, LP> ri = ldv<LP>(r + o);
+#pragma unroll
+    for (int l = 0; l < LP; ++l) rzt.v[l] += ri.v[l] * a.v[l];
   }
   __syncthreads();
 }
@@ -481,13 +576,14 @@ __device__ GPCG_LOOP_INLINE void tail_solve(const DevMatT<VT>& M, VT* __restrict
 // works on the current one, and the next level's bounds a level ahead, so
 // after a level barrier only the gathers of the solved values are waited on.
 template <int T, typename VT, bool FUSED>
-__device__ GPCG_LOOP_INLINE Pair<VT> fwd_pass(const DevMatT<VT>& M, VT* __restrict__ x,
-                                                 VT* __restrict__ r, const VT* __restrict__ p,
-                                                 const VT* __restrict__ q, VT* __restrict__ z,
-                                                 VT al0, VT al1, VT* zt, Pair<VT>& rzt) {
+__device__ GPCG_LOOP_INLINE Vec<VT, Geo<T>::LP> fwd_pass(
+    const DevMatT<VT>& M, VT* __restrict__ x, VT* __restrict__ r, const VT* __restrict__ p,
+    const VT* __restrict__ q, VT* __restrict__ z, const Vec<VT, Geo<T>::LP>& al, VT* zt,
+    Vec<VT, Geo<T>::LP>& rzt) {
+  constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
   constexpr int RPS = Geo<T>::RPS;
-  VT rr0 = 0, rr1 = 0;
+  Vec<VT, LP> rr = vzero<VT, LP>();
   const int nl = M.tail_lev;
   int r0 = 0, r1 = 0, pf = -1, cn[KL];
   if (nl > 0) {
@@ -510,48 +606,32 @@ __device__ GPCG_LOOP_INLINE Pair<VT> fwd_pass(const DevMatT<VT>& M, VT* __restri
       }
       const size_t o = (size_t)i * T + g.lane;
       VT v[KL];
-      Pair<VT> zc[KL], ri, pi, qi, xi;
+      Vec<VT, LP> zc[KL];
       if (M.Lh) ld_halfs<KL>(M.Lh + (size_t)i * KL, v);
       else ld_vals<KL>(M.L.val + (size_t)i * KL, v);
 #pragma unroll
-      for (int k = 0; k < KL; ++k) zc[k] = ld2(z + (size_t)c[k] * T + g.lane);
-      ri = ld2(r + o);
-      if (FUSED) {
-        pi = ld2(p + o);
-        qi = ld2(q + o);
-        xi = ld2(x + o);
-      }
+      for (int k = 0; k < KL; ++k) zc[k] = ldv<LP>(z + (size_t)c[k] * T + g.lane);
       // the thread's next row: in this level, else the first of the next
       const int is = (i + RPS < r1) ? i + RPS : ((lev + 1 < nl && r1 + g.rs < r2) ? r1 + g.rs : -1);
       pf = is;
       if (is >= 0) ld_cols<KL>(M.L.col + (size_t)is * KL, cn);
-      Pair<VT> rv = ri;
-      if (FUSED) {
-        st2(x + o, Pair<VT>{xi.a + al0 * pi.a, xi.b + al1 * pi.b});
-        rv.a -= al0 * qi.a;
-        rv.b -= al1 * qi.b;
-        st2(r + o, rv);
-      } else {
-        st2(x + o, Pair<VT>{(VT)0, (VT)0});
-      }
-      rr0 += rv.a * rv.a;
-      rr1 += rv.b * rv.b;
-      VT a0 = rv.a, a1 = rv.b;
+      Vec<VT, LP> a = pcg_update_row<T, VT, FUSED>(o, x, r, p, q, al, rr);
 #pragma unroll
-      for (int k = 0; k < KL; ++k) {
-        a0 -= v[k] * zc[k].a;
-        a1 -= v[k] * zc[k].b;
-      }
+      for (int k = 0; k < KL; ++k)
+#pragma unroll
+        for (int j = 0; j < LP; ++j) a.v[j] -= v[k] * zc[k].v[j];
       const int o0 = __ldg(M.L.optr + i), o1 = __ldg(M.L.optr + i + 1);
       for (int e = o0; e < o1; ++e) {
         const VT vv = M.Lh ? (VT)__half2float(M.Loh[e]) : __ldg(M.L.oval + e);
-        const Pair<VT> zz = ld2(z + (size_t)__ldg(M.L.ocol + e) * T + g.lane);
-        a0 -= vv * zz.a;
-        a1 -= vv * zz.b;
+        const Vec<VT, LP> zz = ldv<LP>(z + (size_t)__ldg(M.L.ocol + e) * T + g.lane);
+#pragma unroll
+        for (int j = 0; j < LP; ++j) a.v[j] -= vv * zz.v[j];
       }
       // scaled factor: unit diagonal, w = D y is what is stored
       const VT id = M.Lh ? (VT)1 : __ldg(M.inv_diag + i);
-      st2(z + o, Pair<VT>{a0 * id, a1 * id});
+#pragma unroll
+      for (int j = 0; j < LP; ++j) a.v[j] *= id;
+      stv<LP>(z + o, a);
     }
     // no row in this level: load the next level's first row ahead anyway
     if (pf < 0 && lev + 1 < nl && r1 + g.rs < r2) {
@@ -562,20 +642,22 @@ __device__ GPCG_LOOP_INLINE Pair<VT> fwd_pass(const DevMatT<VT>& M, VT* __restri
     r0 = r1;
     r1 = r2;
   }
-  if (M.tail_row0 < M.n) tail_solve<T, VT, FUSED>(M, x, r, p, q, z, al0, al1, zt, rr0, rr1, rzt);
-  return {rr0, rr1};
+  if (M.tail_row0 < M.n) tail_solve<T, VT, FUSED>(M, x, r, p, q, z, al, zt, rr, rzt);
+  return rr;
 }
 
 // Back substitution L^T z = y in place (z holds y on entry), over the
 // backward level schedule of the rows before the tail (the tail was solved
-// in fwd_pass); accumulates r.z.  Rows and their column indices are loaded
-// one row ahead across level barriers, as in fwd_pass.
+// in fwd_pass); accumulates r.z on top of rz.  Rows and their column
+// indices are loaded one row ahead across level barriers, as in fwd_pass.
 template <int T, typename VT>
-__device__ GPCG_LOOP_INLINE Pair<VT> bwd_pass(const DevMatT<VT>& M, const VT* __restrict__ r,
-                                                 VT* __restrict__ z, Pair<VT> rzt) {
+__device__ GPCG_LOOP_INLINE Vec<VT, Geo<T>::LP> bwd_pass(const DevMatT<VT>& M,
+                                                        const VT* __restrict__ r,
+                                                        VT* __restrict__ z,
+                                                        Vec<VT, Geo<T>::LP> rz) {
+  constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
   constexpr int RPS = Geo<T>::RPS;
-  VT rz0 = rzt.a, rz1 = rzt.b;
   const int nb = M.ntblev;
   const int32_t* bptr = M.tblev_ptr;
   const int32_t* brows = M.tblev_rows;
@@ -603,12 +685,12 @@ __device__ GPCG_LOOP_INLINE Pair<VT> bwd_pass(const DevMatT<VT>& M, const VT* __
       }
       const size_t o = (size_t)i * T + g.lane;
       VT v[KU];
-      Pair<VT> zc[KU];
+      Vec<VT, LP> zc[KU];
       if (M.Uh) ld_halfs<KU>(M.Uh + (size_t)i * KU, v);
       else ld_vals<KU>(M.U.val + (size_t)i * KU, v);
 #pragma unroll
-      for (int a = 0; a < KU; ++a) zc[a] = ld2(z + (size_t)c[a] * T + g.lane);
-      const Pair<VT> yi = ld2(z + o), ri = ld2(r + o);
+      for (int a = 0; a < KU; ++a) zc[a] = ldv<LP>(z + (size_t)c[a] * T + g.lane);
+      const Vec<VT, LP> yi = ldv<LP>(z + o), ri = ldv<LP>(r + o);
       const int ks = (k + RPS < r1) ? k + RPS : ((lev + 1 < nb && r1 + g.rs < r2) ? r1 + g.rs : -1);
       pk = ks;
       if (ks >= 0) {
@@ -617,25 +699,27 @@ __device__ GPCG_LOOP_INLINE Pair<VT> bwd_pass(const DevMatT<VT>& M, const VT* __
       }
       // scaled factor: L_s^T z = D^-2 w with a unit diagonal
       const VT pre = M.Uh ? __ldg(M.inv_d2 + i) : (VT)1;
-      VT a0 = yi.a * pre, a1 = yi.b * pre;
+      Vec<VT, LP> acc;
 #pragma unroll
-      for (int a = 0; a < KU; ++a) {
-        a0 -= v[a] * zc[a].a;
-        a1 -= v[a] * zc[a].b;
-      }
+      for (int j = 0; j < LP; ++j) acc.v[j] = yi.v[j] * pre;
+#pragma unroll
+      for (int a = 0; a < KU; ++a)
+#pragma unroll
+        for (int j = 0; j < LP; ++j) acc.v[j] -= v[a] * zc[a].v[j];
       const int o0 = __ldg(M.U.optr + i), o1 = __ldg(M.U.optr + i + 1);
       for (int e = o0; e < o1; ++e) {
         const VT vv = M.Uh ? (VT)__half2float(M.Uoh[e]) : __ldg(M.U.oval + e);
-        const Pair<VT> zz = ld2(z + (size_t)__ldg(M.U.ocol + e) * T + g.lane);
-        a0 -= vv * zz.a;
-        a1 -= vv * zz.b;
+        const Vec<VT, LP> zz = ldv<LP>(z + (size_t)__ldg(M.U.ocol + e) * T + g.lane);
+#pragma unroll
+        for (int j = 0; j < LP; ++j) acc.v[j] -= vv * zz.v[j];
       }
       const VT id = M.Uh ? (VT)1 : __ldg(M.inv_diag + i);
-      a0 *= id;
-      a1 *= id;
-      st2(z + o, Pair<VT>{a0, a1});
-      rz0 += ri.a * a0;
-      rz1 += ri.b * a1;
+#pragma unroll
+      for (int j = 0; j < LP; ++j) {
+        acc.v[j] *= id;
+        rz.v[j] += ri.v[j] * acc.v[j];
+      }
+      stv<LP>(z + o, acc);
     }
     if (pk < 0 && lev + 1 < nb && r1 + g.rs < r2) {
       pk = r1 + g.rs;
@@ -646,7 +730,7 @@ __device__ GPCG_LOOP_INLINE Pair<VT> bwd_pass(const DevMatT<VT>& M, const VT* __
     r0 = r1;
     r1 = r2;
   }
-  return {rz0, rz1};
+  return rz;
 }
 
 // Jacobi: z = r / diag(B_s), the diagonal with the outage applied; a row
@@ -654,32 +738,25 @@ __device__ GPCG_LOOP_INLINE Pair<VT> bwd_pass(const DevMatT<VT>& M, const VT* __
 template <int T, typename VT, bool FUSED>
 __device__ GPCG_LOOP_INLINE void jacobi_pass(const DevMatT<VT>& M, VT* __restrict__ x,
                                             VT* __restrict__ r, const VT* __restrict__ p,
-                                            const VT* __restrict__ q, VT* __restrict__ z, VT al0,
-                                            VT al1, int ra0, int rb0, VT w0, int ra1, int rb1,
-                                            VT w1, Pair<VT>& rr, Pair<VT>& rz) {
+                                            const VT* __restrict__ q, VT* __restrict__ z,
+                                            const Vec<VT, Geo<T>::LP>& al,
+                                            const Stamp<T, VT>& S,
+                                            Vec<VT, Geo<T>::LP>& rr, Vec<VT, Geo<T>::LP>& rz) {
+  constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
   for (int i = g.rs; i < M.n; i += Geo<T>::RPS) {
     const size_t o = (size_t)i * T + g.lane;
-    Pair<VT> ri = ld2(r + o);
-    if (FUSED) {
-      const Pair<VT> pi = ld2(p + o), qi = ld2(q + o), xi = ld2(x + o);
-      st2(x + o, Pair<VT>{xi.a + al0 * pi.a, xi.b + al1 * pi.b});
-      ri.a -= al0 * qi.a;
-      ri.b -= al1 * qi.b;
-      st2(r + o, ri);
-    } else {
-      st2(x + o, Pair<VT>{(VT)0, (VT)0});
-    }
+    const Vec<VT, LP> ri = pcg_update_row<T, VT, FUSED>(o, x, r, p, q, al, rr);
     const VT dg = __ldg(M.diag + i);
-    const VT d0 = dg - ((i == ra0 || i == rb0) ? w0 : (VT)0);
-    const VT d1 = dg - ((i == ra1 || i == rb1) ? w1 : (VT)0);
-    const VT z0 = d0 > (VT)0 ? ri.a / d0 : (VT)0;
-    const VT z1 = d1 > (VT)0 ? ri.b / d1 : (VT)0;
-    st2(z + o, Pair<VT>{z0, z1});
-    rr.a += ri.a * ri.a;
-    rr.b += ri.b * ri.b;
-    rz.a += ri.a * z0;
-    rz.b += ri.b * z1;
+    Vec<VT, LP> zi;
+#pragma unroll
+    for (int j = 0; j < LP; ++j) {
+      const int ln = g.lane + j;
+      const VT d = dg - ((i == S.ra[ln] || i == S.rb[ln]) ? S.w[ln] : (VT)0);
+      zi.v[j] = d > (VT)0 ? ri.v[j] / d : (VT)0;
+      rz.v[j] += ri.v[j] * zi.v[j];
+    }
+    stv<LP>(z + o, zi);
   }
   __syncthreads();
 }
@@ -708,40 +785,48 @@ template <int T, typename VT>
 __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT>& M, LaneState<T>& L, VT* x,
                           VT* r, VT* p, VT* q, VT* z, const int* ra_, const int* rb_,
                           const double* w_, int* iters) {
+  constexpr int LP = Geo<T>::LP;
   __shared__ PcgLanes<T, VT> S;
-  // right-hand side and y of the schedule's tail (lane pairs: 16-byte aligned)
+  __shared__ Stamp<T, VT> St;
+  // right-hand side and y of the schedule's tail (lane groups: 16-byte aligned)
   __shared__ __align__(16) VT zt[TAIL_ROWS * T];
   const Geo<T> g;
-  const int l0 = g.lane, l1 = g.lane + 1;
-  // the outage's rows (-1: none) of the lanes that run; the SpMV reads the
-  // vector at the other end's row
-  const bool on0 = L.active[l0], on1 = L.active[l1];
-  const int ra0 = on0 ? ra_[l0] : -1, rb0 = on0 ? rb_[l0] : -1;
-  const int ra1 = on1 ? ra_[l1] : -1, rb1 = on1 ? rb_[l1] : -1;
-  const VT w0 = (VT)w_[l0], w1 = (VT)w_[l1];
-  const int lo0 = L.lo[l0], cnt0 = L.cnt[l0], lo1 = L.lo[l1], cnt1 = L.cnt[l1];
+  const int tid = threadIdx.x;
   const bool jac = (P.precond == PREC_JACOBI);
-  // the zero row that padding slots point at
+  // the outage's rows of the lanes that run (-1: none); the zero row that
+  // padding slots point at
+  if (tid < T) {
+    const bool on = L.active[tid];
+    St.ra[tid] = on ? ra_[tid] : -1;
+    St.rb[tid] = on ? rb_[tid] : -1;
+    St.w[tid] = (VT)w_[tid];
+  }
   if (g.rs == 0) {
-    st2(p + (size_t)M.n * T + g.lane, Pair<VT>{(VT)0, (VT)0});
-    st2(z + (size_t)M.n * T + g.lane, Pair<VT>{(VT)0, (VT)0});
+    stv<LP>(p + (size_t)M.n * T + g.lane, vzero<VT, LP>());
+    stv<LP>(z + (size_t)M.n * T + g.lane, vzero<VT, LP>());
   }
   __syncthreads();
-  Pair<VT> bbp{0, 0}, rzp{0, 0};
+  const unsigned long long filt = stamp_filter<T, VT>(St);
+  // islands in this tile: the SpMV then masks rows per lane
+  bool islands = false;
+#pragma unroll 1
+  for (int k = 0; k < T; ++k) islands |= L.active[k] && L.cnt[k] > 0;
+  const LaneState<T>* isl = islands ? &L : nullptr;
+  Vec<VT, LP> bbp = vzero<VT, LP>(), rzp = vzero<VT, LP>(), al = vzero<VT, LP>();
   if (jac) {
-    jacobi_pass<T, VT, false>(M, x, r, p, q, z, (VT)0, (VT)0, ra0, rb0, w0, ra1, rb1, w1, bbp, rzp);
+    jacobi_pass<T, VT, false>(M, x, r, p, q, z, al, St, bbp, rzp);
   } else {
-    Pair<VT> rzt{0, 0};
-    bbp = fwd_pass<T, VT, false>(M, x, r, p, q, z, (VT)0, (VT)0, zt, rzt);
+    Vec<VT, LP> rzt = vzero<VT, LP>();
+    bbp = fwd_pass<T, VT, false>(M, x, r, p, q, z, al, zt, rzt);
     rzp = bwd_pass<T, VT>(M, r, z, rzt);
   }
-  const Pair<VT> bb = lane_sum<T, RS_BB>(L, bbp.a, bbp.b);
-  const Pair<VT> rz0 = lane_sum<T, RS_RZ0>(L, rzp.a, rzp.b);
+  const Vec<VT, LP> bb = lane_sum<T, RS_BB>(L, bbp);
+  const Vec<VT, LP> rz0 = lane_sum<T, RS_RZ0>(L, rzp);
   if (g.rs == 0) {
 #pragma unroll
     for (int j = 0; j < LP; ++j) {
       const int ln = g.lane + j;
-      const VT b_ = j ? bb.b : bb.a, r_ = j ? rz0.b : rz0.a;
+      const VT b_ = bb.v[j], r_ = rz0.v[j];
       S.bb[ln] = b_;
       S.rz[0][ln] = r_;
       S.rrmin[ln] = b_;
@@ -754,43 +839,41 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
   __syncthreads();  // publishes S and the first z
   const VT tol2 = (VT)(P.inner_rtol * P.inner_rtol);
   int par = 0;
-  VT be0 = 0, be1 = 0;
+  Vec<VT, LP> be = vzero<VT, LP>();
   for (int it = 0; it < P.max_inner; ++it) {
     bool any = false;
 #pragma unroll 1
     for (int k = 0; k < T; ++k) any |= !(S.pdone[k] | S.stop[k]);
     if (!any) break;
-    const bool run0 = !(S.pdone[l0] | S.stop[l0]), run1 = !(S.pdone[l1] | S.stop[l1]);
     // new direction p = mask(z) + beta p and q = B_s p in one pass
-    const Pair<VT> pqp = spmv_pass<T, VT, true>(M, z, p, q, ra0, rb0, w0, ra1, rb1, w1, be0,
-                                                be1, it == 0, lo0, cnt0, lo1, cnt1);
-    const Pair<VT> pq = lane_sum<T, RS_PQ>(L, pqp.a, pqp.b);
-    VT al0 = 0, al1 = 0;
-    bool bk0 = false, bk1 = false;
-    if (run0) {
-      if (pq.a > (VT)0 && isfinite(pq.a)) al0 = S.rz[par][l0] / pq.a;
-      else bk0 = true;  // breakdown: keep the current iterate
+    const Vec<VT, LP> pqp = spmv_pass<T, VT, true>(M, z, p, q, St, filt, be, it == 0, isl);
+    const Vec<VT, LP> pq = lane_sum<T, RS_PQ>(L, pqp);
+    int bk = 0;  // lanes whose p.Bp broke down: keep the current iterate
+#pragma unroll
+    for (int j = 0; j < LP; ++j) {
+      const int ln = g.lane + j;
+      al.v[j] = (VT)0;
+      if (!(S.pdone[ln] | S.stop[ln])) {
+        if (pq.v[j] > (VT)0 && isfinite(pq.v[j])) al.v[j] = S.rz[par][ln] / pq.v[j];
+        else bk |= 1 << j;
+      }
     }
-    if (run1) {
-      if (pq.b > (VT)0 && isfinite(pq.b)) al1 = S.rz[par][l1] / pq.b;
-      else bk1 = true;
-    }
-    if (g.rs == 0) {
-      if (bk0) S.brk[l0] = 1;
-      if (bk1) S.brk[l1] = 1;
-    }
-    Pair<VT> rrp{0, 0}, rzn{0, 0};
+    if (g.rs == 0)
+#pragma unroll
+      for (int j = 0; j < LP; ++j)
+        if ((bk >> j) & 1) S.brk[g.lane + j] = 1;
+    Vec<VT, LP> rrp = vzero<VT, LP>(), rzn = vzero<VT, LP>();
     if (jac) {
-      jacobi_pass<T, VT, true>(M, x, r, p, q, z, al0, al1, ra0, rb0, w0, ra1, rb1, w1, rrp, rzn);
+      jacobi_pass<T, VT, true>(M, x, r, p, q, z, al, St, rrp, rzn);
     } else {
-      rrp = fwd_pass<T, VT, true>(M, x, r, p, q, z, al0, al1, zt, rzn);  // rzn: the tail's r.z
+      rrp = fwd_pass<T, VT, true>(M, x, r, p, q, z, al, zt, rzn);  // rzn: the tail's r.z
     }
-    const Pair<VT> rr = lane_sum<T, RS_RR>(L, rrp.a, rrp.b);
+    const Vec<VT, LP> rr = lane_sum<T, RS_RR>(L, rrp);
     if (g.rs == 0) {
 #pragma unroll
       for (int j = 0; j < LP; ++j) {
         const int ln = g.lane + j;
-        const VT v = j ? rr.b : rr.a;
+        const VT v = rr.v[j];
         if (S.pdone[ln] | S.stop[ln]) continue;
         if (S.brk[ln]) { S.pdone[ln] = 1; continue; }
         iters[ln] += 1;
@@ -805,21 +888,24 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
     }
     __syncthreads();
     // lanes still running, read before S.stop is next written (after r.z)
-    const bool go0 = !(S.pdone[l0] | S.stop[l0]), go1 = !(S.pdone[l1] | S.stop[l1]);
+    int go = 0;
+#pragma unroll
+    for (int j = 0; j < LP; ++j) go |= (!(S.pdone[g.lane + j] | S.stop[g.lane + j])) << j;
     any = false;
 #pragma unroll 1
     for (int k = 0; k < T; ++k) any |= !(S.pdone[k] | S.stop[k]);
     if (!any) break;
     if (!jac) rzn = bwd_pass<T, VT>(M, r, z, rzn);
-    const Pair<VT> rz = lane_sum<T, RS_RZ>(L, rzn.a, rzn.b);
-    be0 = go0 ? rz.a / S.rz[par][l0] : (VT)0;
-    be1 = go1 ? rz.b / S.rz[par][l1] : (VT)0;
+    const Vec<VT, LP> rz = lane_sum<T, RS_RZ>(L, rzn);
+#pragma unroll
+    for (int j = 0; j < LP; ++j)
+      be.v[j] = ((go >> j) & 1) ? rz.v[j] / S.rz[par][g.lane + j] : (VT)0;
     if (g.rs == 0) {
 #pragma unroll
       for (int j = 0; j < LP; ++j) {
         const int ln = g.lane + j;
-        if (!(j ? go1 : go0)) continue;
-        const VT v = j ? rz.b : rz.a;
+        if (!((go >> j) & 1)) continue;
+        const VT v = rz.v[j];
         S.rz[par ^ 1][ln] = v;
         if (!(v > (VT)0)) S.stop[ln] = 1;
       }
