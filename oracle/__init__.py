@@ -26,15 +26,18 @@ What it computes, and where the paper defines it:
 * ``adjoint``    -- loss and gradients of a smooth overload penalty summed
   over N-1 scenarios of the P-theta (DC) model, by one adjoint solve per
   scenario; pinned by finite differences.
+* ``dc``         -- the N-1 quick screen of the P-theta equation alone (DC
+  model, Sec. IV.A), re-formed and solved directly per scenario; pinned by
+  radial closed forms and line-outage distribution factors.
 
 Parity status of each function is stated in its docstring; the one function
 the paper gives no formula for (the re-dispatch weights) says
 "parity unpinned".
 """
-from . import adjoint, factor, islands, powerflow, redispatch, screen  # noqa: F401
+from . import adjoint, dc, factor, islands, powerflow, redispatch, screen  # noqa: F401
 from .powerflow import (STATUS_DIVERGED, STATUS_ISLAND_NO_GEN, STATUS_MAXITER,
                         STATUS_OK)
 
-__all__ = ["adjoint", "factor", "islands", "powerflow", "redispatch", "screen",
+__all__ = ["adjoint", "dc", "factor", "islands", "powerflow", "redispatch", "screen",
            "STATUS_OK", "STATUS_MAXITER", "STATUS_DIVERGED",
            "STATUS_ISLAND_NO_GEN"]

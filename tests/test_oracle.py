@@ -469,3 +469,122 @@ def test_adjoint_dc_angles_match_sherman_morrison():
         th = adjoint._theta(g, P, S)[keep]
         np.testing.assert_allclose(th, sm, rtol=1e-9, atol=1e-12)
         break
+
+
+# ------------------------------------------------------- DC quick screen
+def _subtree_flows(g, in_service):
+    """DC flows of a radial network by KCL alone: a branch carries the summed
+    injection of the part of the tree beyond it (independent of x)."""
+    n = g.n_bus
+    adj = {i: [] for i in range(n)}
+    for e in range(g.n_branch):
+        if in_service[e]:
+            adj[int(g.f[e])].append((int(g.t[e]), e))
+            adj[int(g.t[e])].append((int(g.f[e]), e))
+    order, par, pedge = [g.slack], {g.slack: -1}, {}
+    for u in order:
+        for v, e in adj[u]:
+            if v not in par:
+                par[v], pedge[v] = u, e
+                order.append(v)
+    sub = g.P_sched.astype(float).copy()
+    for u in reversed(order[1:]):
+        sub[par[u]] += sub[u]
+    f = np.zeros(g.n_branch)
+    for v, e in pedge.items():
+        # flow from parent to child = net injection absorbed beyond the child
+        f[e] = -sub[v] if int(g.t[e]) == v else sub[v]
+    return f
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_dc_radial_flows_are_subtree_injections(seed):
+    """A tree plus one chord; outaging the chord leaves the tree, whose DC
+    flows follow from KCL without any solve."""
+    from oracle import dc
+    g0, parent = random_tree_grid(30, seed)
+    rng = np.random.default_rng(seed + 10)
+    a, b = 0, 0
+    while a == b or parent[a] == b or parent[b] == a:
+        a, b = (int(v) for v in rng.integers(0, 30, 2))
+    g = grid_from_arrays(g0.bus_type, g0.P_sched, g0.Q_sched, g0.P_gen, g0.V_set,
+                         np.r_[g0.f, a], np.r_[g0.t, b], np.r_[g0.r, 0.0],
+                         np.r_[g0.x, 0.1], np.r_[g0.b_sh, 0.0])
+    chord = g.n_branch - 1
+    r = dc.dc_screen(g, [chord])
+    on = np.ones(g.n_branch, bool)
+    on[chord] = False
+    np.testing.assert_allclose(r["flow"][0], _subtree_flows(g, on), rtol=0, atol=1e-12)
+    assert r["flow"][0][chord] == 0.0 and r["status"][0] == 0
+
+
+def test_dc_lodf_matches_reformed_solves():
+    """Non-bridge outages: post-outage flows = base flows + LODF x the outaged
+    branch's base flow, LODF_kl = b_k a_k^T B'^-1 a_l / (1 - b_l a_l^T B'^-1 a_l)
+    from the base matrix only (Sherman-Morrison)."""
+    from oracle import dc
+    g = config_grid("grid120")
+    n, m = g.n_bus, g.n_branch
+    keep = np.flatnonzero(g.bus_type != 2)
+    pos = -np.ones(n, int)
+    pos[keep] = np.arange(keep.size)
+    on = np.ones(m, bool)
+    B0 = pf.bprime(n, g.f, g.t, g.x, on, keep).toarray()
+    Binv = np.linalg.inv(B0)
+    A = np.zeros((m, keep.size))
+    for k in range(m):
+        if pos[g.f[k]] >= 0:
+            A[k, pos[g.f[k]]] = 1.0
+        if pos[g.t[k]] >= 0:
+            A[k, pos[g.t[k]]] = -1.0
+    bvec = 1.0 / g.x
+    f0 = bvec * (A @ (Binv @ g.P_sched[keep]))
+    lab0 = islands.components(n, g.f, g.t, on)
+    outs = []
+    for l in range(m):
+        on_l = on.copy()
+        on_l[l] = False
+        if (islands.components(n, g.f, g.t, on_l) == lab0).all():
+            outs.append(l)
+    r = dc.dc_screen(g, outs)
+    for s, l in enumerate(outs):
+        ptdf = bvec * (A @ (Binv @ A[l]))
+        lodf = ptdf / (1.0 - ptdf[l])
+        exp = f0 + lodf * f0[l]
+        exp[l] = 0.0
+        np.testing.assert_allclose(r["flow"][s], exp, rtol=0, atol=1e-9)
+    assert len(outs) > 100
+
+
+def test_dc_islanding_balance():
+    """Bridge outages: dead branches carry nothing, and on the main island
+    the flows balance the re-dispatched injections at every non-slack bus
+    (the islands' net injection moved onto main-island PV generation)."""
+    from oracle import dc
+    g = config_grid("grid120")
+    n, m = g.n_bus, g.n_branch
+    on = np.ones(m, bool)
+    lab0 = islands.components(n, g.f, g.t, on)
+    bridges = []
+    for l in range(m):
+        on_l = on.copy()
+        on_l[l] = False
+        if (islands.components(n, g.f, g.t, on_l) != lab0).any():
+            bridges.append(l)
+    r = dc.dc_screen(g, bridges)
+    for s, l in enumerate(bridges):
+        isl = r["label"][s] != r["label"][s][g.slack]
+        live = np.ones(m, bool)
+        live[l] = False
+        live &= ~isl[g.f] & ~isl[g.t]
+        assert np.all(r["flow"][s][~live] == 0.0)
+        assert np.all(r["theta"][s][isl] == 0.0)
+        net = np.zeros(n)
+        np.add.at(net, g.f, r["flow"][s])
+        np.add.at(net, g.t, -r["flow"][s])
+        main = ~isl & (g.bus_type != 2)
+        Pt = g.P_sched.copy()
+        gen = (g.bus_type == 1) & ~isl & (g.P_gen > 0)
+        Pt[gen] += g.P_sched[isl].sum() * g.P_gen[gen] / g.P_gen[gen].sum()
+        np.testing.assert_allclose(net[main], Pt[main], rtol=0, atol=1e-10)
+    assert len(bridges) > 5
