@@ -228,6 +228,34 @@ GPCG_API gpcg_status gpcg_n1_adjoint(gpcg_ctx *ctx, const int32_t *outages, int3
                                      const double *b, double *loss, double *dL_dP,
                                      double *dL_db);
 
+/* The N-1 quick screen of the P-theta equation alone (Sec. IV.A: eq. (4)
+ * with |V| = 1, the DC power flow).  For each outage l = outages[s]: remove
+ * the branch, detect islands (Sec. IV.C), re-dispatch the islands' net
+ * injection over the main island's PV generators in proportion to P_gen
+ * (Sec. IV.C), and solve
+ *   B'_s theta_s = R_s P      (slack angle 0, islanded buses 0)
+ * with base-preconditioned CG (Sec. IV.B, eq. (6)); B'_s is B' (weights
+ * 1/x) with the outage's four-element change.  Then
+ *   flow[s][k] = (theta_i - theta_j) / x_k on branches k = (i, j) in service
+ *                between main-island buses, else 0,
+ *   max_loading[s] = max_k |flow[s][k]| / rating_k.
+ * Inputs: P[n_bus] bus injections (NULL: the grid's P_sched), host or device
+ * memory as mem says.  Outputs, each optional: theta[n_out][n_bus],
+ * flow[n_out][n_branch], iters[n_out] (PCG iterations), status[n_out]
+ * (GPCG_SCEN_OK, or GPCG_SCEN_ISLAND_NO_GEN when an island's injection has
+ * no main-island generator to go to and the slack takes it), max_loading.
+ * The solve runs in the context's precision: GPCG_BATCHED_FP64 to a 1e-12
+ * relative residual; GPCG_BATCHED_FP32 and _FP32_F16 with FP32 vectors and
+ * factors to 1e-6, then one step of iterative refinement (FP64 residual,
+ * FP32 correction); GPCG_PLAIN_FP64 is INVALID_ARG.  mem and
+ * stream as in gpcg_n1_screen (device mode returns once the work is
+ * enqueued; host mode when the results are written).  It does not need
+ * gpcg_base_solve.  Errors: INVALID_ARG, OOM, CUDA. */
+GPCG_API gpcg_status gpcg_n1_dc_screen(gpcg_ctx *ctx, const int32_t *outages, int32_t n_out,
+                                       int32_t mem, void *stream, const double *P,
+                                       double *theta, double *flow, int32_t *iters,
+                                       int32_t *status, double *max_loading);
+
 /* Batched operators of the hot path, for verification: each applies, for
  * S scenarios at once, one step of the inner solve to S vectors stored
  * row-major per scenario in the matrix's own row order (gpcg_export_matrix

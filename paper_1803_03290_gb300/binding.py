@@ -54,7 +54,7 @@ class Info(C.Structure):
 EXPORTS = ("gpcg_default_options", "gpcg_create", "gpcg_destroy", "gpcg_set_options",
            "gpcg_get_info", "gpcg_base_solve", "gpcg_n1_screen", "gpcg_apply",
            "gpcg_export_matrix", "gpcg_last_timings", "gpcg_n1_screen_noalloc",
-           "gpcg_n1_adjoint", "gpcg_analyze",
+           "gpcg_n1_adjoint", "gpcg_n1_dc_screen", "gpcg_analyze",
            "gpcg_last_error")
 
 _lib = None
@@ -88,6 +88,7 @@ def load(build_if_missing: bool = True):
     lib.gpcg_export_matrix.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gpcg_last_timings.argtypes = [vp, vp]
     lib.gpcg_n1_adjoint.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
+    lib.gpcg_n1_dc_screen.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp]
     lib.gpcg_analyze.argtypes = [C.POINTER(_Grid), i32, i32, vp, vp, vp, vp, vp, vp, vp]
     lib.gpcg_n1_screen_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gpcg_last_error.argtypes = []
@@ -275,6 +276,32 @@ class GPCG:
             self._h, _ptr(outages), int(outages.shape[0]), C.c_void_p(s.cuda_stream),
             g("theta"), g("V"), g("flow"), g("label"), g("iters"), g("status"),
             g("max_loading")))
+
+    def n1_dc_screen(self, outages, P=None,
+                     outputs=("theta", "flow", "iters", "status", "max_loading")):
+        """DC (P-theta) quick screen with host arrays (gpcg_n1_dc_screen)."""
+        out = np.ascontiguousarray(outages, dtype=np.int32)
+        S = out.shape[0]
+        n, m = self.n_bus, self.n_branch
+        Pa = None if P is None else np.ascontiguousarray(P, dtype=np.float64)
+        spec = dict(theta=((S, n), np.float64), flow=((S, m), np.float64),
+                    iters=((S,), np.int32), status=((S,), np.int32),
+                    max_loading=((S,), np.float64))
+        res = {k: np.empty(*spec[k]) for k in outputs}
+        g = lambda k: _ptr(res.get(k))
+        _check(self._lib, self._lib.gpcg_n1_dc_screen(
+            self._h, _ptr(out), S, 0, None, _ptr(Pa), g("theta"), g("flow"), g("iters"),
+            g("status"), g("max_loading")))
+        return res
+
+    def n1_dc_screen_device(self, outages, out: dict, P=None, stream=None):
+        """Device tensors in and out (see gpcg_n1_dc_screen)."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        g = lambda k: _ptr(out.get(k))
+        _check(self._lib, self._lib.gpcg_n1_dc_screen(
+            self._h, _ptr(outages), int(outages.shape[0]), 1, C.c_void_p(s.cuda_stream),
+            _ptr(P), g("theta"), g("flow"), g("iters"), g("status"), g("max_loading")))
 
     def n1_adjoint(self, outages, P=None, b=None, grads=True):
         """Host arrays: (loss, dL/dP, dL/db) of the N-1 overload penalty."""

@@ -1326,6 +1326,122 @@ extern "C" gpcg_status gpcg_n1_adjoint(gpcg_ctx* c, const int32_t* outages, int3
   return GPCG_OK;
 }
 
+// ---------------------------------------------------------- DC quick screen
+extern "C" gpcg_status gpcg_n1_dc_screen(gpcg_ctx* c, const int32_t* outages, int32_t n_out,
+                                         int32_t mem, void* stream, const double* P_in,
+                                         double* theta, double* flow, int32_t* iters,
+                                         int32_t* status, double* max_loading) {
+  if (!c) return fail(GPCG_ERR_INVALID_ARG, "gpcg_n1_dc_screen: ctx is NULL");
+  if (n_out < 0) return fail(GPCG_ERR_INVALID_ARG, "n_out < 0");
+  if (mem != GPCG_MEM_HOST && mem != GPCG_MEM_DEVICE)
+    return fail(GPCG_ERR_INVALID_ARG, "mem must be 0 (host) or 1 (device)");
+  if (n_out == 0) { g_err.clear(); return GPCG_OK; }
+  if (!outages) return fail(GPCG_ERR_INVALID_ARG, "outages is NULL");
+  if (c->opt.precision == GPCG_PLAIN_FP64)
+    return fail(GPCG_ERR_INVALID_ARG, "gpcg_n1_dc_screen runs batched (precision 1, 2 or 3)");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = c->n, m = c->m;
+  const size_t S = (size_t)n_out;
+  std::vector<int32_t> hout(S);
+  if (mem == GPCG_MEM_HOST) std::memcpy(hout.data(), outages, S * 4);
+  else {
+    CUDA_TRY(cudaMemcpyAsync(hout.data(), outages, S * 4, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  for (size_t s = 0; s < S; ++s)
+    if (hout[s] < 0 || hout[s] >= m)
+      return fail(GPCG_ERR_INVALID_ARG, "outages[%zu] = %d is not a branch index", s, hout[s]);
+  gpcg_status s_ = ensure_scen(c, S);
+  if (s_ != GPCG_OK) return s_;
+  std::vector<void*> tmp;
+  auto cleanup = [&]() { for (void* p : tmp) cudaFreeAsync(p, st); };
+  auto alloc = [&](void** p, size_t bytes) -> cudaError_t {
+    cudaError_t ce = cudaMallocAsync(p, bytes, st);
+    if (ce == cudaSuccess) tmp.push_back(*p);
+    return ce;
+  };
+  // injections: the caller's (host or device, caller's bus order) or P_sched
+  double *dPu = c->u_P_sched, *dPi = nullptr;
+  cudaError_t ce = alloc((void**)&dPi, (size_t)n * 8);
+  if (ce == cudaSuccess && P_in) {
+    if (mem == GPCG_MEM_DEVICE) dPu = const_cast<double*>(P_in);
+    else if ((ce = alloc((void**)&dPu, (size_t)n * 8)) == cudaSuccess)
+      ce = cudaMemcpyAsync(dPu, P_in, (size_t)n * 8, cudaMemcpyHostToDevice, st);
+  }
+  if (ce == cudaSuccess) ce = launch_gather_perm(st, n, c->G.user_of_bus, dPu, dPi);
+  // outputs: device pointers directly, or device staging for host pointers
+  auto stage = [&](auto* user, size_t count, auto** dev) -> cudaError_t {
+    *dev = nullptr;
+    if (!user) return cudaSuccess;
+    if (mem == GPCG_MEM_DEVICE) { *dev = user; return cudaSuccess; }
+    return alloc((void**)dev, count * sizeof(**dev));
+  };
+  double *d_th = nullptr, *d_fl = nullptr, *d_ml = nullptr;
+  int32_t *d_it = nullptr, *d_st = nullptr;
+  if (ce == cudaSuccess) ce = stage(theta, S * n, &d_th);
+  if (ce == cudaSuccess) ce = stage(flow, S * m, &d_fl);
+  if (ce == cudaSuccess) ce = stage(max_loading, S, &d_ml);
+  if (ce == cudaSuccess) ce = stage(iters, S, &d_it);
+  if (ce == cudaSuccess) ce = stage(status, S, &d_st);
+  if (ce != cudaSuccess) {
+    cleanup();
+    return fail(ce == cudaErrorMemoryAllocation ? GPCG_ERR_OOM : GPCG_ERR_CUDA,
+                "dc screen buffers: %s", cudaGetErrorString(ce));
+  }
+  CUDA_TRY(cudaMemcpyAsync(c->d_outages, hout.data(), S * 4, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemsetAsync(c->d_err, 0, 4, st));
+  ce = launch_islands(st, std::min<int>((int)S, c->num_sms * 4), n, m, c->slack_user, (int)S,
+                      c->d_outages, c->u_f, c->u_t, c->u_bus_type, dPu, c->u_P_gen, c->u_pre,
+                      c->d_lo, c->d_cnt, c->d_coef, c->d_nogen, nullptr, c->d_err);
+  if (ce != cudaSuccess) { cleanup(); return fail(GPCG_ERR_CUDA, "islands: %s", cudaGetErrorString(ce)); }
+  const bool f16 = c->opt.precision == GPCG_BATCHED_FP32_F16;
+  const bool f32 = c->opt.precision == GPCG_BATCHED_FP32 || f16;
+  const int T = 2;
+  const int n_tiles = (int)((S + T - 1) / T);
+  const int per_sm = std::max(1, f32 ? dc_max_blocks_per_sm<float>() : dc_max_blocks_per_sm<double>());
+  const int slots = std::max(1, std::min(n_tiles, c->num_sms * per_sm));
+  FdpfParams P = base_params(c);
+  // converged solves (2-3 iterations with the exact factor); FP32 solves are
+  // followed by one refinement step in the kernel
+  P.inner_rtol = std::min(c->opt.inner_rtol, f32 ? 1e-6 : 1e-12);
+  P.S = (int)S;
+  P.n_tiles = n_tiles;
+  P.sc = ScenInfo{c->d_outages, c->d_lo, c->d_cnt, c->d_coef, c->d_nogen};
+  const size_t vt = f32 ? 4 : 8;
+  Layout Lo = make_layout(c, T, slots, vt);
+  s_ = ensure_work(c, Lo.bytes);
+  if (s_ != GPCG_OK) { cleanup(); return s_; }
+  char* base = (char*)c->work;
+  const size_t vb = (size_t)slots * Lo.vec_bytes;
+  const size_t ss = (((Lo.sstride * 8 + 255) / 256) * 256) / 8;
+  P.wx = base; P.wr = base + vb; P.wp = base + 2 * vb; P.wq = base + 3 * vb; P.wz = base + 4 * vb;
+  P.vstride = Lo.vec_bytes / vt;
+  double* sbase = (double*)(base + 5 * vb);
+  P.wth = sbase; P.wV = sbase + slots * ss; P.wc = sbase + 2 * slots * ss;
+  P.ws = sbase + 3 * slots * ss;
+  P.sstride = ss;
+  DcParamsView D{dPi, c->G.user_of_bus, d_th, d_fl, d_ml, d_it, d_st};
+  ce = f32 ? launch_dc<float>(st, slots, P, D, c->MP.view<float>(f16), c->MP.view<double>())
+           : launch_dc<double>(st, slots, P, D, c->MP.view<double>(), c->MP.view<double>());
+  if (ce != cudaSuccess) { cleanup(); return fail(GPCG_ERR_CUDA, "dc screen: %s", cudaGetErrorString(ce)); }
+  if (mem == GPCG_MEM_HOST) {
+    auto back = [&](auto* user, auto* dev, size_t count) -> cudaError_t {
+      if (!user) return cudaSuccess;
+      return cudaMemcpyAsync(user, dev, count * sizeof(*user), cudaMemcpyDeviceToHost, st);
+    };
+    if (ce == cudaSuccess) ce = back(theta, d_th, S * n);
+    if (ce == cudaSuccess) ce = back(flow, d_fl, S * m);
+    if (ce == cudaSuccess) ce = back(max_loading, d_ml, S);
+    if (ce == cudaSuccess) ce = back(iters, d_it, S);
+    if (ce == cudaSuccess) ce = back(status, d_st, S);
+  }
+  cleanup();  // stream-ordered frees: after the kernel and the copies
+  if (mem == GPCG_MEM_HOST && ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) return fail(GPCG_ERR_CUDA, "dc screen: %s", cudaGetErrorString(ce));
+  g_err.clear();
+  return GPCG_OK;
+}
+
 extern "C" gpcg_status gpcg_apply(gpcg_ctx* c, int32_t which, int32_t op, const int32_t* outages,
                                   int32_t S, int32_t precision, const double* X, double* Y) {
   if (!c || !outages || !X || !Y || S < 0)

@@ -57,6 +57,22 @@ struct AdjParamsView {
 cudaError_t launch_adjoint(cudaStream_t st, int grid, const FdpfParams& P, const AdjParamsView& A,
                            const DevMatT<double>& M);
 int adjoint_max_blocks_per_sm();
+
+// Inputs and outputs of the DC (P-theta) quick screen.
+struct DcParamsView {
+  const double* P;              // [n] injections, internal bus order
+  const int32_t* user_of_bus;   // internal bus -> caller's index
+  double* theta;                // [S][n] caller's bus order, or null
+  double* flow;                 // [S][m], or null
+  double* maxload;              // [S], or null
+  int32_t* iters;               // [S] PCG iterations, or null
+  int32_t* status;              // [S], or null
+};
+template <typename VT>
+cudaError_t launch_dc(cudaStream_t st, int grid, const FdpfParams& P, const DcParamsView& D,
+                      const DevMatT<VT>& M, const DevMatT<double>& M64);
+template <typename VT>
+int dc_max_blocks_per_sm();
 cudaError_t launch_slot_sum(cudaStream_t st, int n, int slots, const double* acc,
                             const int32_t* map, double* out);
 cudaError_t launch_gather_perm(cudaStream_t st, int n, const int32_t* idx, const double* src,

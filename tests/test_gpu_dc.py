@@ -1,0 +1,78 @@
+"""The DC (P-theta) N-1 quick screen, CUDA path against the oracle's direct
+per-scenario solves (oracle.dc) on the same seeded grids."""
+import numpy as np
+import pytest
+
+import paper_1803_03290_gb300 as gp
+from gpu_common import grid, sample_outages
+from oracle import dc
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(res, ref, th_tol, f_tol):
+    np.testing.assert_array_equal(res["status"], ref["status"])
+    np.testing.assert_allclose(res["theta"], ref["theta"], rtol=0, atol=th_tol)
+    np.testing.assert_allclose(res["flow"], ref["flow"], rtol=0, atol=f_tol)
+    np.testing.assert_allclose(res["max_loading"], ref["max_loading"], rtol=0, atol=f_tol)
+
+
+# FP32 solves are refined once in FP64: error ~ (FP32 solve error)^2
+@pytest.mark.parametrize("precision,th_tol,f_tol", [
+    (gp.BATCHED_FP64, 1e-10, 1e-8), (gp.BATCHED_FP32, 1e-7, 1e-5),
+    (gp.BATCHED_FP32_F16, 1e-7, 1e-5)])
+def test_dc_grid120_all_outages(precision, th_tol, f_tol):
+    g = grid("grid120")
+    c = gp.GPCG(g, precision=precision)
+    outages = np.arange(g.n_branch, dtype=np.int32)
+    res = c.n1_dc_screen(outages)
+    ref = dc.dc_screen(g, outages)
+    _check(res, ref, th_tol, f_tol)
+    assert (res["iters"] >= 1).all() and (res["iters"] <= 10).all()
+    c.close()
+
+
+def test_dc_grid2k_sample_with_injections():
+    """A seeded sample (bridges included, ragged last tile) with caller
+    injections: P scaled and perturbed, sum kept."""
+    g = grid("grid2k")
+    rng = np.random.default_rng(4)
+    P = g.P_sched * rng.uniform(0.8, 1.2, g.n_bus)
+    c = gp.GPCG(g, precision=gp.BATCHED_FP64)
+    outages = sample_outages(g, 75, seed=6)
+    res = c.n1_dc_screen(outages, P=P)
+    ref = dc.dc_screen(g, outages, P=P)
+    _check(res, ref, 1e-9, 1e-7)
+    c.close()
+
+
+def test_dc_device_mode_matches_host():
+    torch = pytest.importorskip("torch")
+    g = grid("grid2k")
+    dev = torch.device("cuda", 0)
+    c = gp.GPCG(g)
+    outages = sample_outages(g, 40, seed=7)
+    host = c.n1_dc_screen(outages)
+    S = outages.size
+    out = {"theta": torch.empty((S, g.n_bus), dtype=torch.float64, device=dev),
+           "flow": torch.empty((S, g.n_branch), dtype=torch.float64, device=dev),
+           "iters": torch.empty((S,), dtype=torch.int32, device=dev),
+           "status": torch.empty((S,), dtype=torch.int32, device=dev),
+           "max_loading": torch.empty((S,), dtype=torch.float64, device=dev)}
+    c.n1_dc_screen_device(torch.from_numpy(outages).to(dev), out)
+    torch.cuda.synchronize()
+    for k in out:
+        np.testing.assert_array_equal(out[k].cpu().numpy(), host[k])
+    c.close()
+
+
+def test_dc_rejects_bad_input():
+    g = grid("grid120")
+    c = gp.GPCG(g)
+    with pytest.raises(gp.GPCGError):
+        c.n1_dc_screen(np.array([0, g.n_branch], dtype=np.int32))
+    assert c.n1_dc_screen(np.zeros(0, dtype=np.int32))["status"].size == 0
+    c.set_options(precision=gp.PLAIN_FP64)
+    with pytest.raises(gp.GPCGError):
+        c.n1_dc_screen(np.array([0], dtype=np.int32))
+    c.close()
