@@ -261,6 +261,111 @@ def run_gpcg(args):
         dist.destroy_process_group()
 
 
+_DC_GRID = None
+
+
+def _dc_init(name):
+    global _DC_GRID
+    from gridgen import config_grid
+    _DC_GRID = config_grid(name)
+
+
+def _dc_chunk(outs):
+    from oracle import dc
+    dc.dc_screen(_DC_GRID, outs)
+    return len(outs)
+
+
+def run_dc(args):
+    """The DC (P-theta) quick screen of every outage: one batched PCG solve per
+    scenario (plus one FP64 refinement step of FP32 solves), flows, loading."""
+    import torch
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1803_03290_gb300 as gp
+    from gridgen import config_grid
+    g = config_grid(args.config)
+    prec = {"fp32": gp.BATCHED_FP32, "fp64": gp.BATCHED_FP64,
+            "fp16f": gp.BATCHED_FP32_F16}[args.precision]
+    c = gp.GPCG(g, precision=prec)
+    info = c.info()
+    S = g.n_branch if args.n_outages <= 0 else min(args.n_outages, g.n_branch)
+    n, m = g.n_bus, g.n_branch
+    outages = torch.arange(S, dtype=torch.int32, device=dev)
+    out = {"iters": torch.empty(S, dtype=torch.int32, device=dev),
+           "status": torch.empty(S, dtype=torch.int32, device=dev),
+           "max_loading": torch.empty(S, dtype=torch.float64, device=dev)}
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+    for _ in range(args.warmup):
+        c.n1_dc_screen_device(outages, out)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ms = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0.record()
+            c.n1_dc_screen_device(outages, out)
+            ev1.record()
+            torch.cuda.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+    value = S * args.steps / (sum(ms) / 1e3)
+    it = out["iters"].cpu().numpy().astype(np.float64)
+    hout = np.arange(S, dtype=np.int32)
+    e2e_ms = []
+    for k in range(args.steps + 1):
+        t0 = time.perf_counter()
+        r = c.n1_dc_screen(hout, outputs=("status", "max_loading"))
+        if k:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    w = 8 if prec == gp.BATCHED_FP64 else 4
+    refine = 0.0 if w == 8 else 40.0 * info["n_p"]     # FP64 residual and update per scenario
+    algo = (15.0 * w * info["n_p"] * it.sum() +
+            S * (8.0 * info["n_p"] + refine + 8.0 * n + 16.0 * n + 8.0 * m) +
+            it.sum() * (info["nnz_p"] + 2 * info["nnz_lp"]) * (w + 4) / max(S, 1))
+    peak, peak_kind = load_peaks()
+    achieved = algo / (statistics.mean(ms) / 1e3) / 1e9
+    cpu = None
+    if args.cpu_sample > 0:
+        import multiprocessing as mp
+        cores = len(os.sched_getaffinity(0))
+        outs = np.random.default_rng(11).choice(m, args.cpu_sample, replace=False)
+        chunks = [ch for ch in np.array_split(outs, cores) if len(ch)]
+        with mp.get_context("spawn").Pool(cores, initializer=_dc_init,
+                                          initargs=(args.config,)) as pool:
+            pool.map(_dc_chunk, [ch[:1] for ch in chunks])  # every worker warmed
+            t0 = time.perf_counter()
+            pool.map(_dc_chunk, chunks)
+            dt = time.perf_counter() - t0
+        cpu = {"value": round(args.cpu_sample / dt, 2), "unit": "scenarios/s", "cores": cores,
+               "kind": "oracle",
+               "sample": f"{args.cpu_sample} seeded outages, direct solve per scenario, "
+                         f"one process per core ({dt:.1f} s wall)"}
+    line = {"metric": "DC (P-theta) N-1 quick-screen scenarios/sec at 10k buses", "value": round(value, 1),
+            "unit": "scenarios/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(sum(ms) / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if w == 4 else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.config}: {n} buses, {m} branches, {S} single-branch "
+                                   f"outages, DC model, exact base-case preconditioner, "
+                                   f"{args.precision} PCG", "l2": "flushed between steps (512 MiB write)"},
+            "e2e": {"value": S / (statistics.mean(e2e_ms) / 1e3), "unit": "scenarios/s",
+                    "h2d_bytes_per_step": int(hout.nbytes),
+                    "d2h_bytes_per_step": int(r["status"].nbytes + r["max_loading"].nbytes)},
+            "gpu_launches": 2 * args.steps,
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "kernel": "dc_tiles_kernel", "peak_source": peak_kind,
+                         "algorithmic_bytes_per_launch": int(algo)},
+            "cpu_baseline": cpu, "clocks": clk.summary(),
+            "scenarios": {"ok": int((r["status"] == 0).sum()), "island_no_gen": int((r["status"] == 3).sum()),
+                          "mean_iters": float(it.mean())}}
+    print(json.dumps(line), flush=True)
+    c.close()
+
+
 def cpu_baseline(g, sample):
     """The oracle, as it stands, on a seeded sample of outages, all host cores."""
     from oracle import powerflow as pf
@@ -328,9 +433,13 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=400)
     ap.add_argument("--plain-sample", type=int, default=64)
     ap.add_argument("--ref-sample", type=int, default=256)
+    ap.add_argument("--workload", default="ac", choices=["ac", "dc"],
+                    help="ac: the FDPF N-1 screen (the headline); dc: the P-theta quick screen")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "dc":
+        run_dc(args)
     else:
         run_gpcg(args)
 
