@@ -41,12 +41,6 @@ void launch_tail_inverse(cudaStream_t, int, int, const int32_t*, const int32_t*,
                          const double*, double*, double*, float*, float*);
 void launch_adj_values(cudaStream_t, int, const int32_t*, const double*, const double*, double*,
                        double*);
-// islands.cu
-size_t islands_smem(int n);
-cudaError_t launch_islands(cudaStream_t, int, int, int, int, int, const int32_t*, const int32_t*,
-                           const int32_t*, const int8_t*, const double*, const double*,
-                           const int32_t*, int32_t*, int32_t*, double*, int32_t*,
-                           int32_t*, int32_t*);
 }  // namespace gpcg
 
 
@@ -176,6 +170,8 @@ struct gpcg_ctx {
   std::vector<uint8_t> bridge;
   int n_bridges = 0;
   double pv_gen_total = 0.0;
+  IslandPlan isl;              // per-grid islanding data (device)
+  double* d_prefP = nullptr;   // [n + 1] prefix sums of a caller's injections
   int n_adj_slots = 0, n_adj_over = 0;
   std::vector<int32_t> deg;
   int32_t *mis_order = nullptr, *misq_order = nullptr;
@@ -585,11 +581,6 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
   for (int e = 0; e < m; ++e) c->n_bridges += c->bridge[e];
   for (int b = 0; b < n; ++b)
     if (g->bus_type[b] == GPCG_PV && g->P_gen[b] > 0) c->pv_gen_total += g->P_gen[b];
-  if ((size_t)n * sizeof(int32_t) > 227 * 1024) {
-    destroy(c);
-    return fail(GPCG_ERR_INVALID_ARG, "n_bus = %d exceeds the islanding kernel's limit (%d)", n,
-                (int)(227 * 1024 / 4));
-  }
   auto fail_cuda = [&](cudaError_t ce, const char* what) {
     destroy(c);
     return fail(ce == cudaErrorMemoryAllocation ? GPCG_ERR_OOM : GPCG_ERR_CUDA, "%s: %s", what,
@@ -615,6 +606,59 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
     std::vector<int32_t> pre_u(n);
     for (int b = 0; b < n; ++b) pre_u[b] = c->pre[I[b]];
     UP(c->u_pre, pre_u.data(), n);
+    // islanding plan: bridge intervals, labels of both sides, preorder sums
+    std::vector<int32_t> ord(n);
+    for (int b = 0; b < n; ++b) ord[pre_u[b]] = b;
+    std::vector<double> prefPs(n + 1, 0.0), prefG(n + 1, 0.0);
+    std::vector<int32_t> prefGc(n + 1, 0);
+    for (int k = 0; k < n; ++k) {
+      const int b = ord[k];
+      const bool gen = g->bus_type[b] == GPCG_PV && g->P_gen[b] > 0;
+      prefPs[k + 1] = prefPs[k] + g->P_sched[b];
+      prefG[k + 1] = prefG[k] + (gen ? g->P_gen[b] : 0.0);
+      prefGc[k + 1] = prefGc[k] + (gen ? 1 : 0);
+    }
+    // range minimum of the caller's bus indices over preorder intervals
+    std::vector<int32_t> pmin(n + 1, INT32_MAX), smin(n + 1, INT32_MAX);
+    for (int k = 0; k < n; ++k) pmin[k + 1] = std::min(pmin[k], ord[k]);
+    for (int k = n - 1; k >= 0; --k) smin[k] = std::min(smin[k + 1], ord[k]);
+    int lg = 1;
+    while ((1 << lg) <= n) ++lg;
+    std::vector<std::vector<int32_t>> sp(lg, std::vector<int32_t>(n));
+    sp[0] = ord;
+    for (int j = 1; j < lg; ++j)
+      for (int k = 0; k + (1 << j) <= n; ++k)
+        sp[j][k] = std::min(sp[j - 1][k], sp[j - 1][k + (1 << (j - 1))]);
+    auto range_min = [&](int a, int b) {  // [a, b), b > a
+      int j = 31 - __builtin_clz((unsigned)(b - a));
+      return std::min(sp[j][a], sp[j][b - (1 << j)]);
+    };
+    std::vector<int32_t> br_lo(m, 0), br_cnt(m, 0), lab_isl(m, 0), lab_main(m, 0);
+    for (int e = 0; e < m; ++e) {
+      if (!c->bridge[e]) continue;
+      const int a = f_i[e], b = t_i[e];
+      const int child = c->pre[a] > c->pre[b] ? a : b;  // the tree edge's lower end
+      const int lo = c->pre[child], cnt = c->sub[child];
+      br_lo[e] = lo;
+      br_cnt[e] = cnt;
+      lab_isl[e] = range_min(lo, lo + cnt);
+      lab_main[e] = std::min(pmin[lo], smin[lo + cnt]);
+    }
+    int32_t *d_lo_, *d_cnt_, *d_li, *d_lm, *d_ord, *d_gc;
+    double *d_ps, *d_pg;
+    UP(d_lo_, br_lo.data(), m);
+    UP(d_cnt_, br_cnt.data(), m);
+    UP(d_li, lab_isl.data(), m);
+    UP(d_lm, lab_main.data(), m);
+    UP(d_ord, ord.data(), n);
+    UP(d_ps, prefPs.data(), n + 1);
+    UP(d_pg, prefG.data(), n + 1);
+    UP(d_gc, prefGc.data(), n + 1);
+    AL(c->d_prefP, n + 1);
+    c->isl.br_lo = d_lo_; c->isl.br_cnt = d_cnt_;
+    c->isl.lab_isl = d_li; c->isl.lab_main = d_lm;
+    c->isl.u_pre = c->u_pre; c->isl.ord_u = d_ord;
+    c->isl.prefPs = d_ps; c->isl.prefG = d_pg; c->isl.prefGc = d_gc;
   }
   UP(c->u_f, g->from, m);
   UP(c->u_t, g->to, m);
@@ -996,19 +1040,16 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
   const bool plain = c->opt.precision == GPCG_PLAIN_FP64;
   const bool f16 = c->opt.precision == GPCG_BATCHED_FP32_F16;
   const bool f32 = c->opt.precision == GPCG_BATCHED_FP32 || f16;
-  const int cc_grid = std::min<int>((int)S, c->num_sms * 4);
   // islanding for every outage (the autotuner's probes need it too)
   // (inside a stream capture the events become event-record nodes of the graph)
   auto record = [](cudaEvent_t ev, cudaStream_t s, bool cap) {
     return cap ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal) : cudaEventRecord(ev, s);
   };
   auto enqueue_islands = [&](cudaStream_t s, bool cap = false) -> cudaError_t {
-    cudaError_t e = cudaMemsetAsync(c->d_err, 0, 4, s);
-    if (e == cudaSuccess) e = record(c->ev[0], s, cap);
+    cudaError_t e = record(c->ev[0], s, cap);
     if (e == cudaSuccess)
-      e = launch_islands(s, cc_grid, c->n, c->m, c->slack_user, (int)S, c->d_outages, c->u_f,
-                         c->u_t, c->u_bus_type, c->u_P_sched, c->u_P_gen, c->u_pre, c->d_lo,
-                         c->d_cnt, c->d_coef, c->d_nogen, d_lab, c->d_err);
+      e = launch_islands(s, (int)S, c->n, c->d_outages, c->isl, nullptr, nullptr, c->d_lo,
+                         c->d_cnt, c->d_coef, c->d_nogen, d_lab);
     if (e == cudaSuccess) e = record(c->ev[1], s, cap);
     return e;
   };
@@ -1143,11 +1184,8 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
     if (ce == cudaSuccess) ce = back(status, d_stat, S);
     if (ce == cudaSuccess) ce = back(max_loading, d_ml, S);
     cleanup();
-    int32_t herr = 0;
-    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&herr, c->d_err, 4, cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) return fail(GPCG_ERR_CUDA, "n1_screen: %s", cudaGetErrorString(ce));
-    if (herr == 3) return fail(GPCG_ERR_CUDA, "internal: an island is not a depth-first subtree");
   }
   g_err.clear();
   return GPCG_OK;
@@ -1278,10 +1316,8 @@ extern "C" gpcg_status gpcg_n1_adjoint(gpcg_ctx* c, const int32_t* outages, int3
   double* accL = accb + (size_t)slots * m;
   if (S) {
     CUDA_TRY(cudaMemcpyAsync(c->d_outages, hout.data(), S * 4, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemsetAsync(c->d_err, 0, 4, st));
-    ce = launch_islands(st, std::min<int>((int)S, c->num_sms * 4), n, m, c->slack_user, (int)S,
-                        c->d_outages, c->u_f, c->u_t, c->u_bus_type, dPu, c->u_P_gen, c->u_pre,
-                        c->d_lo, c->d_cnt, c->d_coef, c->d_nogen, nullptr, c->d_err);
+    ce = launch_islands(st, (int)S, n, c->d_outages, c->isl, P_in ? dPu : nullptr, c->d_prefP,
+                        c->d_lo, c->d_cnt, c->d_coef, c->d_nogen, nullptr);
     if (ce != cudaSuccess) { cleanup(); return fail(GPCG_ERR_CUDA, "islands: %s", cudaGetErrorString(ce)); }
     FdpfParams P = base_params(c);
     P.inner_rtol = 1e-12;  // gradients want converged solves (2-3 iterations with the exact factor)
@@ -1389,10 +1425,8 @@ extern "C" gpcg_status gpcg_n1_dc_screen(gpcg_ctx* c, const int32_t* outages, in
                 "dc screen buffers: %s", cudaGetErrorString(ce));
   }
   CUDA_TRY(cudaMemcpyAsync(c->d_outages, hout.data(), S * 4, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemsetAsync(c->d_err, 0, 4, st));
-  ce = launch_islands(st, std::min<int>((int)S, c->num_sms * 4), n, m, c->slack_user, (int)S,
-                      c->d_outages, c->u_f, c->u_t, c->u_bus_type, dPu, c->u_P_gen, c->u_pre,
-                      c->d_lo, c->d_cnt, c->d_coef, c->d_nogen, nullptr, c->d_err);
+  ce = launch_islands(st, (int)S, n, c->d_outages, c->isl, P_in ? dPu : nullptr, c->d_prefP,
+                      c->d_lo, c->d_cnt, c->d_coef, c->d_nogen, nullptr);
   if (ce != cudaSuccess) { cleanup(); return fail(GPCG_ERR_CUDA, "islands: %s", cudaGetErrorString(ce)); }
   const bool f16 = c->opt.precision == GPCG_BATCHED_FP32_F16;
   const bool f32 = c->opt.precision == GPCG_BATCHED_FP32 || f16;
@@ -1598,6 +1632,7 @@ bool ctx_view(const gpcg_ctx* c, CtxView* v) {
   v->u_f = c->u_f;
   v->u_t = c->u_t;
   v->u_pre = c->u_pre;
+  v->isl = c->isl;
   v->u_bus_type = c->u_bus_type;
   v->u_P_sched = c->u_P_sched;
   v->u_P_gen = c->u_P_gen;

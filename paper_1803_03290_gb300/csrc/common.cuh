@@ -94,4 +94,30 @@ __device__ __forceinline__ bool in_island(int32_t pre, int32_t lo, int32_t cnt) 
   return (uint32_t)(pre - lo) < (uint32_t)cnt;
 }
 
+// Per-grid islanding data (device arrays).  A single-branch outage islands
+// buses only when the branch is a bridge; the island is then the subtree
+// below it in the depth-first tree rooted at the slack, preorder interval
+// [br_lo, br_lo + br_cnt) (br_cnt = 0: no island).  Preorder prefix sums
+// (n + 1 entries) of P_sched and of the PV generation with P_gen > 0 give
+// the island's injection and the main island's generation by difference.
+struct IslandPlan {
+  const int32_t *br_lo = nullptr, *br_cnt = nullptr;       // [n_branch]
+  const int32_t *lab_isl = nullptr, *lab_main = nullptr;   // [n_branch] component labels
+  const int32_t* u_pre = nullptr;     // [n_bus] preorder of each bus (caller's numbering)
+  const int32_t* ord_u = nullptr;     // [n_bus] caller's bus at each preorder position
+  const double* prefPs = nullptr;     // [n_bus + 1] prefix sums of P_sched
+  const double* prefG = nullptr;      // [n_bus + 1] prefix sums of PV P_gen > 0
+  const int32_t* prefGc = nullptr;    // [n_bus + 1] prefix counts of those generators
+};
+
+// Islanding of S outages: interval, re-dispatch coefficient, no-generator
+// flag per scenario, and (when label_out is given) labels [S][n_bus].
+// P_user: the caller's injections (caller's bus order) for the island sums,
+// with prefP_scratch (n_bus + 1 doubles) to hold their prefix sums; null
+// uses P_sched.
+cudaError_t launch_islands(cudaStream_t st, int S, int n, const int32_t* outages,
+                           const IslandPlan& I, const double* P_user, double* prefP_scratch,
+                           int32_t* isl_lo, int32_t* isl_cnt, double* coef, int32_t* no_gen,
+                           int32_t* label_out);
+
 }  // namespace gpcg

@@ -17,6 +17,7 @@ struct CtxView {
   const int32_t *u_f = nullptr, *u_t = nullptr, *u_pre = nullptr;  // caller numbering
   const int8_t* u_bus_type = nullptr;
   const double *u_P_sched = nullptr, *u_P_gen = nullptr;
+  IslandPlan isl;
   bool base_ok = false;
 };
 

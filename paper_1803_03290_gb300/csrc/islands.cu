@@ -1,129 +1,118 @@
-// Islanding detection (Sec. IV.C) for a batch of outage scenarios, and the
-// per-scenario data of the proportional re-dispatch.
+// Islanding detection (Sec. IV.C) for a batch of single-branch outages, and
+// the per-scenario data of the proportional re-dispatch.
 //
-// One CTA takes one scenario at a time: every bus's parent pointer lives in
-// shared memory; the CTA unites the two ends of every in-service branch
-// (the outaged branch is skipped), always hooking the larger root under the
-// smaller one, so that each component's final root is its smallest bus
-// index -- the canonical label.  The main island is the slack's component.
-//
-// For a single-branch outage of a connected grid the islanded buses are
-// exactly one subtree of a depth-first tree rooted at the slack, hence one
-// interval of the depth-first preorder.  The kernel records that interval
-// (and checks that the island really fills it), so the solve kernels can
-// test island membership with one comparison per bus.
+// The grid is connected, so removing one branch islands buses only when the
+// branch is a bridge, and then the islanded buses are exactly the subtree
+// below the bridge in a depth-first tree rooted at the slack: one interval
+// [lo, lo + cnt) of the depth-first preorder.  The bridges, their intervals
+// and the canonical labels of both sides (the smallest bus index of each
+// component) are found once per grid on the host (Tarjan's bridge search);
+// per scenario the interval is looked up, and the island's net injection
+// and the main island's PV generation come from prefix sums over the
+// preorder.  The solve kernels then test island membership with one
+// comparison per bus.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace gpcg {
 
-__device__ __forceinline__ int uf_find(volatile int32_t* p, int x) {
-  int px = p[x];
-  while (px != x) {
-    int gp = p[px];
-    p[x] = gp;  // path halving; parents only ever decrease
-    x = px;
-    px = gp;
+// One thread per scenario: island interval, re-dispatch coefficient (the
+// island's net injection over the main island's PV generation with
+// P_gen > 0) and the no-generator flag.
+__global__ void islands_kernel(int S, const int32_t* __restrict__ outages,
+                               const int32_t* __restrict__ br_lo,
+                               const int32_t* __restrict__ br_cnt,
+                               const double* __restrict__ prefP, const double* __restrict__ prefG,
+                               const int32_t* __restrict__ prefGc, int n, int32_t* isl_lo,
+                               int32_t* isl_cnt, double* coef, int32_t* no_gen) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  const int l = outages[s];
+  const int lo = br_lo[l], cnt = br_cnt[l];
+  isl_lo[s] = lo;
+  isl_cnt[s] = cnt;
+  if (cnt == 0) {
+    coef[s] = 0.0;
+    no_gen[s] = 0;
+    return;
   }
-  return x;
+  const int hi = lo + cnt;
+  const double sumP = prefP[hi] - prefP[lo];
+  const int gens_main = prefGc[n] - (prefGc[hi] - prefGc[lo]);
+  const double gen_main = prefG[n] - (prefG[hi] - prefG[lo]);
+  const int ng = gens_main == 0;
+  no_gen[s] = ng;
+  coef[s] = ng ? 0.0 : sumP / gen_main;
 }
 
-__device__ __forceinline__ void uf_unite(int32_t* p, int a, int b) {
-  volatile int32_t* vp = p;
-  a = uf_find(vp, a);
-  b = uf_find(vp, b);
-  while (a != b) {
-    if (a < b) { int t = a; a = b; b = t; }
-    int old = atomicCAS(&p[a], a, b);
-    if (old == a) return;
-    a = uf_find(vp, old);
-    b = uf_find(vp, b);
-  }
-}
-
-template <int NT>
-__global__ void __launch_bounds__(NT) islands_kernel(
-    int n, int m, int slack, int S, const int32_t* __restrict__ outages,
-    const int32_t* __restrict__ f, const int32_t* __restrict__ t,
-    const int8_t* __restrict__ bus_type, const double* __restrict__ P_sched,
-    const double* __restrict__ P_gen, const int32_t* __restrict__ pre,
-    int32_t* isl_lo, int32_t* isl_cnt, double* coef, int32_t* no_gen, int32_t* label_out,
-    int32_t* err) {
-  extern __shared__ int32_t parent[];
-  __shared__ double red_d[2][NT / 32];
-  __shared__ int32_t red_i[3][NT / 32];
-  const int tid = threadIdx.x, wid = tid >> 5, ln = tid & 31;
-  for (int s = blockIdx.x; s < S; s += gridDim.x) {
-    int l = outages[s];
-    for (int i = tid; i < n; i += NT) parent[i] = i;
-    __syncthreads();
-    for (int e = tid; e < m; e += NT)
-      if (e != l) uf_unite(parent, f[e], t[e]);
-    __syncthreads();
-    for (int i = tid; i < n; i += NT) parent[i] = uf_find(parent, i);
-    __syncthreads();
-    int main_lab = parent[slack];
-    double sumP = 0.0, genM = 0.0;  // island net injection, main-island PV generation
-    int cnt = 0, lo = 0x7fffffff, hi = -1;
-    for (int i = tid; i < n; i += NT) {
-      int lab = parent[i];
-      if (label_out) label_out[(size_t)s * n + i] = lab;
-      if (lab == main_lab) {
-        if (bus_type[i] == 1 && P_gen[i] > 0.0) genM += P_gen[i];
-      } else {
-        ++cnt;
-        sumP += P_sched[i];
-        int pr = pre[i];
-        lo = min(lo, pr);
-        hi = max(hi, pr);
-      }
-    }
-    for (int o = 16; o; o >>= 1) {
-      sumP += __shfl_xor_sync(0xffffffffu, sumP, o);
-      genM += __shfl_xor_sync(0xffffffffu, genM, o);
-      cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    }
-    if (ln == 0) {
-      red_d[0][wid] = sumP; red_d[1][wid] = genM;
-      red_i[0][wid] = cnt; red_i[1][wid] = lo; red_i[2][wid] = hi;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double sp = 0.0, gi = 0.0;
-      int c = 0, a = 0x7fffffff, b = -1;
-      for (int w = 0; w < NT / 32; ++w) {  // fixed order: deterministic sums
-        sp += red_d[0][w]; gi += red_d[1][w];
-        c += red_i[0][w]; a = min(a, red_i[1][w]); b = max(b, red_i[2][w]);
-      }
-      if (c > 0 && b - a + 1 != c) atomicExch(err, 3);
-      isl_lo[s] = c > 0 ? a : 0;
-      isl_cnt[s] = c;
-      const double den = gi;  // main-island PV generation
-      int ng = (c > 0) && !(den > 0.0);
-      no_gen[s] = ng;
-      coef[s] = (c > 0 && !ng) ? sp / den : 0.0;
-    }
-    __syncthreads();
+// Component labels per scenario and bus (the caller's numbering): the
+// island's smallest bus index inside the interval, the main island's
+// outside it (0 for every bus of a non-bridge outage).
+__global__ void labels_kernel(int S, int n, const int32_t* __restrict__ outages,
+                              const int32_t* __restrict__ pre, const int32_t* __restrict__ isl_lo,
+                              const int32_t* __restrict__ isl_cnt,
+                              const int32_t* __restrict__ lab_isl,
+                              const int32_t* __restrict__ lab_main, int32_t* label_out) {
+  const size_t total = (size_t)S * n;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const int s = (int)(k / n), b = (int)(k % n);
+    const int l = outages[s];
+    label_out[k] = in_island(pre[b], isl_lo[s], isl_cnt[s]) ? lab_isl[l] : lab_main[l];
   }
 }
 
-size_t islands_smem(int n) { return (size_t)n * sizeof(int32_t); }
+// prefP[k] = sum of P over the buses of preorder < k (ord[j]: the bus of
+// preorder j), in a fixed order: each thread sums a contiguous chunk, one
+// thread scans the chunk sums.
+__global__ void __launch_bounds__(1024) preorder_prefix_kernel(int n,
+                                                               const int32_t* __restrict__ ord,
+                                                               const double* __restrict__ P,
+                                                               double* prefP) {
+  __shared__ double part[1024];
+  const int t = threadIdx.x;
+  const int chunk = (n + 1023) / 1024;
+  const int a = min(n, t * chunk), b = min(n, a + chunk);
+  double s = 0.0;
+  for (int k = a; k < b; ++k) s += P[ord[k]];
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    double run = 0.0;
+    for (int k = 0; k < 1024; ++k) {
+      const double v = part[k];
+      part[k] = run;
+      run += v;
+    }
+    prefP[n] = run;
+  }
+  __syncthreads();
+  double run = part[t];
+  for (int k = a; k < b; ++k) {
+    prefP[k] = run;
+    run += P[ord[k]];
+  }
+}
 
-cudaError_t launch_islands(cudaStream_t st, int grid, int n, int m, int slack, int S,
-                           const int32_t* outages, const int32_t* f, const int32_t* t,
-                           const int8_t* bus_type, const double* P_sched, const double* P_gen,
-                           const int32_t* pre, int32_t* isl_lo,
-                           int32_t* isl_cnt, double* coef, int32_t* no_gen, int32_t* label_out,
-                           int32_t* err) {
+cudaError_t launch_islands(cudaStream_t st, int S, int n, const int32_t* outages,
+                           const IslandPlan& I, const double* P_user, double* prefP_scratch,
+                           int32_t* isl_lo, int32_t* isl_cnt, double* coef, int32_t* no_gen,
+                           int32_t* label_out) {
   if (S == 0) return cudaSuccess;
-  size_t smem = islands_smem(n);
-  cudaError_t ce = cudaFuncSetAttribute(islands_kernel<512>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (ce != cudaSuccess) return ce;
-  islands_kernel<512><<<grid, 512, smem, st>>>(n, m, slack, S, outages, f, t, bus_type, P_sched,
-                                               P_gen, pre, isl_lo, isl_cnt, coef,
-                                               no_gen, label_out, err);
+  const double* prefP = I.prefPs;
+  if (P_user) {
+    preorder_prefix_kernel<<<1, 1024, 0, st>>>(n, I.ord_u, P_user, prefP_scratch);
+    prefP = prefP_scratch;
+  }
+  islands_kernel<<<(S + 255) / 256, 256, 0, st>>>(S, outages, I.br_lo, I.br_cnt, prefP, I.prefG,
+                                                   I.prefGc, n, isl_lo, isl_cnt, coef, no_gen);
+  if (label_out) {
+    const size_t total = (size_t)S * n;
+    const int grid = (int)std::min<size_t>((total + 255) / 256, 152 * 64);
+    labels_kernel<<<grid, 256, 0, st>>>(S, n, outages, I.u_pre, isl_lo, isl_cnt, I.lab_isl,
+                                        I.lab_main, label_out);
+  }
   return cudaGetLastError();
 }
 

@@ -15,10 +15,6 @@
 #include "fdpf.h"
 
 namespace gpcg {
-cudaError_t launch_islands(cudaStream_t, int, int, int, int, int, const int32_t*, const int32_t*,
-                           const int32_t*, const int8_t*, const double*, const double*,
-                           const int32_t*, int32_t*, int32_t*, double*, int32_t*, int32_t*,
-                           int32_t*);
 void set_last_error(const char* msg);
 }  // namespace gpcg
 
@@ -126,7 +122,6 @@ extern "C" gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx* ctx, const int32_t* outa
     }
   }
   int32_t* counter = (int32_t*)base;
-  int32_t* eflag = counter + 1;
   unsigned char* q = base + head;
   int32_t* lo = (int32_t*)q;  q += up256(S * 4);
   int32_t* cnt = (int32_t*)q; q += up256(S * 4);
@@ -134,11 +129,10 @@ extern "C" gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx* ctx, const int32_t* outa
   double* coef = (double*)q;  q += up256(S * 8);
   unsigned char* work = q;
 
-  cudaError_t ce = cudaMemsetAsync(base, 0, head, st);  // queue head and error flag start at 0
+  cudaError_t ce = cudaMemsetAsync(base, 0, head, st);  // the queue head starts at 0
   if (ce != cudaSuccess) return err(GPCG_ERR_CUDA, "scratch reset: %s", cudaGetErrorString(ce));
-  ce = launch_islands(st, std::min<int>((int)S, c.num_sms * 4), c.n, c.m, c.slack_user, (int)S,
-                      outages, c.u_f, c.u_t, c.u_bus_type, c.u_P_sched, c.u_P_gen, c.u_pre, lo,
-                      cnt, coef, nogen, island_label, eflag);
+  ce = launch_islands(st, (int)S, c.n, outages, c.isl, nullptr, nullptr, lo, cnt, coef, nogen,
+                      island_label);
   if (ce != cudaSuccess) return err(GPCG_ERR_CUDA, "islands: %s", cudaGetErrorString(ce));
 
   FdpfParams P;
