@@ -522,16 +522,18 @@ __device__ GPCG_LOOP_INLINE void tail_solve(const DevMatT<VT>& M, VT* __restrict
     stv<LP>(s + (size_t)k * T + g.lane, a);
   }
   __syncthreads();
-  // (b) y_t = X rhs: X_kj = xc[j nt + k], zero above the diagonal
+  // (b) y_t = X rhs: X_kj = xc[j nt + k], zero above the diagonal; a warp's
+  // rows k are consecutive, so it stops at the diagonal of its last row
   Vec<VT, LP> y[NPT];
 #pragma unroll
   for (int m = 0; m < NPT; ++m) {
     const int k = g.rs + m * RPS;
+    const int jend = min(nt, __shfl_sync(0xffffffffu, k, 31) + 1);  // every lane takes part
     y[m] = vzero<VT, LP>();
     if (k < nt) {
       const VT* col = M.xc + k;
 #pragma unroll 4
-      for (int j = 0; j < nt; ++j) {
+      for (int j = 0; j < jend; ++j) {
         const VT xv = __ldg(col + (size_t)j * nt);
         const Vec<VT, LP> sv = ldv<LP>(s + (size_t)j * T + g.lane);
 #pragma unroll
@@ -546,15 +548,17 @@ __device__ GPCG_LOOP_INLINE void tail_solve(const DevMatT<VT>& M, VT* __restrict
     if (k < nt) stv<LP>(s + (size_t)k * T + g.lane, y[m]);
   }
   __syncthreads();
-  // (c) z_t = X^T y_t: X_ik = xr[i nt + k], zero for i < k
+  // (c) z_t = X^T y_t: X_ik = xr[i nt + k], zero for i < k; a warp starts at
+  // the diagonal of its first row
 #pragma unroll
   for (int m = 0; m < NPT; ++m) {
     const int k = g.rs + m * RPS;
+    const int ibeg = __shfl_sync(0xffffffffu, k, 0);
     if (k >= nt) continue;
     const VT* col = M.xr + k;
     Vec<VT, LP> a = vzero<VT, LP>();
 #pragma unroll 4
-    for (int i = 0; i < nt; ++i) {
+    for (int i = ibeg; i < nt; ++i) {
       const VT xv = __ldg(col + (size_t)i * nt);
       const Vec<VT, LP> sv = ldv<LP>(s + (size_t)i * T + g.lane);
 #pragma unroll
