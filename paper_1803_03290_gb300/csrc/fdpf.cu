@@ -171,33 +171,26 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
   }
 }
 
-// (cos, sin) of theta + d from those of theta, by rotating through d.  The
-// sine and cosine of d come from their Taylor series: two and three terms
-// for |d| <= 0.005 (remainders d^5/120 and d^6/720 below 3e-14), five up to
-// 0.05 (remainders below 1e-21); larger steps recompute the angle.  Most increments of an
-// N-1 scenario are tiny (the outage moves few angles much), so the short form
-// is the common case and saves most of the FP64 work of the update.
+// (cos, sin) of theta + d from those of theta, by rotating through d:
+//   c' = c - (c (1 - cos d) + s sin d),   s' = s - (s (1 - cos d) - c sin d).
+// For |d| <= 0.05 the two corrections are small (about |d|), so they are
+// formed in FP32 from the Taylor series of 1 - cos d and sin d (three terms
+// each; remainders below 4e-12 relative) and applied in FP64: their rounding
+// error, 6e-8 of |d|, vanishes as the iteration converges (the outer FDPF
+// loop sees the state through e + jf and corrects any drift).  d itself is
+// the FP32 solution of the inner solve.  Larger steps recompute the angle.
 __device__ __forceinline__ void rotate(double th_new, double d, double& c, double& s) {
-  const double ad = fabs(d);
-  double sd, cd;
-  if (ad <= 0.005) {
-    const double d2 = d * d;
-    sd = d - d * d2 * (1.0 / 6.0);
-    cd = 1.0 - d2 * (0.5 - d2 * (1.0 / 24.0));
-  } else if (ad <= 0.05) {
-    // nested Horner forms of the series; 1/k! ratios as multiplications
-    const double d2 = d * d;
-    sd = d * (1.0 - d2 * (1.0 / 6.0) * (1.0 - d2 * (1.0 / 20.0) *
-                                   (1.0 - d2 * (1.0 / 42.0) * (1.0 - d2 * (1.0 / 72.0)))));
-    cd = 1.0 - d2 * 0.5 * (1.0 - d2 * (1.0 / 12.0) * (1.0 - d2 * (1.0 / 30.0) *
-                                   (1.0 - d2 * (1.0 / 56.0) * (1.0 - d2 * (1.0 / 90.0)))));
+  if (fabs(d) <= 0.05) {
+    const float df = (float)d, d2 = df * df;
+    const float omc = d2 * (0.5f - d2 * (1.0f / 24.0f - d2 * (1.0f / 720.0f)));
+    const float sd = df * (1.0f - d2 * (1.0f / 6.0f - d2 * (1.0f / 120.0f)));
+    const float cf = (float)c, sf = (float)s;
+    const float dc = fmaf(cf, omc, sf * sd), ds = fmaf(sf, omc, -cf * sd);
+    c -= (double)dc;
+    s -= (double)ds;
   } else {
     sincos(th_new, &s, &c);
-    return;
   }
-  const double cn = c * cd - s * sd, sn = s * cd + c * sd;
-  c = cn;
-  s = sn;
 }
 
 // theta += dtheta (P half-step) or |V| += dV (Q half-step) on the matrix's
