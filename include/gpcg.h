@@ -109,7 +109,7 @@ typedef struct {
 typedef struct {
   double tol;          /* outer tolerance on max |dP|, |dQ| (p.u.); 1e-4 */
   double base_tol;     /* tolerance of gpcg_base_solve; 1e-10 */
-  double inner_rtol;   /* PCG stops at ||r|| <= inner_rtol ||b||; 1e-5 */
+  double inner_rtol;   /* PCG stops at ||r|| <= inner_rtol ||b||; 3e-3 */
   int32_t max_outer;   /* outer FDPF iteration cap; 50 */
   int32_t max_inner;   /* PCG iteration cap per solve; 500 */
   int32_t precision;   /* GPCG_PLAIN_FP64 / _BATCHED_FP32 / _BATCHED_FP64 */

@@ -19,7 +19,7 @@ struct FdpfParams {
   const double *th0 = nullptr, *V0 = nullptr;  // warm start (bus order)
   const double *c0 = nullptr, *s0 = nullptr;   // cos, sin of th0
   int flat_start = 0;
-  double tol = 1e-4, inner_rtol = 1e-5;
+  double tol = 1e-4, inner_rtol = 3e-3;
   int max_outer = 50, max_inner = 500, precond = PREC_EXACT;
   int32_t* tile_counter = nullptr;     // scenario queue head
   const int32_t* order = nullptr;      // scenarios in processing order (null: 0..S-1)
