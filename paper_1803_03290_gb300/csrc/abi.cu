@@ -171,6 +171,7 @@ struct gpcg_ctx {
   int n_bridges = 0;
   double pv_gen_total = 0.0;
   IslandPlan isl;              // per-grid islanding data (device)
+  double *r0P = nullptr, *r0Q = nullptr;  // base-case mismatch per bus (after the base solve)
   double* d_prefP = nullptr;   // [n + 1] prefix sums of a caller's injections
   int n_adj_slots = 0, n_adj_over = 0;
   std::vector<int32_t> deg;
@@ -728,6 +729,8 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
   AL(c->s0, n);
   AL(c->d_counter, 1);
   AL(c->d_err, 1);
+  AL(c->r0P, n);
+  AL(c->r0Q, n);
   for (auto& e : c->ev)
     if ((ce = cudaEventCreate(&e)) != cudaSuccess) return fail_cuda(ce, "event");
   AL(c->phase, 8);
@@ -887,6 +890,10 @@ static FdpfParams base_params(gpcg_ctx* c) {
   P.max_outer = c->opt.max_outer;
   P.max_inner = c->opt.max_inner;
   P.precond = c->opt.precond;
+  if (c->base_ok) {  // warm starts from the base case
+    P.r0P = c->r0P;
+    P.r0Q = c->r0Q;
+  }
   return P;
 }
 
@@ -908,6 +915,7 @@ extern "C" gpcg_status gpcg_base_solve(gpcg_ctx* c, double* theta, double* vm, d
   P.n_tiles = 1;
   P.sc = ScenInfo{c->d_outages, c->d_lo, c->d_cnt, c->d_coef, c->d_nogen};
   P.flat_start = 1;
+  P.r0P = P.r0Q = nullptr;
   P.tol = c->opt.base_tol;
   P.max_outer = std::max(c->opt.max_outer, 100);
   P.out_theta = c->th0;
@@ -935,6 +943,7 @@ extern "C" gpcg_status gpcg_base_solve(gpcg_ctx* c, double* theta, double* vm, d
                 "base case did not converge (status %d after %d outer iterations)", hs, hit[0]);
   }
   CUDA_TRY(launch_base_trig(0, c->n, c->th0, c->c0, c->s0));
+  CUDA_TRY(launch_base_residual(0, c->G, c->V0, c->c0, c->s0, c->r0P, c->r0Q));
   CUDA_TRY(cudaDeviceSynchronize());
   c->base_flow.resize(c->m);
   CUDA_TRY(cudaMemcpy(c->base_flow.data(), c->flow0, (size_t)c->m * 8, cudaMemcpyDeviceToHost));
@@ -1633,6 +1642,8 @@ bool ctx_view(const gpcg_ctx* c, CtxView* v) {
   v->u_t = c->u_t;
   v->u_pre = c->u_pre;
   v->isl = c->isl;
+  v->r0P = c->r0P;
+  v->r0Q = c->r0Q;
   v->u_bus_type = c->u_bus_type;
   v->u_P_sched = c->u_P_sched;
   v->u_P_gen = c->u_P_gen;

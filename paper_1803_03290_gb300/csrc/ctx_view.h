@@ -18,6 +18,7 @@ struct CtxView {
   const int8_t* u_bus_type = nullptr;
   const double *u_P_sched = nullptr, *u_P_gen = nullptr;
   IslandPlan isl;
+  const double *r0P = nullptr, *r0Q = nullptr;
   bool base_ok = false;
 };
 

@@ -83,8 +83,17 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
       const bool on1 = L.active[l1] && !in_island(pr, L.lo[l1], L.cnt[l1]);
       if (!(on0 || on1)) continue;
       const int br0 = L.l[l0], br1 = L.l[l1];
+      // a lane's first P half-step away from the ends of its outaged branch:
+      // the base-case mismatch holds (the state is the base case there)
+      bool w0 = false, w1 = false;
+      if (WITH_P && P.r0P) {
+        w0 = on0 && L.outer[l0] == 0 && i != L.fb[l0] && i != L.tb[l0];
+        w1 = on1 && L.outer[l1] == 0 && i != L.fb[l1] && i != L.tb[l1];
+      }
+      const bool n0 = on0 && !w0, n1 = on1 && !w1;  // lanes that sum the neighbours
       // -sum over the neighbours of Y_ij V_j, both lanes of the pair
       double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
+      if (n0 || n1) {
 #pragma unroll
       for (int a0 = 0; a0 < KG; a0 += MIS_GROUP) {
         double2 u0[MIS_GROUP], u1[MIS_GROUP];
@@ -103,11 +112,11 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
 #pragma unroll
         for (int a = 0; a < MIS_GROUP; ++a)
           if (a0 + a < deg) {
-            if (on0 && bb[a] != br0) {
+            if (n0 && bb[a] != br0) {
               re0 = fma(-gv[a], u0[a].x, fma(bv[a], u0[a].y, re0));
               im0 = fma(-gv[a], u0[a].y, fma(-bv[a], u0[a].x, im0));
             }
-            if (on1 && bb[a] != br1) {
+            if (n1 && bb[a] != br1) {
               re1 = fma(-gv[a], u1[a].x, fma(bv[a], u1[a].y, re1));
               im1 = fma(-gv[a], u1[a].y, fma(-bv[a], u1[a].x, im1));
             }
@@ -119,18 +128,19 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
         const double gw = __ldg(G.adj_og + e), bw = __ldg(G.adj_ob + e);
         const double2* q2 = reinterpret_cast<const double2*>(EF + ef_at<T>(jn, l0));
         const double2 v0 = q2[0], v1 = q2[1];
-        if (on0 && b_ != br0) {
+        if (n0 && b_ != br0) {
           re0 = fma(-gw, v0.x, fma(bw, v0.y, re0));
           im0 = fma(-gw, v0.y, fma(-bw, v0.x, im0));
         }
-        if (on1 && b_ != br1) {
+        if (n1 && b_ != br1) {
           re1 = fma(-gw, v1.x, fma(bw, v1.y, re1));
           im1 = fma(-gw, v1.y, fma(-bw, v1.x, im1));
         }
       }
+      }
       // own voltage, the diagonal term and the mismatch of each lane
       const double2* own = reinterpret_cast<const double2*>(EF + ef_at<T>(i, l0));
-      const double2 w0 = own[0], w1 = own[1];
+      const double2 ev0 = own[0], ev1 = own[1];
       const Pair<double> vi = ld2(V + (size_t)i * T + l0);
       const int bt = G.bus_type[i];
       const double Gii = __ldg(G.Gii + i), Bii = __ldg(G.Bii + i), qs = __ldg(G.Q_sched + i);
@@ -143,7 +153,14 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
       for (int j = 0; j < 2; ++j) {
         if (!(j ? on1 : on0)) continue;
         const int ln = j ? l1 : l0;
-        const double ei = j ? w1.x : w0.x, fi = j ? w1.y : w0.y;
+        if (j ? w1 : w0) {
+          const double dP = fma(L.coef[ln], pg, __ldg(P.r0P + i));
+          upd_max_bits(errP.v[jp + j], dP);
+          if (bt == 0) upd_max_bits(errQ.v[jp + j], __ldg(P.r0Q + i));
+          out.v[jp + j] = (VT)dP / (VT)(j ? vi.b : vi.a);
+          continue;
+        }
+        const double ei = j ? ev1.x : ev0.x, fi = j ? ev1.y : ev0.y;
         double Gd = Gii, Bd = Bii;
         if (i == L.fb[ln] || i == L.tb[ln]) {  // the outaged branch's share
           Gd -= L.gl[ln];
@@ -596,6 +613,42 @@ __global__ void __launch_bounds__(NTHREADS) apply_kernel(DevMatT<VT> M, int op, 
     }
     __syncthreads();
   }
+}
+
+// Mismatch of the intact grid at the base-case state (eqs. (1)-(3)), per bus:
+// r0P = P_sched - P(V0), r0Q = Q_sched - Q(V0), summed like mismatch_pass.
+// At a scenario's warm start only the two ends of the outaged branch see a
+// different network, so its first P half-step takes every other bus's
+// mismatch from here (plus the re-dispatch).
+__global__ void base_residual_kernel(DevGrid G, const double* __restrict__ V0,
+                                     const double* __restrict__ c0,
+                                     const double* __restrict__ s0, double* r0P, double* r0Q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= G.n) return;
+  const double ei = V0[i] * c0[i], fi = V0[i] * s0[i];
+  double re = fma(G.Gii[i], ei, -G.Bii[i] * fi), im = fma(G.Gii[i], fi, G.Bii[i] * ei);
+  const int deg = G.adj_deg[i];
+  for (int a = 0; a < deg; ++a) {
+    const int j = G.adj_nbr[(size_t)i * KG + a];
+    const double gv = G.adj_g[(size_t)i * KG + a], bv = G.adj_b[(size_t)i * KG + a];
+    const double ej = V0[j] * c0[j], fj = V0[j] * s0[j];
+    re = fma(-gv, ej, fma(bv, fj, re));
+    im = fma(-gv, fj, fma(-bv, ej, im));
+  }
+  for (int e = G.adj_optr[i]; e < G.adj_optr[i + 1]; ++e) {
+    const int j = G.adj_onbr[e];
+    const double ej = V0[j] * c0[j], fj = V0[j] * s0[j];
+    re = fma(-G.adj_og[e], ej, fma(G.adj_ob[e], fj, re));
+    im = fma(-G.adj_og[e], fj, fma(-G.adj_ob[e], ej, im));
+  }
+  r0P[i] = fma(-ei, re, fma(-fi, im, G.P_sched[i]));
+  r0Q[i] = fma(-fi, re, fma(ei, im, G.Q_sched[i]));
+}
+
+cudaError_t launch_base_residual(cudaStream_t st, const DevGrid& G, const double* V0,
+                                 const double* c0, const double* s0, double* r0P, double* r0Q) {
+  base_residual_kernel<<<(G.n + 255) / 256, 256, 0, st>>>(G, V0, c0, s0, r0P, r0Q);
+  return cudaGetLastError();
 }
 
 // Base-case cos/sin per bus, shared by every scenario's warm start.

@@ -18,6 +18,7 @@ struct FdpfParams {
   ScenInfo sc;
   const double *th0 = nullptr, *V0 = nullptr;  // warm start (bus order)
   const double *c0 = nullptr, *s0 = nullptr;   // cos, sin of th0
+  const double *r0P = nullptr, *r0Q = nullptr; // base-case mismatch per bus (null: not used)
   int flat_start = 0;
   double tol = 1e-4, inner_rtol = 3e-3;
   int max_outer = 50, max_inner = 500, precond = PREC_EXACT;
@@ -47,6 +48,8 @@ cudaError_t launch_apply(cudaStream_t st, int grid, const DevMatT<VT>& M, int op
                          const int32_t* outages, const int32_t* f, const int32_t* t,
                          const double* X, double* Y, VT* wbuf, size_t vstride, int precond);
 cudaError_t launch_base_trig(cudaStream_t st, int n, const double* th, double* c, double* s);
+cudaError_t launch_base_residual(cudaStream_t st, const DevGrid& G, const double* V0,
+                                 const double* c0, const double* s0, double* r0P, double* r0Q);
 
 // adjoint.cu
 struct AdjParamsView {

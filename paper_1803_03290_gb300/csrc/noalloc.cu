@@ -139,6 +139,8 @@ extern "C" gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx* ctx, const int32_t* outa
   P.G = c.G;
   P.mis_order = c.mis_order;
   P.misq_order = c.misq_order;
+  P.r0P = c.r0P;
+  P.r0Q = c.r0Q;
   P.tol = c.opt.tol;
   P.inner_rtol = c.opt.inner_rtol;
   P.max_outer = c.opt.max_outer;
