@@ -214,7 +214,8 @@ __device__ __forceinline__ void rotate(double th_new, double d, double& c, doubl
 // rows, then refresh the rectangular voltages; lanes two at a time.
 template <int T, typename VT, bool IS_P>
 __device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>& L,
-                                             const VT* __restrict__ x, double* th, double* V,
+                                             const VT* __restrict__ x,
+                                             const VT* __restrict__ p, double* th, double* V,
                                              double* C, double* Sn, double* EF) {
   constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
@@ -232,7 +233,14 @@ __device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>&
       const bool on1 = L.active[l1] && !in_island(pr, L.lo[l1], L.cnt[l1]);
       if (!on0 && !on1) continue;
       const size_t o = (size_t)i * T + l0;
-      const Pair<VT> dx = ld2(x + (size_t)k * T + l0);
+      Pair<VT> dx = ld2(x + (size_t)k * T + l0);
+      // the inner solve's deferred last step, x += alpha p
+      const VT xa0 = (VT)L.xalpha[l0], xa1 = (VT)L.xalpha[l1];
+      if (xa0 != (VT)0 || xa1 != (VT)0) {
+        const Pair<VT> pv = ld2(p + (size_t)k * T + l0);
+        dx.a = fma(xa0, pv.a, dx.a);  // as the solve's own step would take it
+        dx.b = fma(xa1, pv.b, dx.b);
+      }
       const double d0 = on0 ? (double)dx.a : 0.0, d1 = on1 ? (double)dx.b : 0.0;
       Pair<double> c = ld2(C + o), s = ld2(Sn + o), v = ld2(V + o);
       if (IS_P) {
@@ -529,9 +537,9 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     const bool more = any_lane<T>(L, L.active);
     GPCG_PHASE(1);
     if (!more) continue;
-    pcg_solve<T, VT>(P, MP, L, x, r, p, q, z, L.raP, L.rbP, L.wP, L.inP);
+    pcg_solve<T, VT, true>(P, MP, L, x, r, p, q, z, L.raP, L.rbP, L.wP, L.inP);
     GPCG_PHASE(2);
-    update_pass<T, VT, true>(MP, L, x, th, V, C, Sn, EF);
+    update_pass<T, VT, true>(MP, L, x, p, th, V, C, Sn, EF);
     __syncthreads();
     GPCG_PHASE(3);
     // Q half-step
@@ -539,9 +547,9 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     mismatch_pass<T, VT, false>(P, MP, MQ, L, EF, V, r, d0, d1);
     __syncthreads();
     GPCG_PHASE(4);
-    pcg_solve<T, VT>(P, MQ, L, x, r, p, q, z, L.raQ, L.rbQ, L.wQ, L.inQ);
+    pcg_solve<T, VT, true>(P, MQ, L, x, r, p, q, z, L.raQ, L.rbQ, L.wQ, L.inQ);
     GPCG_PHASE(5);
-    update_pass<T, VT, false>(MQ, L, x, th, V, C, Sn, EF);
+    update_pass<T, VT, false>(MQ, L, x, p, th, V, C, Sn, EF);
     if (g.rs == 0)
 #pragma unroll
       for (int j = 0; j < LP; ++j)

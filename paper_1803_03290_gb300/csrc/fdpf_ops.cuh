@@ -163,8 +163,8 @@ struct Geo {
 };
 
 // ------------------------------------------------------------ lane state
-constexpr int NRED_SITES = 8;  // reduction sites with a buffer of their own
-enum RedSite { RS_BB = 0, RS_RZ0, RS_PQ, RS_RR, RS_RZ, RS_ERRP, RS_ERRQ, RS_LOAD };
+constexpr int NRED_SITES = 10;  // reduction sites with a buffer of their own
+enum RedSite { RS_BB = 0, RS_RZ0, RS_PQ, RS_RR, RS_RZ, RS_ERRP, RS_ERRQ, RS_LOAD, RS_RQ, RS_QQ };
 
 template <int T>
 struct LaneState {
@@ -175,6 +175,7 @@ struct LaneState {
   double err[T], best[T];
   unsigned long long tphase[8];
   int done[T], fresh[T];
+  double xalpha[T];          // a deferred last step x += alpha p of the inner solve
   double red[NTHREADS * 2];  // lane_reduce (two lanes per thread)
   // one small buffer per reduction site (see lane_sum): [site][warp][lane]
   double red2[NRED_SITES * (NTHREADS / 32) * T];
@@ -275,6 +276,49 @@ __device__ __forceinline__ Vec<X, N> lane_sum(LaneState<T>& L, Vec<X, N> v) {
   return s;
 }
 
+// Three sums at three sites with one barrier (see lane_sum).
+template <int T, int S1, int S2, int S3, typename X, int N>
+__device__ __forceinline__ void lane_sum3(LaneState<T>& L, Vec<X, N>& a, Vec<X, N>& b,
+                                          Vec<X, N>& c) {
+  static_assert(N == Geo<T>::LP, "a thread's lanes");
+  const Geo<T> g;
+  constexpr int TPR = Geo<T>::TPR, NW = NTHREADS / 32;
+#pragma unroll
+  for (int off = 16; off >= TPR; off >>= 1)
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      a.v[j] += __shfl_xor_sync(0xffffffffu, a.v[j], off);
+      b.v[j] += __shfl_xor_sync(0xffffffffu, b.v[j], off);
+      c.v[j] += __shfl_xor_sync(0xffffffffu, c.v[j], off);
+    }
+  X* ba = reinterpret_cast<X*>(L.red2 + S1 * NW * T);
+  X* bb = reinterpret_cast<X*>(L.red2 + S2 * NW * T);
+  X* bc = reinterpret_cast<X*>(L.red2 + S3 * NW * T);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) < TPR)
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      ba[w * T + g.lane + j] = a.v[j];
+      bb[w * T + g.lane + j] = b.v[j];
+      bc[w * T + g.lane + j] = c.v[j];
+    }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    a.v[j] = ba[g.lane + j];
+    b.v[j] = bb[g.lane + j];
+    c.v[j] = bc[g.lane + j];
+  }
+#pragma unroll
+  for (int k = 1; k < NW; ++k)
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      a.v[j] += ba[k * T + g.lane + j];
+      b.v[j] += bb[k * T + g.lane + j];
+      c.v[j] += bc[k * T + g.lane + j];
+    }
+}
+
 // The same for running maxima held as abs_bits patterns.
 template <int T, int SITE, int N>
 __device__ __forceinline__ Vec<unsigned long long, N> lane_max_bits(
@@ -347,7 +391,8 @@ template <int T, typename VT, bool DIRECTION>
 __device__ GPCG_LOOP_INLINE Vec<VT, Geo<T>::LP> spmv_pass(
     const DevMatT<VT>& M, const VT* __restrict__ v_, VT* __restrict__ p, VT* __restrict__ q,
     const Stamp<T, VT>& S, unsigned long long filt, Vec<VT, Geo<T>::LP> be, bool first,
-    const LaneState<T>* isl) {
+    const LaneState<T>* isl, const VT* __restrict__ r = nullptr,
+    Vec<VT, Geo<T>::LP>* rq = nullptr, Vec<VT, Geo<T>::LP>* qq = nullptr) {
   constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
   constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
@@ -436,6 +481,14 @@ __device__ GPCG_LOOP_INLINE Vec<VT, Geo<T>::LP> spmv_pass(
         stv<LP>(q + o, qn);
 #pragma unroll
         for (int j = 0; j < LP; ++j) pq.v[j] += pn.v[j] * qn.v[j];
+        if (r) {  // r.q and q.q: the residual after the step, before taking it
+          const Vec<VT, LP> ro = ldv<LP>(r + o);
+#pragma unroll
+          for (int j = 0; j < LP; ++j) {
+            rq->v[j] += ro.v[j] * qn.v[j];
+            qq->v[j] += qn.v[j] * qn.v[j];
+          }
+        }
       } else {
         stv<LP>(q + o, a);
 #pragma unroll
@@ -459,7 +512,7 @@ __device__ __forceinline__ Vec<VT, Geo<T>::LP> pcg_update_row(
     Vec<VT, LP> xi = ldv<LP>(x + o);
 #pragma unroll
     for (int j = 0; j < LP; ++j) {
-      xi.v[j] += al.v[j] * pi.v[j];
+      xi.v[j] = fma(al.v[j], pi.v[j], xi.v[j]);  // as the deferred step takes it
       rv.v[j] -= al.v[j] * qi.v[j];
     }
     stv<LP>(x + o, xi);
@@ -774,6 +827,7 @@ template <int T, typename VT>
 struct PcgLanes {
   VT rz[2][T];
   VT bb[T], rrmin[T];
+  VT rrl[T];     // r.r of the last forward pass (written after r.r)
   int stall[T];
   int pdone[T];  // stopped at the convergence test (written after r.r)
   int brk[T];    // p.Bp breakdown (written after p.Bp)
@@ -785,7 +839,13 @@ struct PcgLanes {
 // count to iters[lane].  Every thread computes alpha and beta of its own
 // lanes from the reduced sums, so an iteration has five barriers besides
 // the substitution levels'.
-template <int T, typename VT>
+//
+// DEFER: when, at some iteration, the residual after the step --
+// ||r - alpha q||^2 = r.r - 2 alpha r.q + alpha^2 q.q, from dot products the
+// SpMV pass accumulates -- meets the tolerance for every running lane, the
+// solve ends there without the forward pass that would apply the step: the
+// step is left in L.xalpha for the caller to apply as x + xalpha p.
+template <int T, typename VT, bool DEFER = false>
 __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT>& M, LaneState<T>& L, VT* x,
                           VT* r, VT* p, VT* q, VT* z, const int* ra_, const int* rb_,
                           const double* w_, int* iters) {
@@ -804,6 +864,7 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
     St.ra[tid] = on ? ra_[tid] : -1;
     St.rb[tid] = on ? rb_[tid] : -1;
     St.w[tid] = (VT)w_[tid];
+    L.xalpha[tid] = 0.0;
   }
   if (g.rs == 0) {
     stv<LP>(p + (size_t)M.n * T + g.lane, vzero<VT, LP>());
@@ -832,6 +893,7 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
       const int ln = g.lane + j;
       const VT b_ = bb.v[j], r_ = rz0.v[j];
       S.bb[ln] = b_;
+      S.rrl[ln] = b_;  // r = b while x = 0
       S.rz[0][ln] = r_;
       S.rrmin[ln] = b_;
       S.stall[ln] = 0;
@@ -850,9 +912,15 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
     for (int k = 0; k < T; ++k) any |= !(S.pdone[k] | S.stop[k]);
     if (!any) break;
     // new direction p = mask(z) + beta p and q = B_s p in one pass
-    const Vec<VT, LP> pqp = spmv_pass<T, VT, true>(M, z, p, q, St, filt, be, it == 0, isl);
-    const Vec<VT, LP> pq = lane_sum<T, RS_PQ>(L, pqp);
-    int bk = 0;  // lanes whose p.Bp broke down: keep the current iterate
+    Vec<VT, LP> rqp = vzero<VT, LP>(), qqp = vzero<VT, LP>();
+    const Vec<VT, LP> pqp = spmv_pass<T, VT, true>(
+        M, z, p, q, St, filt, be, it == 0, isl, (DEFER && Geo<T>::TPR == 1) ? r : nullptr, &rqp,
+        &qqp);
+    Vec<VT, LP> pq = pqp, rq = rqp, qq = qqp;
+    if constexpr (DEFER && Geo<T>::TPR == 1) lane_sum3<T, RS_PQ, RS_RQ, RS_QQ>(L, pq, rq, qq);
+    else pq = lane_sum<T, RS_PQ>(L, pqp);
+    int bk = 0;   // lanes whose p.Bp broke down: keep the current iterate
+    int pok = 0;  // lanes whose predicted residual after the step converged
 #pragma unroll
     for (int j = 0; j < LP; ++j) {
       const int ln = g.lane + j;
@@ -860,6 +928,36 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
       if (!(S.pdone[ln] | S.stop[ln])) {
         if (pq.v[j] > (VT)0 && isfinite(pq.v[j])) al.v[j] = S.rz[par][ln] / pq.v[j];
         else bk |= 1 << j;
+      }
+    }
+    if constexpr (DEFER && Geo<T>::TPR == 1) {
+      // a thread holds every lane of the tile: when each running lane meets
+      // the tolerance with this step, every thread sees it, and the solve
+      // ends here with the step deferred to the caller
+      // A lane converges on the predicted residual whether or not the
+      // step is deferred, so that its iterates do not depend on the
+      // scenarios it shares a tile with.
+      bool fin = true, run = false;
+#pragma unroll
+      for (int j = 0; j < LP; ++j) {
+        const int ln = g.lane + j;
+        if (S.pdone[ln] | S.stop[ln]) continue;
+        run = true;
+        if ((bk >> j) & 1) { fin = false; continue; }
+        const VT pred = S.rrl[ln] - al.v[j] * ((VT)2 * rq.v[j] - al.v[j] * qq.v[j]);
+        if (pred <= tol2 * S.bb[ln]) pok |= 1 << j;
+        else fin = false;
+      }
+      if (run && fin) {
+        if (g.rs == 0)
+#pragma unroll
+          for (int j = 0; j < LP; ++j) {
+            const int ln = g.lane + j;
+            if (S.pdone[ln] | S.stop[ln]) continue;
+            L.xalpha[ln] = (double)al.v[j];
+            iters[ln] += 1;
+          }
+        break;  // the closing barrier publishes xalpha and the counts
       }
     }
     if (g.rs == 0)
@@ -881,11 +979,13 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
         if (S.pdone[ln] | S.stop[ln]) continue;
         if (S.brk[ln]) { S.pdone[ln] = 1; continue; }
         iters[ln] += 1;
+        S.rrl[ln] = v;
         // converged; or stagnated at the rounding floor of VT (no 0.1 % gain
         // in STALL_ITERS iterations); or growing away from the best residual
         if (v < (VT)0.999 * S.rrmin[ln]) { S.rrmin[ln] = v; S.stall[ln] = 0; }
         else S.stall[ln] += 1;
-        if (v <= tol2 * S.bb[ln] || !isfinite(v) || S.stall[ln] >= STALL_ITERS ||
+        if (((pok >> j) & 1) || v <= tol2 * S.bb[ln] || !isfinite(v) ||
+            S.stall[ln] >= STALL_ITERS ||
             v > (VT)1e4 * S.rrmin[ln])
           S.pdone[ln] = 1;
       }
