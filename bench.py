@@ -106,7 +106,7 @@ def algorithmic_bytes(info, iters, w, n_bus, n_branch):
 # (dram__bytes_read.sum + dram__bytes_write.sum, mean of two ncu captures of
 # the timed screens; see profiles/launches_bench_grid10k.md), valid only for
 # the kernel sources with this digest.
-KERNEL_TRAFFIC = {"sha256": "25727c4e0ef94c2a42461c602f00fed240e099b5145f7d325ff5fd837c2af146", "bytes": 313.35e9}
+KERNEL_TRAFFIC = {"sha256": "3b39ea58ad015cd2e2e4464289598edd7e82270beae55dd97c591f9f76878f7b", "bytes": 278.34e9}
 KERNEL_SOURCES = ("fdpf.cu", "fdpf_ops.cuh", "fdpf.h", "common.cuh")
 
 
