@@ -157,7 +157,7 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
           const double dP = fma(L.coef[ln], pg, __ldg(P.r0P + i));
           upd_max_bits(errP.v[jp + j], dP);
           if (bt == 0) upd_max_bits(errQ.v[jp + j], __ldg(P.r0Q + i));
-          out.v[jp + j] = (VT)dP / (VT)(j ? vi.b : vi.a);
+          out.v[jp + j] = to_vt<VT>(dP) / to_vt<VT>(j ? vi.b : vi.a);
           continue;
         }
         const double ei = j ? ev1.x : ev0.x, fi = j ? ev1.y : ev0.y;
@@ -175,10 +175,10 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
           const double dP = fma(-ei, re, fma(-fi, im, fma(L.coef[ln], pg, Ps)));
           upd_max_bits(errP.v[jp + j], dP);
           if (bt == 0) upd_max_bits(errQ.v[jp + j], fma(-fi, re, fma(ei, im, qs)));
-          res = (VT)dP / (VT)(j ? vi.b : vi.a);
+          res = to_vt<VT>(dP) / to_vt<VT>(j ? vi.b : vi.a);
         } else {
           const double dQ = fma(-fi, re, fma(ei, im, qs));
-          res = (VT)dQ / (VT)(j ? vi.b : vi.a);
+          res = to_vt<VT>(dQ) / to_vt<VT>(j ? vi.b : vi.a);
         }
         out.v[jp + j] = res;
       }
@@ -196,15 +196,16 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
 // error, 6e-8 of |d|, vanishes as the iteration converges (the outer FDPF
 // loop sees the state through e + jf and corrects any drift).  d itself is
 // the FP32 solution of the inner solve.  Larger steps recompute the angle.
-__device__ __forceinline__ void rotate(double th_new, double d, double& c, double& s) {
-  if (fabs(d) <= 0.05) {
-    const float df = (float)d, d2 = df * df;
+template <typename VT>
+__device__ __forceinline__ void rotate(double th_new, VT d, double& c, double& s) {
+  if (fabs(d) <= (VT)0.05) {
+    const float df = to_f32(d), d2 = df * df;
     const float omc = d2 * (0.5f - d2 * (1.0f / 24.0f - d2 * (1.0f / 720.0f)));
     const float sd = df * (1.0f - d2 * (1.0f / 6.0f - d2 * (1.0f / 120.0f)));
-    const float cf = (float)c, sf = (float)s;
+    const float cf = cvt_f32(c), sf = cvt_f32(s);
     const float dc = fmaf(cf, omc, sf * sd), ds = fmaf(sf, omc, -cf * sd);
-    c -= (double)dc;
-    s -= (double)ds;
+    c -= cvt_f64(dc);
+    s -= cvt_f64(ds);
   } else {
     sincos(th_new, &s, &c);
   }
@@ -241,14 +242,16 @@ __device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>&
         dx.a = fma(xa0, pv.a, dx.a);  // as the solve's own step would take it
         dx.b = fma(xa1, pv.b, dx.b);
       }
-      const double d0 = on0 ? (double)dx.a : 0.0, d1 = on1 ? (double)dx.b : 0.0;
+      if (!on0) dx.a = (VT)0;
+      if (!on1) dx.b = (VT)0;
+      const double d0 = to_f64(dx.a), d1 = to_f64(dx.b);
       Pair<double> c = ld2(C + o), s = ld2(Sn + o), v = ld2(V + o);
       if (IS_P) {
         Pair<double> t = ld2(th + o);
         t.a += d0;
         t.b += d1;
-        if (on0) rotate(t.a, d0, c.a, s.a);
-        if (on1) rotate(t.b, d1, c.b, s.b);
+        if (on0) rotate(t.a, dx.a, c.a, s.a);
+        if (on1) rotate(t.b, dx.b, c.b, s.b);
         st2(th + o, t);
         st2(C + o, c);
         st2(Sn + o, s);

@@ -45,6 +45,43 @@ constexpr int STALL_ITERS = 50;
 template <typename X> struct Pair { X a, b; };
 template <typename X, int N> struct Vec { X v[N]; };
 
+// FP64 <-> FP32 conversions from the IEEE-754 binary64 / binary32 layouts,
+// in integer operations: GB300 issues the conversion instructions on its
+// FP64 pipe (2 operations per SM per cycle), integer operations run at the
+// FP32 rate.  Both are exact or round to nearest (ties away from zero) for
+// normal numbers; magnitudes below the FP32 normal range become a signed
+// zero (the mixed-precision path never needs them: they are far below the
+// FP32 rounding of any quantity they are added to); infinities and NaNs
+// stay non-finite.
+__device__ __forceinline__ float cvt_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - (1023 - 127);
+  // 20 fraction bits from the high word, 3 from the low one, and the first
+  // dropped bit added: a carry out of the fraction lands in the exponent
+  const unsigned r = ((unsigned)e << 23) + (((hi & 0xfffffu) << 3) | (lo >> 29)) +
+                     ((lo >> 28) & 1u);
+  const unsigned out = e <= 0 ? sign : (e >= 255 || r >= 0x7f800000u) ? (sign | 0x7f800000u)
+                                                                      : (sign | r);
+  return __uint_as_float(out);
+}
+__device__ __forceinline__ double cvt_f64(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned sign = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+  const unsigned eo = e == 255u ? 0x7ffu : e + (1023u - 127u);
+  const unsigned hi = e ? (sign | (eo << 20) | (m >> 3)) : sign;
+  const unsigned lo = e ? (m << 29) : 0u;
+  return __hiloint2double((int)hi, (int)lo);
+}
+template <typename VT> __device__ __forceinline__ VT to_vt(double x);
+template <> __device__ __forceinline__ float to_vt<float>(double x) { return cvt_f32(x); }
+template <> __device__ __forceinline__ double to_vt<double>(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return cvt_f64(x); }
+__device__ __forceinline__ float to_f32(double x) { return cvt_f32(x); }
+__device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+
 __device__ __forceinline__ Pair<float> ld2(const float* p) {
   const float2 v = *reinterpret_cast<const float2*>(p);
   return {v.x, v.y};
