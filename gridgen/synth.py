@@ -55,6 +55,8 @@ class Grid:
     x: np.ndarray         # f64 [m]
     b_sh: np.ndarray      # f64 [m]    total line charging
     rating: np.ndarray    # f64 [m]
+    tap: Optional[np.ndarray] = None  # f64 [m] off-nominal turns ratio at the from end
+                                      # (transformers); None: every branch is a line
     xy: Optional[np.ndarray] = None  # f64 [n, 2] bus coordinates (plotting only)
     meta: dict = dataclasses.field(default_factory=dict)
 
@@ -118,8 +120,12 @@ def make_grid(n_bus: int, n_branch: int, seed: int, spur_frac: float = 0.0,
               pv_frac: float = 0.2, load_scale: float = 1.0,
               gen_share: float = 1.0, knn: int = 6,
               local_gen: bool = True, v_pv: float = 1.02,
-              v_slack: float = 1.04) -> Grid:
-    """Draw a connected synthetic grid with ``n_bus`` buses, ``n_branch`` branches."""
+              v_slack: float = 1.04, xfmr_frac: float = 0.0) -> Grid:
+    """Draw a connected synthetic grid with ``n_bus`` buses, ``n_branch`` branches.
+
+    ``xfmr_frac`` > 0 makes that fraction of the branches transformers with
+    an off-nominal turns ratio U[0.95, 1.05] at the from end; those draws come
+    after every other one, so the rest of the grid is the same as without."""
     rng = np.random.default_rng(seed)
     n_spur = int(round(spur_frac * n_bus))
     n_core = n_bus - n_spur
@@ -196,10 +202,15 @@ def make_grid(n_bus: int, n_branch: int, seed: int, spur_frac: float = 0.0,
     V_set = np.ones(n_bus)
     V_set[bus_type == PV] = v_pv
     V_set[slack] = v_slack
+    tap = None
+    if xfmr_frac > 0.0:
+        tap = np.ones(m)
+        k = rng.choice(m, size=max(1, int(round(xfmr_frac * m))), replace=False)
+        tap[k] = rng.uniform(0.95, 1.05, size=k.shape[0])
     g = Grid(bus_type=bus_type, P_sched=P_sched, Q_sched=Q_sched, P_gen=Pg,
-             V_set=V_set, f=f, t=t, r=r, x=x, b_sh=b_sh, rating=rating, xy=xy,
+             V_set=V_set, f=f, t=t, r=r, x=x, b_sh=b_sh, rating=rating, tap=tap, xy=xy,
              meta=dict(n_bus=n_bus, n_branch=m, seed=seed, spur_frac=spur_frac,
-                       load_scale=load_scale, gen_share=gen_share))
+                       load_scale=load_scale, gen_share=gen_share, xfmr_frac=xfmr_frac))
     return g
 
 

@@ -2,17 +2,24 @@
 
 Test infrastructure (see the package docstring).
 
-Network model (pi-model branch l = (i, j), no taps): series admittance
+Network model (pi-model branch l = (i, j) from i to j): series admittance
 y = 1/(r + jx) = g + j b_y with g = r/(r^2+x^2), b_y = -x/(r^2+x^2); half of
-the total charging b_sh sits at each end.  The bus admittance matrix
-Y = G + jB has Y_ij = -y and Y_ii = sum (y + j b_sh/2); G_ij and B_ij are the
-quantities of eqs. (1)-(3).
+the total charging b_sh sits at each end.  A transformer branch carries an
+off-nominal turns ratio tau (an edge attribute of the paper's graph model,
+Sec. II.B): an ideal tau:1 transformer at the from end in series with the
+pi-model, no phase shift.  Its from-end voltage reaches the pi-model as
+V_i / tau, so with c = 1/tau (c = 1 for a line)
+    Y_ii += c^2 (y + j b_sh/2),  Y_jj += y + j b_sh/2,  Y_ij = Y_ji = -c y.
+G_ij and B_ij of eqs. (1)-(3) are the real and imaginary parts of Y.
 
 Fast-decoupled matrices (eqs. (4)-(5); the paper names no variant, the XB
 form is used): B' is the Laplacian of the in-service branches weighted by
-1/x, B'' the Laplacian weighted by x/(r^2+x^2) (charging excluded).  B' is
-restricted to the non-slack buses of the main island, B'' to its PQ buses;
-both are grounded Laplacians, hence symmetric positive definite.
+1/x (turns ratios and charging left out); B'' is minus the imaginary part
+of the bus admittance matrix of the series branches with their turns ratios,
+charging left out: every branch adds w v v^T with w = x/(r^2+x^2) and
+v = c e_i - e_j.  B' is restricted to the non-slack buses of the main island,
+B'' to its PQ buses; both are sums of positive semi-definite branch terms
+grounded at the removed buses, hence symmetric positive definite.
 
 FDPF (eqs. (4)-(5), Sec. III.B): starting from a given state, repeat
   evaluate dP, dQ; stop when max|dP| (PV and PQ buses) and max|dQ| (PQ buses)
@@ -51,15 +58,21 @@ def series_admittance(r: np.ndarray, x: np.ndarray):
     return r / d, -x / d
 
 
-def ybus_entries(n_bus, f, t, r, x, b_sh, in_service):
+def tap_factor(tap, m):
+    """c = 1/tau per branch (1 for lines; ``tap`` None means no transformers)."""
+    return np.ones(m) if tap is None else 1.0 / np.asarray(tap, dtype=np.float64)
+
+
+def ybus_entries(n_bus, f, t, r, x, b_sh, in_service, tap=None):
     """Summed nonzeros (row, col, G, B) of the bus admittance matrix."""
     on = np.asarray(in_service, dtype=bool)
+    c = tap_factor(tap, len(f))[on]
     f, t, r, x, b_sh = f[on], t[on], r[on], x[on], b_sh[on]
     g, b = series_admittance(r, x)
     rows = np.concatenate([f, t, f, t])
     cols = np.concatenate([t, f, f, t])
-    Gv = np.concatenate([-g, -g, g, g])
-    Bv = np.concatenate([-b, -b, b + 0.5 * b_sh, b + 0.5 * b_sh])
+    Gv = np.concatenate([-c * g, -c * g, c * c * g, g])
+    Bv = np.concatenate([-c * b, -c * b, c * c * (b + 0.5 * b_sh), b + 0.5 * b_sh])
     # diagonal entries for every bus, so isolated buses still appear
     rows = np.concatenate([rows, np.arange(n_bus)])
     cols = np.concatenate([cols, np.arange(n_bus)])
@@ -108,9 +121,19 @@ def bprime(n_bus, f, t, x, in_service, keep):
     return laplacian(n_bus, f, t, 1.0 / x, in_service, keep)
 
 
-def bdprime(n_bus, f, t, r, x, in_service, keep):
-    """B'' (eq. (5)): branch weights x/(r^2+x^2), charging excluded."""
-    return laplacian(n_bus, f, t, x / (r * r + x * x), in_service, keep)
+def bdprime(n_bus, f, t, r, x, in_service, keep, tap=None):
+    """B'' (eq. (5)): branch terms w v v^T, w = x/(r^2+x^2), v = e_i/tau - e_j
+    (charging excluded)."""
+    on = np.asarray(in_service, dtype=bool)
+    c = tap_factor(tap, len(f))[on]
+    w = (x / (r * r + x * x))[on]
+    f, t = f[on], t[on]
+    rows = np.concatenate([f, t, f, t])
+    cols = np.concatenate([f, t, t, f])
+    vals = np.concatenate([c * c * w, w, -c * w, -c * w])
+    L = coo_matrix((vals, (rows, cols)), shape=(n_bus, n_bus)).tocsr()
+    L.sum_duplicates()
+    return L[keep][:, keep].tocsc()
 
 
 class DirectSolver:
@@ -135,16 +158,18 @@ class DirectSolver:
         return self.lu.solve(b)
 
 
-def branch_flows(f, t, r, x, in_service, theta, V):
+def branch_flows(f, t, r, x, in_service, theta, V, tap=None):
     """Active power at both ends of every branch (zero when out of service).
 
-    P_ij = V_i^2 g - V_i V_j (g cos th_ij + b_y sin th_ij), P_ji likewise.
+    P_ij = c^2 V_i^2 g - c V_i V_j (g cos th_ij + b_y sin th_ij),
+    P_ji = V_j^2 g - c V_i V_j (g cos th_ij - b_y sin th_ij),  c = 1/tau.
     """
+    c = tap_factor(tap, len(f))
     g, b = series_admittance(r, x)
     th = theta[f] - theta[t]
     Vf, Vt = V[f], V[t]
-    Pf = Vf * Vf * g - Vf * Vt * (g * np.cos(th) + b * np.sin(th))
-    Pt = Vt * Vt * g - Vf * Vt * (g * np.cos(th) - b * np.sin(th))
+    Pf = c * c * Vf * Vf * g - c * Vf * Vt * (g * np.cos(th) + b * np.sin(th))
+    Pt = Vt * Vt * g - c * Vf * Vt * (g * np.cos(th) - b * np.sin(th))
     on = np.asarray(in_service, dtype=bool)
     return np.where(on, Pf, 0.0), np.where(on, Pt, 0.0)
 
@@ -162,9 +187,10 @@ def fdpf(grid, in_service, active, P_sched, theta0, V0, tol, max_outer, growth_r
     on = np.asarray(in_service, dtype=bool)
     # a branch touching an inactive bus is not part of the main network
     on = on & active[grid.f] & active[grid.t]
-    ybus = ybus_entries(n, grid.f, grid.t, grid.r, grid.x, grid.b_sh, on)
+    tap = getattr(grid, "tap", None)
+    ybus = ybus_entries(n, grid.f, grid.t, grid.r, grid.x, grid.b_sh, on, tap)
     solP = DirectSolver(bprime(n, grid.f, grid.t, grid.x, on, pvpq))
-    solQ = DirectSolver(bdprime(n, grid.f, grid.t, grid.r, grid.x, on, pq))
+    solQ = DirectSolver(bdprime(n, grid.f, grid.t, grid.r, grid.x, on, pq, tap))
     theta = np.where(active, theta0, 0.0).astype(np.float64)
     V = np.where(active, V0, 0.0).astype(np.float64)
     Q_sched = grid.Q_sched

@@ -37,7 +37,7 @@ def solve_outage(grid, theta0, V0, l, tol, max_outer):
     active = ~isl
     theta, V, k, status, err = fdpf(grid, on, active, P, theta0, V0, tol, max_outer)
     live = on & active[grid.f] & active[grid.t]
-    Pf, Pt = branch_flows(grid.f, grid.t, grid.r, grid.x, live, theta, V)
+    Pf, Pt = branch_flows(grid.f, grid.t, grid.r, grid.x, live, theta, V, grid.tap)
     loading = np.maximum(np.abs(Pf), np.abs(Pt)) / grid.rating
     if status == STATUS_OK and no_gen:
         status = STATUS_ISLAND_NO_GEN
@@ -54,7 +54,7 @@ def scenario_mismatch(grid, l, theta, V):
     on, label, isl, P, _ = outage_setup(grid, l)
     active = ~isl
     live = on & active[grid.f] & active[grid.t]
-    yb = ybus_entries(grid.n_bus, grid.f, grid.t, grid.r, grid.x, grid.b_sh, live)
+    yb = ybus_entries(grid.n_bus, grid.f, grid.t, grid.r, grid.x, grid.b_sh, live, grid.tap)
     dP, dQ = mismatch(yb, P, grid.Q_sched, np.where(active, theta, 0.0),
                       np.where(active, V, 0.0))
     bt = grid.bus_type

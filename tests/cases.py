@@ -9,7 +9,7 @@ from gridgen import Grid
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
-def grid_from_arrays(bus_type, P, Q, Pgen, Vset, f, t, r, x, b_sh, rating=None):
+def grid_from_arrays(bus_type, P, Q, Pgen, Vset, f, t, r, x, b_sh, rating=None, tap=None):
     m = len(f)
     return Grid(bus_type=np.asarray(bus_type, dtype=np.int8),
                 P_sched=np.asarray(P, dtype=np.float64),
@@ -19,7 +19,8 @@ def grid_from_arrays(bus_type, P, Q, Pgen, Vset, f, t, r, x, b_sh, rating=None):
                 f=np.asarray(f, dtype=np.int32), t=np.asarray(t, dtype=np.int32),
                 r=np.asarray(r, dtype=np.float64), x=np.asarray(x, dtype=np.float64),
                 b_sh=np.asarray(b_sh, dtype=np.float64),
-                rating=np.ones(m) if rating is None else np.asarray(rating, dtype=np.float64))
+                rating=np.ones(m) if rating is None else np.asarray(rating, dtype=np.float64),
+                tap=None if tap is None else np.asarray(tap, dtype=np.float64))
 
 
 def load_case(name):
@@ -27,7 +28,7 @@ def load_case(name):
         d = json.load(fh)
     return grid_from_arrays(d["bus_type"], d["P_sched"], d["Q_sched"], d["P_gen"],
                             d["V_set"], d["from"], d["to"], d["r"], d["x"], d["b_sh"],
-                            d.get("rating")), d
+                            d.get("rating"), d.get("tap")), d
 
 
 def random_tree_grid(n, seed, lossless=True, all_pv=True):

@@ -85,9 +85,12 @@ def newton_solution(g, tol=1e-13):
     for e in range(g.n_branch):
         i, j = int(g.f[e]), int(g.t[e])
         y = 1.0 / (g.r[e] + 1j * g.x[e])
-        Y[i, j] -= y
-        Y[j, i] -= y
-        Y[i, i] += y + 0.5j * g.b_sh[e]
+        # an ideal transformer a:1 at the from end: the pi-model sees V_i / a
+        # and passes I / a back to bus i
+        a = 1.0 if g.tap is None else float(g.tap[e])
+        Y[i, j] -= y / a
+        Y[j, i] -= y / a
+        Y[i, i] += (y + 0.5j * g.b_sh[e]) / (a * a)
         Y[j, j] += y + 0.5j * g.b_sh[e]
     pvpq = np.flatnonzero(g.bus_type != 2)
     pq = np.flatnonzero(g.bus_type == 0)
@@ -148,6 +151,103 @@ def test_mismatch_zero_only_at_solution():
     thp[3] += 1e-3
     dP2, _ = pf.mismatch(yb, g.P_sched, g.Q_sched, thp, Vn)
     assert np.abs(dP2[1:]).max() > 1e-3
+
+
+# ------------------------------------- transformer turns ratios (Sec. II.B)
+@pytest.mark.parametrize("flip", [False, True])
+def test_two_bus_tap_closed_form(flip):
+    """The tap's side does not matter for the angle: P = V_1 V_2 sin/(tau x)."""
+    g, d = load_case("two_bus_tap.json")
+    if flip:
+        g.f, g.t = g.t.copy(), g.f.copy()
+    th, V, k, st, err = pf.base_case(g, tol=1e-13)
+    assert st == pf.STATUS_OK
+    assert abs(th[1] + np.arcsin(0.8 * 0.25 * 1.05 / (1.03 * 0.98))) < 1e-12
+
+
+def test_two_bus_tap_voltage_closed_form():
+    """A PQ bus behind a tap: the quadratic of Q_2 = (V_2^2 - V_1 V_2/tau)/x,
+    and with the tap on the PQ side V_2 scales by tau."""
+    g, d = load_case("two_bus_tap_pq.json")
+    th, V, k, st, err = pf.base_case(g, tol=1e-13)
+    assert st == pf.STATUS_OK
+    a, q, x, v1 = 0.97, -0.3, 0.2, 1.02
+    assert abs(V[1] - (v1 / a + np.sqrt((v1 / a) ** 2 + 4 * q * x)) / 2) < 1e-12
+    assert abs(th[1]) < 1e-13
+    g.f, g.t = g.t.copy(), g.f.copy()
+    th, V, k, st, err = pf.base_case(g, tol=1e-13)
+    assert st == pf.STATUS_OK
+    assert abs(V[1] - a * (v1 + np.sqrt(v1 * v1 + 4 * q * x)) / 2) < 1e-12
+
+
+def _with_taps(g, seed, frac=0.5):
+    rng = np.random.default_rng(seed)
+    g = g.copy()
+    g.tap = np.where(rng.uniform(size=g.n_branch) < frac,
+                     rng.uniform(0.9, 1.1, g.n_branch), 1.0)
+    return g
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_tapped_lossy_cases_match_newton(seed):
+    g0, _ = load_case("five_bus_lossy.json")
+    for g in (_with_taps(g0, seed), _with_taps(random_tree_grid(12, 7 + seed, lossless=False,
+                                                                all_pv=False)[0], seed)):
+        th, V, k, st, err = pf.base_case(g, tol=1e-12)
+        assert st == pf.STATUS_OK
+        thn, Vn = newton_solution(g)
+        np.testing.assert_allclose(th, thn, atol=1e-9)
+        np.testing.assert_allclose(V, Vn, atol=1e-9)
+
+
+def test_unit_taps_change_nothing():
+    g = config_grid("grid120")
+    gt = g.copy()
+    gt.tap = np.ones(g.n_branch)
+    a = pf.base_case(g)
+    b = pf.base_case(gt)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_tapped_bdprime_is_minus_imag_ybus():
+    """With r = 0 and no charging, B'' is minus the imaginary part of the bus
+    admittance matrix (turns ratios included) on the PQ buses."""
+    g, _ = random_tree_grid(15, 4, lossless=True, all_pv=False)
+    g = _with_taps(g, 9, frac=0.7)
+    on = np.ones(g.n_branch, bool)
+    keep = np.flatnonzero(g.bus_type == 0)
+    row, col, Gv, Bv = pf.ybus_entries(g.n_bus, g.f, g.t, g.r, g.x, g.b_sh, on, g.tap)
+    B = np.zeros((g.n_bus, g.n_bus))
+    np.add.at(B, (row, col), Bv)
+    Bpp = pf.bdprime(g.n_bus, g.f, g.t, g.r, g.x, on, keep, g.tap).toarray()
+    np.testing.assert_allclose(Bpp, -B[np.ix_(keep, keep)], rtol=1e-14, atol=1e-12)
+    assert np.all(np.linalg.eigvalsh(Bpp) > 0)
+
+
+def test_tapped_n1_kcl_and_power_balance():
+    """Flows at both ends (branch_flows, taps included) against the
+    mismatch's bus injections (ybus_entries): Kirchhoff's law per bus and
+    the power balance, on every outage of a grid with 15 % transformers."""
+    from gridgen import make_grid
+    g = make_grid(120, 180, seed=1, load_scale=0.3, xfmr_frac=0.15)
+    th0, V0, _, st, _ = pf.base_case(g)
+    assert st == pf.STATUS_OK
+    res = screen.n1_screen(g, th0, V0, np.arange(g.n_branch), tol=1e-10, processes=1)
+    ok = 0
+    for s in range(g.n_branch):
+        if res["status"][s] != pf.STATUS_OK:
+            continue
+        on, label, isl, P, _ = screen.outage_setup(g, s)
+        net = np.zeros(g.n_bus)
+        np.add.at(net, g.f, res["flow"][s])
+        np.add.at(net, g.t, res["flow_to"][s])
+        nonslack = ~isl & (g.bus_type != 2)
+        assert np.abs(net[nonslack] - P[nonslack]).max() < 1e-9
+        losses = (res["flow"][s] + res["flow_to"][s]).sum()
+        assert abs(P[nonslack].sum() + net[g.slack] - losses) < 1e-9
+        ok += 1
+    assert ok > 0.9 * g.n_branch
 
 
 # ----------------------------------------------- outage algebra (Sec. IV.B)
