@@ -89,7 +89,14 @@ enum {
 };
 
 /* Bus/branch model of Sec. II.B (vertex and edge attributes).  Host
- * pointers.  Exactly one slack bus.  from[l] != to[l], x[l] > 0. */
+ * pointers.  Exactly one slack bus.  from[l] != to[l], x[l] > 0.
+ * A transformer is a branch with an off-nominal turns ratio tap[l] (the
+ * edge attribute "transformer turns ratio" of Sec. II.B): an ideal
+ * tap[l]:1 transformer at the from end in series with the pi-model, no
+ * phase shift, so with c = 1/tap[l]: Y_ff += c^2 (y + j b_sh/2),
+ * Y_tt += y + j b_sh/2, Y_ft = Y_tf = -c y.  B'' takes the turns ratios
+ * (w v v^T, v = c e_from - e_to), B' leaves them out (the XB scheme).
+ * Outaging a transformer is a branch outage like any other. */
 typedef struct {
   int32_t n_bus;
   int32_t n_branch;
@@ -104,6 +111,8 @@ typedef struct {
   const double *x;          /* [n_branch] series reactance, > 0 */
   const double *b_sh;       /* [n_branch] total line charging */
   const double *rating;     /* [n_branch] flow limit, > 0 */
+  const double *tap;        /* [n_branch] turns ratio at the from end, > 0;
+                               NULL: every branch is a line (ratio 1) */
 } gpcg_grid;
 
 typedef struct {

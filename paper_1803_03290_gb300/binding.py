@@ -32,7 +32,7 @@ class _Grid(C.Structure):
                 ("bus_type", C.c_void_p), ("P_sched", C.c_void_p), ("Q_sched", C.c_void_p),
                 ("P_gen", C.c_void_p), ("V_set", C.c_void_p), ("from_", C.c_void_p),
                 ("to", C.c_void_p), ("r", C.c_void_p), ("x", C.c_void_p),
-                ("b_sh", C.c_void_p), ("rating", C.c_void_p)]
+                ("b_sh", C.c_void_p), ("rating", C.c_void_p), ("tap", C.c_void_p)]
 
 
 class Options(C.Structure):
@@ -131,6 +131,9 @@ def _grid_struct(grid):
         x=np.ascontiguousarray(grid.x, dtype=np.float64),
         b_sh=np.ascontiguousarray(grid.b_sh, dtype=np.float64),
         rating=np.ascontiguousarray(grid.rating, dtype=np.float64))
+    tap = getattr(grid, "tap", None)
+    if tap is not None:
+        keep["tap"] = np.ascontiguousarray(tap, dtype=np.float64)
     g = _Grid(n_bus=int(grid.n_bus), n_branch=int(grid.n_branch),
               **{k: v.ctypes.data for k, v in keep.items()})
     return g, keep
@@ -172,20 +175,7 @@ class GPCG:
         self._lib = lib
         self.n_bus = int(grid.n_bus)
         self.n_branch = int(grid.n_branch)
-        keep = dict(
-            bus_type=np.ascontiguousarray(grid.bus_type, dtype=np.int8),
-            P_sched=np.ascontiguousarray(grid.P_sched, dtype=np.float64),
-            Q_sched=np.ascontiguousarray(grid.Q_sched, dtype=np.float64),
-            P_gen=np.ascontiguousarray(grid.P_gen, dtype=np.float64),
-            V_set=np.ascontiguousarray(grid.V_set, dtype=np.float64),
-            from_=np.ascontiguousarray(grid.f, dtype=np.int32),
-            to=np.ascontiguousarray(grid.t, dtype=np.int32),
-            r=np.ascontiguousarray(grid.r, dtype=np.float64),
-            x=np.ascontiguousarray(grid.x, dtype=np.float64),
-            b_sh=np.ascontiguousarray(grid.b_sh, dtype=np.float64),
-            rating=np.ascontiguousarray(grid.rating, dtype=np.float64))
-        g = _Grid(n_bus=self.n_bus, n_branch=self.n_branch,
-                  **{k: v.ctypes.data for k, v in keep.items()})
+        g, keep = _grid_struct(grid)  # keep: the arrays g points into
         self.options = default_options(**options)
         h = C.c_void_p()
         _check(lib, lib.gpcg_create(C.byref(g), C.byref(self.options), C.byref(h)))

@@ -21,11 +21,12 @@ namespace gpcg {
 // build.cu
 void launch_branch_params(cudaStream_t, int, const double*, const double*, double*, double*,
                           double*, double*);
-void launch_ybus_diag(cudaStream_t, int, const int32_t*, const int32_t*, const double*,
-                      const double*, const double*, double*, double*);
+void launch_ybus_diag(cudaStream_t, int, const int32_t*, const int32_t*, const int32_t*,
+                      const double*, const double*, const double*, const double*, double*,
+                      double*);
 void launch_laplacian_values(cudaStream_t, int, const int32_t*, const int32_t*, const int32_t*,
                              const int32_t*, const int32_t*, const double*, const int32_t*,
-                             const int32_t*, double*, int32_t*);
+                             const double*, const int32_t*, const int32_t*, double*, int32_t*);
 void launch_ic_level(cudaStream_t, int, int, const int32_t*, const int32_t*, const double*,
                      const int32_t*, const int32_t*, double*, int32_t*);
 void launch_scatter(cudaStream_t, int, const int32_t*, const double*, double*);
@@ -39,8 +40,8 @@ void launch_gather_half(cudaStream_t, int, const int32_t*, const double*, __half
 void launch_inv_diag(cudaStream_t, int, const int32_t*, const double*, double*, float*);
 void launch_tail_inverse(cudaStream_t, int, int, const int32_t*, const int32_t*, const double*,
                          const double*, double*, double*, float*, float*);
-void launch_adj_values(cudaStream_t, int, const int32_t*, const double*, const double*, double*,
-                       double*);
+void launch_adj_values(cudaStream_t, int, const int32_t*, const double*, const double*,
+                       const double*, double*, double*);
 }  // namespace gpcg
 
 
@@ -106,6 +107,7 @@ struct MatDev {
   float* inv_d2_32 = nullptr;
   EllDev A, L, U;
   double* w = nullptr;  // per-branch weight
+  double* c = nullptr;  // per-branch from-end factor (B'': 1 / turns ratio), null = 1
   template <typename VT>
   DevMatT<VT> view(bool f16 = false) const;
 };
@@ -127,6 +129,7 @@ DevMatT<double> MatDev::view<double>(bool) const {
   M.ntblev = (int)plan.tblev_ptr.size() - 1;
   M.xc = xc; M.xr = xr;
   M.w = w;
+  M.c = c;
   return M;
 }
 template <>
@@ -151,6 +154,7 @@ DevMatT<float> MatDev::view<float>(bool f16) const {
   M.xc = f16 && xch ? xch : xc32;
   M.xr = f16 && xrh ? xrh : xr32;
   M.w = w;
+  M.c = c;
   return M;
 }
 
@@ -331,7 +335,7 @@ static gpcg_status fill_values(gpcg_ctx* c, MatDev& M, const double* w) {
   cudaStream_t st = 0;
   CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int32_t)));
   launch_laplacian_values(st, P.n, M.bus_of_row, M.row_of_bus, c->G.adj_ptr, c->G.adj_idx,
-                          c->G.adj_br, w, M.a_ptr, M.a_idx, M.a_val, c->d_err);
+                          c->G.adj_br, w, c->G.f, M.c, M.a_ptr, M.a_idx, M.a_val, c->d_err);
   for (size_t k = 0; k + 1 < P.lev_ptr.size(); ++k)
     launch_ic_level(st, P.lev_ptr[k], P.lev_ptr[k + 1], M.a_ptr, M.a_idx, M.a_val, M.l_ptr,
                     M.l_idx, M.l_val, c->d_err);
@@ -367,7 +371,7 @@ static gpcg_status fill_values(gpcg_ctx* c, MatDev& M, const double* w) {
 }
 
 static gpcg_status build_matrix(gpcg_ctx* c, MatDev& M, const std::vector<uint8_t>& keep,
-                                double* w, bool fill) {
+                                double* w, double* cf, bool fill) {
   M.plan = plan_matrix(c->n, c->bg, keep, fill);
   plan_tail(M.plan, TAIL_ROWS);
   const MatrixPlan& P = M.plan;
@@ -440,6 +444,7 @@ static gpcg_status build_matrix(gpcg_ctx* c, MatDev& M, const std::vector<uint8_
     }
   }
   M.w = w;
+  M.c = cf;
   return fill_values(c, M, w);
 }
 
@@ -453,9 +458,10 @@ static gpcg_status build_matrices(gpcg_ctx* c) {
     keepQ[b] = c->bus_type[b] == GPCG_PQ;
   }
   const bool fill = c->opt.precond == GPCG_PRECOND_EXACT;
-  gpcg_status st = build_matrix(c, c->MP, keepP, c->wP, fill);
+  // B' leaves turns ratios out, B'' keeps them (the XB scheme)
+  gpcg_status st = build_matrix(c, c->MP, keepP, c->wP, nullptr, fill);
   if (st != GPCG_OK) return st;
-  st = build_matrix(c, c->MQ, keepQ, c->wQ, fill);
+  st = build_matrix(c, c->MQ, keepQ, c->wQ, c->G.cf, fill);
   if (st != GPCG_OK) return st;
   {
     const MatrixPlan& Q = c->MQ.plan;
@@ -519,6 +525,9 @@ static gpcg_status validate_grid(const gpcg_grid* g, int* slack_out) {
     if (!(g->x[e] > 0) || !std::isfinite(g->x[e]) || !(g->r[e] >= 0) ||
         !std::isfinite(g->r[e]) || !std::isfinite(g->b_sh[e]) || !(g->rating[e] > 0))
       return fail(GPCG_ERR_INVALID_ARG, "branch %d: needs x > 0, r >= 0, rating > 0", e);
+    if (g->tap && !(g->tap[e] > 0 && std::isfinite(g->tap[e])))
+      return fail(GPCG_ERR_INVALID_ARG, "branch %d: turns ratio %g is not positive and finite",
+                  e, g->tap[e]);
   }
   *slack_out = slack;
   return GPCG_OK;
@@ -674,6 +683,8 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
     std::vector<double> inv(m);
     for (int e = 0; e < m; ++e) inv[e] = 1.0 / g->rating[e];
     UP(G.inv_rating, inv.data(), m);
+    for (int e = 0; e < m; ++e) inv[e] = g->tap ? 1.0 / g->tap[e] : 1.0;
+    UP(G.cf, inv.data(), m);
   }
   UP(G.adj_ptr, c->bg.adj.ptr.data(), n + 1);
   UP(G.adj_idx, c->bg.adj.idx.data(), c->bg.adj.idx.size());
@@ -743,9 +754,9 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
 #undef UP
 #undef AL
   launch_branch_params(0, m, G.r, G.x, G.g, G.by, c->wP, c->wQ);
-  launch_ybus_diag(0, n, G.adj_ptr, G.adj_br, G.g, G.by, G.b_sh, G.Gii, G.Bii);
-  launch_adj_values(0, c->n_adj_slots, G.adj_brl, G.g, G.by, G.adj_g, G.adj_b);
-  launch_adj_values(0, c->n_adj_over, G.adj_obr, G.g, G.by, G.adj_og, G.adj_ob);
+  launch_ybus_diag(0, n, G.adj_ptr, G.adj_br, G.f, G.cf, G.g, G.by, G.b_sh, G.Gii, G.Bii);
+  launch_adj_values(0, c->n_adj_slots, G.adj_brl, G.cf, G.g, G.by, G.adj_g, G.adj_b);
+  launch_adj_values(0, c->n_adj_over, G.adj_obr, G.cf, G.g, G.by, G.adj_og, G.adj_ob);
   if ((ce = cudaGetLastError()) != cudaSuccess) return fail_cuda(ce, "build kernels");
   st = build_matrices(c);
   if (st != GPCG_OK) {

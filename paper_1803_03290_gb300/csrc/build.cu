@@ -21,10 +21,12 @@ __global__ void branch_params_kernel(int m, const double* __restrict__ r,
   wQ[e] = xx / d;
 }
 
-// Y_ii = sum over incident branches of (y + j b_sh/2), summed in the fixed
-// order of the bus adjacency lists.
+// Y_ii = sum over incident branches of (y + j b_sh/2), times c^2 at the
+// from end of a transformer (c = 1 / turns ratio: the pi-model sees V_i c),
+// summed in the fixed order of the bus adjacency lists.
 __global__ void ybus_diag_kernel(int n, const int32_t* __restrict__ adj_ptr,
                                  const int32_t* __restrict__ adj_br,
+                                 const int32_t* __restrict__ from, const double* __restrict__ cf,
                                  const double* __restrict__ g, const double* __restrict__ by,
                                  const double* __restrict__ b_sh, double* Gii, double* Bii) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -32,23 +34,28 @@ __global__ void ybus_diag_kernel(int n, const int32_t* __restrict__ adj_ptr,
   double G = 0.0, B = 0.0;
   for (int k = adj_ptr[i]; k < adj_ptr[i + 1]; ++k) {
     int e = adj_br[k];
-    G += g[e];
-    B += by[e] + 0.5 * b_sh[e];
+    const double c2 = from[e] == i ? cf[e] * cf[e] : 1.0;
+    G += c2 * g[e];
+    B += c2 * (by[e] + 0.5 * b_sh[e]);
   }
   Gii[i] = G;
   Bii[i] = B;
 }
 
-// Values of a grounded weighted Laplacian on its CSR pattern: one thread
-// per matrix row walks the bus's incident branches in a fixed order.  The
-// diagonal collects every incident branch (also those to buses without a
-// row); each neighbour with a row receives -w in its slot.
+// Values of a grounded sum of branch terms w v v^T, v = c e_from - e_to
+// (c = 1 for every branch when cf is null: a weighted Laplacian), on its CSR
+// pattern: one thread per matrix row walks the bus's incident branches in a
+// fixed order.  The diagonal collects every incident branch (also those to
+// buses without a row), w c^2 at a from end and w at a to end; each
+// neighbour with a row receives -w c in its slot.
 __global__ void laplacian_values_kernel(int nrows, const int32_t* __restrict__ bus_of_row,
                                         const int32_t* __restrict__ row_of_bus,
                                         const int32_t* __restrict__ adj_ptr,
                                         const int32_t* __restrict__ adj_idx,
                                         const int32_t* __restrict__ adj_br,
                                         const double* __restrict__ w,
+                                        const int32_t* __restrict__ from,
+                                        const double* __restrict__ cf,
                                         const int32_t* __restrict__ a_ptr,
                                         const int32_t* __restrict__ a_idx, double* a_val,
                                         int32_t* err) {
@@ -59,8 +66,14 @@ __global__ void laplacian_values_kernel(int nrows, const int32_t* __restrict__ b
   for (int k = s; k < e_; ++k) a_val[k] = 0.0;
   double diag = 0.0;
   for (int k = adj_ptr[b]; k < adj_ptr[b + 1]; ++k) {
-    double we = w[adj_br[k]];
-    diag += we;
+    const int e = adj_br[k];
+    double we = w[e];
+    if (cf) {
+      diag += from[e] == b ? we * cf[e] * cf[e] : we;
+      we *= cf[e];
+    } else {
+      diag += we;
+    }
     int c = row_of_bus[adj_idx[k]];
     if (c < 0) continue;
     int lo = s, hi = e_ - 1, pos = -1;
@@ -161,18 +174,21 @@ void launch_branch_params(cudaStream_t st, int m, const double* r, const double*
   if (m) branch_params_kernel<<<nblk(m, 256), 256, 0, st>>>(m, r, x, g, by, wP, wQ);
 }
 void launch_ybus_diag(cudaStream_t st, int n, const int32_t* adj_ptr, const int32_t* adj_br,
-                      const double* g, const double* by, const double* b_sh, double* Gii,
-                      double* Bii) {
-  if (n) ybus_diag_kernel<<<nblk(n, 256), 256, 0, st>>>(n, adj_ptr, adj_br, g, by, b_sh, Gii, Bii);
+                      const int32_t* from, const double* cf, const double* g, const double* by,
+                      const double* b_sh, double* Gii, double* Bii) {
+  if (n)
+    ybus_diag_kernel<<<nblk(n, 256), 256, 0, st>>>(n, adj_ptr, adj_br, from, cf, g, by, b_sh,
+                                                   Gii, Bii);
 }
 void launch_laplacian_values(cudaStream_t st, int nrows, const int32_t* bus_of_row,
                              const int32_t* row_of_bus, const int32_t* adj_ptr,
                              const int32_t* adj_idx, const int32_t* adj_br, const double* w,
-                             const int32_t* a_ptr, const int32_t* a_idx, double* a_val,
-                             int32_t* err) {
+                             const int32_t* from, const double* cf, const int32_t* a_ptr,
+                             const int32_t* a_idx, double* a_val, int32_t* err) {
   if (nrows)
     laplacian_values_kernel<<<nblk(nrows, 128), 128, 0, st>>>(
-        nrows, bus_of_row, row_of_bus, adj_ptr, adj_idx, adj_br, w, a_ptr, a_idx, a_val, err);
+        nrows, bus_of_row, row_of_bus, adj_ptr, adj_idx, adj_br, w, from, cf, a_ptr, a_idx,
+        a_val, err);
 }
 void launch_ic_level(cudaStream_t st, int row0, int row1, const int32_t* a_ptr,
                      const int32_t* a_idx, const double* a_val, const int32_t* l_ptr,
@@ -224,13 +240,15 @@ __global__ void inv_diag_kernel(int n, const int32_t* __restrict__ pos,
 
 // Per-slot branch admittance of the mismatch adjacency (0 on padding).
 __global__ void adj_values_kernel(int n, const int32_t* __restrict__ br,
+                                  const double* __restrict__ cf,
                                   const double* __restrict__ g, const double* __restrict__ by,
                                   double* ag, double* ab) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int e = br[k];
-  ag[k] = e >= 0 ? g[e] : 0.0;
-  ab[k] = e >= 0 ? by[e] : 0.0;
+  // Y_ij = -c y for either end (c = 1 / turns ratio)
+  ag[k] = e >= 0 ? cf[e] * g[e] : 0.0;
+  ab[k] = e >= 0 ? cf[e] * by[e] : 0.0;
 }
 
 void launch_gather_val(cudaStream_t st, int n, const int32_t* src, const double* csr, double* dst,
@@ -286,9 +304,9 @@ void launch_tail_inverse(cudaStream_t st, int t0, int nt, const int32_t* l_ptr,
     tail_inverse_kernel<<<1, 128, 0, st>>>(t0, nt, l_ptr, l_idx, l_val, lsc, xc, xr, xc32, xr32);
 }
 
-void launch_adj_values(cudaStream_t st, int n, const int32_t* br, const double* g,
-                       const double* by, double* ag, double* ab) {
-  if (n > 0) adj_values_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, br, g, by, ag, ab);
+void launch_adj_values(cudaStream_t st, int n, const int32_t* br, const double* cf,
+                       const double* g, const double* by, double* ag, double* ab) {
+  if (n > 0) adj_values_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, br, cf, g, by, ag, ab);
 }
 
 }  // namespace gpcg

@@ -30,6 +30,7 @@ struct DevGrid {
   int32_t *f = nullptr, *t = nullptr;
   double *r = nullptr, *x = nullptr, *b_sh = nullptr, *rating = nullptr;
   double* inv_rating = nullptr;              // 1 / rating
+  double* cf = nullptr;                      // 1 / turns ratio at the from end (1: a line)
   double *g = nullptr, *by = nullptr;        // series admittance g + j b_y
   int32_t *adj_ptr = nullptr, *adj_idx = nullptr, *adj_br = nullptr;  // CSR adjacency
   double *Gii = nullptr, *Bii = nullptr;     // bus admittance diagonal
@@ -79,6 +80,9 @@ struct DevMatT {
   const int32_t *tblev_ptr = nullptr, *tblev_rows = nullptr;
   const VT *xc = nullptr, *xr = nullptr;
   const double* w = nullptr;                 // per-branch weight of this matrix
+  // per-branch factor of the from end (B'': 1 / turns ratio; null: 1): the
+  // branch adds w v v^T with v = c e_from - e_to
+  const double* c = nullptr;
 };
 
 // What the islanding pass leaves for each scenario.

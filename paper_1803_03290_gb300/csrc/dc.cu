@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
         St64.ra[tid] = on ? L.raP[tid] : -1;
         St64.rb[tid] = on ? L.rbP[tid] : -1;
         St64.w[tid] = L.wP[tid];
+        St64.c[tid] = 1.0;
       }
       if (g.rs == 0) st2(xd + (size_t)M.n * T + g.lane, Pair<double>{0.0, 0.0});
       __syncthreads();

@@ -163,8 +163,9 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
         const double ei = j ? ev1.x : ev0.x, fi = j ? ev1.y : ev0.y;
         double Gd = Gii, Bd = Bii;
         if (i == L.fb[ln] || i == L.tb[ln]) {  // the outaged branch's share
-          Gd -= L.gl[ln];
-          Bd -= L.bl[ln];
+          const double c2 = i == L.fb[ln] ? L.cl[ln] * L.cl[ln] : 1.0;
+          Gd -= c2 * L.gl[ln];
+          Bd -= c2 * L.bl[ln];
         }
         // I_i = Y_ii V_i + sum_j Y_ij V_j
         const double re = fma(Gd, ei, fma(-Bd, fi, j ? re1 : re0));
@@ -290,6 +291,7 @@ __device__ __forceinline__ void setup_lane(const FdpfParams& P, const DevMatT<VT
   L.wQ[ln] = l >= 0 ? MQ.w[l] : 0.0;
   L.gl[ln] = l >= 0 ? G.g[l] : 0.0;
   L.bl[ln] = l >= 0 ? G.by[l] + 0.5 * G.b_sh[l] : 0.0;
+  L.cl[ln] = l >= 0 ? G.cf[l] : 1.0;
   L.active[ln] = 1;
   L.outer[ln] = 0;
   L.inP[ln] = 0;
@@ -363,6 +365,7 @@ __device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& 
       const int a = __ldg(G.f + k), b = __ldg(G.t + k);
       const int pa = __ldg(G.pre + a), pb = __ldg(G.pre + b);
       const double gk = __ldg(G.g + k), bk = __ldg(G.by + k), ir = __ldg(G.inv_rating + k);
+      const double ck = __ldg(G.cf + k);  // 1 / turns ratio at a (1 for a line)
 #pragma unroll 1
       for (int jp = 0; jp < LP; jp += 2) {
         if (!((dn >> jp) & 3)) continue;
@@ -376,12 +379,13 @@ __device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& 
           const int lo = L.lo[ln], cnt = L.cnt[ln];
           double Pab = 0.0;
           if (k != L.l[ln] && !in_island(pa, lo, cnt) && !in_island(pb, lo, cnt)) {
-            // P_ab = g |V_a|^2 - g Re(V_a conj V_b) - b Im(V_a conj V_b), and
-            // P_ba with a and b swapped (the imaginary part changes sign)
+            // P_ab = c^2 g |V_a|^2 - c (g Re(V_a conj V_b) + b Im(V_a conj V_b)),
+            // P_ba = g |V_b|^2 - c (g Re(V_a conj V_b) - b Im(V_a conj V_b)),
+            // c = 1 / turns ratio at a (the pi-model sees V_a c)
             const double ea = va[h].x, fa = va[h].y, eb = vb[h].x, fb = vb[h].y;
-            const double cr = fma(ea, eb, fa * fb), sr = fma(fa, eb, -ea * fb);
+            const double cr = ck * fma(ea, eb, fa * fb), sr = ck * fma(fa, eb, -ea * fb);
             const double gc = gk * cr;
-            Pab = fma(gk, fma(ea, ea, fa * fa), -fma(bk, sr, gc));
+            Pab = fma(gk * ck * ck, fma(ea, ea, fa * fa), -fma(bk, sr, gc));
             const double Pba = fma(gk, fma(eb, eb, fb * fb), fma(bk, sr, -gc));
             // loading max(|P_ab|, |P_ba|) / rating: the larger end picked on
             // the bit patterns, one multiplication
@@ -468,6 +472,7 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     L.l[tid] = L.fb[tid] = L.tb[tid] = -1;
     L.raP[tid] = L.rbP[tid] = L.raQ[tid] = L.rbQ[tid] = -1;
     L.wP[tid] = L.wQ[tid] = 0.0;
+    L.cl[tid] = 1.0;
     L.lo[tid] = L.cnt[tid] = 0;
   }
   __syncthreads();
@@ -550,7 +555,8 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     mismatch_pass<T, VT, false>(P, MP, MQ, L, EF, V, r, d0, d1);
     __syncthreads();
     GPCG_PHASE(4);
-    pcg_solve<T, VT, true>(P, MQ, L, x, r, p, q, z, L.raQ, L.rbQ, L.wQ, L.inQ);
+    pcg_solve<T, VT, true>(P, MQ, L, x, r, p, q, z, L.raQ, L.rbQ, L.wQ, L.inQ,
+                           MQ.c ? L.cl : nullptr);
     GPCG_PHASE(5);
     update_pass<T, VT, false>(MQ, L, x, p, th, V, C, Sn, EF);
     if (g.rs == 0)
@@ -588,6 +594,7 @@ __global__ void __launch_bounds__(NTHREADS) apply_kernel(DevMatT<VT> M, int op, 
       St.ra[threadIdx.x] = l >= 0 ? M.row_of_bus[f_[l]] : -1;
       St.rb[threadIdx.x] = l >= 0 ? M.row_of_bus[t_[l]] : -1;
       St.w[threadIdx.x] = l >= 0 ? (VT)M.w[l] : (VT)0;
+      St.c[threadIdx.x] = l >= 0 && M.c ? (VT)M.c[l] : (VT)1;
     }
     for (int i = g.rs; i <= M.n; i += Geo<T>::RPS) {
       Vec<VT, LP> v = vzero<VT, LP>();

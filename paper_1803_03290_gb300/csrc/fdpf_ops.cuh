@@ -208,6 +208,7 @@ struct LaneState {
   int scen[T], l[T], fb[T], tb[T], lo[T], cnt[T];
   int raP[T], rbP[T], raQ[T], rbQ[T];
   double wP[T], wQ[T], coef[T], gl[T], bl[T];
+  double cl[T];  // the outaged branch's 1 / turns ratio (1 for a line)
   int active[T], outer[T], inP[T], inQ[T], status[T], nogen[T];
   double err[T], best[T];
   unsigned long long tphase[8];
@@ -390,14 +391,15 @@ __device__ __forceinline__ Vec<unsigned long long, N> lane_max_bits(
 }
 
 // ----------------------------------------------------- the outage's change
-// Rows and weight of each lane's outaged branch in the matrix being solved
-// (-1: that end has no row).  stamp_filter sets bit (row & 63) for every
-// such row, so the SpMV tests one bit per row and looks at the lanes only
-// on a hit.
+// Rows, weight and from-end factor of each lane's outaged branch in the
+// matrix being solved (-1: that end has no row): the outage removes
+// w v v^T, v = c e_ra - e_rb (c = 1 / turns ratio in B'', 1 in B').
+// stamp_filter sets bit (row & 63) for every such row, so the SpMV tests one
+// bit per row and looks at the lanes only on a hit.
 template <int T, typename VT>
 struct Stamp {
   int ra[T], rb[T];
-  VT w[T];
+  VT w[T], c[T];
 };
 
 template <int T, typename VT>
@@ -413,8 +415,8 @@ __device__ __forceinline__ unsigned long long stamp_filter(const Stamp<T, VT>& S
 
 // ----------------------------------------------------- batched operators
 // y = B_s v for the thread's lanes: base row times v, plus the outaged
-// branch's four-element change (Sec. IV.B) -- off-diagonal +w, diagonal -w
-// at both ends.
+// branch's four-element change (Sec. IV.B) -- off-diagonal +w c, diagonal
+// -w c^2 at the from end and -w at the to end (c = 1 without a transformer).
 //
 // Plain (DIRECTION = false): q = B_s p, returns the lanes' partial p.q.
 // DIRECTION = true, the PCG direction update folded in: with v = z,
@@ -484,14 +486,16 @@ __device__ GPCG_LOOP_INLINE Vec<VT, Geo<T>::LP> spmv_pass(
         for (int j = 0; j < LP; ++j) a.v[j] += vv * pp.v[j];
       }
       // the outage's change, on the two rows of the outaged branch only:
-      // + w v_other (when the other end has a row) - w v_own
+      // -w v (v.x) with v = c e_ra - e_rb (an end without a row holds 0)
       if ((filt >> (i & 63)) & 1ull) {
 #pragma unroll
         for (int j = 0; j < LP; ++j) {
           const int ln = g.lane + j, ra = S.ra[ln], rb = S.rb[ln];
           if (i == ra || i == rb) {
-            const int oth = (i == ra) ? rb : ra;
-            a.v[j] += S.w[ln] * ((oth >= 0 ? v_[(size_t)oth * T + ln] : (VT)0) - pi.v[j]);
+            const VT xa = i == ra ? pi.v[j] : (ra >= 0 ? v_[(size_t)ra * T + ln] : (VT)0);
+            const VT xb = i == rb ? pi.v[j] : (rb >= 0 ? v_[(size_t)rb * T + ln] : (VT)0);
+            const VT wt = S.w[ln] * (S.c[ln] * xa - xb);
+            a.v[j] += i == ra ? -(S.c[ln] * wt) : wt;
           }
         }
       }
@@ -846,7 +850,8 @@ __device__ GPCG_LOOP_INLINE void jacobi_pass(const DevMatT<VT>& M, VT* __restric
 #pragma unroll
     for (int j = 0; j < LP; ++j) {
       const int ln = g.lane + j;
-      const VT d = dg - ((i == S.ra[ln] || i == S.rb[ln]) ? S.w[ln] : (VT)0);
+      const VT d = dg - (i == S.ra[ln] ? S.w[ln] * S.c[ln] * S.c[ln]
+                                       : i == S.rb[ln] ? S.w[ln] : (VT)0);
       zi.v[j] = d > (VT)0 ? ri.v[j] / d : (VT)0;
       rz.v[j] += ri.v[j] * zi.v[j];
     }
@@ -885,7 +890,7 @@ struct PcgLanes {
 template <int T, typename VT, bool DEFER = false>
 __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT>& M, LaneState<T>& L, VT* x,
                           VT* r, VT* p, VT* q, VT* z, const int* ra_, const int* rb_,
-                          const double* w_, int* iters) {
+                          const double* w_, int* iters, const double* c_ = nullptr) {
   constexpr int LP = Geo<T>::LP;
   __shared__ PcgLanes<T, VT> S;
   __shared__ Stamp<T, VT> St;
@@ -901,6 +906,7 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
     St.ra[tid] = on ? ra_[tid] : -1;
     St.rb[tid] = on ? rb_[tid] : -1;
     St.w[tid] = (VT)w_[tid];
+    St.c[tid] = c_ ? (VT)c_[tid] : (VT)1;
     L.xalpha[tid] = 0.0;
   }
   if (g.rs == 0) {

@@ -4,13 +4,22 @@ import functools
 
 import numpy as np
 
-from gridgen import config_grid
+from gridgen import CONFIGS, config_grid, make_grid
 from oracle import powerflow as pf
 from oracle import screen
+
+# Grids of the named workloads with a share of their branches turned into
+# transformers (off-nominal turns ratios U[0.95, 1.05] at the from end).
+XFMR = {"grid120_xfmr": ("grid120", 0.15), "grid2k_xfmr": ("grid2k", 0.1)}
 
 
 @functools.lru_cache(maxsize=None)
 def grid(name):
+    if name in XFMR:
+        base, frac = XFMR[name]
+        g = make_grid(gen_share=1.0, xfmr_frac=frac, **CONFIGS[base])
+        g.meta["config"] = name
+        return g
     return config_grid(name)
 
 

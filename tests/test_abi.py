@@ -52,5 +52,12 @@ def test_invalid_arguments_fail_before_the_gpu():
     with pytest.raises(binding.GPCGError) as e:
         binding.GPCG(bad)
     assert e.value.status == 1
+    for v in (-1.0, 0.0, float("nan")):
+        bad = g.copy()
+        bad.tap = np.ones(g.n_branch)
+        bad.tap[5] = v
+        with pytest.raises(binding.GPCGError) as e:
+            binding.GPCG(bad)
+        assert e.value.status == 1 and "turns ratio" in str(e.value)
     with pytest.raises(binding.GPCGError):
         binding.default_options(precision=7) and binding.GPCG(g, precision=7)
