@@ -128,6 +128,22 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def bench_grid(args):
+    """The named workload's synthetic grid, with ``--xfmr-frac`` of its
+    branches made transformers (drawn after the rest: the grid is otherwise
+    the same)."""
+    from gridgen import CONFIGS, config_grid, make_grid
+    if args.xfmr_frac <= 0:
+        return config_grid(args.config)
+    g = make_grid(gen_share=1.0, xfmr_frac=args.xfmr_frac, **CONFIGS[args.config])
+    g.meta["config"] = args.config
+    return g
+
+
+def xfmr_note(args):
+    return f", {100 * args.xfmr_frac:g} % transformers" if args.xfmr_frac > 0 else ""
+
+
 def run_gpcg(args):
     import torch
     import torch.distributed as dist
@@ -138,9 +154,8 @@ def run_gpcg(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     import paper_1803_03290_gb300 as gp
-    from gridgen import config_grid
 
-    g = config_grid(args.config)
+    g = bench_grid(args)
     prec = {"fp32": gp.BATCHED_FP32, "fp64": gp.BATCHED_FP64,
             "fp16f": gp.BATCHED_FP32_F16}[args.precision]
     pc = {"exact": gp.PRECOND_EXACT, "ic0": gp.PRECOND_IC0, "jacobi": gp.PRECOND_JACOBI}[args.precond]
@@ -222,6 +237,7 @@ def run_gpcg(args):
     peak, peak_kind = load_peaks()
     achieved = algo / (fd_ms / 1e3) / 1e9
     default_workload = (args.config == "grid10k" and args.precision == "fp32" and
+                        args.xfmr_frac == 0 and
                         args.precond == "exact" and args.n_outages <= 0)
     traffic = (KERNEL_TRAFFIC["bytes"] if default_workload and
                kernel_digest() == KERNEL_TRAFFIC["sha256"] else None)
@@ -240,7 +256,8 @@ def run_gpcg(args):
             "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if w == 4 else "f64",
             "data": "synthetic",
-            "config": {"workload": f"{args.config}: {n} buses, {m} branches, {S} single-branch "
+            "config": {"workload": f"{args.config}: {n} buses, {m} branches{xfmr_note(args)}, "
+                                   f"{S} single-branch "
                                    f"outages, tol 1e-4 p.u., {args.precond} base-case preconditioner, "
                                    f"{args.precision} inner PCG, FP64 mismatch/flows",
                        "n_bus": n, "n_branch": m, "scenarios": S, "tile": info["tile"],
@@ -385,10 +402,9 @@ def run_reference(args):
     rank, world, _ = _env_rank()
     if rank != 0:
         return
-    from gridgen import config_grid
     from oracle import powerflow as pf
     from oracle import screen
-    g = config_grid(args.config)
+    g = bench_grid(args)
     cores = len(os.sched_getaffinity(0))
     th0, V0, _, st, _ = pf.base_case(g, tol=1e-10, max_outer=200)
     per_step = args.ref_sample
@@ -408,7 +424,8 @@ def run_reference(args):
             "ms_per_step": round(1e3 * sum(times) / args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": f"{args.config}: {g.n_bus} buses, {g.n_branch} branches, "
+            "config": {"workload": f"{args.config}: {g.n_bus} buses, {g.n_branch} branches"
+                                   f"{xfmr_note(args)}, "
                                    f"{per_step} seeded outages per step, tol 1e-4 p.u."},
             "cpu_baseline": {"value": round(value, 2), "unit": "scenarios/s", "cores": cores,
                              "kind": "oracle",
@@ -433,6 +450,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=400)
     ap.add_argument("--plain-sample", type=int, default=64)
     ap.add_argument("--ref-sample", type=int, default=256)
+    ap.add_argument("--xfmr-frac", type=float, default=0.0,
+                    help="make this fraction of the branches transformers (turns ratio "
+                         "U[0.95, 1.05] at the from end); 0 = the plain workload")
     ap.add_argument("--workload", default="ac", choices=["ac", "dc"],
                     help="ac: the FDPF N-1 screen (the headline); dc: the P-theta quick screen")
     args = ap.parse_args()
