@@ -17,6 +17,13 @@ scheduled generation, in proportion to that generation:
 The sign is kept, so an exporting island raises the main generators and an
 importing island lowers them.  If the main island has no such generator the
 slack absorbs the difference and the scenario is flagged.
+
+A generator outage (the loss of a single component other than a branch,
+Sec. IV.A) is read the same way: the tripped PV bus loses its scheduled
+generation P_gen[k], and that power is taken up by the other PV generators
+with positive scheduled generation in proportion to it (slack excluded; the
+slack absorbs it if there are none).  Also **parity unpinned** beyond the
+balance invariant.
 """
 from __future__ import annotations
 
@@ -39,4 +46,18 @@ def redispatch(bus_type: np.ndarray, P_sched: np.ndarray, P_gen: np.ndarray,
     w = P_gen[part] / P_gen[part].sum()
     P[part] += dP * w
     P[islanded] = 0.0
+    return P, False
+
+
+def redispatch_generator(bus_type: np.ndarray, P_sched: np.ndarray, P_gen: np.ndarray,
+                         k: int):
+    """Trip the generator of PV bus k: (P_sched after re-dispatch, no_generator_flag)."""
+    P = P_sched.astype(np.float64).copy()
+    lost = float(P_gen[k])
+    P[k] -= lost
+    part = (bus_type == PV) & (P_gen > 0.0)
+    part[k] = False
+    if not part.any():
+        return P, True
+    P[part] += lost * P_gen[part] / P_gen[part].sum()
     return P, False

@@ -7,6 +7,12 @@ islands' injection over the main island; run the FDPF on the main island
 starting from the base-case state (warm start, Sec. III.B); compute branch
 flows and the loading max(|P_ij|, |P_ji|)/rating of every branch.  Islanded
 buses report theta = V = 0, their branches zero flow.
+
+Generator outages (the loss of a single component, Sec. IV.A): the PV bus k
+loses its generator, so it keeps its load (P_sched[k] - P_gen[k] and
+Q_sched[k]) and no longer holds its voltage: it becomes a PQ bus.  The lost
+generation is re-dispatched (``redispatch.redispatch_generator``); no branch
+leaves service and nothing is islanded.
 """
 from __future__ import annotations
 
@@ -18,7 +24,7 @@ import numpy as np
 from .islands import components, island_mask
 from .powerflow import (STATUS_ISLAND_NO_GEN, STATUS_OK, branch_flows,
                         fdpf, mismatch, ybus_entries)
-from .redispatch import redispatch
+from .redispatch import redispatch, redispatch_generator
 
 
 def outage_setup(grid, l):
@@ -63,25 +69,56 @@ def scenario_mismatch(grid, l, theta, V):
     return max(a, b)
 
 
+def generator_setup(grid, k):
+    """The grid after the generator of PV bus k trips, and the no-generator
+    flag of its re-dispatch."""
+    if grid.bus_type[k] != 1:
+        raise ValueError(f"bus {k} is not a PV bus")
+    P, no_gen = redispatch_generator(grid.bus_type, grid.P_sched, grid.P_gen, int(k))
+    g = grid.copy()
+    g.bus_type = grid.bus_type.copy()
+    g.bus_type[k] = 0
+    g.P_sched = P
+    return g, no_gen
+
+
+def solve_generator_outage(grid, theta0, V0, k, tol, max_outer):
+    g, no_gen = generator_setup(grid, k)
+    on = np.ones(g.n_branch, dtype=bool)
+    active = np.ones(g.n_bus, dtype=bool)
+    theta, V, it, status, err = fdpf(g, on, active, g.P_sched, theta0, V0, tol, max_outer)
+    Pf, Pt = branch_flows(g.f, g.t, g.r, g.x, on, theta, V, g.tap)
+    loading = np.maximum(np.abs(Pf), np.abs(Pt)) / g.rating
+    if status == STATUS_OK and no_gen:
+        status = STATUS_ISLAND_NO_GEN
+    return dict(theta=theta, V=V, flow=Pf, flow_to=Pt,
+                label=np.zeros(g.n_bus, dtype=np.int32), outer=it, status=status,
+                max_loading=float(loading.max(initial=0.0)),
+                n_overload=int((loading > 1.0).sum()), err=err, islanded=False)
+
+
 def _worker(args):
-    grid, theta0, V0, ls, tol, max_outer = args
-    return [solve_outage(grid, theta0, V0, int(l), tol, max_outer) for l in ls]
+    grid, theta0, V0, ls, tol, max_outer, kind = args
+    solve = solve_outage if kind == "branch" else solve_generator_outage
+    return [solve(grid, theta0, V0, int(l), tol, max_outer) for l in ls]
 
 
-def n1_screen(grid, theta0, V0, outages, tol=1e-4, max_outer=50, processes=None):
-    """Solve every outage in ``outages``; returns stacked result arrays."""
+def n1_screen(grid, theta0, V0, outages, tol=1e-4, max_outer=50, processes=None,
+              kind="branch"):
+    """Solve every outage in ``outages`` (branch indices, or PV bus indices
+    with kind="generator"); returns stacked result arrays."""
     outages = np.asarray(outages, dtype=np.int64)
     S = outages.shape[0]
     if processes is None:
         processes = len(os.sched_getaffinity(0))
     processes = max(1, min(processes, S))
     if processes == 1 or S < 8:
-        res = _worker((grid, theta0, V0, outages, tol, max_outer))
+        res = _worker((grid, theta0, V0, outages, tol, max_outer, kind))
     else:
         chunks = np.array_split(outages, processes * 4)
         ctx = mp.get_context("spawn")
         with ctx.Pool(processes) as pool:
-            parts = pool.map(_worker, [(grid, theta0, V0, c, tol, max_outer)
+            parts = pool.map(_worker, [(grid, theta0, V0, c, tol, max_outer, kind)
                                        for c in chunks if c.size])
         res = [r for p in parts for r in p]
     out = {}

@@ -250,6 +250,68 @@ def test_tapped_n1_kcl_and_power_balance():
     assert ok > 0.9 * g.n_branch
 
 
+# ------------------------------------------- generator outages (Sec. IV.A)
+def test_two_bus_generator_trip_closed_form():
+    g, d = load_case("two_bus_gen_trip.json")
+    th0, V0, _, st, _ = pf.base_case(g, tol=1e-13)
+    assert st == pf.STATUS_OK and V0[1] == 1.0
+    r = screen.solve_generator_outage(g, th0, V0, 1, tol=1e-13, max_outer=100)
+    # converged; the slack took the lost generation (no other generator)
+    assert r["status"] == pf.STATUS_ISLAND_NO_GEN
+    v1, x, pd, qd = 1.02, 0.2, 0.5, 0.2
+    a = v1 * v1 - 2 * qd * x
+    V2 = np.sqrt((a + np.sqrt(a * a - 4 * x * x * (pd * pd + qd * qd))) / 2)
+    assert abs(r["V"][1] - V2) < 1e-12
+    assert abs(r["theta"][1] + np.arcsin(pd * x / (v1 * V2))) < 1e-12
+    assert abs(r["flow"][0] - pd) < 1e-12   # the line carries the load
+
+
+@pytest.mark.parametrize("seed", [3, 8])
+def test_generator_trip_matches_newton(seed):
+    """The tripped bus as PQ with its load, the rest of the generation
+    scaled up by hand: Newton on that grid reaches the same state."""
+    g, _ = random_tree_grid(14, seed, lossless=False, all_pv=False)
+    g.P_gen = np.where(g.bus_type == 1, np.abs(g.P_sched) + 0.2, 0.0)
+    th0, V0, _, st, _ = pf.base_case(g, tol=1e-12)
+    assert st == pf.STATUS_OK
+    pv = np.flatnonzero(g.bus_type == 1)
+    for k in pv[:3]:
+        r = screen.solve_generator_outage(g, th0, V0, int(k), tol=1e-12, max_outer=200)
+        assert r["status"] in (pf.STATUS_OK, pf.STATUS_ISLAND_NO_GEN)
+        h = g.copy()
+        h.bus_type = g.bus_type.copy()
+        h.bus_type[k] = 0
+        others = [j for j in pv if j != k]
+        h.P_sched = g.P_sched.copy()
+        h.P_sched[k] -= g.P_gen[k]
+        tot = sum(g.P_gen[j] for j in others)
+        for j in others:
+            h.P_sched[j] += g.P_gen[k] * g.P_gen[j] / tot
+        thn, Vn = newton_solution(h)
+        np.testing.assert_allclose(r["theta"], thn, atol=1e-9)
+        np.testing.assert_allclose(r["V"], Vn, atol=1e-9)
+
+
+def test_generator_outages_kcl_and_balance():
+    g = config_grid("grid120")
+    th0, V0, _, st, _ = pf.base_case(g)
+    pv = np.flatnonzero(g.bus_type == 1)
+    res = screen.n1_screen(g, th0, V0, pv, tol=1e-10, processes=1, kind="generator")
+    assert np.all(res["status"] == pf.STATUS_OK)
+    for s, k in enumerate(pv):
+        h, no_gen = screen.generator_setup(g, int(k))
+        assert not no_gen
+        nonslack = g.bus_type != 2
+        # the lost generation is taken up in full by the other generators
+        assert abs(h.P_sched[nonslack].sum() - g.P_sched[nonslack].sum()) < 1e-12
+        net = np.zeros(g.n_bus)
+        np.add.at(net, g.f, res["flow"][s])
+        np.add.at(net, g.t, res["flow_to"][s])
+        assert np.abs(net[nonslack] - h.P_sched[nonslack]).max() < 1e-9
+        # the tripped bus no longer holds its set point
+        assert abs(res["V"][s][k] - g.V_set[k]) > 1e-6
+
+
 # ----------------------------------------------- outage algebra (Sec. IV.B)
 def test_sherman_morrison_first_solve():
     """B'_s = B' - b a a^T (a = e_i - e_j): the solve with the re-formed
