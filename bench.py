@@ -107,7 +107,7 @@ def algorithmic_bytes(info, iters, w, n_bus, n_branch):
 # the timed screens; see profiles/launches_bench_grid10k.md), valid only for
 # the kernel sources with this digest.
 KERNEL_TRAFFIC = {"sha256": "3b39ea58ad015cd2e2e4464289598edd7e82270beae55dd97c591f9f76878f7b", "bytes": 278.34e9}
-KERNEL_SOURCES = ("fdpf.cu", "fdpf_ops.cuh", "fdpf.h", "common.cuh")
+KERNEL_SOURCES = ("fdpf.cu", "fdpf_kernel.cuh", "fdpf_ops.cuh", "fdpf.h", "common.cuh")
 
 
 def kernel_digest():

@@ -213,6 +213,25 @@ GPCG_API gpcg_status gpcg_n1_screen(gpcg_ctx *ctx, const int32_t *outages, int32
                            double *flow, int32_t *island_label, int32_t *iters,
                            int32_t *status, double *max_loading);
 
+/* N-1 screen of generator outages (Sec. IV.A: the loss of a single
+ * component).  Scenario s trips the generator of PV bus gen_buses[s]
+ * (caller's numbering): that bus keeps its load -- P_sched - P_gen and
+ * Q_sched, Q_sched being the reactive injection without the generator --
+ * and no longer holds |V|, so it becomes a PQ bus; its P_gen is taken up by
+ * the other PV generators with P_gen > 0 in proportion to theirs (the
+ * re-dispatch rule of Sec. IV.C; with none left the slack absorbs it and
+ * the status is GPCG_SCEN_ISLAND_NO_GEN).  No branch leaves service and
+ * nothing is islanded (labels all 0).  The P-theta half-step solves with
+ * the base-case B' itself; the Q-V half-step's B'' gains the bus's row, and
+ * the base-case factor preconditions the other rows while that row is
+ * preconditioned by its diagonal.  Outputs, modes, the graph replay and the
+ * tile autotuner as gpcg_n1_screen.  A bus that is not PV (or out of range)
+ * is INVALID_ARG; the slack's generator cannot be tripped. */
+GPCG_API gpcg_status gpcg_n1_gen_screen(gpcg_ctx *ctx, const int32_t *gen_buses, int32_t n_out,
+                               int32_t mem, void *stream, double *theta, double *vm,
+                               double *flow, int32_t *island_label, int32_t *iters,
+                               int32_t *status, double *max_loading);
+
 /* Loss and gradients of a smooth overload penalty summed over the N-1
  * scenarios of the P-theta (DC) model (eq. (4) with |V| = 1, Sec. IV.A's
  * quick screen).  For outage l = outages[s]:

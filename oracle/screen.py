@@ -97,6 +97,17 @@ def solve_generator_outage(grid, theta0, V0, k, tol, max_outer):
                 n_overload=int((loading > 1.0).sum()), err=err, islanded=False)
 
 
+def generator_mismatch(grid, k, theta, V):
+    """Max |dP| (non-slack buses) and |dQ| (PQ buses, the tripped one
+    included) after the generator of bus k trips, at the given state."""
+    g, _ = generator_setup(grid, k)
+    on = np.ones(g.n_branch, dtype=bool)
+    yb = ybus_entries(g.n_bus, g.f, g.t, g.r, g.x, g.b_sh, on, g.tap)
+    dP, dQ = mismatch(yb, g.P_sched, g.Q_sched, theta, V)
+    return max(np.abs(dP[g.bus_type != 2]).max(initial=0.0),
+               np.abs(dQ[g.bus_type == 0]).max(initial=0.0))
+
+
 def _worker(args):
     grid, theta0, V0, ls, tol, max_outer, kind = args
     solve = solve_outage if kind == "branch" else solve_generator_outage

@@ -54,7 +54,7 @@ class Info(C.Structure):
 EXPORTS = ("gpcg_default_options", "gpcg_create", "gpcg_destroy", "gpcg_set_options",
            "gpcg_get_info", "gpcg_base_solve", "gpcg_n1_screen", "gpcg_apply",
            "gpcg_export_matrix", "gpcg_last_timings", "gpcg_n1_screen_noalloc",
-           "gpcg_n1_adjoint", "gpcg_n1_dc_screen", "gpcg_analyze",
+           "gpcg_n1_adjoint", "gpcg_n1_dc_screen", "gpcg_n1_gen_screen", "gpcg_analyze",
            "gpcg_last_error")
 
 _lib = None
@@ -218,8 +218,18 @@ class GPCG:
         _check(self._lib, self._lib.gpcg_base_solve(self._h, _ptr(th), _ptr(vm), _ptr(fl), _ptr(it)))
         return dict(theta=th, V=vm, flow=fl, iters=it)
 
+    def n1_gen_screen(self, gen_buses, outputs=("theta", "V", "flow", "label", "iters",
+                                                "status", "max_loading")):
+        """gpcg_n1_gen_screen: generator outages of the given PV buses
+        (host memory; outputs as n1_screen)."""
+        return self.n1_screen(gen_buses, outputs, _fn="gpcg_n1_gen_screen")
+
+    def n1_gen_screen_device(self, gen_buses, out: dict, stream=None):
+        """Device-memory gpcg_n1_gen_screen (arguments as n1_screen_device)."""
+        return self.n1_screen_device(gen_buses, out, stream, _fn="gpcg_n1_gen_screen")
+
     def n1_screen(self, outages, outputs=("theta", "V", "flow", "label", "iters", "status",
-                                          "max_loading")):
+                                          "max_loading"), _fn="gpcg_n1_screen"):
         """Host-memory screen: returns numpy arrays."""
         out = np.ascontiguousarray(outages, dtype=np.int32)
         S = out.shape[0]
@@ -233,19 +243,19 @@ class GPCG:
             shp, dt = spec[k]
             res[k] = np.empty(shp, dt)
         g = lambda k: _ptr(res.get(k))
-        _check(self._lib, self._lib.gpcg_n1_screen(
+        _check(self._lib, getattr(self._lib, _fn)(
             self._h, _ptr(out), S, 0, None, g("theta"), g("V"), g("flow"), g("label"),
             g("iters"), g("status"), g("max_loading")))
         return res
 
-    def n1_screen_device(self, outages, out: dict, stream=None):
+    def n1_screen_device(self, outages, out: dict, stream=None, _fn="gpcg_n1_screen"):
         """Device-memory screen: `outages` and every tensor in `out` are CUDA
         tensors (keys as in n1_screen); work is ordered on `stream`
         (a torch.cuda.Stream, default the current stream)."""
         import torch
         s = stream if stream is not None else torch.cuda.current_stream()
         g = lambda k: _ptr(out.get(k))
-        _check(self._lib, self._lib.gpcg_n1_screen(
+        _check(self._lib, getattr(self._lib, _fn)(
             self._h, _ptr(outages), int(outages.shape[0]), 1, C.c_void_p(s.cuda_stream),
             g("theta"), g("V"), g("flow"), g("label"), g("iters"), g("status"),
             g("max_loading")))

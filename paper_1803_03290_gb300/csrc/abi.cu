@@ -42,6 +42,9 @@ void launch_tail_inverse(cudaStream_t, int, int, const int32_t*, const int32_t*,
                          const double*, double*, double*, float*, float*);
 void launch_adj_values(cudaStream_t, int, const int32_t*, const double*, const double*,
                        const double*, double*, double*);
+void launch_ext_rows(cudaStream_t, int, const int32_t*, const int32_t*, const int32_t*,
+                     const int32_t*, const double*, const double*, const int32_t*, int32_t*,
+                     double*, float*, double*, float*);
 }  // namespace gpcg
 
 
@@ -108,6 +111,11 @@ struct MatDev {
   EllDev A, L, U;
   double* w = nullptr;  // per-branch weight
   double* c = nullptr;  // per-branch from-end factor (B'': 1 / turns ratio), null = 1
+  // rows for buses without one (B'': tripped generators), see DevMatT
+  const int32_t* xptr = nullptr;
+  int32_t* xrow = nullptr;
+  double *xval = nullptr, *xdiag = nullptr;
+  float *xval32 = nullptr, *xdiag32 = nullptr;
   template <typename VT>
   DevMatT<VT> view(bool f16 = false) const;
 };
@@ -130,6 +138,7 @@ DevMatT<double> MatDev::view<double>(bool) const {
   M.xc = xc; M.xr = xr;
   M.w = w;
   M.c = c;
+  M.xptr = xptr; M.xrow = xrow; M.xval = xval; M.xdiag = xdiag;
   return M;
 }
 template <>
@@ -155,6 +164,7 @@ DevMatT<float> MatDev::view<float>(bool f16) const {
   M.xr = f16 && xrh ? xrh : xr32;
   M.w = w;
   M.c = c;
+  M.xptr = xptr; M.xrow = xrow; M.xval = xval32; M.xdiag = xdiag32;
   return M;
 }
 
@@ -192,7 +202,7 @@ struct gpcg_ctx {
   bool base_ok = false;
   // per-call buffers
   int32_t *d_outages = nullptr, *d_lo = nullptr, *d_cnt = nullptr, *d_nogen = nullptr,
-          *d_order = nullptr;
+          *d_order = nullptr, *d_genbus = nullptr;
   std::vector<double> base_flow;  // |P_ij| of the base case: scheduling priority
   double* d_coef = nullptr;
   size_t sc_cap = 0;
@@ -464,6 +474,22 @@ static gpcg_status build_matrices(gpcg_ctx* c) {
   st = build_matrix(c, c->MQ, keepQ, c->wQ, c->G.cf, fill);
   if (st != GPCG_OK) return st;
   {
+    // B'' rows of PV buses, taken by a bus whose generator trips
+    MatDev& M = c->MQ;
+    auto& own = c->mat_owned;
+    const size_t na = c->bg.adj.idx.size();
+    CUDA_TRY(dalloc(own, &M.xrow, na));
+    CUDA_TRY(dalloc(own, &M.xval, na));
+    CUDA_TRY(dalloc(own, &M.xval32, na));
+    CUDA_TRY(dalloc(own, &M.xdiag, c->n));
+    CUDA_TRY(dalloc(own, &M.xdiag32, c->n));
+    M.xptr = c->G.adj_ptr;
+    launch_ext_rows(0, c->n, c->G.adj_ptr, c->G.adj_idx, c->G.adj_br, c->G.f, c->G.cf, c->wQ,
+                    M.row_of_bus, M.xrow, M.xval, M.xval32, M.xdiag, M.xdiag32);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaDeviceSynchronize());
+  }
+  {
     const MatrixPlan& Q = c->MQ.plan;
     std::vector<int32_t> order(Q.n);
     for (int k = 0; k < Q.n; ++k) order[k] = k;
@@ -492,7 +518,7 @@ static void destroy(gpcg_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   cudaFree(c->d_outages); cudaFree(c->d_lo); cudaFree(c->d_cnt); cudaFree(c->d_nogen);
-  cudaFree(c->d_coef); cudaFree(c->d_order);
+  cudaFree(c->d_coef); cudaFree(c->d_order); cudaFree(c->d_genbus);
   delete c;
 }
 
@@ -824,8 +850,8 @@ static gpcg_status ensure_scen(gpcg_ctx* c, size_t S) {
   if (S <= c->sc_cap) return GPCG_OK;
   drop_graph(c);
   cudaFree(c->d_outages); cudaFree(c->d_lo); cudaFree(c->d_cnt); cudaFree(c->d_nogen);
-  cudaFree(c->d_coef); cudaFree(c->d_order);
-  c->d_outages = c->d_lo = c->d_cnt = c->d_nogen = c->d_order = nullptr;
+  cudaFree(c->d_coef); cudaFree(c->d_order); cudaFree(c->d_genbus);
+  c->d_outages = c->d_lo = c->d_cnt = c->d_nogen = c->d_order = c->d_genbus = nullptr;
   c->d_coef = nullptr;
   c->sc_cap = 0;
   size_t cap = std::max<size_t>(S, 64);
@@ -835,6 +861,7 @@ static gpcg_status ensure_scen(gpcg_ctx* c, size_t S) {
   CUDA_TRY(cudaMalloc(&c->d_nogen, cap * 4));
   CUDA_TRY(cudaMalloc(&c->d_coef, cap * 8));
   CUDA_TRY(cudaMalloc(&c->d_order, cap * 4));
+  CUDA_TRY(cudaMalloc(&c->d_genbus, cap * 4));
   c->sc_cap = cap;
   return GPCG_OK;
 }
@@ -859,7 +886,8 @@ static Layout make_layout(const gpcg_ctx* c, int T, int slots, size_t vt_size) {
   Layout L;
   L.T = T;
   L.slots = slots;
-  const size_t rows = (size_t)std::max(c->MP.plan.n, c->MQ.plan.n) + 1;  // + the zero row
+  // B' rows + its zero row; B'' rows + its zero row + the extension row
+  const size_t rows = (size_t)std::max(c->MP.plan.n + 1, c->MQ.plan.n + 2);
   L.vstride = rows * T;
   L.sstride = (size_t)c->n * T;
   L.vec_bytes = ((L.vstride * vt_size + 255) / 256) * 256;
@@ -985,10 +1013,12 @@ struct OutBuf {
   bool owned = false;
 };
 
-extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32_t n_out,
-                                      int32_t mem, void* stream, double* theta, double* vm,
-                                      double* flow, int32_t* island_label, int32_t* iters,
-                                      int32_t* status, double* max_loading) {
+// The N-1 screen of branch outages (gen = false: `outages` are branch
+// indices) or of generator outages (gen = true: PV bus indices).
+static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n_out,
+                                  int32_t mem, void* stream, double* theta, double* vm,
+                                  double* flow, int32_t* island_label, int32_t* iters,
+                                  int32_t* status, double* max_loading, bool gen) {
   if (!c) return fail(GPCG_ERR_INVALID_ARG, "gpcg_n1_screen: ctx is NULL");
   if (n_out < 0) return fail(GPCG_ERR_INVALID_ARG, "n_out < 0");
   if (mem != GPCG_MEM_HOST && mem != GPCG_MEM_DEVICE)
@@ -1006,19 +1036,29 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
     CUDA_TRY(cudaMemcpyAsync(hout.data(), outages, S * 4, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
   }
-  for (size_t s = 0; s < S; ++s)
-    if (hout[s] < 0 || hout[s] >= c->m)
-      return fail(GPCG_ERR_INVALID_ARG, "outages[%zu] = %d is not a branch index", s, hout[s]);
+  if (gen) {
+    for (size_t s = 0; s < S; ++s) {
+      if (hout[s] < 0 || hout[s] >= c->n || c->bus_type[c->intl[hout[s]]] != GPCG_PV)
+        return fail(GPCG_ERR_INVALID_ARG, "gen_buses[%zu] = %d is not a PV bus", s, hout[s]);
+      hout[s] = c->intl[hout[s]];
+    }
+  } else {
+    for (size_t s = 0; s < S; ++s)
+      if (hout[s] < 0 || hout[s] >= c->m)
+        return fail(GPCG_ERR_INVALID_ARG, "outages[%zu] = %d is not a branch index", s, hout[s]);
+  }
   gpcg_status s_ = ensure_scen(c, S);
   if (s_ != GPCG_OK) return s_;
-  CUDA_TRY(cudaMemcpyAsync(c->d_outages, hout.data(), S * 4, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(gen ? c->d_genbus : c->d_outages, hout.data(), S * 4,
+                           cudaMemcpyHostToDevice, st));
   // scheduling order: heavily loaded branches first (their outages take the
   // most outer iterations), so the longest scenarios start earliest
   std::vector<int32_t> order(S);
   for (size_t s = 0; s < S; ++s) order[s] = (int32_t)s;
-  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-    return c->base_flow[hout[a]] > c->base_flow[hout[b]];
-  });
+  if (!gen)
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      return c->base_flow[hout[a]] > c->base_flow[hout[b]];
+    });
   CUDA_TRY(cudaMemcpyAsync(c->d_order, order.data(), S * 4, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors above go out of scope
 
@@ -1049,7 +1089,8 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
                 "output staging: %s", cudaGetErrorString(ce));
   }
   FdpfParams P = base_params(c);
-  P.sc = ScenInfo{c->d_outages, c->d_lo, c->d_cnt, c->d_coef, c->d_nogen};
+  P.sc = ScenInfo{c->d_outages, c->d_lo, c->d_cnt, c->d_coef, c->d_nogen,
+                  gen ? c->d_genbus : nullptr};
   P.th0 = c->th0;
   P.V0 = c->V0;
   P.c0 = c->c0;
@@ -1067,7 +1108,10 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
   };
   auto enqueue_islands = [&](cudaStream_t s, bool cap = false) -> cudaError_t {
     cudaError_t e = record(c->ev[0], s, cap);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && gen)
+      e = launch_gen_outages(s, (int)S, c->n, c->d_genbus, c->G.P_gen, c->isl, c->d_outages,
+                             c->d_lo, c->d_cnt, c->d_coef, c->d_nogen, d_lab);
+    else if (e == cudaSuccess)
       e = launch_islands(s, (int)S, c->n, c->d_outages, c->isl, nullptr, nullptr, c->d_lo,
                          c->d_cnt, c->d_coef, c->d_nogen, d_lab);
     if (e == cudaSuccess) e = record(c->ev[1], s, cap);
@@ -1089,7 +1133,7 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
         Q.th0 = P.th0; Q.V0 = P.V0; Q.c0 = P.c0; Q.s0 = P.s0;
         Q.S = probe;
         Q.n_tiles = (probe + t - 1) / t;
-        int ps = f32 ? fdpf_max_blocks_per_sm<float>(t) : fdpf_max_blocks_per_sm<double>(t);
+        int ps = f32 ? fdpf_max_blocks_per_sm<float>(t, gen) : fdpf_max_blocks_per_sm<double>(t, gen);
         const int sl = std::max(1, std::min(Q.n_tiles, c->num_sms * std::max(ps, 1)));
         CUDA_TRY(cudaEventRecord(c->ev[3], st));
         rs = f32 ? run_fdpf<float>(c, st, Q, t, sl, f16) : run_fdpf<double>(c, st, Q, t, sl);
@@ -1103,9 +1147,11 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
       c->tile = bestT;
     }
     T = c->opt.tile ? c->opt.tile : (c->tile ? c->tile : 2);
+    if (gen) T = std::min(T, 8);  // the generator-outage kernel comes in tiles of 2, 4, 8
     const int n_tiles = (int)((S + T - 1) / T);
     int per_sm = c->opt.ctas_per_sm;
-    if (per_sm == 0) per_sm = f32 ? fdpf_max_blocks_per_sm<float>(T) : fdpf_max_blocks_per_sm<double>(T);
+    if (per_sm == 0)
+      per_sm = f32 ? fdpf_max_blocks_per_sm<float>(T, gen) : fdpf_max_blocks_per_sm<double>(T, gen);
     per_sm = std::max(per_sm, 1);
     slots = std::max(1, std::min(n_tiles, c->num_sms * per_sm));
     P.S = (int)S;
@@ -1120,7 +1166,8 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
       FdpfParams Q = P;
       Q.S = 1;
       Q.n_tiles = 1;
-      Q.sc = ScenInfo{c->d_outages + s, c->d_lo + s, c->d_cnt + s, c->d_coef + s, c->d_nogen + s};
+      Q.sc = ScenInfo{c->d_outages + s, c->d_lo + s, c->d_cnt + s, c->d_coef + s, c->d_nogen + s,
+                      gen ? c->d_genbus + s : nullptr};
       Q.out_theta = d_theta ? d_theta + s * c->n : nullptr;
       Q.out_vm = d_vm ? d_vm + s * c->n : nullptr;
       Q.out_flow = d_flow ? d_flow + s * c->m : nullptr;
@@ -1140,7 +1187,7 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
                                   (uintptr_t)c->work, (uintptr_t)d_theta, (uintptr_t)d_vm,
                                   (uintptr_t)d_flow, (uintptr_t)d_lab, (uintptr_t)d_iters,
                                   (uintptr_t)d_stat, (uintptr_t)d_ml, (uintptr_t)c->d_outages,
-                                  (uintptr_t)c->d_order, (uintptr_t)c->d_lo};
+                                  (uintptr_t)c->d_order, (uintptr_t)c->d_lo, (uintptr_t)gen};
     {
       double opts[3] = {c->opt.tol, c->opt.inner_rtol, 0.0};
       uintptr_t bits[3];
@@ -1209,6 +1256,22 @@ extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32
   }
   g_err.clear();
   return GPCG_OK;
+}
+
+extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32_t n_out,
+                                      int32_t mem, void* stream, double* theta, double* vm,
+                                      double* flow, int32_t* island_label, int32_t* iters,
+                                      int32_t* status, double* max_loading) {
+  return n1_screen_impl(c, outages, n_out, mem, stream, theta, vm, flow, island_label, iters,
+                        status, max_loading, false);
+}
+
+extern "C" gpcg_status gpcg_n1_gen_screen(gpcg_ctx* c, const int32_t* gen_buses, int32_t n_out,
+                                          int32_t mem, void* stream, double* theta, double* vm,
+                                          double* flow, int32_t* island_label, int32_t* iters,
+                                          int32_t* status, double* max_loading) {
+  return n1_screen_impl(c, gen_buses, n_out, mem, stream, theta, vm, flow, island_label, iters,
+                        status, max_loading, true);
 }
 
 // ------------------------------------------------------------------ adjoint
@@ -1647,7 +1710,7 @@ bool ctx_view(const gpcg_ctx* c, CtxView* v) {
   v->n = c->n;
   v->m = c->m;
   v->slack = c->slack;
-  v->rows = std::max(c->MP.plan.n, c->MQ.plan.n);
+  v->rows = std::max(c->MP.plan.n, c->MQ.plan.n + 1);  // B'': + the extension row
   v->slack_user = c->slack_user;
   v->u_f = c->u_f;
   v->u_t = c->u_t;

@@ -97,6 +97,47 @@ __global__ void laplacian_values_kernel(int nrows, const int32_t* __restrict__ b
   a_val[pos] += diag;
 }
 
+// The row a bus without one would have in a matrix of branch terms w v v^T
+// (v = c e_from - e_to; cf null: c = 1), for every bus: per adjacency entry
+// the neighbour's row (-1: none) and -w c, and per bus the diagonal, summed
+// in the same order and form as laplacian_values_kernel.
+__global__ void ext_rows_kernel(int n, const int32_t* __restrict__ adj_ptr,
+                                const int32_t* __restrict__ adj_idx,
+                                const int32_t* __restrict__ adj_br,
+                                const int32_t* __restrict__ from, const double* __restrict__ cf,
+                                const double* __restrict__ w,
+                                const int32_t* __restrict__ row_of_bus, int32_t* xrow,
+                                double* xval, float* xval32, double* xdiag, float* xdiag32) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  double diag = 0.0;
+  for (int k = adj_ptr[b]; k < adj_ptr[b + 1]; ++k) {
+    const int e = adj_br[k];
+    double we = w[e];
+    if (cf) {
+      diag += from[e] == b ? we * cf[e] * cf[e] : we;
+      we *= cf[e];
+    } else {
+      diag += we;
+    }
+    xrow[k] = row_of_bus[adj_idx[k]];
+    xval[k] = -we;
+    xval32[k] = (float)-we;
+  }
+  xdiag[b] = diag;
+  xdiag32[b] = (float)diag;
+}
+
+void launch_ext_rows(cudaStream_t st, int n, const int32_t* adj_ptr, const int32_t* adj_idx,
+                     const int32_t* adj_br, const int32_t* from, const double* cf,
+                     const double* w, const int32_t* row_of_bus, int32_t* xrow, double* xval,
+                     float* xval32, double* xdiag, float* xdiag32) {
+  if (n > 0)
+    ext_rows_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, adj_ptr, adj_idx, adj_br, from, cf, w,
+                                                     row_of_bus, xrow, xval, xval32, xdiag,
+                                                     xdiag32);
+}
+
 __device__ __forceinline__ double csr_lookup(const int32_t* idx, const double* val, int s,
                                              int e, int col) {
   int lo = s, hi = e - 1;

@@ -83,6 +83,12 @@ struct DevMatT {
   // per-branch factor of the from end (B'': 1 / turns ratio; null: 1): the
   // branch adds w v v^T with v = c e_from - e_to
   const double* c = nullptr;
+  // the row a bus without one would have (B'': a PV bus whose generator
+  // trips becomes PQ): per bus-adjacency entry k (the bus CSR adjacency,
+  // xptr = its row pointer) the neighbour's row (-1: none) and the
+  // off-diagonal value, and per bus the diagonal.  Null: not supported.
+  const int32_t *xptr = nullptr, *xrow = nullptr;
+  const VT *xval = nullptr, *xdiag = nullptr;
 };
 
 // What the islanding pass leaves for each scenario.
@@ -92,6 +98,7 @@ struct ScenInfo {
   int32_t* isl_cnt = nullptr;
   double* coef = nullptr;      // re-dispatch: P_gen multiplier
   int32_t* no_gen = nullptr;
+  int32_t* gen_bus = nullptr;  // tripped generator's bus (-1: none); null: none in the call
 };
 
 __device__ __forceinline__ bool in_island(int32_t pre, int32_t lo, int32_t cnt) {
@@ -123,5 +130,12 @@ cudaError_t launch_islands(cudaStream_t st, int S, int n, const int32_t* outages
                            const IslandPlan& I, const double* P_user, double* prefP_scratch,
                            int32_t* isl_lo, int32_t* isl_cnt, double* coef, int32_t* no_gen,
                            int32_t* label_out);
+// Generator outages of S PV buses (internal indices): per-scenario data as
+// launch_islands leaves it (no branch out, nothing islanded) and the
+// re-dispatch of the tripped generation; labels all 0 when requested.
+cudaError_t launch_gen_outages(cudaStream_t st, int S, int n, const int32_t* gen_bus,
+                               const double* P_gen, const IslandPlan& I, int32_t* outage,
+                               int32_t* isl_lo, int32_t* isl_cnt, double* coef, int32_t* no_gen,
+                               int32_t* label_out);
 
 }  // namespace gpcg

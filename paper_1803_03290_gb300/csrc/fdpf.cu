@@ -1,575 +1,10 @@
-// The persistent N-1 kernel: one CTA owns a tile of T scenarios and runs the
-// whole fast-decoupled power flow of that tile (Sec. III.B eqs. (4)-(5),
-// Sec. IV) without leaving the kernel, then takes the next tile from a
-// device-side counter.  Vectors live in global memory as [row][T] per CTA
-// slot, so a row touches one contiguous chunk across the tile's scenarios;
-// each thread owns two adjacent scenario lanes of a row.  Tiles are
-// independent: the only inter-CTA traffic is the atomic tile counter, and no
-// CTA ever waits on another.
-//
-// Per outer iteration and scenario (Sec. III.B, eqs. (4)-(5)):
-//   FP64 mismatch dP, dQ (eqs. (1)-(3)), convergence test;
-//   PCG on B'_s dtheta = dP/V preconditioned by the base-case factor
-//   (Sec. IV.B eq. (6)); theta += dtheta (FP64);
-//   FP64 mismatch dQ; PCG on B''_s dV = dQ/V; V += dV (FP64).
-// B'_s and B''_s are the base-case matrices with the outaged branch's
-// four-element change (Sec. IV.B) applied on the fly inside the SpMV.
-// Islanded buses (Sec. IV.C) are masked out of the right-hand side and of
-// the search directions; their state stays zero.
-//
-// Every sparse row is read through a padded descriptor (ELL): its column
-// indices and values sit at fixed offsets, so a thread issues all of a row's
-// gathers at once instead of walking a row pointer first.
-#include <math.h>
-#include "common.cuh"
-#include "fdpf.h"
-#include "fdpf_ops.cuh"
+// Instantiation of the persistent N-1 kernel (fdpf_kernel.cuh) for branch
+// outages, the batched operator application used to verify the operators,
+// and the base-case helpers.  The generator-outage kernel is built in
+// fdpf_gen.cu.
+#include "fdpf_kernel.cuh"
 
 namespace gpcg {
-
-// ------------------------------------------------------------ mismatch
-// The rectangular voltages e + jf of a slot are stored interleaved,
-// [bus][lane][e, f], so one 16-byte load gives a lane's (e, f) and a thread's
-// two lanes sit in 32 contiguous bytes.
-template <int T>
-__device__ __forceinline__ size_t ef_at(int bus, int lane) {
-  return ((size_t)bus * T + lane) * 2;
-}
-
-// dP_i, dQ_i of eqs. (1)-(3) from the rectangular voltages:
-// I = Y V, P + jQ = V conj(I).  The outaged branch is left out of the
-// neighbour sum and of the diagonal.  WITH_P: the P half-step (writes
-// dP/V into the B' right-hand side and tracks max|dP| and max|dQ| for the
-// convergence test); otherwise writes dQ/V into the B'' right-hand side.
-// A thread takes a bus and its lanes two at a time: each neighbour's
-// admittance and the pair's voltages are loaded once for the two lanes.
-template <int T, typename VT, bool WITH_P>
-__device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMatT<VT>& MP,
-                                               const DevMatT<VT>& MQ, LaneState<T>& L,
-                                               const double* __restrict__ EF,
-                                               const double* __restrict__ V,
-                                               VT* __restrict__ rhs,
-                                               Vec<unsigned long long, Geo<T>::LP>& errP,
-                                               Vec<unsigned long long, Geo<T>::LP>& errQ) {
-  constexpr int LP = Geo<T>::LP;
-  const Geo<T> g;
-  const DevGrid& G = P.G;
-  // rows are visited in order of bus degree, so the threads of a warp run
-  // neighbour loops of equal length and no FP64 work is spent on padding
-  const int nrows = WITH_P ? G.n - 1 : MQ.n;
-  const int32_t* order = WITH_P ? P.mis_order : P.misq_order;
-  int kn = 0, nbn[KG];
-  if (g.rs < nrows) {
-    kn = __ldg(order + g.rs);
-    ld_cols<KG>(G.adj_nbr + (size_t)(WITH_P ? kn : __ldg(MQ.bus_of_row + kn)) * KG, nbn);
-  }
-  for (int kk = g.rs; kk < nrows; kk += Geo<T>::RPS) {
-    const int k = kn;
-    int nb[KG];
-#pragma unroll
-    for (int a = 0; a < KG; ++a) nb[a] = nbn[a];
-    if (kk + Geo<T>::RPS < nrows) {
-      kn = __ldg(order + kk + Geo<T>::RPS);
-      ld_cols<KG>(G.adj_nbr + (size_t)(WITH_P ? kn : __ldg(MQ.bus_of_row + kn)) * KG, nbn);
-    }
-    const int i = WITH_P ? k : __ldg(MQ.bus_of_row + k);
-    const int pr = __ldg(G.pre + i);
-    const int deg = __ldg(G.adj_deg + i);
-    Vec<VT, LP> out = vzero<VT, LP>();
-#pragma unroll 1
-    for (int jp = 0; jp < LP; jp += 2) {
-      const int l0 = g.lane + jp, l1 = l0 + 1;
-      const bool on0 = L.active[l0] && !in_island(pr, L.lo[l0], L.cnt[l0]);
-      const bool on1 = L.active[l1] && !in_island(pr, L.lo[l1], L.cnt[l1]);
-      if (!(on0 || on1)) continue;
-      const int br0 = L.l[l0], br1 = L.l[l1];
-      // a lane's first P half-step away from the ends of its outaged branch:
-      // the base-case mismatch holds (the state is the base case there)
-      bool w0 = false, w1 = false;
-      if (WITH_P && P.r0P) {
-        w0 = on0 && L.outer[l0] == 0 && i != L.fb[l0] && i != L.tb[l0];
-        w1 = on1 && L.outer[l1] == 0 && i != L.fb[l1] && i != L.tb[l1];
-      }
-      const bool n0 = on0 && !w0, n1 = on1 && !w1;  // lanes that sum the neighbours
-      // -sum over the neighbours of Y_ij V_j, both lanes of the pair
-      double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
-      if (n0 || n1) {
-#pragma unroll
-      for (int a0 = 0; a0 < KG; a0 += MIS_GROUP) {
-        double2 u0[MIS_GROUP], u1[MIS_GROUP];
-        double gv[MIS_GROUP], bv[MIS_GROUP];
-        int bb[MIS_GROUP];
-#pragma unroll
-        for (int a = 0; a < MIS_GROUP; ++a)
-          if (a0 + a < deg) {
-            const double2* q2 = reinterpret_cast<const double2*>(EF + ef_at<T>(nb[a0 + a], l0));
-            u0[a] = q2[0];
-            u1[a] = q2[1];
-            gv[a] = __ldg(G.adj_g + (size_t)i * KG + a0 + a);
-            bv[a] = __ldg(G.adj_b + (size_t)i * KG + a0 + a);
-            bb[a] = __ldg(G.adj_brl + (size_t)i * KG + a0 + a);
-          }
-#pragma unroll
-        for (int a = 0; a < MIS_GROUP; ++a)
-          if (a0 + a < deg) {
-            if (n0 && bb[a] != br0) {
-              re0 = fma(-gv[a], u0[a].x, fma(bv[a], u0[a].y, re0));
-              im0 = fma(-gv[a], u0[a].y, fma(-bv[a], u0[a].x, im0));
-            }
-            if (n1 && bb[a] != br1) {
-              re1 = fma(-gv[a], u1[a].x, fma(bv[a], u1[a].y, re1));
-              im1 = fma(-gv[a], u1[a].y, fma(-bv[a], u1[a].x, im1));
-            }
-          }
-      }
-      const int o0 = __ldg(G.adj_optr + i), o1 = __ldg(G.adj_optr + i + 1);
-      for (int e = o0; e < o1; ++e) {
-        const int jn = __ldg(G.adj_onbr + e), b_ = __ldg(G.adj_obr + e);
-        const double gw = __ldg(G.adj_og + e), bw = __ldg(G.adj_ob + e);
-        const double2* q2 = reinterpret_cast<const double2*>(EF + ef_at<T>(jn, l0));
-        const double2 v0 = q2[0], v1 = q2[1];
-        if (n0 && b_ != br0) {
-          re0 = fma(-gw, v0.x, fma(bw, v0.y, re0));
-          im0 = fma(-gw, v0.y, fma(-bw, v0.x, im0));
-        }
-        if (n1 && b_ != br1) {
-          re1 = fma(-gw, v1.x, fma(bw, v1.y, re1));
-          im1 = fma(-gw, v1.y, fma(-bw, v1.x, im1));
-        }
-      }
-      }
-      // own voltage, the diagonal term and the mismatch of each lane
-      const double2* own = reinterpret_cast<const double2*>(EF + ef_at<T>(i, l0));
-      const double2 ev0 = own[0], ev1 = own[1];
-      const Pair<double> vi = ld2(V + (size_t)i * T + l0);
-      const int bt = G.bus_type[i];
-      const double Gii = __ldg(G.Gii + i), Bii = __ldg(G.Bii + i), qs = __ldg(G.Q_sched + i);
-      double Ps = 0.0, pg = 0.0;
-      if (WITH_P) {
-        Ps = __ldg(G.P_sched + i);
-        if (bt == 1) pg = fmax(__ldg(G.P_gen + i), 0.0);  // generators with P_gen > 0 take it
-      }
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        if (!(j ? on1 : on0)) continue;
-        const int ln = j ? l1 : l0;
-        if (j ? w1 : w0) {
-          const double dP = fma(L.coef[ln], pg, __ldg(P.r0P + i));
-          upd_max_bits(errP.v[jp + j], dP);
-          if (bt == 0) upd_max_bits(errQ.v[jp + j], __ldg(P.r0Q + i));
-          out.v[jp + j] = to_vt<VT>(dP) / to_vt<VT>(j ? vi.b : vi.a);
-          continue;
-        }
-        const double ei = j ? ev1.x : ev0.x, fi = j ? ev1.y : ev0.y;
-        double Gd = Gii, Bd = Bii;
-        if (i == L.fb[ln] || i == L.tb[ln]) {  // the outaged branch's share
-          const double c2 = i == L.fb[ln] ? L.cl[ln] * L.cl[ln] : 1.0;
-          Gd -= c2 * L.gl[ln];
-          Bd -= c2 * L.bl[ln];
-        }
-        // I_i = Y_ii V_i + sum_j Y_ij V_j
-        const double re = fma(Gd, ei, fma(-Bd, fi, j ? re1 : re0));
-        const double im = fma(Gd, fi, fma(Bd, ei, j ? im1 : im0));
-        // dQ = Q_sched - Im(V_i conj(I_i)); dP = P_sched + re-dispatch - Re(...)
-        VT res;
-        if (WITH_P) {
-          const double dP = fma(-ei, re, fma(-fi, im, fma(L.coef[ln], pg, Ps)));
-          upd_max_bits(errP.v[jp + j], dP);
-          if (bt == 0) upd_max_bits(errQ.v[jp + j], fma(-fi, re, fma(ei, im, qs)));
-          res = to_vt<VT>(dP) / to_vt<VT>(j ? vi.b : vi.a);
-        } else {
-          const double dQ = fma(-fi, re, fma(ei, im, qs));
-          res = to_vt<VT>(dQ) / to_vt<VT>(j ? vi.b : vi.a);
-        }
-        out.v[jp + j] = res;
-      }
-    }
-    if (WITH_P) stv<LP>(rhs + (size_t)__ldg(MP.row_of_bus + i) * T + g.lane, out);
-    else stv<LP>(rhs + (size_t)k * T + g.lane, out);
-  }
-}
-
-// (cos, sin) of theta + d from those of theta, by rotating through d:
-//   c' = c - (c (1 - cos d) + s sin d),   s' = s - (s (1 - cos d) - c sin d).
-// For |d| <= 0.05 the two corrections are small (about |d|), so they are
-// formed in FP32 from the Taylor series of 1 - cos d and sin d (three terms
-// each; remainders below 4e-12 relative) and applied in FP64: their rounding
-// error, 6e-8 of |d|, vanishes as the iteration converges (the outer FDPF
-// loop sees the state through e + jf and corrects any drift).  d itself is
-// the FP32 solution of the inner solve.  Larger steps recompute the angle.
-template <typename VT>
-__device__ __forceinline__ void rotate(double th_new, VT d, double& c, double& s) {
-  if (fabs(d) <= (VT)0.05) {
-    const float df = to_f32(d), d2 = df * df;
-    const float omc = d2 * (0.5f - d2 * (1.0f / 24.0f - d2 * (1.0f / 720.0f)));
-    const float sd = df * (1.0f - d2 * (1.0f / 6.0f - d2 * (1.0f / 120.0f)));
-    const float cf = cvt_f32(c), sf = cvt_f32(s);
-    const float dc = fmaf(cf, omc, sf * sd), ds = fmaf(sf, omc, -cf * sd);
-    c -= cvt_f64(dc);
-    s -= cvt_f64(ds);
-  } else {
-    sincos(th_new, &s, &c);
-  }
-}
-
-// theta += dtheta (P half-step) or |V| += dV (Q half-step) on the matrix's
-// rows, then refresh the rectangular voltages; lanes two at a time.
-template <int T, typename VT, bool IS_P>
-__device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>& L,
-                                             const VT* __restrict__ x,
-                                             const VT* __restrict__ p, double* th, double* V,
-                                             double* C, double* Sn, double* EF) {
-  constexpr int LP = Geo<T>::LP;
-  const Geo<T> g;
-  bool any = false;
-#pragma unroll
-  for (int j = 0; j < LP; ++j) any |= L.active[g.lane + j] != 0;
-  if (!any) return;
-  for (int k = g.rs; k < M.n; k += Geo<T>::RPS) {
-    const int pr = __ldg(M.pre_of_row + k);
-    const int i = __ldg(M.bus_of_row + k);
-#pragma unroll 1
-    for (int jp = 0; jp < LP; jp += 2) {
-      const int l0 = g.lane + jp, l1 = l0 + 1;
-      const bool on0 = L.active[l0] && !in_island(pr, L.lo[l0], L.cnt[l0]);
-      const bool on1 = L.active[l1] && !in_island(pr, L.lo[l1], L.cnt[l1]);
-      if (!on0 && !on1) continue;
-      const size_t o = (size_t)i * T + l0;
-      Pair<VT> dx = ld2(x + (size_t)k * T + l0);
-      // the inner solve's deferred last step, x += alpha p
-      const VT xa0 = (VT)L.xalpha[l0], xa1 = (VT)L.xalpha[l1];
-      if (xa0 != (VT)0 || xa1 != (VT)0) {
-        const Pair<VT> pv = ld2(p + (size_t)k * T + l0);
-        dx.a = fma(xa0, pv.a, dx.a);  // as the solve's own step would take it
-        dx.b = fma(xa1, pv.b, dx.b);
-      }
-      if (!on0) dx.a = (VT)0;
-      if (!on1) dx.b = (VT)0;
-      const double d0 = to_f64(dx.a), d1 = to_f64(dx.b);
-      Pair<double> c = ld2(C + o), s = ld2(Sn + o), v = ld2(V + o);
-      if (IS_P) {
-        Pair<double> t = ld2(th + o);
-        t.a += d0;
-        t.b += d1;
-        if (on0) rotate(t.a, dx.a, c.a, s.a);
-        if (on1) rotate(t.b, dx.b, c.b, s.b);
-        st2(th + o, t);
-        st2(C + o, c);
-        st2(Sn + o, s);
-      } else {
-        v.a += d0;
-        v.b += d1;
-        st2(V + o, v);
-      }
-      double2* ef = reinterpret_cast<double2*>(EF + ef_at<T>(i, l0));
-      ef[0] = make_double2(v.a * c.a, v.a * s.a);
-      ef[1] = make_double2(v.b * c.b, v.b * s.b);
-    }
-  }
-}
-
-// ------------------------------------------------------------ the kernel
-// Scenario info of a lane taking scenario s (thread `ln`, one per lane).
-template <int T, typename VT>
-__device__ __forceinline__ void setup_lane(const FdpfParams& P, const DevMatT<VT>& MP,
-                                           const DevMatT<VT>& MQ, LaneState<T>& L, int ln) {
-  const DevGrid& G = P.G;
-  const int s = L.scen[ln];
-  const int l = P.sc.outage[s];
-  L.l[ln] = l;
-  L.fb[ln] = l >= 0 ? G.f[l] : -1;
-  L.tb[ln] = l >= 0 ? G.t[l] : -1;
-  L.lo[ln] = P.sc.isl_lo[s];
-  L.cnt[ln] = P.sc.isl_cnt[s];
-  L.coef[ln] = P.sc.coef[s];
-  L.nogen[ln] = P.sc.no_gen[s];
-  L.raP[ln] = l >= 0 ? MP.row_of_bus[G.f[l]] : -1;
-  L.rbP[ln] = l >= 0 ? MP.row_of_bus[G.t[l]] : -1;
-  L.raQ[ln] = l >= 0 ? MQ.row_of_bus[G.f[l]] : -1;
-  L.rbQ[ln] = l >= 0 ? MQ.row_of_bus[G.t[l]] : -1;
-  L.wP[ln] = l >= 0 ? MP.w[l] : 0.0;
-  L.wQ[ln] = l >= 0 ? MQ.w[l] : 0.0;
-  L.gl[ln] = l >= 0 ? G.g[l] : 0.0;
-  L.bl[ln] = l >= 0 ? G.by[l] + 0.5 * G.b_sh[l] : 0.0;
-  L.cl[ln] = l >= 0 ? G.cf[l] : 1.0;
-  L.active[ln] = 1;
-  L.outer[ln] = 0;
-  L.inP[ln] = 0;
-  L.inQ[ln] = 0;
-  L.status[ln] = 0;
-  L.err[ln] = 0.0;
-  L.best[ln] = INFINITY;
-}
-
-// Warm start (Sec. III.B) of the lanes flagged `fresh`: the base-case state,
-// zero on islanded buses.  Other lanes keep their state.
-template <int T>
-__device__ GPCG_PASS_INLINE void init_pass(const FdpfParams& P, LaneState<T>& L, double* th,
-                                           double* V, double* C, double* Sn, double* EF) {
-  constexpr int LP = Geo<T>::LP;
-  const Geo<T> g;
-  const DevGrid& G = P.G;
-  int fresh = 0;
-#pragma unroll
-  for (int j = 0; j < LP; ++j) fresh |= (L.fresh[g.lane + j] != 0) << j;
-  if (!fresh) return;
-  for (int i = g.rs; i < G.n; i += Geo<T>::RPS) {
-    double t0, v0, c0, s0;
-    if (P.flat_start) { t0 = 0.0; v0 = G.V_set[i]; c0 = 1.0; s0 = 0.0; }
-    else { t0 = P.th0[i]; v0 = P.V0[i]; c0 = P.c0[i]; s0 = P.s0[i]; }
-    const int pr = G.pre[i];
-#pragma unroll
-    for (int j = 0; j < LP; ++j) {
-      if (!((fresh >> j) & 1)) continue;
-      const int ln = g.lane + j;
-      const size_t o = (size_t)i * T + ln;
-      const bool isl = in_island(pr, L.lo[ln], L.cnt[ln]);
-      th[o] = isl ? 0.0 : t0;
-      V[o] = isl ? 0.0 : v0;
-      C[o] = c0;
-      Sn[o] = s0;
-      reinterpret_cast<double2*>(EF + ef_at<T>(i, ln))[0] =
-          isl ? make_double2(0.0, 0.0) : make_double2(v0 * c0, v0 * s0);
-    }
-  }
-}
-
-// Outputs of the lanes flagged `done`: state, branch flows and loading
-// (Sec. I: overload screening), status and iteration counts.
-template <int T>
-__device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& L,
-                                             const double* th, const double* V,
-                                             const double* EF) {
-  constexpr int LP = Geo<T>::LP;
-  const Geo<T> g;
-  const DevGrid& G = P.G;
-  int dn = 0;
-#pragma unroll
-  for (int j = 0; j < LP; ++j) dn |= (L.done[g.lane + j] != 0) << j;
-  if ((P.out_theta || P.out_vm) && dn) {
-    for (int i = g.rs; i < G.n; i += Geo<T>::RPS) {
-      const int iu = P.out_bus_map ? __ldg(P.out_bus_map + i) : i;
-#pragma unroll
-      for (int j = 0; j < LP; ++j) {
-        if (!((dn >> j) & 1)) continue;
-        const int ln = g.lane + j, s = L.scen[ln];
-        const size_t o = (size_t)i * T + ln;
-        if (P.out_theta) P.out_theta[(size_t)s * G.n + iu] = th[o];
-        if (P.out_vm) P.out_vm[(size_t)s * G.n + iu] = V[o];
-      }
-    }
-  }
-  Vec<unsigned long long, LP> ml = vzero<unsigned long long, LP>();  // abs_bits patterns
-  if (dn) {
-    for (int k = g.rs; k < G.m; k += Geo<T>::RPS) {
-      const int a = __ldg(G.f + k), b = __ldg(G.t + k);
-      const int pa = __ldg(G.pre + a), pb = __ldg(G.pre + b);
-      const double gk = __ldg(G.g + k), bk = __ldg(G.by + k), ir = __ldg(G.inv_rating + k);
-      const double ck = __ldg(G.cf + k);  // 1 / turns ratio at a (1 for a line)
-#pragma unroll 1
-      for (int jp = 0; jp < LP; jp += 2) {
-        if (!((dn >> jp) & 3)) continue;
-        const double2* qa = reinterpret_cast<const double2*>(EF + ef_at<T>(a, g.lane + jp));
-        const double2* qb = reinterpret_cast<const double2*>(EF + ef_at<T>(b, g.lane + jp));
-        const double2 va[2] = {qa[0], qa[1]}, vb[2] = {qb[0], qb[1]};
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int j = jp + h, ln = g.lane + j;
-          if (!((dn >> j) & 1)) continue;
-          const int lo = L.lo[ln], cnt = L.cnt[ln];
-          double Pab = 0.0;
-          if (k != L.l[ln] && !in_island(pa, lo, cnt) && !in_island(pb, lo, cnt)) {
-            // P_ab = c^2 g |V_a|^2 - c (g Re(V_a conj V_b) + b Im(V_a conj V_b)),
-            // P_ba = g |V_b|^2 - c (g Re(V_a conj V_b) - b Im(V_a conj V_b)),
-            // c = 1 / turns ratio at a (the pi-model sees V_a c)
-            const double ea = va[h].x, fa = va[h].y, eb = vb[h].x, fb = vb[h].y;
-            const double cr = ck * fma(ea, eb, fa * fb), sr = ck * fma(fa, eb, -ea * fb);
-            const double gc = gk * cr;
-            Pab = fma(gk * ck * ck, fma(ea, ea, fa * fa), -fma(bk, sr, gc));
-            const double Pba = fma(gk, fma(eb, eb, fb * fb), fma(bk, sr, -gc));
-            // loading max(|P_ab|, |P_ba|) / rating: the larger end picked on
-            // the bit patterns, one multiplication
-            const unsigned long long u = abs_bits(Pab), v = abs_bits(Pba);
-            upd_max_bits(ml.v[j], __longlong_as_double((long long)(u > v ? u : v)) * ir);
-          }
-          if (P.out_flow) P.out_flow[(size_t)L.scen[ln] * G.m + k] = Pab;
-        }
-      }
-    }
-  }
-  const Vec<unsigned long long, LP> mlb = lane_max_bits<T, RS_LOAD>(L, ml);
-  if (g.rs == 0) {
-#pragma unroll
-    for (int j = 0; j < LP; ++j) {
-      const int ln = g.lane + j, s = L.scen[ln];
-      if (!L.done[ln] || s < 0) continue;
-      int st = L.status[ln];
-      if (st == 0 && L.nogen[ln]) st = 3;
-      if (P.out_status) P.out_status[s] = st;
-      if (P.out_iters) {
-        P.out_iters[(size_t)s * 3 + 0] = L.outer[ln];
-        P.out_iters[(size_t)s * 3 + 1] = L.inP[ln];
-        P.out_iters[(size_t)s * 3 + 2] = L.inQ[ln];
-      }
-      if (P.out_maxload) P.out_maxload[s] = from_bits(mlb.v[j]);
-      L.done[ln] = 0;
-      L.scen[ln] = -1;
-    }
-  }
-  __syncthreads();
-}
-
-// One persistent CTA = one slot of T scenario lanes.  Lanes draw scenarios
-// from a device-side queue (in the order P.order gives); a lane whose
-// scenario has converged, failed or diverged is retired at the next outer
-// iteration and immediately refilled, so converged scenarios never hold a
-// lane (the slot's lanes are compacted onto live work) and the kernel ends
-// when the queue is drained and every lane has retired.
-template <int T, typename VT>
-__global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
-    fdpf_tiles_kernel(FdpfParams P_, DevMatT<VT> MP_, DevMatT<VT> MQ_) {
-  __shared__ LaneState<T> L;
-  // the parameter blocks in shared memory: the out-of-line passes take them
-  // by reference, so their fields are read from shared memory rather than
-  // from a per-thread local copy
-  __shared__ __align__(16) unsigned char pbuf[sizeof(FdpfParams)];
-  __shared__ __align__(16) unsigned char mbuf[2][sizeof(DevMatT<VT>)];
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    memcpy(pbuf, &P_, sizeof(FdpfParams));
-    memcpy(mbuf[0], &MP_, sizeof(DevMatT<VT>));
-    memcpy(mbuf[1], &MQ_, sizeof(DevMatT<VT>));
-  }
-  __syncthreads();
-  const FdpfParams& P = *reinterpret_cast<const FdpfParams*>(pbuf);
-  const DevMatT<VT>& MP = *reinterpret_cast<const DevMatT<VT>*>(mbuf[0]);
-  const DevMatT<VT>& MQ = *reinterpret_cast<const DevMatT<VT>*>(mbuf[1]);
-  constexpr int LP = Geo<T>::LP;
-  const Geo<T> g;
-  VT* x = (VT*)P.wx + (size_t)blockIdx.x * P.vstride;
-  VT* r = (VT*)P.wr + (size_t)blockIdx.x * P.vstride;
-  VT* p = (VT*)P.wp + (size_t)blockIdx.x * P.vstride;
-  VT* q = (VT*)P.wq + (size_t)blockIdx.x * P.vstride;
-  VT* z = (VT*)P.wz + (size_t)blockIdx.x * P.vstride;
-  const size_t so = (size_t)blockIdx.x * P.sstride;
-  // E and F regions of the slots taken together: [slot][bus][lane][e, f]
-  double *th = P.wth + so, *V = P.wV + so, *C = P.wc + so, *Sn = P.ws + so, *EF = P.we + 2 * so;
-
-  // optional per-phase cycle counters (thread 0's view of the CTA)
-  const bool tim = P.phase_cycles != nullptr;
-  long long t_prev = 0;
-  if (tid == 0) {
-    for (int k = 0; k < 8; ++k) L.tphase[k] = 0;
-    t_prev = clock64();
-    L.drained = 0;
-  }
-  if (tid < T) {
-    // a lane the queue never fills keeps these: no outage, nothing islanded
-    L.scen[tid] = -1;
-    L.active[tid] = 0;
-    L.done[tid] = 0;
-    L.fresh[tid] = 0;
-    L.l[tid] = L.fb[tid] = L.tb[tid] = -1;
-    L.raP[tid] = L.rbP[tid] = L.raQ[tid] = L.rbQ[tid] = -1;
-    L.wP[tid] = L.wQ[tid] = 0.0;
-    L.cl[tid] = 1.0;
-    L.lo[tid] = L.cnt[tid] = 0;
-  }
-  __syncthreads();
-#define GPCG_PHASE(k)                                  \
-  if (tim && tid == 0) {                               \
-    const long long t_ = clock64();                    \
-    L.tphase[k] += (unsigned long long)(t_ - t_prev);  \
-    t_prev = t_;                                       \
-  }
-
-  for (;;) {
-    // retire finished lanes, then refill empty lanes from the queue
-    if (any_lane<T>(L, L.done)) retire_pass<T>(P, L, th, V, EF);
-    GPCG_PHASE(7);
-    if (tid == 0 && !L.drained) {
-      int need = 0;
-      for (int s = 0; s < T; ++s) need += (L.scen[s] < 0);
-      if (need) {
-        const int base = atomicAdd(P.tile_counter, need);
-        int j = 0;
-        for (int s = 0; s < T; ++s) {
-          if (L.scen[s] >= 0) continue;
-          const int qi = base + j++;
-          if (qi < P.S) {
-            L.scen[s] = P.order ? P.order[qi] : qi;
-            L.fresh[s] = 1;
-          }
-        }
-        if (base + need >= P.S) L.drained = 1;
-      }
-    }
-    __syncthreads();
-    if (tid < T && L.fresh[tid]) setup_lane<T, VT>(P, MP, MQ, L, tid);
-    __syncthreads();
-    init_pass<T>(P, L, th, V, C, Sn, EF);
-    __syncthreads();
-    if (tid < T) L.fresh[tid] = 0;
-    GPCG_PHASE(0);
-    if (!any_lane<T>(L, L.active)) {
-      if (L.drained) break;
-      continue;
-    }
-    // P half-step: mismatch + convergence test
-    Vec<unsigned long long, LP> eP = vzero<unsigned long long, LP>(), eQ = eP;
-    mismatch_pass<T, VT, true>(P, MP, MQ, L, EF, V, r, eP, eQ);
-    const Vec<unsigned long long, LP> bP = lane_max_bits<T, RS_ERRP>(L, eP);
-    const Vec<unsigned long long, LP> bQ = lane_max_bits<T, RS_ERRQ>(L, eQ);
-    if (g.rs == 0) {
-#pragma unroll
-      for (int j = 0; j < LP; ++j) {
-        const int ln = g.lane + j;
-        if (!L.active[ln]) continue;
-        const double a = from_bits(bP.v[j]), b = from_bits(bQ.v[j]);
-        const double e2 = (a != a || b != b) ? INFINITY : fmax(a, b);
-        L.err[ln] = e2;
-        int st = -1;
-        // growth rule only for warm-started scenarios: a flat start may pass
-        // through large mismatches on its way
-        if (!(e2 <= DIVERGE_LIMIT) || (!P.flat_start && e2 > DIVERGE_GROWTH * L.best[ln])) st = 2;
-        else if (e2 <= P.tol) st = 0;
-        else if (L.outer[ln] >= P.max_outer) st = 1;
-        L.best[ln] = fmin(L.best[ln], e2);
-        if (st >= 0) {
-          L.status[ln] = st;
-          L.active[ln] = 0;
-          L.done[ln] = 1;
-        }
-      }
-    }
-    const bool more = any_lane<T>(L, L.active);
-    GPCG_PHASE(1);
-    if (!more) continue;
-    pcg_solve<T, VT, true>(P, MP, L, x, r, p, q, z, L.raP, L.rbP, L.wP, L.inP);
-    GPCG_PHASE(2);
-    update_pass<T, VT, true>(MP, L, x, p, th, V, C, Sn, EF);
-    __syncthreads();
-    GPCG_PHASE(3);
-    // Q half-step
-    Vec<unsigned long long, LP> d0 = vzero<unsigned long long, LP>(), d1 = d0;
-    mismatch_pass<T, VT, false>(P, MP, MQ, L, EF, V, r, d0, d1);
-    __syncthreads();
-    GPCG_PHASE(4);
-    pcg_solve<T, VT, true>(P, MQ, L, x, r, p, q, z, L.raQ, L.rbQ, L.wQ, L.inQ,
-                           MQ.c ? L.cl : nullptr);
-    GPCG_PHASE(5);
-    update_pass<T, VT, false>(MQ, L, x, p, th, V, C, Sn, EF);
-    if (g.rs == 0)
-#pragma unroll
-      for (int j = 0; j < LP; ++j)
-        if (L.active[g.lane + j]) L.outer[g.lane + j] += 1;
-    __syncthreads();
-    GPCG_PHASE(6);
-  }
-  if (tim && tid == 0)
-    for (int k = 0; k < 8; ++k) atomicAdd(P.phase_cycles + k, L.tphase[k]);
-#undef GPCG_PHASE
-}
 
 // Batched operator application for verification (gpcg_apply): X and Y are
 // [S][rows]; each CTA handles tiles of T scenarios.
@@ -676,38 +111,16 @@ __global__ void base_trig_kernel(int n, const double* th, double* c, double* s) 
 }
 
 // ----------------------------------------------------------- launchers
-template <int T, typename VT>
-cudaError_t launch_fdpf_t(cudaStream_t st, int grid, const FdpfParams& P, const DevMatT<VT>& MP,
-                          const DevMatT<VT>& MQ) {
-  fdpf_tiles_kernel<T, VT><<<grid, NTHREADS, 0, st>>>(P, MP, MQ);
-  return cudaGetLastError();
-}
-
 template <typename VT>
 cudaError_t launch_fdpf(cudaStream_t st, int T, int grid, const FdpfParams& P,
                         const DevMatT<VT>& MP, const DevMatT<VT>& MQ) {
-  switch (T) {
-    case 2: return launch_fdpf_t<2, VT>(st, grid, P, MP, MQ);
-    case 4: return launch_fdpf_t<4, VT>(st, grid, P, MP, MQ);
-    case 8: return launch_fdpf_t<8, VT>(st, grid, P, MP, MQ);
-    case 16: return launch_fdpf_t<16, VT>(st, grid, P, MP, MQ);
-    case 32: return launch_fdpf_t<32, VT>(st, grid, P, MP, MQ);
-    default: return cudaErrorInvalidValue;
-  }
+  if (P.sc.gen_bus) return launch_fdpf_gen<VT>(st, T, grid, P, MP, MQ);
+  return launch_fdpf_g<false, VT>(st, T, grid, P, MP, MQ);
 }
 
 template <typename VT>
-int fdpf_max_blocks_per_sm(int T) {
-  int nb = 0;
-  cudaError_t ce = cudaErrorInvalidValue;
-  switch (T) {
-    case 2: ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fdpf_tiles_kernel<2, VT>, NTHREADS, 0); break;
-    case 4: ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fdpf_tiles_kernel<4, VT>, NTHREADS, 0); break;
-    case 8: ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fdpf_tiles_kernel<8, VT>, NTHREADS, 0); break;
-    case 16: ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fdpf_tiles_kernel<16, VT>, NTHREADS, 0); break;
-    case 32: ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fdpf_tiles_kernel<32, VT>, NTHREADS, 0); break;
-  }
-  return ce == cudaSuccess ? nb : 0;
+int fdpf_max_blocks_per_sm(int T, bool gen) {
+  return gen ? fdpf_blocks_gen<VT>(T) : fdpf_blocks_g<false, VT>(T);
 }
 
 template <typename VT>
@@ -728,8 +141,8 @@ template cudaError_t launch_fdpf<float>(cudaStream_t, int, int, const FdpfParams
                                         const DevMatT<float>&, const DevMatT<float>&);
 template cudaError_t launch_fdpf<double>(cudaStream_t, int, int, const FdpfParams&,
                                          const DevMatT<double>&, const DevMatT<double>&);
-template int fdpf_max_blocks_per_sm<float>(int);
-template int fdpf_max_blocks_per_sm<double>(int);
+template int fdpf_max_blocks_per_sm<float>(int, bool);
+template int fdpf_max_blocks_per_sm<double>(int, bool);
 template cudaError_t launch_apply<float>(cudaStream_t, int, const DevMatT<float>&, int, int,
                                          const int32_t*, const int32_t*, const int32_t*,
                                          const double*, double*, float*, size_t, int);

@@ -38,11 +38,19 @@ struct FdpfParams {
   const int32_t* misq_order = nullptr;  // B'' rows sorted by their bus's degree
 };
 
+// The persistent N-1 kernel for tiles of T scenarios (2 to 32; generator
+// outages, P.sc.gen_bus set: 2, 4 or 8) on `grid` slots.
 template <typename VT>
 cudaError_t launch_fdpf(cudaStream_t st, int T, int grid, const FdpfParams& P,
                         const DevMatT<VT>& MP, const DevMatT<VT>& MQ);
 template <typename VT>
-int fdpf_max_blocks_per_sm(int T);
+int fdpf_max_blocks_per_sm(int T, bool gen = false);
+// the generator-outage kernel (fdpf_gen.cu)
+template <typename VT>
+cudaError_t launch_fdpf_gen(cudaStream_t st, int T, int grid, const FdpfParams& P,
+                            const DevMatT<VT>& MP, const DevMatT<VT>& MQ);
+template <typename VT>
+int fdpf_blocks_gen(int T);
 template <typename VT>
 cudaError_t launch_apply(cudaStream_t st, int grid, const DevMatT<VT>& M, int op, int S,
                          const int32_t* outages, const int32_t* f, const int32_t* t,

@@ -209,6 +209,7 @@ struct LaneState {
   int raP[T], rbP[T], raQ[T], rbQ[T];
   double wP[T], wQ[T], coef[T], gl[T], bl[T];
   double cl[T];  // the outaged branch's 1 / turns ratio (1 for a line)
+  int gb[T];     // bus of a tripped generator (-1: none): it gets a B'' row
   int active[T], outer[T], inP[T], inQ[T], status[T], nogen[T];
   double err[T], best[T];
   unsigned long long tphase[8];
@@ -402,6 +403,17 @@ struct Stamp {
   VT w[T], c[T];
 };
 
+// A tripped generator's bus gets the matrix row it lacks (B'': the PV bus
+// becomes PQ), one extension row per lane at vector row n + 1 (row n is the
+// zero row): per lane the bus (-1: none) and the row's diagonal.  The
+// base-case factor preconditions the rows it has, the diagonal this one
+// (a block-diagonal preconditioner).
+template <int T, typename VT>
+struct Ext {
+  int gb[T];
+  VT gd[T];
+};
+
 template <int T, typename VT>
 __device__ __forceinline__ unsigned long long stamp_filter(const Stamp<T, VT>& S) {
   unsigned long long f = 0ull;
@@ -431,7 +443,8 @@ __device__ GPCG_LOOP_INLINE Vec<VT, Geo<T>::LP> spmv_pass(
     const DevMatT<VT>& M, const VT* __restrict__ v_, VT* __restrict__ p, VT* __restrict__ q,
     const Stamp<T, VT>& S, unsigned long long filt, Vec<VT, Geo<T>::LP> be, bool first,
     const LaneState<T>* isl, const VT* __restrict__ r = nullptr,
-    Vec<VT, Geo<T>::LP>* rq = nullptr, Vec<VT, Geo<T>::LP>* qq = nullptr) {
+    Vec<VT, Geo<T>::LP>* rq = nullptr, Vec<VT, Geo<T>::LP>* qq = nullptr,
+    const Ext<T, VT>* X = nullptr) {
   constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
   constexpr int RPS = Geo<T>::RPS, STEP = RPS * UNR;
@@ -498,6 +511,19 @@ __device__ GPCG_LOOP_INLINE Vec<VT, Geo<T>::LP> spmv_pass(
             a.v[j] += i == ra ? -(S.c[ln] * wt) : wt;
           }
         }
+        // a neighbour of a tripped generator's bus: its coupling to the
+        // lane's extension row
+        if (X) {
+#pragma unroll
+          for (int j = 0; j < LP; ++j) {
+            const int ln = g.lane + j, b = X->gb[ln];
+            if (b < 0) continue;
+            const VT ve = v_[(size_t)(M.n + 1) * T + ln];
+            const int e1 = __ldg(M.xptr + b + 1);
+            for (int e = __ldg(M.xptr + b); e < e1; ++e)
+              if (__ldg(M.xrow + e) == i) a.v[j] += __ldg(M.xval + e) * ve;
+          }
+        }
       }
       if (DIRECTION) {
         Vec<VT, LP> pn = pi, qn = a;
@@ -537,7 +563,67 @@ __device__ GPCG_LOOP_INLINE Vec<VT, Geo<T>::LP> spmv_pass(
       }
     }
   }
+  // the extension rows (a lane without one has zeros there)
+  if (DIRECTION && X && g.rs == 0) {
+#pragma unroll
+    for (int j = 0; j < LP; ++j) {
+      const int ln = g.lane + j, b = X->gb[ln];
+      const size_t o = (size_t)(M.n + 1) * T + ln;
+      const VT ve = v_[o];
+      VT a = X->gd[ln] * ve;
+      if (b >= 0) {
+        const int e1 = __ldg(M.xptr + b + 1);
+        for (int e = __ldg(M.xptr + b); e < e1; ++e) {
+          const int rw = __ldg(M.xrow + e);
+          if (rw >= 0) a += __ldg(M.xval + e) * v_[(size_t)rw * T + ln];
+        }
+      }
+      VT pn = ve, qn = a;
+      if (!first) {
+        pn += be.v[j] * p[o];
+        qn += be.v[j] * q[o];
+      }
+      p[o] = pn;
+      q[o] = qn;
+      pq.v[j] += pn * qn;
+      if (r) {
+        rq->v[j] += r[o] * qn;
+        qq->v[j] += qn * qn;
+      }
+    }
+  }
   return pq;
+}
+
+// The extension rows in the forward (or Jacobi) pass: the PCG update
+// (FUSED) or x = 0, r.r, and z = r / diagonal with its r.z.
+template <int T, typename VT, bool FUSED>
+__device__ __forceinline__ void ext_update(const DevMatT<VT>& M, const Ext<T, VT>* X,
+                                           VT* __restrict__ x, VT* __restrict__ r,
+                                           const VT* __restrict__ p, const VT* __restrict__ q,
+                                           VT* __restrict__ z, const Vec<VT, Geo<T>::LP>& al,
+                                           Vec<VT, Geo<T>::LP>& rr, Vec<VT, Geo<T>::LP>& rz) {
+  constexpr int LP = Geo<T>::LP;
+  const Geo<T> g;
+  if (!X || g.rs != 0) return;
+#pragma unroll
+  for (int j = 0; j < LP; ++j) {
+    const int ln = g.lane + j;
+    const size_t o = (size_t)(M.n + 1) * T + ln;
+    VT rv = r[o];
+    if (FUSED) {
+      x[o] = fma(al.v[j], p[o], x[o]);
+      rv -= al.v[j] * q[o];
+      r[o] = rv;
+    } else {
+      x[o] = (VT)0;
+    }
+    rr.v[j] += rv * rv;
+    const VT d = X->gd[ln];
+    const VT zv = d > (VT)0 ? rv / d : (VT)0;
+    z[o] = zv;
+    rz.v[j] += rv * zv;
+  }
 }
 
 // The PCG update of one row in the forward pass: x += alpha p, r -= alpha q
@@ -677,11 +763,12 @@ template <int T, typename VT, bool FUSED>
 __device__ GPCG_LOOP_INLINE Vec<VT, Geo<T>::LP> fwd_pass(
     const DevMatT<VT>& M, VT* __restrict__ x, VT* __restrict__ r, const VT* __restrict__ p,
     const VT* __restrict__ q, VT* __restrict__ z, const Vec<VT, Geo<T>::LP>& al, VT* zt,
-    Vec<VT, Geo<T>::LP>& rzt) {
+    Vec<VT, Geo<T>::LP>& rzt, const Ext<T, VT>* X = nullptr) {
   constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
   constexpr int RPS = Geo<T>::RPS;
   Vec<VT, LP> rr = vzero<VT, LP>();
+  ext_update<T, VT, FUSED>(M, X, x, r, p, q, z, al, rr, rzt);
   const int nl = M.tail_lev;
   int r0 = 0, r1 = 0, pf = -1, cn[KL];
   if (nl > 0) {
@@ -839,9 +926,11 @@ __device__ GPCG_LOOP_INLINE void jacobi_pass(const DevMatT<VT>& M, VT* __restric
                                             const VT* __restrict__ q, VT* __restrict__ z,
                                             const Vec<VT, Geo<T>::LP>& al,
                                             const Stamp<T, VT>& S,
-                                            Vec<VT, Geo<T>::LP>& rr, Vec<VT, Geo<T>::LP>& rz) {
+                                            Vec<VT, Geo<T>::LP>& rr, Vec<VT, Geo<T>::LP>& rz,
+                                            const Ext<T, VT>* X = nullptr) {
   constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
+  ext_update<T, VT, FUSED>(M, X, x, r, p, q, z, al, rr, rz);
   for (int i = g.rs; i < M.n; i += Geo<T>::RPS) {
     const size_t o = (size_t)i * T + g.lane;
     const Vec<VT, LP> ri = pcg_update_row<T, VT, FUSED>(o, x, r, p, q, al, rr);
@@ -887,13 +976,15 @@ struct PcgLanes {
 // SpMV pass accumulates -- meets the tolerance for every running lane, the
 // solve ends there without the forward pass that would apply the step: the
 // step is left in L.xalpha for the caller to apply as x + xalpha p.
-template <int T, typename VT, bool DEFER = false>
+template <int T, typename VT, bool DEFER = false, bool GEN = false>
 __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT>& M, LaneState<T>& L, VT* x,
                           VT* r, VT* p, VT* q, VT* z, const int* ra_, const int* rb_,
-                          const double* w_, int* iters, const double* c_ = nullptr) {
+                          const double* w_, int* iters, const double* c_ = nullptr,
+                          const int* gb_ = nullptr) {
   constexpr int LP = Geo<T>::LP;
   __shared__ PcgLanes<T, VT> S;
   __shared__ Stamp<T, VT> St;
+  __shared__ Ext<T, VT> Xs;
   // right-hand side and y of the schedule's tail (lane groups: 16-byte aligned)
   __shared__ __align__(16) VT zt[TAIL_ROWS * T];
   const Geo<T> g;
@@ -908,13 +999,35 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
     St.w[tid] = (VT)w_[tid];
     St.c[tid] = c_ ? (VT)c_[tid] : (VT)1;
     L.xalpha[tid] = 0.0;
+    if constexpr (GEN) {
+      const int b = (gb_ && M.xptr && on) ? gb_[tid] : -1;
+      Xs.gb[tid] = b;
+      Xs.gd[tid] = b >= 0 ? M.xdiag[b] : (VT)0;
+    }
   }
   if (g.rs == 0) {
     stv<LP>(p + (size_t)M.n * T + g.lane, vzero<VT, LP>());
     stv<LP>(z + (size_t)M.n * T + g.lane, vzero<VT, LP>());
   }
   __syncthreads();
-  const unsigned long long filt = stamp_filter<T, VT>(St);
+  unsigned long long filt = stamp_filter<T, VT>(St);
+  // lanes with a tripped generator: their extension rows, and the rows
+  // coupled to them in the filter
+  bool ext = false;
+  if constexpr (GEN) {
+#pragma unroll 1
+    for (int k = 0; k < T; ++k) {
+      const int b = Xs.gb[k];
+      if (b < 0) continue;
+      ext = true;
+      const int e1 = __ldg(M.xptr + b + 1);
+      for (int e = __ldg(M.xptr + b); e < e1; ++e) {
+        const int rw = __ldg(M.xrow + e);
+        if (rw >= 0) filt |= 1ull << (rw & 63);
+      }
+    }
+  }
+  const Ext<T, VT>* X = (GEN && ext) ? &Xs : nullptr;
   // islands in this tile: the SpMV then masks rows per lane
   bool islands = false;
 #pragma unroll 1
@@ -922,10 +1035,10 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
   const LaneState<T>* isl = islands ? &L : nullptr;
   Vec<VT, LP> bbp = vzero<VT, LP>(), rzp = vzero<VT, LP>(), al = vzero<VT, LP>();
   if (jac) {
-    jacobi_pass<T, VT, false>(M, x, r, p, q, z, al, St, bbp, rzp);
+    jacobi_pass<T, VT, false>(M, x, r, p, q, z, al, St, bbp, rzp, X);
   } else {
     Vec<VT, LP> rzt = vzero<VT, LP>();
-    bbp = fwd_pass<T, VT, false>(M, x, r, p, q, z, al, zt, rzt);
+    bbp = fwd_pass<T, VT, false>(M, x, r, p, q, z, al, zt, rzt, X);
     rzp = bwd_pass<T, VT>(M, r, z, rzt);
   }
   const Vec<VT, LP> bb = lane_sum<T, RS_BB>(L, bbp);
@@ -958,7 +1071,7 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
     Vec<VT, LP> rqp = vzero<VT, LP>(), qqp = vzero<VT, LP>();
     const Vec<VT, LP> pqp = spmv_pass<T, VT, true>(
         M, z, p, q, St, filt, be, it == 0, isl, (DEFER && Geo<T>::TPR == 1) ? r : nullptr, &rqp,
-        &qqp);
+        &qqp, X);
     Vec<VT, LP> pq = pqp, rq = rqp, qq = qqp;
     if constexpr (DEFER && Geo<T>::TPR == 1) lane_sum3<T, RS_PQ, RS_RQ, RS_QQ>(L, pq, rq, qq);
     else pq = lane_sum<T, RS_PQ>(L, pqp);
@@ -1009,9 +1122,9 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
         if ((bk >> j) & 1) S.brk[g.lane + j] = 1;
     Vec<VT, LP> rrp = vzero<VT, LP>(), rzn = vzero<VT, LP>();
     if (jac) {
-      jacobi_pass<T, VT, true>(M, x, r, p, q, z, al, St, rrp, rzn);
+      jacobi_pass<T, VT, true>(M, x, r, p, q, z, al, St, rrp, rzn, X);
     } else {
-      rrp = fwd_pass<T, VT, true>(M, x, r, p, q, z, al, zt, rzn);  // rzn: the tail's r.z
+      rrp = fwd_pass<T, VT, true>(M, x, r, p, q, z, al, zt, rzn, X);  // rzn: the tail's r.z
     }
     const Vec<VT, LP> rr = lane_sum<T, RS_RR>(L, rrp);
     if (g.rs == 0) {

@@ -95,6 +95,45 @@ __global__ void __launch_bounds__(1024) preorder_prefix_kernel(int n,
   }
 }
 
+// Generator outages, one thread per scenario: no branch out (outage -1),
+// nothing islanded, and the tripped bus's P_gen shared by the other PV
+// generators with P_gen > 0 in proportion to theirs (coef = P_gen,k over
+// their total; no_gen when there are none).  gen_bus: internal bus indices
+// of PV buses (checked on the host).
+__global__ void gen_outage_kernel(int S, int n, const int32_t* __restrict__ gen_bus,
+                                  const double* __restrict__ P_gen,
+                                  const double* __restrict__ prefG,
+                                  const int32_t* __restrict__ prefGc, int32_t* outage,
+                                  int32_t* isl_lo, int32_t* isl_cnt, double* coef,
+                                  int32_t* no_gen) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  const int k = gen_bus[s];
+  const double pg = P_gen[k];
+  const bool in = pg > 0.0;  // k counts among the sharing generators
+  const int others = prefGc[n] - (in ? 1 : 0);
+  const double rest = prefG[n] - (in ? pg : 0.0);
+  outage[s] = -1;
+  isl_lo[s] = 0;
+  isl_cnt[s] = 0;
+  no_gen[s] = others == 0;
+  coef[s] = others == 0 ? 0.0 : pg / rest;
+}
+
+cudaError_t launch_gen_outages(cudaStream_t st, int S, int n, const int32_t* gen_bus,
+                               const double* P_gen, const IslandPlan& I, int32_t* outage,
+                               int32_t* isl_lo, int32_t* isl_cnt, double* coef, int32_t* no_gen,
+                               int32_t* label_out) {
+  if (S == 0) return cudaSuccess;
+  gen_outage_kernel<<<(S + 255) / 256, 256, 0, st>>>(S, n, gen_bus, P_gen, I.prefG, I.prefGc,
+                                                      outage, isl_lo, isl_cnt, coef, no_gen);
+  cudaError_t e = cudaGetLastError();
+  // one component: every bus carries the smallest bus index, 0
+  if (e == cudaSuccess && label_out)
+    e = cudaMemsetAsync(label_out, 0, (size_t)S * n * sizeof(int32_t), st);
+  return e;
+}
+
 cudaError_t launch_islands(cudaStream_t st, int S, int n, const int32_t* outages,
                            const IslandPlan& I, const double* P_user, double* prefP_scratch,
                            int32_t* isl_lo, int32_t* isl_cnt, double* coef, int32_t* no_gen,
