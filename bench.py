@@ -293,6 +293,101 @@ def _dc_chunk(outs):
     return len(outs)
 
 
+def _gen_chunk(args):
+    name, xf, buses = args
+    from oracle import powerflow as pf
+    from oracle import screen
+    g = bench_grid(argparse.Namespace(config=name, xfmr_frac=xf))
+    th0, V0, _, _, _ = pf.base_case(g, tol=1e-10, max_outer=200)
+    t0 = time.perf_counter()
+    screen.n1_screen(g, th0, V0, buses, tol=1e-4, processes=1, kind="generator")
+    return time.perf_counter() - t0
+
+
+def run_gen(args):
+    """The N-1 screen of generator outages: every PV bus's generator trips in
+    turn (the bus becomes PQ with its load, the lost generation is
+    re-dispatched); the same persistent kernel with a B'' extension row."""
+    import torch
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1803_03290_gb300 as gp
+    g = bench_grid(args)
+    prec = {"fp32": gp.BATCHED_FP32, "fp64": gp.BATCHED_FP64,
+            "fp16f": gp.BATCHED_FP32_F16}[args.precision]
+    c = gp.GPCG(g, precision=prec, tol=1e-4)
+    c.base_solve()
+    pv = np.flatnonzero(g.bus_type == 1).astype(np.int32)
+    if args.n_outages > 0:
+        pv = pv[:args.n_outages]
+    S, n, m = pv.size, g.n_bus, g.n_branch
+    buses = torch.from_numpy(pv).to(dev)
+    out = {"iters": torch.empty(S, 3, dtype=torch.int32, device=dev),
+           "status": torch.empty(S, dtype=torch.int32, device=dev),
+           "max_loading": torch.empty(S, dtype=torch.float64, device=dev)}
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+    for _ in range(args.warmup):
+        c.n1_gen_screen_device(buses, out)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ms = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0.record()
+            c.n1_gen_screen_device(buses, out)
+            ev1.record()
+            torch.cuda.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+    value = S * args.steps / (sum(ms) / 1e3)
+    e2e_ms = []
+    for k in range(args.steps + 1):
+        t0 = time.perf_counter()
+        c.n1_gen_screen(pv, outputs=("status", "max_loading", "iters"))
+        if k:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    status = out["status"].cpu().numpy()
+    iters = out["iters"].cpu().numpy()
+    cpu = None
+    if args.cpu_sample > 0:
+        import multiprocessing as mp
+        cores = len(os.sched_getaffinity(0))
+        k = min(args.cpu_sample, S)
+        sample = np.random.default_rng(12).choice(pv, k, replace=False)
+        chunks = [ch for ch in np.array_split(sample, cores) if len(ch)]
+        t0 = time.perf_counter()
+        with mp.get_context("spawn").Pool(len(chunks)) as pool:
+            solve_s = pool.map(_gen_chunk, [(args.config, args.xfmr_frac, ch) for ch in chunks])
+        wall = time.perf_counter() - t0
+        cpu = {"value": round(k / max(solve_s), 2), "unit": "scenarios/s", "cores": len(chunks),
+               "kind": "oracle",
+               "sample": f"{k} seeded generator outages, tol 1e-4 p.u., one process per core "
+                         f"(solve time of the slowest process; {wall:.1f} s wall with set-up)"}
+    line = {"metric": "N-1 generator-outage scenarios/sec at 10k buses (mismatch<=1e-4 p.u.)",
+            "value": round(value, 1), "unit": "scenarios/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(sum(ms) / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec != gp.BATCHED_FP64 else "f64", "data": "synthetic",
+            "config": {"workload": f"{args.config}: {n} buses, {m} branches{xfmr_note(args)}, "
+                                   f"generator outages of all {S} PV buses, tol 1e-4 p.u., "
+                                   f"exact base-case preconditioner, {args.precision} inner PCG",
+                       "scenarios": S, "l2": "flushed between steps (512 MiB write)"},
+            "e2e": {"value": round(S / (statistics.mean(e2e_ms) / 1e3), 1), "unit": "scenarios/s",
+                    "h2d_bytes_per_step": 4 * S, "d2h_bytes_per_step": 24 * S},
+            "gpu_launches": 2 * args.steps, "cpu_baseline": cpu, "clocks": clk.summary(),
+            "scenarios": {"converged": int((status == 0).sum()),
+                          "no_gen": int((status == 3).sum()),
+                          "maxiter": int((status == 1).sum()),
+                          "diverged": int((status == 2).sum()),
+                          "mean_outer": float(iters[:, 0].mean()),
+                          "mean_inner_P": float(iters[:, 1].mean()),
+                          "mean_inner_Q": float(iters[:, 2].mean())}}
+    print(json.dumps(line), flush=True)
+    c.close()
+
+
 def run_dc(args):
     """The DC (P-theta) quick screen of every outage: one batched PCG solve per
     scenario (plus one FP64 refinement step of FP32 solves), flows, loading."""
@@ -453,13 +548,16 @@ def main():
     ap.add_argument("--xfmr-frac", type=float, default=0.0,
                     help="make this fraction of the branches transformers (turns ratio "
                          "U[0.95, 1.05] at the from end); 0 = the plain workload")
-    ap.add_argument("--workload", default="ac", choices=["ac", "dc"],
-                    help="ac: the FDPF N-1 screen (the headline); dc: the P-theta quick screen")
+    ap.add_argument("--workload", default="ac", choices=["ac", "dc", "gen"],
+                    help="ac: the FDPF N-1 screen of branch outages (the headline); dc: the "
+                         "P-theta quick screen; gen: the FDPF screen of generator outages")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "dc":
         run_dc(args)
+    elif args.workload == "gen":
+        run_gen(args)
     else:
         run_gpcg(args)
 
