@@ -332,7 +332,7 @@ def run_gen(args):
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    ms = []
+    ms, kern_ms = [], []
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.zero_()
@@ -341,6 +341,7 @@ def run_gen(args):
             ev1.record()
             torch.cuda.synchronize()
             ms.append(ev0.elapsed_time(ev1))
+            kern_ms.append(c.last_timings())
     value = S * args.steps / (sum(ms) / 1e3)
     e2e_ms = []
     for k in range(args.steps + 1):
@@ -350,6 +351,19 @@ def run_gen(args):
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     status = out["status"].cpu().numpy()
     iters = out["iters"].cpu().numpy()
+    info = c.info()
+    w = 8 if prec == gp.BATCHED_FP64 else 4
+    # the extension row adds one row to every B'' pass
+    info_x = dict(info, n_q=info["n_q"] + 1)
+    algo = algorithmic_bytes(info_x, iters, w, n, m)
+    fd_ms = statistics.mean(k[1] for k in kern_ms)
+    peak, peak_kind = load_peaks()
+    achieved = algo / (fd_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "kernel": "fdpf_tiles_kernel (generator outages)", "peak_source": peak_kind,
+            "algorithmic_bytes_per_launch": int(algo), "kernel_ms": round(fd_ms, 3),
+            "setup_kernel_ms": round(statistics.mean(k[0] for k in kern_ms), 3)}
     cpu = None
     if args.cpu_sample > 0:
         import multiprocessing as mp
@@ -376,7 +390,8 @@ def run_gen(args):
                        "scenarios": S, "l2": "flushed between steps (512 MiB write)"},
             "e2e": {"value": round(S / (statistics.mean(e2e_ms) / 1e3), 1), "unit": "scenarios/s",
                     "h2d_bytes_per_step": 4 * S, "d2h_bytes_per_step": 24 * S},
-            "gpu_launches": 2 * args.steps, "cpu_baseline": cpu, "clocks": clk.summary(),
+            "gpu_launches": 2 * args.steps, "roofline": roof, "cpu_baseline": cpu,
+            "clocks": clk.summary(),
             "scenarios": {"converged": int((status == 0).sum()),
                           "no_gen": int((status == 3).sum()),
                           "maxiter": int((status == 1).sum()),
