@@ -102,7 +102,7 @@ def test_preconditioner_apply(which, precond):
     for s in range(0, outages.size, 6):
         ref = factor.apply_preconditioner(L, X[s])
         np.testing.assert_allclose(Y64[s], ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
-    # FP32: the substitutions are backward stable; judge them by the
+    # FP32: the substitutions are backward stable; assess them by the
     # residual of the FP64 factor, || L L^T y - x || <= c eps ||L|| ||L^T y||
     import scipy.sparse as sp
     Ls = sp.csr_matrix((d["lval"], d["lcol"], d["lrowptr"]), shape=(n, n))
