@@ -35,7 +35,7 @@ def _compare(res, ref, n_out):
 @pytest.mark.parametrize("precision,precond", [
     (gp.BATCHED_FP32, gp.PRECOND_EXACT), (gp.BATCHED_FP64, gp.PRECOND_EXACT),
     (gp.BATCHED_FP32, gp.PRECOND_IC0), (gp.BATCHED_FP64, gp.PRECOND_JACOBI),
-    (gp.PLAIN_FP64, gp.PRECOND_EXACT)])
+    (gp.PLAIN_FP64, gp.PRECOND_EXACT), (gp.BATCHED_FP32_F16, gp.PRECOND_EXACT)])
 def test_gen_outages_grid120_all(name, precision, precond):
     g = grid(name)
     c = gp.GPCG(g, precision=precision, precond=precond, tol=1e-10, max_outer=100,
@@ -115,4 +115,27 @@ def test_gen_outage_rejects_non_pv_buses():
         assert e.value.status == 1
     r = c.n1_gen_screen(np.zeros(0, np.int32))
     assert r["theta"].shape == (0, g.n_bus)
+    c.close()
+
+
+def test_gen_outages_without_other_generators():
+    """Only one PV generator carries P_gen: tripping it leaves nobody to take
+    the re-dispatch (the slack absorbs it: ISLAND_NO_GEN); tripping a PV bus
+    with P_gen = 0 re-dispatches nothing.  Against the oracle."""
+    import paper_1803_03290_gb300 as gp
+    from oracle import powerflow as pf
+    g = grid("grid120").copy()
+    pv = np.flatnonzero(g.bus_type == 1)
+    g.P_gen = g.P_gen.copy()
+    g.P_gen[pv[1:]] = 0.0          # bus pv[0] is the only generator with P_gen > 0
+    th0, V0, _, st, _ = pf.base_case(g, tol=1e-11, max_outer=200)
+    assert st == pf.STATUS_OK
+    buses = pv[:8].astype(np.int32)
+    c = gp.GPCG(g, tol=1e-10, max_outer=100)
+    c.base_solve()
+    res = c.n1_gen_screen(buses)
+    ref = screen.n1_screen(g, th0, V0, buses, tol=1e-10, max_outer=100, processes=1,
+                           kind="generator")
+    assert ref["status"][0] == pf.STATUS_ISLAND_NO_GEN
+    _compare(res, ref, buses.size)
     c.close()

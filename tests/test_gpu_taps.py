@@ -96,7 +96,8 @@ def _compare(res, ref, n_out):
 
 @pytest.mark.parametrize("precision,precond", [
     (gp.BATCHED_FP32, gp.PRECOND_EXACT), (gp.BATCHED_FP64, gp.PRECOND_EXACT),
-    (gp.BATCHED_FP32, gp.PRECOND_IC0), (gp.BATCHED_FP64, gp.PRECOND_JACOBI)])
+    (gp.BATCHED_FP32, gp.PRECOND_IC0), (gp.BATCHED_FP64, gp.PRECOND_JACOBI),
+    (gp.BATCHED_FP32_F16, gp.PRECOND_EXACT), (gp.PLAIN_FP64, gp.PRECOND_EXACT)])
 def test_tapped_n1_grid120_all_outages(precision, precond):
     g = grid("grid120_xfmr")
     c = gp.GPCG(g, precision=precision, precond=precond, tol=1e-10, max_outer=100,
