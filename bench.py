@@ -165,18 +165,35 @@ def run_gpcg(args):
     S = g.n_branch if args.n_outages <= 0 else min(args.n_outages, g.n_branch)
     outages = torch.arange(S, dtype=torch.int32, device=dev)
     n, m = g.n_bus, g.n_branch
+    # one screen call for all outages, or (--chunk K) one call per chunk of K
+    # outages into the same output buffers (each chunk size replays its graph)
+    K = S if args.chunk <= 0 else min(args.chunk, S)
     out = {
-        "theta": torch.empty((S, n), dtype=torch.float64, device=dev),
-        "V": torch.empty((S, n), dtype=torch.float64, device=dev),
-        "flow": torch.empty((S, m), dtype=torch.float64, device=dev),
-        "iters": torch.empty((S, 3), dtype=torch.int32, device=dev),
-        "status": torch.empty((S,), dtype=torch.int32, device=dev),
-        "max_loading": torch.empty((S,), dtype=torch.float64, device=dev),
+        "theta": torch.empty((K, n), dtype=torch.float64, device=dev),
+        "V": torch.empty((K, n), dtype=torch.float64, device=dev),
+        "flow": torch.empty((K, m), dtype=torch.float64, device=dev),
+        "iters": torch.empty((K, 3), dtype=torch.int32, device=dev),
+        "status": torch.empty((K,), dtype=torch.int32, device=dev),
+        "max_loading": torch.empty((K,), dtype=torch.float64, device=dev),
     }
+    all_iters = torch.empty((S, 3), dtype=torch.int32, device=dev)
+    all_status = torch.empty((S,), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
+
+    def screen_all(timings=None):
+        for k0 in range(0, S, K):
+            k1 = min(S, k0 + K)
+            o = {key: v[:k1 - k0] for key, v in out.items()}
+            c.n1_screen_device(outages[k0:k1], o, stream)
+            all_iters[k0:k1].copy_(o["iters"])
+            all_status[k0:k1].copy_(o["status"])
+            if timings is not None:
+                torch.cuda.synchronize()
+                timings.append(c.last_timings())
+
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
     for _ in range(args.warmup):
-        c.n1_screen_device(outages, out, stream)
+        screen_all()
     torch.cuda.synchronize()
     info = c.info()  # the tile width the autotuner chose on the first call
     step_ms, kern_ms = [], []
@@ -188,20 +205,24 @@ def run_gpcg(args):
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.zero_()
+            chunk_ms = []
             ev0.record(stream)
-            c.n1_screen_device(outages, out, stream)
+            screen_all(chunk_ms if K < S else None)
             ev1.record(stream)
             torch.cuda.synchronize()
             step_ms.append(ev0.elapsed_time(ev1))
-            kern_ms.append(c.last_timings())
+            if K < S:
+                kern_ms.append((sum(t[0] for t in chunk_ms), sum(t[1] for t in chunk_ms)))
+            else:
+                kern_ms.append(c.last_timings())
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     from paper_1803_03290_gb300.shard import max_over_ranks
     total_ms = max_over_ranks(float(sum(step_ms)), device=dev)
     value = world * S * args.steps / (total_ms / 1e3)
-    iters = out["iters"].cpu().numpy()
-    status = out["status"].cpu().numpy()
+    iters = all_iters.cpu().numpy()
+    status = all_status.cpu().numpy()
 
     # end to end through the public C ABI with host buffers: outage list in,
     # per-scenario screening results (status, iterations, max loading) out
@@ -237,7 +258,7 @@ def run_gpcg(args):
     peak, peak_kind = load_peaks()
     achieved = algo / (fd_ms / 1e3) / 1e9
     default_workload = (args.config == "grid10k" and args.precision == "fp32" and
-                        args.xfmr_frac == 0 and
+                        args.xfmr_frac == 0 and args.chunk <= 0 and
                         args.precond == "exact" and args.n_outages <= 0)
     traffic = (KERNEL_TRAFFIC["bytes"] if default_workload and
                kernel_digest() == KERNEL_TRAFFIC["sha256"] else None)
@@ -246,6 +267,9 @@ def run_gpcg(args):
             "kernel": "fdpf_tiles_kernel", "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": int(algo), "kernel_ms": round(fd_ms, 3),
             "islands_kernel_ms": round(statistics.mean(k[0] for k in kern_ms), 3)}
+    n_chunks = (S + K - 1) // K
+    if n_chunks > 1:  # bytes and kernel time summed over the step's launches
+        roof["launches_per_step"] = n_chunks
     cpu = None
     if rank == 0 and world == 1 and args.cpu_sample > 0:
         cpu = cpu_baseline(g, args.cpu_sample)
@@ -258,12 +282,14 @@ def run_gpcg(args):
             "data": "synthetic",
             "config": {"workload": f"{args.config}: {n} buses, {m} branches{xfmr_note(args)}, "
                                    f"{S} single-branch "
-                                   f"outages, tol 1e-4 p.u., {args.precond} base-case preconditioner, "
+                                   f"outages{f' in chunks of {K}' if n_chunks > 1 else ''}, "
+                                   f"tol 1e-4 p.u., {args.precond} base-case preconditioner, "
                                    f"{args.precision} inner PCG, FP64 mismatch/flows",
                        "n_bus": n, "n_branch": m, "scenarios": S, "tile": info["tile"],
+                       "chunk": K,
                        "l2": "flushed between steps (512 MiB write)",
                        "precond": args.precond, "precision": args.precision},
-            "e2e": e2e, "gpu_launches": 2 * args.steps,
+            "e2e": e2e, "gpu_launches": 2 * n_chunks * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "plain": plain,
             "clocks": clk.summary(),
             "scenarios": {"converged": int((status == 0).sum()), "island_no_gen": int((status == 3).sum()),
@@ -557,6 +583,8 @@ def main():
     ap.add_argument("--precond", default="exact", choices=["exact", "ic0", "jacobi"])
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--n-outages", type=int, default=0, help="screen only the first K outages (0 = all)")
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="screen the outages in calls of this many (0 = one call)")
     ap.add_argument("--cpu-sample", type=int, default=400)
     ap.add_argument("--plain-sample", type=int, default=64)
     ap.add_argument("--ref-sample", type=int, default=256)
