@@ -429,6 +429,92 @@ def run_gen(args):
     c.close()
 
 
+def _adj_chunk(args):
+    name, outs = args
+    from gridgen import config_grid
+    from oracle import adjoint
+    g = config_grid(name)
+    t0 = time.perf_counter()
+    adjoint.loss_and_grad(g, outs, g.P_sched, 1.0 / g.x)
+    return time.perf_counter() - t0
+
+
+def run_adjoint(args):
+    """The adjoint workload: loss and gradients (w.r.t. the bus injections and
+    the branch susceptances) of the smooth overload penalty summed over every
+    single-branch outage of the DC model -- per scenario one batched PCG for
+    theta and one with the symmetric B'_s for lambda, then the sums."""
+    import torch
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1803_03290_gb300 as gp
+    from gridgen import config_grid
+    name = args.config if args.config != WORKLOAD else "grid2k"
+    g = config_grid(name)
+    c = gp.GPCG(g)
+    S = g.n_branch if args.n_outages <= 0 else min(args.n_outages, g.n_branch)
+    n, m = g.n_bus, g.n_branch
+    outages = torch.arange(S, dtype=torch.int32, device=dev)
+    P = torch.from_numpy(g.P_sched.astype(np.float64)).to(dev)
+    b = torch.from_numpy((1.0 / g.x).astype(np.float64)).to(dev)
+    loss = torch.empty(1, dtype=torch.float64, device=dev)
+    gP = torch.empty(n, dtype=torch.float64, device=dev)
+    gb = torch.empty(m, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+    for _ in range(args.warmup):
+        c.n1_adjoint_device(outages, P, b, loss, gP, gb)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ms = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0.record()
+            c.n1_adjoint_device(outages, P, b, loss, gP, gb)
+            ev1.record()
+            torch.cuda.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+    value = S * args.steps / (sum(ms) / 1e3)
+    hout = np.arange(S, dtype=np.int32)
+    e2e_ms = []
+    for k in range(args.steps + 1):
+        t0 = time.perf_counter()
+        c.n1_adjoint(hout, g.P_sched, 1.0 / g.x)
+        if k:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    cpu = None
+    if args.cpu_sample > 0:
+        import multiprocessing as mp
+        cores = len(os.sched_getaffinity(0))
+        k = min(args.cpu_sample, S)
+        sample = np.random.default_rng(14).choice(S, k, replace=False)
+        chunks = [ch for ch in np.array_split(sample, cores) if len(ch)]
+        with mp.get_context("spawn").Pool(len(chunks)) as pool:
+            secs = pool.map(_adj_chunk, [(name, ch) for ch in chunks])
+        cpu = {"value": round(k / max(secs), 2), "unit": "scenarios/s", "cores": len(chunks),
+               "kind": "oracle",
+               "sample": f"{k} seeded outages (loss and both gradients), one process per core "
+                         f"(time of the slowest process)"}
+    line = {"metric": "N-1 overload-penalty adjoint scenarios/sec at 2k buses (loss + dL/dP + dL/db)",
+            "value": round(value, 1), "unit": "scenarios/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(sum(ms) / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{name}: {n} buses, {m} branches, all {S} single-branch "
+                                   f"outages, DC model, softplus^2 overload penalty, FP64 "
+                                   f"batched PCG with the exact base-case preconditioner",
+                       "scenarios": S, "l2": "flushed between steps (512 MiB write)"},
+            "e2e": {"value": round(S / (statistics.mean(e2e_ms) / 1e3), 1), "unit": "scenarios/s",
+                    "h2d_bytes_per_step": 4 * S + 8 * (n + m),
+                    "d2h_bytes_per_step": 8 * (1 + n + m)},
+            "gpu_launches": None, "roofline": None, "cpu_baseline": cpu,
+            "clocks": clk.summary(), "loss": float(loss.item())}
+    print(json.dumps(line), flush=True)
+    c.close()
+
+
 def run_dc(args):
     """The DC (P-theta) quick screen of every outage: one batched PCG solve per
     scenario (plus one FP64 refinement step of FP32 solves), flows, loading."""
@@ -591,9 +677,10 @@ def main():
     ap.add_argument("--xfmr-frac", type=float, default=0.0,
                     help="make this fraction of the branches transformers (turns ratio "
                          "U[0.95, 1.05] at the from end); 0 = the plain workload")
-    ap.add_argument("--workload", default="ac", choices=["ac", "dc", "gen"],
+    ap.add_argument("--workload", default="ac", choices=["ac", "dc", "gen", "adjoint"],
                     help="ac: the FDPF N-1 screen of branch outages (the headline); dc: the "
-                         "P-theta quick screen; gen: the FDPF screen of generator outages")
+                         "P-theta quick screen; gen: the FDPF screen of generator outages; "
+                         "adjoint: loss and gradients of the overload penalty (grid2k)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -601,6 +688,8 @@ def main():
         run_dc(args)
     elif args.workload == "gen":
         run_gen(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_gpcg(args)
 
