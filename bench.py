@@ -179,17 +179,40 @@ def run_gpcg(args):
     all_iters = torch.empty((S, 3), dtype=torch.int32, device=dev)
     all_status = torch.empty((S,), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
+    # --streams N (with --chunk): N contexts, each with its own stream and
+    # buffers, take the chunks in turn, so a chunk's kernel fills the SMs
+    # that the previous chunk's draining kernel has left
+    NS = max(1, args.streams) if K < S else 1
+    ctxs, streams, outs = [c], [stream], [out]
+    for _ in range(NS - 1):
+        ci = gp.GPCG(g, precision=prec, precond=pc, tol=1e-4, tile=args.tile)
+        ci.base_solve()
+        ctxs.append(ci)
+        streams.append(torch.cuda.Stream(device=dev))
+        outs.append({key: torch.empty_like(v) for key, v in out.items()})
 
     def screen_all(timings=None):
-        for k0 in range(0, S, K):
+        if NS > 1:
+            start = torch.cuda.Event()
+            start.record(stream)
+            for st in streams[1:]:
+                st.wait_event(start)
+        for j, k0 in enumerate(range(0, S, K)):
             k1 = min(S, k0 + K)
-            o = {key: v[:k1 - k0] for key, v in out.items()}
-            c.n1_screen_device(outages[k0:k1], o, stream)
-            all_iters[k0:k1].copy_(o["iters"])
-            all_status[k0:k1].copy_(o["status"])
-            if timings is not None:
+            cj, sj, oj = ctxs[j % NS], streams[j % NS], outs[j % NS]
+            o = {key: v[:k1 - k0] for key, v in oj.items()}
+            cj.n1_screen_device(outages[k0:k1], o, sj)
+            with torch.cuda.stream(sj):
+                all_iters[k0:k1].copy_(o["iters"])
+                all_status[k0:k1].copy_(o["status"])
+            if timings is not None and NS == 1:
                 torch.cuda.synchronize()
-                timings.append(c.last_timings())
+                timings.append(cj.last_timings())
+        if NS > 1:
+            for st in streams[1:]:
+                done = torch.cuda.Event()
+                done.record(st)
+                stream.wait_event(done)
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
     for _ in range(args.warmup):
@@ -211,7 +234,9 @@ def run_gpcg(args):
             ev1.record(stream)
             torch.cuda.synchronize()
             step_ms.append(ev0.elapsed_time(ev1))
-            if K < S:
+            if NS > 1:  # concurrent chunks: the step's span stands for the kernel time
+                kern_ms.append((0.0, step_ms[-1]))
+            elif K < S:
                 kern_ms.append((sum(t[0] for t in chunk_ms), sum(t[1] for t in chunk_ms)))
             else:
                 kern_ms.append(c.last_timings())
@@ -282,11 +307,12 @@ def run_gpcg(args):
             "data": "synthetic",
             "config": {"workload": f"{args.config}: {n} buses, {m} branches{xfmr_note(args)}, "
                                    f"{S} single-branch "
-                                   f"outages{f' in chunks of {K}' if n_chunks > 1 else ''}, "
+                                   f"outages{f' in chunks of {K}' if n_chunks > 1 else ''}"
+                                   f"{f' on {NS} streams' if NS > 1 else ''}, "
                                    f"tol 1e-4 p.u., {args.precond} base-case preconditioner, "
                                    f"{args.precision} inner PCG, FP64 mismatch/flows",
                        "n_bus": n, "n_branch": m, "scenarios": S, "tile": info["tile"],
-                       "chunk": K,
+                       "chunk": K, "streams": NS,
                        "l2": "flushed between steps (512 MiB write)",
                        "precond": args.precond, "precision": args.precision},
             "e2e": e2e, "gpu_launches": 2 * n_chunks * args.steps,
@@ -299,7 +325,8 @@ def run_gpcg(args):
                           "mean_inner_Q": float(iters[:, 2].mean())},
         }
         print(json.dumps(line), flush=True)
-    c.close()
+    for ci in ctxs:
+        ci.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -671,6 +698,8 @@ def main():
     ap.add_argument("--n-outages", type=int, default=0, help="screen only the first K outages (0 = all)")
     ap.add_argument("--chunk", type=int, default=0,
                     help="screen the outages in calls of this many (0 = one call)")
+    ap.add_argument("--streams", type=int, default=1,
+                    help="with --chunk: contexts and streams that take the chunks in turn")
     ap.add_argument("--cpu-sample", type=int, default=400)
     ap.add_argument("--plain-sample", type=int, default=64)
     ap.add_argument("--ref-sample", type=int, default=256)
