@@ -57,6 +57,8 @@ class Grid:
     rating: np.ndarray    # f64 [m]
     tap: Optional[np.ndarray] = None  # f64 [m] off-nominal turns ratio at the from end
                                       # (transformers); None: every branch is a line
+    Q_min: Optional[np.ndarray] = None  # f64 [n] reactive limits of the PV generators
+    Q_max: Optional[np.ndarray] = None  # (None: no limits)
     xy: Optional[np.ndarray] = None  # f64 [n, 2] bus coordinates (plotting only)
     meta: dict = dataclasses.field(default_factory=dict)
 

@@ -25,6 +25,14 @@ FDPF (eqs. (4)-(5), Sec. III.B): starting from a given state, repeat
   evaluate dP, dQ; stop when max|dP| (PV and PQ buses) and max|dQ| (PQ buses)
   are both <= tol; solve B' dtheta = dP/V, theta += dtheta; evaluate dQ;
   solve B'' dV = dQ/V, V += dV.
+
+Reactive limits of the PV generators (Q_min, Q_max per bus; the paper has
+none, this is the usual enforcement): when the iteration has converged, the
+generator output a PV bus needs, Q_g = Q(V) - Q_sched = -dQ, is compared
+with its limits; every PV bus outside them becomes a PQ bus whose generator
+is held at the violated limit (Q_sched += Q_max or Q_min), B'' gains its row,
+and the iteration continues from the current state.  A bus never switches
+back.  The result converges with every remaining PV bus within its limits.
 The paper gives no stopping rule for a diverging case; here a run is
 declared diverged when the mismatch is not finite, exceeds DIVERGE_LIMIT, or
 (for warm-started scenarios) has grown to DIVERGE_GROWTH times the smallest
@@ -174,14 +182,20 @@ def branch_flows(f, t, r, x, in_service, theta, V, tap=None):
     return np.where(on, Pf, 0.0), np.where(on, Pt, 0.0)
 
 
-def fdpf(grid, in_service, active, P_sched, theta0, V0, tol, max_outer, growth_rule=True):
+def fdpf(grid, in_service, active, P_sched, theta0, V0, tol, max_outer, growth_rule=True,
+         switched=None):
     """Fast-decoupled power flow on the buses marked ``active``.
 
     ``active`` excludes islanded buses (they keep theta = V = 0).  Returns
-    (theta, V, outer_iterations, status, final_max_mismatch).
+    (theta, V, outer_iterations, status, final_max_mismatch).  With reactive
+    limits on the grid, the buses switched to PQ are appended to the list
+    ``switched`` (when given) in the order they switched, lowest index first
+    within one switch.
     """
     n = grid.n_bus
-    bt = grid.bus_type
+    bt = grid.bus_type.copy()
+    Q_min, Q_max = getattr(grid, "Q_min", None), getattr(grid, "Q_max", None)
+    qlim = Q_min is not None and Q_max is not None
     pvpq = np.flatnonzero(active & (bt != SLACK))
     pq = np.flatnonzero(active & (bt == PQ))
     on = np.asarray(in_service, dtype=bool)
@@ -193,7 +207,7 @@ def fdpf(grid, in_service, active, P_sched, theta0, V0, tol, max_outer, growth_r
     solQ = DirectSolver(bdprime(n, grid.f, grid.t, grid.r, grid.x, on, pq, tap))
     theta = np.where(active, theta0, 0.0).astype(np.float64)
     V = np.where(active, V0, 0.0).astype(np.float64)
-    Q_sched = grid.Q_sched
+    Q_sched = grid.Q_sched.astype(np.float64).copy()
     k = 0
     best = np.inf
     while True:
@@ -204,6 +218,21 @@ def fdpf(grid, in_service, active, P_sched, theta0, V0, tol, max_outer, growth_r
             return theta, V, k, STATUS_DIVERGED, err
         best = min(best, err)
         if err <= tol:
+            if qlim:
+                cand = np.flatnonzero(active & (bt == PV))
+                qg = -dQ[cand]  # generator output beyond the scheduled injection
+                hi, lo = qg > Q_max[cand], qg < Q_min[cand]
+                if hi.any() or lo.any():
+                    Q_sched[cand[hi]] += Q_max[cand[hi]]
+                    Q_sched[cand[lo]] += Q_min[cand[lo]]
+                    sw = cand[hi | lo]
+                    bt[sw] = PQ
+                    if switched is not None:
+                        switched.extend(int(b) for b in sw)
+                    pq = np.flatnonzero(active & (bt == PQ))
+                    solQ = DirectSolver(bdprime(n, grid.f, grid.t, grid.r, grid.x, on, pq, tap))
+                    best = np.inf  # the switch raises the mismatch on purpose
+                    continue
             return theta, V, k, STATUS_OK, err
         if k >= max_outer:
             return theta, V, k, STATUS_MAXITER, err

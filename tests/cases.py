@@ -9,7 +9,8 @@ from gridgen import Grid
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
-def grid_from_arrays(bus_type, P, Q, Pgen, Vset, f, t, r, x, b_sh, rating=None, tap=None):
+def grid_from_arrays(bus_type, P, Q, Pgen, Vset, f, t, r, x, b_sh, rating=None, tap=None,
+                     Q_min=None, Q_max=None):
     m = len(f)
     return Grid(bus_type=np.asarray(bus_type, dtype=np.int8),
                 P_sched=np.asarray(P, dtype=np.float64),
@@ -20,7 +21,9 @@ def grid_from_arrays(bus_type, P, Q, Pgen, Vset, f, t, r, x, b_sh, rating=None, 
                 r=np.asarray(r, dtype=np.float64), x=np.asarray(x, dtype=np.float64),
                 b_sh=np.asarray(b_sh, dtype=np.float64),
                 rating=np.ones(m) if rating is None else np.asarray(rating, dtype=np.float64),
-                tap=None if tap is None else np.asarray(tap, dtype=np.float64))
+                tap=None if tap is None else np.asarray(tap, dtype=np.float64),
+                Q_min=None if Q_min is None else np.asarray(Q_min, dtype=np.float64),
+                Q_max=None if Q_max is None else np.asarray(Q_max, dtype=np.float64))
 
 
 def load_case(name):
@@ -28,7 +31,7 @@ def load_case(name):
         d = json.load(fh)
     return grid_from_arrays(d["bus_type"], d["P_sched"], d["Q_sched"], d["P_gen"],
                             d["V_set"], d["from"], d["to"], d["r"], d["x"], d["b_sh"],
-                            d.get("rating"), d.get("tap")), d
+                            d.get("rating"), d.get("tap"), d.get("Q_min"), d.get("Q_max")), d
 
 
 def random_tree_grid(n, seed, lossless=True, all_pv=True):

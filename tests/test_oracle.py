@@ -312,6 +312,80 @@ def test_generator_outages_kcl_and_balance():
         assert abs(res["V"][s][k] - g.V_set[k]) > 1e-6
 
 
+# -------------------------------------------- reactive limits of PV buses
+def test_two_bus_q_limit_closed_form():
+    g, d = load_case("two_bus_qlim.json")
+    sw = []
+    th, V, k, st, err = pf.fdpf(g, np.ones(1, bool), np.ones(2, bool), g.P_sched,
+                                np.zeros(2), g.V_set.astype(float), 1e-13, 100, False, sw)
+    assert st == pf.STATUS_OK and sw == [1]
+    v1, x, pc, qc = 1.0, 0.2, 0.3, -0.1        # P, Q consumed at bus 2 after the switch
+    a = v1 * v1 - 2 * qc * x
+    V2 = np.sqrt((a + np.sqrt(a * a - 4 * x * x * (pc * pc + qc * qc))) / 2)
+    assert abs(V[1] - V2) < 1e-12
+    assert abs(th[1] + np.arcsin(pc * x / (v1 * V2))) < 1e-12
+    # without the limit the bus holds its set point
+    g.Q_max = None
+    th2, V2b, _, st2, _ = pf.base_case(g, tol=1e-13)
+    assert st2 == pf.STATUS_OK and V2b[1] == 1.05
+
+
+def test_q_limit_lower_bound_and_no_switch():
+    """A limit that is never reached changes nothing; a lower limit above the
+    needed output holds the generator at Q_min."""
+    g, _ = load_case("two_bus_qlim.json")
+    g.Q_max = np.array([0.0, 5.0])
+    free = g.copy()
+    free.Q_min = free.Q_max = None
+    ref = pf.base_case(free, tol=1e-13)
+    got = pf.base_case(g, tol=1e-13)
+    np.testing.assert_array_equal(got[0], ref[0])
+    np.testing.assert_array_equal(got[1], ref[1])
+    g.Q_min = np.array([0.0, 0.5])               # more than the ~0.37 the set point needs
+    sw = []
+    th, V, k, st, err = pf.fdpf(g, np.ones(1, bool), np.ones(2, bool), g.P_sched,
+                                np.zeros(2), g.V_set.astype(float), 1e-13, 100, False, sw)
+    assert st == pf.STATUS_OK and sw == [1] and V[1] > 1.05
+    yb = pf.ybus_entries(2, g.f, g.t, g.r, g.x, g.b_sh, np.ones(1, bool))
+    dP, dQ = pf.mismatch(yb, g.P_sched, g.Q_sched, th, V)
+    assert abs(-dQ[1] - 0.5) < 1e-11             # the generator sits at Q_min
+
+
+@pytest.mark.parametrize("seed", [2, 6])
+def test_q_limits_match_newton_and_hold(seed):
+    """On a lossy tree with tight limits: every PV bus left is within its
+    limits at the result, every switched one is at a limit, and Newton on the
+    grid with those buses turned PQ at their limits reaches the same state."""
+    g, _ = random_tree_grid(14, seed, lossless=False, all_pv=False)
+    th0, V0, _, st, _ = pf.base_case(g, tol=1e-12)
+    yb = pf.ybus_entries(g.n_bus, g.f, g.t, g.r, g.x, g.b_sh, np.ones(g.n_branch, bool))
+    dP, dQ = pf.mismatch(yb, g.P_sched, g.Q_sched, th0, V0)
+    pv = np.flatnonzero(g.bus_type == 1)
+    qg = -dQ[pv]
+    g.Q_min = np.full(g.n_bus, -10.0)
+    g.Q_max = np.full(g.n_bus, 10.0)
+    g.Q_max[pv] = qg - 0.02 - 0.05 * np.abs(qg)  # every generator a little short
+    g.Q_min[pv] = qg - 1.0
+    sw = []
+    th, V, k, st, err = pf.fdpf(g, np.ones(g.n_branch, bool), np.ones(g.n_bus, bool),
+                                g.P_sched, np.zeros(g.n_bus), g.V_set.astype(float), 1e-12,
+                                200, False, sw)
+    assert st == pf.STATUS_OK and len(sw) > 0
+    dP, dQ = pf.mismatch(yb, g.P_sched, g.Q_sched, th, V)
+    left = np.setdiff1d(pv, sw)
+    assert np.all(-dQ[left] <= g.Q_max[left] + 1e-9) and np.all(-dQ[left] >= g.Q_min[left] - 1e-9)
+    h = g.copy()
+    h.bus_type = g.bus_type.copy()
+    h.Q_sched = g.Q_sched.copy()
+    for b in sw:
+        h.bus_type[b] = 0
+        h.Q_sched[b] += g.Q_max[b]             # all switched at Q_max here
+    h.Q_min = h.Q_max = None
+    thn, Vn = newton_solution(h)
+    np.testing.assert_allclose(th, thn, atol=1e-9)
+    np.testing.assert_allclose(V, Vn, atol=1e-9)
+
+
 # ----------------------------------------------- outage algebra (Sec. IV.B)
 def test_sherman_morrison_first_solve():
     """B'_s = B' - b a a^T (a = e_i - e_j): the solve with the re-formed
