@@ -58,9 +58,12 @@ enum {
   GPCG_SCEN_OK = 0,             /* converged to the mismatch tolerance */
   GPCG_SCEN_MAXITER = 1,        /* outer iteration cap reached */
   GPCG_SCEN_DIVERGED = 2,       /* non-finite or > 1e4 p.u. mismatch */
-  GPCG_SCEN_ISLAND_NO_GEN = 3   /* converged, but the main island had no
+  GPCG_SCEN_ISLAND_NO_GEN = 3,  /* converged, but the main island had no
                                    generator to take the re-dispatch: the
                                    slack absorbed it */
+  GPCG_SCEN_QLIM_OVERFLOW = 4   /* reactive limits: more PV buses had to turn
+                                   PQ than a scenario can hold (four rows,
+                                   a tripped generator's bus included) */
 };
 
 enum { GPCG_PQ = 0, GPCG_PV = 1, GPCG_SLACK = 2 };        /* bus_type */
@@ -96,7 +99,14 @@ enum {
  * phase shift, so with c = 1/tap[l]: Y_ff += c^2 (y + j b_sh/2),
  * Y_tt += y + j b_sh/2, Y_ft = Y_tf = -c y.  B'' takes the turns ratios
  * (w v v^T, v = c e_from - e_to), B' leaves them out (the XB scheme).
- * Outaging a transformer is a branch outage like any other. */
+ * Outaging a transformer is a branch outage like any other.
+ * Reactive limits (Q_min, Q_max; the paper models none): a PV generator's
+ * output is Q(V) - Q_sched at its bus.  When a scenario has converged, every
+ * PV bus whose generator is outside its limits turns PQ with the generator
+ * held at the violated limit (Q_sched + Q_max or Q_min), B'' gains its row,
+ * and the iteration goes on from there; a bus never turns back.  A scenario
+ * holds at most four such rows (GPCG_SCEN_QLIM_OVERFLOW beyond).  The base
+ * case must be within the limits (gpcg_base_solve fails otherwise). */
 typedef struct {
   int32_t n_bus;
   int32_t n_branch;
@@ -113,6 +123,8 @@ typedef struct {
   const double *rating;     /* [n_branch] flow limit, > 0 */
   const double *tap;        /* [n_branch] turns ratio at the from end, > 0;
                                NULL: every branch is a line (ratio 1) */
+  const double *Q_min;      /* [n_bus] reactive limits of the PV buses'    */
+  const double *Q_max;      /* generators (Q_min <= Q_max); both NULL: none */
 } gpcg_grid;
 
 typedef struct {

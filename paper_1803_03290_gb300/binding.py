@@ -18,7 +18,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "BASE_NOT_CONVERGED", 4: "BAS
           5: "TIMEOUT", 6: "OOM", 7: "NOT_READY"}
 PLAIN_FP64, BATCHED_FP32, BATCHED_FP64, BATCHED_FP32_F16 = 0, 1, 2, 3
 PRECOND_IC0, PRECOND_JACOBI, PRECOND_EXACT = 0, 1, 2
-SCEN_OK, SCEN_MAXITER, SCEN_DIVERGED, SCEN_ISLAND_NO_GEN = 0, 1, 2, 3
+SCEN_OK, SCEN_MAXITER, SCEN_DIVERGED, SCEN_ISLAND_NO_GEN, SCEN_QLIM_OVERFLOW = 0, 1, 2, 3, 4
 
 
 class GPCGError(RuntimeError):
@@ -32,7 +32,8 @@ class _Grid(C.Structure):
                 ("bus_type", C.c_void_p), ("P_sched", C.c_void_p), ("Q_sched", C.c_void_p),
                 ("P_gen", C.c_void_p), ("V_set", C.c_void_p), ("from_", C.c_void_p),
                 ("to", C.c_void_p), ("r", C.c_void_p), ("x", C.c_void_p),
-                ("b_sh", C.c_void_p), ("rating", C.c_void_p), ("tap", C.c_void_p)]
+                ("b_sh", C.c_void_p), ("rating", C.c_void_p), ("tap", C.c_void_p),
+                ("Q_min", C.c_void_p), ("Q_max", C.c_void_p)]
 
 
 class Options(C.Structure):
@@ -131,9 +132,10 @@ def _grid_struct(grid):
         x=np.ascontiguousarray(grid.x, dtype=np.float64),
         b_sh=np.ascontiguousarray(grid.b_sh, dtype=np.float64),
         rating=np.ascontiguousarray(grid.rating, dtype=np.float64))
-    tap = getattr(grid, "tap", None)
-    if tap is not None:
-        keep["tap"] = np.ascontiguousarray(tap, dtype=np.float64)
+    for k in ("tap", "Q_min", "Q_max"):
+        v = getattr(grid, k, None)
+        if v is not None:
+            keep[k] = np.ascontiguousarray(v, dtype=np.float64)
     g = _Grid(n_bus=int(grid.n_bus), n_branch=int(grid.n_branch),
               **{k: v.ctypes.data for k, v in keep.items()})
     return g, keep

@@ -112,7 +112,7 @@ struct MatDev {
   double* w = nullptr;  // per-branch weight
   double* c = nullptr;  // per-branch from-end factor (B'': 1 / turns ratio), null = 1
   // rows for buses without one (B'': tripped generators), see DevMatT
-  const int32_t* xptr = nullptr;
+  const int32_t *xptr = nullptr, *xnb = nullptr, *xbr = nullptr;
   int32_t* xrow = nullptr;
   double *xval = nullptr, *xdiag = nullptr;
   float *xval32 = nullptr, *xdiag32 = nullptr;
@@ -138,7 +138,7 @@ DevMatT<double> MatDev::view<double>(bool) const {
   M.xc = xc; M.xr = xr;
   M.w = w;
   M.c = c;
-  M.xptr = xptr; M.xrow = xrow; M.xval = xval; M.xdiag = xdiag;
+  M.xptr = xptr; M.xrow = xrow; M.xval = xval; M.xdiag = xdiag; M.xnb = xnb; M.xbr = xbr;
   return M;
 }
 template <>
@@ -164,7 +164,7 @@ DevMatT<float> MatDev::view<float>(bool f16) const {
   M.xr = f16 && xrh ? xrh : xr32;
   M.w = w;
   M.c = c;
-  M.xptr = xptr; M.xrow = xrow; M.xval = xval32; M.xdiag = xdiag32;
+  M.xptr = xptr; M.xrow = xrow; M.xval = xval32; M.xdiag = xdiag32; M.xnb = xnb; M.xbr = xbr;
   return M;
 }
 
@@ -484,6 +484,8 @@ static gpcg_status build_matrices(gpcg_ctx* c) {
     CUDA_TRY(dalloc(own, &M.xdiag, c->n));
     CUDA_TRY(dalloc(own, &M.xdiag32, c->n));
     M.xptr = c->G.adj_ptr;
+    M.xnb = c->G.adj_idx;
+    M.xbr = c->G.adj_br;
     launch_ext_rows(0, c->n, c->G.adj_ptr, c->G.adj_idx, c->G.adj_br, c->G.f, c->G.cf, c->wQ,
                     M.row_of_bus, M.xrow, M.xval, M.xval32, M.xdiag, M.xdiag32);
     CUDA_TRY(cudaGetLastError());
@@ -555,6 +557,14 @@ static gpcg_status validate_grid(const gpcg_grid* g, int* slack_out) {
       return fail(GPCG_ERR_INVALID_ARG, "branch %d: turns ratio %g is not positive and finite",
                   e, g->tap[e]);
   }
+  if (!g->Q_min != !g->Q_max)
+    return fail(GPCG_ERR_INVALID_ARG, "Q_min and Q_max come together (both or neither)");
+  if (g->Q_max)
+    for (int b = 0; b < n; ++b)
+      if (g->bus_type[b] == GPCG_PV &&
+          !(std::isfinite(g->Q_min[b]) && std::isfinite(g->Q_max[b]) && g->Q_min[b] <= g->Q_max[b]))
+        return fail(GPCG_ERR_INVALID_ARG, "bus %d: reactive limits [%g, %g] are not an interval",
+                    b, g->Q_min[b], g->Q_max[b]);
   *slack_out = slack;
   return GPCG_OK;
 }
@@ -589,13 +599,21 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
   const std::vector<int32_t>& U = c->user_of;
   const std::vector<int32_t>& I = c->intl;
   std::vector<int8_t> bt_i(n);
-  std::vector<double> P_i(n), Q_i(n), Pg_i(n), V_i(n);
+  std::vector<double> P_i(n), Q_i(n), Pg_i(n), V_i(n), qmin_i, qmax_i;
   for (int k = 0; k < n; ++k) {
     bt_i[k] = g->bus_type[U[k]];
     P_i[k] = g->P_sched[U[k]];
     Q_i[k] = g->Q_sched[U[k]];
     Pg_i[k] = g->P_gen[U[k]];
     V_i[k] = g->V_set[U[k]];
+  }
+  if (g->Q_max) {
+    qmin_i.resize(n);
+    qmax_i.resize(n);
+    for (int k = 0; k < n; ++k) {
+      qmin_i[k] = g->Q_min[U[k]];
+      qmax_i[k] = g->Q_max[U[k]];
+    }
   }
   std::vector<int32_t> f_i(m), t_i(m);
   for (int e = 0; e < m; ++e) {
@@ -635,6 +653,10 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
   UP(G.Q_sched, Q_i.data(), n);
   UP(G.P_gen, Pg_i.data(), n);
   UP(G.V_set, V_i.data(), n);
+  if (g->Q_max) {
+    UP(G.qmin, qmin_i.data(), n);
+    UP(G.qmax, qmax_i.data(), n);
+  }
   UP(G.f, f_i.data(), m);
   UP(G.t, t_i.data(), m);
   UP(G.user_of_bus, U.data(), n);
@@ -886,8 +908,8 @@ static Layout make_layout(const gpcg_ctx* c, int T, int slots, size_t vt_size) {
   Layout L;
   L.T = T;
   L.slots = slots;
-  // B' rows + its zero row; B'' rows + its zero row + the extension row
-  const size_t rows = (size_t)std::max(c->MP.plan.n + 1, c->MQ.plan.n + 2);
+  // B' rows + its zero row; B'' rows + its zero row + the extension rows
+  const size_t rows = (size_t)std::max(c->MP.plan.n + 1, c->MQ.plan.n + 1 + KX);
   L.vstride = rows * T;
   L.sstride = (size_t)c->n * T;
   L.vec_bytes = ((L.vstride * vt_size + 255) / 256) * 256;
@@ -976,6 +998,11 @@ extern "C" gpcg_status gpcg_base_solve(gpcg_ctx* c, double* theta, double* vm, d
   cudaFree(d_iters3);
   if (s != GPCG_OK) return s;
   c->base_outer = hit[0];
+  if (hs == GPCG_SCEN_QLIM_OVERFLOW) {
+    c->base_ok = false;
+    return fail(GPCG_ERR_BASE_NOT_CONVERGED,
+                "the base case needs PV generators outside their reactive limits");
+  }
   if (hs != GPCG_SCEN_OK) {
     c->base_ok = false;
     return fail(GPCG_ERR_BASE_NOT_CONVERGED,
@@ -1099,6 +1126,8 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
   P.out_bus_map = c->G.user_of_bus;
   P.out_iters = d_iters; P.out_status = d_stat;
   const bool plain = c->opt.precision == GPCG_PLAIN_FP64;
+  // generator outages and reactive limits take the kernel with extension rows
+  const bool ext = gen || c->G.qmax != nullptr;
   const bool f16 = c->opt.precision == GPCG_BATCHED_FP32_F16;
   const bool f32 = c->opt.precision == GPCG_BATCHED_FP32 || f16;
   // islanding for every outage (the autotuner's probes need it too)
@@ -1133,7 +1162,7 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
         Q.th0 = P.th0; Q.V0 = P.V0; Q.c0 = P.c0; Q.s0 = P.s0;
         Q.S = probe;
         Q.n_tiles = (probe + t - 1) / t;
-        int ps = f32 ? fdpf_max_blocks_per_sm<float>(t, gen) : fdpf_max_blocks_per_sm<double>(t, gen);
+        int ps = f32 ? fdpf_max_blocks_per_sm<float>(t, ext) : fdpf_max_blocks_per_sm<double>(t, ext);
         const int sl = std::max(1, std::min(Q.n_tiles, c->num_sms * std::max(ps, 1)));
         CUDA_TRY(cudaEventRecord(c->ev[3], st));
         rs = f32 ? run_fdpf<float>(c, st, Q, t, sl, f16) : run_fdpf<double>(c, st, Q, t, sl);
@@ -1147,11 +1176,11 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
       c->tile = bestT;
     }
     T = c->opt.tile ? c->opt.tile : (c->tile ? c->tile : 2);
-    if (gen) T = std::min(T, 8);  // the generator-outage kernel comes in tiles of 2, 4, 8
+    if (ext) T = std::min(T, 8);  // the kernel with extension rows: tiles of 2, 4, 8
     const int n_tiles = (int)((S + T - 1) / T);
     int per_sm = c->opt.ctas_per_sm;
     if (per_sm == 0)
-      per_sm = f32 ? fdpf_max_blocks_per_sm<float>(T, gen) : fdpf_max_blocks_per_sm<double>(T, gen);
+      per_sm = f32 ? fdpf_max_blocks_per_sm<float>(T, ext) : fdpf_max_blocks_per_sm<double>(T, ext);
     per_sm = std::max(per_sm, 1);
     slots = std::max(1, std::min(n_tiles, c->num_sms * per_sm));
     P.S = (int)S;
@@ -1710,7 +1739,7 @@ bool ctx_view(const gpcg_ctx* c, CtxView* v) {
   v->n = c->n;
   v->m = c->m;
   v->slack = c->slack;
-  v->rows = std::max(c->MP.plan.n, c->MQ.plan.n + 1);  // B'': + the extension row
+  v->rows = std::max(c->MP.plan.n, c->MQ.plan.n + KX);  // B'': + the extension rows
   v->slack_user = c->slack_user;
   v->u_f = c->u_f;
   v->u_t = c->u_t;

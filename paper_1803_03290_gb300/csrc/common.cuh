@@ -31,6 +31,7 @@ struct DevGrid {
   double *r = nullptr, *x = nullptr, *b_sh = nullptr, *rating = nullptr;
   double* inv_rating = nullptr;              // 1 / rating
   double* cf = nullptr;                      // 1 / turns ratio at the from end (1: a line)
+  double *qmin = nullptr, *qmax = nullptr;   // PV generators' reactive limits (null: none)
   double *g = nullptr, *by = nullptr;        // series admittance g + j b_y
   int32_t *adj_ptr = nullptr, *adj_idx = nullptr, *adj_br = nullptr;  // CSR adjacency
   double *Gii = nullptr, *Bii = nullptr;     // bus admittance diagonal
@@ -88,8 +89,14 @@ struct DevMatT {
   // xptr = its row pointer) the neighbour's row (-1: none) and the
   // off-diagonal value, and per bus the diagonal.  Null: not supported.
   const int32_t *xptr = nullptr, *xrow = nullptr;
+  const int32_t* xnb = nullptr;  // the neighbour bus of each adjacency entry
+  const int32_t* xbr = nullptr;  // the branch of each adjacency entry
   const VT *xval = nullptr, *xdiag = nullptr;
 };
+
+// Extension rows a lane may carry at once (see Ext in fdpf_ops.cuh): a
+// tripped generator's bus and PV buses switched to PQ at a reactive limit.
+constexpr int KX = 4;
 
 // What the islanding pass leaves for each scenario.
 struct ScenInfo {

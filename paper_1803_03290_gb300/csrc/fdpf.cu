@@ -114,7 +114,7 @@ __global__ void base_trig_kernel(int n, const double* th, double* c, double* s) 
 template <typename VT>
 cudaError_t launch_fdpf(cudaStream_t st, int T, int grid, const FdpfParams& P,
                         const DevMatT<VT>& MP, const DevMatT<VT>& MQ) {
-  if (P.sc.gen_bus) return launch_fdpf_gen<VT>(st, T, grid, P, MP, MQ);
+  if (P.sc.gen_bus || P.G.qmax) return launch_fdpf_gen<VT>(st, T, grid, P, MP, MQ);
   return launch_fdpf_g<false, VT>(st, T, grid, P, MP, MQ);
 }
 

@@ -21,9 +21,10 @@
 // indices and values sit at fixed offsets, so a thread issues all of a row's
 // gathers at once instead of walking a row pointer first.
 //
-// GEN: the kernel for generator outages, whose B'' has an extension row per
-// lane (the tripped generator's bus); the branch-outage kernel is built
-// without that code.
+// GEN: the kernel with B'' extension rows -- for generator outages (the
+// tripped generator's bus) and for grids whose PV generators have reactive
+// limits (buses switched to PQ at a limit); the kernel for branch outages
+// without limits is built without that code.
 #pragma once
 #include <math.h>
 #include "common.cuh"
@@ -41,14 +42,16 @@ __device__ __forceinline__ size_t ef_at(int bus, int lane) {
   return ((size_t)bus * T + lane) * 2;
 }
 
-// I_i = sum_j Y_ij V_j at bus i for one lane (no branch out of service),
-// summed like mismatch_pass.
+// I_i = sum_j Y_ij V_j at bus i for lane ln, the lane's outaged branch left
+// out (off the diagonal and its share of it), summed like mismatch_pass.
 template <int T>
-__device__ __forceinline__ double2 bus_current(const DevGrid& G, const double* __restrict__ EF,
-                                               int i, int ln) {
+__device__ __forceinline__ double2 bus_current(const DevGrid& G, const LaneState<T>& L,
+                                               const double* __restrict__ EF, int i, int ln) {
   double re = 0.0, im = 0.0;
+  const int br = L.l[ln];
   const int deg = __ldg(G.adj_deg + i);
   for (int a = 0; a < deg; ++a) {
+    if (__ldg(G.adj_brl + (size_t)i * KG + a) == br) continue;
     const int j = __ldg(G.adj_nbr + (size_t)i * KG + a);
     const double gv = __ldg(G.adj_g + (size_t)i * KG + a), bv = __ldg(G.adj_b + (size_t)i * KG + a);
     const double2 u = *reinterpret_cast<const double2*>(EF + ef_at<T>(j, ln));
@@ -57,6 +60,7 @@ __device__ __forceinline__ double2 bus_current(const DevGrid& G, const double* _
   }
   const int o1 = __ldg(G.adj_optr + i + 1);
   for (int e = __ldg(G.adj_optr + i); e < o1; ++e) {
+    if (__ldg(G.adj_obr + e) == br) continue;
     const int j = __ldg(G.adj_onbr + e);
     const double gw = __ldg(G.adj_og + e), bw = __ldg(G.adj_ob + e);
     const double2 u = *reinterpret_cast<const double2*>(EF + ef_at<T>(j, ln));
@@ -64,7 +68,12 @@ __device__ __forceinline__ double2 bus_current(const DevGrid& G, const double* _
     im = fma(-gw, u.y, fma(-bw, u.x, im));
   }
   const double2 v = *reinterpret_cast<const double2*>(EF + ef_at<T>(i, ln));
-  const double Gii = __ldg(G.Gii + i), Bii = __ldg(G.Bii + i);
+  double Gii = __ldg(G.Gii + i), Bii = __ldg(G.Bii + i);
+  if (i == L.fb[ln] || i == L.tb[ln]) {
+    const double c2 = i == L.fb[ln] ? L.cl[ln] * L.cl[ln] : 1.0;
+    Gii -= c2 * L.gl[ln];
+    Bii -= c2 * L.bl[ln];
+  }
   return make_double2(fma(Gii, v.x, fma(-Bii, v.y, re)), fma(Gii, v.y, fma(Bii, v.x, im)));
 }
 
@@ -188,14 +197,24 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
       for (int j = 0; j < 2; ++j) {
         if (!(j ? on1 : on0)) continue;
         const int ln = j ? l1 : l0;
-        // a tripped generator's bus keeps only its load, takes no share of
-        // the re-dispatch, and its reactive mismatch now counts
+        // a tripped generator's bus keeps only its load and takes no share
+        // of the re-dispatch; a bus with an extension row (that one, or a PV
+        // bus held at a reactive limit) is PQ with the injection qx
         const bool tr = GEN && WITH_P && i == L.gb[ln];
         const double pgl = tr ? 0.0 : pg;
+        bool xe = false;
+        double qx = qs;
+        if (GEN && WITH_P)
+          for (int s = 0; s < L.nx[ln]; ++s)
+            if (L.xb[ln][s] == i) { xe = true; qx = L.xq[ln][s]; }
         if (j ? w1 : w0) {
+          // the base-case state here: the base case is within the reactive limits
           const double dP = fma(L.coef[ln], pgl, __ldg(P.r0P + i)) - (tr ? Pgr : 0.0);
           upd_max_bits(errP.v[jp + j], dP);
-          if (bt == 0 || tr) upd_max_bits(errQ.v[jp + j], __ldg(P.r0Q + i));
+          if (bt == 0 || xe) {
+            const double q0 = __ldg(P.r0Q + i);
+            upd_max_bits(errQ.v[jp + j], xe ? q0 + (qx - qs) : q0);
+          }
           out.v[jp + j] = to_vt<VT>(dP) / to_vt<VT>(j ? vi.b : vi.a);
           continue;
         }
@@ -215,7 +234,20 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
           const double dP =
               fma(-ei, re, fma(-fi, im, fma(L.coef[ln], pgl, tr ? Ps - Pgr : Ps)));
           upd_max_bits(errP.v[jp + j], dP);
-          if (bt == 0 || tr) upd_max_bits(errQ.v[jp + j], fma(-fi, re, fma(ei, im, qs)));
+          if (bt == 0 || xe) upd_max_bits(errQ.v[jp + j], fma(-fi, re, fma(ei, im, qx)));
+          if (GEN && bt == 1 && !xe && G.qmax) {
+            // a PV generator's output Q(V) - Q_sched = -dQ against its limits:
+            // a violation is a candidate for the switch to PQ at that limit
+            const double qg = -fma(-fi, re, fma(ei, im, qs));
+            const double hi = __ldg(G.qmax + i), lo = __ldg(G.qmin + i);
+            if (qg > hi || qg < lo) {
+              const int at = atomicAdd(&L.nc[ln], 1);
+              if (at < KX) {
+                L.cb[ln][at] = i;
+                L.cq[ln][at] = qs + (qg > hi ? hi : lo);
+              }
+            }
+          }
           res = to_vt<VT>(dP) / to_vt<VT>(j ? vi.b : vi.a);
         } else {
           const double dQ = fma(-fi, re, fma(ei, im, qs));
@@ -227,26 +259,21 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
     if (WITH_P) stv<LP>(rhs + (size_t)__ldg(MP.row_of_bus + i) * T + g.lane, out);
     else stv<LP>(rhs + (size_t)k * T + g.lane, out);
   }
-  // the B'' extension rows of lanes with a tripped generator: dQ/V at its
-  // bus (zero for the tile's other lanes)
-  if (GEN && !WITH_P && MQ.xptr && g.rs == 0) {
-    bool any = false;
-#pragma unroll 1
-    for (int k = 0; k < T; ++k) any |= L.active[k] && L.gb[k] >= 0;
-    if (any)
+  // the B'' extension rows: dQ/V at their buses, with the reactive
+  // injection each holds
+  if (GEN && !WITH_P && MQ.xptr && g.rs == 0)
 #pragma unroll
-      for (int j = 0; j < LP; ++j) {
-        const int ln = g.lane + j, b = L.active[ln] ? L.gb[ln] : -1;
-        VT out = (VT)0;
-        if (b >= 0) {
-          const double2 I = bus_current<T>(G, EF, b, ln);
-          const double2 v = *reinterpret_cast<const double2*>(EF + ef_at<T>(b, ln));
-          const double dQ = fma(-v.y, I.x, fma(v.x, I.y, __ldg(G.Q_sched + b)));
-          out = to_vt<VT>(dQ) / to_vt<VT>(V[(size_t)b * T + ln]);
-        }
-        rhs[(size_t)(MQ.n + 1) * T + ln] = out;
+    for (int j = 0; j < LP; ++j) {
+      const int ln = g.lane + j;
+      if (!L.active[ln]) continue;
+      for (int s = 0; s < L.nx[ln]; ++s) {
+        const int b = L.xb[ln][s];
+        const double2 I = bus_current<T>(G, L, EF, b, ln);
+        const double2 v = *reinterpret_cast<const double2*>(EF + ef_at<T>(b, ln));
+        const double dQ = fma(-v.y, I.x, fma(v.x, I.y, L.xq[ln][s]));
+        rhs[(size_t)(MQ.n + 1 + s) * T + ln] = to_vt<VT>(dQ) / to_vt<VT>(V[(size_t)b * T + ln]);
       }
-  }
+    }
 }
 
 // (cos, sin) of theta + d from those of theta, by rotating through d:
@@ -326,13 +353,15 @@ __device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>&
       ef[1] = make_double2(v.b * c.b, v.b * s.b);
     }
   }
-  // |V| of a tripped generator's bus from the B'' extension row
+  // |V| of the extension rows' buses
   if (GEN && !IS_P && M.xptr && g.rs == 0)
 #pragma unroll
-    for (int j = 0; j < LP; ++j) {
-      const int ln = g.lane + j, b = L.active[ln] ? L.gb[ln] : -1;
-      if (b < 0) continue;
-      const size_t oe = (size_t)(M.n + 1) * T + ln;
+    for (int j = 0; j < LP; ++j)
+    for (int s = 0; s < L.nx[g.lane + j]; ++s) {
+      const int ln = g.lane + j;
+      if (!L.active[ln]) continue;
+      const int b = L.xb[ln][s];
+      const size_t oe = (size_t)(M.n + 1 + s) * T + ln;
       VT dx = x[oe];
       const VT xa = (VT)L.xalpha[ln];
       if (xa != (VT)0) dx = fma(xa, p[oe], dx);
@@ -368,6 +397,14 @@ __device__ __forceinline__ void setup_lane(const FdpfParams& P, const DevMatT<VT
   L.bl[ln] = l >= 0 ? G.by[l] + 0.5 * G.b_sh[l] : 0.0;
   L.cl[ln] = l >= 0 ? G.cf[l] : 1.0;
   L.gb[ln] = P.sc.gen_bus ? P.sc.gen_bus[s] : -1;
+  // the tripped generator's bus is the lane's first extension row, with its
+  // load's reactive injection
+  L.nx[ln] = L.gb[ln] >= 0 ? 1 : 0;
+  if (L.gb[ln] >= 0) {
+    L.xb[ln][0] = L.gb[ln];
+    L.xq[ln][0] = G.Q_sched[L.gb[ln]];
+  }
+  L.nc[ln] = 0;
   L.active[ln] = 1;
   L.outer[ln] = 0;
   L.inP[ln] = 0;
@@ -550,6 +587,8 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     L.wP[tid] = L.wQ[tid] = 0.0;
     L.cl[tid] = 1.0;
     L.gb[tid] = -1;
+    L.nx[tid] = 0;
+    L.nc[tid] = 0;
     L.lo[tid] = L.cnt[tid] = 0;
   }
   __syncthreads();
@@ -612,6 +651,34 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
         else if (e2 <= P.tol) st = 0;
         else if (L.outer[ln] >= P.max_outer) st = 1;
         L.best[ln] = fmin(L.best[ln], e2);
+        if (GEN && st == 0 && L.nc[ln] > 0) {
+          // converged with PV generators outside their reactive limits: they
+          // turn PQ at the violated limit (in bus order) and the iteration
+          // goes on; the base case must be within its limits, and a lane
+          // holds at most KX extension rows
+          const int nc = L.nc[ln];
+          if (P.flat_start || L.nx[ln] + nc > KX) {
+            st = 4;
+          } else {
+            for (int u = 1; u < nc; ++u)
+              for (int v = u; v > 0 && L.cb[ln][v - 1] > L.cb[ln][v]; --v) {
+                const int tb = L.cb[ln][v];
+                L.cb[ln][v] = L.cb[ln][v - 1];
+                L.cb[ln][v - 1] = tb;
+                const double tq = L.cq[ln][v];
+                L.cq[ln][v] = L.cq[ln][v - 1];
+                L.cq[ln][v - 1] = tq;
+              }
+            for (int u = 0; u < nc; ++u) {
+              L.xb[ln][L.nx[ln] + u] = L.cb[ln][u];
+              L.xq[ln][L.nx[ln] + u] = L.cq[ln][u];
+            }
+            L.nx[ln] += nc;
+            L.best[ln] = INFINITY;  // the switch raises the mismatch on purpose
+            st = -1;
+          }
+        }
+        if (GEN) L.nc[ln] = 0;
         if (st >= 0) {
           L.status[ln] = st;
           L.active[ln] = 0;
@@ -633,7 +700,7 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     __syncthreads();
     GPCG_PHASE(4);
     pcg_solve<T, VT, true, GEN>(P, MQ, L, x, r, p, q, z, L.raQ, L.rbQ, L.wQ, L.inQ,
-                                MQ.c ? L.cl : nullptr, GEN ? L.gb : nullptr);
+                                MQ.c ? L.cl : nullptr, GEN);
     GPCG_PHASE(5);
     update_pass<T, VT, false, GEN>(MQ, L, x, p, th, V, C, Sn, EF);
     if (g.rs == 0)

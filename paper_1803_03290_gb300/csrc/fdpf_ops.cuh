@@ -209,7 +209,15 @@ struct LaneState {
   int raP[T], rbP[T], raQ[T], rbQ[T];
   double wP[T], wQ[T], coef[T], gl[T], bl[T];
   double cl[T];  // the outaged branch's 1 / turns ratio (1 for a line)
-  int gb[T];     // bus of a tripped generator (-1: none): it gets a B'' row
+  int gb[T];     // bus of a tripped generator (-1: none)
+  // B'' extension rows: the tripped generator's bus and PV buses switched to
+  // PQ at a reactive limit, with the reactive injection each now holds
+  int nx[T], xb[T][KX];
+  double xq[T][KX];
+  // PV buses found outside their reactive limits by the last P mismatch
+  // (nc may exceed KX: only the first KX are kept), and their new injection
+  int nc[T], cb[T][KX];
+  double cq[T][KX];
   int active[T], outer[T], inP[T], inQ[T], status[T], nogen[T];
   double err[T], best[T];
   unsigned long long tphase[8];
@@ -403,15 +411,17 @@ struct Stamp {
   VT w[T], c[T];
 };
 
-// A tripped generator's bus gets the matrix row it lacks (B'': the PV bus
-// becomes PQ), one extension row per lane at vector row n + 1 (row n is the
-// zero row): per lane the bus (-1: none) and the row's diagonal.  The
-// base-case factor preconditions the rows it has, the diagonal this one
-// (a block-diagonal preconditioner).
+// A PV bus that becomes PQ -- its generator tripped, or held at a reactive
+// limit -- gets the B'' row it lacks: extension row s of a lane sits at
+// vector row n + 1 + s (row n is the zero row), up to KX per lane; per lane
+// their number, buses and diagonals.  The base-case factor preconditions
+// the rows it has, the diagonals these (a block-diagonal preconditioner).
 template <int T, typename VT>
 struct Ext {
-  int gb[T];
-  VT gd[T];
+  int n[T];
+  int lb[T];  // the lane's outaged branch (-1: none): not part of these rows
+  int gb[T][KX];
+  VT gd[T][KX];
 };
 
 template <int T, typename VT>
@@ -511,17 +521,19 @@ __device__ GPCG_LOOP_INLINE Vec<VT, Geo<T>::LP> spmv_pass(
             a.v[j] += i == ra ? -(S.c[ln] * wt) : wt;
           }
         }
-        // a neighbour of a tripped generator's bus: its coupling to the
-        // lane's extension row
+        // a neighbour of an extension row's bus: its coupling to that row
         if (X) {
 #pragma unroll
           for (int j = 0; j < LP; ++j) {
-            const int ln = g.lane + j, b = X->gb[ln];
-            if (b < 0) continue;
-            const VT ve = v_[(size_t)(M.n + 1) * T + ln];
-            const int e1 = __ldg(M.xptr + b + 1);
-            for (int e = __ldg(M.xptr + b); e < e1; ++e)
-              if (__ldg(M.xrow + e) == i) a.v[j] += __ldg(M.xval + e) * ve;
+            const int ln = g.lane + j, ne = X->n[ln];
+            for (int s = 0; s < ne; ++s) {
+              const int b = X->gb[ln][s];
+              const VT ve = v_[(size_t)(M.n + 1 + s) * T + ln];
+              const int e1 = __ldg(M.xptr + b + 1);
+              for (int e = __ldg(M.xptr + b); e < e1; ++e)
+                if (__ldg(M.xrow + e) == i && __ldg(M.xbr + e) != X->lb[ln])
+                  a.v[j] += __ldg(M.xval + e) * ve;
+            }
           }
         }
       }
@@ -563,19 +575,27 @@ __device__ GPCG_LOOP_INLINE Vec<VT, Geo<T>::LP> spmv_pass(
       }
     }
   }
-  // the extension rows (a lane without one has zeros there)
+  // the extension rows: couplings to the matrix rows and to the lane's
+  // other extension rows (two switched buses next to each other)
   if (DIRECTION && X && g.rs == 0) {
 #pragma unroll
-    for (int j = 0; j < LP; ++j) {
-      const int ln = g.lane + j, b = X->gb[ln];
-      const size_t o = (size_t)(M.n + 1) * T + ln;
+    for (int j = 0; j < LP; ++j)
+    for (int s = 0; s < X->n[g.lane + j]; ++s) {
+      const int ln = g.lane + j, ne = X->n[ln], b = X->gb[ln][s];
+      const size_t o = (size_t)(M.n + 1 + s) * T + ln;
       const VT ve = v_[o];
-      VT a = X->gd[ln] * ve;
-      if (b >= 0) {
-        const int e1 = __ldg(M.xptr + b + 1);
-        for (int e = __ldg(M.xptr + b); e < e1; ++e) {
-          const int rw = __ldg(M.xrow + e);
-          if (rw >= 0) a += __ldg(M.xval + e) * v_[(size_t)rw * T + ln];
+      VT a = X->gd[ln][s] * ve;
+      const int e1 = __ldg(M.xptr + b + 1);
+      for (int e = __ldg(M.xptr + b); e < e1; ++e) {
+        if (__ldg(M.xbr + e) == X->lb[ln]) continue;  // the outaged branch
+        const int rw = __ldg(M.xrow + e);
+        if (rw >= 0) {
+          a += __ldg(M.xval + e) * v_[(size_t)rw * T + ln];
+        } else {
+          const int nb = __ldg(M.xnb + e);
+          for (int t = 0; t < ne; ++t)
+            if (t != s && X->gb[ln][t] == nb)
+              a += __ldg(M.xval + e) * v_[(size_t)(M.n + 1 + t) * T + ln];
         }
       }
       VT pn = ve, qn = a;
@@ -607,9 +627,10 @@ __device__ __forceinline__ void ext_update(const DevMatT<VT>& M, const Ext<T, VT
   const Geo<T> g;
   if (!X || g.rs != 0) return;
 #pragma unroll
-  for (int j = 0; j < LP; ++j) {
+  for (int j = 0; j < LP; ++j)
+  for (int s = 0; s < X->n[g.lane + j]; ++s) {
     const int ln = g.lane + j;
-    const size_t o = (size_t)(M.n + 1) * T + ln;
+    const size_t o = (size_t)(M.n + 1 + s) * T + ln;
     VT rv = r[o];
     if (FUSED) {
       x[o] = fma(al.v[j], p[o], x[o]);
@@ -619,7 +640,7 @@ __device__ __forceinline__ void ext_update(const DevMatT<VT>& M, const Ext<T, VT
       x[o] = (VT)0;
     }
     rr.v[j] += rv * rv;
-    const VT d = X->gd[ln];
+    const VT d = X->gd[ln][s];
     const VT zv = d > (VT)0 ? rv / d : (VT)0;
     z[o] = zv;
     rz.v[j] += rv * zv;
@@ -980,7 +1001,7 @@ template <int T, typename VT, bool DEFER = false, bool GEN = false>
 __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT>& M, LaneState<T>& L, VT* x,
                           VT* r, VT* p, VT* q, VT* z, const int* ra_, const int* rb_,
                           const double* w_, int* iters, const double* c_ = nullptr,
-                          const int* gb_ = nullptr) {
+                          bool ext_rows = false) {
   constexpr int LP = Geo<T>::LP;
   __shared__ PcgLanes<T, VT> S;
   __shared__ Stamp<T, VT> St;
@@ -1000,9 +1021,20 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
     St.c[tid] = c_ ? (VT)c_[tid] : (VT)1;
     L.xalpha[tid] = 0.0;
     if constexpr (GEN) {
-      const int b = (gb_ && M.xptr && on) ? gb_[tid] : -1;
-      Xs.gb[tid] = b;
-      Xs.gd[tid] = b >= 0 ? M.xdiag[b] : (VT)0;
+      const int ne = (ext_rows && M.xptr && on) ? L.nx[tid] : 0;
+      Xs.n[tid] = ne;
+      Xs.lb[tid] = on ? L.l[tid] : -1;
+      for (int s = 0; s < ne; ++s) {
+        const int b = L.xb[tid][s];
+        Xs.gb[tid][s] = b;
+        // the diagonal without the outaged branch's term (w c^2 at its from
+        // end, w at its to end)
+        VT d = M.xdiag[b];
+        const VT c = c_ ? (VT)c_[tid] : (VT)1;
+        if (b == L.fb[tid]) d -= (VT)w_[tid] * c * c;
+        else if (b == L.tb[tid]) d -= (VT)w_[tid];
+        Xs.gd[tid][s] = d;
+      }
     }
   }
   if (g.rs == 0) {
@@ -1011,21 +1043,20 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
   }
   __syncthreads();
   unsigned long long filt = stamp_filter<T, VT>(St);
-  // lanes with a tripped generator: their extension rows, and the rows
-  // coupled to them in the filter
+  // lanes with extension rows: the rows coupled to them go in the filter
   bool ext = false;
   if constexpr (GEN) {
 #pragma unroll 1
-    for (int k = 0; k < T; ++k) {
-      const int b = Xs.gb[k];
-      if (b < 0) continue;
-      ext = true;
-      const int e1 = __ldg(M.xptr + b + 1);
-      for (int e = __ldg(M.xptr + b); e < e1; ++e) {
-        const int rw = __ldg(M.xrow + e);
-        if (rw >= 0) filt |= 1ull << (rw & 63);
+    for (int k = 0; k < T; ++k)
+      for (int s = 0; s < Xs.n[k]; ++s) {
+        const int b = Xs.gb[k][s];
+        ext = true;
+        const int e1 = __ldg(M.xptr + b + 1);
+        for (int e = __ldg(M.xptr + b); e < e1; ++e) {
+          const int rw = __ldg(M.xrow + e);
+          if (rw >= 0) filt |= 1ull << (rw & 63);
+        }
       }
-    }
   }
   const Ext<T, VT>* X = (GEN && ext) ? &Xs : nullptr;
   // islands in this tile: the SpMV then masks rows per lane

@@ -86,7 +86,10 @@ extern "C" gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx* ctx, const int32_t* outa
 
   // layout: [counter, error flag] [per-scenario island data] [solve slots]
   const size_t S = (size_t)n_out;
-  const int T = c.opt.tile ? c.opt.tile : (c.tile ? c.tile : 2);
+  // reactive limits take the kernel with extension rows (tiles of 2, 4, 8)
+  const bool ext = c.G.qmax != nullptr;
+  int T = c.opt.tile ? c.opt.tile : (c.tile ? c.tile : 2);
+  if (ext) T = std::min(T, 8);
   const bool f32 = c.opt.precision != GPCG_BATCHED_FP64;
   const size_t vt = f32 ? 4 : 8;
   const size_t head = 256;
@@ -102,7 +105,8 @@ extern "C" gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx* ctx, const int32_t* outa
                S, c.n, head + scen + per_slot, cap);
   const int n_tiles = (int)((S + T - 1) / T);
   int per_sm = c.opt.ctas_per_sm;
-  if (per_sm == 0) per_sm = f32 ? fdpf_max_blocks_per_sm<float>(T) : fdpf_max_blocks_per_sm<double>(T);
+  if (per_sm == 0)
+    per_sm = f32 ? fdpf_max_blocks_per_sm<float>(T, ext) : fdpf_max_blocks_per_sm<double>(T, ext);
   per_sm = std::max(per_sm, 1);
   const size_t fit = (cap - head - scen) / per_slot;
   const int slots = (int)std::max<size_t>(1, std::min<size_t>(

@@ -13,8 +13,30 @@ from oracle import screen
 XFMR = {"grid120_xfmr": ("grid120", 0.15), "grid2k_xfmr": ("grid2k", 0.1)}
 
 
+# Grids with reactive limits around their PV generators' base-case output:
+# Q_max = Q_g + 0.05 + 0.1 |Q_g|, Q_min = Q_g - 0.05 - 0.1 |Q_g|, so the base
+# case is within them and outages push some generators out.
+QLIM = {"grid120_qlim": "grid120", "grid2k_qlim": "grid2k"}
+
+
+def _with_q_limits(g):
+    th, V, _, st, _ = pf.base_case(g, tol=1e-11, max_outer=200)
+    assert st == pf.STATUS_OK
+    yb = pf.ybus_entries(g.n_bus, g.f, g.t, g.r, g.x, g.b_sh, np.ones(g.n_branch, bool), g.tap)
+    _, dQ = pf.mismatch(yb, g.P_sched, g.Q_sched, th, V)
+    qg = -dQ
+    g = g.copy()
+    g.Q_max = qg + 0.05 + 0.1 * np.abs(qg)
+    g.Q_min = qg - 0.05 - 0.1 * np.abs(qg)
+    return g
+
+
 @functools.lru_cache(maxsize=None)
 def grid(name):
+    if name in QLIM:
+        g = _with_q_limits(config_grid(QLIM[name]))
+        g.meta["config"] = name
+        return g
     if name in XFMR:
         base, frac = XFMR[name]
         g = make_grid(gen_share=1.0, xfmr_frac=frac, **CONFIGS[base])
