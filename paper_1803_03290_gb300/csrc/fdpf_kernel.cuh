@@ -205,8 +205,8 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
         bool xe = false;
         double qx = qs;
         if (GEN && WITH_P)
-          for (int s = 0; s < L.nx[ln]; ++s)
-            if (L.xb[ln][s] == i) { xe = true; qx = L.xq[ln][s]; }
+          for (int s = 0; s < L.sw->nx[ln]; ++s)
+            if (L.sw->xb[ln][s] == i) { xe = true; qx = L.sw->xq[ln][s]; }
         if (j ? w1 : w0) {
           // the base-case state here: the base case is within the reactive limits
           const double dP = fma(L.coef[ln], pgl, __ldg(P.r0P + i)) - (tr ? Pgr : 0.0);
@@ -241,10 +241,10 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
             const double qg = -fma(-fi, re, fma(ei, im, qs));
             const double hi = __ldg(G.qmax + i), lo = __ldg(G.qmin + i);
             if (qg > hi || qg < lo) {
-              const int at = atomicAdd(&L.nc[ln], 1);
+              const int at = atomicAdd(&L.sw->nc[ln], 1);
               if (at < KX) {
-                L.cb[ln][at] = i;
-                L.cq[ln][at] = qs + (qg > hi ? hi : lo);
+                L.sw->cb[ln][at] = i;
+                L.sw->cq[ln][at] = qs + (qg > hi ? hi : lo);
               }
             }
           }
@@ -266,11 +266,11 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
     for (int j = 0; j < LP; ++j) {
       const int ln = g.lane + j;
       if (!L.active[ln]) continue;
-      for (int s = 0; s < L.nx[ln]; ++s) {
-        const int b = L.xb[ln][s];
+      for (int s = 0; s < L.sw->nx[ln]; ++s) {
+        const int b = L.sw->xb[ln][s];
         const double2 I = bus_current<T>(G, L, EF, b, ln);
         const double2 v = *reinterpret_cast<const double2*>(EF + ef_at<T>(b, ln));
-        const double dQ = fma(-v.y, I.x, fma(v.x, I.y, L.xq[ln][s]));
+        const double dQ = fma(-v.y, I.x, fma(v.x, I.y, L.sw->xq[ln][s]));
         rhs[(size_t)(MQ.n + 1 + s) * T + ln] = to_vt<VT>(dQ) / to_vt<VT>(V[(size_t)b * T + ln]);
       }
     }
@@ -357,10 +357,10 @@ __device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>&
   if (GEN && !IS_P && M.xptr && g.rs == 0)
 #pragma unroll
     for (int j = 0; j < LP; ++j)
-    for (int s = 0; s < L.nx[g.lane + j]; ++s) {
+    for (int s = 0; s < L.sw->nx[g.lane + j]; ++s) {
       const int ln = g.lane + j;
       if (!L.active[ln]) continue;
-      const int b = L.xb[ln][s];
+      const int b = L.sw->xb[ln][s];
       const size_t oe = (size_t)(M.n + 1 + s) * T + ln;
       VT dx = x[oe];
       const VT xa = (VT)L.xalpha[ln];
@@ -399,12 +399,14 @@ __device__ __forceinline__ void setup_lane(const FdpfParams& P, const DevMatT<VT
   L.gb[ln] = P.sc.gen_bus ? P.sc.gen_bus[s] : -1;
   // the tripped generator's bus is the lane's first extension row, with its
   // load's reactive injection
-  L.nx[ln] = L.gb[ln] >= 0 ? 1 : 0;
-  if (L.gb[ln] >= 0) {
-    L.xb[ln][0] = L.gb[ln];
-    L.xq[ln][0] = G.Q_sched[L.gb[ln]];
+  if (L.sw) {
+    L.sw->nx[ln] = L.gb[ln] >= 0 ? 1 : 0;
+    if (L.gb[ln] >= 0) {
+      L.sw->xb[ln][0] = L.gb[ln];
+      L.sw->xq[ln][0] = G.Q_sched[L.gb[ln]];
+    }
+    L.sw->nc[ln] = 0;
   }
-  L.nc[ln] = 0;
   L.active[ln] = 1;
   L.outer[ln] = 0;
   L.inP[ln] = 0;
@@ -553,6 +555,12 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     memcpy(mbuf[0], &MP_, sizeof(DevMatT<VT>));
     memcpy(mbuf[1], &MQ_, sizeof(DevMatT<VT>));
   }
+  if constexpr (GEN) {
+    __shared__ SwitchState<T> sw;  // the extension rows' lane state
+    if (tid == 0) L.sw = &sw;
+  } else {
+    if (tid == 0) L.sw = nullptr;
+  }
   __syncthreads();
   const FdpfParams& P = *reinterpret_cast<const FdpfParams*>(pbuf);
   const DevMatT<VT>& MP = *reinterpret_cast<const DevMatT<VT>*>(mbuf[0]);
@@ -587,8 +595,10 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     L.wP[tid] = L.wQ[tid] = 0.0;
     L.cl[tid] = 1.0;
     L.gb[tid] = -1;
-    L.nx[tid] = 0;
-    L.nc[tid] = 0;
+    if constexpr (GEN) {
+      L.sw->nx[tid] = 0;
+      L.sw->nc[tid] = 0;
+    }
     L.lo[tid] = L.cnt[tid] = 0;
   }
   __syncthreads();
@@ -651,34 +661,34 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
         else if (e2 <= P.tol) st = 0;
         else if (L.outer[ln] >= P.max_outer) st = 1;
         L.best[ln] = fmin(L.best[ln], e2);
-        if (GEN && st == 0 && L.nc[ln] > 0) {
+        if (GEN && st == 0 && L.sw->nc[ln] > 0) {
           // converged with PV generators outside their reactive limits: they
           // turn PQ at the violated limit (in bus order) and the iteration
           // goes on; the base case must be within its limits, and a lane
           // holds at most KX extension rows
-          const int nc = L.nc[ln];
-          if (P.flat_start || L.nx[ln] + nc > KX) {
+          const int nc = L.sw->nc[ln];
+          if (P.flat_start || L.sw->nx[ln] + nc > KX) {
             st = 4;
           } else {
             for (int u = 1; u < nc; ++u)
-              for (int v = u; v > 0 && L.cb[ln][v - 1] > L.cb[ln][v]; --v) {
-                const int tb = L.cb[ln][v];
-                L.cb[ln][v] = L.cb[ln][v - 1];
-                L.cb[ln][v - 1] = tb;
-                const double tq = L.cq[ln][v];
-                L.cq[ln][v] = L.cq[ln][v - 1];
-                L.cq[ln][v - 1] = tq;
+              for (int v = u; v > 0 && L.sw->cb[ln][v - 1] > L.sw->cb[ln][v]; --v) {
+                const int tb = L.sw->cb[ln][v];
+                L.sw->cb[ln][v] = L.sw->cb[ln][v - 1];
+                L.sw->cb[ln][v - 1] = tb;
+                const double tq = L.sw->cq[ln][v];
+                L.sw->cq[ln][v] = L.sw->cq[ln][v - 1];
+                L.sw->cq[ln][v - 1] = tq;
               }
             for (int u = 0; u < nc; ++u) {
-              L.xb[ln][L.nx[ln] + u] = L.cb[ln][u];
-              L.xq[ln][L.nx[ln] + u] = L.cq[ln][u];
+              L.sw->xb[ln][L.sw->nx[ln] + u] = L.sw->cb[ln][u];
+              L.sw->xq[ln][L.sw->nx[ln] + u] = L.sw->cq[ln][u];
             }
-            L.nx[ln] += nc;
+            L.sw->nx[ln] += nc;
             L.best[ln] = INFINITY;  // the switch raises the mismatch on purpose
             st = -1;
           }
         }
-        if (GEN) L.nc[ln] = 0;
+        if constexpr (GEN) L.sw->nc[ln] = 0;
         if (st >= 0) {
           L.status[ln] = st;
           L.active[ln] = 0;

@@ -200,6 +200,19 @@ struct Geo {
 };
 
 // ------------------------------------------------------------ lane state
+// Per-lane B'' extension rows (the kernel with extension rows keeps this
+// in shared memory of its own): the tripped generator's bus and PV buses
+// switched to PQ at a reactive limit, with the reactive injection each now
+// holds; and the PV buses the last P mismatch found outside their limits
+// (nc may exceed KX: only the first KX are kept), with their new injection.
+template <int T>
+struct SwitchState {
+  int nx[T], xb[T][KX];
+  double xq[T][KX];
+  int nc[T], cb[T][KX];
+  double cq[T][KX];
+};
+
 constexpr int NRED_SITES = 10;  // reduction sites with a buffer of their own
 enum RedSite { RS_BB = 0, RS_RZ0, RS_PQ, RS_RR, RS_RZ, RS_ERRP, RS_ERRQ, RS_LOAD, RS_RQ, RS_QQ };
 
@@ -210,14 +223,6 @@ struct LaneState {
   double wP[T], wQ[T], coef[T], gl[T], bl[T];
   double cl[T];  // the outaged branch's 1 / turns ratio (1 for a line)
   int gb[T];     // bus of a tripped generator (-1: none)
-  // B'' extension rows: the tripped generator's bus and PV buses switched to
-  // PQ at a reactive limit, with the reactive injection each now holds
-  int nx[T], xb[T][KX];
-  double xq[T][KX];
-  // PV buses found outside their reactive limits by the last P mismatch
-  // (nc may exceed KX: only the first KX are kept), and their new injection
-  int nc[T], cb[T][KX];
-  double cq[T][KX];
   int active[T], outer[T], inP[T], inQ[T], status[T], nogen[T];
   double err[T], best[T];
   unsigned long long tphase[8];
@@ -228,6 +233,7 @@ struct LaneState {
   double red2[NRED_SITES * (NTHREADS / 32) * T];
   int flag;
   int drained;
+  SwitchState<T>* sw;  // the kernel with extension rows only (else null)
 };
 
 // Sum (or max) over the row slots of each lane's partial values, for
@@ -416,12 +422,12 @@ struct Stamp {
 // vector row n + 1 + s (row n is the zero row), up to KX per lane; per lane
 // their number, buses and diagonals.  The base-case factor preconditions
 // the rows it has, the diagonals these (a block-diagonal preconditioner).
-template <int T, typename VT>
+template <int T, typename VT, int K = KX>
 struct Ext {
   int n[T];
   int lb[T];  // the lane's outaged branch (-1: none): not part of these rows
-  int gb[T][KX];
-  VT gd[T][KX];
+  int gb[T][K];
+  VT gd[T][K];
 };
 
 template <int T, typename VT>
@@ -1005,7 +1011,7 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
   constexpr int LP = Geo<T>::LP;
   __shared__ PcgLanes<T, VT> S;
   __shared__ Stamp<T, VT> St;
-  __shared__ Ext<T, VT> Xs;
+  __shared__ Ext<T, VT, GEN ? KX : 1> Xs;  // the kernel without extension rows needs none
   // right-hand side and y of the schedule's tail (lane groups: 16-byte aligned)
   __shared__ __align__(16) VT zt[TAIL_ROWS * T];
   const Geo<T> g;
@@ -1021,11 +1027,11 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
     St.c[tid] = c_ ? (VT)c_[tid] : (VT)1;
     L.xalpha[tid] = 0.0;
     if constexpr (GEN) {
-      const int ne = (ext_rows && M.xptr && on) ? L.nx[tid] : 0;
+      const int ne = (ext_rows && M.xptr && on) ? L.sw->nx[tid] : 0;
       Xs.n[tid] = ne;
       Xs.lb[tid] = on ? L.l[tid] : -1;
       for (int s = 0; s < ne; ++s) {
-        const int b = L.xb[tid][s];
+        const int b = L.sw->xb[tid][s];
         Xs.gb[tid][s] = b;
         // the diagonal without the outaged branch's term (w c^2 at its from
         // end, w at its to end)
@@ -1058,7 +1064,9 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
         }
       }
   }
-  const Ext<T, VT>* X = (GEN && ext) ? &Xs : nullptr;
+  const Ext<T, VT>* X = nullptr;
+  if constexpr (GEN)
+    if (ext) X = &Xs;
   // islands in this tile: the SpMV then masks rows per lane
   bool islands = false;
 #pragma unroll 1
