@@ -1,7 +1,8 @@
-// Instantiation of the persistent N-1 kernel (fdpf_kernel.cuh) for
-// generator outages: B'' carries one extension row per lane, the bus whose
-// generator trips (Sec. IV.A, the loss of a single component).  Tiles of 2,
-// 4 and 8 scenarios.
+// Instantiation of the persistent N-1 kernel (fdpf_kernel.cuh) with B''
+// extension rows: for generator outages (the bus whose generator trips,
+// Sec. IV.A, the loss of a single component) and for grids whose PV
+// generators have reactive limits (buses held at a limit turn PQ).  Tiles
+// of 2, 4 and 8 scenarios.
 #include "fdpf_kernel.cuh"
 
 namespace gpcg {

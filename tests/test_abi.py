@@ -59,5 +59,16 @@ def test_invalid_arguments_fail_before_the_gpu():
         with pytest.raises(binding.GPCGError) as e:
             binding.GPCG(bad)
         assert e.value.status == 1 and "turns ratio" in str(e.value)
+    pv = int(np.flatnonzero(g.bus_type == 1)[0])
+    bad = g.copy()
+    bad.Q_max = np.ones(g.n_bus)               # Q_max without Q_min
+    with pytest.raises(binding.GPCGError) as e:
+        binding.GPCG(bad)
+    assert e.value.status == 1 and "Q_min and Q_max" in str(e.value)
+    bad.Q_min = np.zeros(g.n_bus)
+    bad.Q_min[pv] = 2.0                        # an empty interval at a PV bus
+    with pytest.raises(binding.GPCGError) as e:
+        binding.GPCG(bad)
+    assert e.value.status == 1 and "reactive limits" in str(e.value)
     with pytest.raises(binding.GPCGError):
         binding.default_options(precision=7) and binding.GPCG(g, precision=7)
