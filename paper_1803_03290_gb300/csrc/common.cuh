@@ -16,7 +16,7 @@ constexpr int KG = 6;   // bus adjacency of the mismatch
 // Tail of the forward level schedule solved with the dense inverse of its
 // factor block: the last levels, together at most TAIL_ROWS rows.
 #ifndef GPCG_TAIL_ROWS
-#define GPCG_TAIL_ROWS 256
+#define GPCG_TAIL_ROWS 248
 #endif
 constexpr int TAIL_ROWS = GPCG_TAIL_ROWS;
 

@@ -91,7 +91,8 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
                                                const double* __restrict__ V,
                                                VT* __restrict__ rhs,
                                                Vec<unsigned long long, Geo<T>::LP>& errP,
-                                               Vec<unsigned long long, Geo<T>::LP>& errQ) {
+                                               Vec<unsigned long long, Geo<T>::LP>& errQ,
+                                               SwitchState<T>* SW = nullptr) {
   constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
   const DevGrid& G = P.G;
@@ -205,8 +206,8 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
         bool xe = false;
         double qx = qs;
         if (GEN && WITH_P)
-          for (int s = 0; s < L.sw->nx[ln]; ++s)
-            if (L.sw->xb[ln][s] == i) { xe = true; qx = L.sw->xq[ln][s]; }
+          for (int s = 0; s < SW->nx[ln]; ++s)
+            if (SW->xb[ln][s] == i) { xe = true; qx = SW->xq[ln][s]; }
         if (j ? w1 : w0) {
           // the base-case state here: the base case is within the reactive limits
           const double dP = fma(L.coef[ln], pgl, __ldg(P.r0P + i)) - (tr ? Pgr : 0.0);
@@ -241,10 +242,10 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
             const double qg = -fma(-fi, re, fma(ei, im, qs));
             const double hi = __ldg(G.qmax + i), lo = __ldg(G.qmin + i);
             if (qg > hi || qg < lo) {
-              const int at = atomicAdd(&L.sw->nc[ln], 1);
+              const int at = atomicAdd(&SW->nc[ln], 1);
               if (at < KX) {
-                L.sw->cb[ln][at] = i;
-                L.sw->cq[ln][at] = qs + (qg > hi ? hi : lo);
+                SW->cb[ln][at] = i;
+                SW->cq[ln][at] = qs + (qg > hi ? hi : lo);
               }
             }
           }
@@ -266,11 +267,11 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
     for (int j = 0; j < LP; ++j) {
       const int ln = g.lane + j;
       if (!L.active[ln]) continue;
-      for (int s = 0; s < L.sw->nx[ln]; ++s) {
-        const int b = L.sw->xb[ln][s];
+      for (int s = 0; s < SW->nx[ln]; ++s) {
+        const int b = SW->xb[ln][s];
         const double2 I = bus_current<T>(G, L, EF, b, ln);
         const double2 v = *reinterpret_cast<const double2*>(EF + ef_at<T>(b, ln));
-        const double dQ = fma(-v.y, I.x, fma(v.x, I.y, L.sw->xq[ln][s]));
+        const double dQ = fma(-v.y, I.x, fma(v.x, I.y, SW->xq[ln][s]));
         rhs[(size_t)(MQ.n + 1 + s) * T + ln] = to_vt<VT>(dQ) / to_vt<VT>(V[(size_t)b * T + ln]);
       }
     }
@@ -305,7 +306,8 @@ template <int T, typename VT, bool IS_P, bool GEN>
 __device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>& L,
                                              const VT* __restrict__ x,
                                              const VT* __restrict__ p, double* th, double* V,
-                                             double* C, double* Sn, double* EF) {
+                                             double* C, double* Sn, double* EF,
+                                             const SwitchState<T>* SW = nullptr) {
   constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
   bool any = false;
@@ -357,10 +359,10 @@ __device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>&
   if (GEN && !IS_P && M.xptr && g.rs == 0)
 #pragma unroll
     for (int j = 0; j < LP; ++j)
-    for (int s = 0; s < L.sw->nx[g.lane + j]; ++s) {
+    for (int s = 0; s < SW->nx[g.lane + j]; ++s) {
       const int ln = g.lane + j;
       if (!L.active[ln]) continue;
-      const int b = L.sw->xb[ln][s];
+      const int b = SW->xb[ln][s];
       const size_t oe = (size_t)(M.n + 1 + s) * T + ln;
       VT dx = x[oe];
       const VT xa = (VT)L.xalpha[ln];
@@ -376,7 +378,8 @@ __device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>&
 // Scenario info of a lane taking scenario s (thread `ln`, one per lane).
 template <int T, typename VT>
 __device__ __forceinline__ void setup_lane(const FdpfParams& P, const DevMatT<VT>& MP,
-                                           const DevMatT<VT>& MQ, LaneState<T>& L, int ln) {
+                                           const DevMatT<VT>& MQ, LaneState<T>& L, int ln,
+                                           SwitchState<T>* SW) {
   const DevGrid& G = P.G;
   const int s = L.scen[ln];
   const int l = P.sc.outage[s];
@@ -399,13 +402,13 @@ __device__ __forceinline__ void setup_lane(const FdpfParams& P, const DevMatT<VT
   L.gb[ln] = P.sc.gen_bus ? P.sc.gen_bus[s] : -1;
   // the tripped generator's bus is the lane's first extension row, with its
   // load's reactive injection
-  if (L.sw) {
-    L.sw->nx[ln] = L.gb[ln] >= 0 ? 1 : 0;
+  if (SW) {
+    SW->nx[ln] = L.gb[ln] >= 0 ? 1 : 0;
     if (L.gb[ln] >= 0) {
-      L.sw->xb[ln][0] = L.gb[ln];
-      L.sw->xq[ln][0] = G.Q_sched[L.gb[ln]];
+      SW->xb[ln][0] = L.gb[ln];
+      SW->xq[ln][0] = G.Q_sched[L.gb[ln]];
     }
-    L.sw->nc[ln] = 0;
+    SW->nc[ln] = 0;
   }
   L.active[ln] = 1;
   L.outer[ln] = 0;
@@ -555,11 +558,11 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     memcpy(mbuf[0], &MP_, sizeof(DevMatT<VT>));
     memcpy(mbuf[1], &MQ_, sizeof(DevMatT<VT>));
   }
+  // the extension rows' lane state, in the kernel with extension rows only
+  SwitchState<T>* SW = nullptr;
   if constexpr (GEN) {
-    __shared__ SwitchState<T> sw;  // the extension rows' lane state
-    if (tid == 0) L.sw = &sw;
-  } else {
-    if (tid == 0) L.sw = nullptr;
+    __shared__ SwitchState<T> sw;
+    SW = &sw;
   }
   __syncthreads();
   const FdpfParams& P = *reinterpret_cast<const FdpfParams*>(pbuf);
@@ -596,8 +599,8 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     L.cl[tid] = 1.0;
     L.gb[tid] = -1;
     if constexpr (GEN) {
-      L.sw->nx[tid] = 0;
-      L.sw->nc[tid] = 0;
+      SW->nx[tid] = 0;
+      SW->nc[tid] = 0;
     }
     L.lo[tid] = L.cnt[tid] = 0;
   }
@@ -631,7 +634,7 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
       }
     }
     __syncthreads();
-    if (tid < T && L.fresh[tid]) setup_lane<T, VT>(P, MP, MQ, L, tid);
+    if (tid < T && L.fresh[tid]) setup_lane<T, VT>(P, MP, MQ, L, tid, SW);
     __syncthreads();
     init_pass<T>(P, L, th, V, C, Sn, EF);
     __syncthreads();
@@ -643,7 +646,7 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     }
     // P half-step: mismatch + convergence test
     Vec<unsigned long long, LP> eP = vzero<unsigned long long, LP>(), eQ = eP;
-    mismatch_pass<T, VT, true, GEN>(P, MP, MQ, L, EF, V, r, eP, eQ);
+    mismatch_pass<T, VT, true, GEN>(P, MP, MQ, L, EF, V, r, eP, eQ, SW);
     const Vec<unsigned long long, LP> bP = lane_max_bits<T, RS_ERRP>(L, eP);
     const Vec<unsigned long long, LP> bQ = lane_max_bits<T, RS_ERRQ>(L, eQ);
     if (g.rs == 0) {
@@ -661,34 +664,34 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
         else if (e2 <= P.tol) st = 0;
         else if (L.outer[ln] >= P.max_outer) st = 1;
         L.best[ln] = fmin(L.best[ln], e2);
-        if (GEN && st == 0 && L.sw->nc[ln] > 0) {
+        if (GEN && st == 0 && SW->nc[ln] > 0) {
           // converged with PV generators outside their reactive limits: they
           // turn PQ at the violated limit (in bus order) and the iteration
           // goes on; the base case must be within its limits, and a lane
           // holds at most KX extension rows
-          const int nc = L.sw->nc[ln];
-          if (P.flat_start || L.sw->nx[ln] + nc > KX) {
+          const int nc = SW->nc[ln];
+          if (P.flat_start || SW->nx[ln] + nc > KX) {
             st = 4;
           } else {
             for (int u = 1; u < nc; ++u)
-              for (int v = u; v > 0 && L.sw->cb[ln][v - 1] > L.sw->cb[ln][v]; --v) {
-                const int tb = L.sw->cb[ln][v];
-                L.sw->cb[ln][v] = L.sw->cb[ln][v - 1];
-                L.sw->cb[ln][v - 1] = tb;
-                const double tq = L.sw->cq[ln][v];
-                L.sw->cq[ln][v] = L.sw->cq[ln][v - 1];
-                L.sw->cq[ln][v - 1] = tq;
+              for (int v = u; v > 0 && SW->cb[ln][v - 1] > SW->cb[ln][v]; --v) {
+                const int tb = SW->cb[ln][v];
+                SW->cb[ln][v] = SW->cb[ln][v - 1];
+                SW->cb[ln][v - 1] = tb;
+                const double tq = SW->cq[ln][v];
+                SW->cq[ln][v] = SW->cq[ln][v - 1];
+                SW->cq[ln][v - 1] = tq;
               }
             for (int u = 0; u < nc; ++u) {
-              L.sw->xb[ln][L.sw->nx[ln] + u] = L.sw->cb[ln][u];
-              L.sw->xq[ln][L.sw->nx[ln] + u] = L.sw->cq[ln][u];
+              SW->xb[ln][SW->nx[ln] + u] = SW->cb[ln][u];
+              SW->xq[ln][SW->nx[ln] + u] = SW->cq[ln][u];
             }
-            L.sw->nx[ln] += nc;
+            SW->nx[ln] += nc;
             L.best[ln] = INFINITY;  // the switch raises the mismatch on purpose
             st = -1;
           }
         }
-        if constexpr (GEN) L.sw->nc[ln] = 0;
+        if constexpr (GEN) SW->nc[ln] = 0;
         if (st >= 0) {
           L.status[ln] = st;
           L.active[ln] = 0;
@@ -701,18 +704,18 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     if (!more) continue;
     pcg_solve<T, VT, true, GEN>(P, MP, L, x, r, p, q, z, L.raP, L.rbP, L.wP, L.inP);
     GPCG_PHASE(2);
-    update_pass<T, VT, true, GEN>(MP, L, x, p, th, V, C, Sn, EF);
+    update_pass<T, VT, true, GEN>(MP, L, x, p, th, V, C, Sn, EF, SW);
     __syncthreads();
     GPCG_PHASE(3);
     // Q half-step
     Vec<unsigned long long, LP> d0 = vzero<unsigned long long, LP>(), d1 = d0;
-    mismatch_pass<T, VT, false, GEN>(P, MP, MQ, L, EF, V, r, d0, d1);
+    mismatch_pass<T, VT, false, GEN>(P, MP, MQ, L, EF, V, r, d0, d1, SW);
     __syncthreads();
     GPCG_PHASE(4);
     pcg_solve<T, VT, true, GEN>(P, MQ, L, x, r, p, q, z, L.raQ, L.rbQ, L.wQ, L.inQ,
-                                MQ.c ? L.cl : nullptr, GEN);
+                                MQ.c ? L.cl : nullptr, SW);
     GPCG_PHASE(5);
-    update_pass<T, VT, false, GEN>(MQ, L, x, p, th, V, C, Sn, EF);
+    update_pass<T, VT, false, GEN>(MQ, L, x, p, th, V, C, Sn, EF, SW);
     if (g.rs == 0)
 #pragma unroll
       for (int j = 0; j < LP; ++j)

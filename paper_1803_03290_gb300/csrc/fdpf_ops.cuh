@@ -233,7 +233,6 @@ struct LaneState {
   double red2[NRED_SITES * (NTHREADS / 32) * T];
   int flag;
   int drained;
-  SwitchState<T>* sw;  // the kernel with extension rows only (else null)
 };
 
 // Sum (or max) over the row slots of each lane's partial values, for
@@ -1007,11 +1006,16 @@ template <int T, typename VT, bool DEFER = false, bool GEN = false>
 __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT>& M, LaneState<T>& L, VT* x,
                           VT* r, VT* p, VT* q, VT* z, const int* ra_, const int* rb_,
                           const double* w_, int* iters, const double* c_ = nullptr,
-                          bool ext_rows = false) {
+                          const SwitchState<T>* SW = nullptr) {
   constexpr int LP = Geo<T>::LP;
   __shared__ PcgLanes<T, VT> S;
   __shared__ Stamp<T, VT> St;
-  __shared__ Ext<T, VT, GEN ? KX : 1> Xs;  // the kernel without extension rows needs none
+  // the extension rows' block: in the kernel with extension rows only
+  Ext<T, VT>* Xw = nullptr;
+  if constexpr (GEN) {
+    __shared__ Ext<T, VT> Xs;
+    Xw = &Xs;
+  }
   // right-hand side and y of the schedule's tail (lane groups: 16-byte aligned)
   __shared__ __align__(16) VT zt[TAIL_ROWS * T];
   const Geo<T> g;
@@ -1027,19 +1031,19 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
     St.c[tid] = c_ ? (VT)c_[tid] : (VT)1;
     L.xalpha[tid] = 0.0;
     if constexpr (GEN) {
-      const int ne = (ext_rows && M.xptr && on) ? L.sw->nx[tid] : 0;
-      Xs.n[tid] = ne;
-      Xs.lb[tid] = on ? L.l[tid] : -1;
+      const int ne = (SW && M.xptr && on) ? SW->nx[tid] : 0;
+      Xw->n[tid] = ne;
+      Xw->lb[tid] = on ? L.l[tid] : -1;
       for (int s = 0; s < ne; ++s) {
-        const int b = L.sw->xb[tid][s];
-        Xs.gb[tid][s] = b;
+        const int b = SW->xb[tid][s];
+        Xw->gb[tid][s] = b;
         // the diagonal without the outaged branch's term (w c^2 at its from
         // end, w at its to end)
         VT d = M.xdiag[b];
         const VT c = c_ ? (VT)c_[tid] : (VT)1;
         if (b == L.fb[tid]) d -= (VT)w_[tid] * c * c;
         else if (b == L.tb[tid]) d -= (VT)w_[tid];
-        Xs.gd[tid][s] = d;
+        Xw->gd[tid][s] = d;
       }
     }
   }
@@ -1054,8 +1058,8 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
   if constexpr (GEN) {
 #pragma unroll 1
     for (int k = 0; k < T; ++k)
-      for (int s = 0; s < Xs.n[k]; ++s) {
-        const int b = Xs.gb[k][s];
+      for (int s = 0; s < Xw->n[k]; ++s) {
+        const int b = Xw->gb[k][s];
         ext = true;
         const int e1 = __ldg(M.xptr + b + 1);
         for (int e = __ldg(M.xptr + b); e < e1; ++e) {
@@ -1066,7 +1070,7 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
   }
   const Ext<T, VT>* X = nullptr;
   if constexpr (GEN)
-    if (ext) X = &Xs;
+    if (ext) X = Xw;
   // islands in this tile: the SpMV then masks rows per lane
   bool islands = false;
 #pragma unroll 1
