@@ -14,7 +14,11 @@ constexpr int KL = 4;   // strictly lower part of the factor
 constexpr int KU = 4;   // strictly upper part (L^T)
 constexpr int KG = 6;   // bus adjacency of the mismatch
 // Tail of the forward level schedule solved with the dense inverse of its
-// factor block: the last levels, together at most TAIL_ROWS rows.
+// factor block: the last levels, together at most TAIL_ROWS rows.  Its
+// right-hand side sits in shared memory (TAIL_ROWS x T values); 248 rows keep
+// the persistent kernel's CTA (T = 2, FP32) at or under 9 KB of shared
+// memory, so five resident CTAs fit the 50 KB carveout that leaves the L1
+// cache its size.
 #ifndef GPCG_TAIL_ROWS
 #define GPCG_TAIL_ROWS 248
 #endif
