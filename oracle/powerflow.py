@@ -182,6 +182,13 @@ def branch_flows(f, t, r, x, in_service, theta, V, tap=None):
     return np.where(on, Pf, 0.0), np.where(on, Pt, 0.0)
 
 
+def limit_violations(cand, dQ, Q_min, Q_max):
+    """PV buses ``cand`` whose generator output Q(V) - Q_sched = -dQ is above
+    Q_max (first array) or below Q_min (second)."""
+    qg = -dQ[cand]
+    return cand[qg > Q_max[cand]], cand[qg < Q_min[cand]]
+
+
 def fdpf(grid, in_service, active, P_sched, theta0, V0, tol, max_outer, growth_rule=True,
          switched=None):
     """Fast-decoupled power flow on the buses marked ``active``.
@@ -219,13 +226,11 @@ def fdpf(grid, in_service, active, P_sched, theta0, V0, tol, max_outer, growth_r
         best = min(best, err)
         if err <= tol:
             if qlim:
-                cand = np.flatnonzero(active & (bt == PV))
-                qg = -dQ[cand]  # generator output beyond the scheduled injection
-                hi, lo = qg > Q_max[cand], qg < Q_min[cand]
-                if hi.any() or lo.any():
-                    Q_sched[cand[hi]] += Q_max[cand[hi]]
-                    Q_sched[cand[lo]] += Q_min[cand[lo]]
-                    sw = cand[hi | lo]
+                hi, lo = limit_violations(np.flatnonzero(active & (bt == PV)), dQ, Q_min, Q_max)
+                if hi.size or lo.size:
+                    Q_sched[hi] += Q_max[hi]
+                    Q_sched[lo] += Q_min[lo]
+                    sw = np.sort(np.concatenate([hi, lo]))
                     bt[sw] = PQ
                     if switched is not None:
                         switched.extend(int(b) for b in sw)

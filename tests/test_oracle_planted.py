@@ -77,3 +77,14 @@ def test_generation_not_removed_is_caught(monkeypatch):
     monkeypatch.setattr(screen, "redispatch_generator", keeps_generation)
     with pytest.raises(AssertionError):
         pins.test_two_bus_generator_trip_closed_form()
+
+
+def test_limit_sign_flipped_is_caught(monkeypatch):
+    def flipped(cand, dQ, Q_min, Q_max):
+        qg = dQ[cand]                      # Q_sched - Q(V) taken for the output
+        return cand[qg > Q_max[cand]], cand[qg < Q_min[cand]]
+
+    monkeypatch.setattr(pf, "limit_violations", flipped)
+    with pytest.raises(AssertionError):
+        pins.test_two_bus_q_limit_closed_form()
+
