@@ -5,9 +5,12 @@
  * of every single-branch outage scenario (Sec. IV.A) with conjugate gradient
  * preconditioned by a factorisation of the base-case matrix (Sec. IV.B,
  * eqs. (6)-(7)), after islanding detection and proportional re-dispatch
- * (Sec. IV.C).  All numerical work runs in CUDA kernels on the current
- * device; the host code only validates arguments, analyses the sparsity
- * structure once per grid, and enqueues work.
+ * (Sec. IV.C).  Beyond branch outages: generator outages
+ * (gpcg_n1_gen_screen), transformer turns ratios and PV reactive limits
+ * (gpcg_grid), the P-theta quick screen (gpcg_n1_dc_screen) and the adjoint
+ * of an overload penalty (gpcg_n1_adjoint).  All numerical work runs in CUDA
+ * kernels on the current device; the host code only validates arguments,
+ * analyses the sparsity structure once per grid, and enqueues work.
  *
  * Conventions
  *  - Buses and branches are 0-based.  Per-unit quantities.
@@ -46,14 +49,15 @@ typedef enum {
   GPCG_OK = 0,
   GPCG_ERR_INVALID_ARG = 1,     /* bad size, index, pointer or option */
   GPCG_ERR_CUDA = 2,            /* a CUDA runtime call failed */
-  GPCG_ERR_BASE_NOT_CONVERGED = 3,
+  GPCG_ERR_BASE_NOT_CONVERGED = 3, /* also: the base case needs PV generators
+                                     outside their reactive limits */
   GPCG_ERR_BASE_ISLANDED = 4,   /* the intact grid is not connected */
   GPCG_ERR_TIMEOUT = 5,         /* reserved: no kernel of this library waits on another */
   GPCG_ERR_OOM = 6,             /* a device allocation failed */
   GPCG_ERR_NOT_READY = 7        /* gpcg_base_solve has not succeeded yet */
 } gpcg_status;
 
-/* Per-scenario outcome written to status[] by gpcg_n1_screen. */
+/* Per-scenario outcome written to status[] by the screens. */
 enum {
   GPCG_SCEN_OK = 0,             /* converged to the mismatch tolerance */
   GPCG_SCEN_MAXITER = 1,        /* outer iteration cap reached */
