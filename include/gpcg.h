@@ -71,6 +71,10 @@ enum {
 };
 
 enum { GPCG_PQ = 0, GPCG_PV = 1, GPCG_SLACK = 2 };        /* bus_type */
+
+/* 32-bit words of one scenario's row of the branch overload mask. */
+#define GPCG_MASK_WORDS(n_branch) (((n_branch) + 31) / 32)
+
 enum { GPCG_MEM_HOST = 0, GPCG_MEM_DEVICE = 1 };
 
 /* Precision of the inner PCG (the mismatch, state update and flows are
@@ -210,6 +214,13 @@ GPCG_API gpcg_status gpcg_base_solve(gpcg_ctx *ctx, double *theta, double *vm,
  *   status[n_out]                             GPCG_SCEN_*
  *   max_loading[n_out]                        max over branches of
  *                                             max(|P_ij|,|P_ji|)/rating
+ *   n_overload[n_out]                         branches whose loading
+ *                                             max(|P_ij|,|P_ji|)/rating
+ *                                             exceeds 1 (the violations
+ *                                             the screen flags, Sec. I)
+ *   overload[n_out][GPCG_MASK_WORDS(n_branch)] the same branches as a bit
+ *                                             mask: bit k % 32 of word
+ *                                             k / 32 is set for branch k
  * n_out may be 0.  An outage index outside [0, n_branch) is INVALID_ARG.
  * Requires a successful gpcg_base_solve (else NOT_READY).  A scenario that
  * fails to converge never fails the call: see status[].
@@ -227,7 +238,8 @@ GPCG_API gpcg_status gpcg_base_solve(gpcg_ctx *ctx, double *theta, double *vm,
 GPCG_API gpcg_status gpcg_n1_screen(gpcg_ctx *ctx, const int32_t *outages, int32_t n_out,
                            int32_t mem, void *stream, double *theta, double *vm,
                            double *flow, int32_t *island_label, int32_t *iters,
-                           int32_t *status, double *max_loading);
+                           int32_t *status, double *max_loading, int32_t *n_overload,
+                           uint32_t *overload);
 
 /* N-1 screen of generator outages (Sec. IV.A: the loss of a single
  * component).  Scenario s trips the generator of PV bus gen_buses[s]
@@ -246,7 +258,8 @@ GPCG_API gpcg_status gpcg_n1_screen(gpcg_ctx *ctx, const int32_t *outages, int32
 GPCG_API gpcg_status gpcg_n1_gen_screen(gpcg_ctx *ctx, const int32_t *gen_buses, int32_t n_out,
                                int32_t mem, void *stream, double *theta, double *vm,
                                double *flow, int32_t *island_label, int32_t *iters,
-                               int32_t *status, double *max_loading);
+                               int32_t *status, double *max_loading, int32_t *n_overload,
+                               uint32_t *overload);
 
 /* Loss and gradients of a smooth overload penalty summed over the N-1
  * scenarios of the P-theta (DC) model (eq. (4) with |V| = 1, Sec. IV.A's
@@ -282,12 +295,15 @@ GPCG_API gpcg_status gpcg_n1_adjoint(gpcg_ctx *ctx, const int32_t *outages, int3
  * 1/x) with the outage's four-element change.  Then
  *   flow[s][k] = (theta_i - theta_j) / x_k on branches k = (i, j) in service
  *                between main-island buses, else 0,
- *   max_loading[s] = max_k |flow[s][k]| / rating_k.
+ *   max_loading[s] = max_k |flow[s][k]| / rating_k,
+ *   n_overload[s]  = the number of branches with |flow[s][k]| / rating_k > 1,
+ *   overload[s]    = those branches as a bit mask (as in gpcg_n1_screen).
  * Inputs: P[n_bus] bus injections (NULL: the grid's P_sched), host or device
  * memory as mem says.  Outputs, each optional: theta[n_out][n_bus],
  * flow[n_out][n_branch], iters[n_out] (PCG iterations), status[n_out]
  * (GPCG_SCEN_OK, or GPCG_SCEN_ISLAND_NO_GEN when an island's injection has
- * no main-island generator to go to and the slack takes it), max_loading.
+ * no main-island generator to go to and the slack takes it), max_loading,
+ * n_overload[n_out], overload[n_out][GPCG_MASK_WORDS(n_branch)].
  * The solve runs in the context's precision: GPCG_BATCHED_FP64 to a 1e-12
  * relative residual; GPCG_BATCHED_FP32 and _FP32_F16 with FP32 vectors and
  * factors to 1e-6, then one step of iterative refinement (FP64 residual,
@@ -298,7 +314,8 @@ GPCG_API gpcg_status gpcg_n1_adjoint(gpcg_ctx *ctx, const int32_t *outages, int3
 GPCG_API gpcg_status gpcg_n1_dc_screen(gpcg_ctx *ctx, const int32_t *outages, int32_t n_out,
                                        int32_t mem, void *stream, const double *P,
                                        double *theta, double *flow, int32_t *iters,
-                                       int32_t *status, double *max_loading);
+                                       int32_t *status, double *max_loading,
+                                       int32_t *n_overload, uint32_t *overload);
 
 /* Batched operators of the hot path, for verification: each applies, for
  * S scenarios at once, one step of the inner solve to S vectors stored
@@ -346,20 +363,27 @@ GPCG_API gpcg_status gpcg_last_timings(gpcg_ctx *ctx, float *ms /*[2]*/);
  *
  * It allocates nothing: all scratch (island data, the solve's per-tile
  * vectors and state, the scenario queue) comes from one static device array
- * of GPCG_NOALLOC_SCRATCH_BYTES that every GPU which loads the library holds
- * until the process exits.  The first call on a device looks the array up
- * for that device (cudaGetSymbolAddress); make that first call before any
- * stream capture.  The caller provides the context (built earlier by
- * gpcg_create and gpcg_base_solve, which do allocate) and every input and
- * output, all in device memory; outputs as in gpcg_n1_screen.  The outage
- * list is checked through a fixed host buffer, which synchronises `stream`;
- * the rest is enqueued on `stream`.
+ * of GPCG_NOALLOC_SCRATCH_BYTES that every CUDA context which loads the
+ * library holds until it is destroyed or the process exits.  Each call looks
+ * up that array's address in the current context (cudaGetSymbolAddress).
+ * The caller provides the context (built earlier by gpcg_create and
+ * gpcg_base_solve, which do allocate) and every input and output, all in
+ * device memory; outputs as in gpcg_n1_screen.  The outage list is checked
+ * through a fixed host buffer, which synchronises `stream`: the call cannot
+ * be made while `stream` is being captured into a CUDA graph.  The rest is
+ * enqueued on `stream`.
  *
- * Every call shares the one array, which keeps the previous call's contents
- * (the call resets what must start at zero): calls that overlap on the GPU
- * -- from two streams, threads or contexts of the same device -- race and
- * give wrong results.  The solve runs as many scenario tiles at once as fit
- * in the array, so large grids run with fewer tiles than gpcg_n1_screen.
+ * Scheduling differs from gpcg_n1_screen, results do not: scenarios are
+ * taken in the order given (gpcg_n1_screen starts the outages of heavily
+ * loaded branches first), and the tile width is the context's option, else
+ * the one gpcg_n1_screen's autotuner chose, else 2.
+ *
+ * Every call shares the one array of its context, which keeps the previous
+ * call's contents (the call resets what must start at zero): calls that
+ * overlap on the GPU -- from two streams or threads in the same context --
+ * race and give wrong results.  The solve runs as many scenario tiles at
+ * once as fit in the array, so large grids run with fewer tiles than
+ * gpcg_n1_screen.
  * Errors: INVALID_ARG when the scenarios and one tile of the grid do not
  * fit in the array (the message gives the bytes needed), when an outage is
  * not a branch index, or when the context's precision is
@@ -369,7 +393,8 @@ GPCG_API gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx *ctx, const int32_t *outage
                                             int32_t n_out, void *stream, double *theta,
                                             double *vm, double *flow, int32_t *island_label,
                                             int32_t *iters, int32_t *status,
-                                            double *max_loading);
+                                            double *max_loading, int32_t *n_overload,
+                                            uint32_t *overload);
 
 /* Sizes of a structural plan (gpcg_analyze). */
 typedef struct {

@@ -84,14 +84,15 @@ def load(build_if_missing: bool = True):
     lib.gpcg_set_options.argtypes = [vp, C.POINTER(Options)]
     lib.gpcg_get_info.argtypes = [vp, C.POINTER(Info)]
     lib.gpcg_base_solve.argtypes = [vp, f64p, f64p, f64p, vp]
-    lib.gpcg_n1_screen.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.gpcg_n1_screen.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.gpcg_n1_gen_screen.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gpcg_apply.argtypes = [vp, i32, i32, vp, i32, i32, vp, vp]
     lib.gpcg_export_matrix.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gpcg_last_timings.argtypes = [vp, vp]
     lib.gpcg_n1_adjoint.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
-    lib.gpcg_n1_dc_screen.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp]
+    lib.gpcg_n1_dc_screen.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gpcg_analyze.argtypes = [C.POINTER(_Grid), i32, i32, vp, vp, vp, vp, vp, vp, vp]
-    lib.gpcg_n1_screen_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.gpcg_n1_screen_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gpcg_last_error.argtypes = []
     lib.gpcg_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -104,6 +105,18 @@ def load(build_if_missing: bool = True):
 def _check(lib, st):
     if st != GPCG_OK:
         raise GPCGError(st, lib.gpcg_last_error().decode())
+
+
+def mask_words(n_branch: int) -> int:
+    """32-bit words per scenario of the overload bit mask (GPCG_MASK_WORDS)."""
+    return (int(n_branch) + 31) // 32
+
+
+def unpack_mask(words, n_branch: int):
+    """Bool array [..., n_branch] from overload mask words [..., mask_words]."""
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    bits = np.unpackbits(w.view(np.uint8), axis=-1, bitorder="little")
+    return bits[..., :n_branch].astype(bool)
 
 
 def _ptr(a):
@@ -240,14 +253,15 @@ class GPCG:
         spec = dict(theta=((S, n), np.float64), V=((S, n), np.float64),
                     flow=((S, m), np.float64), label=((S, n), np.int32),
                     iters=((S, 3), np.int32), status=((S,), np.int32),
-                    max_loading=((S,), np.float64))
+                    max_loading=((S,), np.float64), n_overload=((S,), np.int32),
+                    overload=((S, mask_words(m)), np.uint32))
         for k in outputs:
             shp, dt = spec[k]
             res[k] = np.empty(shp, dt)
         g = lambda k: _ptr(res.get(k))
         _check(self._lib, getattr(self._lib, _fn)(
             self._h, _ptr(out), S, 0, None, g("theta"), g("V"), g("flow"), g("label"),
-            g("iters"), g("status"), g("max_loading")))
+            g("iters"), g("status"), g("max_loading"), g("n_overload"), g("overload")))
         return res
 
     def n1_screen_device(self, outages, out: dict, stream=None, _fn="gpcg_n1_screen"):
@@ -260,7 +274,7 @@ class GPCG:
         _check(self._lib, getattr(self._lib, _fn)(
             self._h, _ptr(outages), int(outages.shape[0]), 1, C.c_void_p(s.cuda_stream),
             g("theta"), g("V"), g("flow"), g("label"), g("iters"), g("status"),
-            g("max_loading")))
+            g("max_loading"), g("n_overload"), g("overload")))
 
     def last_timings(self):
         """(islanding kernel ms, N-1 solve kernel ms) of the last screen."""
@@ -277,7 +291,7 @@ class GPCG:
         _check(self._lib, self._lib.gpcg_n1_screen_noalloc(
             self._h, _ptr(outages), int(outages.shape[0]), C.c_void_p(s.cuda_stream),
             g("theta"), g("V"), g("flow"), g("label"), g("iters"), g("status"),
-            g("max_loading")))
+            g("max_loading"), g("n_overload"), g("overload")))
 
     def n1_dc_screen(self, outages, P=None,
                      outputs=("theta", "flow", "iters", "status", "max_loading")):
@@ -288,12 +302,13 @@ class GPCG:
         Pa = None if P is None else np.ascontiguousarray(P, dtype=np.float64)
         spec = dict(theta=((S, n), np.float64), flow=((S, m), np.float64),
                     iters=((S,), np.int32), status=((S,), np.int32),
-                    max_loading=((S,), np.float64))
+                    max_loading=((S,), np.float64), n_overload=((S,), np.int32),
+                    overload=((S, mask_words(m)), np.uint32))
         res = {k: np.empty(*spec[k]) for k in outputs}
         g = lambda k: _ptr(res.get(k))
         _check(self._lib, self._lib.gpcg_n1_dc_screen(
             self._h, _ptr(out), S, 0, None, _ptr(Pa), g("theta"), g("flow"), g("iters"),
-            g("status"), g("max_loading")))
+            g("status"), g("max_loading"), g("n_overload"), g("overload")))
         return res
 
     def n1_dc_screen_device(self, outages, out: dict, P=None, stream=None):
@@ -303,7 +318,8 @@ class GPCG:
         g = lambda k: _ptr(out.get(k))
         _check(self._lib, self._lib.gpcg_n1_dc_screen(
             self._h, _ptr(outages), int(outages.shape[0]), 1, C.c_void_p(s.cuda_stream),
-            _ptr(P), g("theta"), g("flow"), g("iters"), g("status"), g("max_loading")))
+            _ptr(P), g("theta"), g("flow"), g("iters"), g("status"), g("max_loading"),
+            g("n_overload"), g("overload")))
 
     def n1_adjoint(self, outages, P=None, b=None, grads=True):
         """Host arrays: (loss, dL/dP, dL/db) of the N-1 overload penalty."""

@@ -1045,7 +1045,8 @@ struct OutBuf {
 static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n_out,
                                   int32_t mem, void* stream, double* theta, double* vm,
                                   double* flow, int32_t* island_label, int32_t* iters,
-                                  int32_t* status, double* max_loading, bool gen) {
+                                  int32_t* status, double* max_loading, int32_t* n_overload,
+                                  uint32_t* overload, bool gen) {
   if (!c) return fail(GPCG_ERR_INVALID_ARG, "gpcg_n1_screen: ctx is NULL");
   if (n_out < 0) return fail(GPCG_ERR_INVALID_ARG, "n_out < 0");
   if (mem != GPCG_MEM_HOST && mem != GPCG_MEM_DEVICE)
@@ -1100,7 +1101,9 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
     return ce;
   };
   double *d_theta, *d_vm, *d_flow, *d_ml;
-  int32_t *d_lab, *d_iters, *d_stat;
+  int32_t *d_lab, *d_iters, *d_stat, *d_nov;
+  uint32_t* d_ovm;
+  const size_t nw = (size_t)GPCG_MASK_WORDS(c->m);
   cudaError_t ce = cudaSuccess;
   if (ce == cudaSuccess) ce = stage(theta, S * c->n, &d_theta);
   if (ce == cudaSuccess) ce = stage(vm, S * c->n, &d_vm);
@@ -1109,6 +1112,8 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
   if (ce == cudaSuccess) ce = stage(iters, S * 3, &d_iters);
   if (ce == cudaSuccess) ce = stage(status, S, &d_stat);
   if (ce == cudaSuccess) ce = stage(max_loading, S, &d_ml);
+  if (ce == cudaSuccess) ce = stage(n_overload, S, &d_nov);
+  if (ce == cudaSuccess) ce = stage(overload, S * nw, &d_ovm);
   auto cleanup = [&]() { for (void* p : staging) cudaFreeAsync(p, st); };
   if (ce != cudaSuccess) {
     cleanup();
@@ -1125,6 +1130,7 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
   P.out_theta = d_theta; P.out_vm = d_vm; P.out_flow = d_flow; P.out_maxload = d_ml;
   P.out_bus_map = c->G.user_of_bus;
   P.out_iters = d_iters; P.out_status = d_stat;
+  P.out_nover = d_nov; P.out_ovmask = d_ovm;
   const bool plain = c->opt.precision == GPCG_PLAIN_FP64;
   // generator outages and reactive limits take the kernel with extension rows
   const bool ext = gen || c->G.qmax != nullptr;
@@ -1203,6 +1209,8 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
       Q.out_maxload = d_ml ? d_ml + s : nullptr;
       Q.out_iters = d_iters ? d_iters + 3 * s : nullptr;
       Q.out_status = d_stat ? d_stat + s : nullptr;
+      Q.out_nover = d_nov ? d_nov + s : nullptr;
+      Q.out_ovmask = d_ovm ? d_ovm + s * nw : nullptr;
       rs = run_fdpf<double>(c, st, Q, 2, 1);
     }
   } else if (mem == GPCG_MEM_DEVICE && !c->phase_on) {
@@ -1215,7 +1223,8 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
                                   (uintptr_t)c->opt.precision, (uintptr_t)c->opt.precond,
                                   (uintptr_t)c->work, (uintptr_t)d_theta, (uintptr_t)d_vm,
                                   (uintptr_t)d_flow, (uintptr_t)d_lab, (uintptr_t)d_iters,
-                                  (uintptr_t)d_stat, (uintptr_t)d_ml, (uintptr_t)c->d_outages,
+                                  (uintptr_t)d_stat, (uintptr_t)d_ml, (uintptr_t)d_nov,
+                                  (uintptr_t)d_ovm, (uintptr_t)c->d_outages,
                                   (uintptr_t)c->d_order, (uintptr_t)c->d_lo, (uintptr_t)gen};
     {
       double opts[3] = {c->opt.tol, c->opt.inner_rtol, 0.0};
@@ -1279,6 +1288,8 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
     if (ce == cudaSuccess) ce = back(iters, d_iters, S * 3);
     if (ce == cudaSuccess) ce = back(status, d_stat, S);
     if (ce == cudaSuccess) ce = back(max_loading, d_ml, S);
+    if (ce == cudaSuccess) ce = back(n_overload, d_nov, S);
+    if (ce == cudaSuccess) ce = back(overload, d_ovm, S * nw);
     cleanup();
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) return fail(GPCG_ERR_CUDA, "n1_screen: %s", cudaGetErrorString(ce));
@@ -1290,17 +1301,19 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
 extern "C" gpcg_status gpcg_n1_screen(gpcg_ctx* c, const int32_t* outages, int32_t n_out,
                                       int32_t mem, void* stream, double* theta, double* vm,
                                       double* flow, int32_t* island_label, int32_t* iters,
-                                      int32_t* status, double* max_loading) {
+                                      int32_t* status, double* max_loading, int32_t* n_overload,
+                                      uint32_t* overload) {
   return n1_screen_impl(c, outages, n_out, mem, stream, theta, vm, flow, island_label, iters,
-                        status, max_loading, false);
+                        status, max_loading, n_overload, overload, false);
 }
 
 extern "C" gpcg_status gpcg_n1_gen_screen(gpcg_ctx* c, const int32_t* gen_buses, int32_t n_out,
                                           int32_t mem, void* stream, double* theta, double* vm,
                                           double* flow, int32_t* island_label, int32_t* iters,
-                                          int32_t* status, double* max_loading) {
+                                          int32_t* status, double* max_loading,
+                                          int32_t* n_overload, uint32_t* overload) {
   return n1_screen_impl(c, gen_buses, n_out, mem, stream, theta, vm, flow, island_label, iters,
-                        status, max_loading, true);
+                        status, max_loading, n_overload, overload, true);
 }
 
 // ------------------------------------------------------------------ adjoint
@@ -1478,7 +1491,8 @@ extern "C" gpcg_status gpcg_n1_adjoint(gpcg_ctx* c, const int32_t* outages, int3
 extern "C" gpcg_status gpcg_n1_dc_screen(gpcg_ctx* c, const int32_t* outages, int32_t n_out,
                                          int32_t mem, void* stream, const double* P_in,
                                          double* theta, double* flow, int32_t* iters,
-                                         int32_t* status, double* max_loading) {
+                                         int32_t* status, double* max_loading,
+                                         int32_t* n_overload, uint32_t* overload) {
   if (!c) return fail(GPCG_ERR_INVALID_ARG, "gpcg_n1_dc_screen: ctx is NULL");
   if (n_out < 0) return fail(GPCG_ERR_INVALID_ARG, "n_out < 0");
   if (mem != GPCG_MEM_HOST && mem != GPCG_MEM_DEVICE)
@@ -1525,7 +1539,11 @@ extern "C" gpcg_status gpcg_n1_dc_screen(gpcg_ctx* c, const int32_t* outages, in
     return alloc((void**)dev, count * sizeof(**dev));
   };
   double *d_th = nullptr, *d_fl = nullptr, *d_ml = nullptr;
-  int32_t *d_it = nullptr, *d_st = nullptr;
+  int32_t *d_it = nullptr, *d_st = nullptr, *d_nov = nullptr;
+  uint32_t* d_ovm = nullptr;
+  const size_t nw = (size_t)GPCG_MASK_WORDS(m);
+  if (ce == cudaSuccess) ce = stage(n_overload, S, &d_nov);
+  if (ce == cudaSuccess) ce = stage(overload, S * nw, &d_ovm);
   if (ce == cudaSuccess) ce = stage(theta, S * n, &d_th);
   if (ce == cudaSuccess) ce = stage(flow, S * m, &d_fl);
   if (ce == cudaSuccess) ce = stage(max_loading, S, &d_ml);
@@ -1566,7 +1584,7 @@ extern "C" gpcg_status gpcg_n1_dc_screen(gpcg_ctx* c, const int32_t* outages, in
   P.wth = sbase; P.wV = sbase + slots * ss; P.wc = sbase + 2 * slots * ss;
   P.ws = sbase + 3 * slots * ss;
   P.sstride = ss;
-  DcParamsView D{dPi, c->G.user_of_bus, d_th, d_fl, d_ml, d_it, d_st};
+  DcParamsView D{dPi, c->G.user_of_bus, d_th, d_fl, d_ml, d_it, d_st, d_nov, d_ovm};
   ce = f32 ? launch_dc<float>(st, slots, P, D, c->MP.view<float>(f16), c->MP.view<double>())
            : launch_dc<double>(st, slots, P, D, c->MP.view<double>(), c->MP.view<double>());
   if (ce != cudaSuccess) { cleanup(); return fail(GPCG_ERR_CUDA, "dc screen: %s", cudaGetErrorString(ce)); }
@@ -1580,6 +1598,8 @@ extern "C" gpcg_status gpcg_n1_dc_screen(gpcg_ctx* c, const int32_t* outages, in
     if (ce == cudaSuccess) ce = back(max_loading, d_ml, S);
     if (ce == cudaSuccess) ce = back(iters, d_it, S);
     if (ce == cudaSuccess) ce = back(status, d_st, S);
+    if (ce == cudaSuccess) ce = back(n_overload, d_nov, S);
+    if (ce == cudaSuccess) ce = back(overload, d_ovm, S * nw);
   }
   cleanup();  // stream-ordered frees: after the kernel and the copies
   if (mem == GPCG_MEM_HOST && ce == cudaSuccess) ce = cudaStreamSynchronize(st);

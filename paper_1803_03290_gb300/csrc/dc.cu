@@ -119,8 +119,18 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
       }
     }
     __syncthreads();
-    // flows on the branches in service between main-island buses; loading
+    // flows on the branches in service between main-island buses; loading,
+    // and the branches loaded above their rating (count and bit mask)
     Vec<unsigned long long, 2> ml = vzero<unsigned long long, 2>();
+    Vec<int, 2> nov = vzero<int, 2>();
+    const int nw = (G.m + 31) >> 5;
+    if (D.ovmask) {
+      for (int w = g.rs; w < nw; w += Geo<T>::RPS) {
+        if (v0) D.ovmask[(size_t)L.scen[l0] * nw + w] = 0u;
+        if (v1) D.ovmask[(size_t)L.scen[l1] * nw + w] = 0u;
+      }
+      __syncthreads();  // the rows are cleared before any bit is set
+    }
     for (int k = g.rs; k < G.m; k += Geo<T>::RPS) {
       const int a = G.f[k], b = G.t[k];
       const int pa = G.pre[a], pb = G.pre[b];
@@ -129,11 +139,21 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
       double f0 = 0.0, f1 = 0.0;
       if (v0 && k != br0 && !in_island(pa, lo0, cnt0) && !in_island(pb, lo0, cnt0)) {
         f0 = bk * (ta.a - tb.a);
-        upd_max_bits(ml.v[0], f0 * ir);
+        const double ld = f0 * ir;
+        upd_max_bits(ml.v[0], ld);
+        if (overloaded(ld)) {
+          nov.v[0] += 1;
+          if (D.ovmask) atomicOr(D.ovmask + (size_t)L.scen[l0] * nw + (k >> 5), 1u << (k & 31));
+        }
       }
       if (v1 && k != br1 && !in_island(pa, lo1, cnt1) && !in_island(pb, lo1, cnt1)) {
         f1 = bk * (ta.b - tb.b);
-        upd_max_bits(ml.v[1], f1 * ir);
+        const double ld = f1 * ir;
+        upd_max_bits(ml.v[1], ld);
+        if (overloaded(ld)) {
+          nov.v[1] += 1;
+          if (D.ovmask) atomicOr(D.ovmask + (size_t)L.scen[l1] * nw + (k >> 5), 1u << (k & 31));
+        }
       }
       if (D.flow) {
         if (v0) D.flow[(size_t)L.scen[l0] * G.m + k] = f0;
@@ -141,12 +161,14 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
       }
     }
     const Vec<unsigned long long, 2> mlb = lane_max_bits<T, RS_LOAD>(L, ml);
+    if (D.nover) nov = lane_sum<T, RS_BB>(L, nov);
     if (g.rs == 0) {
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int ln = g.lane + j, s = L.scen[ln];
         if (s < 0) continue;
         if (D.maxload) D.maxload[s] = from_bits(mlb.v[j]);
+        if (D.nover) D.nover[s] = nov.v[j];
         if (D.iters) D.iters[s] = L.inP[ln];
         if (D.status) D.status[s] = (L.cnt[ln] > 0 && L.nogen[ln]) ? 3 : 0;
       }

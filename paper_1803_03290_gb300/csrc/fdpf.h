@@ -33,6 +33,10 @@ struct FdpfParams {
   double *out_theta = nullptr, *out_vm = nullptr, *out_flow = nullptr, *out_maxload = nullptr;
   const int32_t* out_bus_map = nullptr;  // internal bus -> output column (null: identity)
   int32_t *out_iters = nullptr, *out_status = nullptr;
+  // overload screen: per scenario the number of branches loaded above their
+  // rating, and those branches as a bit mask of mask_words words
+  int32_t* out_nover = nullptr;
+  uint32_t* out_ovmask = nullptr;
   unsigned long long* phase_cycles = nullptr;  // [8] per-phase SM cycles, or null
   const int32_t* mis_order = nullptr;   // non-slack buses sorted by degree
   const int32_t* misq_order = nullptr;  // B'' rows sorted by their bus's degree
@@ -78,6 +82,8 @@ struct DcParamsView {
   double* maxload;              // [S], or null
   int32_t* iters;               // [S] PCG iterations, or null
   int32_t* status;              // [S], or null
+  int32_t* nover;               // [S] branches loaded above their rating, or null
+  uint32_t* ovmask;             // [S][(m + 31) / 32] those branches as bits, or null
 };
 template <typename VT>
 cudaError_t launch_dc(cudaStream_t st, int grid, const FdpfParams& P, const DcParamsView& D,

@@ -478,6 +478,15 @@ __device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& 
     }
   }
   Vec<unsigned long long, LP> ml = vzero<unsigned long long, LP>();  // abs_bits patterns
+  Vec<int, LP> nov = vzero<int, LP>();  // branches loaded above their rating
+  const int nw = (G.m + 31) >> 5;       // words of a scenario's overload mask
+  if (P.out_ovmask && dn) {
+    for (int w = g.rs; w < nw; w += Geo<T>::RPS)
+#pragma unroll
+      for (int j = 0; j < LP; ++j)
+        if ((dn >> j) & 1) P.out_ovmask[(size_t)L.scen[g.lane + j] * nw + w] = 0u;
+    __syncthreads();  // the rows are cleared before any bit is set
+  }
   if (dn) {
     for (int k = g.rs; k < G.m; k += Geo<T>::RPS) {
       const int a = __ldg(G.f + k), b = __ldg(G.t + k);
@@ -508,7 +517,13 @@ __device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& 
             // loading max(|P_ab|, |P_ba|) / rating: the larger end picked on
             // the bit patterns, one multiplication
             const unsigned long long u = abs_bits(Pab), v = abs_bits(Pba);
-            upd_max_bits(ml.v[j], __longlong_as_double((long long)(u > v ? u : v)) * ir);
+            const double ld = __longlong_as_double((long long)(u > v ? u : v)) * ir;
+            upd_max_bits(ml.v[j], ld);
+            if (overloaded(ld)) {
+              nov.v[j] += 1;
+              if (P.out_ovmask)
+                atomicOr(P.out_ovmask + (size_t)L.scen[ln] * nw + (k >> 5), 1u << (k & 31));
+            }
           }
           if (P.out_flow) P.out_flow[(size_t)L.scen[ln] * G.m + k] = Pab;
         }
@@ -516,6 +531,9 @@ __device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& 
     }
   }
   const Vec<unsigned long long, LP> mlb = lane_max_bits<T, RS_LOAD>(L, ml);
+  // (the counts take the buffer of the solve's first reduction, which is
+  // idle between solves)
+  if (P.out_nover) nov = lane_sum<T, RS_BB>(L, nov);
   if (g.rs == 0) {
 #pragma unroll
     for (int j = 0; j < LP; ++j) {
@@ -530,6 +548,7 @@ __device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& 
         P.out_iters[(size_t)s * 3 + 2] = L.inQ[ln];
       }
       if (P.out_maxload) P.out_maxload[s] = from_bits(mlb.v[j]);
+      if (P.out_nover) P.out_nover[s] = nov.v[j];
       L.done[ln] = 0;
       L.scen[ln] = -1;
     }

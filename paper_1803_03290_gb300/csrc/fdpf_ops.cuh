@@ -292,6 +292,12 @@ __device__ __forceinline__ void upd_max_bits(unsigned long long& m, double d) {
   const unsigned long long a = abs_bits(d);
   m = a > m ? a : m;
 }
+// A loading (non-negative) above 1, infinity included and NaN not, decided on
+// the bit pattern (the order of non-negative doubles is their integer order).
+__device__ __forceinline__ bool overloaded(double ld) {
+  const unsigned long long b = abs_bits(ld);
+  return b > 0x3ff0000000000000ull && b <= 0x7ff0000000000000ull;
+}
 __device__ __forceinline__ double from_bits(unsigned long long b) {
   const double v = __longlong_as_double((long long)b);
   return v == v ? v : INFINITY;

@@ -7,7 +7,6 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstdarg>
-#include <mutex>
 
 #include "../../include/gpcg.h"
 #include "common.cuh"
@@ -27,10 +26,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[GPCG_NOALLOC_SC
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
 gpcg_status err(gpcg_status st, const char* fmt, ...) {
   char buf[512];
   va_list ap;
@@ -41,22 +36,18 @@ gpcg_status err(gpcg_status st, const char* fmt, ...) {
   return st;
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (with that device current) and cached.
+// Device address of the scratch array in the calling thread's current CUDA
+// context.  Each context that loads the library's device code has its own
+// copy of the array at its own address (a second context on a device, or
+// the primary context after cudaDeviceReset, gets a new one), so the address
+// is looked up on every call rather than cached: the lookup is a table
+// search in the runtime, small beside the call's own synchronisation.
 gpcg_status scratch_address(unsigned char** out) {
-  int dev = 0;
-  cudaError_t ce = cudaGetDevice(&dev);
-  if (ce != cudaSuccess) return err(GPCG_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(ce));
-  if (dev < 0 || dev >= kMaxDevices) return err(GPCG_ERR_INVALID_ARG, "device %d out of range", dev);
-  std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    ce = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (ce != cudaSuccess || !p)
-      return err(GPCG_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(ce));
-    g_scratch_addr[dev] = p;
-  }
-  *out = (unsigned char*)g_scratch_addr[dev];
+  void* p = nullptr;
+  const cudaError_t ce = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (ce != cudaSuccess || !p)
+    return err(GPCG_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(ce));
+  *out = (unsigned char*)p;
   return GPCG_OK;
 }
 
@@ -68,7 +59,8 @@ extern "C" gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx* ctx, const int32_t* outa
                                               int32_t n_out, void* stream, double* theta,
                                               double* vm, double* flow, int32_t* island_label,
                                               int32_t* iters, int32_t* status,
-                                              double* max_loading) {
+                                              double* max_loading, int32_t* n_overload,
+                                              uint32_t* overload) {
   CtxView c;
   if (!ctx_view(ctx, &c)) return err(GPCG_ERR_INVALID_ARG, "gpcg_n1_screen_noalloc: ctx is NULL");
   if (n_out < 0) return err(GPCG_ERR_INVALID_ARG, "n_out < 0");
@@ -84,7 +76,7 @@ extern "C" gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx* ctx, const int32_t* outa
   gpcg_status s = scratch_address(&base);
   if (s != GPCG_OK) return s;
 
-  // layout: [counter, error flag] [per-scenario island data] [solve slots]
+  // layout: [queue counter] [per-scenario island data] [solve slots]
   const size_t S = (size_t)n_out;
   // reactive limits take the kernel with extension rows (tiles of 2, 4, 8)
   const bool ext = c.G.qmax != nullptr;
@@ -154,6 +146,7 @@ extern "C" gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx* ctx, const int32_t* outa
   P.th0 = c.th0; P.V0 = c.V0; P.c0 = c.c0; P.s0 = c.s0;
   P.out_theta = theta; P.out_vm = vm; P.out_flow = flow; P.out_maxload = max_loading;
   P.out_iters = iters; P.out_status = status;
+  P.out_nover = n_overload; P.out_ovmask = overload;
   P.out_bus_map = c.G.user_of_bus;
   P.S = (int)S;
   P.n_tiles = n_tiles;

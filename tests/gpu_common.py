@@ -77,3 +77,79 @@ def sample_outages(g, k, seed=0, include_bridges=True):
                 if found >= max(2, k // 8):
                     break
     return np.array(sorted(picks), dtype=np.int32)
+
+
+# ---------------------------------------------------------------------------
+# Every outage of a screen against the oracle, scenario by scenario.
+def _every_outage_worker(args):
+    """One chunk of scenarios: the oracle's own FDPF (status, labels), and
+    the oracle's FP64 evaluation of the GPU's state (mismatch, overloads)."""
+    g, th0, V0, idx, outages, paths, tol, max_outer = args
+    th = np.load(paths["theta"], mmap_mode="r")
+    V = np.load(paths["V"], mmap_mode="r")
+    lab = np.load(paths["label"], mmap_mode="r")
+    st = np.load(paths["status"], mmap_mode="r")
+    from oracle import powerflow as opf
+    rows = []
+    for s in idx:
+        l = int(outages[s])
+        r = screen.solve_outage(g, th0, V0, l, tol, max_outer)
+        lab_ok = bool(np.array_equal(r["label"], lab[s]))
+        err = np.nan
+        nov, ties = -1, 0
+        if st[s] in (0, 3):
+            ths, Vs = np.asarray(th[s]), np.asarray(V[s])
+            err = screen.scenario_mismatch(g, l, ths, Vs)
+            on, _, isl, _, _ = screen.outage_setup(g, l)
+            live = on & ~isl[g.f] & ~isl[g.t]
+            Pf, Pt = opf.branch_flows(g.f, g.t, g.r, g.x, live, np.where(isl, 0.0, ths),
+                                      np.where(isl, 0.0, Vs), g.tap)
+            ld = np.maximum(np.abs(Pf), np.abs(Pt)) / g.rating
+            nov = int((ld > 1.0).sum())
+            ties = int((np.abs(ld - 1.0) <= 1e-12).sum())
+        rows.append((int(r["status"]), lab_ok, float(err), nov, ties))
+    return idx, rows
+
+
+def check_every_outage(g, th0, V0, outages, res, tol, tmpdir, max_outer=50, processes=None):
+    """Run the oracle on every scenario of a GPU screen `res` (host outputs
+    theta, V, label, status, n_overload of `outages`) in a pool of host
+    processes.  Returns per scenario: the oracle's status, whether the island
+    labels are identical, the oracle's FP64 mismatch of the GPU's state (NaN
+    where the GPU did not converge), and the oracle's overload count at the
+    GPU's state with the number of branches within 1e-12 of their rating."""
+    import multiprocessing as mp
+    import os
+    paths = {}
+    for k in ("theta", "V", "label", "status"):
+        paths[k] = os.path.join(str(tmpdir), f"{k}.npy")
+        np.save(paths[k], res[k])
+    S = len(outages)
+    if processes is None:
+        processes = len(os.sched_getaffinity(0))
+    chunks = [c for c in np.array_split(np.arange(S), max(1, processes * 8)) if c.size]
+    args = [(g, th0, V0, c, np.asarray(outages), paths, tol, max_outer) for c in chunks]
+    st = np.empty(S, np.int32)
+    lab_ok = np.empty(S, bool)
+    err = np.empty(S)
+    nov = np.empty(S, np.int32)
+    ties = np.empty(S, np.int32)
+    with mp.get_context("spawn").Pool(processes) as pool:
+        for idx, rows in pool.imap_unordered(_every_outage_worker, args):
+            for s, row in zip(idx, rows):
+                st[s], lab_ok[s], err[s], nov[s], ties[s] = row
+    return dict(status=st, label_ok=lab_ok, err=err, n_overload=nov, ties=ties)
+
+
+def with_tight_ratings(g, seed):
+    """The grid with every branch rated at U[1.0, 1.5] times its base-case
+    loading max(|P_ij|, |P_ji|) (plus 1e-3 p.u.), so that outages push flows
+    above the ratings of their neighbours.  Ratings do not enter the power
+    flow: only the overload screen sees them."""
+    th, V, _, st, _ = pf.base_case(g, tol=1e-11, max_outer=200)
+    assert st == pf.STATUS_OK
+    Pf, Pt = pf.branch_flows(g.f, g.t, g.r, g.x, np.ones(g.n_branch, bool), th, V, g.tap)
+    rng = np.random.default_rng(seed)
+    g = g.copy()
+    g.rating = np.maximum(np.abs(Pf), np.abs(Pt)) * rng.uniform(1.0, 1.5, g.n_branch) + 1e-3
+    return g

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import paper_1803_03290_gb300 as gp
-from gpu_common import grid, sample_outages
+from gpu_common import grid, sample_outages, with_tight_ratings
 from oracle import dc
 
 pytestmark = pytest.mark.gpu
@@ -30,6 +30,27 @@ def test_dc_grid120_all_outages(precision, th_tol, f_tol):
     _check(res, ref, th_tol, f_tol)
     assert (res["iters"] >= 1).all() and (res["iters"] <= 10).all()
     c.close()
+
+
+@pytest.mark.parametrize("precision", [gp.BATCHED_FP64, gp.BATCHED_FP32])
+def test_dc_grid120_overload_screen(precision):
+    """Branches above their rating per DC scenario (count and bit mask)
+    against the oracle's DC flows; branches within 1e-5 of their rating
+    (the FP32 solves' flow tolerance) are left out."""
+    g = with_tight_ratings(grid("grid120"), seed=13)
+    c = gp.GPCG(g, precision=precision)
+    outages = np.arange(g.n_branch, dtype=np.int32)
+    res = c.n1_dc_screen(outages, outputs=("status", "n_overload", "overload", "flow"))
+    c.close()
+    ref = dc.dc_screen(g, outages)
+    ld = np.abs(ref["flow"]) / g.rating
+    tie = np.abs(ld - 1.0) <= 1e-5
+    bits = gp.unpack_mask(res["overload"], g.n_branch)
+    np.testing.assert_array_equal(bits & ~tie, (ld > 1.0) & ~tie)
+    clear = ~tie.any(axis=1)
+    np.testing.assert_array_equal(res["n_overload"][clear], ref["n_overload"][clear])
+    np.testing.assert_array_equal(bits.sum(axis=1), res["n_overload"])
+    assert (ref["n_overload"] > 0).sum() >= 20
 
 
 def test_dc_grid2k_sample_with_injections():

@@ -819,8 +819,76 @@ def test_dc_islanding_balance():
         np.add.at(net, g.f, r["flow"][s])
         np.add.at(net, g.t, -r["flow"][s])
         main = ~isl & (g.bus_type != 2)
-        Pt = g.P_sched.copy()
-        gen = (g.bus_type == 1) & ~isl & (g.P_gen > 0)
-        Pt[gen] += g.P_sched[isl].sum() * g.P_gen[gen] / g.P_gen[gen].sum()
+        # the re-dispatch itself is pinned by the hand-derived ring below
+        Pt, _ = redispatch.redispatch(g.bus_type, g.P_sched, g.P_gen, isl)
         np.testing.assert_allclose(net[main], Pt[main], rtol=0, atol=1e-10)
     assert len(bridges) > 5
+
+
+# ------------------------------------------------------------ re-dispatch
+def ring_case():
+    """The hand-derived re-dispatch fixture (tests/golden/redispatch_ring.json)."""
+    import json
+    import os
+    from cases import GOLDEN
+    with open(os.path.join(GOLDEN, "redispatch_ring.json")) as fh:
+        d = json.load(fh)
+    gd = d["grid"]
+    g = grid_from_arrays(gd["bus_type"], gd["P_sched"], gd["Q_sched"], gd["P_gen"],
+                         gd["V_set"], gd["from"], gd["to"], gd["r"], gd["x"], gd["b_sh"],
+                         gd["rating"])
+    return g, d
+
+
+def test_redispatch_hand_derived_ring():
+    """Sec. IV.C's proportional re-dispatch against values worked out by hand
+    on a ring with a spur: an exporting island (its surplus shared 2:1 by the
+    two main generators; a PV bus with no scheduled generation takes no
+    share), an importing island (three generators share the deficit), a ring
+    outage that moves nothing, and a generator trip.  An equal-shares or
+    sign-flipped rule fails these; the balance invariant alone would not."""
+    g, d = ring_case()
+    n = g.n_bus
+    for case in d["branch_outages"]:
+        on, label, isl, P, no_gen = screen.outage_setup(g, case["outage"])
+        assert np.flatnonzero(isl).tolist() == case["islanded"]
+        np.testing.assert_allclose(P, case["P_after"], rtol=0, atol=1e-15)
+        assert no_gen == case["no_gen"]
+        P2, ng2 = redispatch.redispatch(g.bus_type, g.P_sched, g.P_gen, isl)
+        np.testing.assert_allclose(P2, case["P_after"], rtol=0, atol=1e-15)
+    for case in d["generator_outages"]:
+        g2, no_gen = screen.generator_setup(g, case["bus"])
+        np.testing.assert_allclose(g2.P_sched, case["P_after"], rtol=0, atol=1e-15)
+        assert no_gen == case["no_gen"]
+    c = d["no_generator_case"]
+    on = np.ones(len(c["from"]), bool)
+    on[c["outage"]] = False
+    lab = islands.components(len(c["bus_type"]), np.array(c["from"]), np.array(c["to"]), on)
+    isl = islands.island_mask(lab, 0)
+    assert np.flatnonzero(isl).tolist() == c["islanded"]
+    P, no_gen = redispatch.redispatch(np.array(c["bus_type"], np.int8),
+                                      np.array(c["P_sched"]), np.array(c["P_gen"]), isl)
+    np.testing.assert_allclose(P, c["P_after"], rtol=0, atol=1e-15)
+    assert no_gen is True
+    assert n == 7
+
+
+def test_redispatch_ring_power_flow_balance():
+    """The ring's N-1 solutions carry the hand-derived injections: at every
+    main-island bus but the slack, the FP64 mismatch against P_after vanishes
+    (so the FDPF used the re-dispatched schedule, not the original)."""
+    g, d = ring_case()
+    th0, V0, _, st, _ = pf.base_case(g, tol=1e-12, max_outer=200)
+    assert st == pf.STATUS_OK
+    for case in d["branch_outages"]:
+        r = screen.solve_outage(g, th0, V0, case["outage"], 1e-12, 100)
+        assert r["status"] == pf.STATUS_OK
+        on = np.ones(g.n_branch, bool)
+        on[case["outage"]] = False
+        isl = np.zeros(g.n_bus, bool)
+        isl[case["islanded"]] = True
+        live = on & ~isl[g.f] & ~isl[g.t]
+        yb = pf.ybus_entries(g.n_bus, g.f, g.t, g.r, g.x, g.b_sh, live)
+        dP, _ = pf.mismatch(yb, np.array(case["P_after"]), g.Q_sched, r["theta"], r["V"])
+        main = ~isl & (g.bus_type != 2)
+        assert np.abs(dP[main]).max() <= 1e-11

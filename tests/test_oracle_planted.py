@@ -88,3 +88,45 @@ def test_limit_sign_flipped_is_caught(monkeypatch):
     with pytest.raises(AssertionError):
         pins.test_two_bus_q_limit_closed_form()
 
+
+
+def test_equal_shares_redispatch_is_caught(monkeypatch):
+    """The island's power split equally over the main generators instead of
+    in proportion to their scheduled generation."""
+    from oracle import redispatch
+
+    def equal_shares(bus_type, P_sched, P_gen, islanded):
+        P = P_sched.astype(np.float64).copy()
+        if not islanded.any():
+            return P, False
+        part = (bus_type == 1) & (~islanded) & (P_gen > 0.0)
+        if not part.any():
+            P[islanded] = 0.0
+            return P, True
+        P[part] += float(P_sched[islanded].sum()) / part.sum()
+        P[islanded] = 0.0
+        return P, False
+
+    monkeypatch.setattr(screen, "redispatch", equal_shares)
+    monkeypatch.setattr(redispatch, "redispatch", equal_shares)
+    with pytest.raises(AssertionError):
+        pins.test_redispatch_hand_derived_ring()
+
+
+def test_redispatch_sign_flipped_is_caught(monkeypatch):
+    """The island's net injection subtracted from the main generators."""
+    from oracle import redispatch
+
+    def flipped(bus_type, P_sched, P_gen, islanded):
+        P = P_sched.astype(np.float64).copy()
+        if not islanded.any():
+            return P, False
+        part = (bus_type == 1) & (~islanded) & (P_gen > 0.0)
+        P[part] -= float(P_sched[islanded].sum()) * P_gen[part] / P_gen[part].sum()
+        P[islanded] = 0.0
+        return P, False
+
+    monkeypatch.setattr(screen, "redispatch", flipped)
+    monkeypatch.setattr(redispatch, "redispatch", flipped)
+    with pytest.raises(AssertionError):
+        pins.test_redispatch_hand_derived_ring()
