@@ -103,9 +103,9 @@ def algorithmic_bytes(info, iters, w, n_bus, n_branch):
 
 
 # DRAM bytes per launch of the N-1 kernel on the default grid10k workload
-# (dram__bytes_read.sum + dram__bytes_write.sum, mean of two ncu captures of
-# the timed screens; see profiles/launches_bench_grid10k.md), valid only for
-# the kernel sources with this digest.
+# (dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture of the
+# timed screens, taken by hand and recorded here), valid only for the kernel
+# sources with this digest; the bench line labels it as such.
 KERNEL_TRAFFIC = {"sha256": "ac7698b4de57d49b53789da9bd22a78f96fb8bae642a034641f89474a8f722a3", "bytes": 273.82e9}
 KERNEL_SOURCES = ("fdpf.cu", "fdpf_kernel.cuh", "fdpf_ops.cuh", "fdpf.h", "common.cuh")
 
@@ -175,6 +175,7 @@ def run_gpcg(args):
         "iters": torch.empty((K, 3), dtype=torch.int32, device=dev),
         "status": torch.empty((K,), dtype=torch.int32, device=dev),
         "max_loading": torch.empty((K,), dtype=torch.float64, device=dev),
+        "n_overload": torch.empty((K,), dtype=torch.int32, device=dev),
     }
     all_iters = torch.empty((S, 3), dtype=torch.int32, device=dev)
     all_status = torch.empty((S,), dtype=torch.int32, device=dev)
@@ -249,20 +250,36 @@ def run_gpcg(args):
     iters = all_iters.cpu().numpy()
     status = all_status.cpu().numpy()
 
-    # end to end through the public C ABI with host buffers: outage list in,
-    # per-scenario screening results (status, iterations, max loading) out
+    # end to end through the public C ABI with host buffers (pinned): outage
+    # list in, results out -- the screening summary (status, iterations, max
+    # loading, overload count) and, separately, every output of the screen
+    # (also angles, magnitudes, flows and island labels)
     hout = np.arange(S, dtype=np.int32)
-    e2e_ms = []
-    for k in range(args.steps + 1):
-        t0 = time.perf_counter()
-        r = c.n1_screen(hout, outputs=("iters", "status", "max_loading"))
-        dt = (time.perf_counter() - t0) * 1e3
-        if k:
-            e2e_ms.append(dt)
-    e2e = {"value": world * S / (statistics.mean(e2e_ms) / 1e3), "unit": "scenarios/s",
-           "h2d_bytes_per_step": int(hout.nbytes),
-           "d2h_bytes_per_step": int(r["iters"].nbytes + r["status"].nbytes +
-                                     r["max_loading"].nbytes)}
+
+    def e2e_run(names):
+        shapes = {"theta": ((S, n), torch.float64), "V": ((S, n), torch.float64),
+                  "flow": ((S, m), torch.float64), "label": ((S, n), torch.int32),
+                  "iters": ((S, 3), torch.int32), "status": ((S,), torch.int32),
+                  "max_loading": ((S,), torch.float64), "n_overload": ((S,), torch.int32)}
+        bufs = {k: torch.empty(*shapes[k][:1], dtype=shapes[k][1], pin_memory=True)
+                for k in names}
+        ms = []
+        for k in range(args.steps + 1):
+            t0 = time.perf_counter()
+            c.n1_screen(hout, out=bufs)
+            dt = (time.perf_counter() - t0) * 1e3
+            if k:
+                ms.append(dt)
+        return {"value": world * S / (statistics.mean(ms) / 1e3), "unit": "scenarios/s",
+                "h2d_bytes_per_step": int(hout.nbytes),
+                "d2h_bytes_per_step": int(sum(b.numel() * b.element_size() for b in bufs.values())),
+                "outputs": ", ".join(names)}
+
+    e2e = e2e_run(("iters", "status", "max_loading", "n_overload"))
+    e2e_full = None
+    if not args.e2e_summary_only:
+        e2e_full = e2e_run(("theta", "V", "flow", "label", "iters", "status", "max_loading",
+                            "n_overload"))
 
     # plain per-scenario FP64 PCG on a sample (one scenario per launch sequence)
     plain = None
@@ -289,6 +306,8 @@ def run_gpcg(args):
                kernel_digest() == KERNEL_TRAFFIC["sha256"] else None)
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic,
+            "traffic_source": ("recorded ncu capture of these kernel sources" if traffic
+                               else None),
             "kernel": "fdpf_tiles_kernel", "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": int(algo), "kernel_ms": round(fd_ms, 3),
             "islands_kernel_ms": round(statistics.mean(k[0] for k in kern_ms), 3)}
@@ -315,7 +334,7 @@ def run_gpcg(args):
                        "chunk": K, "streams": NS,
                        "l2": "flushed between steps (512 MiB write)",
                        "precond": args.precond, "precision": args.precision},
-            "e2e": e2e, "gpu_launches": 2 * n_chunks * args.steps,
+            "e2e": e2e, "e2e_full": e2e_full, "gpu_launches": 2 * n_chunks * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "plain": plain,
             "clocks": clk.summary(),
             "scenarios": {"converged": int((status == 0).sum()), "island_no_gen": int((status == 3).sum()),
@@ -701,6 +720,8 @@ def main():
     ap.add_argument("--streams", type=int, default=1,
                     help="with --chunk: contexts and streams that take the chunks in turn")
     ap.add_argument("--cpu-sample", type=int, default=400)
+    ap.add_argument("--e2e-summary-only", action="store_true",
+                    help="skip the end-to-end run that returns every output")
     ap.add_argument("--plain-sample", type=int, default=64)
     ap.add_argument("--ref-sample", type=int, default=256)
     ap.add_argument("--xfmr-frac", type=float, default=0.0,

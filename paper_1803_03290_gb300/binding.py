@@ -244,11 +244,21 @@ class GPCG:
         return self.n1_screen_device(gen_buses, out, stream, _fn="gpcg_n1_gen_screen")
 
     def n1_screen(self, outages, outputs=("theta", "V", "flow", "label", "iters", "status",
-                                          "max_loading"), _fn="gpcg_n1_screen"):
-        """Host-memory screen: returns numpy arrays."""
+                                          "max_loading"), _fn="gpcg_n1_screen", out=None):
+        """Host-memory screen: returns numpy arrays.  `out` (optional) maps
+        output names to caller-allocated host arrays of the right shape and
+        type -- numpy arrays or CPU torch tensors, pinned or not -- which are
+        filled instead of new arrays; `outputs` is then ignored."""
+        hold = out
         out = np.ascontiguousarray(outages, dtype=np.int32)
         S = out.shape[0]
         n, m = self.n_bus, self.n_branch
+        if hold is not None:
+            g = lambda k: _ptr(hold.get(k))
+            _check(self._lib, getattr(self._lib, _fn)(
+                self._h, _ptr(out), S, 0, None, g("theta"), g("V"), g("flow"), g("label"),
+                g("iters"), g("status"), g("max_loading"), g("n_overload"), g("overload")))
+            return hold
         res = {}
         spec = dict(theta=((S, n), np.float64), V=((S, n), np.float64),
                     flow=((S, m), np.float64), label=((S, n), np.int32),

@@ -190,8 +190,14 @@ struct gpcg_ctx {
   int n_adj_slots = 0, n_adj_over = 0;
   std::vector<int32_t> deg;
   int32_t *mis_order = nullptr, *misq_order = nullptr;
-  unsigned long long* phase = nullptr;
+  unsigned long long* phase = nullptr;  // diagnostics: [8 + 2 phase_cap]
+  size_t phase_cap = 0;
   bool phase_on = false;
+  // each tile's z vector in shared memory where it fits (branch outages
+  // without reactive limits, tiles of 2 or 4), asked for with GPCG_Z_SMEM=1:
+  // it halves a scenario's latency but fits 2 CTAs per SM instead of 5, so a
+  // full screen is slower
+  bool zs_allowed = false;
   DevGrid G;
   double *wP = nullptr, *wQ = nullptr;
   MatDev MP, MQ;
@@ -792,12 +798,15 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
   AL(c->r0Q, n);
   for (auto& e : c->ev)
     if ((ce = cudaEventCreate(&e)) != cudaSuccess) return fail_cuda(ce, "event");
-  AL(c->phase, 8);
+  AL(c->phase, 8 + 2);
+  c->phase_cap = 1;
   if ((ce = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return fail_cuda(ce, "stream");
   {
     const char* ev = std::getenv("GPCG_PHASE_TIMERS");
     c->phase_on = ev && ev[0] == '1';
+    const char* zv = std::getenv("GPCG_Z_SMEM");
+    c->zs_allowed = zv && zv[0] == '1';
   }
 #undef UP
 #undef AL
@@ -904,7 +913,7 @@ struct Layout {
   size_t vstride = 0, sstride = 0, vec_bytes = 0, bytes = 0;
 };
 
-static Layout make_layout(const gpcg_ctx* c, int T, int slots, size_t vt_size) {
+static Layout make_layout(const gpcg_ctx* c, int T, int slots, size_t vt_size, bool zs = false) {
   Layout L;
   L.T = T;
   L.slots = slots;
@@ -914,29 +923,34 @@ static Layout make_layout(const gpcg_ctx* c, int T, int slots, size_t vt_size) {
   L.sstride = (size_t)c->n * T;
   L.vec_bytes = ((L.vstride * vt_size + 255) / 256) * 256;
   const size_t st_bytes = ((L.sstride * 8 + 255) / 256) * 256;
-  L.bytes = (size_t)slots * (5 * L.vec_bytes + 6 * st_bytes);
+  L.bytes = (size_t)slots * ((zs ? 4 : 5) * L.vec_bytes + 4 * st_bytes);
   return L;
 }
 
+// zs: each tile's z vector in the kernel's dynamic shared memory (the
+// vector's bytes of it) instead of the work buffer.
 template <typename VT>
 static gpcg_status run_fdpf(gpcg_ctx* c, cudaStream_t st, FdpfParams P, int T, int slots,
-                            bool f16 = false) {
-  Layout Lo = make_layout(c, T, slots, sizeof(VT));
+                            bool f16 = false, bool zs = false) {
+  Layout Lo = make_layout(c, T, slots, sizeof(VT), zs);
   gpcg_status s = ensure_work(c, Lo.bytes);
   if (s != GPCG_OK) return s;
   char* base = (char*)c->work;
   const size_t vb = (size_t)slots * Lo.vec_bytes;
   const size_t sb = (size_t)slots * (((Lo.sstride * 8 + 255) / 256) * 256);
-  P.wx = base; P.wr = base + vb; P.wp = base + 2 * vb; P.wq = base + 3 * vb; P.wz = base + 4 * vb;
+  const int nv = zs ? 4 : 5;
+  P.wx = base; P.wr = base + vb; P.wp = base + 2 * vb; P.wq = base + 3 * vb;
+  P.wz = zs ? nullptr : base + 4 * vb;
   P.vstride = Lo.vec_bytes / sizeof(VT);
-  double* sbase = (double*)(base + 5 * vb);
+  double* sbase = (double*)(base + nv * vb);
   const size_t ss = sb / slots / 8;
-  P.wth = sbase; P.wV = sbase + slots * ss; P.wc = sbase + 2 * slots * ss;
-  P.ws = sbase + 3 * slots * ss; P.we = sbase + 4 * slots * ss; P.wf = sbase + 5 * slots * ss;
+  P.wth = sbase; P.wV = sbase + slots * ss; P.we = sbase + 2 * slots * ss;
+  P.wf = sbase + 3 * slots * ss;
   P.sstride = ss;
   P.tile_counter = c->d_counter;
   CUDA_TRY(cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), st));
-  CUDA_TRY(launch_fdpf<VT>(st, T, slots, P, c->MP.view<VT>(f16), c->MQ.view<VT>(f16)));
+  CUDA_TRY(launch_fdpf<VT>(st, T, slots, P, c->MP.view<VT>(f16), c->MQ.view<VT>(f16),
+                           zs ? Lo.vec_bytes : 0));
   return GPCG_OK;
 }
 
@@ -1120,6 +1134,15 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
     return fail(ce == cudaErrorMemoryAllocation ? GPCG_ERR_OOM : GPCG_ERR_CUDA,
                 "output staging: %s", cudaGetErrorString(ce));
   }
+  if (c->phase_on && S > c->phase_cap) {
+    // diagnostics: room for every scenario's start and finish times
+    CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(c->phase);
+    c->phase = nullptr;
+    c->phase_cap = 0;
+    CUDA_TRY(cudaMalloc(&c->phase, (8 + 2 * S) * sizeof(unsigned long long)));
+    c->phase_cap = S;
+  }
   FdpfParams P = base_params(c);
   P.sc = ScenInfo{c->d_outages, c->d_lo, c->d_cnt, c->d_coef, c->d_nogen,
                   gen ? c->d_genbus : nullptr};
@@ -1154,6 +1177,16 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
   };
   gpcg_status rs = GPCG_OK;
   int T = 2, slots = 1;
+  bool zs = false;
+  // CTAs per SM of tile width t, with z in shared memory or not (0: does not fit)
+  auto blocks = [&](int t, bool z) {
+    const size_t zb = z ? make_layout(c, t, 1, f32 ? 4 : 8, true).vec_bytes : 0;
+    return f32 ? fdpf_max_blocks_per_sm<float>(t, ext, zb)
+               : fdpf_max_blocks_per_sm<double>(t, ext, zb);
+  };
+  auto use_zs = [&](int t) {
+    return c->zs_allowed && !ext && (t == 2 || t == 4) && blocks(t, true) > 0;
+  };
   if (!plain) {
     if (!c->opt.tile && !c->tile) {
       // autotuner: the tile width that screens a probe of the first outages
@@ -1168,10 +1201,12 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
         Q.th0 = P.th0; Q.V0 = P.V0; Q.c0 = P.c0; Q.s0 = P.s0;
         Q.S = probe;
         Q.n_tiles = (probe + t - 1) / t;
-        int ps = f32 ? fdpf_max_blocks_per_sm<float>(t, ext) : fdpf_max_blocks_per_sm<double>(t, ext);
+        const bool z = use_zs(t);
+        const int ps = blocks(t, z);
         const int sl = std::max(1, std::min(Q.n_tiles, c->num_sms * std::max(ps, 1)));
         CUDA_TRY(cudaEventRecord(c->ev[3], st));
-        rs = f32 ? run_fdpf<float>(c, st, Q, t, sl, f16) : run_fdpf<double>(c, st, Q, t, sl);
+        rs = f32 ? run_fdpf<float>(c, st, Q, t, sl, f16, z)
+                 : run_fdpf<double>(c, st, Q, t, sl, false, z);
         if (rs != GPCG_OK) { cleanup(); return rs; }
         CUDA_TRY(cudaEventRecord(c->ev[2], st));
         CUDA_TRY(cudaEventSynchronize(c->ev[2]));
@@ -1183,17 +1218,17 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
     }
     T = c->opt.tile ? c->opt.tile : (c->tile ? c->tile : 2);
     if (ext) T = std::min(T, 8);  // the kernel with extension rows: tiles of 2, 4, 8
+    zs = use_zs(T);
     const int n_tiles = (int)((S + T - 1) / T);
     int per_sm = c->opt.ctas_per_sm;
-    if (per_sm == 0)
-      per_sm = f32 ? fdpf_max_blocks_per_sm<float>(T, ext) : fdpf_max_blocks_per_sm<double>(T, ext);
+    if (per_sm == 0 || (zs && per_sm > blocks(T, true))) per_sm = blocks(T, zs);
     per_sm = std::max(per_sm, 1);
     slots = std::max(1, std::min(n_tiles, c->num_sms * per_sm));
     P.S = (int)S;
     P.n_tiles = n_tiles;
     P.order = c->d_order;
   }
-  if (c->phase_on) CUDA_TRY(cudaMemsetAsync(c->phase, 0, 8 * sizeof(unsigned long long), st));
+  if (c->phase_on) CUDA_TRY(cudaMemsetAsync(c->phase, 0, (8 + 2 * S) * sizeof(unsigned long long), st));
   if (plain) {
     CUDA_TRY(enqueue_islands(st));
     // one scenario at a time: no batching across scenarios
@@ -1216,7 +1251,7 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
   } else if (mem == GPCG_MEM_DEVICE && !c->phase_on) {
     // device mode: islanding + solve as one CUDA graph, captured on the
     // context's own stream for this argument set and replayed on `st`
-    Layout Lo = make_layout(c, T, slots, f32 ? 4 : 8);
+    Layout Lo = make_layout(c, T, slots, f32 ? 4 : 8, zs);
     s_ = ensure_work(c, Lo.bytes);
     if (s_ != GPCG_OK) { cleanup(); return s_; }
     std::vector<uintptr_t> key = {S, (uintptr_t)T, (uintptr_t)slots,
@@ -1225,7 +1260,8 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
                                   (uintptr_t)d_flow, (uintptr_t)d_lab, (uintptr_t)d_iters,
                                   (uintptr_t)d_stat, (uintptr_t)d_ml, (uintptr_t)d_nov,
                                   (uintptr_t)d_ovm, (uintptr_t)c->d_outages,
-                                  (uintptr_t)c->d_order, (uintptr_t)c->d_lo, (uintptr_t)gen};
+                                  (uintptr_t)c->d_order, (uintptr_t)c->d_lo, (uintptr_t)gen,
+                                  (uintptr_t)zs};
     {
       double opts[3] = {c->opt.tol, c->opt.inner_rtol, 0.0};
       uintptr_t bits[3];
@@ -1239,8 +1275,8 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
       CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
       cudaError_t e = enqueue_islands(c->cap_stream, true);
       if (e == cudaSuccess) {
-        rs = f32 ? run_fdpf<float>(c, c->cap_stream, P, T, slots, f16)
-                 : run_fdpf<double>(c, c->cap_stream, P, T, slots);
+        rs = f32 ? run_fdpf<float>(c, c->cap_stream, P, T, slots, f16, zs)
+                 : run_fdpf<double>(c, c->cap_stream, P, T, slots, false, zs);
         if (rs == GPCG_OK) e = record(c->ev[2], c->cap_stream, true);
       }
       cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &gr);
@@ -1257,7 +1293,8 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
     return GPCG_OK;
   } else {
     CUDA_TRY(enqueue_islands(st));
-    rs = f32 ? run_fdpf<float>(c, st, P, T, slots, f16) : run_fdpf<double>(c, st, P, T, slots);
+    rs = f32 ? run_fdpf<float>(c, st, P, T, slots, f16, zs)
+             : run_fdpf<double>(c, st, P, T, slots, false, zs);
   }
   if (rs != GPCG_OK) { cleanup(); return rs; }
   CUDA_TRY(cudaEventRecord(c->ev[2], st));
@@ -1275,6 +1312,39 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
     std::fprintf(stderr, "gpcg phase cycles (sum over CTAs):");
     for (int k = 0; k < 8; ++k) std::fprintf(stderr, " %s=%.1f%%", names[k], 100.0 * h[k] / tot);
     std::fprintf(stderr, " total=%.3e\n", tot);
+  }
+  if (c->phase_on && !plain) {
+    // per-scenario start and finish times: completion profile and the
+    // longest scenarios (the tail of the persistent launch)
+    std::vector<unsigned long long> tt(2 * S);
+    CUDA_TRY(cudaMemcpy(tt.data(), c->phase + 8, 2 * S * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost));
+    unsigned long long t0 = ~0ull, t1 = 0;
+    for (size_t k = 0; k < S; ++k) {
+      t0 = std::min(t0, tt[2 * k]);
+      t1 = std::max(t1, tt[2 * k + 1]);
+    }
+    std::vector<double> fin(S), dur(S);
+    for (size_t k = 0; k < S; ++k) {
+      fin[k] = 1e-6 * (double)(tt[2 * k + 1] - t0);
+      dur[k] = 1e-6 * (double)(tt[2 * k + 1] - tt[2 * k]);
+    }
+    std::vector<double> fs = fin, ds = dur;
+    std::sort(fs.begin(), fs.end());
+    std::sort(ds.begin(), ds.end());
+    auto q = [&](const std::vector<double>& v, double f) {
+      return v[std::min(v.size() - 1, (size_t)(f * (double)(v.size() - 1)))];
+    };
+    std::fprintf(stderr,
+                 "gpcg scenario finish (ms after the first start): 50%% %.2f, 90%% %.2f, "
+                 "99%% %.2f, last %.2f; scenario durations: median %.2f, 99%% %.2f, max %.2f\n",
+                 q(fs, 0.5), q(fs, 0.9), q(fs, 0.99), 1e-6 * (double)(t1 - t0), q(ds, 0.5),
+                 q(ds, 0.99), ds.back());
+    size_t kmax = 0;
+    for (size_t k = 0; k < S; ++k)
+      if (dur[k] > dur[kmax]) kmax = k;
+    std::fprintf(stderr, "gpcg longest scenario: index %zu (outage %d), start %.2f ms, %.2f ms\n",
+                 kmax, hout[kmax], 1e-6 * (double)(tt[2 * kmax] - t0), dur[kmax]);
   }
   if (mem == GPCG_MEM_HOST) {
     auto back = [&](auto* user, auto* dev, size_t count) -> cudaError_t {
@@ -1459,8 +1529,8 @@ extern "C" gpcg_status gpcg_n1_adjoint(gpcg_ctx* c, const int32_t* outages, int3
     P.wx = base; P.wr = base + vb; P.wp = base + 2 * vb; P.wq = base + 3 * vb; P.wz = base + 4 * vb;
     P.vstride = Lo.vec_bytes / 8;
     double* sbase = (double*)(base + 5 * vb);
-    P.wth = sbase; P.wV = sbase + slots * ss; P.wc = sbase + 2 * slots * ss;
-    P.ws = sbase + 3 * slots * ss; P.we = sbase + 4 * slots * ss; P.wf = sbase + 5 * slots * ss;
+    P.wth = sbase; P.wV = sbase + slots * ss; P.we = sbase + 2 * slots * ss;
+    P.wf = sbase + 3 * slots * ss;
     P.sstride = ss;
     P.tile_counter = c->d_counter;
     CUDA_TRY(cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), st));
@@ -1581,8 +1651,8 @@ extern "C" gpcg_status gpcg_n1_dc_screen(gpcg_ctx* c, const int32_t* outages, in
   P.wx = base; P.wr = base + vb; P.wp = base + 2 * vb; P.wq = base + 3 * vb; P.wz = base + 4 * vb;
   P.vstride = Lo.vec_bytes / vt;
   double* sbase = (double*)(base + 5 * vb);
-  P.wth = sbase; P.wV = sbase + slots * ss; P.wc = sbase + 2 * slots * ss;
-  P.ws = sbase + 3 * slots * ss;
+  P.wth = sbase; P.wV = sbase + slots * ss; P.we = sbase + 2 * slots * ss;
+  P.wf = sbase + 3 * slots * ss;
   P.sstride = ss;
   DcParamsView D{dPi, c->G.user_of_bus, d_th, d_fl, d_ml, d_it, d_st, d_nov, d_ovm};
   ce = f32 ? launch_dc<float>(st, slots, P, D, c->MP.view<float>(f16), c->MP.view<double>())

@@ -32,8 +32,8 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
   double* th = P.wth + (size_t)blockIdx.x * P.sstride;  // theta by bus, [bus][lane]
   // FP64 work by row for the refinement step: solution, B_s x, right-hand side
   double* xd = P.wV + (size_t)blockIdx.x * P.sstride;
-  double* qd = P.wc + (size_t)blockIdx.x * P.sstride;
-  double* bd = P.ws + (size_t)blockIdx.x * P.sstride;
+  double* qd = P.we + (size_t)blockIdx.x * P.sstride;
+  double* bd = P.wf + (size_t)blockIdx.x * P.sstride;
   __shared__ Stamp<T, double> St64;
   const int l0 = g.lane, l1 = g.lane + 1;
   for (int tile = blockIdx.x; tile < P.n_tiles; tile += gridDim.x) {

@@ -113,14 +113,18 @@ __global__ void base_trig_kernel(int n, const double* th, double* c, double* s) 
 // ----------------------------------------------------------- launchers
 template <typename VT>
 cudaError_t launch_fdpf(cudaStream_t st, int T, int grid, const FdpfParams& P,
-                        const DevMatT<VT>& MP, const DevMatT<VT>& MQ) {
-  if (P.sc.gen_bus || P.G.qmax) return launch_fdpf_gen<VT>(st, T, grid, P, MP, MQ);
-  return launch_fdpf_g<false, VT>(st, T, grid, P, MP, MQ);
+                        const DevMatT<VT>& MP, const DevMatT<VT>& MQ, size_t zbytes) {
+  if (P.sc.gen_bus || P.G.qmax) {
+    if (zbytes) return cudaErrorInvalidValue;
+    return launch_fdpf_gen<VT>(st, T, grid, P, MP, MQ);
+  }
+  return launch_fdpf_g<false, VT>(st, T, grid, P, MP, MQ, zbytes);
 }
 
 template <typename VT>
-int fdpf_max_blocks_per_sm(int T, bool gen) {
-  return gen ? fdpf_blocks_gen<VT>(T) : fdpf_blocks_g<false, VT>(T);
+int fdpf_max_blocks_per_sm(int T, bool gen, size_t zbytes) {
+  if (gen) return zbytes ? 0 : fdpf_blocks_gen<VT>(T);
+  return fdpf_blocks_g<false, VT>(T, zbytes);
 }
 
 template <typename VT>
@@ -138,11 +142,11 @@ cudaError_t launch_base_trig(cudaStream_t st, int n, const double* th, double* c
 }
 
 template cudaError_t launch_fdpf<float>(cudaStream_t, int, int, const FdpfParams&,
-                                        const DevMatT<float>&, const DevMatT<float>&);
+                                        const DevMatT<float>&, const DevMatT<float>&, size_t);
 template cudaError_t launch_fdpf<double>(cudaStream_t, int, int, const FdpfParams&,
-                                         const DevMatT<double>&, const DevMatT<double>&);
-template int fdpf_max_blocks_per_sm<float>(int, bool);
-template int fdpf_max_blocks_per_sm<double>(int, bool);
+                                         const DevMatT<double>&, const DevMatT<double>&, size_t);
+template int fdpf_max_blocks_per_sm<float>(int, bool, size_t);
+template int fdpf_max_blocks_per_sm<double>(int, bool, size_t);
 template cudaError_t launch_apply<float>(cudaStream_t, int, const DevMatT<float>&, int, int,
                                          const int32_t*, const int32_t*, const int32_t*,
                                          const double*, double*, float*, size_t, int);

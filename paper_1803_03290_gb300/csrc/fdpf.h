@@ -26,9 +26,9 @@ struct FdpfParams {
   const int32_t* order = nullptr;      // scenarios in processing order (null: 0..S-1)
   void *wx = nullptr, *wr = nullptr, *wp = nullptr, *wq = nullptr, *wz = nullptr;
   size_t vstride = 0;  // elements per slot of one vector
-  // FP64 state per slot: theta, |V|, cos, sin; e + jf interleaved over the we
-  // and wf regions together ([slot][bus][lane][e, f], 2 sstride per slot)
-  double *wth = nullptr, *wV = nullptr, *wc = nullptr, *ws = nullptr, *we = nullptr, *wf = nullptr;
+  // FP64 state per slot: theta, |V|; e + jf interleaved over the we and wf
+  // regions together ([slot][bus][lane][e, f], 2 sstride per slot)
+  double *wth = nullptr, *wV = nullptr, *we = nullptr, *wf = nullptr;
   size_t sstride = 0;  // elements per slot of one state array
   double *out_theta = nullptr, *out_vm = nullptr, *out_flow = nullptr, *out_maxload = nullptr;
   const int32_t* out_bus_map = nullptr;  // internal bus -> output column (null: identity)
@@ -37,18 +37,22 @@ struct FdpfParams {
   // rating, and those branches as a bit mask of mask_words words
   int32_t* out_nover = nullptr;
   uint32_t* out_ovmask = nullptr;
-  unsigned long long* phase_cycles = nullptr;  // [8] per-phase SM cycles, or null
+  // diagnostics, or null: [8] per-phase SM cycles summed over CTAs, then per
+  // scenario the global timer (ns) when a lane took it and when it retired
+  unsigned long long* phase_cycles = nullptr;
   const int32_t* mis_order = nullptr;   // non-slack buses sorted by degree
   const int32_t* misq_order = nullptr;  // B'' rows sorted by their bus's degree
 };
 
 // The persistent N-1 kernel for tiles of T scenarios (2 to 32; generator
-// outages, P.sc.gen_bus set: 2, 4 or 8) on `grid` slots.
+// outages, P.sc.gen_bus set: 2, 4 or 8) on `grid` slots.  zbytes > 0 (branch
+// outages without reactive limits, T = 2 or 4): each tile's z vector in
+// zbytes of dynamic shared memory, P.wz unused.
 template <typename VT>
 cudaError_t launch_fdpf(cudaStream_t st, int T, int grid, const FdpfParams& P,
-                        const DevMatT<VT>& MP, const DevMatT<VT>& MQ);
+                        const DevMatT<VT>& MP, const DevMatT<VT>& MQ, size_t zbytes = 0);
 template <typename VT>
-int fdpf_max_blocks_per_sm(int T, bool gen = false);
+int fdpf_max_blocks_per_sm(int T, bool gen = false, size_t zbytes = 0);
 // the generator-outage kernel (fdpf_gen.cu)
 template <typename VT>
 cudaError_t launch_fdpf_gen(cudaStream_t st, int T, int grid, const FdpfParams& P,

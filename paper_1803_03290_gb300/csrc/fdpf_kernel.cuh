@@ -277,37 +277,53 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
     }
 }
 
-// (cos, sin) of theta + d from those of theta, by rotating through d:
-//   c' = c - (c (1 - cos d) + s sin d),   s' = s - (s (1 - cos d) - c sin d).
-// For |d| <= 0.05 the two corrections are small (about |d|), so they are
-// formed in FP32 from the Taylor series of 1 - cos d and sin d (three terms
-// each; remainders below 4e-12 relative) and applied in FP64: their rounding
-// error, 6e-8 of |d|, vanishes as the iteration converges (the outer FDPF
-// loop sees the state through e + jf and corrects any drift).  d itself is
-// the FP32 solution of the inner solve.  Larger steps recompute the angle.
-template <typename VT>
-__device__ __forceinline__ void rotate(double th_new, VT d, double& c, double& s) {
-  if (fabs(d) <= (VT)0.05) {
-    const float df = to_f32(d), d2 = df * df;
-    const float omc = d2 * (0.5f - d2 * (1.0f / 24.0f - d2 * (1.0f / 720.0f)));
-    const float sd = df * (1.0f - d2 * (1.0f / 6.0f - d2 * (1.0f / 120.0f)));
-    const float cf = cvt_f32(c), sf = cvt_f32(s);
-    const float dc = fmaf(cf, omc, sf * sd), ds = fmaf(sf, omc, -cf * sd);
-    c -= cvt_f64(dc);
-    s -= cvt_f64(ds);
+// (e, f) rotated through the angle d, in FP64:
+//   e' = e cos d - f sin d = e - (e a + f b),  f' = f - (f a - e b),
+// with a = 1 - cos d and b = sin d.  For |d| <= 0.02 both come from their
+// Taylor series in u = d^2 (a = u/2 - u^2/24 + u^3/720, b = d - d^3/6 +
+// d^5/120; the first dropped terms are below 3e-16 there), larger steps call
+// sincos.  The rotation is exact to FP64 rounding, so the state (e, f) stays
+// at the angle theta and modulus |V| that the kernel reports: the state whose
+// mismatch the convergence test evaluated is the state that is returned.
+__device__ __forceinline__ void rotate_ef(double d, double& e, double& f) {
+  double a, b;
+  if (fabs(d) <= 0.02) {
+    const double u = d * d;
+    a = u * fma(u, fma(u, 1.0 / 720.0, -1.0 / 24.0), 0.5);
+    b = fma(d * u, fma(u, 1.0 / 120.0, -1.0 / 6.0), d);
   } else {
-    sincos(th_new, &s, &c);
+    double c;
+    sincos(d, &b, &c);
+    a = 1.0 - c;
   }
+  const double e0 = e;
+  e = fma(-e0, a, fma(-f, b, e0));
+  f = fma(-f, a, fma(e0, b, f));
+}
+
+// The relative step r = dV / |V| of a |V| update: FP32 vectors take it in
+// FP32 (the step is an inner-solve iterate that the outer FP64 loop refines;
+// r is then exact as an FP64 number), FP64 vectors in FP64.
+template <typename VT>
+__device__ __forceinline__ double v_ratio(VT dv, double v);
+template <>
+__device__ __forceinline__ double v_ratio<float>(float dv, double v) {
+  return cvt_f64(__fdividef(dv, cvt_f32(v)));
+}
+template <>
+__device__ __forceinline__ double v_ratio<double>(double dv, double v) {
+  return dv / v;
 }
 
 // theta += dtheta (P half-step) or |V| += dV (Q half-step) on the matrix's
-// rows, then refresh the rectangular voltages; lanes two at a time.
+// rows, with the rectangular voltages moved with them: (e, f) rotated through
+// dtheta, or |V|, e and f all scaled by the same factor 1 + dV/|V|, so that
+// e + jf = |V| exp(j theta) holds to FP64 rounding; lanes two at a time.
 template <int T, typename VT, bool IS_P, bool GEN>
 __device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>& L,
                                              const VT* __restrict__ x,
                                              const VT* __restrict__ p, double* th, double* V,
-                                             double* C, double* Sn, double* EF,
-                                             const SwitchState<T>* SW = nullptr) {
+                                             double* EF, const SwitchState<T>* SW = nullptr) {
   constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
   bool any = false;
@@ -332,27 +348,37 @@ __device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>&
         dx.a = fma(xa0, pv.a, dx.a);  // as the solve's own step would take it
         dx.b = fma(xa1, pv.b, dx.b);
       }
-      if (!on0) dx.a = (VT)0;
-      if (!on1) dx.b = (VT)0;
-      const double d0 = to_f64(dx.a), d1 = to_f64(dx.b);
-      Pair<double> c = ld2(C + o), s = ld2(Sn + o), v = ld2(V + o);
+      double2* ef = reinterpret_cast<double2*>(EF + ef_at<T>(i, l0));
+      double2 u0 = ef[0], u1 = ef[1];
       if (IS_P) {
         Pair<double> t = ld2(th + o);
-        t.a += d0;
-        t.b += d1;
-        if (on0) rotate(t.a, dx.a, c.a, s.a);
-        if (on1) rotate(t.b, dx.b, c.b, s.b);
+        if (on0) {
+          const double d = to_f64(dx.a);
+          t.a += d;
+          rotate_ef(d, u0.x, u0.y);
+        }
+        if (on1) {
+          const double d = to_f64(dx.b);
+          t.b += d;
+          rotate_ef(d, u1.x, u1.y);
+        }
         st2(th + o, t);
-        st2(C + o, c);
-        st2(Sn + o, s);
       } else {
-        v.a += d0;
-        v.b += d1;
+        Pair<double> v = ld2(V + o);
+        if (on0) {
+          const double r = v_ratio<VT>(dx.a, v.a);
+          v.a = fma(v.a, r, v.a);
+          u0 = make_double2(fma(u0.x, r, u0.x), fma(u0.y, r, u0.y));
+        }
+        if (on1) {
+          const double r = v_ratio<VT>(dx.b, v.b);
+          v.b = fma(v.b, r, v.b);
+          u1 = make_double2(fma(u1.x, r, u1.x), fma(u1.y, r, u1.y));
+        }
         st2(V + o, v);
       }
-      double2* ef = reinterpret_cast<double2*>(EF + ef_at<T>(i, l0));
-      ef[0] = make_double2(v.a * c.a, v.a * s.a);
-      ef[1] = make_double2(v.b * c.b, v.b * s.b);
+      ef[0] = u0;
+      ef[1] = u1;
     }
   }
   // |V| of the extension rows' buses
@@ -368,13 +394,21 @@ __device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>&
       const VT xa = (VT)L.xalpha[ln];
       if (xa != (VT)0) dx = fma(xa, p[oe], dx);
       const size_t o = (size_t)b * T + ln;
-      const double v = V[o] + to_f64(dx);
-      V[o] = v;
-      reinterpret_cast<double2*>(EF + ef_at<T>(b, ln))[0] = make_double2(v * C[o], v * Sn[o]);
+      const double r = v_ratio<VT>(dx, V[o]);
+      V[o] = fma(V[o], r, V[o]);
+      double2* ef = reinterpret_cast<double2*>(EF + ef_at<T>(b, ln));
+      const double2 u = ef[0];
+      ef[0] = make_double2(fma(u.x, r, u.x), fma(u.y, r, u.y));
     }
 }
 
 // ------------------------------------------------------------ the kernel
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Scenario info of a lane taking scenario s (thread `ln`, one per lane).
 template <int T, typename VT>
 __device__ __forceinline__ void setup_lane(const FdpfParams& P, const DevMatT<VT>& MP,
@@ -423,7 +457,7 @@ __device__ __forceinline__ void setup_lane(const FdpfParams& P, const DevMatT<VT
 // zero on islanded buses.  Other lanes keep their state.
 template <int T>
 __device__ GPCG_PASS_INLINE void init_pass(const FdpfParams& P, LaneState<T>& L, double* th,
-                                           double* V, double* C, double* Sn, double* EF) {
+                                           double* V, double* EF) {
   constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
   const DevGrid& G = P.G;
@@ -444,8 +478,6 @@ __device__ GPCG_PASS_INLINE void init_pass(const FdpfParams& P, LaneState<T>& L,
       const bool isl = in_island(pr, L.lo[ln], L.cnt[ln]);
       th[o] = isl ? 0.0 : t0;
       V[o] = isl ? 0.0 : v0;
-      C[o] = c0;
-      Sn[o] = s0;
       reinterpret_cast<double2*>(EF + ef_at<T>(i, ln))[0] =
           isl ? make_double2(0.0, 0.0) : make_double2(v0 * c0, v0 * s0);
     }
@@ -549,6 +581,7 @@ __device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& 
       }
       if (P.out_maxload) P.out_maxload[s] = from_bits(mlb.v[j]);
       if (P.out_nover) P.out_nover[s] = nov.v[j];
+      if (P.phase_cycles) P.phase_cycles[8 + 2 * (size_t)s + 1] = global_ns();
       L.done[ln] = 0;
       L.scen[ln] = -1;
     }
@@ -562,8 +595,15 @@ __device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& 
 // iteration and immediately refilled, so converged scenarios never hold a
 // lane (the slot's lanes are compacted onto live work) and the kernel ends
 // when the queue is drained and every lane has retired.
-template <int T, typename VT, bool GEN>
-__global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
+//
+// ZS: the tile's z vector -- the one the substitutions and the SpMV gather
+// from, level after level -- lives in the CTA's dynamic shared memory
+// instead of global memory, so those dependent gathers wait on shared memory
+// rather than on L2 or DRAM; the CTA then takes rows x T x sizeof(VT) bytes
+// of shared memory (80 KB for FP32 tiles of two on a 10,000-bus grid), two
+// CTAs fit an SM, and the register budget is set for two.
+template <int T, typename VT, bool GEN, bool ZS = false>
+__global__ void __launch_bounds__(NTHREADS, ZS ? 2 : FDPF_MIN_BLOCKS)
     fdpf_tiles_kernel(FdpfParams P_, DevMatT<VT> MP_, DevMatT<VT> MQ_) {
   __shared__ LaneState<T> L;
   // the parameter blocks in shared memory: the out-of-line passes take them
@@ -593,10 +633,11 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
   VT* r = (VT*)P.wr + (size_t)blockIdx.x * P.vstride;
   VT* p = (VT*)P.wp + (size_t)blockIdx.x * P.vstride;
   VT* q = (VT*)P.wq + (size_t)blockIdx.x * P.vstride;
-  VT* z = (VT*)P.wz + (size_t)blockIdx.x * P.vstride;
+  extern __shared__ __align__(16) unsigned char zdyn[];
+  VT* z = ZS ? reinterpret_cast<VT*>(zdyn) : (VT*)P.wz + (size_t)blockIdx.x * P.vstride;
   const size_t so = (size_t)blockIdx.x * P.sstride;
   // E and F regions of the slots taken together: [slot][bus][lane][e, f]
-  double *th = P.wth + so, *V = P.wV + so, *C = P.wc + so, *Sn = P.ws + so, *EF = P.we + 2 * so;
+  double *th = P.wth + so, *V = P.wV + so, *EF = P.we + 2 * so;
 
   // optional per-phase cycle counters (thread 0's view of the CTA)
   const bool tim = P.phase_cycles != nullptr;
@@ -653,9 +694,12 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
       }
     }
     __syncthreads();
-    if (tid < T && L.fresh[tid]) setup_lane<T, VT>(P, MP, MQ, L, tid, SW);
+    if (tid < T && L.fresh[tid]) {
+      setup_lane<T, VT>(P, MP, MQ, L, tid, SW);
+      if (tim) P.phase_cycles[8 + 2 * (size_t)L.scen[tid]] = global_ns();
+    }
     __syncthreads();
-    init_pass<T>(P, L, th, V, C, Sn, EF);
+    init_pass<T>(P, L, th, V, EF);
     __syncthreads();
     if (tid < T) L.fresh[tid] = 0;
     GPCG_PHASE(0);
@@ -723,7 +767,7 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     if (!more) continue;
     pcg_solve<T, VT, true, GEN>(P, MP, L, x, r, p, q, z, L.raP, L.rbP, L.wP, L.inP);
     GPCG_PHASE(2);
-    update_pass<T, VT, true, GEN>(MP, L, x, p, th, V, C, Sn, EF, SW);
+    update_pass<T, VT, true, GEN>(MP, L, x, p, th, V, EF, SW);
     __syncthreads();
     GPCG_PHASE(3);
     // Q half-step
@@ -734,7 +778,7 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     pcg_solve<T, VT, true, GEN>(P, MQ, L, x, r, p, q, z, L.raQ, L.rbQ, L.wQ, L.inQ,
                                 MQ.c ? L.cl : nullptr, SW);
     GPCG_PHASE(5);
-    update_pass<T, VT, false, GEN>(MQ, L, x, p, th, V, C, Sn, EF, SW);
+    update_pass<T, VT, false, GEN>(MQ, L, x, p, th, V, EF, SW);
     if (g.rs == 0)
 #pragma unroll
       for (int j = 0; j < LP; ++j)
@@ -749,9 +793,31 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
 
 
 // ----------------------------------------------------------- launchers
+// zbytes > 0: the variant with z in `zbytes` of dynamic shared memory (branch
+// outages, tiles of 2 or 4); 0: z in global memory.
+template <int T, typename VT, bool ZS>
+cudaError_t set_zs_smem(size_t zbytes) {
+  if constexpr (!ZS) return cudaSuccess;
+  else return cudaFuncSetAttribute(fdpf_tiles_kernel<T, VT, false, true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zbytes);
+}
+
 template <bool GEN, typename VT>
 cudaError_t launch_fdpf_g(cudaStream_t st, int T, int grid, const FdpfParams& P,
-                          const DevMatT<VT>& MP, const DevMatT<VT>& MQ) {
+                          const DevMatT<VT>& MP, const DevMatT<VT>& MQ, size_t zbytes = 0) {
+  if (zbytes) {
+    if constexpr (GEN) return cudaErrorInvalidValue;
+    else {
+      cudaError_t ce = cudaErrorInvalidValue;
+      if (T == 2 && (ce = set_zs_smem<2, VT, true>(zbytes)) == cudaSuccess)
+        fdpf_tiles_kernel<2, VT, false, true><<<grid, NTHREADS, zbytes, st>>>(P, MP, MQ);
+      else if (T == 4 && (ce = set_zs_smem<4, VT, true>(zbytes)) == cudaSuccess)
+        fdpf_tiles_kernel<4, VT, false, true><<<grid, NTHREADS, zbytes, st>>>(P, MP, MQ);
+      else
+        return ce;
+      return cudaGetLastError();
+    }
+  }
   switch (T) {
     case 2: fdpf_tiles_kernel<2, VT, GEN><<<grid, NTHREADS, 0, st>>>(P, MP, MQ); break;
     case 4: fdpf_tiles_kernel<4, VT, GEN><<<grid, NTHREADS, 0, st>>>(P, MP, MQ); break;
@@ -770,9 +836,20 @@ cudaError_t launch_fdpf_g(cudaStream_t st, int T, int grid, const FdpfParams& P,
 }
 
 template <bool GEN, typename VT>
-int fdpf_blocks_g(int T) {
+int fdpf_blocks_g(int T, size_t zbytes = 0) {
   int nb = 0;
   cudaError_t ce = cudaErrorInvalidValue;
+  if (zbytes) {
+    if constexpr (!GEN) {
+      if (T == 2 && set_zs_smem<2, VT, true>(zbytes) == cudaSuccess)
+        ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &nb, fdpf_tiles_kernel<2, VT, false, true>, NTHREADS, zbytes);
+      else if (T == 4 && set_zs_smem<4, VT, true>(zbytes) == cudaSuccess)
+        ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &nb, fdpf_tiles_kernel<4, VT, false, true>, NTHREADS, zbytes);
+    }
+    return ce == cudaSuccess ? nb : 0;
+  }
   switch (T) {
     case 2: ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fdpf_tiles_kernel<2, VT, GEN>, NTHREADS, 0); break;
     case 4: ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fdpf_tiles_kernel<4, VT, GEN>, NTHREADS, 0); break;

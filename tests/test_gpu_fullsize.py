@@ -12,6 +12,13 @@ from gpu_common import (check_every_outage, grid, oracle_base, oracle_n1, sample
 
 pytestmark = pytest.mark.gpu
 
+# The oracle evaluates eqs. (1)-(3) in polar form, the kernel in rectangular
+# form: two FP64 evaluations of one state differ by rounding, about 1e-16
+# times the sum of the magnitudes of a bus's terms (|Y_ii| |V|^2, below 1e3
+# here), so a state the kernel found at the tolerance may read up to ~1e-13
+# above it in the oracle.
+EVAL_SLACK = 1e-11
+
 
 def test_grid10k_every_outage_against_oracle(tmp_path):
     """Every one of the 13,500 outages of grid10k (Sec. IV.A), screened in one
@@ -44,7 +51,7 @@ def test_grid10k_every_outage_against_oracle(tmp_path):
     assert ref["label_ok"].all(), np.flatnonzero(~ref["label_ok"])[:20]
     conv = np.isin(st, (gp.SCEN_OK, gp.SCEN_ISLAND_NO_GEN))
     assert conv.sum() >= 0.99 * g.n_branch
-    assert np.nanmax(ref["err"][conv]) <= 1e-4 * (1 + 1e-9), np.nanmax(ref["err"][conv])
+    assert np.nanmax(ref["err"][conv]) <= 1e-4 + EVAL_SLACK, np.nanmax(ref["err"][conv])
     # islanding outages are part of the run
     islanding = (res["label"] != 0).any(axis=1)
     assert islanding.sum() > 500

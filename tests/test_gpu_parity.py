@@ -244,7 +244,9 @@ def test_n1_grid2k_every_outage(tmp_path):
     assert ref["label_ok"].all()
     conv = np.isin(res["status"], (gp.SCEN_OK, gp.SCEN_ISLAND_NO_GEN))
     assert conv.sum() > 0.9 * outages.size
-    assert np.nanmax(ref["err"][conv]) <= MISMATCH_TOL * (1 + 1e-9)
+    # (the oracle's polar and the kernel's rectangular FP64 evaluations of a
+    # state differ by rounding, ~1e-13 here)
+    assert np.nanmax(ref["err"][conv]) <= MISMATCH_TOL + 1e-11
     clear = conv & (ref["ties"] == 0)
     np.testing.assert_array_equal(res["n_overload"][clear], ref["n_overload"][clear])
     assert (res["n_overload"] > 0).sum() > 20
