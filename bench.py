@@ -133,15 +133,22 @@ def bench_grid(args):
     branches made transformers (drawn after the rest: the grid is otherwise
     the same)."""
     from gridgen import CONFIGS, config_grid, make_grid
-    if args.xfmr_frac <= 0:
+    lam = getattr(args, "load_scale", 0.0) or 0.0
+    if args.xfmr_frac <= 0 and lam <= 0:
         return config_grid(args.config)
-    g = make_grid(gen_share=1.0, xfmr_frac=args.xfmr_frac, **CONFIGS[args.config])
+    kw = dict(CONFIGS[args.config])
+    if lam > 0:
+        kw["load_scale"] = lam
+    g = make_grid(gen_share=1.0, xfmr_frac=args.xfmr_frac, **kw)
     g.meta["config"] = args.config
     return g
 
 
 def xfmr_note(args):
-    return f", {100 * args.xfmr_frac:g} % transformers" if args.xfmr_frac > 0 else ""
+    note = f", {100 * args.xfmr_frac:g} % transformers" if args.xfmr_frac > 0 else ""
+    if getattr(args, "load_scale", 0.0) > 0:
+        note += f", loads scaled by {args.load_scale:g}"
+    return note
 
 
 def run_gpcg(args):
@@ -300,7 +307,7 @@ def run_gpcg(args):
     peak, peak_kind = load_peaks()
     achieved = algo / (fd_ms / 1e3) / 1e9
     default_workload = (args.config == "grid10k" and args.precision == "fp32" and
-                        args.xfmr_frac == 0 and args.chunk <= 0 and
+                        args.xfmr_frac == 0 and args.chunk <= 0 and args.load_scale <= 0 and
                         args.precond == "exact" and args.n_outages <= 0)
     traffic = (KERNEL_TRAFFIC["bytes"] if default_workload and
                kernel_digest() == KERNEL_TRAFFIC["sha256"] else None)
@@ -724,6 +731,8 @@ def main():
                     help="skip the end-to-end run that returns every output")
     ap.add_argument("--plain-sample", type=int, default=64)
     ap.add_argument("--ref-sample", type=int, default=256)
+    ap.add_argument("--load-scale", type=float, default=0.0,
+                    help="loading factor lambda of the grid's loads (0: the workload's own)")
     ap.add_argument("--xfmr-frac", type=float, default=0.0,
                     help="make this fraction of the branches transformers (turns ratio "
                          "U[0.95, 1.05] at the from end); 0 = the plain workload")

@@ -224,6 +224,10 @@ struct gpcg_ctx {
   size_t adj_acc_bytes = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   bool timed = false;
+  // the plain FP64 path's work buffers (allocated on first use)
+  PlainBuffers plainb;
+  int plain_grid_size = 0;
+  std::vector<void*> plain_owned;
   // the screen's launch sequence, captured once per argument set and replayed
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -516,6 +520,7 @@ static gpcg_status build_matrices(gpcg_ctx* c) {
 
 static void destroy(gpcg_ctx* c) {
   if (!c) return;
+  free_list(c->plain_owned);
   free_list(c->adj_owned);
   if (c->adj_acc) cudaFree(c->adj_acc);
   free_list(c->mat_owned);
@@ -798,7 +803,7 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
   AL(c->r0Q, n);
   for (auto& e : c->ev)
     if ((ce = cudaEventCreate(&e)) != cudaSuccess) return fail_cuda(ce, "event");
-  AL(c->phase, 8 + 2);
+  AL(c->phase, 8 + 2 + 4);
   c->phase_cap = 1;
   if ((ce = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return fail_cuda(ce, "stream");
@@ -1046,6 +1051,25 @@ extern "C" gpcg_status gpcg_base_solve(gpcg_ctx* c, double* theta, double* vm, d
   return GPCG_OK;
 }
 
+// Work buffers of the plain path for this context's grid.
+static gpcg_status ensure_plain(gpcg_ctx* c) {
+  if (c->plain_grid_size) return GPCG_OK;
+  const int grid = plain_grid(c->num_sms);
+  if (grid <= 0) return fail(GPCG_ERR_CUDA, "plain path: no cooperative launch configuration");
+  PlainBuffers& B = c->plainb;
+  auto& own = c->plain_owned;
+  const size_t rows = (size_t)std::max(c->MP.plan.n, c->MQ.plan.n) + 1;
+  CUDA_TRY(dalloc(own, &B.part, (size_t)2 * 4 * grid));
+  CUDA_TRY(dalloc(own, &B.bar, 2));
+  CUDA_TRY(dalloc(own, &B.err, 1));
+  for (double** v : {&B.x, &B.r, &B.p, &B.q, &B.z, &B.t}) CUDA_TRY(dalloc(own, v, rows));
+  CUDA_TRY(dalloc(own, &B.th, (size_t)c->n));
+  CUDA_TRY(dalloc(own, &B.V, (size_t)c->n));
+  CUDA_TRY(dalloc(own, &B.ef, (size_t)2 * c->n));
+  c->plain_grid_size = grid;
+  return GPCG_OK;
+}
+
 template <typename X>
 struct OutBuf {
   X* dev = nullptr;
@@ -1140,7 +1164,7 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
     cudaFree(c->phase);
     c->phase = nullptr;
     c->phase_cap = 0;
-    CUDA_TRY(cudaMalloc(&c->phase, (8 + 2 * S) * sizeof(unsigned long long)));
+    CUDA_TRY(cudaMalloc(&c->phase, (8 + 2 * S + 4) * sizeof(unsigned long long)));
     c->phase_cap = S;
   }
   FdpfParams P = base_params(c);
@@ -1228,10 +1252,31 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
     P.n_tiles = n_tiles;
     P.order = c->d_order;
   }
-  if (c->phase_on) CUDA_TRY(cudaMemsetAsync(c->phase, 0, (8 + 2 * S) * sizeof(unsigned long long), st));
-  if (plain) {
+  if (c->phase_on) CUDA_TRY(cudaMemsetAsync(c->phase, 0, (8 + 2 * S + 4) * sizeof(unsigned long long), st));
+  if (plain && !ext) {
+    // one scenario at a time, each spread over the whole GPU (cooperative
+    // launches with grid-wide barriers): no batching across scenarios
     CUDA_TRY(enqueue_islands(st));
-    // one scenario at a time: no batching across scenarios
+    rs = ensure_plain(c);
+    if (rs != GPCG_OK) { cleanup(); return rs; }
+    CUDA_TRY(cudaMemsetAsync(c->plainb.bar, 0, 2 * sizeof(unsigned int), st));
+    CUDA_TRY(cudaMemsetAsync(c->plainb.err, 0, sizeof(int), st));
+    P.S = (int)S;
+    P.phase_cycles = nullptr;
+    const DevMatT<double> MPd = c->MP.view<double>(), MQd = c->MQ.view<double>();
+    for (size_t s = 0; s < S; ++s)
+      CUDA_TRY(launch_plain(st, c->plain_grid_size, P, MPd, MQd, c->plainb, (int)s));
+    int32_t herr = 0;
+    CUDA_TRY(cudaMemcpyAsync(&herr, c->plainb.err, sizeof herr, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (herr) {
+      cleanup();
+      return fail(GPCG_ERR_TIMEOUT, "plain path: a grid-wide barrier wait gave up");
+    }
+  } else if (plain) {
+    CUDA_TRY(enqueue_islands(st));
+    // one scenario at a time: no batching across scenarios (the kernel with
+    // extension rows, one CTA per scenario)
     for (size_t s = 0; s < S && rs == GPCG_OK; ++s) {
       FdpfParams Q = P;
       Q.S = 1;
@@ -1312,6 +1357,12 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
     std::fprintf(stderr, "gpcg phase cycles (sum over CTAs):");
     for (int k = 0; k < 8; ++k) std::fprintf(stderr, " %s=%.1f%%", names[k], 100.0 * h[k] / tot);
     std::fprintf(stderr, " total=%.3e\n", tot);
+    if (!plain) {
+      unsigned long long sub[3];
+      CUDA_TRY(cudaMemcpy(sub, c->phase + 8 + 2 * S, sizeof sub, cudaMemcpyDeviceToHost));
+      std::fprintf(stderr, "gpcg inner-solve cycles: spmv=%.1f%% fwd=%.1f%% bwd=%.1f%% of all\n",
+                   100.0 * sub[0] / tot, 100.0 * sub[1] / tot, 100.0 * sub[2] / tot);
+    }
   }
   if (c->phase_on && !plain) {
     // per-scenario start and finish times: completion profile and the
@@ -1515,6 +1566,7 @@ extern "C" gpcg_status gpcg_n1_adjoint(gpcg_ctx* c, const int32_t* outages, int3
                         c->d_lo, c->d_cnt, c->d_coef, c->d_nogen, nullptr);
     if (ce != cudaSuccess) { cleanup(); return fail(GPCG_ERR_CUDA, "islands: %s", cudaGetErrorString(ce)); }
     FdpfParams P = base_params(c);
+    P.phase_cycles = nullptr;  // the diagnostics cover the N-1 screens
     P.inner_rtol = 1e-12;  // gradients want converged solves (2-3 iterations with the exact factor)
     P.max_inner = std::max(c->opt.max_inner, 2000);
     P.S = (int)S;
@@ -1635,6 +1687,7 @@ extern "C" gpcg_status gpcg_n1_dc_screen(gpcg_ctx* c, const int32_t* outages, in
   const int per_sm = std::max(1, f32 ? dc_max_blocks_per_sm<float>() : dc_max_blocks_per_sm<double>());
   const int slots = std::max(1, std::min(n_tiles, c->num_sms * per_sm));
   FdpfParams P = base_params(c);
+  P.phase_cycles = nullptr;  // the diagnostics cover the AC screens
   // converged solves (2-3 iterations with the exact factor); FP32 solves are
   // followed by one refinement step in the kernel
   P.inner_rtol = std::min(c->opt.inner_rtol, f32 ? 1e-6 : 1e-12);

@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     adjoint_tiles_kernel(FdpfParams P, AdjParams A, DevMatT<VT> M) {
   static_assert(T == 2 && Geo<T>::LP == 2, "one thread per row, two lanes: the slot sums need no atomics");
   __shared__ LaneState<T> L;
+  __shared__ double red[NTHREADS * 2];  // lane_reduce and the loss sum
   const Geo<T> g;
   const int tid = threadIdx.x;
   const DevGrid& G = P.G;
@@ -155,8 +156,8 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
         if (!in_island(pr, lo1, cnt1)) { wl1 += pg * b; dn1 += pg; }
       }
     }
-    const Pair<double> WL = lane_reduce<T, false>(L, wl0, wl1);
-    const Pair<double> DN = lane_reduce<T, false>(L, dn0, dn1);
+    const Pair<double> WL = lane_reduce<T, false>(red, wl0, wl1);
+    const Pair<double> DN = lane_reduce<T, false>(red, dn0, dn1);
     const double W0 = (v0 && cnt0 > 0 && !L.nogen[l0] && DN.a > 0.0) ? WL.a / DN.a : 0.0;
     const double W1 = (v1 && cnt1 > 0 && !L.nogen[l1] && DN.b > 0.0) ? WL.b / DN.b : 0.0;
     for (int i = g.rs; i < G.n; i += Geo<T>::RPS) {
@@ -186,11 +187,11 @@ __global__ void __launch_bounds__(NTHREADS, FDPF_MIN_BLOCKS)
     __syncthreads();
   }
   // the CTA's loss: sum over threads in a fixed order
-  L.red[tid] = loss_acc;
+  red[tid] = loss_acc;
   __syncthreads();
   if (tid == 0) {
     double s = 0.0;
-    for (int k = 0; k < NTHREADS; ++k) s += L.red[k];
+    for (int k = 0; k < NTHREADS; ++k) s += red[k];
     A.loss[blockIdx.x] = s;
   }
 }

@@ -67,6 +67,20 @@ cudaError_t launch_base_trig(cudaStream_t st, int n, const double* th, double* c
 cudaError_t launch_base_residual(cudaStream_t st, const DevGrid& G, const double* V0,
                                  const double* c0, const double* s0, double* r0P, double* r0Q);
 
+// plain.cu: the unbatched FP64 path, one scenario per cooperative launch
+// over the whole GPU.  Work buffers, device memory owned by the caller.
+struct PlainBuffers {
+  double* part = nullptr;          // [2 * 4 * grid]
+  unsigned int* bar = nullptr;     // [2], zero before the first launch
+  int* err = nullptr;              // [1], zero before the first launch
+  double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *t = nullptr;
+  double *th = nullptr, *V = nullptr, *ef = nullptr;  // [n], [n], [2 n]
+};
+cudaError_t launch_plain(cudaStream_t st, int grid, const FdpfParams& P,
+                         const DevMatT<double>& MP, const DevMatT<double>& MQ,
+                         const PlainBuffers& B, int s);
+int plain_grid(int num_sms);  // CTAs of the cooperative launch (0: not available)
+
 // adjoint.cu
 struct AdjParamsView {
   const double* P;   // [n] injections, internal bus order

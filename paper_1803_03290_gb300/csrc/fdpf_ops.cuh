@@ -228,7 +228,6 @@ struct LaneState {
   unsigned long long tphase[8];
   int done[T], fresh[T];
   double xalpha[T];          // a deferred last step x += alpha p of the inner solve
-  double red[NTHREADS * 2];  // lane_reduce (two lanes per thread)
   // one small buffer per reduction site (see lane_sum): [site][warp][lane]
   double red2[NRED_SITES * (NTHREADS / 32) * T];
   int flag;
@@ -236,14 +235,15 @@ struct LaneState {
 };
 
 // Sum (or max) over the row slots of each lane's partial values, for
-// layouts with two lanes per thread.
+// layouts with two lanes per thread, through `red` (NTHREADS * 2 doubles of
+// shared memory that the calling kernel provides).
 template <int T, bool MAX>
-__device__ __forceinline__ Pair<double> lane_reduce(LaneState<T>& L, double v0, double v1) {
+__device__ __forceinline__ Pair<double> lane_reduce(double* red, double v0, double v1) {
   static_assert(Geo<T>::LP == 2, "two lanes per thread");
   const Geo<T> g;
   constexpr int RPS = Geo<T>::RPS;
-  L.red[g.rs * T + g.lane] = v0;
-  L.red[g.rs * T + g.lane + 1] = v1;
+  red[g.rs * T + g.lane] = v0;
+  red[g.rs * T + g.lane + 1] = v1;
   __syncthreads();
 #pragma unroll
   for (int st = RPS / 2; st > 0; st >>= 1) {
@@ -251,13 +251,13 @@ __device__ __forceinline__ Pair<double> lane_reduce(LaneState<T>& L, double v0, 
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int o = g.rs * T + g.lane + j;
-        const double a = L.red[o], b = L.red[o + st * T];
-        L.red[o] = MAX ? ((b > a || b != b) ? b : a) : a + b;
+        const double a = red[o], b = red[o + st * T];
+        red[o] = MAX ? ((b > a || b != b) ? b : a) : a + b;
       }
     }
     __syncthreads();
   }
-  const Pair<double> out{L.red[g.lane], L.red[g.lane + 1]};
+  const Pair<double> out{red[g.lane], red[g.lane + 1]};
   __syncthreads();
   return out;
 }
@@ -1083,12 +1083,19 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
   for (int k = 0; k < T; ++k) islands |= L.active[k] && L.cnt[k] > 0;
   const LaneState<T>* isl = islands ? &L : nullptr;
   Vec<VT, LP> bbp = vzero<VT, LP>(), rzp = vzero<VT, LP>(), al = vzero<VT, LP>();
+  const bool tim0 = P.phase_cycles != nullptr && tid == 0;
+  long long t0a = tim0 ? clock64() : 0, t0b = 0;
   if (jac) {
     jacobi_pass<T, VT, false>(M, x, r, p, q, z, al, St, bbp, rzp, X);
   } else {
     Vec<VT, LP> rzt = vzero<VT, LP>();
     bbp = fwd_pass<T, VT, false>(M, x, r, p, q, z, al, zt, rzt, X);
+    if (tim0) t0b = clock64();
     rzp = bwd_pass<T, VT>(M, r, z, rzt);
+  }
+  if (tim0 && !jac) {
+    atomicAdd(P.phase_cycles + 8 + 2 * (size_t)P.S + 1, (unsigned long long)(t0b - t0a));
+    atomicAdd(P.phase_cycles + 8 + 2 * (size_t)P.S + 2, (unsigned long long)(clock64() - t0b));
   }
   const Vec<VT, LP> bb = lane_sum<T, RS_BB>(L, bbp);
   const Vec<VT, LP> rz0 = lane_sum<T, RS_RZ0>(L, rzp);
@@ -1109,6 +1116,16 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
   }
   __syncthreads();  // publishes S and the first z
   const VT tol2 = (VT)(P.inner_rtol * P.inner_rtol);
+  // diagnostics (P.phase_cycles set): thread 0's SM cycles in the SpMV, the
+  // forward and the backward passes of this solve, added to the three slots
+  // after the per-scenario times
+  const bool tim = P.phase_cycles != nullptr && tid == 0;
+  unsigned long long tsub[3] = {0ull, 0ull, 0ull};
+  long long tmark = 0;
+#define GPCG_SUB_BEGIN() \
+  if (tim) tmark = clock64();
+#define GPCG_SUB_END(k) \
+  if (tim) tsub[k] += (unsigned long long)(clock64() - tmark);
   int par = 0;
   Vec<VT, LP> be = vzero<VT, LP>();
   for (int it = 0; it < P.max_inner; ++it) {
@@ -1118,9 +1135,11 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
     if (!any) break;
     // new direction p = mask(z) + beta p and q = B_s p in one pass
     Vec<VT, LP> rqp = vzero<VT, LP>(), qqp = vzero<VT, LP>();
+    GPCG_SUB_BEGIN();
     const Vec<VT, LP> pqp = spmv_pass<T, VT, true>(
         M, z, p, q, St, filt, be, it == 0, isl, (DEFER && Geo<T>::TPR == 1) ? r : nullptr, &rqp,
         &qqp, X);
+    GPCG_SUB_END(0);
     Vec<VT, LP> pq = pqp, rq = rqp, qq = qqp;
     if constexpr (DEFER && Geo<T>::TPR == 1) lane_sum3<T, RS_PQ, RS_RQ, RS_QQ>(L, pq, rq, qq);
     else pq = lane_sum<T, RS_PQ>(L, pqp);
@@ -1170,11 +1189,13 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
       for (int j = 0; j < LP; ++j)
         if ((bk >> j) & 1) S.brk[g.lane + j] = 1;
     Vec<VT, LP> rrp = vzero<VT, LP>(), rzn = vzero<VT, LP>();
+    GPCG_SUB_BEGIN();
     if (jac) {
       jacobi_pass<T, VT, true>(M, x, r, p, q, z, al, St, rrp, rzn, X);
     } else {
       rrp = fwd_pass<T, VT, true>(M, x, r, p, q, z, al, zt, rzn, X);  // rzn: the tail's r.z
     }
+    GPCG_SUB_END(1);
     const Vec<VT, LP> rr = lane_sum<T, RS_RR>(L, rrp);
     if (g.rs == 0) {
 #pragma unroll
@@ -1204,7 +1225,9 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
 #pragma unroll 1
     for (int k = 0; k < T; ++k) any |= !(S.pdone[k] | S.stop[k]);
     if (!any) break;
+    GPCG_SUB_BEGIN();
     if (!jac) rzn = bwd_pass<T, VT>(M, r, z, rzn);
+    GPCG_SUB_END(2);
     const Vec<VT, LP> rz = lane_sum<T, RS_RZ>(L, rzn);
 #pragma unroll
     for (int j = 0; j < LP; ++j)
@@ -1222,6 +1245,10 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
     __syncthreads();  // publishes S.rz, S.stop and z
     par ^= 1;
   }
+  if (tim)
+    for (int k = 0; k < 3; ++k) atomicAdd(P.phase_cycles + 8 + 2 * (size_t)P.S + k, tsub[k]);
+#undef GPCG_SUB_BEGIN
+#undef GPCG_SUB_END
   __syncthreads();
 }
 

@@ -163,6 +163,7 @@ def _compare(g, res, ref, outages, angle_tol):
     (gp.BATCHED_FP64, gp.PRECOND_EXACT), (gp.BATCHED_FP32, gp.PRECOND_EXACT),
     (gp.BATCHED_FP64, gp.PRECOND_IC0), (gp.BATCHED_FP32, gp.PRECOND_IC0),
     (gp.BATCHED_FP64, gp.PRECOND_JACOBI), (gp.PLAIN_FP64, gp.PRECOND_EXACT),
+    (gp.PLAIN_FP64, gp.PRECOND_IC0), (gp.PLAIN_FP64, gp.PRECOND_JACOBI),
     (gp.BATCHED_FP32_F16, gp.PRECOND_EXACT), (gp.BATCHED_FP32_F16, gp.PRECOND_IC0)])
 def test_n1_grid120_all_outages(precision, precond):
     g = grid("grid120")
@@ -202,6 +203,31 @@ def test_n1_grid120_overload_screen(precision):
     np.testing.assert_array_equal(res["n_overload"][clear], ref["n_overload"][clear])
     np.testing.assert_array_equal(bits.sum(axis=1), res["n_overload"])
     assert (ref["n_overload"][ok] > 0).sum() >= 20
+
+
+def test_plain_path_grid2k_sample():
+    """The plain FP64 path -- one scenario at a time, its rows spread over
+    every CTA of a cooperative launch with grid-wide barriers between the
+    levels of the substitutions -- on a seeded grid2k sample (islanding
+    outages included) at a 1e-10 p.u. mismatch: statuses and labels exact,
+    angles and magnitudes within 1e-6 of the oracle's."""
+    g = grid("grid2k")
+    samp = sample_outages(g, 24, seed=14)
+    c = make("grid2k", precision=gp.PLAIN_FP64, tol=1e-10, max_outer=100)
+    c.base_solve()
+    res = c.n1_screen(samp, outputs=("theta", "V", "status", "label", "iters", "flow",
+                                     "max_loading", "n_overload"))
+    c.close()
+    ref = oracle_n1("grid2k", samp, tol=1e-10)
+    np.testing.assert_array_equal(res["status"], ref["status"])
+    np.testing.assert_array_equal(res["label"], ref["label"])
+    ok = np.isin(ref["status"], [0, 3])
+    assert ok.sum() >= 0.9 * samp.size and (res["label"] != 0).any()
+    assert np.abs(res["theta"][ok] - ref["theta"][ok]).max() <= ANGLE_TOL
+    assert np.abs(res["V"][ok] - ref["V"][ok]).max() <= ANGLE_TOL
+    assert np.abs(res["flow"][ok] - ref["flow"][ok]).max() <= 10 * ANGLE_TOL
+    np.testing.assert_array_equal(res["n_overload"][ok], ref["n_overload"][ok])
+    assert (res["iters"][ok, 1] >= 1).all()
 
 
 @pytest.mark.parametrize("tile", [8, 16, 32])
