@@ -757,10 +757,15 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
       for (int k = c->bg.adj.ptr[b]; k < c->bg.adj.ptr[b + 1]; ++k)
         rows[b].push_back({c->bg.adj.idx[k], c->bg.adj_branch[k]});
     EllHost E = ell_from_rows(rows, KG, 0);
-    std::vector<int32_t> pad_nbr(E.col), brl(E.src);
+    // slot-major: slot k of bus b at k * n + b
+    std::vector<int32_t> pad_nbr(E.col.size()), brl(E.src.size());
     for (int b = 0; b < n; ++b)
-      for (int k = 0; k < KG; ++k)
-        if (brl[(size_t)b * KG + k] < 0) { pad_nbr[(size_t)b * KG + k] = b; brl[(size_t)b * KG + k] = -2; }
+      for (int k = 0; k < KG; ++k) {
+        const size_t o = (size_t)b * KG + k, t = (size_t)k * n + b;
+        const bool pad = E.src[o] < 0;
+        pad_nbr[t] = pad ? b : E.col[o];
+        brl[t] = pad ? -2 : E.src[o];
+      }
     UP(G.adj_nbr, pad_nbr.data(), pad_nbr.size());
     UP(G.adj_brl, brl.data(), brl.size());
     UP(G.adj_optr, E.optr.data(), E.optr.size());

@@ -273,6 +273,13 @@ std::vector<int32_t> rcm_order(int n, const BusGraph& g) {
     bfs(start, out, seen);
     std::reverse(out.begin() + before, out.end());
   }
+  // within each window of 128 consecutive positions, buses of higher degree
+  // first (stable): kernels that take one bus per thread in this order read
+  // consecutive buses and run neighbour loops of nearly equal length in a
+  // warp; the permutation stays inside the window, so neighbours stay close
+  for (size_t w0 = 0; w0 < out.size(); w0 += 128)
+    std::stable_sort(out.begin() + w0, out.begin() + std::min(out.size(), w0 + 128),
+                     [&](int a, int b) { return deg[a] > deg[b]; });
   return out;
 }
 

@@ -41,7 +41,9 @@ struct DevGrid {
   double *Gii = nullptr, *Bii = nullptr;     // bus admittance diagonal
   int32_t *pre = nullptr, *sub = nullptr;    // depth-first preorder, subtree size
   int32_t* user_of_bus = nullptr;            // internal bus index -> caller's index
-  // padded adjacency for the mismatch: neighbour, branch, -g, -b_y per slot
+  // padded adjacency for the mismatch: neighbour, branch, -g, -b_y per slot,
+  // slot-major (slot a of bus i at a * n + i: a warp taking consecutive buses
+  // reads consecutive entries)
   int32_t *adj_nbr = nullptr, *adj_brl = nullptr, *adj_deg = nullptr;  // deg = used slots
   double *adj_g = nullptr, *adj_b = nullptr;
   int32_t *adj_optr = nullptr, *adj_onbr = nullptr, *adj_obr = nullptr;

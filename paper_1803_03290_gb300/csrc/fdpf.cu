@@ -82,8 +82,8 @@ __global__ void base_residual_kernel(DevGrid G, const double* __restrict__ V0,
   double re = fma(G.Gii[i], ei, -G.Bii[i] * fi), im = fma(G.Gii[i], fi, G.Bii[i] * ei);
   const int deg = G.adj_deg[i];
   for (int a = 0; a < deg; ++a) {
-    const int j = G.adj_nbr[(size_t)i * KG + a];
-    const double gv = G.adj_g[(size_t)i * KG + a], bv = G.adj_b[(size_t)i * KG + a];
+    const int j = G.adj_nbr[(size_t)a * G.n + i];
+    const double gv = G.adj_g[(size_t)a * G.n + i], bv = G.adj_b[(size_t)a * G.n + i];
     const double ej = V0[j] * c0[j], fj = V0[j] * s0[j];
     re = fma(-gv, ej, fma(bv, fj, re));
     im = fma(-gv, fj, fma(-bv, ej, im));

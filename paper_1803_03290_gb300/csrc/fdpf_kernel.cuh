@@ -42,6 +42,12 @@ __device__ __forceinline__ size_t ef_at(int bus, int lane) {
   return ((size_t)bus * T + lane) * 2;
 }
 
+// The neighbour slots of bus i (slot-major adjacency).
+__device__ __forceinline__ void ld_nbrs(const DevGrid& G, int i, int (&nb)[KG]) {
+#pragma unroll
+  for (int a = 0; a < KG; ++a) nb[a] = __ldg(G.adj_nbr + (size_t)a * G.n + i);
+}
+
 // I_i = sum_j Y_ij V_j at bus i for lane ln, the lane's outaged branch left
 // out (off the diagonal and its share of it), summed like mismatch_pass.
 template <int T>
@@ -51,9 +57,9 @@ __device__ __forceinline__ double2 bus_current(const DevGrid& G, const LaneState
   const int br = L.l[ln];
   const int deg = __ldg(G.adj_deg + i);
   for (int a = 0; a < deg; ++a) {
-    if (__ldg(G.adj_brl + (size_t)i * KG + a) == br) continue;
-    const int j = __ldg(G.adj_nbr + (size_t)i * KG + a);
-    const double gv = __ldg(G.adj_g + (size_t)i * KG + a), bv = __ldg(G.adj_b + (size_t)i * KG + a);
+    if (__ldg(G.adj_brl + (size_t)a * G.n + i) == br) continue;
+    const int j = __ldg(G.adj_nbr + (size_t)a * G.n + i);
+    const double gv = __ldg(G.adj_g + (size_t)a * G.n + i), bv = __ldg(G.adj_b + (size_t)a * G.n + i);
     const double2 u = *reinterpret_cast<const double2*>(EF + ef_at<T>(j, ln));
     re = fma(-gv, u.x, fma(bv, u.y, re));
     im = fma(-gv, u.y, fma(-bv, u.x, im));
@@ -103,7 +109,7 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
   int kn = 0, nbn[KG];
   if (g.rs < nrows) {
     kn = __ldg(order + g.rs);
-    ld_cols<KG>(G.adj_nbr + (size_t)(WITH_P ? kn : __ldg(MQ.bus_of_row + kn)) * KG, nbn);
+    ld_nbrs(G, WITH_P ? kn : __ldg(MQ.bus_of_row + kn), nbn);
   }
   for (int kk = g.rs; kk < nrows; kk += Geo<T>::RPS) {
     const int k = kn;
@@ -112,7 +118,7 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
     for (int a = 0; a < KG; ++a) nb[a] = nbn[a];
     if (kk + Geo<T>::RPS < nrows) {
       kn = __ldg(order + kk + Geo<T>::RPS);
-      ld_cols<KG>(G.adj_nbr + (size_t)(WITH_P ? kn : __ldg(MQ.bus_of_row + kn)) * KG, nbn);
+      ld_nbrs(G, WITH_P ? kn : __ldg(MQ.bus_of_row + kn), nbn);
     }
     const int i = WITH_P ? k : __ldg(MQ.bus_of_row + k);
     const int pr = __ldg(G.pre + i);
@@ -147,9 +153,9 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
             const double2* q2 = reinterpret_cast<const double2*>(EF + ef_at<T>(nb[a0 + a], l0));
             u0[a] = q2[0];
             u1[a] = q2[1];
-            gv[a] = __ldg(G.adj_g + (size_t)i * KG + a0 + a);
-            bv[a] = __ldg(G.adj_b + (size_t)i * KG + a0 + a);
-            bb[a] = __ldg(G.adj_brl + (size_t)i * KG + a0 + a);
+            gv[a] = __ldg(G.adj_g + (size_t)(a0 + a) * G.n + i);
+            bv[a] = __ldg(G.adj_b + (size_t)(a0 + a) * G.n + i);
+            bb[a] = __ldg(G.adj_brl + (size_t)(a0 + a) * G.n + i);
           }
 #pragma unroll
         for (int a = 0; a < MIS_GROUP; ++a)

@@ -165,9 +165,9 @@ __device__ double2 current_at(const DevGrid& G, const Scen& c, const double2* __
   double re = 0.0, im = 0.0;
   const int deg = __ldg(G.adj_deg + i);
   for (int a = 0; a < deg; ++a) {
-    if (__ldg(G.adj_brl + (size_t)i * KG + a) == c.l) continue;
-    const int j = __ldg(G.adj_nbr + (size_t)i * KG + a);
-    const double gv = __ldg(G.adj_g + (size_t)i * KG + a), bv = __ldg(G.adj_b + (size_t)i * KG + a);
+    if (__ldg(G.adj_brl + (size_t)a * G.n + i) == c.l) continue;
+    const int j = __ldg(G.adj_nbr + (size_t)a * G.n + i);
+    const double gv = __ldg(G.adj_g + (size_t)a * G.n + i), bv = __ldg(G.adj_b + (size_t)a * G.n + i);
     const double2 u = EF[j];
     re = fma(-gv, u.x, fma(bv, u.y, re));
     im = fma(-gv, u.y, fma(-bv, u.x, im));
