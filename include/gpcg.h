@@ -226,7 +226,11 @@ GPCG_API gpcg_status gpcg_base_solve(gpcg_ctx *ctx, double *theta, double *vm,
  * fails to converge never fails the call: see status[].
  *
  * mem = 0: every pointer is host memory; the call returns with the results
- * written.  mem = 1: every pointer is device memory; the outage list is read
+ * written.  Outputs in page-locked host memory (cudaHostAlloc,
+ * cudaHostRegister) are written by the kernels in place, through their
+ * device-visible addresses, while the solve runs; other host outputs go
+ * through device buffers copied back at the end.  mem = 1: every pointer
+ * is device memory; the outage list is read
  * back to validate it and order the scenarios (a synchronisation of
  * `stream`), and the call returns once the solve is enqueued on `stream`.
  * In device mode the islanding and solve launches are captured once as a

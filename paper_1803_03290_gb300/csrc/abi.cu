@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/gpcg.h"
@@ -1133,12 +1134,22 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
   CUDA_TRY(cudaMemcpyAsync(c->d_order, order.data(), S * 4, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors above go out of scope
 
-  // outputs: device pointers directly, or device staging for host pointers
+  // outputs: device pointers directly; host pointers to page-locked memory
+  // through their device-visible addresses (the kernels store into host
+  // memory over the host link as scenarios retire, overlapped with the
+  // solve); other host pointers through device staging, copied back after
   std::vector<void*> staging;
   auto stage = [&](auto* user, size_t count, auto** dev) -> cudaError_t {
     *dev = nullptr;
     if (!user) return cudaSuccess;
     if (mem == GPCG_MEM_DEVICE) { *dev = user; return cudaSuccess; }
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, user) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer) {
+      *dev = static_cast<std::remove_reference_t<decltype(*dev)>>(at.devicePointer);
+      return cudaSuccess;
+    }
+    cudaGetLastError();  // an unregistered pointer is not an error here
     cudaError_t ce = cudaMallocAsync((void**)dev, count * sizeof(**dev), st);
     if (ce == cudaSuccess) staging.push_back((void*)*dev);
     return ce;
@@ -1405,6 +1416,8 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
   if (mem == GPCG_MEM_HOST) {
     auto back = [&](auto* user, auto* dev, size_t count) -> cudaError_t {
       if (!user) return cudaSuccess;
+      if (std::find(staging.begin(), staging.end(), (void*)dev) == staging.end())
+        return cudaSuccess;  // written in place (page-locked host memory)
       return cudaMemcpyAsync(user, dev, count * sizeof(*user), cudaMemcpyDeviceToHost, st);
     };
     if (ce == cudaSuccess) ce = back(theta, d_theta, S * c->n);
