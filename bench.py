@@ -102,6 +102,27 @@ def algorithmic_bytes(info, iters, w, n_bus, n_branch):
     return vec + mis + flows + mats
 
 
+def fp64_operations(g, iters):
+    """FP64 operations (an FMA counts once) the screen's FP64 parts take per
+    launch, from the kernel's arithmetic: per full P mismatch 4 per adjacency
+    entry and 7 per non-slack bus (+2 per PQ bus for dQ), per Q mismatch 4
+    per adjacency entry and 6 per PQ bus, per angle update 12 per non-slack
+    bus (the exact rotation of e + jf), per |V| update 3 per PQ bus, the first
+    P mismatch 1 per non-slack bus (the base case's is stored), and 16 per
+    branch for the flows and loading; k outer iterations take k full P
+    mismatches, k Q mismatches and k updates of each kind."""
+    bt = np.asarray(g.bus_type)
+    deg = np.bincount(np.r_[g.f, g.t], minlength=g.n_bus)
+    nP, nQ = int((bt != 2).sum()), int((bt == 0).sum())
+    AP, AQ = int(deg[bt != 2].sum()), int(deg[bt == 0].sum())
+    per_outer = (4 * AP + 7 * nP + 2 * nQ) + (4 * AQ + 6 * nQ) + 12 * nP + 3 * nQ
+    k = iters[:, 0].astype(np.float64)
+    return float((k * per_outer).sum() + iters.shape[0] * (nP + 16 * g.n_branch))
+
+
+FP64_PEAK_GOPS = 625.0  # nominal 1.25 TFLOP/s of GB300 with an FMA as 2 FLOP
+
+
 # DRAM bytes per launch of the N-1 kernel on the default grid10k workload
 # (dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture of the
 # timed screens, taken by hand and recorded here), valid only for the kernel
@@ -318,6 +339,13 @@ def run_gpcg(args):
             "kernel": "fdpf_tiles_kernel", "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": int(algo), "kernel_ms": round(fd_ms, 3),
             "islands_kernel_ms": round(statistics.mean(k[0] for k in kern_ms), 3)}
+    if w == 4:  # FP32 inner solves: the FP64 work is the mismatch, updates and flows
+        f64 = fp64_operations(g, iters)
+        roof["fp64_pipe"] = {"ops_per_launch": int(f64),
+                             "achieved_gops": round(f64 / (fd_ms / 1e3) / 1e9, 1),
+                             "peak_gops": FP64_PEAK_GOPS,
+                             "frac": round(f64 / (fd_ms / 1e3) / 1e9 / FP64_PEAK_GOPS, 4),
+                             "peak_source": "nominal (1.25 TFLOP/s, FMA = 2 FLOP)"}
     n_chunks = (S + K - 1) // K
     if n_chunks > 1:  # bytes and kernel time summed over the step's launches
         roof["launches_per_step"] = n_chunks

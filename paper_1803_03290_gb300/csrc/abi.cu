@@ -191,6 +191,7 @@ struct gpcg_ctx {
   int n_adj_slots = 0, n_adj_over = 0;
   std::vector<int32_t> deg;
   int32_t *mis_order = nullptr, *misq_order = nullptr;
+  int32_t* d_bus_of_user = nullptr;  // caller's bus -> internal bus
   unsigned long long* phase = nullptr;  // diagnostics: [8 + 2 phase_cap]
   size_t phase_cap = 0;
   bool phase_on = false;
@@ -672,6 +673,7 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
   UP(G.f, f_i.data(), m);
   UP(G.t, t_i.data(), m);
   UP(G.user_of_bus, U.data(), n);
+  UP(c->d_bus_of_user, I.data(), n);
   {
     std::vector<int32_t> pre_u(n);
     for (int b = 0; b < n; ++b) pre_u[b] = c->pre[I[b]];
@@ -1191,7 +1193,7 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
   P.c0 = c->c0;
   P.s0 = c->s0;
   P.out_theta = d_theta; P.out_vm = d_vm; P.out_flow = d_flow; P.out_maxload = d_ml;
-  P.out_bus_map = c->G.user_of_bus;
+  P.out_bus_map = c->d_bus_of_user;
   P.out_iters = d_iters; P.out_status = d_stat;
   P.out_nover = d_nov; P.out_ovmask = d_ovm;
   const bool plain = c->opt.precision == GPCG_PLAIN_FP64;
@@ -1894,6 +1896,7 @@ bool ctx_view(const gpcg_ctx* c, CtxView* v) {
   v->c0 = c->c0;
   v->s0 = c->s0;
   v->mis_order = c->mis_order;
+  v->bus_of_user = c->d_bus_of_user;
   v->misq_order = c->misq_order;
   v->opt = c->opt;
   v->num_sms = c->num_sms;

@@ -12,6 +12,7 @@ struct CtxView {
   DevMatT<double> MPd, MQd;
   const double *th0 = nullptr, *V0 = nullptr, *c0 = nullptr, *s0 = nullptr;
   const int32_t *mis_order = nullptr, *misq_order = nullptr;
+  const int32_t* bus_of_user = nullptr;  // caller's bus -> internal bus
   gpcg_options opt{};
   int num_sms = 0, n = 0, m = 0, slack = -1, rows = 0, tile = 0, slack_user = -1;
   const int32_t *u_f = nullptr, *u_t = nullptr, *u_pre = nullptr;  // caller numbering

@@ -31,7 +31,9 @@ struct FdpfParams {
   double *wth = nullptr, *wV = nullptr, *we = nullptr, *wf = nullptr;
   size_t sstride = 0;  // elements per slot of one state array
   double *out_theta = nullptr, *out_vm = nullptr, *out_flow = nullptr, *out_maxload = nullptr;
-  const int32_t* out_bus_map = nullptr;  // internal bus -> output column (null: identity)
+  // output column -> internal bus (null: identity): the outputs are written
+  // column by column, so neighbouring threads store neighbouring columns
+  const int32_t* out_bus_map = nullptr;
   int32_t *out_iters = nullptr, *out_status = nullptr;
   // overload screen: per scenario the number of branches loaded above their
   // rating, and those branches as a bit mask of mask_words words

@@ -503,8 +503,8 @@ __device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& 
 #pragma unroll
   for (int j = 0; j < LP; ++j) dn |= (L.done[g.lane + j] != 0) << j;
   if ((P.out_theta || P.out_vm) && dn) {
-    for (int i = g.rs; i < G.n; i += Geo<T>::RPS) {
-      const int iu = P.out_bus_map ? __ldg(P.out_bus_map + i) : i;
+    for (int iu = g.rs; iu < G.n; iu += Geo<T>::RPS) {
+      const int i = P.out_bus_map ? __ldg(P.out_bus_map + iu) : iu;
 #pragma unroll
       for (int j = 0; j < LP; ++j) {
         if (!((dn >> j) & 1)) continue;

@@ -147,7 +147,7 @@ extern "C" gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx* ctx, const int32_t* outa
   P.out_theta = theta; P.out_vm = vm; P.out_flow = flow; P.out_maxload = max_loading;
   P.out_iters = iters; P.out_status = status;
   P.out_nover = n_overload; P.out_ovmask = overload;
-  P.out_bus_map = c.G.user_of_bus;
+  P.out_bus_map = c.bus_of_user;
   P.S = (int)S;
   P.n_tiles = n_tiles;
   P.tile_counter = counter;

@@ -446,8 +446,8 @@ __global__ void __launch_bounds__(PT) plain_fdpf_kernel(FdpfParams P, DevMatT<do
   }
   // outputs (Sec. I): state, branch flows, loading and overloads
   const int nw = (G.m + 31) >> 5;
-  for (int i = gt; i < n; i += NT) {
-    const int iu = P.out_bus_map ? P.out_bus_map[i] : i;
+  for (int iu = gt; iu < n; iu += NT) {
+    const int i = P.out_bus_map ? P.out_bus_map[iu] : iu;
     if (P.out_theta) P.out_theta[(size_t)s * n + iu] = W.th[i];
     if (P.out_vm) P.out_vm[(size_t)s * n + iu] = W.V[i];
   }
