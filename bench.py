@@ -187,7 +187,8 @@ def run_gpcg(args):
     prec = {"fp32": gp.BATCHED_FP32, "fp64": gp.BATCHED_FP64,
             "fp16f": gp.BATCHED_FP32_F16}[args.precision]
     pc = {"exact": gp.PRECOND_EXACT, "ic0": gp.PRECOND_IC0, "jacobi": gp.PRECOND_JACOBI}[args.precond]
-    c = gp.GPCG(g, precision=prec, precond=pc, tol=1e-4, tile=args.tile)
+    knobs = dict(tile=args.tile, ctas_per_sm=args.ctas_per_sm, tail_rows=args.tail_rows)
+    c = gp.GPCG(g, precision=prec, precond=pc, tol=1e-4, **knobs)
     c.base_solve()
     info = c.info()
     S = g.n_branch if args.n_outages <= 0 else min(args.n_outages, g.n_branch)
@@ -214,7 +215,7 @@ def run_gpcg(args):
     NS = max(1, args.streams) if K < S else 1
     ctxs, streams, outs = [c], [stream], [out]
     for _ in range(NS - 1):
-        ci = gp.GPCG(g, precision=prec, precond=pc, tol=1e-4, tile=args.tile)
+        ci = gp.GPCG(g, precision=prec, precond=pc, tol=1e-4, **knobs)
         ci.base_solve()
         ctxs.append(ci)
         streams.append(torch.cuda.Stream(device=dev))
@@ -366,6 +367,10 @@ def run_gpcg(args):
                                    f"tol 1e-4 p.u., {args.precond} base-case preconditioner, "
                                    f"{args.precision} inner PCG, FP64 mismatch/flows",
                        "n_bus": n, "n_branch": m, "scenarios": S, "tile": info["tile"],
+                       "ctas_per_sm": info["ctas_per_sm"],
+                       "tail_rows": [info["tail_rows_p"], info["tail_rows_q"]],
+                       "knobs": {0: "options", 1: "autotuner probes",
+                                 2: "autotuner cache"}[info["tuned"]],
                        "chunk": K, "streams": NS,
                        "l2": "flushed between steps (512 MiB write)",
                        "precond": args.precond, "precision": args.precision},
@@ -748,7 +753,10 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16f"],
                     help="inner PCG: FP32, FP64, or FP32 vectors with a scaled FP16 factor")
     ap.add_argument("--precond", default="exact", choices=["exact", "ic0", "jacobi"])
-    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--tile", type=int, default=0, help="scenarios per tile (0: autotuned)")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="tiles per SM (0: autotuned)")
+    ap.add_argument("--tail-rows", type=int, default=0,
+                    help="dense-tail cap of the substitutions (0: autotuned, -1: none)")
     ap.add_argument("--n-outages", type=int, default=0, help="screen only the first K outages (0 = all)")
     ap.add_argument("--chunk", type=int, default=0,
                     help="screen the outages in calls of this many (0 = one call)")

@@ -143,10 +143,35 @@ typedef struct {
   int32_t max_inner;   /* PCG iteration cap per solve; 500 */
   int32_t precision;   /* GPCG_PLAIN_FP64 / _BATCHED_FP32 / _BATCHED_FP64 */
   int32_t precond;     /* GPCG_PRECOND_*; default GPCG_PRECOND_EXACT */
-  int32_t tile;        /* scenarios per tile: 2, 4, 8, 16 or 32; 0 = chosen by
-                          the library's autotuner on first use */
-  int32_t ctas_per_sm; /* resident tiles per SM; 0 = from the occupancy API */
+  int32_t tile;        /* scenarios per tile (the scenario chunk a CTA solves
+                          together): 2, 4, 8, 16 or 32; 0 = autotuned */
+  int32_t ctas_per_sm; /* resident tiles per SM, which sets the scenarios in
+                          flight (tile x ctas_per_sm x SMs); 0 = autotuned
+                          among the occupancy maximum and the two counts below
+                          it */
+  int32_t tail_rows;   /* level-tile shape of the substitutions: the factor's
+                          last levels, together at most this many rows, are
+                          solved with the dense inverse of their block
+                          (1 ... GPCG_MAX_TAIL_ROWS), the levels before it one
+                          block barrier each; -1 = no dense tail; 0 = autotuned */
 } gpcg_options;
+
+/* Largest dense tail of a factor (rows); the tail's right-hand side is kept
+ * in shared memory. */
+#define GPCG_MAX_TAIL_ROWS 248
+
+/* The autotuner (options left at 0) runs on the first batched screen of a
+ * context, and again when the number of scenarios of a call moves to another
+ * power of two.  It screens probes of the call's first outages (at least
+ * 1,024, or twice the scenarios the candidate keeps in flight, at most the
+ * call's) and keeps the fastest in scenarios per second: first the tile width
+ * (2, 4, 8), then the tiles per SM, then the dense tail (248, 128, 64 rows or
+ * none).  Choices are cached for the process, keyed by the device (SM count,
+ * compute capability), the grid's sizes (buses, branches, nonzeros of B', B''
+ * and their factors), precision, preconditioner, kernel kind and the power of
+ * two of the scenario count; a context whose key is cached takes the cached
+ * choice without probing.  Every choice gives the same results up to the
+ * rounding of the inner solve. */
 
 /* Sizes of the structures built by gpcg_create. */
 typedef struct {
@@ -160,6 +185,11 @@ typedef struct {
   int32_t tile;                /* tile width in use (0 until chosen) */
   int32_t num_sms;
   int32_t base_outer;          /* outer iterations of the base solve, -1 if none */
+  int32_t ctas_per_sm;         /* tiles per SM in use (0 until chosen) */
+  int32_t tail_rows_p;         /* rows of the B' factor solved by the dense tail */
+  int32_t tail_rows_q;         /* rows of the B'' factor solved by the dense tail */
+  int32_t tuned;               /* 0: not tuned (or every knob fixed by options);
+                                  1: chosen by probes; 2: taken from the cache */
 } gpcg_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -236,9 +266,10 @@ GPCG_API gpcg_status gpcg_base_solve(gpcg_ctx *ctx, double *theta, double *vm,
  * In device mode the islanding and solve launches are captured once as a
  * CUDA graph, keyed on n_out, the output pointers and the options, and
  * replayed while that key holds (gpcg_set_options drops it).
- * With opt.tile = 0 the first batched screen of a context times tiles of
- * 2, 4 and 8 scenarios on its first min(n_out, 1024) outages and keeps the
- * fastest for the life of the context (gpcg_info.tile). */
+ * Knobs left at 0 in the options (tile width, tiles per SM, dense tail) are
+ * chosen by the autotuner described with gpcg_options on the first batched
+ * screen of the context and whenever n_out moves to another power of two
+ * (gpcg_info reports the choice and whether it came from the cache). */
 GPCG_API gpcg_status gpcg_n1_screen(gpcg_ctx *ctx, const int32_t *outages, int32_t n_out,
                            int32_t mem, void *stream, double *theta, double *vm,
                            double *flow, int32_t *island_label, int32_t *iters,
@@ -379,8 +410,9 @@ GPCG_API gpcg_status gpcg_last_timings(gpcg_ctx *ctx, float *ms /*[2]*/);
  *
  * Scheduling differs from gpcg_n1_screen, results do not: scenarios are
  * taken in the order given (gpcg_n1_screen starts the outages of heavily
- * loaded branches first), and the tile width is the context's option, else
- * the one gpcg_n1_screen's autotuner chose, else 2.
+ * loaded branches first); the tile width and the tiles per SM are the
+ * context's options, else the ones gpcg_n1_screen's autotuner chose last,
+ * else 2 and the occupancy maximum; the dense tails are the factors' own.
  *
  * Every call shares the one array of its context, which keeps the previous
  * call's contents (the call resets what must start at zero): calls that

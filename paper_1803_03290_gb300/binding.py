@@ -19,6 +19,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "BASE_NOT_CONVERGED", 4: "BAS
 PLAIN_FP64, BATCHED_FP32, BATCHED_FP64, BATCHED_FP32_F16 = 0, 1, 2, 3
 PRECOND_IC0, PRECOND_JACOBI, PRECOND_EXACT = 0, 1, 2
 SCEN_OK, SCEN_MAXITER, SCEN_DIVERGED, SCEN_ISLAND_NO_GEN, SCEN_QLIM_OVERFLOW = 0, 1, 2, 3, 4
+MAX_TAIL_ROWS = 248  # GPCG_MAX_TAIL_ROWS: largest dense tail of a factor (rows)
 
 
 class GPCGError(RuntimeError):
@@ -39,14 +40,15 @@ class _Grid(C.Structure):
 class Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("base_tol", C.c_double), ("inner_rtol", C.c_double),
                 ("max_outer", C.c_int32), ("max_inner", C.c_int32), ("precision", C.c_int32),
-                ("precond", C.c_int32), ("tile", C.c_int32), ("ctas_per_sm", C.c_int32)]
+                ("precond", C.c_int32), ("tile", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("tail_rows", C.c_int32)]
 
 
 class Info(C.Structure):
     _fields_ = [(k, C.c_int32) for k in (
         "n_bus", "n_branch", "slack", "n_p", "n_q", "nnz_p", "nnz_q", "nnz_lp", "nnz_lq",
         "levels_p", "levels_q", "blevels_p", "blevels_q", "n_bridges", "tile", "num_sms",
-        "base_outer")]
+        "base_outer", "ctas_per_sm", "tail_rows_p", "tail_rows_q", "tuned")]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -8,6 +8,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -218,6 +220,15 @@ struct gpcg_ctx {
   void* work = nullptr;
   size_t work_bytes = 0;
   int tile = 0;
+  // the autotuner's state: tiles per SM and dense-tail cap in use (0: not
+  // chosen yet), how they were chosen (0 none, 1 probes, 2 cache) and the
+  // power of two of the scenario count they were chosen for
+  int per_sm = 0, per_sm_used = 0, tuned = 0, tuned_bucket = -1;
+  int tail_rows_now = TAIL_ROWS;  // the cap the factors' tails are built with
+  // the factors' dense-tail data of B' (0) and B'' (1): level schedule of the
+  // rows before the tail and the tail block's inverse, rebuilt when the tail
+  // cap changes
+  std::vector<void*> tail_owned[2];
   // adjoint: B' with caller-given susceptances (structure of MP, own values)
   MatDev MA;
   bool ma_ready = false;
@@ -271,6 +282,7 @@ extern "C" gpcg_status gpcg_default_options(gpcg_options* opt) {
   opt->precond = GPCG_PRECOND_EXACT;
   opt->tile = 0;
   opt->ctas_per_sm = 0;
+  opt->tail_rows = 0;
   g_err.clear();
   return GPCG_OK;
 }
@@ -290,6 +302,8 @@ static gpcg_status check_options(const gpcg_options& o) {
     return fail(GPCG_ERR_INVALID_ARG, "tile must be 0, 2, 4, 8, 16 or 32");
   if (o.ctas_per_sm < 0 || o.ctas_per_sm > 64)
     return fail(GPCG_ERR_INVALID_ARG, "ctas_per_sm must be in [0, 64]");
+  if (o.tail_rows < -1 || o.tail_rows > GPCG_MAX_TAIL_ROWS)
+    return fail(GPCG_ERR_INVALID_ARG, "tail_rows must be -1, 0 or in [1, %d]", GPCG_MAX_TAIL_ROWS);
   return GPCG_OK;
 }
 
@@ -350,6 +364,41 @@ static void ell_fill(cudaStream_t st, EllDev& D, const double* csr_val) {
 // Values of a matrix whose structure is built: the weighted Laplacian
 // (weights w per branch), its factor on the planned pattern, diagonals and
 // padded-row values.  Synchronous.
+// The dense tail of a factor: the last forward levels, together at most
+// `cap` rows (0: none), solved with the inverse of their block; the rows
+// before it get a backward level schedule of their own.  Allocates the
+// schedule and the inverse's arrays (FP64, FP32, and for the FP16-stored
+// factor) in the matrix's own tail list, replacing earlier ones.
+static gpcg_status alloc_tail(gpcg_ctx* c, MatDev& M, int which, int cap) {
+  auto& own = c->tail_owned[which];
+  free_list(own);
+  plan_tail(M.plan, cap);
+  const MatrixPlan& P = M.plan;
+  CUDA_TRY(upload(own, &M.tblev_ptr, P.tblev_ptr.data(), P.tblev_ptr.size()));
+  M.tblev_rows = nullptr;
+  if (!P.tblev_rows.empty())
+    CUDA_TRY(upload(own, &M.tblev_rows, P.tblev_rows.data(), P.tblev_rows.size()));
+  const size_t nt = (size_t)(P.n - P.tail_row0);
+  CUDA_TRY(dalloc(own, &M.xc, nt * nt));
+  CUDA_TRY(dalloc(own, &M.xr, nt * nt));
+  CUDA_TRY(dalloc(own, &M.xc32, nt * nt));
+  CUDA_TRY(dalloc(own, &M.xr32, nt * nt));
+  CUDA_TRY(dalloc(own, &M.xch, nt * nt));
+  CUDA_TRY(dalloc(own, &M.xrh, nt * nt));
+  return GPCG_OK;
+}
+
+// The tail block's inverse from the factor's values: of the FP16-stored
+// factor first (M.xc as FP64 scratch), then of the factor itself.
+static void launch_tail_inverses(const MatDev& M, cudaStream_t st) {
+  const MatrixPlan& P = M.plan;
+  if (M.lsc && M.xch)
+    launch_tail_inverse(st, P.tail_row0, P.n - P.tail_row0, M.l_ptr, M.l_idx, M.l_val, M.lsc,
+                        M.xc, nullptr, M.xch, M.xrh);
+  launch_tail_inverse(st, P.tail_row0, P.n - P.tail_row0, M.l_ptr, M.l_idx, M.l_val, nullptr,
+                      M.xc, M.xr, M.xc32, M.xr32);
+}
+
 static gpcg_status fill_values(gpcg_ctx* c, MatDev& M, const double* w) {
   const MatrixPlan& P = M.plan;
   const int nl = P.L.nnz();
@@ -374,14 +423,8 @@ static gpcg_status fill_values(gpcg_ctx* c, MatDev& M, const double* w) {
       launch_gather_half(st, E->nslot, E->src, M.lsc, E->valh);
       launch_gather_half(st, E->nover, E->osrc, M.lsc, E->ovalh);
     }
-    // tail inverse of the FP16-stored factor (M.xc as FP64 scratch, then
-    // overwritten below)
-    if (M.xch)
-      launch_tail_inverse(st, P.tail_row0, P.n - P.tail_row0, M.l_ptr, M.l_idx, M.l_val, M.lsc,
-                          M.xc, nullptr, M.xch, M.xrh);
   }
-  launch_tail_inverse(st, P.tail_row0, P.n - P.tail_row0, M.l_ptr, M.l_idx, M.l_val, nullptr,
-                      M.xc, M.xr, M.xc32, M.xr32);
+  launch_tail_inverses(M, st);
   CUDA_TRY(cudaGetLastError());
   int32_t herr = 0;
   CUDA_TRY(cudaMemcpy(&herr, c->d_err, sizeof herr, cudaMemcpyDeviceToHost));
@@ -392,10 +435,14 @@ static gpcg_status fill_values(gpcg_ctx* c, MatDev& M, const double* w) {
   return GPCG_OK;
 }
 
-static gpcg_status build_matrix(gpcg_ctx* c, MatDev& M, const std::vector<uint8_t>& keep,
-                                double* w, double* cf, bool fill) {
+static gpcg_status build_matrix(gpcg_ctx* c, MatDev& M, int which,
+                                const std::vector<uint8_t>& keep, double* w, double* cf,
+                                bool fill) {
   M.plan = plan_matrix(c->n, c->bg, keep, fill);
-  plan_tail(M.plan, TAIL_ROWS);
+  {
+    gpcg_status st = alloc_tail(c, M, which, c->tail_rows_now);
+    if (st != GPCG_OK) return st;
+  }
   const MatrixPlan& P = M.plan;
   auto& own = c->mat_owned;
   std::vector<int32_t> pre_of_row(P.n);
@@ -418,16 +465,6 @@ static gpcg_status build_matrix(gpcg_ctx* c, MatDev& M, const std::vector<uint8_
   CUDA_TRY(upload(own, &M.lev_ptr, P.lev_ptr.data(), P.lev_ptr.size()));
   CUDA_TRY(upload(own, &M.blev_ptr, P.blev_ptr.data(), P.blev_ptr.size()));
   CUDA_TRY(upload(own, &M.blev_rows, P.blev_rows.data(), P.blev_rows.size()));
-  CUDA_TRY(upload(own, &M.tblev_ptr, P.tblev_ptr.data(), P.tblev_ptr.size()));
-  if (!P.tblev_rows.empty())
-    CUDA_TRY(upload(own, &M.tblev_rows, P.tblev_rows.data(), P.tblev_rows.size()));
-  {
-    const size_t nt = (size_t)(P.n - P.tail_row0);
-    CUDA_TRY(dalloc(own, &M.xc, nt * nt));
-    CUDA_TRY(dalloc(own, &M.xr, nt * nt));
-    CUDA_TRY(dalloc(own, &M.xc32, nt * nt));
-    CUDA_TRY(dalloc(own, &M.xr32, nt * nt));
-  }
   std::vector<int32_t> ldiag(P.n);
   for (int i = 0; i < P.n; ++i) ldiag[i] = P.L.ptr[i + 1] - 1;
   CUDA_TRY(upload(own, &M.l_diag, ldiag.data(), P.n));
@@ -439,11 +476,6 @@ static gpcg_status build_matrix(gpcg_ctx* c, MatDev& M, const std::vector<uint8_
   CUDA_TRY(dalloc(own, &M.inv_diag, P.n));
   CUDA_TRY(dalloc(own, &M.inv_diag32, P.n));
   CUDA_TRY(dalloc(own, &M.lsc, nl));
-  {
-    const size_t nt = (size_t)(P.n - P.tail_row0);
-    CUDA_TRY(dalloc(own, &M.xch, nt * nt));
-    CUDA_TRY(dalloc(own, &M.xrh, nt * nt));
-  }
   CUDA_TRY(dalloc(own, &M.inv_d2, P.n));
   CUDA_TRY(dalloc(own, &M.inv_d2_32, P.n));
   // padded rows: A (all entries), strictly lower L, strictly upper L^T
@@ -481,9 +513,9 @@ static gpcg_status build_matrices(gpcg_ctx* c) {
   }
   const bool fill = c->opt.precond == GPCG_PRECOND_EXACT;
   // B' leaves turns ratios out, B'' keeps them (the XB scheme)
-  gpcg_status st = build_matrix(c, c->MP, keepP, c->wP, nullptr, fill);
+  gpcg_status st = build_matrix(c, c->MP, 0, keepP, c->wP, nullptr, fill);
   if (st != GPCG_OK) return st;
-  st = build_matrix(c, c->MQ, keepQ, c->wQ, c->G.cf, fill);
+  st = build_matrix(c, c->MQ, 1, keepQ, c->wQ, c->G.cf, fill);
   if (st != GPCG_OK) return st;
   {
     // B'' rows of PV buses, taken by a bus whose generator trips
@@ -526,6 +558,7 @@ static void destroy(gpcg_ctx* c) {
   free_list(c->adj_owned);
   if (c->adj_acc) cudaFree(c->adj_acc);
   free_list(c->mat_owned);
+  for (auto& v : c->tail_owned) free_list(v);
   free_list(c->owned);
   if (c->work) cudaFree(c->work);
   for (auto& e : c->ev)
@@ -598,6 +631,8 @@ extern "C" gpcg_status gpcg_create(const gpcg_grid* g, const gpcg_options* opt, 
   gpcg_ctx* c = new gpcg_ctx();
   c->opt = o;
   c->tile = o.tile;  // 0: chosen on the first batched screen
+  c->per_sm = o.ctas_per_sm;
+  c->tail_rows_now = o.tail_rows > 0 ? o.tail_rows : (o.tail_rows < 0 ? 0 : TAIL_ROWS);
   c->n = n;
   c->m = m;
   c->slack_user = slack;
@@ -847,6 +882,26 @@ static void drop_graph(gpcg_ctx* c) {
   c->graph_key.clear();
 }
 
+// Both factors' dense tails rebuilt with at most `cap` rows (0: none).
+static gpcg_status set_tail(gpcg_ctx* c, int cap) {
+  if (cap == c->tail_rows_now) return GPCG_OK;
+  CUDA_TRY(cudaDeviceSynchronize());  // launches in flight read the old tails
+  c->tail_rows_now = cap;
+  for (int k = 0; k < 2; ++k) {
+    MatDev& M = k ? c->MQ : c->MP;
+    gpcg_status s = alloc_tail(c, M, k, cap);
+    if (s != GPCG_OK) return s;
+    launch_tail_inverses(M, 0);
+  }
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaDeviceSynchronize());
+  // the adjoint's copy of B' shares the tail's schedule: rebuilt on next use
+  free_list(c->adj_owned);
+  c->ma_ready = false;
+  drop_graph(c);
+  return GPCG_OK;
+}
+
 extern "C" gpcg_status gpcg_set_options(gpcg_ctx* c, const gpcg_options* opt) {
   if (!c || !opt) return fail(GPCG_ERR_INVALID_ARG, "gpcg_set_options: NULL argument");
   gpcg_status st = check_options(*opt);
@@ -854,13 +909,27 @@ extern "C" gpcg_status gpcg_set_options(gpcg_ctx* c, const gpcg_options* opt) {
   const bool rebuild = opt->precond != c->planned_precond &&
                        ((opt->precond == GPCG_PRECOND_EXACT) !=
                         (c->planned_precond == GPCG_PRECOND_EXACT));
+  // a knob, the precision or the preconditioner changed: tune again
+  const bool retune = opt->tile != c->opt.tile || opt->ctas_per_sm != c->opt.ctas_per_sm ||
+                      opt->tail_rows != c->opt.tail_rows || opt->precision != c->opt.precision ||
+                      opt->precond != c->opt.precond;
   drop_graph(c);
   c->opt = *opt;
-  if (opt->tile) c->tile = opt->tile;
-  if (rebuild) {
-    st = build_matrices(c);
-    if (st != GPCG_OK) return st;
+  if (retune) {
+    c->tile = opt->tile;
+    c->per_sm = opt->ctas_per_sm;
+    c->tuned = 0;
+    c->tuned_bucket = -1;
   }
+  const int cap = opt->tail_rows > 0 ? opt->tail_rows
+                                     : (opt->tail_rows < 0 ? 0 : c->tail_rows_now);
+  if (rebuild) {
+    c->tail_rows_now = cap;
+    st = build_matrices(c);
+  } else {
+    st = set_tail(c, cap);
+  }
+  if (st != GPCG_OK) return st;
   c->planned_precond = opt->precond;
   g_err.clear();
   return GPCG_OK;
@@ -885,6 +954,10 @@ extern "C" gpcg_status gpcg_get_info(const gpcg_ctx* c, gpcg_info* info) {
   info->tile = c->tile;
   info->num_sms = c->num_sms;
   info->base_outer = c->base_outer;
+  info->ctas_per_sm = c->per_sm_used;
+  info->tail_rows_p = c->MP.plan.n - c->MP.plan.tail_row0;
+  info->tail_rows_q = c->MQ.plan.n - c->MQ.plan.tail_row0;
+  info->tuned = c->tuned;
   g_err.clear();
   return GPCG_OK;
 }
@@ -1078,6 +1151,25 @@ static gpcg_status ensure_plain(gpcg_ctx* c) {
   return GPCG_OK;
 }
 
+// The autotuner's choices, shared by the contexts of the process: keyed by
+// the device, the grid's sizes, precision, preconditioner, kernel kind, the
+// options that fix knobs, and the power of two of the scenario count.
+struct TuneChoice {
+  int tile, per_sm, tail;
+};
+static std::mutex g_tune_mu;
+static std::map<std::vector<long long>, TuneChoice> g_tune_cache;
+
+static std::vector<long long> tune_key(const gpcg_ctx* c, bool ext, int bucket) {
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, c->device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, c->device);
+  return {c->num_sms, major, minor, c->n, c->m,
+          c->MP.plan.A.nnz(), c->MP.plan.L.nnz(), c->MQ.plan.A.nnz(), c->MQ.plan.L.nnz(),
+          c->opt.precision, c->opt.precond, ext, c->zs_allowed, bucket,
+          c->opt.tile, c->opt.ctas_per_sm, c->opt.tail_rows};
+}
+
 template <typename X>
 struct OutBuf {
   X* dev = nullptr;
@@ -1230,41 +1322,102 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
     return c->zs_allowed && !ext && (t == 2 || t == 4) && blocks(t, true) > 0;
   };
   if (!plain) {
-    if (!c->opt.tile && !c->tile) {
-      // autotuner: the tile width that screens a probe of the first outages
-      // fastest, chosen on the first batched screen of the context
-      CUDA_TRY(enqueue_islands(st));
-      const int probe = (int)std::min<size_t>(S, 1024);
-      float best = 0.f;
-      int bestT = 2;
-      for (int t : {2, 4, 8}) {
-        FdpfParams Q = base_params(c);
-        Q.sc = P.sc;
-        Q.th0 = P.th0; Q.V0 = P.V0; Q.c0 = P.c0; Q.s0 = P.s0;
-        Q.S = probe;
-        Q.n_tiles = (probe + t - 1) / t;
-        const bool z = use_zs(t);
-        const int ps = blocks(t, z);
-        const int sl = std::max(1, std::min(Q.n_tiles, c->num_sms * std::max(ps, 1)));
-        CUDA_TRY(cudaEventRecord(c->ev[3], st));
-        rs = f32 ? run_fdpf<float>(c, st, Q, t, sl, f16, z)
-                 : run_fdpf<double>(c, st, Q, t, sl, false, z);
-        if (rs != GPCG_OK) { cleanup(); return rs; }
-        CUDA_TRY(cudaEventRecord(c->ev[2], st));
-        CUDA_TRY(cudaEventSynchronize(c->ev[2]));
-        float ms = 0.f;
-        CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[3], c->ev[2]));
-        if (t == 2 || ms < best) { best = ms; bestT = t; }
+    // tile width, tiles per SM and dense tail: fixed by the options, else
+    // chosen by the autotuner for this power of two of the scenario count
+    int bucket = 0;
+    while (((size_t)1 << bucket) < S) ++bucket;
+    const bool knobs = !c->opt.tile || !c->opt.ctas_per_sm || !c->opt.tail_rows;
+    if (knobs && bucket != c->tuned_bucket) {
+      const std::vector<long long> key = tune_key(c, ext, bucket);
+      TuneChoice got{0, 0, 0};
+      bool hit = false;
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) { got = it->second; hit = true; }
       }
-      c->tile = bestT;
+      if (!hit) {
+        // probes of the call's first outages: each candidate screens at
+        // least 1,024 of them, or twice the scenarios it keeps in flight
+        CUDA_TRY(enqueue_islands(st));
+        auto rate = [&](int t, int ps, int cap, bool timed, double* out) -> gpcg_status {
+          gpcg_status r = set_tail(c, cap);
+          if (r != GPCG_OK) return r;
+          FdpfParams Q = base_params(c);
+          Q.sc = P.sc;
+          Q.th0 = P.th0; Q.V0 = P.V0; Q.c0 = P.c0; Q.s0 = P.s0;
+          const size_t want = timed ? std::max<size_t>(1024, (size_t)2 * t * ps * c->num_sms)
+                                    : (size_t)t * c->num_sms;
+          const int np = (int)std::min(S, want);
+          Q.S = np;
+          Q.n_tiles = (np + t - 1) / t;
+          const bool z = use_zs(t);
+          const int sl = std::max(1, std::min(Q.n_tiles, c->num_sms * ps));
+          CUDA_TRY(cudaEventRecord(c->ev[3], st));
+          r = f32 ? run_fdpf<float>(c, st, Q, t, sl, f16, z)
+                  : run_fdpf<double>(c, st, Q, t, sl, false, z);
+          if (r != GPCG_OK) return r;
+          CUDA_TRY(cudaEventRecord(c->ev[2], st));
+          CUDA_TRY(cudaEventSynchronize(c->ev[2]));
+          float ms = 0.f;
+          CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[3], c->ev[2]));
+          *out = np / std::max(ms, 1e-3f);  // scenarios per ms
+          return GPCG_OK;
+        };
+        auto max_ps = [&](int t) { return std::max(1, blocks(t, use_zs(t))); };
+        const int cap0 = c->opt.tail_rows > 0 ? c->opt.tail_rows
+                         : (c->opt.tail_rows < 0 ? 0 : TAIL_ROWS);
+        std::vector<int> tiles = c->opt.tile ? std::vector<int>{c->opt.tile}
+                                             : std::vector<int>{2, 4, 8};
+        if (ext)
+          for (int& t : tiles) t = std::min(t, 8);
+        // (a) the tile width, at the most tiles per SM and the widest tail
+        double best = -1.0;
+        int bT = tiles[0], bP = 0, bC = cap0;
+        for (int t : tiles) {
+          const int ps = c->opt.ctas_per_sm ? c->opt.ctas_per_sm : max_ps(t);
+          double v = 0.0;
+          gpcg_status r = rate(t, ps, cap0, false, &v);  // first launch of the variant: untimed
+          if (r == GPCG_OK) r = rate(t, ps, cap0, true, &v);
+          if (r != GPCG_OK) { cleanup(); return r; }
+          if (v > best) { best = v; bT = t; bP = ps; }
+        }
+        // (b) tiles per SM: the occupancy maximum and the two counts below it
+        if (!c->opt.ctas_per_sm)
+          for (int ps = max_ps(bT) - 1; ps >= std::max(1, max_ps(bT) - 2); --ps) {
+            double v = 0.0;
+            gpcg_status r = rate(bT, ps, cap0, true, &v);
+            if (r != GPCG_OK) { cleanup(); return r; }
+            if (v > best) { best = v; bP = ps; }
+          }
+        // (c) the dense tail: 248, 128, 64 rows or none
+        if (!c->opt.tail_rows)
+          for (int cap : {128, 64, 0}) {
+            double v = 0.0;
+            gpcg_status r = rate(bT, bP, cap, true, &v);
+            if (r != GPCG_OK) { cleanup(); return r; }
+            if (v > best) { best = v; bC = cap; }
+          }
+        got = TuneChoice{bT, bP, bC};
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = got;
+      }
+      gpcg_status r = set_tail(c, got.tail);
+      if (r != GPCG_OK) { cleanup(); return r; }
+      c->tile = got.tile;
+      c->per_sm = got.per_sm;
+      c->tuned = hit ? 2 : 1;
+      c->tuned_bucket = bucket;
     }
     T = c->opt.tile ? c->opt.tile : (c->tile ? c->tile : 2);
     if (ext) T = std::min(T, 8);  // the kernel with extension rows: tiles of 2, 4, 8
     zs = use_zs(T);
     const int n_tiles = (int)((S + T - 1) / T);
-    int per_sm = c->opt.ctas_per_sm;
+    int per_sm = c->opt.ctas_per_sm ? c->opt.ctas_per_sm : c->per_sm;
+    if (!c->opt.ctas_per_sm && per_sm > blocks(T, zs)) per_sm = blocks(T, zs);
     if (per_sm == 0 || (zs && per_sm > blocks(T, true))) per_sm = blocks(T, zs);
     per_sm = std::max(per_sm, 1);
+    c->per_sm_used = per_sm;
     slots = std::max(1, std::min(n_tiles, c->num_sms * per_sm));
     P.S = (int)S;
     P.n_tiles = n_tiles;
@@ -1915,6 +2068,7 @@ bool ctx_view(const gpcg_ctx* c, CtxView* v) {
   v->u_P_sched = c->u_P_sched;
   v->u_P_gen = c->u_P_gen;
   v->tile = c->tile;
+  v->per_sm = c->per_sm;
   v->base_ok = c->base_ok;
   return true;
 }

@@ -15,6 +15,7 @@ struct CtxView {
   const int32_t* bus_of_user = nullptr;  // caller's bus -> internal bus
   gpcg_options opt{};
   int num_sms = 0, n = 0, m = 0, slack = -1, rows = 0, tile = 0, slack_user = -1;
+  int per_sm = 0;  // tiles per SM the autotuner chose (0: none yet)
   const int32_t *u_f = nullptr, *u_t = nullptr, *u_pre = nullptr;  // caller numbering
   const int8_t* u_bus_type = nullptr;
   const double *u_P_sched = nullptr, *u_P_gen = nullptr;

@@ -96,9 +96,10 @@ extern "C" gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx* ctx, const int32_t* outa
                "scratch, more than the %zu-byte limit",
                S, c.n, head + scen + per_slot, cap);
   const int n_tiles = (int)((S + T - 1) / T);
-  int per_sm = c.opt.ctas_per_sm;
-  if (per_sm == 0)
-    per_sm = f32 ? fdpf_max_blocks_per_sm<float>(T, ext) : fdpf_max_blocks_per_sm<double>(T, ext);
+  const int occ =
+      f32 ? fdpf_max_blocks_per_sm<float>(T, ext) : fdpf_max_blocks_per_sm<double>(T, ext);
+  int per_sm = c.opt.ctas_per_sm ? c.opt.ctas_per_sm : std::min(c.per_sm, occ);
+  if (per_sm <= 0) per_sm = occ;
   per_sm = std::max(per_sm, 1);
   const size_t fit = (cap - head - scen) / per_slot;
   const int slots = (int)std::max<size_t>(1, std::min<size_t>(

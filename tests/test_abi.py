@@ -72,3 +72,33 @@ def test_invalid_arguments_fail_before_the_gpu():
     assert e.value.status == 1 and "reactive limits" in str(e.value)
     with pytest.raises(binding.GPCGError):
         binding.default_options(precision=7) and binding.GPCG(g, precision=7)
+
+
+def _struct_fields(name):
+    src = open(os.path.join(ROOT, "include", "gpcg.h")).read()
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + ";", src).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            out += [v.strip().lstrip("*") for v in decl.split(None, 1)[1].split(",")]
+    return out
+
+
+def test_binding_structs_follow_the_header():
+    from paper_1803_03290_gb300 import binding
+    assert [k for k, _ in binding.Options._fields_] == _struct_fields("gpcg_options")
+    assert [k for k, _ in binding.Info._fields_] == _struct_fields("gpcg_info")
+    src = open(os.path.join(ROOT, "include", "gpcg.h")).read()
+    assert int(re.search(r"#define GPCG_MAX_TAIL_ROWS (\d+)", src).group(1)) == binding.MAX_TAIL_ROWS
+
+
+@pytest.mark.parametrize("bad", [dict(tail_rows=-2), dict(tail_rows=249), dict(tile=3),
+                                 dict(ctas_per_sm=-1)])
+def test_bad_options_fail_before_the_gpu(bad):
+    from paper_1803_03290_gb300 import binding
+    from gridgen import config_grid
+    with pytest.raises(binding.GPCGError) as e:
+        binding.GPCG(config_grid("grid120"), **bad)
+    assert e.value.status == 1

@@ -85,7 +85,9 @@ def test_noalloc_matches_regular_screen_twice(name, precision):
 def test_noalloc_on_a_fresh_context():
     """The no-allocation screen as the context's first screen (no tile
     chosen yet: tiles of 2), then the regular screen: the same statuses,
-    labels and overloads, and states within tolerance."""
+    labels and overloads, and states within tolerance (iteration counts
+    too when the autotuner kept tiles of 2 and the factors' dense tails:
+    another tail rounds the inner solve differently)."""
     torch = pytest.importorskip("torch")
     import paper_1803_03290_gb300 as gp
     from gpu_common import grid
@@ -100,12 +102,15 @@ def test_noalloc_on_a_fresh_context():
     got = [_device_outputs(torch, S, g.n_bus, g.n_branch, dev) for _ in range(2)]
     c.n1_screen_noalloc_device(outages, got[0])
     torch.cuda.synchronize()
-    assert c.info()["tile"] == 0
+    before = c.info()
+    assert before["tile"] == 0
     ref = _device_outputs(torch, S, g.n_bus, g.n_branch, dev)
     c.n1_screen_device(outages, ref)
     c.n1_screen_noalloc_device(outages, got[1])
     torch.cuda.synchronize()
-    _compare(got[0], ref, c.info()["tile"] == 2, 0)
+    after = c.info()
+    same = after["tile"] == 2 and all(after[k] == before[k] for k in ("tail_rows_p", "tail_rows_q"))
+    _compare(got[0], ref, same, 0)
     _compare(got[1], ref, True, 1)
     c.close()
 
