@@ -107,15 +107,15 @@ def fp64_operations(g, iters):
     launch, from the kernel's arithmetic: per full P mismatch 4 per adjacency
     entry and 7 per non-slack bus (+2 per PQ bus for dQ), per Q mismatch 4
     per adjacency entry and 6 per PQ bus, per angle update 12 per non-slack
-    bus (the exact rotation of e + jf), per |V| update 3 per PQ bus, the first
-    P mismatch 1 per non-slack bus (the base case's is stored), and 16 per
-    branch for the flows and loading; k outer iterations take k full P
-    mismatches, k Q mismatches and k updates of each kind."""
+    bus (the exact rotation of e + jf), per |V| update 2 per PQ bus (e and f
+    scaled), the first P mismatch 1 per non-slack bus (the base case's is
+    stored), and 16 per branch for the flows and loading; k outer iterations
+    take k full P mismatches, k Q mismatches and k updates of each kind."""
     bt = np.asarray(g.bus_type)
     deg = np.bincount(np.r_[g.f, g.t], minlength=g.n_bus)
     nP, nQ = int((bt != 2).sum()), int((bt == 0).sum())
     AP, AQ = int(deg[bt != 2].sum()), int(deg[bt == 0].sum())
-    per_outer = (4 * AP + 7 * nP + 2 * nQ) + (4 * AQ + 6 * nQ) + 12 * nP + 3 * nQ
+    per_outer = (4 * AP + 7 * nP + 2 * nQ) + (4 * AQ + 6 * nQ) + 12 * nP + 2 * nQ
     k = iters[:, 0].astype(np.float64)
     return float((k * per_outer).sum() + iters.shape[0] * (nP + 16 * g.n_branch))
 

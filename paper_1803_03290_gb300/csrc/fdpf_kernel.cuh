@@ -33,6 +33,23 @@
 
 namespace gpcg {
 
+// 1 / |V| of the rectangular voltage e + jf in the inner solve's precision.
+// It only scales inner-solve quantities -- the right-hand sides dP/|V| and
+// dQ/|V| and the relative step dV/|V| -- which the outer FP64 loop refines,
+// so the FP32 form's few-ulp rounding moves no converged state.  The state
+// keeps no |V| of its own: e + jf is the state.
+template <typename VT>
+__device__ __forceinline__ VT inv_vmag(double e, double f);
+template <>
+__device__ __forceinline__ float inv_vmag<float>(double e, double f) {
+  const float a = to_f32(e), b = to_f32(f);
+  return rsqrtf(fmaf(a, a, b * b));
+}
+template <>
+__device__ __forceinline__ double inv_vmag<double>(double e, double f) {
+  return 1.0 / sqrt(fma(e, e, f * f));
+}
+
 // ------------------------------------------------------------ mismatch
 // The rectangular voltages e + jf of a slot are stored interleaved,
 // [bus][lane][e, f], so one 16-byte load gives a lane's (e, f) and a thread's
@@ -94,7 +111,6 @@ template <int T, typename VT, bool WITH_P, bool GEN>
 __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMatT<VT>& MP,
                                                const DevMatT<VT>& MQ, LaneState<T>& L,
                                                const double* __restrict__ EF,
-                                               const double* __restrict__ V,
                                                VT* __restrict__ rhs,
                                                Vec<unsigned long long, Geo<T>::LP>& errP,
                                                Vec<unsigned long long, Geo<T>::LP>& errQ,
@@ -189,7 +205,6 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
       // own voltage, the diagonal term and the mismatch of each lane
       const double2* own = reinterpret_cast<const double2*>(EF + ef_at<T>(i, l0));
       const double2 ev0 = own[0], ev1 = own[1];
-      const Pair<double> vi = ld2(V + (size_t)i * T + l0);
       const int bt = G.bus_type[i];
       const double Gii = __ldg(G.Gii + i), Bii = __ldg(G.Bii + i), qs = __ldg(G.Q_sched + i);
       double Ps = 0.0, pg = 0.0, Pgr = 0.0;
@@ -222,10 +237,12 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
             const double q0 = __ldg(P.r0Q + i);
             upd_max_bits(errQ.v[jp + j], xe ? q0 + (qx - qs) : q0);
           }
-          out.v[jp + j] = to_vt<VT>(dP) / to_vt<VT>(j ? vi.b : vi.a);
+          out.v[jp + j] = to_vt<VT>(dP) * (j ? inv_vmag<VT>(ev1.x, ev1.y)
+                                             : inv_vmag<VT>(ev0.x, ev0.y));
           continue;
         }
         const double ei = j ? ev1.x : ev0.x, fi = j ? ev1.y : ev0.y;
+        const VT iv = inv_vmag<VT>(ei, fi);
         double Gd = Gii, Bd = Bii;
         if (i == L.fb[ln] || i == L.tb[ln]) {  // the outaged branch's share
           const double c2 = i == L.fb[ln] ? L.cl[ln] * L.cl[ln] : 1.0;
@@ -255,10 +272,10 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
               }
             }
           }
-          res = to_vt<VT>(dP) / to_vt<VT>(j ? vi.b : vi.a);
+          res = to_vt<VT>(dP) * iv;
         } else {
           const double dQ = fma(-fi, re, fma(ei, im, qs));
-          res = to_vt<VT>(dQ) / to_vt<VT>(j ? vi.b : vi.a);
+          res = to_vt<VT>(dQ) * iv;
         }
         out.v[jp + j] = res;
       }
@@ -278,7 +295,7 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
         const double2 I = bus_current<T>(G, L, EF, b, ln);
         const double2 v = *reinterpret_cast<const double2*>(EF + ef_at<T>(b, ln));
         const double dQ = fma(-v.y, I.x, fma(v.x, I.y, SW->xq[ln][s]));
-        rhs[(size_t)(MQ.n + 1 + s) * T + ln] = to_vt<VT>(dQ) / to_vt<VT>(V[(size_t)b * T + ln]);
+        rhs[(size_t)(MQ.n + 1 + s) * T + ln] = to_vt<VT>(dQ) * inv_vmag<VT>(v.x, v.y);
       }
     }
 }
@@ -307,28 +324,23 @@ __device__ __forceinline__ void rotate_ef(double d, double& e, double& f) {
   f = fma(-f, a, fma(e0, b, f));
 }
 
-// The relative step r = dV / |V| of a |V| update: FP32 vectors take it in
-// FP32 (the step is an inner-solve iterate that the outer FP64 loop refines;
-// r is then exact as an FP64 number), FP64 vectors in FP64.
+// The relative step r = dV / |V| of a |V| update at the voltage e + jf:
+// FP32 vectors take it in FP32 (the step is an inner-solve iterate that the
+// outer FP64 loop refines; r is then exact as an FP64 number), FP64 vectors
+// in FP64.
 template <typename VT>
-__device__ __forceinline__ double v_ratio(VT dv, double v);
-template <>
-__device__ __forceinline__ double v_ratio<float>(float dv, double v) {
-  return cvt_f64(__fdividef(dv, cvt_f32(v)));
-}
-template <>
-__device__ __forceinline__ double v_ratio<double>(double dv, double v) {
-  return dv / v;
+__device__ __forceinline__ double v_ratio(VT dv, double e, double f) {
+  return to_f64(dv * inv_vmag<VT>(e, f));
 }
 
 // theta += dtheta (P half-step) or |V| += dV (Q half-step) on the matrix's
-// rows, with the rectangular voltages moved with them: (e, f) rotated through
-// dtheta, or |V|, e and f all scaled by the same factor 1 + dV/|V|, so that
+// rows, as moves of the rectangular voltage: (e, f) rotated through dtheta
+// (theta kept beside it), or e and f both scaled by 1 + dV/|V|, so that
 // e + jf = |V| exp(j theta) holds to FP64 rounding; lanes two at a time.
 template <int T, typename VT, bool IS_P, bool GEN>
 __device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>& L,
                                              const VT* __restrict__ x,
-                                             const VT* __restrict__ p, double* th, double* V,
+                                             const VT* __restrict__ p, double* th,
                                              double* EF, const SwitchState<T>* SW = nullptr) {
   constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
@@ -370,18 +382,14 @@ __device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>&
         }
         st2(th + o, t);
       } else {
-        Pair<double> v = ld2(V + o);
         if (on0) {
-          const double r = v_ratio<VT>(dx.a, v.a);
-          v.a = fma(v.a, r, v.a);
+          const double r = v_ratio<VT>(dx.a, u0.x, u0.y);
           u0 = make_double2(fma(u0.x, r, u0.x), fma(u0.y, r, u0.y));
         }
         if (on1) {
-          const double r = v_ratio<VT>(dx.b, v.b);
-          v.b = fma(v.b, r, v.b);
+          const double r = v_ratio<VT>(dx.b, u1.x, u1.y);
           u1 = make_double2(fma(u1.x, r, u1.x), fma(u1.y, r, u1.y));
         }
-        st2(V + o, v);
       }
       ef[0] = u0;
       ef[1] = u1;
@@ -399,11 +407,9 @@ __device__ GPCG_LOOP_INLINE void update_pass(const DevMatT<VT>& M, LaneState<T>&
       VT dx = x[oe];
       const VT xa = (VT)L.xalpha[ln];
       if (xa != (VT)0) dx = fma(xa, p[oe], dx);
-      const size_t o = (size_t)b * T + ln;
-      const double r = v_ratio<VT>(dx, V[o]);
-      V[o] = fma(V[o], r, V[o]);
       double2* ef = reinterpret_cast<double2*>(EF + ef_at<T>(b, ln));
       const double2 u = ef[0];
+      const double r = v_ratio<VT>(dx, u.x, u.y);
       ef[0] = make_double2(fma(u.x, r, u.x), fma(u.y, r, u.y));
     }
 }
@@ -463,7 +469,7 @@ __device__ __forceinline__ void setup_lane(const FdpfParams& P, const DevMatT<VT
 // zero on islanded buses.  Other lanes keep their state.
 template <int T>
 __device__ GPCG_PASS_INLINE void init_pass(const FdpfParams& P, LaneState<T>& L, double* th,
-                                           double* V, double* EF) {
+                                           double* EF) {
   constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
   const DevGrid& G = P.G;
@@ -483,7 +489,6 @@ __device__ GPCG_PASS_INLINE void init_pass(const FdpfParams& P, LaneState<T>& L,
       const size_t o = (size_t)i * T + ln;
       const bool isl = in_island(pr, L.lo[ln], L.cnt[ln]);
       th[o] = isl ? 0.0 : t0;
-      V[o] = isl ? 0.0 : v0;
       reinterpret_cast<double2*>(EF + ef_at<T>(i, ln))[0] =
           isl ? make_double2(0.0, 0.0) : make_double2(v0 * c0, v0 * s0);
     }
@@ -494,8 +499,7 @@ __device__ GPCG_PASS_INLINE void init_pass(const FdpfParams& P, LaneState<T>& L,
 // (Sec. I: overload screening), status and iteration counts.
 template <int T>
 __device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& L,
-                                             const double* th, const double* V,
-                                             const double* EF) {
+                                             const double* th, const double* EF) {
   constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
   const DevGrid& G = P.G;
@@ -511,7 +515,10 @@ __device__ GPCG_PASS_INLINE void retire_pass(const FdpfParams& P, LaneState<T>& 
         const int ln = g.lane + j, s = L.scen[ln];
         const size_t o = (size_t)i * T + ln;
         if (P.out_theta) P.out_theta[(size_t)s * G.n + iu] = th[o];
-        if (P.out_vm) P.out_vm[(size_t)s * G.n + iu] = V[o];
+        if (P.out_vm) {  // |V| of the state e + jf (0 on islanded buses)
+          const double2 u = *reinterpret_cast<const double2*>(EF + ef_at<T>(i, ln));
+          P.out_vm[(size_t)s * G.n + iu] = sqrt(fma(u.x, u.x, u.y * u.y));
+        }
       }
     }
   }
@@ -643,7 +650,7 @@ __global__ void __launch_bounds__(NTHREADS, ZS ? 2 : FDPF_MIN_BLOCKS)
   VT* z = ZS ? reinterpret_cast<VT*>(zdyn) : (VT*)P.wz + (size_t)blockIdx.x * P.vstride;
   const size_t so = (size_t)blockIdx.x * P.sstride;
   // E and F regions of the slots taken together: [slot][bus][lane][e, f]
-  double *th = P.wth + so, *V = P.wV + so, *EF = P.we + 2 * so;
+  double *th = P.wth + so, *EF = P.we + 2 * so;
 
   // optional per-phase cycle counters (thread 0's view of the CTA)
   const bool tim = P.phase_cycles != nullptr;
@@ -680,7 +687,7 @@ __global__ void __launch_bounds__(NTHREADS, ZS ? 2 : FDPF_MIN_BLOCKS)
 
   for (;;) {
     // retire finished lanes, then refill empty lanes from the queue
-    if (any_lane<T>(L, L.done)) retire_pass<T>(P, L, th, V, EF);
+    if (any_lane<T>(L, L.done)) retire_pass<T>(P, L, th, EF);
     GPCG_PHASE(7);
     if (tid == 0 && !L.drained) {
       int need = 0;
@@ -705,7 +712,7 @@ __global__ void __launch_bounds__(NTHREADS, ZS ? 2 : FDPF_MIN_BLOCKS)
       if (tim) P.phase_cycles[8 + 2 * (size_t)L.scen[tid]] = global_ns();
     }
     __syncthreads();
-    init_pass<T>(P, L, th, V, EF);
+    init_pass<T>(P, L, th, EF);
     __syncthreads();
     if (tid < T) L.fresh[tid] = 0;
     GPCG_PHASE(0);
@@ -715,7 +722,7 @@ __global__ void __launch_bounds__(NTHREADS, ZS ? 2 : FDPF_MIN_BLOCKS)
     }
     // P half-step: mismatch + convergence test
     Vec<unsigned long long, LP> eP = vzero<unsigned long long, LP>(), eQ = eP;
-    mismatch_pass<T, VT, true, GEN>(P, MP, MQ, L, EF, V, r, eP, eQ, SW);
+    mismatch_pass<T, VT, true, GEN>(P, MP, MQ, L, EF, r, eP, eQ, SW);
     const Vec<unsigned long long, LP> bP = lane_max_bits<T, RS_ERRP>(L, eP);
     const Vec<unsigned long long, LP> bQ = lane_max_bits<T, RS_ERRQ>(L, eQ);
     if (g.rs == 0) {
@@ -773,18 +780,18 @@ __global__ void __launch_bounds__(NTHREADS, ZS ? 2 : FDPF_MIN_BLOCKS)
     if (!more) continue;
     pcg_solve<T, VT, true, GEN>(P, MP, L, x, r, p, q, z, L.raP, L.rbP, L.wP, L.inP);
     GPCG_PHASE(2);
-    update_pass<T, VT, true, GEN>(MP, L, x, p, th, V, EF, SW);
+    update_pass<T, VT, true, GEN>(MP, L, x, p, th, EF, SW);
     __syncthreads();
     GPCG_PHASE(3);
     // Q half-step
     Vec<unsigned long long, LP> d0 = vzero<unsigned long long, LP>(), d1 = d0;
-    mismatch_pass<T, VT, false, GEN>(P, MP, MQ, L, EF, V, r, d0, d1, SW);
+    mismatch_pass<T, VT, false, GEN>(P, MP, MQ, L, EF, r, d0, d1, SW);
     __syncthreads();
     GPCG_PHASE(4);
     pcg_solve<T, VT, true, GEN>(P, MQ, L, x, r, p, q, z, L.raQ, L.rbQ, L.wQ, L.inQ,
                                 MQ.c ? L.cl : nullptr, SW);
     GPCG_PHASE(5);
-    update_pass<T, VT, false, GEN>(MQ, L, x, p, th, V, EF, SW);
+    update_pass<T, VT, false, GEN>(MQ, L, x, p, th, EF, SW);
     if (g.rs == 0)
 #pragma unroll
       for (int j = 0; j < LP; ++j)
