@@ -126,8 +126,10 @@ FP64_PEAK_GOPS = 625.0  # nominal 1.25 TFLOP/s of GB300 with an FMA as 2 FLOP
 # DRAM bytes per launch of the N-1 kernel on the default grid10k workload
 # (dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture of the
 # timed screens, taken by hand and recorded here), valid only for the kernel
-# sources with this digest; the bench line labels it as such.
-KERNEL_TRAFFIC = {"sha256": "ac7698b4de57d49b53789da9bd22a78f96fb8bae642a034641f89474a8f722a3", "bytes": 273.82e9}
+# sources with this digest and the launch shape it was taken with; the bench
+# line labels it as such.
+KERNEL_TRAFFIC = {"sha256": "7136ee4ce5d3f18b853f8f30b799c0b55a58d8eae23bbcdb4f1a7f1372015eac", "bytes": 190.13e9,
+                  "knobs": {"tile": 2, "ctas_per_sm": 5, "tail_rows": [241, 236]}}
 KERNEL_SOURCES = ("fdpf.cu", "fdpf_kernel.cuh", "fdpf_ops.cuh", "fdpf.h", "common.cuh")
 
 
@@ -331,8 +333,10 @@ def run_gpcg(args):
     default_workload = (args.config == "grid10k" and args.precision == "fp32" and
                         args.xfmr_frac == 0 and args.chunk <= 0 and args.load_scale <= 0 and
                         args.precond == "exact" and args.n_outages <= 0)
-    traffic = (KERNEL_TRAFFIC["bytes"] if default_workload and
-               kernel_digest() == KERNEL_TRAFFIC["sha256"] else None)
+    shape = {"tile": info["tile"], "ctas_per_sm": info["ctas_per_sm"],
+             "tail_rows": [info["tail_rows_p"], info["tail_rows_q"]]}
+    traffic = (KERNEL_TRAFFIC["bytes"] if default_workload and shape == KERNEL_TRAFFIC["knobs"]
+               and kernel_digest() == KERNEL_TRAFFIC["sha256"] else None)
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic,
             "traffic_source": ("recorded ncu capture of these kernel sources" if traffic

@@ -162,16 +162,18 @@ typedef struct {
 
 /* The autotuner (options left at 0) runs on the first batched screen of a
  * context, and again when the number of scenarios of a call moves to another
- * power of two.  It screens probes of the call's first outages (at least
- * 1,024, or twice the scenarios the candidate keeps in flight, at most the
- * call's) and keeps the fastest in scenarios per second: first the tile width
- * (2, 4, 8), then the tiles per SM, then the dense tail (248, 128, 64 rows or
- * none).  Choices are cached for the process, keyed by the device (SM count,
- * compute capability), the grid's sizes (buses, branches, nonzeros of B', B''
- * and their factors), precision, preconditioner, kernel kind and the power of
- * two of the scenario count; a context whose key is cached takes the cached
- * choice without probing.  Every choice gives the same results up to the
- * rounding of the inner solve. */
+ * power of two.  Every candidate screens the same probe of the call's
+ * outages (at least 1,024, or three times the most scenarios a candidate
+ * keeps in flight, at most all of the call's, taken at an even stride from
+ * the call's scheduling order); the fastest is kept, a candidate replacing
+ * the one before it only when 3 % faster: first the tile width (2, 4, 8),
+ * then the tiles per SM, then the dense tail (248, 128, 64 rows or none).  Choices are cached
+ * for the process, keyed by the device (SM count, compute capability), the
+ * grid's sizes (buses, branches, nonzeros of B', B'' and their factors),
+ * precision, preconditioner, kernel kind and the power of two of the
+ * scenario count; a context whose key is cached takes the cached choice
+ * without probing.  Every choice gives the same results up to the rounding
+ * of the inner solve. */
 
 /* Sizes of the structures built by gpcg_create. */
 typedef struct {

@@ -213,6 +213,7 @@ struct gpcg_ctx {
   // per-call buffers
   int32_t *d_outages = nullptr, *d_lo = nullptr, *d_cnt = nullptr, *d_nogen = nullptr,
           *d_order = nullptr, *d_genbus = nullptr;
+  int32_t* d_porder = nullptr;  // the autotuner's probe: a strided subset of d_order
   std::vector<double> base_flow;  // |P_ij| of the base case: scheduling priority
   double* d_coef = nullptr;
   size_t sc_cap = 0;
@@ -566,7 +567,7 @@ static void destroy(gpcg_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   cudaFree(c->d_outages); cudaFree(c->d_lo); cudaFree(c->d_cnt); cudaFree(c->d_nogen);
-  cudaFree(c->d_coef); cudaFree(c->d_order); cudaFree(c->d_genbus);
+  cudaFree(c->d_coef); cudaFree(c->d_order); cudaFree(c->d_genbus); cudaFree(c->d_porder);
   delete c;
 }
 
@@ -967,7 +968,8 @@ static gpcg_status ensure_scen(gpcg_ctx* c, size_t S) {
   if (S <= c->sc_cap) return GPCG_OK;
   drop_graph(c);
   cudaFree(c->d_outages); cudaFree(c->d_lo); cudaFree(c->d_cnt); cudaFree(c->d_nogen);
-  cudaFree(c->d_coef); cudaFree(c->d_order); cudaFree(c->d_genbus);
+  cudaFree(c->d_coef); cudaFree(c->d_order); cudaFree(c->d_genbus); cudaFree(c->d_porder);
+  c->d_porder = nullptr;
   c->d_outages = c->d_lo = c->d_cnt = c->d_nogen = c->d_order = c->d_genbus = nullptr;
   c->d_coef = nullptr;
   c->sc_cap = 0;
@@ -979,6 +981,7 @@ static gpcg_status ensure_scen(gpcg_ctx* c, size_t S) {
   CUDA_TRY(cudaMalloc(&c->d_coef, cap * 8));
   CUDA_TRY(cudaMalloc(&c->d_order, cap * 4));
   CUDA_TRY(cudaMalloc(&c->d_genbus, cap * 4));
+  CUDA_TRY(cudaMalloc(&c->d_porder, cap * 4));
   c->sc_cap = cap;
   return GPCG_OK;
 }
@@ -1337,8 +1340,25 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
         if (it != g_tune_cache.end()) { got = it->second; hit = true; }
       }
       if (!hit) {
-        // probes of the call's first outages: each candidate screens at
-        // least 1,024 of them, or twice the scenarios it keeps in flight
+        auto max_ps = [&](int t) { return std::max(1, blocks(t, use_zs(t))); };
+        std::vector<int> tiles = c->opt.tile ? std::vector<int>{c->opt.tile}
+                                             : std::vector<int>{2, 4, 8};
+        if (ext)
+          for (int& t : tiles) t = std::min(t, 8);
+        // the probe every candidate screens: at least 1,024 outages, or three
+        // times the most scenarios a candidate keeps in flight (at most the
+        // call's), taken at an even stride from the call's scheduling order,
+        // so that it mixes light and heavy scenarios as the call does and
+        // every candidate does the same work
+        size_t lanes = 0;
+        for (int t : tiles)
+          lanes = std::max(lanes, (size_t)t * (c->opt.ctas_per_sm ? c->opt.ctas_per_sm
+                                                                  : max_ps(t)) * c->num_sms);
+        const int np = (int)std::min(S, std::max<size_t>(1024, 3 * lanes));
+        std::vector<int32_t> po(np);
+        for (int k = 0; k < np; ++k) po[k] = order[(size_t)k * S / np];
+        CUDA_TRY(cudaMemcpyAsync(c->d_porder, po.data(), (size_t)np * 4,
+                                 cudaMemcpyHostToDevice, st));
         CUDA_TRY(enqueue_islands(st));
         auto rate = [&](int t, int ps, int cap, bool timed, double* out) -> gpcg_status {
           gpcg_status r = set_tail(c, cap);
@@ -1346,11 +1366,11 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
           FdpfParams Q = base_params(c);
           Q.sc = P.sc;
           Q.th0 = P.th0; Q.V0 = P.V0; Q.c0 = P.c0; Q.s0 = P.s0;
-          const size_t want = timed ? std::max<size_t>(1024, (size_t)2 * t * ps * c->num_sms)
-                                    : (size_t)t * c->num_sms;
-          const int np = (int)std::min(S, want);
-          Q.S = np;
-          Q.n_tiles = (np + t - 1) / t;
+          // untimed: the first launch of a kernel variant, one tile per SM
+          const int nq = timed ? np : std::min(np, t * c->num_sms);
+          Q.S = nq;
+          Q.n_tiles = (nq + t - 1) / t;
+          Q.order = c->d_porder;
           const bool z = use_zs(t);
           const int sl = std::max(1, std::min(Q.n_tiles, c->num_sms * ps));
           CUDA_TRY(cudaEventRecord(c->ev[3], st));
@@ -1361,16 +1381,15 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
           CUDA_TRY(cudaEventSynchronize(c->ev[2]));
           float ms = 0.f;
           CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[3], c->ev[2]));
-          *out = np / std::max(ms, 1e-3f);  // scenarios per ms
+          *out = nq / std::max(ms, 1e-3f);  // scenarios per ms
           return GPCG_OK;
         };
-        auto max_ps = [&](int t) { return std::max(1, blocks(t, use_zs(t))); };
         const int cap0 = c->opt.tail_rows > 0 ? c->opt.tail_rows
                          : (c->opt.tail_rows < 0 ? 0 : TAIL_ROWS);
-        std::vector<int> tiles = c->opt.tile ? std::vector<int>{c->opt.tile}
-                                             : std::vector<int>{2, 4, 8};
-        if (ext)
-          for (int& t : tiles) t = std::min(t, 8);
+        // a candidate replaces the one before it (narrower tiles, more tiles
+        // per SM, the wider tail) only when it is 3 % faster: probes are
+        // short, and their timing noise must not move the choice
+        constexpr double MARGIN = 1.03;
         // (a) the tile width, at the most tiles per SM and the widest tail
         double best = -1.0;
         int bT = tiles[0], bP = 0, bC = cap0;
@@ -1380,7 +1399,7 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
           gpcg_status r = rate(t, ps, cap0, false, &v);  // first launch of the variant: untimed
           if (r == GPCG_OK) r = rate(t, ps, cap0, true, &v);
           if (r != GPCG_OK) { cleanup(); return r; }
-          if (v > best) { best = v; bT = t; bP = ps; }
+          if (v > best * MARGIN) { best = v; bT = t; bP = ps; }
         }
         // (b) tiles per SM: the occupancy maximum and the two counts below it
         if (!c->opt.ctas_per_sm)
@@ -1388,7 +1407,7 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
             double v = 0.0;
             gpcg_status r = rate(bT, ps, cap0, true, &v);
             if (r != GPCG_OK) { cleanup(); return r; }
-            if (v > best) { best = v; bP = ps; }
+            if (v > best * MARGIN) { best = v; bP = ps; }
           }
         // (c) the dense tail: 248, 128, 64 rows or none
         if (!c->opt.tail_rows)
@@ -1396,7 +1415,7 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
             double v = 0.0;
             gpcg_status r = rate(bT, bP, cap, true, &v);
             if (r != GPCG_OK) { cleanup(); return r; }
-            if (v > best) { best = v; bC = cap; }
+            if (v > best * MARGIN) { best = v; bC = cap; }
           }
         got = TuneChoice{bT, bP, bC};
         std::lock_guard<std::mutex> lk(g_tune_mu);
