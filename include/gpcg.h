@@ -65,10 +65,15 @@ enum {
   GPCG_SCEN_ISLAND_NO_GEN = 3,  /* converged, but the main island had no
                                    generator to take the re-dispatch: the
                                    slack absorbed it */
-  GPCG_SCEN_QLIM_OVERFLOW = 4   /* reactive limits: more PV buses had to turn
-                                   PQ than a scenario can hold (four rows,
-                                   a tripped generator's bus included) */
+  GPCG_SCEN_QLIM_OVERFLOW = 4   /* reactive limits: more buses had to be
+                                   held at a limit at once than a scenario
+                                   can hold (GPCG_MAX_EXT_ROWS rows, a tripped
+                                   generator's bus included) */
 };
+
+/* B'' rows a scenario can add beyond the base case's PQ buses: a tripped
+ * generator's bus and PV buses held at a reactive limit. */
+#define GPCG_MAX_EXT_ROWS 8
 
 enum { GPCG_PQ = 0, GPCG_PV = 1, GPCG_SLACK = 2 };        /* bus_type */
 
@@ -111,10 +116,14 @@ enum {
  * Reactive limits (Q_min, Q_max; the paper models none): a PV generator's
  * output is Q(V) - Q_sched at its bus.  When a scenario has converged, every
  * PV bus whose generator is outside its limits turns PQ with the generator
- * held at the violated limit (Q_sched + Q_max or Q_min), B'' gains its row,
- * and the iteration goes on from there; a bus never turns back.  A scenario
- * holds at most four such rows (GPCG_SCEN_QLIM_OVERFLOW beyond).  The base
- * case must be within the limits (gpcg_base_solve fails otherwise). */
+ * held at the violated limit (Q_sched + Q_max or Q_min), B'' gains its row;
+ * at the same check every held bus whose |V| has passed its set point (above
+ * it at Q_max, below it at Q_min) turns back PV at the set point; the
+ * iteration then goes on from the mismatch of that state.  At the result
+ * every PV generator is within its limits and every held one on its side of
+ * the set point.  A scenario holds at most GPCG_MAX_EXT_ROWS such rows at
+ * once (GPCG_SCEN_QLIM_OVERFLOW beyond).  The base case must be within the
+ * limits (gpcg_base_solve fails otherwise). */
 typedef struct {
   int32_t n_bus;
   int32_t n_branch;

@@ -31,8 +31,11 @@ none, this is the usual enforcement): when the iteration has converged, the
 generator output a PV bus needs, Q_g = Q(V) - Q_sched = -dQ, is compared
 with its limits; every PV bus outside them becomes a PQ bus whose generator
 is held at the violated limit (Q_sched += Q_max or Q_min), B'' gains its row,
-and the iteration continues from the current state.  A bus never switches
-back.  The result converges with every remaining PV bus within its limits.
+and the iteration continues from the current state.  At the same check a
+bus held at Q_max whose |V| has risen above its set point (or held at Q_min,
+fallen below it) turns back PV at the set point: its generator can hold the
+set point within its limits again.  The result converges with every PV bus
+within its limits and every held bus on its side of the set point.
 The paper gives no stopping rule for a diverging case; here a run is
 declared diverged when the mismatch is not finite, exceeds DIVERGE_LIMIT, or
 (for warm-started scenarios) has grown to DIVERGE_GROWTH times the smallest
@@ -189,15 +192,26 @@ def limit_violations(cand, dQ, Q_min, Q_max):
     return cand[qg > Q_max[cand]], cand[qg < Q_min[cand]]
 
 
+def returns_to_pv(held, V, V_set):
+    """Buses held at a reactive limit (``held``: bus -> +1 at Q_max, -1 at
+    Q_min) whose generator can hold the set point again, in bus order: |V|
+    above the set point at Q_max (less reactive output would do), below it at
+    Q_min."""
+    return sorted(b for b, side in held.items()
+                  if (side > 0 and V[b] > V_set[b]) or (side < 0 and V[b] < V_set[b]))
+
+
 def fdpf(grid, in_service, active, P_sched, theta0, V0, tol, max_outer, growth_rule=True,
-         switched=None):
+         switched=None, returned=None, held_count=None):
     """Fast-decoupled power flow on the buses marked ``active``.
 
     ``active`` excludes islanded buses (they keep theta = V = 0).  Returns
     (theta, V, outer_iterations, status, final_max_mismatch).  With reactive
     limits on the grid, the buses switched to PQ are appended to the list
     ``switched`` (when given) in the order they switched, lowest index first
-    within one switch.
+    within one switch; the buses that turned back PV to ``returned``; and
+    after every switch the number of buses then held at a limit to
+    ``held_count``.
     """
     n = grid.n_bus
     bt = grid.bus_type.copy()
@@ -215,6 +229,7 @@ def fdpf(grid, in_service, active, P_sched, theta0, V0, tol, max_outer, growth_r
     theta = np.where(active, theta0, 0.0).astype(np.float64)
     V = np.where(active, V0, 0.0).astype(np.float64)
     Q_sched = grid.Q_sched.astype(np.float64).copy()
+    held = {}  # bus -> +1 held at Q_max, -1 held at Q_min
     k = 0
     best = np.inf
     while True:
@@ -227,13 +242,25 @@ def fdpf(grid, in_service, active, P_sched, theta0, V0, tol, max_outer, growth_r
         if err <= tol:
             if qlim:
                 hi, lo = limit_violations(np.flatnonzero(active & (bt == PV)), dQ, Q_min, Q_max)
-                if hi.size or lo.size:
+                back = returns_to_pv(held, V, grid.V_set)
+                if hi.size or lo.size or back:
+                    for b in back:
+                        bt[b] = PV
+                        Q_sched[b] = grid.Q_sched[b]
+                        V[b] = grid.V_set[b]
+                        del held[b]
                     Q_sched[hi] += Q_max[hi]
                     Q_sched[lo] += Q_min[lo]
+                    held.update({int(b): 1 for b in hi})
+                    held.update({int(b): -1 for b in lo})
                     sw = np.sort(np.concatenate([hi, lo]))
                     bt[sw] = PQ
                     if switched is not None:
                         switched.extend(int(b) for b in sw)
+                    if returned is not None:
+                        returned.extend(back)
+                    if held_count is not None:
+                        held_count.append(len(held))
                     pq = np.flatnonzero(active & (bt == PQ))
                     solQ = DirectSolver(bdprime(n, grid.f, grid.t, grid.r, grid.x, on, pq, tap))
                     best = np.inf  # the switch raises the mismatch on purpose

@@ -41,9 +41,9 @@ def outage_setup(grid, l):
 def solve_outage(grid, theta0, V0, l, tol, max_outer):
     on, label, isl, P, no_gen = outage_setup(grid, l)
     active = ~isl
-    switched = []
+    switched, returned, held = [], [], []
     theta, V, k, status, err = fdpf(grid, on, active, P, theta0, V0, tol, max_outer,
-                                    switched=switched)
+                                    switched=switched, returned=returned, held_count=held)
     live = on & active[grid.f] & active[grid.t]
     Pf, Pt = branch_flows(grid.f, grid.t, grid.r, grid.x, live, theta, V, grid.tap)
     loading = np.maximum(np.abs(Pf), np.abs(Pt)) / grid.rating
@@ -52,7 +52,8 @@ def solve_outage(grid, theta0, V0, l, tol, max_outer):
     return dict(theta=theta, V=V, flow=Pf, flow_to=Pt, label=label, outer=k,
                 status=status, max_loading=float(loading.max(initial=0.0)),
                 n_overload=int((loading > 1.0).sum()), err=err,
-                islanded=bool(isl.any()), n_switched=len(switched))
+                islanded=bool(isl.any()), n_switched=len(switched),
+                n_returned=len(returned), n_held=max(held, default=0))
 
 
 def scenario_mismatch(grid, l, theta, V):
@@ -88,9 +89,9 @@ def solve_generator_outage(grid, theta0, V0, k, tol, max_outer):
     g, no_gen = generator_setup(grid, k)
     on = np.ones(g.n_branch, dtype=bool)
     active = np.ones(g.n_bus, dtype=bool)
-    switched = []
+    switched, returned, held = [], [], []
     theta, V, it, status, err = fdpf(g, on, active, g.P_sched, theta0, V0, tol, max_outer,
-                                     switched=switched)
+                                     switched=switched, returned=returned, held_count=held)
     Pf, Pt = branch_flows(g.f, g.t, g.r, g.x, on, theta, V, g.tap)
     loading = np.maximum(np.abs(Pf), np.abs(Pt)) / g.rating
     if status == STATUS_OK and no_gen:
@@ -99,7 +100,8 @@ def solve_generator_outage(grid, theta0, V0, k, tol, max_outer):
                 label=np.zeros(g.n_bus, dtype=np.int32), outer=it, status=status,
                 max_loading=float(loading.max(initial=0.0)),
                 n_overload=int((loading > 1.0).sum()), err=err, islanded=False,
-                n_switched=len(switched))
+                n_switched=len(switched), n_returned=len(returned),
+                n_held=max(held, default=0))
 
 
 def generator_mismatch(grid, k, theta, V):
@@ -142,7 +144,8 @@ def n1_screen(grid, theta0, V0, outages, tol=1e-4, max_outer=50, processes=None,
         out[key] = np.stack([r[key] for r in res]) if S else np.zeros((0, 0))
     for key, dt in (("outer", np.int32), ("status", np.int32),
                     ("max_loading", np.float64), ("n_overload", np.int32),
-                    ("err", np.float64), ("islanded", bool), ("n_switched", np.int32)):
+                    ("err", np.float64), ("islanded", bool), ("n_switched", np.int32),
+                    ("n_returned", np.int32), ("n_held", np.int32)):
         out[key] = np.asarray([r[key] for r in res], dtype=dt)
     out["processes"] = processes
     return out

@@ -20,6 +20,7 @@ PLAIN_FP64, BATCHED_FP32, BATCHED_FP64, BATCHED_FP32_F16 = 0, 1, 2, 3
 PRECOND_IC0, PRECOND_JACOBI, PRECOND_EXACT = 0, 1, 2
 SCEN_OK, SCEN_MAXITER, SCEN_DIVERGED, SCEN_ISLAND_NO_GEN, SCEN_QLIM_OVERFLOW = 0, 1, 2, 3, 4
 MAX_TAIL_ROWS = 248  # GPCG_MAX_TAIL_ROWS: largest dense tail of a factor (rows)
+MAX_EXT_ROWS = 8  # GPCG_MAX_EXT_ROWS: B'' rows a scenario can add (held buses, tripped one)
 
 
 class GPCGError(RuntimeError):

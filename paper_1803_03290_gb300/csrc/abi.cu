@@ -1163,6 +1163,9 @@ struct TuneChoice {
 static std::mutex g_tune_mu;
 static std::map<std::vector<long long>, TuneChoice> g_tune_cache;
 
+static_assert(KX == GPCG_MAX_EXT_ROWS, "extension rows of the kernel and of the C ABI");
+static_assert(TAIL_ROWS >= GPCG_MAX_TAIL_ROWS, "the kernel's tail buffer holds the largest tail");
+
 static std::vector<long long> tune_key(const gpcg_ctx* c, bool ext, int bucket) {
   int major = 0, minor = 0;
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, c->device);
@@ -1366,11 +1369,12 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
           FdpfParams Q = base_params(c);
           Q.sc = P.sc;
           Q.th0 = P.th0; Q.V0 = P.V0; Q.c0 = P.c0; Q.s0 = P.s0;
-          // untimed: the first launch of a kernel variant, one tile per SM
-          const int nq = timed ? np : std::min(np, t * c->num_sms);
+          // untimed: the first launch of a kernel variant, one tile of the
+          // probe's lightest scenarios (the end of the scheduling order)
+          const int nq = timed ? np : std::min(np, t);
           Q.S = nq;
           Q.n_tiles = (nq + t - 1) / t;
-          Q.order = c->d_porder;
+          Q.order = c->d_porder + (np - nq);
           const bool z = use_zs(t);
           const int sl = std::max(1, std::min(Q.n_tiles, c->num_sms * ps));
           CUDA_TRY(cudaEventRecord(c->ev[3], st));

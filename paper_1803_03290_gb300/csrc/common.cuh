@@ -101,8 +101,9 @@ struct DevMatT {
 };
 
 // Extension rows a lane may carry at once (see Ext in fdpf_ops.cuh): a
-// tripped generator's bus and PV buses switched to PQ at a reactive limit.
-constexpr int KX = 4;
+// tripped generator's bus and PV buses switched to PQ at a reactive limit
+// (GPCG_MAX_EXT_ROWS of the C ABI).
+constexpr int KX = 8;
 
 // What the islanding pass leaves for each scenario.
 struct ScenInfo {

@@ -226,9 +226,10 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
         const double pgl = tr ? 0.0 : pg;
         bool xe = false;
         double qx = qs;
+        int xr = -1;  // the bus's extension row
         if (GEN && WITH_P)
           for (int s = 0; s < SW->nx[ln]; ++s)
-            if (SW->xb[ln][s] == i) { xe = true; qx = SW->xq[ln][s]; }
+            if (SW->xb[ln][s] == i) { xe = true; qx = SW->xq[ln][s]; xr = s; }
         if (j ? w1 : w0) {
           // the base-case state here: the base case is within the reactive limits
           const double dP = fma(L.coef[ln], pgl, __ldg(P.r0P + i)) - (tr ? Pgr : 0.0);
@@ -269,8 +270,17 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
               if (at < KX) {
                 SW->cb[ln][at] = i;
                 SW->cq[ln][at] = qs + (qg > hi ? hi : lo);
+                SW->cs[ln][at] = qg > hi ? 1 : -1;
               }
             }
+          }
+          if (GEN && xe && SW->xs[ln][xr] != 0) {
+            // a generator held at Q_max whose |V| is above its set point (at
+            // Q_min, below) can hold the set point again: back to PV
+            const double vm = sqrt(fma(ei, ei, fi * fi)), vs = __ldg(G.V_set + i);
+            const int side = SW->xs[ln][xr];
+            if ((side > 0 && vm > vs) || (side < 0 && vm < vs))
+              atomicOr(&SW->bk[ln], 1u << xr);
           }
           res = to_vt<VT>(dP) * iv;
         } else {
@@ -453,8 +463,11 @@ __device__ __forceinline__ void setup_lane(const FdpfParams& P, const DevMatT<VT
     if (L.gb[ln] >= 0) {
       SW->xb[ln][0] = L.gb[ln];
       SW->xq[ln][0] = G.Q_sched[L.gb[ln]];
+      SW->xs[ln][0] = 0;
     }
     SW->nc[ln] = 0;
+    SW->bk[ln] = 0u;
+    SW->skip[ln] = 0;
   }
   L.active[ln] = 1;
   L.outer[ln] = 0;
@@ -674,6 +687,8 @@ __global__ void __launch_bounds__(NTHREADS, ZS ? 2 : FDPF_MIN_BLOCKS)
     if constexpr (GEN) {
       SW->nx[tid] = 0;
       SW->nc[tid] = 0;
+      SW->bk[tid] = 0u;
+      SW->skip[tid] = 0;
     }
     L.lo[tid] = L.cnt[tid] = 0;
   }
@@ -715,6 +730,14 @@ __global__ void __launch_bounds__(NTHREADS, ZS ? 2 : FDPF_MIN_BLOCKS)
     init_pass<T>(P, L, th, EF);
     __syncthreads();
     if (tid < T) L.fresh[tid] = 0;
+    if constexpr (GEN) {
+      // lanes that sat out the last outer iteration after a switch
+      if (tid < T && SW->skip[tid]) {
+        SW->skip[tid] = 0;
+        L.active[tid] = 1;
+      }
+      __syncthreads();
+    }
     GPCG_PHASE(0);
     if (!any_lane<T>(L, L.active)) {
       if (L.drained) break;
@@ -740,15 +763,35 @@ __global__ void __launch_bounds__(NTHREADS, ZS ? 2 : FDPF_MIN_BLOCKS)
         else if (e2 <= P.tol) st = 0;
         else if (L.outer[ln] >= P.max_outer) st = 1;
         L.best[ln] = fmin(L.best[ln], e2);
-        if (GEN && st == 0 && SW->nc[ln] > 0) {
-          // converged with PV generators outside their reactive limits: they
-          // turn PQ at the violated limit (in bus order) and the iteration
-          // goes on; the base case must be within its limits, and a lane
+        if (GEN && st == 0 && (SW->nc[ln] > 0 || SW->bk[ln] != 0u)) {
+          // converged with PV generators outside their reactive limits, or
+          // held ones able to hold their set point again: the latter turn
+          // back PV at the set point, the former PQ at the violated limit
+          // (in bus order), and the lane sits out the rest of this outer
+          // iteration, so the next starts from the mismatch of the new
+          // state; the base case must be within its limits, and a lane
           // holds at most KX extension rows
           const int nc = SW->nc[ln];
-          if (P.flat_start || SW->nx[ln] + nc > KX) {
+          const unsigned bk = SW->bk[ln];
+          if (P.flat_start || SW->nx[ln] - __popc(bk) + nc > KX) {
             st = 4;
           } else {
+            int w = 0;
+            for (int u = 0; u < SW->nx[ln]; ++u) {
+              if ((bk >> u) & 1u) {
+                // |V| back to the set point, the angle kept
+                const int b = SW->xb[ln][u];
+                double2* ef = reinterpret_cast<double2*>(EF + ef_at<T>(b, ln));
+                const double2 v = ef[0];
+                const double k = P.G.V_set[b] / sqrt(fma(v.x, v.x, v.y * v.y));
+                ef[0] = make_double2(v.x * k, v.y * k);
+                continue;
+              }
+              SW->xb[ln][w] = SW->xb[ln][u];
+              SW->xq[ln][w] = SW->xq[ln][u];
+              SW->xs[ln][w] = SW->xs[ln][u];
+              ++w;
+            }
             for (int u = 1; u < nc; ++u)
               for (int v = u; v > 0 && SW->cb[ln][v - 1] > SW->cb[ln][v]; --v) {
                 const int tb = SW->cb[ln][v];
@@ -757,21 +800,31 @@ __global__ void __launch_bounds__(NTHREADS, ZS ? 2 : FDPF_MIN_BLOCKS)
                 const double tq = SW->cq[ln][v];
                 SW->cq[ln][v] = SW->cq[ln][v - 1];
                 SW->cq[ln][v - 1] = tq;
+                const int ts = SW->cs[ln][v];
+                SW->cs[ln][v] = SW->cs[ln][v - 1];
+                SW->cs[ln][v - 1] = ts;
               }
             for (int u = 0; u < nc; ++u) {
-              SW->xb[ln][SW->nx[ln] + u] = SW->cb[ln][u];
-              SW->xq[ln][SW->nx[ln] + u] = SW->cq[ln][u];
+              SW->xb[ln][w + u] = SW->cb[ln][u];
+              SW->xq[ln][w + u] = SW->cq[ln][u];
+              SW->xs[ln][w + u] = SW->cs[ln][u];
             }
-            SW->nx[ln] += nc;
+            SW->nx[ln] = w + nc;
             L.best[ln] = INFINITY;  // the switch raises the mismatch on purpose
+            SW->skip[ln] = 1;
             st = -1;
           }
         }
-        if constexpr (GEN) SW->nc[ln] = 0;
+        if constexpr (GEN) {
+          SW->nc[ln] = 0;
+          SW->bk[ln] = 0u;
+        }
         if (st >= 0) {
           L.status[ln] = st;
           L.active[ln] = 0;
           L.done[ln] = 1;
+        } else if (GEN && SW->skip[ln]) {
+          L.active[ln] = 0;  // back at the top of the next outer iteration
         }
       }
     }

@@ -203,14 +203,20 @@ struct Geo {
 // Per-lane B'' extension rows (the kernel with extension rows keeps this
 // in shared memory of its own): the tripped generator's bus and PV buses
 // switched to PQ at a reactive limit, with the reactive injection each now
-// holds; and the PV buses the last P mismatch found outside their limits
-// (nc may exceed KX: only the first KX are kept), with their new injection.
+// holds and the limit it is held at (xs: +1 Q_max, -1 Q_min, 0 the tripped
+// bus); the PV buses the last P mismatch found outside their limits (nc may
+// exceed KX: only the first KX are kept), with their new injection and
+// limit; the extension rows whose bus can hold its set point again (bk, a
+// bit per row); and the lanes that sit out the rest of an outer iteration
+// after a switch (skip), so that the next one starts from a fresh mismatch.
 template <int T>
 struct SwitchState {
-  int nx[T], xb[T][KX];
+  int nx[T], xb[T][KX], xs[T][KX];
   double xq[T][KX];
-  int nc[T], cb[T][KX];
+  int nc[T], cb[T][KX], cs[T][KX];
   double cq[T][KX];
+  unsigned bk[T];
+  int skip[T];
 };
 
 constexpr int NRED_SITES = 10;  // reduction sites with a buffer of their own

@@ -92,6 +92,7 @@ def test_binding_structs_follow_the_header():
     assert [k for k, _ in binding.Info._fields_] == _struct_fields("gpcg_info")
     src = open(os.path.join(ROOT, "include", "gpcg.h")).read()
     assert int(re.search(r"#define GPCG_MAX_TAIL_ROWS (\d+)", src).group(1)) == binding.MAX_TAIL_ROWS
+    assert int(re.search(r"#define GPCG_MAX_EXT_ROWS (\d+)", src).group(1)) == binding.MAX_EXT_ROWS
 
 
 @pytest.mark.parametrize("bad", [dict(tail_rows=-2), dict(tail_rows=249), dict(tile=3),

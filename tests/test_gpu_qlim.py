@@ -1,8 +1,8 @@
 """Reactive limits of the PV generators through the CUDA path against the
 CPU oracle: converged scenarios whose generators left their limits turn
-those buses PQ at the limit (B'' extension rows) and go on to the same
-state; a scenario that needs more rows than it holds reports
-QLIM_OVERFLOW."""
+those buses PQ at the limit (B'' extension rows), held ones whose |V| passed
+the set point turn back PV, and both go on to the same state; a scenario
+that needs more rows at once than it holds reports QLIM_OVERFLOW."""
 import numpy as np
 import pytest
 
@@ -13,29 +13,31 @@ from oracle import screen
 pytestmark = pytest.mark.gpu
 
 ANGLE_TOL = 1e-6
-KX = 4  # extension rows a scenario holds
+KX = gp.MAX_EXT_ROWS  # extension rows a scenario holds
 
 
 def expected_status(ref, cap):
     """The status the GPU must report for each scenario: the oracle's, except
-    that a scenario the oracle took through more than `cap` switches (whether
-    it then converged or not) overflows the rows a scenario holds."""
-    return np.where(ref["n_switched"] > cap, gp.SCEN_QLIM_OVERFLOW, ref["status"])
+    that a scenario in which the oracle held more than `cap` buses at their
+    limits at once (whether it then converged or not) overflows the rows a
+    scenario holds."""
+    return np.where(ref["n_held"] > cap, gp.SCEN_QLIM_OVERFLOW, ref["status"])
 
 
 def _check(res, ref, cap):
     """Every scenario's status and island labels against the oracle; the
     states of the scenarios both solve agree."""
-    sw, st = ref["n_switched"], ref["status"]
+    st = ref["status"]
     np.testing.assert_array_equal(res["status"], expected_status(ref, cap))
     np.testing.assert_array_equal(res["label"], ref["label"])
-    fit = (st == 0) & (sw <= cap)
+    fit = (st == 0) & (ref["n_held"] <= cap)
     assert fit.sum() > 0.8 * st.size
-    assert (fit & (sw > 0)).sum() >= 5          # the limits are exercised
+    assert (fit & (ref["n_switched"] > 0)).sum() >= 5   # the limits are exercised
+    assert (fit & (ref["n_returned"] > 0)).sum() >= 1   # and the way back to PV
     for k, tol in (("theta", ANGLE_TOL), ("V", ANGLE_TOL), ("flow", 10 * ANGLE_TOL),
                    ("max_loading", 10 * ANGLE_TOL)):
         np.testing.assert_allclose(res[k][fit], ref[k][fit], rtol=0, atol=tol)
-    assert ((st == 0) & (sw > cap)).any()       # the overflow is exercised
+    assert (ref["n_held"] > cap).any()          # the overflow is exercised
 
 
 @pytest.mark.parametrize("precision", [gp.BATCHED_FP32, gp.BATCHED_FP64])
@@ -67,7 +69,7 @@ def test_q_limits_generator_outages():
     # compared, failures included (the tripped bus holds one of the rows)
     np.testing.assert_array_equal(res["status"], expected_status(ref, KX - 1))
     assert (st != 0).sum() >= 1
-    fit = (st == 0) & (sw <= KX - 1)
+    fit = (st == 0) & (ref["n_held"] <= KX - 1)
     assert fit.sum() >= 8 and (fit & (sw > 0)).sum() >= 1
     for k in ("theta", "V"):
         np.testing.assert_allclose(res[k][fit], ref[k][fit], rtol=0, atol=ANGLE_TOL)

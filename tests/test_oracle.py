@@ -386,6 +386,61 @@ def test_q_limits_match_newton_and_hold(seed):
     np.testing.assert_allclose(V, Vn, atol=1e-9)
 
 
+def limit_complementarity(name, kind="branch"):
+    """Every N-1 scenario of a grid with reactive limits, in process (so that
+    a rule replaced in this process is the one used).  At each converged
+    state, for every PV generator of the main island (Q_g = Q(V) - Q_sched,
+    the output it needs): one still at its set point is within [Q_min, Q_max];
+    one off its set point is held at a limit, at Q_max only with |V| at or
+    below the set point and at Q_min only at or above it.  These are the
+    conditions under which no generator can switch either way.  Returns the
+    oracle's screen result."""
+    from gpu_common import grid, oracle_base
+    g = grid(name)
+    th0, V0 = oracle_base(name)
+    units = (np.arange(g.n_branch) if kind == "branch"
+             else np.flatnonzero(g.bus_type == 1)).astype(np.int32)
+    res = screen.n1_screen(g, th0, V0, units, tol=1e-10, max_outer=100, processes=1,
+                           kind="generator" if kind != "branch" else "branch")
+    for s in np.flatnonzero(res["status"] == pf.STATUS_OK):
+        if kind == "branch":
+            on, _, isl, P, _ = screen.outage_setup(g, int(units[s]))
+            h = g
+        else:
+            h, _ = screen.generator_setup(g, int(units[s]))
+            on, isl, P = np.ones(g.n_branch, bool), np.zeros(g.n_bus, bool), h.P_sched
+        live = on & ~isl[g.f] & ~isl[g.t]
+        yb = pf.ybus_entries(g.n_bus, g.f, g.t, g.r, g.x, g.b_sh, live, g.tap)
+        th, V = res["theta"][s], res["V"][s]
+        _, dQ = pf.mismatch(yb, P, g.Q_sched, th, V)
+        qg = -dQ
+        for b in np.flatnonzero((h.bus_type == 1) & ~isl):
+            if abs(V[b] - g.V_set[b]) <= 1e-9:
+                assert g.Q_min[b] - 1e-8 <= qg[b] <= g.Q_max[b] + 1e-8, (s, b)
+            elif abs(qg[b] - g.Q_max[b]) <= 1e-8:
+                assert V[b] <= g.V_set[b] + 1e-12, (s, b, "held at Q_max above its set point")
+            else:
+                assert abs(qg[b] - g.Q_min[b]) <= 1e-8, (s, b, "off its set point, at no limit")
+                assert V[b] >= g.V_set[b] - 1e-12, (s, b, "held at Q_min below its set point")
+    return res
+
+
+def test_limit_complementarity_every_outage_grid120():
+    """Branch outages of grid120 with reactive limits: enough converge, some
+    generator turns back PV on the way, and every converged state meets the
+    switching conditions."""
+    res = limit_complementarity("grid120_qlim")
+    ok = res["status"] == pf.STATUS_OK
+    assert ok.sum() >= 0.9 * ok.size
+    assert (ok & (res["n_returned"] > 0)).sum() >= 1
+    assert (ok & (res["n_switched"] > 0)).sum() >= 10
+
+
+def test_limit_complementarity_generator_outages_grid120():
+    res = limit_complementarity("grid120_qlim", kind="generator")
+    assert (res["status"] == pf.STATUS_OK).sum() >= 8
+
+
 # ----------------------------------------------- outage algebra (Sec. IV.B)
 def test_sherman_morrison_first_solve():
     """B'_s = B' - b a a^T (a = e_i - e_j): the solve with the re-formed

@@ -90,6 +90,25 @@ def test_limit_sign_flipped_is_caught(monkeypatch):
 
 
 
+def test_return_to_pv_side_flipped_is_caught(monkeypatch):
+    """A held generator sent back to PV on the wrong side of its set point
+    (at Q_max when |V| is below it)."""
+    def flipped(held, V, V_set):
+        return sorted(b for b, side in held.items()
+                      if (side > 0 and V[b] < V_set[b]) or (side < 0 and V[b] > V_set[b]))
+
+    monkeypatch.setattr(pf, "returns_to_pv", flipped)
+    with pytest.raises(AssertionError):
+        pins.test_limit_complementarity_every_outage_grid120()
+
+
+def test_no_return_to_pv_is_caught(monkeypatch):
+    """Held generators never sent back to PV (the earlier rule)."""
+    monkeypatch.setattr(pf, "returns_to_pv", lambda held, V, V_set: [])
+    with pytest.raises(AssertionError):
+        pins.test_limit_complementarity_every_outage_grid120()
+
+
 def test_equal_shares_redispatch_is_caught(monkeypatch):
     """The island's power split equally over the main generators instead of
     in proportion to their scheduled generation."""
