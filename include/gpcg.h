@@ -171,12 +171,13 @@ typedef struct {
 
 /* The autotuner (options left at 0) runs on the first batched screen of a
  * context, and again when the number of scenarios of a call moves to another
- * power of two.  Every candidate screens the same probe of the call's
- * outages (at least 1,024, or three times the most scenarios a candidate
- * keeps in flight, at most all of the call's, taken at an even stride from
- * the call's scheduling order); the fastest is kept, a candidate replacing
- * the one before it only when 3 % faster: first the tile width (2, 4, 8),
- * then the tiles per SM, then the dense tail (248, 128, 64 rows or none).  Choices are cached
+ * power of two.  Every candidate screens the same probe: all of the call's
+ * outages, or for calls of more than 16,384 (and more than eight times the
+ * most scenarios a candidate keeps in flight) that many taken at an even
+ * stride from the call's scheduling order; the fastest is kept, a candidate
+ * replacing the one before it only when 3 % faster: first the tile width
+ * (2, 4, 8), then the tiles per SM, then the dense tail (248, 128, 64 rows
+ * or none).  Choices are cached
  * for the process, keyed by the device (SM count, compute capability), the
  * grid's sizes (buses, branches, nonzeros of B', B'' and their factors),
  * precision, preconditioner, kernel kind and the power of two of the

@@ -1348,16 +1348,19 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
                                              : std::vector<int>{2, 4, 8};
         if (ext)
           for (int& t : tiles) t = std::min(t, 8);
-        // the probe every candidate screens: at least 1,024 outages, or three
-        // times the most scenarios a candidate keeps in flight (at most the
-        // call's), taken at an even stride from the call's scheduling order,
-        // so that it mixes light and heavy scenarios as the call does and
-        // every candidate does the same work
+        // the probe every candidate screens: the call's outages, or when
+        // there are more than 16,384 of them (and more than eight times the
+        // most scenarios a candidate keeps in flight) that many taken at an
+        // even stride from the call's scheduling order, so that it mixes
+        // light and heavy scenarios as the call does, every candidate does
+        // the same work, and the drain at the end of a persistent launch
+        // weighs as much as in the call (shorter probes favour fewer
+        // scenarios in flight, which the full call does not)
         size_t lanes = 0;
         for (int t : tiles)
           lanes = std::max(lanes, (size_t)t * (c->opt.ctas_per_sm ? c->opt.ctas_per_sm
                                                                   : max_ps(t)) * c->num_sms);
-        const int np = (int)std::min(S, std::max<size_t>(1024, 3 * lanes));
+        const int np = (int)std::min(S, std::max<size_t>(16384, 8 * lanes));
         std::vector<int32_t> po(np);
         for (int k = 0; k < np; ++k) po[k] = order[(size_t)k * S / np];
         CUDA_TRY(cudaMemcpyAsync(c->d_porder, po.data(), (size_t)np * 4,
