@@ -151,17 +151,20 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def bench_grid(args):
+def bench_grid(args, point=0):
     """The named workload's synthetic grid, with ``--xfmr-frac`` of its
     branches made transformers (drawn after the rest: the grid is otherwise
-    the same)."""
+    the same).  ``point`` > 0 is another operating point of the same grid:
+    every load scaled by 1 + 0.02 point (the rank's share of a multi-point
+    study when several GPUs run)."""
     from gridgen import CONFIGS, config_grid, make_grid
     lam = getattr(args, "load_scale", 0.0) or 0.0
-    if args.xfmr_frac <= 0 and lam <= 0:
+    if args.xfmr_frac <= 0 and lam <= 0 and point == 0:
         return config_grid(args.config)
     kw = dict(CONFIGS[args.config])
     if lam > 0:
         kw["load_scale"] = lam
+    kw["load_scale"] *= 1.0 + 0.02 * point
     g = make_grid(gen_share=1.0, xfmr_frac=args.xfmr_frac, **kw)
     g.meta["config"] = args.config
     return g
@@ -185,7 +188,10 @@ def run_gpcg(args):
     dev = torch.device("cuda", local)
     import paper_1803_03290_gb300 as gp
 
-    g = bench_grid(args)
+    # weak scaling over GPUs: rank r screens every outage of operating point
+    # r of the grid (its loads scaled by 1 + 0.02 r), so the units -- pairs of
+    # operating point and outage -- are sharded by point with no collective
+    g = bench_grid(args, rank if world > 1 else 0)
     prec = {"fp32": gp.BATCHED_FP32, "fp64": gp.BATCHED_FP64,
             "fp16f": gp.BATCHED_FP32_F16}[args.precision]
     pc = {"exact": gp.PRECOND_EXACT, "ic0": gp.PRECOND_IC0, "jacobi": gp.PRECOND_JACOBI}[args.precond]
@@ -369,7 +375,8 @@ def run_gpcg(args):
                                    f"outages{f' in chunks of {K}' if n_chunks > 1 else ''}"
                                    f"{f' on {NS} streams' if NS > 1 else ''}, "
                                    f"tol 1e-4 p.u., {args.precond} base-case preconditioner, "
-                                   f"{args.precision} inner PCG, FP64 mismatch/flows",
+                                   f"{args.precision} inner PCG, FP64 mismatch/flows"
+                                   f"{f'; {world} operating points (loads x 1 + 0.02 r), one per GPU' if world > 1 else ''}",
                        "n_bus": n, "n_branch": m, "scenarios": S, "tile": info["tile"],
                        "ctas_per_sm": info["ctas_per_sm"],
                        "tail_rows": [info["tail_rows_p"], info["tail_rows_q"]],
