@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import paper_1803_03290_gb300 as gp
-from gpu_common import grid, sample_outages, with_tight_ratings
+from gpu_common import check_every_dc_outage, grid, sample_outages, with_tight_ratings
 from oracle import dc
 
 pytestmark = pytest.mark.gpu
@@ -97,3 +97,43 @@ def test_dc_rejects_bad_input():
     with pytest.raises(gp.GPCGError):
         c.n1_dc_screen(np.array([0], dtype=np.int32))
     c.close()
+
+
+def _with_tight_dc_ratings(g, seed):
+    """Ratings U[1.0, 1.5] times each branch's DC base-case flow plus 1e-3
+    p.u. (the DC flows of the intact grid, B' theta = P with the slack's
+    angle 0), so that outages push the DC flows of their neighbours over."""
+    import scipy.sparse as sps
+    from scipy.sparse.linalg import spsolve
+    n = g.n_bus
+    w = 1.0 / g.x
+    B = sps.csr_matrix((np.r_[w, w, -w, -w], (np.r_[g.f, g.t, g.f, g.t], np.r_[g.f, g.t, g.t, g.f])),
+                       shape=(n, n))
+    keep = np.flatnonzero(g.bus_type != 2)
+    th = np.zeros(n)
+    th[keep] = spsolve(B[keep][:, keep].tocsc(), g.P_sched[keep])
+    f = w * (th[g.f] - th[g.t])
+    g = g.copy()
+    g.rating = np.abs(f) * np.random.default_rng(seed).uniform(1.0, 1.5, g.n_branch) + 1e-3
+    return g
+
+
+def test_dc_grid10k_every_outage(tmp_path):
+    """Every one of grid10k's 13,500 outages through the DC quick screen with
+    FP32 solves refined once in FP64, against the oracle's direct solves
+    scenario by scenario: statuses, angles within 1e-7 rad, flows within
+    1e-5 p.u., overload counts exactly where no branch is within 1e-5 of
+    its rating (ratings set just above the base-case flows)."""
+    g = _with_tight_dc_ratings(grid("grid10k"), seed=17)
+    c = gp.GPCG(g)
+    outages = np.arange(g.n_branch, dtype=np.int32)
+    res = c.n1_dc_screen(outages, outputs=("theta", "flow", "status", "n_overload"))
+    c.close()
+    ref = check_every_dc_outage(g, outages, res, tmp_path)
+    np.testing.assert_array_equal(res["status"], ref["status"])
+    assert ref["dtheta"].max() <= 1e-7, ref["dtheta"].max()
+    assert ref["dflow"].max() <= 1e-5, ref["dflow"].max()
+    clear = ref["ties"] == 0
+    np.testing.assert_array_equal(res["n_overload"][clear], ref["n_overload"][clear])
+    assert clear.sum() >= 0.95 * outages.size
+    assert (ref["n_overload"] > 0).sum() > 100
