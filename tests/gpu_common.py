@@ -142,47 +142,53 @@ def check_every_outage(g, th0, V0, outages, res, tol, tmpdir, max_outer=50, proc
 
 
 def _every_dc_outage_worker(args):
-    """One chunk of DC scenarios: the oracle's direct solves against the
-    GPU's angles and flows (max abs differences), its status, and its
+    """One chunk of DC scenarios: the oracle's direct solves against each
+    GPU run's angles and flows (max abs differences), its status, and its
     overload count with the branches within `tie` of their rating."""
     g, idx, outages, paths, tie = args
     from oracle import dc
-    th = np.load(paths["theta"], mmap_mode="r")
-    fl = np.load(paths["flow"], mmap_mode="r")
+    runs = {name: (np.load(p["theta"], mmap_mode="r"), np.load(p["flow"], mmap_mode="r"))
+            for name, p in paths.items()}
     rows = []
     for s in idx:
         r = dc.dc_screen(g, outages[s:s + 1])
         ld = np.abs(r["flow"][0]) / g.rating
-        rows.append((int(r["status"][0]), float(np.abs(r["theta"][0] - th[s]).max()),
-                     float(np.abs(r["flow"][0] - fl[s]).max()), int(r["n_overload"][0]),
-                     int((np.abs(ld - 1.0) <= tie).sum())))
+        diffs = {name: (float(np.abs(r["theta"][0] - th[s]).max()),
+                        float(np.abs(r["flow"][0] - fl[s]).max()))
+                 for name, (th, fl) in runs.items()}
+        rows.append((int(r["status"][0]), int(r["n_overload"][0]),
+                     int((np.abs(ld - 1.0) <= tie).sum()), diffs))
     return idx, rows
 
 
-def check_every_dc_outage(g, outages, res, tmpdir, tie=1e-5, processes=None):
-    """The DC oracle on every scenario of a GPU DC screen `res` (host
-    outputs theta, flow of `outages`) in a pool of host processes.  Returns
-    per scenario the oracle's status, the max angle and flow differences,
-    and the oracle's overload count with its number of near-ties."""
+def check_every_dc_outage(g, outages, runs, tmpdir, tie=1e-6, processes=None):
+    """The DC oracle on every scenario of GPU DC screens (`runs`: name ->
+    host outputs theta, flow of `outages`) in a pool of host processes.
+    Returns per scenario the oracle's status, overload count and number of
+    near-ties, and for each run the max angle and flow differences."""
     import multiprocessing as mp
     import os
     paths = {}
-    for k in ("theta", "flow"):
-        paths[k] = os.path.join(str(tmpdir), f"dc_{k}.npy")
-        np.save(paths[k], res[k])
+    for name, res in runs.items():
+        paths[name] = {}
+        for k in ("theta", "flow"):
+            paths[name][k] = os.path.join(str(tmpdir), f"dc_{name}_{k}.npy")
+            np.save(paths[name][k], res[k])
     S = len(outages)
     if processes is None:
         processes = len(os.sched_getaffinity(0))
     chunks = [c for c in np.array_split(np.arange(S), max(1, processes * 8)) if c.size]
     args = [(g, c, np.asarray(outages), paths, tie) for c in chunks]
-    out = {k: np.empty(S, dt) for k, dt in (("status", np.int32), ("dtheta", np.float64),
-                                           ("dflow", np.float64), ("n_overload", np.int32),
-                                           ("ties", np.int32))}
+    out = {"status": np.empty(S, np.int32), "n_overload": np.empty(S, np.int32),
+           "ties": np.empty(S, np.int32)}
+    for name in runs:
+        out[name] = {"dtheta": np.empty(S), "dflow": np.empty(S)}
     with mp.get_context("spawn").Pool(processes) as pool:
         for idx, rows in pool.imap_unordered(_every_dc_outage_worker, args):
-            for s, row in zip(idx, rows):
-                for k, v in zip(("status", "dtheta", "dflow", "n_overload", "ties"), row):
-                    out[k][s] = v
+            for s, (st, nov, ties, diffs) in zip(idx, rows):
+                out["status"][s], out["n_overload"][s], out["ties"][s] = st, nov, ties
+                for name, (dt, dfl) in diffs.items():
+                    out[name]["dtheta"][s], out[name]["dflow"][s] = dt, dfl
     return out
 
 
