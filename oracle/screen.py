@@ -16,6 +16,7 @@ leaves service and nothing is islanded.
 """
 from __future__ import annotations
 
+import contextlib
 import multiprocessing as mp
 import os
 
@@ -25,6 +26,29 @@ from .islands import components, island_mask
 from .powerflow import (STATUS_ISLAND_NO_GEN, STATUS_OK, branch_flows,
                         fdpf, mismatch, ybus_entries)
 from .redispatch import redispatch, redispatch_generator
+
+
+_BLAS_THREADS = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+@contextlib.contextmanager
+def worker_pool(processes):
+    """A pool of `processes` spawned workers whose linear algebra runs on one
+    thread each (the dense factorisations of small matrices would otherwise
+    start a BLAS thread per core in every worker)."""
+    saved = {k: os.environ.get(k) for k in _BLAS_THREADS}
+    for k in _BLAS_THREADS:
+        os.environ[k] = "1"
+    try:
+        pool = mp.get_context("spawn").Pool(processes)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    with pool:
+        yield pool
 
 
 def outage_setup(grid, l):
@@ -134,8 +158,7 @@ def n1_screen(grid, theta0, V0, outages, tol=1e-4, max_outer=50, processes=None,
         res = _worker((grid, theta0, V0, outages, tol, max_outer, kind))
     else:
         chunks = np.array_split(outages, processes * 4)
-        ctx = mp.get_context("spawn")
-        with ctx.Pool(processes) as pool:
+        with worker_pool(processes) as pool:
             parts = pool.map(_worker, [(grid, theta0, V0, c, tol, max_outer, kind)
                                        for c in chunks if c.size])
         res = [r for p in parts for r in p]

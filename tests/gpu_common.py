@@ -118,7 +118,6 @@ def check_every_outage(g, th0, V0, outages, res, tol, tmpdir, max_outer=50, proc
     labels are identical, the oracle's FP64 mismatch of the GPU's state (NaN
     where the GPU did not converge), and the oracle's overload count at the
     GPU's state with the number of branches within 1e-12 of their rating."""
-    import multiprocessing as mp
     import os
     paths = {}
     for k in ("theta", "V", "label", "status"):
@@ -134,7 +133,7 @@ def check_every_outage(g, th0, V0, outages, res, tol, tmpdir, max_outer=50, proc
     err = np.empty(S)
     nov = np.empty(S, np.int32)
     ties = np.empty(S, np.int32)
-    with mp.get_context("spawn").Pool(processes) as pool:
+    with screen.worker_pool(processes) as pool:
         for idx, rows in pool.imap_unordered(_every_outage_worker, args):
             for s, row in zip(idx, rows):
                 st[s], lab_ok[s], err[s], nov[s], ties[s] = row
@@ -166,7 +165,6 @@ def check_every_dc_outage(g, outages, runs, tmpdir, tie=1e-6, processes=None):
     host outputs theta, flow of `outages`) in a pool of host processes.
     Returns per scenario the oracle's status, overload count and number of
     near-ties, and for each run the max angle and flow differences."""
-    import multiprocessing as mp
     import os
     paths = {}
     for name, res in runs.items():
@@ -183,7 +181,7 @@ def check_every_dc_outage(g, outages, runs, tmpdir, tie=1e-6, processes=None):
            "ties": np.empty(S, np.int32)}
     for name in runs:
         out[name] = {"dtheta": np.empty(S), "dflow": np.empty(S)}
-    with mp.get_context("spawn").Pool(processes) as pool:
+    with screen.worker_pool(processes) as pool:
         for idx, rows in pool.imap_unordered(_every_dc_outage_worker, args):
             for s, (st, nov, ties, diffs) in zip(idx, rows):
                 out["status"][s], out["n_overload"][s], out["ties"][s] = st, nov, ties
