@@ -48,7 +48,8 @@ def test_every_outage_of_seeded_grids(name, precision, precond):
     g, outages, ref = _case(name)
     c = gp.GPCG(g, precision=precision, precond=precond, tol=1e-10, max_outer=100)
     c.base_solve()
-    res = c.n1_screen(outages)
+    res = c.n1_screen(outages, outputs=("theta", "V", "flow", "label", "status",
+                                        "max_loading", "n_overload"))
     c.close()
     np.testing.assert_array_equal(res["status"], ref["status"])
     np.testing.assert_array_equal(res["label"], ref["label"])
