@@ -26,8 +26,10 @@ struct FdpfParams {
   const int32_t* order = nullptr;      // scenarios in processing order (null: 0..S-1)
   void *wx = nullptr, *wr = nullptr, *wp = nullptr, *wq = nullptr, *wz = nullptr;
   size_t vstride = 0;  // elements per slot of one vector
-  // FP64 state per slot: theta, |V|; e + jf interleaved over the we and wf
-  // regions together ([slot][bus][lane][e, f], 2 sstride per slot)
+  // FP64 state per slot: theta, and e + jf interleaved over the we and wf
+  // regions together ([slot][bus][lane][e, f], 2 sstride per slot); the
+  // persistent N-1 kernel keeps no |V| (|e + jf|), so wV is scratch for the
+  // DC and adjoint kernels only
   double *wth = nullptr, *wV = nullptr, *we = nullptr, *wf = nullptr;
   size_t sstride = 0;  // elements per slot of one state array
   double *out_theta = nullptr, *out_vm = nullptr, *out_flow = nullptr, *out_maxload = nullptr;
