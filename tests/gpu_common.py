@@ -10,13 +10,14 @@ from oracle import screen
 
 # Grids of the named workloads with a share of their branches turned into
 # transformers (off-nominal turns ratios U[0.95, 1.05] at the from end).
-XFMR = {"grid120_xfmr": ("grid120", 0.15), "grid2k_xfmr": ("grid2k", 0.1)}
+XFMR = {"grid120_xfmr": ("grid120", 0.15), "grid2k_xfmr": ("grid2k", 0.1),
+        "grid10k_xfmr": ("grid10k", 0.1)}
 
 
 # Grids with reactive limits around their PV generators' base-case output:
 # Q_max = Q_g + 0.05 + 0.1 |Q_g|, Q_min = Q_g - 0.05 - 0.1 |Q_g|, so the base
 # case is within them and outages push some generators out.
-QLIM = {"grid120_qlim": "grid120", "grid2k_qlim": "grid2k"}
+QLIM = {"grid120_qlim": "grid120", "grid2k_qlim": "grid2k", "grid10k_qlim": "grid10k"}
 
 
 def _with_q_limits(g):
@@ -107,7 +108,7 @@ def _every_outage_worker(args):
             ld = np.maximum(np.abs(Pf), np.abs(Pt)) / g.rating
             nov = int((ld > 1.0).sum())
             ties = int((np.abs(ld - 1.0) <= 1e-12).sum())
-        rows.append((int(r["status"]), lab_ok, float(err), nov, ties))
+        rows.append((int(r["status"]), lab_ok, float(err), nov, ties, int(r["n_held"])))
     return idx, rows
 
 
@@ -117,7 +118,8 @@ def check_every_outage(g, th0, V0, outages, res, tol, tmpdir, max_outer=50, proc
     processes.  Returns per scenario: the oracle's status, whether the island
     labels are identical, the oracle's FP64 mismatch of the GPU's state (NaN
     where the GPU did not converge), and the oracle's overload count at the
-    GPU's state with the number of branches within 1e-12 of their rating."""
+    GPU's state with the number of branches within 1e-12 of their rating,
+    and the peak number of buses the oracle held at a reactive limit."""
     import os
     paths = {}
     for k in ("theta", "V", "label", "status"):
@@ -133,11 +135,12 @@ def check_every_outage(g, th0, V0, outages, res, tol, tmpdir, max_outer=50, proc
     err = np.empty(S)
     nov = np.empty(S, np.int32)
     ties = np.empty(S, np.int32)
+    held = np.empty(S, np.int32)
     with screen.worker_pool(processes) as pool:
         for idx, rows in pool.imap_unordered(_every_outage_worker, args):
             for s, row in zip(idx, rows):
-                st[s], lab_ok[s], err[s], nov[s], ties[s] = row
-    return dict(status=st, label_ok=lab_ok, err=err, n_overload=nov, ties=ties)
+                st[s], lab_ok[s], err[s], nov[s], ties[s], held[s] = row
+    return dict(status=st, label_ok=lab_ok, err=err, n_overload=nov, ties=ties, n_held=held)
 
 
 def _every_dc_outage_worker(args):
@@ -188,6 +191,51 @@ def check_every_dc_outage(g, outages, runs, tmpdir, tie=1e-6, processes=None):
                 for name, (dt, dfl) in diffs.items():
                     out[name]["dtheta"][s], out[name]["dflow"][s] = dt, dfl
     return out
+
+
+def _every_generator_outage_worker(args):
+    """One chunk of generator outages: the oracle's own FDPF (status, peak
+    number of held buses) and its FP64 evaluation of the GPU's state."""
+    g, th0, V0, idx, buses, paths, tol, max_outer = args
+    th = np.load(paths["theta"], mmap_mode="r")
+    V = np.load(paths["V"], mmap_mode="r")
+    st = np.load(paths["status"], mmap_mode="r")
+    rows = []
+    for s in idx:
+        k = int(buses[s])
+        r = screen.solve_generator_outage(g, th0, V0, k, tol, max_outer)
+        err = np.nan
+        if st[s] in (0, 3):
+            err = screen.generator_mismatch(g, k, np.asarray(th[s]), np.asarray(V[s]))
+        rows.append((int(r["status"]), float(err), int(r["n_held"])))
+    return idx, rows
+
+
+def check_every_generator_outage(g, th0, V0, buses, res, tol, tmpdir, max_outer=50,
+                                 processes=None):
+    """The oracle on every generator outage of a GPU screen `res` (host
+    outputs theta, V, status of the tripped PV `buses`) in a pool of host
+    processes: per scenario the oracle's status, its FP64 mismatch of the
+    GPU's state (NaN where the GPU did not converge) and the peak number of
+    buses it held at a reactive limit."""
+    import os
+    paths = {}
+    for k in ("theta", "V", "status"):
+        paths[k] = os.path.join(str(tmpdir), f"gen_{k}.npy")
+        np.save(paths[k], res[k])
+    S = len(buses)
+    if processes is None:
+        processes = len(os.sched_getaffinity(0))
+    chunks = [c for c in np.array_split(np.arange(S), max(1, processes * 8)) if c.size]
+    args = [(g, th0, V0, c, np.asarray(buses), paths, tol, max_outer) for c in chunks]
+    st = np.empty(S, np.int32)
+    err = np.empty(S)
+    held = np.empty(S, np.int32)
+    with screen.worker_pool(processes) as pool:
+        for idx, rows in pool.imap_unordered(_every_generator_outage_worker, args):
+            for s, row in zip(idx, rows):
+                st[s], err[s], held[s] = row
+    return dict(status=st, err=err, n_held=held)
 
 
 def with_tight_ratings(g, seed):

@@ -7,8 +7,9 @@ import numpy as np
 import pytest
 
 import paper_1803_03290_gb300 as gp
-from gpu_common import (check_every_outage, grid, oracle_base, oracle_n1, sample_outages,
-                        with_tight_ratings)
+from gpu_common import (check_every_generator_outage, check_every_outage, grid, oracle_base,
+                        oracle_n1, sample_outages, with_tight_ratings)
+from oracle import screen
 
 pytestmark = pytest.mark.gpu
 
@@ -65,6 +66,88 @@ def test_grid10k_every_outage_against_oracle(tmp_path):
     print(f"grid10k: {conv.sum()} converged, {np.bincount(st)} statuses, "
           f"{islanding.sum()} islanding, max mismatch {np.nanmax(ref['err'][conv]):.2e} p.u., "
           f"{(res['n_overload'] > 0).sum()} scenarios with overloads")
+
+
+def test_grid10k_transformers_every_outage(tmp_path):
+    """The benchmark's transformer variant (10 % of grid10k's branches
+    transformers, turns ratio U[0.95, 1.05] at the from end): every outage
+    screened with the benchmark's options and checked one by one (statuses
+    and island labels exact, every converged state's FP64 mismatch by the
+    oracle at most 1e-4 p.u.)."""
+    g = grid("grid10k_xfmr")
+    th0, V0 = oracle_base("grid10k_xfmr")
+    c = gp.GPCG(g)
+    c.base_solve()
+    outages = np.arange(g.n_branch, dtype=np.int32)
+    res = c.n1_screen(outages, outputs=("theta", "V", "status", "label"))
+    c.close()
+    ref = check_every_outage(g, th0, V0, outages, res, tol=1e-4, tmpdir=tmp_path)
+    st = res["status"]
+    bad = np.flatnonzero(st != ref["status"])
+    assert bad.size == 0, [(int(s), int(st[s]), int(ref["status"][s])) for s in bad[:20]]
+    assert ref["label_ok"].all()
+    conv = np.isin(st, (gp.SCEN_OK, gp.SCEN_ISLAND_NO_GEN))
+    assert conv.sum() >= 0.99 * g.n_branch
+    assert np.nanmax(ref["err"][conv]) <= 1e-4 + EVAL_SLACK, np.nanmax(ref["err"][conv])
+
+
+def test_grid10k_reactive_limits_every_outage(tmp_path):
+    """grid10k with reactive limits around each PV generator's base-case
+    output: every outage screened with the benchmark's options and checked
+    one by one -- statuses exact (QLIM_OVERFLOW exactly where the oracle held
+    more buses at once than a scenario can), labels exact, every converged
+    state's FP64 mismatch by the oracle at most 1e-4 p.u. with the
+    generators' reactive outputs within their limits or held at one."""
+    from oracle import powerflow as pf
+    g = grid("grid10k_qlim")
+    th0, V0 = oracle_base("grid10k_qlim")
+    c = gp.GPCG(g)
+    c.base_solve()
+    outages = np.arange(g.n_branch, dtype=np.int32)
+    res = c.n1_screen(outages, outputs=("theta", "V", "status", "label"))
+    c.close()
+    ref = check_every_outage(g, th0, V0, outages, res, tol=1e-4, tmpdir=tmp_path)
+    expect = np.where(ref["n_held"] > gp.MAX_EXT_ROWS, gp.SCEN_QLIM_OVERFLOW, ref["status"])
+    st = res["status"]
+    bad = np.flatnonzero(st != expect)
+    assert bad.size == 0, [(int(s), int(st[s]), int(expect[s])) for s in bad[:20]]
+    assert ref["label_ok"].all()
+    conv = np.isin(st, (gp.SCEN_OK, gp.SCEN_ISLAND_NO_GEN))
+    assert conv.sum() >= 0.95 * g.n_branch
+    assert np.nanmax(ref["err"][conv]) <= 1e-4 + EVAL_SLACK, np.nanmax(ref["err"][conv])
+    # the limits hold at a sample of converged states: a PV generator at its
+    # set point is within them, one off it is held at one
+    for s in np.flatnonzero(conv)[::97]:
+        on, _, isl, P, _ = screen.outage_setup(g, int(outages[s]))
+        live = on & ~isl[g.f] & ~isl[g.t]
+        yb = pf.ybus_entries(g.n_bus, g.f, g.t, g.r, g.x, g.b_sh, live, g.tap)
+        _, dQ = pf.mismatch(yb, P, g.Q_sched, res["theta"][s], res["V"][s])
+        pv = (g.bus_type == 1) & ~isl
+        at_set = pv & (np.abs(res["V"][s] - g.V_set) <= 1e-9)
+        qg = -dQ
+        assert np.all(qg[at_set] <= g.Q_max[at_set] + 1e-4)
+        assert np.all(qg[at_set] >= g.Q_min[at_set] - 1e-4)
+        off = pv & ~at_set
+        gap = np.minimum(np.abs(qg[off] - g.Q_max[off]), np.abs(qg[off] - g.Q_min[off]))
+        assert np.all(gap <= 1e-4 * (1 + 1e-9))
+
+
+def test_grid10k_generator_outages_every_bus(tmp_path):
+    """The generator of every one of grid10k's 1,999 PV buses tripped in turn
+    (the bench's generator workload): statuses exact and every converged
+    state's FP64 mismatch by the oracle at most 1e-4 p.u."""
+    g = grid("grid10k")
+    th0, V0 = oracle_base("grid10k")
+    c = gp.GPCG(g)
+    c.base_solve()
+    buses = np.flatnonzero(g.bus_type == 1).astype(np.int32)
+    res = c.n1_gen_screen(buses, outputs=("theta", "V", "status"))
+    c.close()
+    ref = check_every_generator_outage(g, th0, V0, buses, res, tol=1e-4, tmpdir=tmp_path)
+    np.testing.assert_array_equal(res["status"], ref["status"])
+    conv = np.isin(res["status"], (gp.SCEN_OK, gp.SCEN_ISLAND_NO_GEN))
+    assert conv.sum() >= 0.99 * buses.size
+    assert np.nanmax(ref["err"][conv]) <= 1e-4 + EVAL_SLACK, np.nanmax(ref["err"][conv])
 
 
 def test_grid10k_refined_sample_angles():
