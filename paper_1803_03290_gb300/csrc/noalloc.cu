@@ -88,7 +88,8 @@ extern "C" gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx* ctx, const int32_t* outa
   const size_t scen = up256(S * 4) * 3 + up256(S * 8);
   const size_t vec_bytes = up256((size_t)(c.rows + 1) * T * vt);
   const size_t st_bytes = up256((size_t)c.n * T * 8);
-  const size_t per_slot = 5 * vec_bytes + 4 * st_bytes;
+  // five vectors; the state theta and e + jf (two arrays' worth)
+  const size_t per_slot = 5 * vec_bytes + 3 * st_bytes;
   const size_t cap = GPCG_NOALLOC_SCRATCH_BYTES;
   if (head + scen + per_slot > cap)
     return err(GPCG_ERR_INVALID_ARG,
@@ -158,8 +159,7 @@ extern "C" gpcg_status gpcg_n1_screen_noalloc(gpcg_ctx* ctx, const int32_t* outa
   double* sbase = (double*)(work + 5 * vb);
   const size_t ss = st_bytes / 8;
   (void)sb;
-  P.wth = sbase; P.wV = sbase + slots * ss; P.we = sbase + 2 * slots * ss;
-  P.wf = sbase + 3 * slots * ss;
+  P.wth = sbase; P.we = sbase + slots * ss; P.wf = sbase + 2 * slots * ss;
   P.sstride = ss;
   ce = f32 ? launch_fdpf<float>(st, T, slots, P, c.MPf, c.MQf)
            : launch_fdpf<double>(st, T, slots, P, c.MPd, c.MQd);
