@@ -146,7 +146,6 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
       const bool on0 = L.active[l0] && !in_island(pr, L.lo[l0], L.cnt[l0]);
       const bool on1 = L.active[l1] && !in_island(pr, L.lo[l1], L.cnt[l1]);
       if (!(on0 || on1)) continue;
-      const int br0 = L.l[l0], br1 = L.l[l1];
       // a lane's first P half-step away from the ends of its outaged branch:
       // the base-case mismatch holds (the state is the base case there)
       bool w0 = false, w1 = false;
@@ -162,7 +161,6 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
       for (int a0 = 0; a0 < KG; a0 += MIS_GROUP) {
         double2 u0[MIS_GROUP], u1[MIS_GROUP];
         double gv[MIS_GROUP], bv[MIS_GROUP];
-        int bb[MIS_GROUP];
 #pragma unroll
         for (int a = 0; a < MIS_GROUP; ++a)
           if (a0 + a < deg) {
@@ -171,16 +169,15 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
             u1[a] = q2[1];
             gv[a] = __ldg(G.adj_g + (size_t)(a0 + a) * G.n + i);
             bv[a] = __ldg(G.adj_b + (size_t)(a0 + a) * G.n + i);
-            bb[a] = __ldg(G.adj_brl + (size_t)(a0 + a) * G.n + i);
           }
 #pragma unroll
         for (int a = 0; a < MIS_GROUP; ++a)
           if (a0 + a < deg) {
-            if (n0 && bb[a] != br0) {
+            if (n0) {
               re0 = fma(-gv[a], u0[a].x, fma(bv[a], u0[a].y, re0));
               im0 = fma(-gv[a], u0[a].y, fma(-bv[a], u0[a].x, im0));
             }
-            if (n1 && bb[a] != br1) {
+            if (n1) {
               re1 = fma(-gv[a], u1[a].x, fma(bv[a], u1[a].y, re1));
               im1 = fma(-gv[a], u1[a].y, fma(-bv[a], u1[a].x, im1));
             }
@@ -188,18 +185,32 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
       }
       const int o0 = __ldg(G.adj_optr + i), o1 = __ldg(G.adj_optr + i + 1);
       for (int e = o0; e < o1; ++e) {
-        const int jn = __ldg(G.adj_onbr + e), b_ = __ldg(G.adj_obr + e);
+        const int jn = __ldg(G.adj_onbr + e);
         const double gw = __ldg(G.adj_og + e), bw = __ldg(G.adj_ob + e);
         const double2* q2 = reinterpret_cast<const double2*>(EF + ef_at<T>(jn, l0));
         const double2 v0 = q2[0], v1 = q2[1];
-        if (n0 && b_ != br0) {
+        if (n0) {
           re0 = fma(-gw, v0.x, fma(bw, v0.y, re0));
           im0 = fma(-gw, v0.y, fma(-bw, v0.x, im0));
         }
-        if (n1 && b_ != br1) {
+        if (n1) {
           re1 = fma(-gw, v1.x, fma(bw, v1.y, re1));
           im1 = fma(-gw, v1.y, fma(-bw, v1.x, im1));
         }
+      }
+      // the outaged branch's term back out at its two end buses
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int ln = j ? l1 : l0;
+        if (!(j ? n1 : n0) || (i != L.fb[ln] && i != L.tb[ln])) continue;
+        const int e = i == L.fb[ln] ? 0 : 1;
+        const double2 v = *reinterpret_cast<const double2*>(
+            EF + ef_at<T>(e ? L.fb[ln] : L.tb[ln], ln));
+        const double go = L.og[ln][e], bo = L.ob[ln][e];
+        double& re = j ? re1 : re0;
+        double& im = j ? im1 : im0;
+        re -= fma(-go, v.x, bo * v.y);
+        im -= fma(-go, v.y, -bo * v.x);
       }
       }
       // own voltage, the diagonal term and the mismatch of each lane
@@ -455,6 +466,28 @@ __device__ __forceinline__ void setup_lane(const FdpfParams& P, const DevMatT<VT
   L.gl[ln] = l >= 0 ? G.g[l] : 0.0;
   L.bl[ln] = l >= 0 ? G.by[l] + 0.5 * G.b_sh[l] : 0.0;
   L.cl[ln] = l >= 0 ? G.cf[l] : 1.0;
+  // the adjacency entries of the outaged branch at its two ends: the
+  // mismatch sums every neighbour and takes these back out
+  for (int e = 0; e < 2; ++e) {
+    L.og[ln][e] = 0.0;
+    L.ob[ln][e] = 0.0;
+    const int x = e ? L.tb[ln] : L.fb[ln];
+    if (x < 0) continue;
+    bool hit = false;
+    const int dg = G.adj_deg[x];
+    for (int a = 0; a < dg && !hit; ++a)
+      if (G.adj_brl[(size_t)a * G.n + x] == l) {
+        L.og[ln][e] = G.adj_g[(size_t)a * G.n + x];
+        L.ob[ln][e] = G.adj_b[(size_t)a * G.n + x];
+        hit = true;
+      }
+    for (int k = G.adj_optr[x]; k < G.adj_optr[x + 1] && !hit; ++k)
+      if (G.adj_obr[k] == l) {
+        L.og[ln][e] = G.adj_og[k];
+        L.ob[ln][e] = G.adj_ob[k];
+        hit = true;
+      }
+  }
   L.gb[ln] = P.sc.gen_bus ? P.sc.gen_bus[s] : -1;
   // the tripped generator's bus is the lane's first extension row, with its
   // load's reactive injection

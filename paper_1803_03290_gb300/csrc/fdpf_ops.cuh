@@ -228,6 +228,9 @@ struct LaneState {
   int raP[T], rbP[T], raQ[T], rbQ[T];
   double wP[T], wQ[T], coef[T], gl[T], bl[T];
   double cl[T];  // the outaged branch's 1 / turns ratio (1 for a line)
+  // the outaged branch's off-diagonal admittance entries as the bus
+  // adjacency holds them, at its from end [0] and its to end [1]
+  double og[T][2], ob[T][2];
   int gb[T];     // bus of a tripped generator (-1: none)
   int active[T], outer[T], inP[T], inQ[T], status[T], nogen[T];
   double err[T], best[T];
