@@ -14,8 +14,12 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("name,world", [("grid2k", 3), ("grid120", 4)])
 def test_sharded_screen_is_bit_exact(name, world):
+    """The tile width and the dense tail are fixed (they change the rounding
+    of the inner solve, and the autotuner may choose them per scenario
+    count); the tiles per SM stay with the autotuner, which may give the
+    shards and the whole list different numbers of tiles in flight."""
     g = grid(name)
-    c = gp.GPCG(g, tile=2)
+    c = gp.GPCG(g, tile=2, tail_rows=gp.MAX_TAIL_ROWS)
     c.base_solve()
     outages = np.random.default_rng(8).permutation(g.n_branch).astype(np.int32)[:301]
     outs = ("theta", "V", "flow", "label", "iters", "status", "max_loading")
