@@ -815,12 +815,27 @@ __device__ GPCG_LOOP_INLINE Vec<VT, Geo<T>::LP> fwd_pass(
   if (nl > 0) {
     r0 = __ldg(M.lev_ptr);
     r1 = __ldg(M.lev_ptr + 1);
-    if (r0 + g.rs < r1) {
-      pf = r0 + g.rs;
+    // level 0: the rows without off-diagonal entries in L (a third of the
+    // rows on these grids) take the update and the diagonal scaling only,
+    // with nothing to gather; the next level's first row is loaded ahead
+    const int r2 = nl > 1 ? __ldg(M.lev_ptr + 2) : r1;
+    if (nl > 1 && r1 + g.rs < r2) {
+      pf = r1 + g.rs;
       ld_cols<KL>(M.L.col + (size_t)pf * KL, cn);
     }
+    for (int i = r0 + g.rs; i < r1; i += RPS) {
+      const size_t o = (size_t)i * T + g.lane;
+      Vec<VT, LP> a = pcg_update_row<T, VT, FUSED>(o, x, r, p, q, al, rr);
+      const VT id = M.Lh ? (VT)1 : __ldg(M.inv_diag + i);
+#pragma unroll
+      for (int j = 0; j < LP; ++j) a.v[j] *= id;
+      stv<LP>(z + o, a);
+    }
+    __syncthreads();
+    r0 = r1;
+    r1 = r2;
   }
-  for (int lev = 0; lev < nl; ++lev) {
+  for (int lev = 1; lev < nl; ++lev) {
     const int r2 = (lev + 1 < nl) ? __ldg(M.lev_ptr + lev + 2) : r1;  // end of the next level
     for (int i = r0 + g.rs; i < r1; i += RPS) {
       int c[KL];
