@@ -52,7 +52,9 @@ typedef enum {
   GPCG_ERR_BASE_NOT_CONVERGED = 3, /* also: the base case needs PV generators
                                      outside their reactive limits */
   GPCG_ERR_BASE_ISLANDED = 4,   /* the intact grid is not connected */
-  GPCG_ERR_TIMEOUT = 5,         /* reserved: no kernel of this library waits on another */
+  GPCG_ERR_TIMEOUT = 5,         /* a bounded device wait gave up (the grid-wide
+                                   barriers of the plain FP64 path; see
+                                   gpcg_options.wait_limit) */
   GPCG_ERR_OOM = 6,             /* a device allocation failed */
   GPCG_ERR_NOT_READY = 7        /* gpcg_base_solve has not succeeded yet */
 } gpcg_status;
@@ -163,6 +165,11 @@ typedef struct {
                           solved with the dense inverse of their block
                           (1 ... GPCG_MAX_TAIL_ROWS), the levels before it one
                           block barrier each; -1 = no dense tail; 0 = autotuned */
+  int32_t wait_limit;  /* bounded device waits: the polls (about 64 ns apart)
+                          a grid-wide barrier of the plain FP64 path makes
+                          before it gives up, which ends the call with
+                          GPCG_ERR_TIMEOUT and leaves the context usable;
+                          0 = 2^25 (about 2 s) */
 } gpcg_options;
 
 /* Largest dense tail of a factor (rows); the tail's right-hand side is kept

@@ -42,7 +42,7 @@ class Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("base_tol", C.c_double), ("inner_rtol", C.c_double),
                 ("max_outer", C.c_int32), ("max_inner", C.c_int32), ("precision", C.c_int32),
                 ("precond", C.c_int32), ("tile", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("tail_rows", C.c_int32)]
+                ("tail_rows", C.c_int32), ("wait_limit", C.c_int32)]
 
 
 class Info(C.Structure):

@@ -284,6 +284,7 @@ extern "C" gpcg_status gpcg_default_options(gpcg_options* opt) {
   opt->tile = 0;
   opt->ctas_per_sm = 0;
   opt->tail_rows = 0;
+  opt->wait_limit = 0;
   g_err.clear();
   return GPCG_OK;
 }
@@ -303,6 +304,8 @@ static gpcg_status check_options(const gpcg_options& o) {
     return fail(GPCG_ERR_INVALID_ARG, "tile must be 0, 2, 4, 8, 16 or 32");
   if (o.ctas_per_sm < 0 || o.ctas_per_sm > 64)
     return fail(GPCG_ERR_INVALID_ARG, "ctas_per_sm must be in [0, 64]");
+  if (o.wait_limit < 0)
+    return fail(GPCG_ERR_INVALID_ARG, "wait_limit must be >= 0");
   if (o.tail_rows < -1 || o.tail_rows > GPCG_MAX_TAIL_ROWS)
     return fail(GPCG_ERR_INVALID_ARG, "tail_rows must be -1, 0 or in [1, %d]", GPCG_MAX_TAIL_ROWS);
   return GPCG_OK;
@@ -1458,6 +1461,7 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
     if (rs != GPCG_OK) { cleanup(); return rs; }
     CUDA_TRY(cudaMemsetAsync(c->plainb.bar, 0, 2 * sizeof(unsigned int), st));
     CUDA_TRY(cudaMemsetAsync(c->plainb.err, 0, sizeof(int), st));
+    c->plainb.wait_limit = c->opt.wait_limit > 0 ? (unsigned)c->opt.wait_limit : (1u << 25);
     P.S = (int)S;
     P.phase_cycles = nullptr;
     const DevMatT<double> MPd = c->MP.view<double>(), MQd = c->MQ.view<double>();

@@ -77,6 +77,7 @@ struct PlainBuffers {
   double* part = nullptr;          // [2 * 4 * grid]
   unsigned int* bar = nullptr;     // [2], zero before the first launch
   int* err = nullptr;              // [1], zero before the first launch
+  unsigned wait_limit = 1u << 25;  // polls of a barrier wait (~64 ns each) before it gives up
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *t = nullptr;
   double *th = nullptr, *V = nullptr, *ef = nullptr;  // [n], [n], [2 n]
 };

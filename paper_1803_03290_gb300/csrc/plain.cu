@@ -24,12 +24,12 @@ namespace {
 
 constexpr int PT = 256;               // threads per CTA
 constexpr int PW = PT / 32;           // warps per CTA
-constexpr unsigned kSpinLimit = 1u << 25;  // barrier polls (about 2 s with the sleeps)
 
 struct PlainState {
   double* part;          // [2][4 * grid] per-CTA partials (two alternating sets)
   unsigned int* bar;     // [2] arrival count, generation
   int* err;              // set when a barrier wait gave up
+  unsigned limit;        // polls a barrier wait makes before it gives up
   double *x, *r, *p, *q, *z, *t;  // [rows + 1]; t: the tail's right-hand side
   double *th, *V, *ef;   // state by bus: theta, |V|, (e, f) interleaved
 };
@@ -48,12 +48,15 @@ __device__ bool grid_barrier(const PlainState& W) {
       __threadfence();
       atomicAdd(W.bar + 1, 1u);
     } else {
+      // poll until the last CTA arrives; give up after W.limit polls, or as
+      // soon as another CTA has given up (its flag is set)
       unsigned int spins = 0;
       while (*gen == g) {
-        if (++spins > kSpinLimit) {
+        if (++spins > W.limit) {
           atomicExch(W.err, 1);
           break;
         }
+        if (*(volatile int*)W.err) break;
         __nanosleep(64);
       }
     }
@@ -500,6 +503,7 @@ cudaError_t launch_plain(cudaStream_t st, int grid, const FdpfParams& P,
                          const PlainBuffers& B, int s) {
   PlainState W;
   W.part = B.part; W.bar = B.bar; W.err = B.err;
+  W.limit = B.wait_limit;
   W.x = B.x; W.r = B.r; W.p = B.p; W.q = B.q; W.z = B.z; W.t = B.t;
   W.th = B.th; W.V = B.V; W.ef = B.ef;
   FdpfParams Pc = P;

@@ -96,7 +96,7 @@ def test_binding_structs_follow_the_header():
 
 
 @pytest.mark.parametrize("bad", [dict(tail_rows=-2), dict(tail_rows=249), dict(tile=3),
-                                 dict(ctas_per_sm=-1)])
+                                 dict(ctas_per_sm=-1), dict(wait_limit=-1)])
 def test_bad_options_fail_before_the_gpu(bad):
     from paper_1803_03290_gb300 import binding
     from gridgen import config_grid

@@ -230,6 +230,29 @@ def test_plain_path_grid2k_sample():
     assert (res["iters"][ok, 1] >= 1).all()
 
 
+def test_plain_path_bounded_wait_gives_up_and_recovers():
+    """Bounded device waits: the plain path's grid-wide barriers allowed a
+    single poll give up (the CTAs of a launch never arrive within 64 ns of
+    each other), so the call ends with GPCG_ERR_TIMEOUT instead of waiting;
+    the same context then screens with the default limit and matches the
+    oracle."""
+    g = grid("grid120")
+    samp = np.arange(0, g.n_branch, 9, dtype=np.int32)
+    c = make("grid120", precision=gp.PLAIN_FP64, tol=1e-10, max_outer=100, wait_limit=1)
+    c.base_solve()
+    with pytest.raises(gp.GPCGError) as e:
+        c.n1_screen(samp, outputs=("status",))
+    assert e.value.status == 5 and "barrier" in str(e.value)
+    c.set_options(wait_limit=0)
+    res = c.n1_screen(samp, outputs=("theta", "status", "label"))
+    c.close()
+    ref = oracle_n1("grid120", samp, tol=1e-10)
+    np.testing.assert_array_equal(res["status"], ref["status"])
+    np.testing.assert_array_equal(res["label"], ref["label"])
+    ok = ref["status"] == 0
+    assert np.abs(res["theta"][ok] - ref["theta"][ok]).max() <= ANGLE_TOL
+
+
 @pytest.mark.parametrize("tile", [8, 16, 32])
 def test_n1_tiles_ragged(tile):
     g = grid("grid120")
