@@ -23,8 +23,11 @@ grounded at the removed buses, hence symmetric positive definite.
 
 FDPF (eqs. (4)-(5), Sec. III.B): starting from a given state, repeat
   evaluate dP, dQ; stop when max|dP| (PV and PQ buses) and max|dQ| (PQ buses)
-  are both <= tol; solve B' dtheta = dP/V, theta += dtheta; evaluate dQ;
-  solve B'' dV = dQ/V, V += dV.
+  are both <= tol; unless max|dP| is already <= tol, solve B' dtheta = dP/V,
+  theta += dtheta and evaluate dQ again; unless max|dQ| is then <= tol,
+  solve B'' dV = dQ/V, V += dV.  (A half-step whose own mismatch is within
+  the tolerance is skipped, as in the fast-decoupled method the paper builds
+  on; the outer count advances once per pass through the loop.)
 
 Reactive limits of the PV generators (Q_min, Q_max per bus; the paper has
 none, this is the usual enforcement): when the iteration has converged, the
@@ -268,9 +271,11 @@ def fdpf(grid, in_service, active, P_sched, theta0, V0, tol, max_outer, growth_r
             return theta, V, k, STATUS_OK, err
         if k >= max_outer:
             return theta, V, k, STATUS_MAXITER, err
-        theta[pvpq] += solP.solve(dP[pvpq] / V[pvpq])
-        dP, dQ = mismatch(ybus, P_sched, Q_sched, theta, V)
-        V[pq] += solQ.solve(dQ[pq] / V[pq])
+        if np.abs(dP[pvpq]).max(initial=0.0) > tol:
+            theta[pvpq] += solP.solve(dP[pvpq] / V[pvpq])
+            dP, dQ = mismatch(ybus, P_sched, Q_sched, theta, V)
+        if np.abs(dQ[pq]).max(initial=0.0) > tol:
+            V[pq] += solQ.solve(dQ[pq] / V[pq])
         k += 1
 
 

@@ -296,6 +296,7 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
           res = to_vt<VT>(dP) * iv;
         } else {
           const double dQ = fma(-fi, re, fma(ei, im, qs));
+          upd_max_bits(errQ.v[jp + j], dQ);  // decides whether the Q step is taken
           res = to_vt<VT>(dQ) * iv;
         }
         out.v[jp + j] = res;
@@ -316,6 +317,7 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
         const double2 I = bus_current<T>(G, L, EF, b, ln);
         const double2 v = *reinterpret_cast<const double2*>(EF + ef_at<T>(b, ln));
         const double dQ = fma(-v.y, I.x, fma(v.x, I.y, SW->xq[ln][s]));
+        upd_max_bits(errQ.v[j], dQ);
         rhs[(size_t)(MQ.n + 1 + s) * T + ln] = to_vt<VT>(dQ) * inv_vmag<VT>(v.x, v.y);
       }
     }
@@ -859,25 +861,38 @@ __global__ void __launch_bounds__(NTHREADS, ZS ? 2 : FDPF_MIN_BLOCKS)
         } else if (GEN && SW->skip[ln]) {
           L.active[ln] = 0;  // back at the top of the next outer iteration
         }
+        // a P mismatch already within the tolerance takes no P step
+        L.hold[ln] = a <= P.tol;
       }
     }
     const bool more = any_lane<T>(L, L.active);
     GPCG_PHASE(1);
     if (!more) continue;
-    pcg_solve<T, VT, true, GEN>(P, MP, L, x, r, p, q, z, L.raP, L.rbP, L.wP, L.inP);
-    GPCG_PHASE(2);
-    update_pass<T, VT, true, GEN>(MP, L, x, p, th, EF, SW);
+    if (any_stepping<T>(L)) {
+      pcg_solve<T, VT, true, GEN>(P, MP, L, x, r, p, q, z, L.raP, L.rbP, L.wP, L.inP, nullptr,
+                                  nullptr, L.hold);
+      GPCG_PHASE(2);
+      update_pass<T, VT, true, GEN>(MP, L, x, p, th, EF, SW);
+    }
     __syncthreads();
     GPCG_PHASE(3);
-    // Q half-step
+    // Q half-step: the Q mismatch after the P step; a lane whose Q mismatch
+    // is within the tolerance takes no Q step
     Vec<unsigned long long, LP> d0 = vzero<unsigned long long, LP>(), d1 = d0;
     mismatch_pass<T, VT, false, GEN>(P, MP, MQ, L, EF, r, d0, d1, SW);
-    __syncthreads();
+    {
+      const Vec<unsigned long long, LP> bQ2 = lane_max_bits<T, RS_ERRQ>(L, d1);
+      if (g.rs == 0)
+#pragma unroll
+        for (int j = 0; j < LP; ++j) L.hold[g.lane + j] = from_bits(bQ2.v[j]) <= P.tol;
+    }
     GPCG_PHASE(4);
-    pcg_solve<T, VT, true, GEN>(P, MQ, L, x, r, p, q, z, L.raQ, L.rbQ, L.wQ, L.inQ,
-                                MQ.c ? L.cl : nullptr, SW);
-    GPCG_PHASE(5);
-    update_pass<T, VT, false, GEN>(MQ, L, x, p, th, EF, SW);
+    if (any_stepping<T>(L)) {
+      pcg_solve<T, VT, true, GEN>(P, MQ, L, x, r, p, q, z, L.raQ, L.rbQ, L.wQ, L.inQ,
+                                  MQ.c ? L.cl : nullptr, SW, L.hold);
+      GPCG_PHASE(5);
+      update_pass<T, VT, false, GEN>(MQ, L, x, p, th, EF, SW);
+    }
     if (g.rs == 0)
 #pragma unroll
       for (int j = 0; j < LP; ++j)

@@ -236,6 +236,9 @@ struct LaneState {
   double err[T], best[T];
   unsigned long long tphase[8];
   int done[T], fresh[T];
+  // lanes that take no step in the current half-step: their own mismatch is
+  // already within the tolerance
+  int hold[T];
   double xalpha[T];          // a deferred last step x += alpha p of the inner solve
   // one small buffer per reduction site (see lane_sum): [site][warp][lane]
   double red2[NRED_SITES * (NTHREADS / 32) * T];
@@ -269,6 +272,21 @@ __device__ __forceinline__ Pair<double> lane_reduce(double* red, double v0, doub
   const Pair<double> out{red[g.lane], red[g.lane + 1]};
   __syncthreads();
   return out;
+}
+
+// True when some active lane is not held (block-uniform).
+template <int T>
+__device__ __forceinline__ bool any_stepping(LaneState<T>& L) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int any = 0;
+    for (int s = 0; s < T; ++s) any |= (L.active[s] != 0 && L.hold[s] == 0);
+    L.flag = any;
+  }
+  __syncthreads();
+  const bool r = L.flag != 0;
+  __syncthreads();
+  return r;
 }
 
 // True when some lane has a nonzero flag (block-uniform).
@@ -1036,7 +1054,7 @@ template <int T, typename VT, bool DEFER = false, bool GEN = false>
 __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT>& M, LaneState<T>& L, VT* x,
                           VT* r, VT* p, VT* q, VT* z, const int* ra_, const int* rb_,
                           const double* w_, int* iters, const double* c_ = nullptr,
-                          const SwitchState<T>* SW = nullptr) {
+                          const SwitchState<T>* SW = nullptr, const int* hold = nullptr) {
   constexpr int LP = Geo<T>::LP;
   __shared__ PcgLanes<T, VT> S;
   __shared__ Stamp<T, VT> St;
@@ -1135,7 +1153,8 @@ __device__ GPCG_PASS_INLINE void pcg_solve(const FdpfParams& P, const DevMatT<VT
       S.stall[ln] = 0;
       S.brk[ln] = 0;
       S.stop[ln] = 0;
-      S.pdone[ln] = !L.active[ln] || !(b_ > (VT)0) || !(r_ > (VT)0);
+      // held lanes take no step: x stays 0
+      S.pdone[ln] = !L.active[ln] || (hold && hold[ln]) || !(b_ > (VT)0) || !(r_ > (VT)0);
     }
   }
   __syncthreads();  // publishes S and the first z

@@ -411,40 +411,48 @@ __global__ void __launch_bounds__(PT) plain_fdpf_kernel(FdpfParams P, DevMatT<do
     else if (outer >= P.max_outer) status = 1;
     best = fmin(best, err);
     if (status >= 0) break;
-    if (!plain_pcg(P, MP, c, W, round, raP, rbP, wP, 1.0, inP)) return;
-    // theta += dtheta, (e, f) rotated with it
-    for (int k = gt; k < MP.n; k += NT) {
-      const int i = MP.bus_of_row[k];
-      if (in_island(G.pre[i], c.lo, c.cnt)) continue;
-      const double d = W.x[k];
-      W.th[i] += d;
-      double2 u = EF[i];
-      rotate_ef(d, u.x, u.y);
-      EF[i] = u;
+    // P half-step, unless the P mismatch is already within the tolerance
+    if (!(a <= P.tol)) {
+      if (!plain_pcg(P, MP, c, W, round, raP, rbP, wP, 1.0, inP)) return;
+      // theta += dtheta, (e, f) rotated with it
+      for (int k = gt; k < MP.n; k += NT) {
+        const int i = MP.bus_of_row[k];
+        if (in_island(G.pre[i], c.lo, c.cnt)) continue;
+        const double d = W.x[k];
+        W.th[i] += d;
+        double2 u = EF[i];
+        rotate_ef(d, u.x, u.y);
+        EF[i] = u;
+      }
+      if (!grid_barrier(W)) return;
     }
-    if (!grid_barrier(W)) return;
-    // Q half-step on the PQ buses
+    // Q half-step on the PQ buses, unless their mismatch is within the tolerance
+    unsigned long long mq[1] = {0ull};
     for (int k = gt; k < MQ.n; k += NT) {
       const int i = MQ.bus_of_row[k];
       double rhs = 0.0;
       if (!in_island(G.pre[i], c.lo, c.cnt)) {
         const double2 I = current_at(G, c, EF, i);
         const double2 v = EF[i];
-        rhs = fma(-v.y, I.x, fma(v.x, I.y, G.Q_sched[i])) / W.V[i];
+        const double dQ = fma(-v.y, I.x, fma(v.x, I.y, G.Q_sched[i]));
+        upd_max_bits(mq[0], dQ);
+        rhs = dQ / W.V[i];
       }
       W.r[k] = rhs;
     }
-    if (!grid_barrier(W)) return;
-    if (!plain_pcg(P, MQ, c, W, round, raQ, rbQ, wQ, cQ, inQ)) return;
-    for (int k = gt; k < MQ.n; k += NT) {
-      const int i = MQ.bus_of_row[k];
-      if (in_island(G.pre[i], c.lo, c.cnt)) continue;
-      const double r = W.x[k] / W.V[i];
-      W.V[i] = fma(W.V[i], r, W.V[i]);
-      const double2 u = EF[i];
-      EF[i] = make_double2(fma(u.x, r, u.x), fma(u.y, r, u.y));
+    if (!grid_maxes<1>(W, round, mq)) return;
+    if (!(from_bits(mq[0]) <= P.tol)) {
+      if (!plain_pcg(P, MQ, c, W, round, raQ, rbQ, wQ, cQ, inQ)) return;
+      for (int k = gt; k < MQ.n; k += NT) {
+        const int i = MQ.bus_of_row[k];
+        if (in_island(G.pre[i], c.lo, c.cnt)) continue;
+        const double r = W.x[k] / W.V[i];
+        W.V[i] = fma(W.V[i], r, W.V[i]);
+        const double2 u = EF[i];
+        EF[i] = make_double2(fma(u.x, r, u.x), fma(u.y, r, u.y));
+      }
+      if (!grid_barrier(W)) return;
     }
-    if (!grid_barrier(W)) return;
     outer += 1;
   }
   // outputs (Sec. I): state, branch flows, loading and overloads
