@@ -152,7 +152,8 @@ typedef struct {
   double inner_rtol;   /* PCG stops at ||r|| <= inner_rtol ||b||; 3e-3 */
   int32_t max_outer;   /* outer FDPF iteration cap; 50 */
   int32_t max_inner;   /* PCG iteration cap per solve; 500 */
-  int32_t precision;   /* GPCG_PLAIN_FP64 / _BATCHED_FP32 / _BATCHED_FP64 */
+  int32_t precision;   /* GPCG_PLAIN_FP64 / _BATCHED_FP32 / _BATCHED_FP64 /
+                          _BATCHED_FP32_F16 */
   int32_t precond;     /* GPCG_PRECOND_*; default GPCG_PRECOND_EXACT */
   int32_t tile;        /* scenarios per tile (the scenario chunk a CTA solves
                           together): 2, 4, 8, 16 or 32; 0 = autotuned */
@@ -251,6 +252,11 @@ GPCG_API gpcg_status gpcg_base_solve(gpcg_ctx *ctx, double *theta, double *vm,
  * PV generators in proportion to P_gen (Sec. IV.C), solve the FDPF of the
  * main island from the base-case state with base-preconditioned CG
  * (Sec. IV.B), and screen the branch flows against their ratings (Sec. I).
+ * The FDPF loop (Sec. III.B, eqs. (4)-(5)): evaluate dP and dQ; stop when
+ * max|dP| (non-slack buses) and max|dQ| (PQ buses) are both within tol;
+ * take the P-theta step unless max|dP| is already within tol; evaluate dQ;
+ * take the Q-V step unless max|dQ| is then within tol; one outer iteration
+ * per pass.
  * Islanded buses report theta = vm = 0; branches touching them, and the
  * outaged branch, report zero flow.
  *
