@@ -1366,9 +1366,15 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
         const int np = (int)std::min(S, std::max<size_t>(16384, 8 * lanes));
         std::vector<int32_t> po(np);
         for (int k = 0; k < np; ++k) po[k] = order[(size_t)k * S / np];
-        CUDA_TRY(cudaMemcpyAsync(c->d_porder, po.data(), (size_t)np * 4,
-                                 cudaMemcpyHostToDevice, st));
-        CUDA_TRY(enqueue_islands(st));
+        {
+          cudaError_t e = cudaMemcpyAsync(c->d_porder, po.data(), (size_t)np * 4,
+                                          cudaMemcpyHostToDevice, st);
+          if (e == cudaSuccess) e = enqueue_islands(st);
+          if (e != cudaSuccess) {
+            cleanup();
+            return fail(GPCG_ERR_CUDA, "autotuner set-up: %s", cudaGetErrorString(e));
+          }
+        }
         auto rate = [&](int t, int ps, int cap, bool timed, double* out) -> gpcg_status {
           gpcg_status r = set_tail(c, cap);
           if (r != GPCG_OK) return r;
