@@ -76,6 +76,19 @@ static gpcg_status fail(gpcg_status st, const char* fmt, ...) {
     }                                                                                   \
   } while (0)
 
+// CUDA_TRY for the screen after its output staging exists: the staging is
+// freed before the error returns (`cleanup` in scope).
+#define CUDA_TRY_C(call)                                                                \
+  do {                                                                                  \
+    cudaError_t ce_ = (call);                                                           \
+    if (ce_ != cudaSuccess) {                                                           \
+      cleanup();                                                                        \
+      if (ce_ == cudaErrorMemoryAllocation)                                             \
+        return fail(GPCG_ERR_OOM, "%s: %s", #call, cudaGetErrorString(ce_));            \
+      return fail(GPCG_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(ce_));             \
+    }                                                                                   \
+  } while (0)
+
 // ------------------------------------------------------------------ context
 // Padded rows (ELL) of one operator: integer structure built on the host,
 // values gathered on the device from the CSR values through `src`.
@@ -1279,11 +1292,11 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
   }
   if (c->phase_on && S > c->phase_cap) {
     // diagnostics: room for every scenario's start and finish times
-    CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY_C(cudaStreamSynchronize(st));
     cudaFree(c->phase);
     c->phase = nullptr;
     c->phase_cap = 0;
-    CUDA_TRY(cudaMalloc(&c->phase, (8 + 2 * S + 4) * sizeof(unsigned long long)));
+    CUDA_TRY_C(cudaMalloc(&c->phase, (8 + 2 * S + 4) * sizeof(unsigned long long)));
     c->phase_cap = S;
   }
   FdpfParams P = base_params(c);
@@ -1458,30 +1471,30 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
     P.n_tiles = n_tiles;
     P.order = c->d_order;
   }
-  if (c->phase_on) CUDA_TRY(cudaMemsetAsync(c->phase, 0, (8 + 2 * S + 4) * sizeof(unsigned long long), st));
+  if (c->phase_on) CUDA_TRY_C(cudaMemsetAsync(c->phase, 0, (8 + 2 * S + 4) * sizeof(unsigned long long), st));
   if (plain && !ext) {
     // one scenario at a time, each spread over the whole GPU (cooperative
     // launches with grid-wide barriers): no batching across scenarios
-    CUDA_TRY(enqueue_islands(st));
+    CUDA_TRY_C(enqueue_islands(st));
     rs = ensure_plain(c);
     if (rs != GPCG_OK) { cleanup(); return rs; }
-    CUDA_TRY(cudaMemsetAsync(c->plainb.bar, 0, 2 * sizeof(unsigned int), st));
-    CUDA_TRY(cudaMemsetAsync(c->plainb.err, 0, sizeof(int), st));
+    CUDA_TRY_C(cudaMemsetAsync(c->plainb.bar, 0, 2 * sizeof(unsigned int), st));
+    CUDA_TRY_C(cudaMemsetAsync(c->plainb.err, 0, sizeof(int), st));
     c->plainb.wait_limit = c->opt.wait_limit > 0 ? (unsigned)c->opt.wait_limit : (1u << 25);
     P.S = (int)S;
     P.phase_cycles = nullptr;
     const DevMatT<double> MPd = c->MP.view<double>(), MQd = c->MQ.view<double>();
     for (size_t s = 0; s < S; ++s)
-      CUDA_TRY(launch_plain(st, c->plain_grid_size, P, MPd, MQd, c->plainb, (int)s));
+      CUDA_TRY_C(launch_plain(st, c->plain_grid_size, P, MPd, MQd, c->plainb, (int)s));
     int32_t herr = 0;
-    CUDA_TRY(cudaMemcpyAsync(&herr, c->plainb.err, sizeof herr, cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY_C(cudaMemcpyAsync(&herr, c->plainb.err, sizeof herr, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY_C(cudaStreamSynchronize(st));
     if (herr) {
       cleanup();
       return fail(GPCG_ERR_TIMEOUT, "plain path: a grid-wide barrier wait gave up");
     }
   } else if (plain) {
-    CUDA_TRY(enqueue_islands(st));
+    CUDA_TRY_C(enqueue_islands(st));
     // one scenario at a time: no batching across scenarios (the kernel with
     // extension rows, one CTA per scenario)
     for (size_t s = 0; s < S && rs == GPCG_OK; ++s) {
@@ -1524,7 +1537,7 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
     if (!c->graph || key != c->graph_key) {
       if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
       cudaGraph_t gr = nullptr;
-      CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+      CUDA_TRY_C(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
       cudaError_t e = enqueue_islands(c->cap_stream, true);
       if (e == cudaSuccess) {
         rs = f32 ? run_fdpf<float>(c, c->cap_stream, P, T, slots, f16, zs)
@@ -1539,24 +1552,24 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
       if (e != cudaSuccess) { c->graph = nullptr; cleanup(); return fail(GPCG_ERR_CUDA, "graph: %s", cudaGetErrorString(e)); }
       c->graph_key = key;
     }
-    CUDA_TRY(cudaGraphLaunch(c->graph, st));
+    CUDA_TRY_C(cudaGraphLaunch(c->graph, st));
     c->timed = true;
     g_err.clear();
     return GPCG_OK;
   } else {
-    CUDA_TRY(enqueue_islands(st));
+    CUDA_TRY_C(enqueue_islands(st));
     rs = f32 ? run_fdpf<float>(c, st, P, T, slots, f16, zs)
              : run_fdpf<double>(c, st, P, T, slots, false, zs);
   }
   if (rs != GPCG_OK) { cleanup(); return rs; }
-  CUDA_TRY(cudaEventRecord(c->ev[2], st));
+  CUDA_TRY_C(cudaEventRecord(c->ev[2], st));
   c->timed = true;
   if (c->phase_on) {
     // diagnostics requested through GPCG_PHASE_TIMERS=1: SM cycles per phase,
     // summed over CTAs (thread 0 of each CTA)
     unsigned long long h[8];
-    CUDA_TRY(cudaMemcpyAsync(h, c->phase, sizeof h, cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY_C(cudaMemcpyAsync(h, c->phase, sizeof h, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY_C(cudaStreamSynchronize(st));
     static const char* names[8] = {"init", "mismatchP", "pcgP", "updateP", "mismatchQ",
                                    "pcgQ", "updateQ", "output"};
     double tot = 0;
@@ -1566,7 +1579,7 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
     std::fprintf(stderr, " total=%.3e\n", tot);
     if (!plain) {
       unsigned long long sub[3];
-      CUDA_TRY(cudaMemcpy(sub, c->phase + 8 + 2 * S, sizeof sub, cudaMemcpyDeviceToHost));
+      CUDA_TRY_C(cudaMemcpy(sub, c->phase + 8 + 2 * S, sizeof sub, cudaMemcpyDeviceToHost));
       std::fprintf(stderr, "gpcg inner-solve cycles: spmv=%.1f%% fwd=%.1f%% bwd=%.1f%% of all\n",
                    100.0 * sub[0] / tot, 100.0 * sub[1] / tot, 100.0 * sub[2] / tot);
     }
@@ -1575,7 +1588,7 @@ static gpcg_status n1_screen_impl(gpcg_ctx* c, const int32_t* outages, int32_t n
     // per-scenario start and finish times: completion profile and the
     // longest scenarios (the tail of the persistent launch)
     std::vector<unsigned long long> tt(2 * S);
-    CUDA_TRY(cudaMemcpy(tt.data(), c->phase + 8, 2 * S * sizeof(unsigned long long),
+    CUDA_TRY_C(cudaMemcpy(tt.data(), c->phase + 8, 2 * S * sizeof(unsigned long long),
                         cudaMemcpyDeviceToHost));
     unsigned long long t0 = ~0ull, t1 = 0;
     for (size_t k = 0; k < S; ++k) {
