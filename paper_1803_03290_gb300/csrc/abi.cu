@@ -1783,7 +1783,7 @@ extern "C" gpcg_status gpcg_n1_adjoint(gpcg_ctx* c, const int32_t* outages, int3
   double* accb = accP + (size_t)slots * n;
   double* accL = accb + (size_t)slots * m;
   if (S) {
-    CUDA_TRY(cudaMemcpyAsync(c->d_outages, hout.data(), S * 4, cudaMemcpyHostToDevice, st));
+    CUDA_TRY_C(cudaMemcpyAsync(c->d_outages, hout.data(), S * 4, cudaMemcpyHostToDevice, st));
     ce = launch_islands(st, (int)S, n, c->d_outages, c->isl, P_in ? dPu : nullptr, c->d_prefP,
                         c->d_lo, c->d_cnt, c->d_coef, c->d_nogen, nullptr);
     if (ce != cudaSuccess) { cleanup(); return fail(GPCG_ERR_CUDA, "islands: %s", cudaGetErrorString(ce)); }
@@ -1898,7 +1898,7 @@ extern "C" gpcg_status gpcg_n1_dc_screen(gpcg_ctx* c, const int32_t* outages, in
     return fail(ce == cudaErrorMemoryAllocation ? GPCG_ERR_OOM : GPCG_ERR_CUDA,
                 "dc screen buffers: %s", cudaGetErrorString(ce));
   }
-  CUDA_TRY(cudaMemcpyAsync(c->d_outages, hout.data(), S * 4, cudaMemcpyHostToDevice, st));
+  CUDA_TRY_C(cudaMemcpyAsync(c->d_outages, hout.data(), S * 4, cudaMemcpyHostToDevice, st));
   ce = launch_islands(st, (int)S, n, c->d_outages, c->isl, P_in ? dPu : nullptr, c->d_prefP,
                       c->d_lo, c->d_cnt, c->d_coef, c->d_nogen, nullptr);
   if (ce != cudaSuccess) { cleanup(); return fail(GPCG_ERR_CUDA, "islands: %s", cudaGetErrorString(ce)); }
