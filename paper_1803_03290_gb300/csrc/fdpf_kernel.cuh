@@ -112,12 +112,15 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
                                                const DevMatT<VT>& MQ, LaneState<T>& L,
                                                const double* __restrict__ EF,
                                                VT* __restrict__ rhs,
-                                               Vec<unsigned long long, Geo<T>::LP>& errP,
-                                               Vec<unsigned long long, Geo<T>::LP>& errQ,
+                                               Vec<unsigned long long, Geo<T>::LP>& errP_,
+                                               Vec<unsigned long long, Geo<T>::LP>& errQ_,
                                                SwitchState<T>* SW = nullptr) {
   constexpr int LP = Geo<T>::LP;
   const Geo<T> g;
   const DevGrid& G = P.G;
+  // the running maxima in registers through the row loop (the caller's
+  // copies sit in its local memory)
+  Vec<unsigned long long, LP> errP = errP_, errQ = errQ_;
   // rows are visited in order of bus degree, so the threads of a warp run
   // neighbour loops of equal length and no FP64 work is spent on padding
   const int nrows = WITH_P ? G.n - 1 : MQ.n;
@@ -321,6 +324,8 @@ __device__ GPCG_PASS_INLINE void mismatch_pass(const FdpfParams& P, const DevMat
         rhs[(size_t)(MQ.n + 1 + s) * T + ln] = to_vt<VT>(dQ) * inv_vmag<VT>(v.x, v.y);
       }
     }
+  errP_ = errP;
+  errQ_ = errQ;
 }
 
 // (e, f) rotated through the angle d, in FP64:
