@@ -102,6 +102,21 @@ def algorithmic_bytes(info, iters, w, n_bus, n_branch):
     return vec + mis + flows + mats
 
 
+def island_split(g, iters):
+    """Mean iterations of the outages that island buses (the bridges) and of
+    the rest, outage k being branch k: the islanding scenarios' extra inner
+    iterations are reported, not asserted."""
+    from paper_1803_03290_gb300 import binding
+    br = binding.analyze(g)["bridge"][:iters.shape[0]].astype(bool)
+    out = {"outages": int(br.sum())}
+    for key, sel in (("islanding", br), ("other", ~br)):
+        if sel.any():
+            out[key] = {"mean_outer": round(float(iters[sel, 0].mean()), 3),
+                        "mean_inner_P": round(float(iters[sel, 1].mean()), 3),
+                        "mean_inner_Q": round(float(iters[sel, 2].mean()), 3)}
+    return out
+
+
 def fp64_operations(g, iters):
     """FP64 operations (an FMA counts once) the screen's FP64 parts take per
     launch, from the kernel's arithmetic: per full P mismatch 4 per adjacency
@@ -398,7 +413,8 @@ def run_gpcg(args):
                           "maxiter": int((status == 1).sum()), "diverged": int((status == 2).sum()),
                           "mean_outer": float(iters[:, 0].mean()),
                           "mean_inner_P": float(iters[:, 1].mean()),
-                          "mean_inner_Q": float(iters[:, 2].mean())},
+                          "mean_inner_Q": float(iters[:, 2].mean()),
+                          "islanding": island_split(g, iters)},
         }
         print(json.dumps(line), flush=True)
     for ci in ctxs:

@@ -100,3 +100,21 @@ def test_reference_arm_other_ranks_exit_quietly(tmp_path):
     r = _run_reference({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, tmp_path)
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_island_split_groups_bridge_outages():
+    """Outage k is branch k: the bridges' rows and the others' are averaged
+    apart (grid120's bridges from the host plan)."""
+    b = _bench()
+    from gridgen import config_grid
+    from paper_1803_03290_gb300 import binding
+    g = config_grid("grid120")
+    br = binding.analyze(g)["bridge"].astype(bool)
+    assert 0 < br.sum() < g.n_branch
+    iters = np.zeros((g.n_branch, 3), dtype=np.int32)
+    iters[br] = (3, 5, 7)
+    iters[~br] = (2, 2, 1)
+    out = b.island_split(g, iters)
+    assert out["outages"] == int(br.sum())
+    assert out["islanding"] == {"mean_outer": 3.0, "mean_inner_P": 5.0, "mean_inner_Q": 7.0}
+    assert out["other"] == {"mean_outer": 2.0, "mean_inner_P": 2.0, "mean_inner_Q": 1.0}
