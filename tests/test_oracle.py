@@ -508,6 +508,33 @@ def test_bridge_iff_ptdf_one():
     assert n_bridge > 0
 
 
+def test_bridge_outage_schur_complement_is_main_island_bprime():
+    """For a bridge outage, the base-case B' inverted and restricted to the
+    main island equals the inverse of the post-outage B' of the main island
+    (the island's Laplacian annihilates the all-ones vector, so the Schur
+    complement of the island block removes exactly the bridge's diagonal
+    term): the base-case factor is an exact preconditioner for the P-theta
+    system of every islanding outage (Sec. IV.B eq. (6), Sec. IV.C)."""
+    g = config_grid("grid120")
+    n = g.n_bus
+    keep = np.flatnonzero(g.bus_type != 2)
+    pos = -np.ones(n, int)
+    pos[keep] = np.arange(keep.size)
+    on = np.ones(g.n_branch, bool)
+    Binv = np.linalg.inv(pf.bprime(n, g.f, g.t, g.x, on, keep).toarray())
+    checked = 0
+    for l in range(g.n_branch):
+        on_l, label, isl, _, _ = screen.outage_setup(g, l)
+        if not isl.any():
+            continue
+        main = np.flatnonzero(~isl & (g.bus_type != 2))
+        Bs = pf.bprime(n, g.f, g.t, g.x, on_l, main).toarray()
+        sub = Binv[np.ix_(pos[main], pos[main])]
+        np.testing.assert_allclose(sub @ Bs, np.eye(main.size), rtol=0, atol=1e-9)
+        checked += 1
+    assert checked > 0
+
+
 def test_four_element_difference():
     """Sec. IV.B: an outage changes exactly A_ii, A_jj, A_ij, A_ji of B'
     (fewer when an endpoint is the slack; B'' only at PQ endpoints)."""
