@@ -303,6 +303,31 @@ def test_n1_grid2k_every_outage(tmp_path):
     np.testing.assert_array_equal(bits.sum(axis=1), res["n_overload"])
 
 
+@pytest.mark.parametrize("name", ["grid2k", "grid10k"])
+def test_bridge_outages_take_one_pcg_iteration_per_p_step(name):
+    """With the exact base-case factor the P-theta system of an islanding
+    (bridge) outage is preconditioned exactly on the main island: the Schur
+    complement of the island's block of the base-case B' is the post-outage
+    B' of the main island (the identity the oracle tests pin).  So every P
+    solve of such a scenario stops after one PCG iteration, at most one per
+    outer iteration, while the outages that island nothing take more."""
+    from paper_1803_03290_gb300 import binding
+    g = grid(name)
+    c = gp.GPCG(g)
+    c.base_solve()
+    outages = np.arange(g.n_branch, dtype=np.int32)
+    res = c.n1_screen(outages, outputs=("iters", "status"))
+    c.close()
+    br = binding.analyze(g)["bridge"].astype(bool)
+    ok = res["status"] == gp.SCEN_OK
+    it = res["iters"]
+    sel, rest = br & ok, ~br & ok
+    assert sel.sum() > 100 and rest.sum() > 100
+    assert (it[sel, 1] <= it[sel, 0]).all()
+    assert it[sel, 1].sum() >= 0.9 * it[sel, 0].sum()
+    assert it[rest, 1].sum() > 1.3 * it[rest, 0].sum()
+
+
 def test_edge_cases():
     g = grid("grid120")
     c = make("grid120")
