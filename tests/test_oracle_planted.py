@@ -149,3 +149,21 @@ def test_redispatch_sign_flipped_is_caught(monkeypatch):
     monkeypatch.setattr(redispatch, "redispatch", flipped)
     with pytest.raises(AssertionError):
         pins.test_redispatch_hand_derived_ring()
+
+
+def test_bridge_left_in_service_is_caught(monkeypatch):
+    """The island found, but the outaged bridge kept in the post-outage B':
+    the main island's matrix keeps the bridge's diagonal term, and the
+    Schur-complement pin fails."""
+    right = screen.outage_setup
+
+    def keeps_branch(grid, l):
+        on, label, isl, P, no_gen = right(grid, l)
+        on = on.copy()
+        if l >= 0:
+            on[l] = True
+        return on, label, isl, P, no_gen
+
+    monkeypatch.setattr(screen, "outage_setup", keeps_branch)
+    with pytest.raises(AssertionError):
+        pins.test_bridge_outage_schur_complement_is_main_island_bprime()
